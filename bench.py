@@ -1,0 +1,364 @@
+"""Benchmark of the D²IP fitting path on GB300 (one JSON line on rank 0).
+
+A step is one pass of the whole hot path over one synthetic workload: load and
+column-normalise J, set Z and the Kaiming weights, then fit the whole sequence (UPWS on
+frame 0, then every frame with TPP) through the C ABI, each DIP iteration being forward,
+data term, adjoint, backward and Adam.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload seq32|single16]
+    python bench.py --impl reference ...     (the FP64 oracle on the host cores)
+
+Multi-GPU: replicas only.  Every rank fits its own copy of the workload (weak scaling);
+there is no collective on the data path, only a barrier and a max over ranks of the time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2507_14046_gb300 import synth  # noqa: E402
+
+METRIC = "DIP iters/s and tsEIT frames/s at equal ERR; BF16 batched vs plain FP32"
+UNIT = "DIP iters/s"
+WORKLOADS = {"seq32": synth.SEQ_32, "single16": synth.SINGLE_16, "seq64": synth.SEQ_64}
+FP32_LANES_PER_SM = 128
+SMS = 152
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def iters_per_step(w) -> int:
+    return w.upws_steps + w.first_steps + (w.frames - 1) * w.later_steps
+
+
+# ------------------------------------------------------------------------------------------
+# oracle (CPU baseline and the reference arm)
+# ------------------------------------------------------------------------------------------
+
+def oracle_leg(workload: str, iters: int) -> dict:
+    """Time ``iters`` FP64 oracle DIP iterations on the workload (first frame, from the
+    Kaiming weights); returns iterations/s."""
+    from oracle import dip, network as onet
+    w = WORKLOADS[workload]
+    J, truth, V, Zin = synth.make_problem(w)
+    spec = onet.NetSpec(w.grid, w.levels, w.widths, w.c_in)
+    table = [(k, o, c, f) for _, _, k, f, o, c in onet.param_layout(spec)]
+    th = synth.kaiming_theta(table, w.seed).astype(np.float64)
+    Jn, _ = dip.normalise_columns(J)
+    Z64, dv = Zin.astype(np.float64), V[0].astype(np.float64)
+    st = dip.AdamState.fresh(th.size)
+    dip.dip_step(spec, Jn, Z64, dv, th, st, w.lr)  # warm the allocator
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        th = dip.dip_step(spec, Jn, Z64, dv, th, st, w.lr).theta
+    dt = time.perf_counter() - t0
+    return {"iters": iters, "seconds": dt, "iters_per_s": iters / dt}
+
+
+def run_oracle_subprocess(workload: str, iters: int) -> dict:
+    cores = os.cpu_count() or 1
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-leg", workload,
+                          "--oracle-iters", str(iters)], capture_output=True, text=True,
+                         env=env, check=True)
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    res["cores"] = cores
+    return res
+
+
+def oracle_iters_for(workload: str) -> int:
+    # about 10-30 s of host work per sample on a Grace host
+    return {"single16": 200, "seq32": 12, "seq64": 2}[workload]
+
+
+# ------------------------------------------------------------------------------------------
+# clocks
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int, path: str):
+        self.path = path
+        self.proc = None
+        try:
+            self.f = open(path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+
+def _err(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2507_14046_gb300 import binding as B
+
+    w = WORKLOADS[args.workload]
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    J, truth, V, Zin = synth.make_problem(w)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = B.Context(w.grid, w.levels, w.widths, w.c_in, B.D2IP_FP32, 1, device=local_rank,
+                    stream=stream.cuda_stream)
+    table = ctx.table()
+    theta0 = synth.kaiming_theta([tuple(r) for r in table], w.seed)
+    m, n, T = J.shape[0], J.shape[1], w.frames
+    Jd = torch.from_numpy(J).to(dev)
+    Zd = torch.from_numpy(Zin).to(dev)
+    thd = torch.from_numpy(theta0).to(dev)
+    Vd = torch.from_numpy(np.ascontiguousarray(V)).to(dev)
+    Sig = torch.zeros((1, T, n), device=dev)
+    res = torch.zeros((1, T), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    ctx.set_optim(w.lr)
+    hd = ctx.handle
+
+    def step(Jp, Zp, thp, Vp, Sp, Rp):
+        B.d2ip_load_J(hd, Jp, m, n, 1)
+        B.d2ip_set_input(hd, Zp, thp)
+        B.d2ip_fit_sequence(hd, Vp, T, None, w.upws_steps, w.first_steps, w.later_steps, Sp, Rp)
+
+    for _ in range(args.warmup):
+        step(Jd, Zd, thd, Vd, Sig, res)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local_rank, os.path.join(ROOT, "gpurun_out", f"clocks_r{rank}.csv")
+                          if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                          else f"/tmp/d2ip_clocks_r{rank}.csv")
+    total_ms = 0.0
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(Jd, Zd, thd, Vd, Sig, res)
+        e1.record(stream)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        total_ms = float(t.item())
+    its = iters_per_step(w)
+    value = world * args.steps * its / (total_ms / 1e3)
+    frames_s = world * args.steps * T / (total_ms / 1e3)
+
+    # equal-ERR record of the last step's reconstruction
+    S = Sig.cpu().numpy()[0]
+    errs = [_err(S[t], truth[t]) for t in range(T) if np.abs(truth[t]).max() > 0]
+
+    # roofline of the dominant kernel class, from CUDA events around every launch
+    ctx.set_input(Zd, thd)
+    prof = ctx.profile(Vd[0], 10)
+    peaks, kind = _peaks()
+    dom = max(prof, key=lambda k: prof[k][0])
+    ms, work, cnt = prof[dom]
+    avg_ms = ms / cnt
+    per_launch = work / cnt
+    if dom.startswith("conv"):
+        mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        peak = SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": per_launch / (avg_ms * 1e-3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "traffic": None,
+                "peak_source": f"FP32 FFMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                               f"{mhz:.0f} MHz (median sampled SM clock)"}
+    else:
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": per_launch / (avg_ms * 1e-3) / 1e9, "peak": peak,
+                "unit": "GB/s", "traffic": None, "peak_source": f"{kind} hbm_gbs"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dom
+    roof["avg_launch_us"] = avg_ms * 1e3
+    roof["work_per_launch"] = per_launch
+    step_ms_total = sum(v[0] for v in prof.values())
+    roof["share_of_traced_time"] = ms / step_ms_total
+    kpl = {"conv_wgrad": 2, "ln_bwd": 2, "up_bwd": 2}
+    launches_per_iter = sum(v[2] * kpl.get(k, 1) for k, v in prof.items()) / 10.0
+    fwd_launches = sum(prof[k][2] for k in ("conv_fwd", "ln_fwd", "up_fwd")) / 10.0 + 2
+    gpu_launches = int(args.steps * (its * launches_per_iter + T * fwd_launches + 1))
+
+    # end to end through the C ABI with pinned host buffers
+    Jh = torch.from_numpy(J).pin_memory()
+    Zh = torch.from_numpy(Zin).pin_memory()
+    thh = torch.from_numpy(theta0).pin_memory()
+    Vh = torch.from_numpy(np.ascontiguousarray(V)).pin_memory()
+    Sh = torch.zeros((1, T, n)).pin_memory()
+    Rh = torch.zeros((1, T), dtype=torch.float64).pin_memory()
+    step(Jh, Zh, thh, Vh, Sh, Rh)
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(Jh, Zh, thh, Vh, Sh, Rh)
+        e2e_s += time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = J.nbytes + Zin.nbytes + theta0.nbytes + V.nbytes
+    d2h = Sh.numel() * 4 + Rh.numel() * 8
+    ctx.close()
+    return {
+        "value": value, "ms_per_step": total_ms / args.steps, "frames_per_s": frames_s,
+        "e2e": {"value": world * args.steps * its / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "frames_per_s": world * args.steps * T / e2e_s},
+        "roofline": roof, "clocks": clk, "gpu_launches": gpu_launches,
+        "err": {"mean": float(np.mean(errs)), "min": float(np.min(errs)),
+                "max": float(np.max(errs)), "frames": len(errs)},
+        "profile_ms_per_iter": {k: round(v[0] / 10.0, 4) for k, v in prof.items()},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="seq32", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-leg", default=None)
+    ap.add_argument("--oracle-iters", type=int, default=5)
+    args = ap.parse_args()
+
+    if args.oracle_leg:
+        print(json.dumps(oracle_leg(args.oracle_leg, args.oracle_iters)))
+        return
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    w = WORKLOADS[args.workload]
+    its = iters_per_step(w)
+    config = {"workload": w.name + (", FP32" if args.impl == "ours" else ", FP64 oracle"),
+              "grid": list(w.grid), "m": w.m, "levels": w.levels, "widths": list(w.widths),
+              "frames": w.frames, "schedule": [w.upws_steps, w.first_steps, w.later_steps],
+              "lr": w.lr, "iters_per_step": its, "precision": "fp32",
+              "l2": "512 MB buffer written between timed steps (working set < L2)",
+              "parallelism": f"replicas x{args.gpus}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        per = oracle_iters_for(args.workload)
+        per = max(1, per // 4)
+        for _ in range(args.warmup):
+            oracle_leg(args.workload, 1)
+        tot_it, tot_s = 0, 0.0
+        for _ in range(args.steps):
+            r = oracle_leg(args.workload, per)
+            tot_it += r["iters"]
+            tot_s += r["seconds"]
+        v = tot_it / tot_s
+        cores = os.cpu_count() or 1
+        sample = (f"{per} FP64 oracle DIP iterations per step (first frame of the workload, "
+                  f"from the Kaiming weights) on {cores} host cores")
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample}}))
+        return
+
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    out = run_gpu(args, rank, world, local_rank)
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        r = run_oracle_subprocess(args.workload, oracle_iters_for(args.workload))
+        cpu = {"value": r["iters_per_s"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+               "sample": f"{r['iters']} FP64 oracle DIP iterations (first frame of the same "
+                         f"workload) in {r['seconds']:.1f} s, NumPy/BLAS on {r['cores']} "
+                         "host threads"}
+    line = {"metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config, "frames_per_s": out["frames_per_s"],
+            "e2e": out["e2e"], "roofline": out["roofline"], "cpu_baseline": cpu,
+            "clocks": out["clocks"], "gpu_launches": out["gpu_launches"], "err": out["err"],
+            "profile_ms_per_iter": out["profile_ms_per_iter"]}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

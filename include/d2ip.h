@@ -1,0 +1,247 @@
+/*
+ * d2ip.h -- C ABI of the GB300 D²IP fitting library (libd2ip.so).
+ *
+ * The library fits a sequence of 3D conductivity changes to EIT boundary voltages with a
+ * deep image prior: each frame's Delta sigma is the output of a residual 3D U-Net phi(theta | Z)
+ * fed with a fixed noise volume Z (paper Eq. 2); theta minimises the l2 data term
+ * ||J Delta sigma - Delta v||^2 of the linearised model V = J Sigma (Eq. 1, Eq. 4) with Adam;
+ * UPWS warm-starts theta on one frame (Eqs. 5-7) and TPP carries it from frame to frame
+ * (Eqs. 8-9).  Every step runs in CUDA kernels for sm_103a on one GPU.
+ *
+ * Conventions (all entry points):
+ *  - Return D2IP_OK (0) or a negative d2ip_status; no exception crosses the ABI.  Shapes and
+ *    arguments are validated on the host before any launch.  d2ip_last_error(ctx) (or
+ *    d2ip_last_error(NULL) for the context-free op calls) gives a message for the calling
+ *    context / thread.
+ *  - Volumes are channels-last: element (voxel q, channel c) at q*C + c with
+ *    q = (z*Y + y)*X + x (x fastest); a batch of B problems is B such volumes back to back.
+ *    The vectorised Delta sigma uses the same voxel order (the operator V of Eq. 2).
+ *  - Sensitivity matrix J: M x V row-major float32 (V = X*Y*Z voxels, M measurements).
+ *  - Flat parameter arena theta, in module order (see d2ip_param_table); a convolution stores
+ *    W[co][kz][ky][kx][ci] then b[co]; a LayerNorm stores gamma[c] then beta[c].
+ *  - Context calls accept HOST or DEVICE pointers for their arrays unless stated otherwise:
+ *    copies use cudaMemcpyDefault, so unified addressing tells them apart (pageable host
+ *    memory works; pinned host memory is faster).  Context calls return after their results
+ *    are written.
+ *  - Context-free op calls (d2ip_conv3d_*, d2ip_layernorm_*, ...) take DEVICE pointers only,
+ *    enqueue on `stream` (a cudaStream_t; NULL = legacy default stream) and return at once.
+ *  - The caller owns every pointer it passes; the library never frees or keeps them beyond
+ *    the call, except the context, which owns its copy of J, Z, theta and its workspace.
+ */
+#ifndef D2IP_H
+#define D2IP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int d2ip_status;
+#define D2IP_OK 0
+#define D2IP_ERR_BAD_ARG (-1)   /* null pointer, bad enum, bad hyperparameter            */
+#define D2IP_ERR_BAD_SHAPE (-2) /* inconsistent sizes (m, n, grid, widths, batch)         */
+#define D2IP_ERR_OOM (-3)       /* device allocation failed                               */
+#define D2IP_ERR_NONFINITE (-4) /* a loss or residual became NaN/Inf                      */
+#define D2IP_ERR_TIMEOUT (-5)   /* a bounded device wait ran out                          */
+#define D2IP_ERR_CUDA (-6)      /* a CUDA runtime call failed (message in last_error)     */
+#define D2IP_ERR_STATE (-7)     /* call out of order (e.g. fit before d2ip_load_J)        */
+
+#define D2IP_FP32 0 /* convolutions and J products in FP32 (SIMT), FP32 accumulation      */
+#define D2IP_BF16 1 /* convolutions on tcgen05 tensor cores, BF16 x BF16 -> FP32            */
+
+/* parameter-table kinds */
+#define D2IP_PARAM_CONV_W 0
+#define D2IP_PARAM_CONV_B 1
+#define D2IP_PARAM_LN_GAMMA 2
+#define D2IP_PARAM_LN_BETA 3
+
+typedef struct d2ip_ctx d2ip_ctx;
+
+/* ---------------------------------------------------------------------------------------
+ * Context: one network shape, one grid, one J, B independent problems fitted in lockstep.
+ * ------------------------------------------------------------------------------------- */
+
+/* Create a context on CUDA `device`.  `stream` (a cudaStream_t) is the stream all work is
+ * issued on; NULL makes the context create its own non-blocking stream (graph capture needs
+ * a stream other than the legacy default one).  *out receives the context. */
+d2ip_status d2ip_create(d2ip_ctx** out, int device, void* stream);
+/* Free the context and all its device memory.  NULL is accepted. */
+d2ip_status d2ip_destroy(d2ip_ctx* ctx);
+
+/* Reconstruction grid X x Y x Z (rows, columns, planes of Eq. 1; V = X*Y*Z voxels). */
+d2ip_status d2ip_set_grid(d2ip_ctx* ctx, int X, int Y, int Z);
+
+/* Residual 3D U-Net of `levels` levels with channel widths[levels] (each a multiple of 4,
+ * at most 128), `c_in` input channels of Z, `precision` D2IP_FP32 or D2IP_BF16, and `batch`
+ * independent problems (each with its own theta, Adam state, Z and measurements; all share
+ * the grid and J).  Layout: stem act(LN(conv3(c_in->w0))); per level a ResBlock, preceded
+ * for l > 0 by act(LN(conv3 stride 2)); decoder Up(trilinear) + concat(skip) + ResBlock with
+ * a 1x1x1 projection; tail conv1(w0->1), linear.  ResBlock: act(LN(conv3(act(LN(conv3 x))))
+ * + P x) with the second act after the residual sum.  LN over the channels of each voxel,
+ * eps 1e-5; act LeakyReLU(0.2).  (Sec. III-D: residual connections and LayerNorm.) */
+d2ip_status d2ip_set_network(d2ip_ctx* ctx, int levels, const int* widths, int c_in,
+                             int precision, int batch);
+
+/* Number of parameters P of one problem's theta. */
+d2ip_status d2ip_param_count(d2ip_ctx* ctx, long long* count);
+/* Parameter table: row r = {kind, offset, count, fan_in} (kind: D2IP_PARAM_*), written to
+ * rows[4*r .. 4*r+3] (host memory) for r < cap; *n_rows receives the number of rows. */
+d2ip_status d2ip_param_table(d2ip_ctx* ctx, long long* rows, int cap, int* n_rows);
+
+/* Copy J (m x n, n = X*Y*Z) into the context.  normalize_cols != 0 scales every column to
+ * unit l2 norm with the norm accumulated in FP64 (Eq. 1, "normalized" sensitivity); a zero
+ * column is left as is.  J may be host or device memory. */
+d2ip_status d2ip_load_J(d2ip_ctx* ctx, const float* J, int m, int n, int normalize_cols);
+/* The FP64 column norms used by the last d2ip_load_J (n values; host or device memory). */
+d2ip_status d2ip_get_colnorms(d2ip_ctx* ctx, double* out);
+
+/* Fixed network input Z ([batch][n][c_in], Eq. 2) and initial weights theta0 ([batch][P],
+ * UPWS starts from them, Sec. III-B).  Resets the Adam state. */
+d2ip_status d2ip_set_input(d2ip_ctx* ctx, const float* Z, const float* theta0);
+
+/* Adam hyperparameters (Sec. III-A; defaults lr 1e-3, 0.9, 0.999, 1e-8).  Given in double:
+ * (1 - beta) is formed in double before rounding to the float the kernels use. */
+d2ip_status d2ip_set_optim(d2ip_ctx* ctx, double lr, double beta1, double beta2, double eps);
+/* Zero the Adam moments and step count (done at the start of every fitted frame). */
+d2ip_status d2ip_reset_optimizer(d2ip_ctx* ctx);
+
+/* n_steps DIP iterations (forward phi, r = J phi - dv, loss = |r|^2/m in FP64, gradient
+ * (2/m) J^T r back through phi, Adam) on measurements dV ([batch][m]) WITHOUT resetting the
+ * Adam state.  loss_trace ([n_steps][batch], host, FP64) receives the loss at each iterate
+ * before its update, or pass NULL. */
+d2ip_status d2ip_run_steps(d2ip_ctx* ctx, const float* dV, int n_steps, double* loss_trace);
+/* Delta sigma = phi(theta | Z) at the current theta ([batch][n]). */
+d2ip_status d2ip_forward(d2ip_ctx* ctx, float* dsigma_out);
+/* dL/dtheta of the last iteration ([batch][P]). */
+d2ip_status d2ip_get_grad(d2ip_ctx* ctx, float* grad_out);
+
+/* One frame (Eqs. 4 and 6): reset Adam, n_steps iterations on dV ([batch][m]), then
+ * dsigma_out ([batch][n]) = phi at the last iterate and residual_out ([batch], FP64, host or
+ * device) = |J dsigma - dV|^2 / m.  loss_trace as in d2ip_run_steps (or NULL). */
+d2ip_status d2ip_fit_frame(d2ip_ctx* ctx, const float* dV, int n_steps, float* dsigma_out,
+                           double* residual_out, double* loss_trace);
+
+/* A time sequence (Secs. III-B, III-C): UPWS = upws_steps iterations on dV0 ([batch][m];
+ * NULL = frame 0 of V) from the current theta; then frame 0 with first_steps and each later
+ * frame with later_steps iterations, each frame starting from the previous frame's weights
+ * with a fresh Adam state.  V is [batch][T][m]; Sigma_out [batch][T][n] receives each frame's
+ * phi at its last iterate; residual_out [batch][T] (FP64) its data residual. */
+d2ip_status d2ip_fit_sequence(d2ip_ctx* ctx, const float* V, int T, const float* dV0,
+                              int upws_steps, int first_steps, int later_steps,
+                              float* Sigma_out, double* residual_out);
+
+/* Checkpoint: theta, Adam m and v ([batch][P] each) and the Adam step count.  Any pointer
+ * may be NULL to skip that part. */
+d2ip_status d2ip_get_state(d2ip_ctx* ctx, float* theta, float* adam_m, float* adam_v,
+                           int* adam_t);
+d2ip_status d2ip_set_state(d2ip_ctx* ctx, const float* theta, const float* adam_m,
+                           const float* adam_v, int adam_t);
+
+/* ERR = |est - truth| / |truth| per problem in FP64 (Sec. V-A); est, truth [batch][n]. */
+d2ip_status d2ip_err_ratio(d2ip_ctx* ctx, const float* est, const float* truth, double* out);
+
+/* Kernel classes reported by d2ip_profile_iterations, in this order. */
+#define D2IP_KCLASS_CONV_FWD 0   /* work: FLOPs (2 * out voxels * K^3 * ci * co)        */
+#define D2IP_KCLASS_CONV_DGRAD 1 /* work: FLOPs (same count as the forward)             */
+#define D2IP_KCLASS_CONV_WGRAD 2 /* work: FLOPs (same count; includes the chunk sum)    */
+#define D2IP_KCLASS_LN_FWD 3     /* work: bytes read + written                          */
+#define D2IP_KCLASS_LN_BWD 4     /* work: bytes (includes the dgamma/dbeta sum)          */
+#define D2IP_KCLASS_UP_FWD 5     /* work: bytes                                          */
+#define D2IP_KCLASS_UP_BWD 6     /* work: bytes                                          */
+#define D2IP_KCLASS_JMUL 7       /* work: bytes of J + vectors                          */
+#define D2IP_KCLASS_LOSS 8       /* work: bytes                                          */
+#define D2IP_KCLASS_JTMUL 9      /* work: bytes of J + vectors                          */
+#define D2IP_KCLASS_ADAM 10      /* work: bytes (7 x 4 per parameter)                   */
+#define D2IP_KCLASS_MISC 11      /* residual adds; work: bytes                          */
+#define D2IP_KCLASS_COUNT 12
+
+/* Tracing: run n_iters DIP iterations eagerly (no graph) on dV ([batch][m]) with a CUDA-event
+ * pair around every kernel launch, and accumulate per kernel class (D2IP_KCLASS_*) the
+ * device time in ms, the algorithmic work and the number of launches (host arrays of
+ * D2IP_KCLASS_COUNT entries).  The iterations update theta like d2ip_run_steps. */
+d2ip_status d2ip_profile_iterations(d2ip_ctx* ctx, const float* dV, int n_iters, double* ms,
+                                    double* work, long long* launches);
+
+/* Wait for the context's stream; report asynchronous CUDA errors. */
+d2ip_status d2ip_sync(d2ip_ctx* ctx);
+/* Message of the last failure of `ctx` (NULL: of the calling thread's op calls). */
+const char* d2ip_last_error(d2ip_ctx* ctx);
+
+/* ---------------------------------------------------------------------------------------
+ * Context-free ops (DEVICE pointers, asynchronous on `stream`).  Volume dims are (dz, dy,
+ * dx) of the op's input; a K^3 conv (K = 3 or 1) with stride S and zero padding (K-1)/2 has
+ * output dims (d + 2*((K-1)/2) - K)/S + 1 per axis.  Weights W are [co][K^3][ci] followed
+ * by bias [co] in a per-problem block; `w_batch_stride` is the distance between problems'
+ * blocks (0 = shared).
+ * ------------------------------------------------------------------------------------- */
+
+/* y = conv(x, W) + b  (implicit GEMM; FP32). */
+d2ip_status d2ip_conv3d_forward(const float* x, const float* W, const float* b, float* y,
+                                int batch, int dz, int dy, int dx, int ci, int co, int ksize,
+                                int stride, long long w_batch_stride, void* stream);
+/* dx (=, or += when accumulate) transposed conv of dy with W: the input gradient. */
+d2ip_status d2ip_conv3d_dgrad(const float* dy, const float* W, float* dx, int batch, int dz,
+                              int dy_, int dx_, int ci, int co, int ksize, int stride,
+                              long long w_batch_stride, int accumulate, void* stream);
+/* Workspace bytes needed by d2ip_conv3d_wgrad for these sizes. */
+long long d2ip_conv3d_wgrad_workspace(int batch, int dz, int dy, int dx, int ci, int co,
+                                      int ksize, int stride);
+/* dWb[batch][co*K^3*ci + co] (=, or +=) weight and bias gradients of conv(x) against dy
+ * (deterministic: per-chunk partial sums in `workspace`, then a fixed-order sum). */
+d2ip_status d2ip_conv3d_wgrad(const float* x, const float* dy, float* dWb, int batch, int dz,
+                              int dy_, int dx_, int ci, int co, int ksize, int stride,
+                              long long dw_batch_stride, int accumulate, void* workspace,
+                              long long workspace_bytes, void* stream);
+
+/* y = act(gamma * xhat + beta (+ resid)), xhat = (z - mean)/sqrt(var + 1e-5) over the c
+ * channels of each voxel; saves xhat ([batch][nvox][c]) and rstd ([batch][nvox]) for the
+ * backward.  gamma_beta = [gamma[c], beta[c]] per problem.  act: 0 none, 1 LeakyReLU(0.2).
+ * c must be a multiple of 4, at most 128. */
+d2ip_status d2ip_layernorm_act_forward(const float* z, const float* gamma_beta,
+                                       const float* resid, float* y, float* xhat, float* rstd,
+                                       int batch, long long nvox, int c, int act,
+                                       long long gb_batch_stride, void* stream);
+long long d2ip_layernorm_workspace(int batch, long long nvox, int c);
+/* Backward of the above given dy = dL/dy: dpre = dy * act'(act_out) (act_out NULL: no act),
+ * dt = dpre (optional, the residual-branch gradient), dz = LN backward of dpre, and
+ * dgamma_beta[batch][2c] (=, or +=) sum over voxels of (dpre * xhat, dpre). */
+d2ip_status d2ip_layernorm_act_backward(const float* dy, const float* act_out,
+                                        const float* xhat, const float* rstd,
+                                        const float* gamma_beta, float* dz, float* dt,
+                                        float* dgamma_beta, int batch, long long nvox, int c,
+                                        long long gb_batch_stride, int accumulate,
+                                        void* workspace, long long workspace_bytes,
+                                        void* stream);
+
+/* cat[:, :cu] = trilinear(low (lz,ly,lx) -> (oz,oy,ox)), half-pixel centres, source index
+ * clamped at 0 (PyTorch align_corners=False with an explicit size); cat[:, cu:] = skip. */
+d2ip_status d2ip_upsample_concat_forward(const float* low, const float* skip, float* cat,
+                                         int batch, int lz, int ly, int lx, int oz, int oy,
+                                         int ox, int cu, int cs, void* stream);
+/* Adjoint: dlow = upsample^T(dcat[:, :cu]) (a gather, deterministic); dskip = dcat[:, cu:]
+ * (dskip may be NULL). */
+d2ip_status d2ip_upsample_concat_backward(const float* dcat, float* dlow, float* dskip,
+                                          int batch, int lz, int ly, int lx, int oz, int oy,
+                                          int ox, int cu, int cs, void* stream);
+
+/* Data term of Eq. 4: r[b] = J x[b] - dv[b] (FP32, x [batch][n]) and, when loss is not NULL,
+ * loss[b] = |r[b]|^2 / m accumulated in FP64 (device memory). */
+d2ip_status d2ip_sensitivity_residual(const float* J, const float* x, const float* dv,
+                                      float* r, double* loss, int batch, int m, int n,
+                                      void* stream);
+/* g[b] = scale * J^T r[b]  (scale = 2/m gives the gradient of the mean-square data term). */
+d2ip_status d2ip_sensitivity_adjoint(const float* J, const float* r, float* g, float scale,
+                                     int batch, int m, int n, void* stream);
+/* In place: J[:, j] /= |J[:, j]|_2 with the norm in FP64; colnorm[j] receives it. */
+d2ip_status d2ip_normalize_columns(float* J, double* colnorm, int m, int n, void* stream);
+/* One Adam step (bias-corrected, step number t >= 1) over `count` parameters. */
+d2ip_status d2ip_adam_update(float* theta, const float* g, float* m, float* v,
+                             long long count, double lr, double beta1, double beta2,
+                             double eps, int t, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* D2IP_H */

@@ -1,0 +1,96 @@
+// Shared definitions for the D²IP CUDA library (device side and launchers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <climits>
+#include <cstdint>
+
+namespace d2ip {
+
+struct Dims3 {
+  int z, y, x;
+  __host__ __device__ long long count() const { return (long long)z * y * x; }
+};
+
+// Output size of a K^3 convolution, stride S, zero padding (K-1)/2: ceil(D/S) for K = 3.
+__host__ __device__ inline Dims3 conv_out_dims(Dims3 in, int K, int S) {
+  const int p = (K - 1) / 2;
+  return Dims3{(in.z + 2 * p - K) / S + 1, (in.y + 2 * p - K) / S + 1,
+               (in.x + 2 * p - K) / S + 1};
+}
+
+inline long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
+
+constexpr float kLeakySlope = 0.2f;
+constexpr float kLnEps = 1e-5f;
+
+// ---------------------------------------------------------------------------------
+// Launchers (all asynchronous on `stream`, all capturable in a CUDA graph).
+// Tensors are channels-last: element (voxel q, channel c) at q*C + c, voxel
+// q = (z*Y + y)*X + x.  `*_bs` are batch strides in elements.  Return cudaError_t of
+// the launch.
+// ---------------------------------------------------------------------------------
+
+// y = conv(x, W) + b.  W is [Co][K^3][Ci] (tap-major, channel fastest).
+cudaError_t conv3d_fwd_f32(const float* x, const float* W, const float* bias, float* y,
+                           int B, Dims3 din, int Ci, int Co, int K, int S,
+                           long long x_bs, long long y_bs, long long w_bs,
+                           cudaStream_t stream);
+// dx (=|+=) conv^T(dy, W).
+cudaError_t conv3d_dgrad_f32(const float* dy, const float* W, float* dx, int B, Dims3 din,
+                             int Ci, int Co, int K, int S, long long dy_bs, long long dx_bs,
+                             long long w_bs, int accumulate, cudaStream_t stream);
+// Per-chunk partial weight gradients: part[b][chunk][Co*K^3*Ci + Co] (W part then bias).
+long long conv3d_wgrad_chunks(Dims3 din, int K, int S);
+cudaError_t conv3d_wgrad_partial_f32(const float* x, const float* dy, float* part, int B,
+                                     Dims3 din, int Ci, int Co, int K, int S,
+                                     long long x_bs, long long dy_bs, cudaStream_t stream);
+// out[b*out_bs + j] (=|+=) sum_r part[(b*R + r)*N + j]
+cudaError_t reduce_rows_f32(const float* part, float* out, int B, long long R, long long N,
+                            long long out_bs, int accumulate, cudaStream_t stream);
+
+// LayerNorm over channels (+ residual) (+ LeakyReLU).
+int layernorm_bwd_blocks(long long nvox, int C);
+cudaError_t layernorm_act_fwd_f32(const float* z, const float* gamma, const float* resid,
+                                  float* y, float* xhat, float* rstd, int B, long long nvox,
+                                  int C, int act, long long g_bs, cudaStream_t stream);
+// part: [B][blocks][2C] partial (dgamma, dbeta).
+cudaError_t layernorm_act_bwd_f32(const float* dy, const float* act_out, const float* xhat,
+                                  const float* rstd, const float* gamma, float* dz, float* dt,
+                                  float* part, int B, long long nvox, int C, long long g_bs,
+                                  cudaStream_t stream);
+
+// cat[:, :Cu] = trilinear(low -> dout), cat[:, Cu:] = skip.
+cudaError_t upsample_concat_fwd_f32(const float* low, const float* skip, float* cat, int B,
+                                    Dims3 dlow, Dims3 dout, int Cu, int Cs,
+                                    cudaStream_t stream);
+// dlow = adjoint of the upsample applied to dcat[:, :Cu]; dskip = dcat[:, Cu:].
+cudaError_t upsample_concat_bwd_f32(const float* dcat, float* dlow, float* dskip, int B,
+                                    Dims3 dlow_dims, Dims3 dout, int Cu, int Cs,
+                                    cudaStream_t stream);
+cudaError_t add_inplace_f32(float* y, const float* x, long long count, cudaStream_t stream);
+
+// Data term.  r[b] = J x[b] - dv[b];  g[b] = scale * J^T r[b];  loss in FP64.
+cudaError_t jmul_residual_f32(const float* J, const float* x, const float* dv, float* r,
+                              int B, int m, int n, long long x_bs, cudaStream_t stream);
+// Per-device kernel attributes (opt-in shared memory); call once per device before launches.
+cudaError_t prepare_pointwise_kernels();
+cudaError_t jtmul_f32(const float* J, const float* r, float* g, float scale, int B, int m,
+                      int n, long long g_bs, cudaStream_t stream);
+// loss[b] = (1/m) sum r^2 (FP64); optional trace slot; optional Adam step counter bump;
+// status bit 1 set when a loss is not finite.
+cudaError_t residual_loss_f64(const float* r, double* loss, double* trace, int* trace_pos,
+                              int* adam_t, int* status, int B, int m, cudaStream_t stream);
+cudaError_t normalize_columns_f64(float* J, double* colnorm, int m, int n,
+                                  cudaStream_t stream);
+cudaError_t err_ratio_f64(const float* est, const float* truth, double* out, int B,
+                          long long n, cudaStream_t stream);
+
+// Adam over a flat arena; the step count t is read from device memory (after the bump
+// done by residual_loss_f64), or taken from `t_host` when t_dev is null.
+cudaError_t adam_step_f32(float* theta, const float* g, float* m, float* v, long long count,
+                          double lr, double beta1, double beta2, double eps, const int* t_dev,
+                          int t_host, cudaStream_t stream);
+
+}  // namespace d2ip

@@ -1,0 +1,551 @@
+// LayerNorm(+residual)(+LeakyReLU) forward/backward, trilinear up + concat and its adjoint,
+// the data term (J x - dv, J^T r, FP64 loss), FP64 column normalisation of J, ERR, Adam.
+#include "common.cuh"
+
+namespace d2ip {
+namespace {
+
+// ------------------------------------------------------------------------------------
+// LayerNorm over the channel vector of a voxel.  A group of GP lanes (power of two)
+// serves one voxel; lane l holds channels 4l .. 4l+3 (C <= 4*GP, C % 4 == 0).
+// ------------------------------------------------------------------------------------
+template <int GP>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = GP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, GP);
+  return v;
+}
+
+template <int GP>
+__global__ void __launch_bounds__(256)
+ln_fwd_kernel(const float* __restrict__ z, const float* __restrict__ gamma,
+              const float* __restrict__ resid, float* __restrict__ y, float* __restrict__ xhat,
+              float* __restrict__ rstd, long long nvox, int C, int act, long long g_bs) {
+  const int b = blockIdx.y;
+  const long long off = (long long)b * nvox * C;
+  const float* beta = gamma + b * g_bs + C;
+  gamma += b * g_bs;
+  const int lane = threadIdx.x % GP;
+  const long long vox = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / GP;
+  const int c = lane * 4;
+  const bool on = vox < nvox && c < C;
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (on) v = *reinterpret_cast<const float4*>(z + off + vox * C + c);
+  const float inv_c = 1.0f / (float)C;
+  const float mean = group_sum<GP>(v.x + v.y + v.z + v.w) * inv_c;
+  float4 d = make_float4(v.x - mean, v.y - mean, v.z - mean, v.w - mean);
+  if (!on) d = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float var = group_sum<GP>(d.x * d.x + d.y * d.y + d.z * d.z + d.w * d.w) * inv_c;
+  const float rs = 1.0f / sqrtf(var + kLnEps);
+  if (!on) return;
+  const float4 g = *reinterpret_cast<const float4*>(gamma + c);
+  const float4 be = *reinterpret_cast<const float4*>(beta + c);
+  float4 xh = make_float4(d.x * rs, d.y * rs, d.z * rs, d.w * rs);
+  float4 o = make_float4(fmaf(xh.x, g.x, be.x), fmaf(xh.y, g.y, be.y), fmaf(xh.z, g.z, be.z),
+                         fmaf(xh.w, g.w, be.w));
+  if (resid) {
+    const float4 r = *reinterpret_cast<const float4*>(resid + off + vox * C + c);
+    o.x += r.x;
+    o.y += r.y;
+    o.z += r.z;
+    o.w += r.w;
+  }
+  if (act) {
+    o.x = o.x > 0.f ? o.x : kLeakySlope * o.x;
+    o.y = o.y > 0.f ? o.y : kLeakySlope * o.y;
+    o.z = o.z > 0.f ? o.z : kLeakySlope * o.z;
+    o.w = o.w > 0.f ? o.w : kLeakySlope * o.w;
+  }
+  *reinterpret_cast<float4*>(y + off + vox * C + c) = o;
+  *reinterpret_cast<float4*>(xhat + off + vox * C + c) = xh;
+  if (lane == 0) rstd[(long long)b * nvox + vox] = rs;
+}
+
+// dpre = dy * act'(.) (mask from the stored activation output), dz = LN backward of dpre,
+// dt = dpre (optional); per-block partial sums of (dgamma, dbeta).
+template <int GP>
+__global__ void __launch_bounds__(256)
+ln_bwd_kernel(const float* __restrict__ dy, const float* __restrict__ act_out,
+              const float* __restrict__ xhat, const float* __restrict__ rstd,
+              const float* __restrict__ gamma, float* __restrict__ dz, float* __restrict__ dt,
+              float* __restrict__ part, long long nvox, int C, long long g_bs) {
+  constexpr int kGroups = 256 / GP;
+  __shared__ float red[kGroups][2 * 4 * GP];
+  const int b = blockIdx.y;
+  const long long off = (long long)b * nvox * C;
+  gamma += b * g_bs;
+  const int lane = threadIdx.x % GP;
+  const int grp = threadIdx.x / GP;
+  const int c = lane * 4;
+  const bool con = c < C;
+  float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (con) g = *reinterpret_cast<const float4*>(gamma + c);
+  const float inv_c = 1.0f / (float)C;
+  float ag[4] = {0.f, 0.f, 0.f, 0.f}, ab[4] = {0.f, 0.f, 0.f, 0.f};
+  const long long step = (long long)gridDim.x * kGroups;
+  for (long long base = (long long)blockIdx.x * kGroups; base < nvox; base += step) {
+    const long long vox = base + grp;
+    const bool on = vox < nvox && con;
+    float4 d = make_float4(0.f, 0.f, 0.f, 0.f), xh = d;
+    float rs = 0.f;
+    if (on) {
+      d = *reinterpret_cast<const float4*>(dy + off + vox * C + c);
+      xh = *reinterpret_cast<const float4*>(xhat + off + vox * C + c);
+      rs = rstd[(long long)b * nvox + vox];
+      if (act_out) {
+        const float4 a = *reinterpret_cast<const float4*>(act_out + off + vox * C + c);
+        d.x = a.x > 0.f ? d.x : kLeakySlope * d.x;
+        d.y = a.y > 0.f ? d.y : kLeakySlope * d.y;
+        d.z = a.z > 0.f ? d.z : kLeakySlope * d.z;
+        d.w = a.w > 0.f ? d.w : kLeakySlope * d.w;
+      }
+      if (dt) *reinterpret_cast<float4*>(dt + off + vox * C + c) = d;
+    }
+    const float4 dx = make_float4(d.x * g.x, d.y * g.y, d.z * g.z, d.w * g.w);
+    const float s1 = group_sum<GP>(dx.x + dx.y + dx.z + dx.w) * inv_c;
+    const float s2 =
+        group_sum<GP>(dx.x * xh.x + dx.y * xh.y + dx.z * xh.z + dx.w * xh.w) * inv_c;
+    if (on) {
+      float4 o;
+      o.x = rs * (dx.x - s1 - xh.x * s2);
+      o.y = rs * (dx.y - s1 - xh.y * s2);
+      o.z = rs * (dx.z - s1 - xh.z * s2);
+      o.w = rs * (dx.w - s1 - xh.w * s2);
+      *reinterpret_cast<float4*>(dz + off + vox * C + c) = o;
+      ag[0] += d.x * xh.x;
+      ag[1] += d.y * xh.y;
+      ag[2] += d.z * xh.z;
+      ag[3] += d.w * xh.w;
+      ab[0] += d.x;
+      ab[1] += d.y;
+      ab[2] += d.z;
+      ab[3] += d.w;
+    }
+  }
+  for (int i = 0; i < 4; ++i) {
+    red[grp][c + i] = ag[i];
+    red[grp][4 * GP + c + i] = ab[i];
+  }
+  __syncthreads();
+  float* out = part + ((long long)b * gridDim.x + blockIdx.x) * 2 * C;
+  for (int ch = threadIdx.x; ch < 2 * C; ch += blockDim.x) {
+    const int col = ch < C ? ch : 4 * GP + (ch - C);
+    float s = 0.f;
+    for (int q = 0; q < kGroups; ++q) s += red[q][col];
+    out[ch] = s;
+  }
+}
+
+inline int lanes_for(int C) {
+  const int g = (C + 3) / 4;
+  int p = 1;
+  while (p < g) p <<= 1;
+  return p;
+}
+
+// ------------------------------------------------------------------------------------
+// trilinear resampling, half-pixel centres, explicit target size
+// ------------------------------------------------------------------------------------
+struct AxisW {
+  int i0, i1;
+  float w1;
+};
+
+// src = ((2o+1) s_in - s_out) / (2 s_out), clamped at 0: integer form, exact index map.
+__device__ __forceinline__ AxisW axis_map(int o, int s_in, int s_out) {
+  long long num = (long long)(2 * o + 1) * s_in - s_out;
+  if (num < 0) num = 0;
+  const long long den = 2LL * s_out;
+  AxisW a;
+  a.i0 = (int)(num / den);
+  a.w1 = (float)(num - (long long)a.i0 * den) / (float)den;
+  a.i1 = a.i0 + 1 < s_in ? a.i0 + 1 : s_in - 1;
+  return a;
+}
+
+__global__ void up_concat_fwd_kernel(const float* __restrict__ low,
+                                     const float* __restrict__ skip, float* __restrict__ cat,
+                                     Dims3 dl, Dims3 dout, int Cu, int Cs) {
+  const int b = blockIdx.y;
+  const int Ct = Cu + Cs;
+  const long long nout = dout.count();
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nout * Ct) return;
+  const long long vox = e / Ct;
+  const int c = (int)(e % Ct);
+  float val;
+  if (c >= Cu) {
+    val = skip[((long long)b * nout + vox) * Cs + (c - Cu)];
+  } else {
+    const int ox = (int)(vox % dout.x);
+    const long long r = vox / dout.x;
+    const int oy = (int)(r % dout.y), oz = (int)(r / dout.y);
+    const AxisW az = axis_map(oz, dl.z, dout.z), ay = axis_map(oy, dl.y, dout.y),
+                ax = axis_map(ox, dl.x, dout.x);
+    const float* L = low + (long long)b * dl.count() * Cu + c;
+    const int zs[2] = {az.i0, az.i1}, ys[2] = {ay.i0, ay.i1}, xs[2] = {ax.i0, ax.i1};
+    const float wz[2] = {1.f - az.w1, az.w1}, wy[2] = {1.f - ay.w1, ay.w1},
+                wx[2] = {1.f - ax.w1, ax.w1};
+    val = 0.f;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+          val += wz[i] * wy[j] * wx[k] *
+                 L[(((long long)zs[i] * dl.y + ys[j]) * dl.x + xs[k]) * Cu];
+  }
+  cat[((long long)b * nout + vox) * Ct + c] = val;
+}
+
+// Output positions along one axis that read input index i, with their weights.
+__device__ __forceinline__ int axis_sources(int i, int s_in, int s_out, int* os, float* ws) {
+  const double r = (double)s_out / (double)s_in;
+  int lo = (int)floor((i - 0.5) * r - 0.5) - 1;
+  int hi = (int)ceil((i + 1.5) * r - 0.5) + 1;
+  if (lo < 0) lo = 0;
+  if (hi > s_out - 1) hi = s_out - 1;
+  int n = 0;
+  for (int o = lo; o <= hi && n < 8; ++o) {
+    const AxisW a = axis_map(o, s_in, s_out);
+    float w = 0.f;
+    if (a.i0 == i) w += 1.f - a.w1;
+    if (a.i1 == i) w += a.w1;
+    if (a.i0 == i || a.i1 == i) {
+      os[n] = o;
+      ws[n] = w;
+      ++n;
+    }
+  }
+  return n;
+}
+
+__global__ void up_bwd_kernel(const float* __restrict__ dcat, float* __restrict__ dlow,
+                              Dims3 dl, Dims3 dout, int Cu, int Cs) {
+  const int b = blockIdx.y;
+  const int Ct = Cu + Cs;
+  const long long nl = dl.count();
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nl * Cu) return;
+  const long long vox = e / Cu;
+  const int c = (int)(e % Cu);
+  const int ix = (int)(vox % dl.x);
+  const long long r = vox / dl.x;
+  const int iy = (int)(r % dl.y), iz = (int)(r / dl.y);
+  int oz[8], oy[8], ox[8];
+  float wz[8], wy[8], wx[8];
+  const int nz = axis_sources(iz, dl.z, dout.z, oz, wz);
+  const int ny = axis_sources(iy, dl.y, dout.y, oy, wy);
+  const int nx = axis_sources(ix, dl.x, dout.x, ox, wx);
+  const float* D = dcat + (long long)b * dout.count() * Ct + c;
+  float acc = 0.f;
+  for (int a = 0; a < nz; ++a)
+    for (int q = 0; q < ny; ++q)
+      for (int k = 0; k < nx; ++k)
+        acc += wz[a] * wy[q] * wx[k] *
+               D[(((long long)oz[a] * dout.y + oy[q]) * dout.x + ox[k]) * Ct];
+  dlow[((long long)b * nl + vox) * Cu + c] = acc;
+}
+
+__global__ void split_skip_kernel(const float* __restrict__ dcat, float* __restrict__ dskip,
+                                  long long nout, int Cu, int Cs) {
+  const int b = blockIdx.y;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nout * Cs) return;
+  const long long vox = e / Cs;
+  const int c = (int)(e % Cs);
+  dskip[((long long)b * nout + vox) * Cs + c] =
+      dcat[((long long)b * nout + vox) * (Cu + Cs) + Cu + c];
+}
+
+__global__ void add_kernel(float* __restrict__ y, const float* __restrict__ x, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += x[i];
+}
+
+// ------------------------------------------------------------------------------------
+// data term
+// ------------------------------------------------------------------------------------
+constexpr int kJB = 8;  // problems per block in the J kernels
+constexpr int kJtmulMaxSmem = 200 * 1024;
+
+__global__ void __launch_bounds__(256)
+jmul_kernel(const float* __restrict__ J, const float* __restrict__ x,
+            const float* __restrict__ dv, float* __restrict__ r, int B, int m, int n,
+            long long x_bs) {
+  __shared__ float red[kJB][8];
+  const int i = blockIdx.x;
+  const int b0 = blockIdx.y * kJB;
+  const int nb = B - b0 < kJB ? B - b0 : kJB;
+  const float* row = J + (long long)i * n;
+  float acc[kJB];
+#pragma unroll
+  for (int q = 0; q < kJB; ++q) acc[q] = 0.f;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const float a = row[j];
+#pragma unroll
+    for (int q = 0; q < kJB; ++q)
+      if (q < nb) acc[q] = fmaf(a, x[(long long)(b0 + q) * x_bs + j], acc[q]);
+  }
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+#pragma unroll
+  for (int q = 0; q < kJB; ++q) {
+    float v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (l == 0) red[q][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nb) {
+    const int q = threadIdx.x;
+    float s = 0.f;
+    for (int k = 0; k < 8; ++k) s += red[q][k];
+    r[(long long)(b0 + q) * m + i] = s - dv[(long long)(b0 + q) * m + i];
+  }
+}
+
+__global__ void __launch_bounds__(256)
+jtmul_kernel(const float* __restrict__ J, const float* __restrict__ r, float* __restrict__ g,
+             float scale, int B, int m, int n, long long g_bs) {
+  extern __shared__ float rs[];  // [kJB][m]
+  const int b0 = blockIdx.y * kJB;
+  const int nb = B - b0 < kJB ? B - b0 : kJB;
+  for (int e = threadIdx.x; e < nb * m; e += blockDim.x) rs[e] = r[(long long)b0 * m + e];
+  __syncthreads();
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  float acc[kJB];
+#pragma unroll
+  for (int q = 0; q < kJB; ++q) acc[q] = 0.f;
+  for (int i = 0; i < m; ++i) {
+    const float a = J[(long long)i * n + j];
+#pragma unroll
+    for (int q = 0; q < kJB; ++q)
+      if (q < nb) acc[q] = fmaf(a, rs[q * m + i], acc[q]);
+  }
+  for (int q = 0; q < nb; ++q) g[(long long)(b0 + q) * g_bs + j] = scale * acc[q];
+}
+
+__global__ void __launch_bounds__(256)
+loss_kernel(const float* __restrict__ r, double* __restrict__ loss, double* __restrict__ trace,
+            int* __restrict__ trace_pos, int* __restrict__ adam_t, int* __restrict__ status,
+            int B, int m) {
+  __shared__ double red[256];
+  const int pos = trace_pos ? *trace_pos : 0;
+  bool bad = false;
+  for (int b = 0; b < B; ++b) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const double v = (double)r[(long long)b * m + i];
+      s += v * v;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const double L = red[0] / (double)m;
+      loss[b] = L;
+      if (trace) trace[(long long)pos * B + b] = L;
+      if (!isfinite(L)) bad = true;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (trace_pos) *trace_pos = pos + 1;
+    if (adam_t) *adam_t += 1;
+    if (bad && status) *status |= 1;
+  }
+}
+
+__global__ void colnorm_kernel(float* __restrict__ J, double* __restrict__ cn, int m, int n) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double s = 0.0;
+  for (int i = 0; i < m; ++i) {
+    const double v = (double)J[(long long)i * n + j];
+    s += v * v;
+  }
+  const double c = sqrt(s);
+  cn[j] = c;
+  if (c > 0.0)
+    for (int i = 0; i < m; ++i) J[(long long)i * n + j] = (float)((double)J[(long long)i * n + j] / c);
+}
+
+__global__ void err_kernel(const float* __restrict__ est, const float* __restrict__ truth,
+                           double* __restrict__ out, long long n) {
+  __shared__ double ra[256], rb[256];
+  const int b = blockIdx.x;
+  double a = 0.0, t = 0.0;
+  for (long long j = threadIdx.x; j < n; j += blockDim.x) {
+    const double e = (double)est[b * n + j], g = (double)truth[b * n + j];
+    a += (e - g) * (e - g);
+    t += g * g;
+  }
+  ra[threadIdx.x] = a;
+  rb[threadIdx.x] = t;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      ra[threadIdx.x] += ra[threadIdx.x + o];
+      rb[threadIdx.x] += rb[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[b] = sqrt(ra[0] / rb[0]);
+}
+
+__global__ void __launch_bounds__(256)
+adam_kernel(float* __restrict__ theta, const float* __restrict__ g, float* __restrict__ m,
+            float* __restrict__ v, long long count, float lr, double b1, double b2, float eps,
+            const int* __restrict__ t_dev, int t_host) {
+  // beta and (1 - beta) are rounded to float from double so that (1 - 0.999) keeps full
+  // float precision; the bias corrections 1 - beta^t are formed in double.
+  __shared__ float bc[2];
+  if (threadIdx.x == 0) {
+    const int t = t_dev ? *t_dev : t_host;
+    bc[0] = (float)(1.0 / (1.0 - pow(b1, (double)t)));
+    bc[1] = (float)(1.0 / (1.0 - pow(b2, (double)t)));
+  }
+  __syncthreads();
+  const float ibc1 = bc[0], ibc2 = bc[1];
+  const float b1f = (float)b1, b2f = (float)b2, o1 = (float)(1.0 - b1), o2 = (float)(1.0 - b2);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = fmaf(b1f, m[i], o1 * gi);
+    const float vi = fmaf(b2f, v[i], o2 * gi * gi);
+    m[i] = mi;
+    v[i] = vi;
+    theta[i] -= lr * (mi * ibc1) / (sqrtf(vi * ibc2) + eps);
+  }
+}
+
+}  // namespace
+
+int layernorm_bwd_blocks(long long nvox, int C) {
+  const int gp = lanes_for(C);
+  const long long need = ceil_div(nvox, 256 / gp);
+  return (int)(need < 256 ? need : 256);
+}
+
+cudaError_t layernorm_act_fwd_f32(const float* z, const float* gamma, const float* resid,
+                                  float* y, float* xhat, float* rstd, int B, long long nvox,
+                                  int C, int act, long long g_bs, cudaStream_t stream) {
+  if (C % 4 != 0 || C > 128) return cudaErrorInvalidValue;
+  const int gp = lanes_for(C);
+  dim3 grid((unsigned)ceil_div(nvox * gp, 256), B);
+#define D2IP_LNF(G) \
+  ln_fwd_kernel<G><<<grid, 256, 0, stream>>>(z, gamma, resid, y, xhat, rstd, nvox, C, act, g_bs)
+  switch (gp) {
+    case 1: D2IP_LNF(1); break;
+    case 2: D2IP_LNF(2); break;
+    case 4: D2IP_LNF(4); break;
+    case 8: D2IP_LNF(8); break;
+    case 16: D2IP_LNF(16); break;
+    default: D2IP_LNF(32); break;
+  }
+#undef D2IP_LNF
+  return cudaGetLastError();
+}
+
+cudaError_t layernorm_act_bwd_f32(const float* dy, const float* act_out, const float* xhat,
+                                  const float* rstd, const float* gamma, float* dz, float* dt,
+                                  float* part, int B, long long nvox, int C, long long g_bs,
+                                  cudaStream_t stream) {
+  if (C % 4 != 0 || C > 128) return cudaErrorInvalidValue;
+  const int gp = lanes_for(C);
+  dim3 grid(layernorm_bwd_blocks(nvox, C), B);
+#define D2IP_LNB(G)                                                                          \
+  ln_bwd_kernel<G><<<grid, 256, 0, stream>>>(dy, act_out, xhat, rstd, gamma, dz, dt, part, \
+                                             nvox, C, g_bs)
+  switch (gp) {
+    case 1: D2IP_LNB(1); break;
+    case 2: D2IP_LNB(2); break;
+    case 4: D2IP_LNB(4); break;
+    case 8: D2IP_LNB(8); break;
+    case 16: D2IP_LNB(16); break;
+    default: D2IP_LNB(32); break;
+  }
+#undef D2IP_LNB
+  return cudaGetLastError();
+}
+
+cudaError_t upsample_concat_fwd_f32(const float* low, const float* skip, float* cat, int B,
+                                    Dims3 dlow, Dims3 dout, int Cu, int Cs,
+                                    cudaStream_t stream) {
+  const long long total = dout.count() * (Cu + Cs);
+  dim3 grid((unsigned)ceil_div(total, 256), B);
+  up_concat_fwd_kernel<<<grid, 256, 0, stream>>>(low, skip, cat, dlow, dout, Cu, Cs);
+  return cudaGetLastError();
+}
+
+cudaError_t upsample_concat_bwd_f32(const float* dcat, float* dlow, float* dskip, int B,
+                                    Dims3 dlow_dims, Dims3 dout, int Cu, int Cs,
+                                    cudaStream_t stream) {
+  dim3 g1((unsigned)ceil_div(dlow_dims.count() * Cu, 256), B);
+  up_bwd_kernel<<<g1, 256, 0, stream>>>(dcat, dlow, dlow_dims, dout, Cu, Cs);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !dskip || Cs == 0) return e;
+  dim3 g2((unsigned)ceil_div(dout.count() * Cs, 256), B);
+  split_skip_kernel<<<g2, 256, 0, stream>>>(dcat, dskip, dout.count(), Cu, Cs);
+  return cudaGetLastError();
+}
+
+cudaError_t add_inplace_f32(float* y, const float* x, long long count, cudaStream_t stream) {
+  add_kernel<<<(unsigned)ceil_div(count, 256), 256, 0, stream>>>(y, x, count);
+  return cudaGetLastError();
+}
+
+cudaError_t jmul_residual_f32(const float* J, const float* x, const float* dv, float* r,
+                              int B, int m, int n, long long x_bs, cudaStream_t stream) {
+  dim3 grid(m, (unsigned)ceil_div(B, kJB));
+  jmul_kernel<<<grid, 256, 0, stream>>>(J, x, dv, r, B, m, n, x_bs);
+  return cudaGetLastError();
+}
+
+cudaError_t jtmul_f32(const float* J, const float* r, float* g, float scale, int B, int m,
+                      int n, long long g_bs, cudaStream_t stream) {
+  const size_t smem = (size_t)kJB * m * sizeof(float);
+  if (smem > (size_t)kJtmulMaxSmem) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)ceil_div(n, 256), (unsigned)ceil_div(B, kJB));
+  jtmul_kernel<<<grid, 256, smem, stream>>>(J, r, g, scale, B, m, n, g_bs);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_pointwise_kernels() {
+  return cudaFuncSetAttribute(jtmul_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kJtmulMaxSmem);
+}
+
+cudaError_t residual_loss_f64(const float* r, double* loss, double* trace, int* trace_pos,
+                              int* adam_t, int* status, int B, int m, cudaStream_t stream) {
+  loss_kernel<<<1, 256, 0, stream>>>(r, loss, trace, trace_pos, adam_t, status, B, m);
+  return cudaGetLastError();
+}
+
+cudaError_t normalize_columns_f64(float* J, double* colnorm, int m, int n,
+                                  cudaStream_t stream) {
+  colnorm_kernel<<<(unsigned)ceil_div(n, 128), 128, 0, stream>>>(J, colnorm, m, n);
+  return cudaGetLastError();
+}
+
+cudaError_t err_ratio_f64(const float* est, const float* truth, double* out, int B,
+                          long long n, cudaStream_t stream) {
+  err_kernel<<<B, 256, 0, stream>>>(est, truth, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t adam_step_f32(float* theta, const float* g, float* m, float* v, long long count,
+                          double lr, double beta1, double beta2, double eps, const int* t_dev,
+                          int t_host, cudaStream_t stream) {
+  long long blocks = ceil_div(count, 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  adam_kernel<<<(unsigned)blocks, 256, 0, stream>>>(theta, g, m, v, count, (float)lr, beta1,
+                                                    beta2, (float)eps, t_dev, t_host);
+  return cudaGetLastError();
+}
+
+}  // namespace d2ip

@@ -1,0 +1,1193 @@
+// Runtime of the D²IP fitting library: the network plan (module order, parameter arena,
+// activation and gradient buffers), the launch sequences of one DIP iteration, CUDA-graph
+// capture and replay, the UPWS/TPP sequence driver and the C-ABI entry points.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/d2ip.h"
+#include "common.cuh"
+#include "conv_bf16.cuh"
+
+using namespace d2ip;
+
+namespace {
+
+thread_local std::string g_op_error;
+
+constexpr int kTraceCap = 4096;  // device loss-trace ring (iterations)
+constexpr long long kAlign = 64;  // floats (256 bytes)
+
+long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
+
+struct ConvL {
+  int ci = 0, co = 0, k = 3, s = 1;
+  Dims3 din{}, dout{};
+  long long w_off = 0;  // bias follows at w_off + co*k^3*ci
+  long long wcount() const { return (long long)co * k * k * k * ci; }
+};
+
+struct LnL {
+  int c = 0;
+  long long g_off = 0;  // beta follows at g_off + c
+};
+
+struct Unit {  // act(LN(conv(x))): the stem and the stride-2 down convolutions
+  ConvL conv;
+  LnL ln;
+  int lvl_in = 0, lvl_out = 0;
+  const float* x = nullptr;
+  float *xh = nullptr, *rs = nullptr, *a = nullptr;
+};
+
+struct Res {  // act(LN_b(conv_b(act(LN_a(conv_a(x))))) + P(x))
+  ConvL a, b, p;
+  LnL lna, lnb;
+  bool proj = false;
+  int lvl = 0;
+  const float* x = nullptr;
+  float *xh_a = nullptr, *rs_a = nullptr, *h1 = nullptr, *xh_b = nullptr, *rs_b = nullptr,
+        *out = nullptr;
+};
+
+struct LevelBufs {
+  float *g1 = nullptr, *g2 = nullptr, *tz = nullptr, *tt = nullptr, *th = nullptr,
+        *de = nullptr, *cat = nullptr;
+};
+
+}  // namespace
+
+struct d2ip_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+
+  // configuration
+  int X = 0, Y = 0, Z = 0;
+  int L = 0, c_in = 0, precision = D2IP_FP32, B = 1;
+  std::vector<int> w;
+  bool net_ready = false;
+  int m = 0;
+  bool j_ready = false, input_ready = false;
+  double lr = 1e-3, beta1 = 0.9, beta2 = 0.999, eps = 1e-8;
+
+  // plan
+  std::vector<Dims3> dims;
+  std::vector<long long> table;  // rows of {kind, offset, count, fan_in}
+  long long P = 0, Pp = 0;       // parameters, padded per-problem stride
+  Unit stem;
+  std::vector<Unit> down;        // index l (l >= 1)
+  std::vector<Res> enc, dec;     // enc[l], dec[l] (l <= L-2)
+  ConvL tail;
+  std::vector<LevelBufs> lb;
+  long long ws_floats = 0;
+
+  // device memory
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  float *theta = nullptr, *grad = nullptr, *am = nullptr, *av = nullptr;
+  float *zin = nullptr, *dsigma = nullptr, *r = nullptr, *gds = nullptr, *dv = nullptr;
+  float *ztmp = nullptr, *ptmp = nullptr, *ws = nullptr, *stage = nullptr;
+  double *loss = nullptr, *resid = nullptr, *trace = nullptr, *seq_resid = nullptr;
+  int *trace_pos = nullptr, *adam_t = nullptr, *status = nullptr;
+  float* J = nullptr;
+  double* colnorm = nullptr;
+  size_t j_bytes = 0;
+  int seq_T_cap = 0;
+  Bf16Net bf;  // tensor-core path state (BF16 copies of weights and activations)
+
+  // graphs
+  cudaGraphExec_t g_step = nullptr, g_eval = nullptr;
+
+  long long n() const { return (long long)X * Y * Z; }
+};
+
+namespace {
+
+d2ip_status fail(d2ip_ctx* c, d2ip_status st, const std::string& msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_op_error = msg;
+  return st;
+}
+
+d2ip_status cuda_fail(d2ip_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, D2IP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                         \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);               \
+  } while (0)
+
+void drop_graphs(d2ip_ctx* c) {
+  if (c->g_step) cudaGraphExecDestroy(c->g_step);
+  if (c->g_eval) cudaGraphExecDestroy(c->g_eval);
+  c->g_step = c->g_eval = nullptr;
+}
+
+void free_arena(d2ip_ctx* c) {
+  drop_graphs(c);
+  if (c->arena) cudaFree(c->arena);
+  c->arena = nullptr;
+  c->arena_bytes = 0;
+  c->bf = Bf16Net{};
+}
+
+// ------------------------------------------------------------------------------------
+// plan construction (module order = parameter order)
+// ------------------------------------------------------------------------------------
+struct Builder {
+  d2ip_ctx* c;
+  long long off = 0;
+  ConvL conv(int ci, int co, int k, int s, int lvl_in) {
+    ConvL L;
+    L.ci = ci;
+    L.co = co;
+    L.k = k;
+    L.s = s;
+    L.din = c->dims[lvl_in];
+    L.dout = conv_out_dims(L.din, k, s);
+    L.w_off = off;
+    const long long fan = (long long)ci * k * k * k;
+    c->table.insert(c->table.end(), {D2IP_PARAM_CONV_W, off, L.wcount(), fan});
+    off += L.wcount();
+    c->table.insert(c->table.end(), {D2IP_PARAM_CONV_B, off, (long long)co, fan});
+    off += co;
+    return L;
+  }
+  LnL ln(int ch) {
+    LnL L;
+    L.c = ch;
+    L.g_off = off;
+    c->table.insert(c->table.end(), {D2IP_PARAM_LN_GAMMA, off, (long long)ch, (long long)ch});
+    off += ch;
+    c->table.insert(c->table.end(), {D2IP_PARAM_LN_BETA, off, (long long)ch, (long long)ch});
+    off += ch;
+    return L;
+  }
+  Res res(int ci, int co, int lvl) {
+    Res R;
+    R.lvl = lvl;
+    R.a = conv(ci, co, 3, 1, lvl);
+    R.lna = ln(co);
+    R.b = conv(co, co, 3, 1, lvl);
+    R.lnb = ln(co);
+    R.proj = ci != co;
+    if (R.proj) R.p = conv(ci, co, 1, 1, lvl);
+    return R;
+  }
+};
+
+void build_plan(d2ip_ctx* c) {
+  c->dims.assign(c->L, Dims3{});
+  c->dims[0] = Dims3{c->Z, c->Y, c->X};
+  for (int l = 1; l < c->L; ++l) c->dims[l] = conv_out_dims(c->dims[l - 1], 3, 2);
+  c->table.clear();
+  Builder b{c};
+  const auto& w = c->w;
+  c->stem.conv = b.conv(c->c_in, w[0], 3, 1, 0);
+  c->stem.ln = b.ln(w[0]);
+  c->stem.lvl_in = c->stem.lvl_out = 0;
+  c->enc.assign(c->L, Res{});
+  c->down.assign(c->L, Unit{});
+  c->dec.assign(c->L > 1 ? c->L - 1 : 0, Res{});
+  c->enc[0] = b.res(w[0], w[0], 0);
+  for (int l = 1; l < c->L; ++l) {
+    c->down[l].conv = b.conv(w[l - 1], w[l], 3, 2, l - 1);
+    c->down[l].ln = b.ln(w[l]);
+    c->down[l].lvl_in = l - 1;
+    c->down[l].lvl_out = l;
+    c->enc[l] = b.res(w[l], w[l], l);
+  }
+  for (int l = c->L - 2; l >= 0; --l) c->dec[l] = b.res(w[l + 1] + w[l], w[l], l);
+  c->tail = b.conv(w[0], 1, 1, 1, 0);
+  c->P = b.off;
+  c->Pp = round_up(c->P, kAlign);
+}
+
+// ------------------------------------------------------------------------------------
+// buffers
+// ------------------------------------------------------------------------------------
+struct Carve {
+  char* base;
+  size_t used = 0;
+  bool dry;
+  template <class T>
+  T* take(long long count) {
+    const size_t bytes = (size_t)round_up(count * (long long)sizeof(T), 256);
+    T* p = dry ? nullptr : reinterpret_cast<T*>(base + used);
+    used += bytes;
+    return p;
+  }
+};
+
+long long conv_ws_floats(const d2ip_ctx* c, const ConvL& L) {
+  return (long long)c->B * conv3d_wgrad_chunks(L.din, L.k, L.s) * (L.wcount() + L.co);
+}
+long long ln_ws_floats(const d2ip_ctx* c, const LnL& L, int lvl) {
+  return (long long)c->B * layernorm_bwd_blocks(c->dims[lvl].count(), L.c) * 2 * L.c;
+}
+
+void layout_buffers(d2ip_ctx* c, Carve& cv) {
+  const int B = c->B;
+  const auto& w = c->w;
+  const auto nv = [&](int l) { return c->dims[l].count(); };
+  c->theta = cv.take<float>(B * c->Pp);
+  c->grad = cv.take<float>(B * c->Pp);
+  c->am = cv.take<float>(B * c->Pp);
+  c->av = cv.take<float>(B * c->Pp);
+  c->zin = cv.take<float>(B * nv(0) * c->c_in);
+  c->dsigma = cv.take<float>(B * nv(0));
+  c->gds = cv.take<float>(B * nv(0));
+  c->stage = cv.take<float>(B * nv(0));
+  long long maxz = 0;
+  for (int l = 0; l < c->L; ++l) maxz = std::max(maxz, nv(l) * w[l]);
+  c->ztmp = cv.take<float>(B * maxz);
+  c->ptmp = cv.take<float>(B * maxz);
+  auto unit_bufs = [&](Unit& u) {
+    const long long n = nv(u.lvl_out);
+    u.xh = cv.take<float>(B * n * u.ln.c);
+    u.rs = cv.take<float>(B * n);
+    u.a = cv.take<float>(B * n * u.ln.c);
+  };
+  auto res_bufs = [&](Res& R) {
+    const long long n = nv(R.lvl);
+    const int co = R.lna.c;
+    R.xh_a = cv.take<float>(B * n * co);
+    R.rs_a = cv.take<float>(B * n);
+    R.h1 = cv.take<float>(B * n * co);
+    R.xh_b = cv.take<float>(B * n * co);
+    R.rs_b = cv.take<float>(B * n);
+    R.out = cv.take<float>(B * n * co);
+  };
+  unit_bufs(c->stem);
+  for (int l = 0; l < c->L; ++l) {
+    if (l > 0) unit_bufs(c->down[l]);
+    res_bufs(c->enc[l]);
+  }
+  for (int l = 0; l + 1 < c->L; ++l) res_bufs(c->dec[l]);
+  c->lb.assign(c->L, LevelBufs{});
+  for (int l = 0; l < c->L; ++l) {
+    const long long cmax = w[l] + (l + 1 < c->L ? w[l + 1] : 0);
+    LevelBufs& L = c->lb[l];
+    L.g1 = cv.take<float>(B * nv(l) * cmax);
+    L.g2 = cv.take<float>(B * nv(l) * cmax);
+    L.tz = cv.take<float>(B * nv(l) * w[l]);
+    L.tt = cv.take<float>(B * nv(l) * w[l]);
+    L.th = cv.take<float>(B * nv(l) * w[l]);
+    L.de = cv.take<float>(B * nv(l) * w[l]);
+    if (l + 1 < c->L) L.cat = cv.take<float>(B * nv(l) * cmax);
+  }
+  // wiring of block inputs
+  c->stem.x = c->zin;
+  c->enc[0].x = c->stem.a;
+  for (int l = 1; l < c->L; ++l) {
+    c->down[l].x = c->enc[l - 1].out;
+    c->enc[l].x = c->down[l].a;
+  }
+  for (int l = 0; l + 1 < c->L; ++l) c->dec[l].x = c->lb[l].cat;
+  // workspace: the largest split-K / LayerNorm partial buffer of any layer
+  long long ws = conv_ws_floats(c, c->stem.conv);
+  ws = std::max(ws, ln_ws_floats(c, c->stem.ln, 0));
+  auto res_ws = [&](const Res& R) {
+    ws = std::max(ws, conv_ws_floats(c, R.a));
+    ws = std::max(ws, conv_ws_floats(c, R.b));
+    if (R.proj) ws = std::max(ws, conv_ws_floats(c, R.p));
+    ws = std::max(ws, ln_ws_floats(c, R.lna, R.lvl));
+    ws = std::max(ws, ln_ws_floats(c, R.lnb, R.lvl));
+  };
+  for (int l = 0; l < c->L; ++l) {
+    res_ws(c->enc[l]);
+    if (l > 0) {
+      ws = std::max(ws, conv_ws_floats(c, c->down[l].conv));
+      ws = std::max(ws, ln_ws_floats(c, c->down[l].ln, l));
+    }
+  }
+  for (int l = 0; l + 1 < c->L; ++l) res_ws(c->dec[l]);
+  ws = std::max(ws, conv_ws_floats(c, c->tail));
+  c->ws_floats = ws;
+  c->ws = cv.take<float>(ws);
+  c->loss = cv.take<double>(B);
+  c->resid = cv.take<double>(B);
+  c->trace = cv.take<double>((long long)kTraceCap * B);
+  c->trace_pos = cv.take<int>(1);
+  c->adam_t = cv.take<int>(1);
+  c->status = cv.take<int>(1);
+  if (c->precision == D2IP_BF16)
+    bf16_layout(c->bf, cv.dry ? nullptr : cv.base, cv.used, B, c->Pp, maxz, nv(0) * c->c_in);
+}
+
+d2ip_status ensure_arena(d2ip_ctx* c) {
+  if (c->arena) return D2IP_OK;
+  Carve dry{nullptr, 0, true};
+  layout_buffers(c, dry);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, dry.used);
+  if (e != cudaSuccess) return fail(c, D2IP_ERR_OOM, "device allocation of the workspace failed");
+  c->arena = p;
+  c->arena_bytes = dry.used;
+  Carve real{static_cast<char*>(p), 0, false};
+  layout_buffers(c, real);
+  CK(cudaMemsetAsync(p, 0, dry.used, c->stream));
+  return D2IP_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// launch sequences
+// ------------------------------------------------------------------------------------
+// Optional per-launch CUDA-event tracing (d2ip_profile_iterations).
+struct Tracer {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> cls;
+  std::vector<double> work;
+  size_t used = 0;
+  cudaError_t begin(int k, double w, cudaStream_t s) {
+    if (used + 2 > pool.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        pool.push_back(e);
+      }
+    }
+    cls.push_back(k);
+    work.push_back(w);
+    return cudaEventRecord(pool[used++], s);
+  }
+  cudaError_t end(cudaStream_t s) { return cudaEventRecord(pool[used++], s); }
+  void release() {
+    for (auto e : pool) cudaEventDestroy(e);
+    pool.clear();
+    cls.clear();
+    work.clear();
+    used = 0;
+  }
+};
+
+struct Launcher {
+  d2ip_ctx* c;
+  Tracer* tr = nullptr;
+  cudaError_t e = cudaSuccess;
+  void ok(cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  }
+  // bracket one kernel launch of class k with algorithmic work w (FLOPs or bytes)
+  void beg(int k, double w) {
+    if (tr) ok(tr->begin(k, w, c->stream));
+  }
+  void fin() {
+    if (tr) ok(tr->end(c->stream));
+  }
+  float* W(const ConvL& L) { return c->theta + L.w_off; }
+  float* G(long long off) { return c->grad + off; }
+  double conv_flops(const ConvL& L) const {
+    return 2.0 * c->B * (double)L.dout.count() * L.k * L.k * L.k * L.ci * L.co;
+  }
+
+  void conv_fwd(const ConvL& L, const float* x, float* y) {
+    beg(D2IP_KCLASS_CONV_FWD, conv_flops(L));
+    if (c->precision == D2IP_BF16 && bf16_conv_supported(L.ci, L.co, L.k)) {
+      ok(bf16_conv_fwd(c->bf, c->theta, L.w_off, x, y, c->B, L.din, L.ci, L.co, L.k, L.s,
+                       L.din.count() * L.ci, L.dout.count() * L.co, c->Pp, c->stream));
+    } else {
+      ok(conv3d_fwd_f32(x, W(L), W(L) + L.wcount(), y, c->B, L.din, L.ci, L.co, L.k, L.s,
+                        L.din.count() * L.ci, L.dout.count() * L.co, c->Pp, c->stream));
+    }
+    fin();
+  }
+  void conv_dgrad(const ConvL& L, const float* dy, float* dx, int acc) {
+    beg(D2IP_KCLASS_CONV_DGRAD, conv_flops(L));
+    ok(conv3d_dgrad_f32(dy, W(L), dx, c->B, L.din, L.ci, L.co, L.k, L.s, L.dout.count() * L.co,
+                        L.din.count() * L.ci, c->Pp, acc, c->stream));
+    fin();
+  }
+  void conv_wgrad(const ConvL& L, const float* x, const float* dy) {
+    beg(D2IP_KCLASS_CONV_WGRAD, conv_flops(L));
+    ok(conv3d_wgrad_partial_f32(x, dy, c->ws, c->B, L.din, L.ci, L.co, L.k, L.s,
+                                L.din.count() * L.ci, L.dout.count() * L.co, c->stream));
+    ok(reduce_rows_f32(c->ws, G(L.w_off), c->B, conv3d_wgrad_chunks(L.din, L.k, L.s),
+                       L.wcount() + L.co, c->Pp, 0, c->stream));
+    fin();
+  }
+  void ln_fwd(const LnL& L, int lvl, const float* z, const float* resid, float* y, float* xh,
+              float* rs) {
+    const double nv = (double)c->dims[lvl].count() * c->B;
+    beg(D2IP_KCLASS_LN_FWD, 4.0 * nv * (L.c * (resid ? 4 : 3) + 1));
+    ok(layernorm_act_fwd_f32(z, c->theta + L.g_off, resid, y, xh, rs, c->B,
+                             c->dims[lvl].count(), L.c, 1, c->Pp, c->stream));
+    fin();
+  }
+  void ln_bwd(const LnL& L, int lvl, const float* dy, const float* aout, const float* xh,
+              const float* rs, float* dz, float* dt) {
+    const long long nv = c->dims[lvl].count();
+    beg(D2IP_KCLASS_LN_BWD, 4.0 * c->B * nv * (L.c * (dt ? 5 : 4) + 1));
+    ok(layernorm_act_bwd_f32(dy, aout, xh, rs, c->theta + L.g_off, dz, dt, c->ws, c->B, nv,
+                             L.c, c->Pp, c->stream));
+    ok(reduce_rows_f32(c->ws, G(L.g_off), c->B, layernorm_bwd_blocks(nv, L.c), 2 * L.c, c->Pp,
+                       0, c->stream));
+    fin();
+  }
+
+  void unit_fwd(Unit& u) {
+    conv_fwd(u.conv, u.x, c->ztmp);
+    ln_fwd(u.ln, u.lvl_out, c->ztmp, nullptr, u.a, u.xh, u.rs);
+  }
+  void res_fwd(Res& R) {
+    conv_fwd(R.a, R.x, c->ztmp);
+    ln_fwd(R.lna, R.lvl, c->ztmp, nullptr, R.h1, R.xh_a, R.rs_a);
+    if (R.proj) conv_fwd(R.p, R.x, c->ptmp);
+    conv_fwd(R.b, R.h1, c->ztmp);
+    ln_fwd(R.lnb, R.lvl, c->ztmp, R.proj ? c->ptmp : R.x, R.out, R.xh_b, R.rs_b);
+  }
+  void forward() {
+    if (c->precision == D2IP_BF16) ok(bf16_prepare_weights(c->bf, c->theta, c->B, c->Pp, c->stream));
+    unit_fwd(c->stem);
+    res_fwd(c->enc[0]);
+    for (int l = 1; l < c->L; ++l) {
+      unit_fwd(c->down[l]);
+      res_fwd(c->enc[l]);
+    }
+    const float* cur = c->enc[c->L - 1].out;
+    for (int l = c->L - 2; l >= 0; --l) {
+      const double bytes = 4.0 * c->B *
+                           ((double)c->dims[l + 1].count() * c->w[l + 1] +
+                            2.0 * c->dims[l].count() * c->w[l] +
+                            (double)c->dims[l].count() * c->w[l + 1]);
+      beg(D2IP_KCLASS_UP_FWD, bytes);
+      ok(upsample_concat_fwd_f32(cur, c->enc[l].out, c->lb[l].cat, c->B, c->dims[l + 1],
+                                 c->dims[l], c->w[l + 1], c->w[l], c->stream));
+      fin();
+      res_fwd(c->dec[l]);
+      cur = c->dec[l].out;
+    }
+    conv_fwd(c->tail, cur, c->dsigma);
+  }
+  void data_term(bool training) {
+    const long long n = c->n();
+    const double jb = 4.0 * c->m * (double)n, vb = 4.0 * c->B * ((double)n + 2.0 * c->m);
+    beg(D2IP_KCLASS_JMUL, jb + vb);
+    ok(jmul_residual_f32(c->J, c->dsigma, c->dv, c->r, c->B, c->m, (int)n, n, c->stream));
+    fin();
+    beg(D2IP_KCLASS_LOSS, 4.0 * c->B * c->m);
+    if (training) {
+      ok(residual_loss_f64(c->r, c->loss, c->trace, c->trace_pos, c->adam_t, c->status, c->B,
+                           c->m, c->stream));
+    } else {
+      ok(residual_loss_f64(c->r, c->resid, nullptr, nullptr, nullptr, c->status, c->B, c->m,
+                           c->stream));
+    }
+    fin();
+    if (training) {
+      beg(D2IP_KCLASS_JTMUL, jb + vb);
+      ok(jtmul_f32(c->J, c->r, c->gds, 2.0f / (float)c->m, c->B, c->m, (int)n, n, c->stream));
+      fin();
+    }
+  }
+  // dout: gradient of R.out; writes dx (gradient of R.x)
+  void res_bwd(Res& R, const float* dout, float* dx) {
+    LevelBufs& T = c->lb[R.lvl];
+    ln_bwd(R.lnb, R.lvl, dout, R.out, R.xh_b, R.rs_b, T.tz, T.tt);
+    conv_dgrad(R.b, T.tz, T.th, 0);
+    conv_wgrad(R.b, R.h1, T.tz);
+    ln_bwd(R.lna, R.lvl, T.th, R.h1, R.xh_a, R.rs_a, T.tz, nullptr);
+    conv_dgrad(R.a, T.tz, dx, 0);
+    conv_wgrad(R.a, R.x, T.tz);
+    if (R.proj) {
+      conv_dgrad(R.p, T.tt, dx, 1);
+      conv_wgrad(R.p, R.x, T.tt);
+    } else {
+      const long long cnt = c->B * c->dims[R.lvl].count() * R.lna.c;
+      beg(D2IP_KCLASS_MISC, 12.0 * cnt);
+      ok(add_inplace_f32(dx, T.tt, cnt, c->stream));
+      fin();
+    }
+  }
+  void unit_bwd(Unit& u, const float* da, float* dx, int acc, bool dgrad) {
+    float* tz = c->lb[u.lvl_out].tz;
+    ln_bwd(u.ln, u.lvl_out, da, u.a, u.xh, u.rs, tz, nullptr);
+    if (dgrad) conv_dgrad(u.conv, tz, dx, acc);
+    conv_wgrad(u.conv, u.x, tz);
+  }
+  void backward() {
+    const int L = c->L;
+    const float* tail_in = L > 1 ? c->dec[0].out : c->enc[0].out;
+    conv_dgrad(c->tail, c->gds, c->lb[0].g1, 0);
+    conv_wgrad(c->tail, tail_in, c->gds);
+    for (int l = 0; l + 1 < L; ++l) {
+      res_bwd(c->dec[l], c->lb[l].g1, c->lb[l].g2);
+      const double bytes = 4.0 * c->B *
+                           ((double)c->dims[l + 1].count() * c->w[l + 1] +
+                            2.0 * c->dims[l].count() * c->w[l] +
+                            (double)c->dims[l].count() * c->w[l + 1]);
+      beg(D2IP_KCLASS_UP_BWD, bytes);
+      ok(upsample_concat_bwd_f32(c->lb[l].g2, c->lb[l + 1].g1, c->lb[l].de, c->B,
+                                 c->dims[l + 1], c->dims[l], c->w[l + 1], c->w[l], c->stream));
+      fin();
+    }
+    for (int l = L - 1; l >= 1; --l) {
+      const float* dout = l == L - 1 ? c->lb[l].g1 : c->lb[l].de;
+      res_bwd(c->enc[l], dout, c->lb[l].g2);
+      unit_bwd(c->down[l], c->lb[l].g2, c->lb[l - 1].de, 1, true);
+    }
+    const float* d0 = L == 1 ? c->lb[0].g1 : c->lb[0].de;
+    res_bwd(c->enc[0], d0, c->lb[0].g2);
+    unit_bwd(c->stem, c->lb[0].g2, nullptr, 0, false);
+  }
+  void adam() {
+    beg(D2IP_KCLASS_ADAM, 28.0 * c->B * c->P);
+    ok(adam_step_f32(c->theta, c->grad, c->am, c->av, (long long)c->B * c->Pp, c->lr,
+                     c->beta1, c->beta2, c->eps, c->adam_t, 0, c->stream));
+    fin();
+  }
+};
+
+d2ip_status capture(d2ip_ctx* c, bool step, cudaGraphExec_t* out) {
+  CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  Launcher Lr{c};
+  Lr.forward();
+  Lr.data_term(step);
+  if (step) {
+    Lr.backward();
+    Lr.adam();
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (Lr.e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(c, Lr.e, "kernel launch during capture");
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+  return D2IP_OK;
+}
+
+d2ip_status ready(d2ip_ctx* c) {
+  if (!c) return fail(nullptr, D2IP_ERR_BAD_ARG, "null context");
+  if (!c->net_ready || !c->X) return fail(c, D2IP_ERR_STATE, "grid and network not set");
+  if (!c->j_ready) return fail(c, D2IP_ERR_STATE, "J not loaded");
+  if (!c->input_ready) return fail(c, D2IP_ERR_STATE, "input Z and theta0 not set");
+  CK(cudaSetDevice(c->device));
+  if (!c->g_step) {
+    d2ip_status s = capture(c, true, &c->g_step);
+    if (s) return s;
+  }
+  if (!c->g_eval) {
+    d2ip_status s = capture(c, false, &c->g_eval);
+    if (s) return s;
+  }
+  return D2IP_OK;
+}
+
+d2ip_status check_status(d2ip_ctx* c) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (st & 1) {
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    return fail(c, D2IP_ERR_NONFINITE, "a loss or residual became NaN or Inf");
+  }
+  return D2IP_OK;
+}
+
+// copy rows: dst[b*dpitch ..] <- src[b*spitch ..], `width` floats, B rows (host or device)
+cudaError_t copy_rows(void* dst, long long dpitch, const void* src, long long spitch,
+                      long long width, int rows, size_t elem, cudaStream_t s) {
+  return cudaMemcpy2DAsync(dst, dpitch * elem, src, spitch * elem, width * elem, rows,
+                           cudaMemcpyDefault, s);
+}
+
+d2ip_status reset_optimizer(d2ip_ctx* c) {
+  CK(cudaMemsetAsync(c->am, 0, sizeof(float) * c->B * c->Pp, c->stream));
+  CK(cudaMemsetAsync(c->av, 0, sizeof(float) * c->B * c->Pp, c->stream));
+  CK(cudaMemsetAsync(c->adam_t, 0, sizeof(int), c->stream));
+  return D2IP_OK;
+}
+
+d2ip_status run_steps(d2ip_ctx* c, int n_steps, double* loss_trace) {
+  int done = 0;
+  while (done < n_steps) {
+    const int chunk = std::min(kTraceCap, n_steps - done);
+    CK(cudaMemsetAsync(c->trace_pos, 0, sizeof(int), c->stream));
+    for (int i = 0; i < chunk; ++i) CK(cudaGraphLaunch(c->g_step, c->stream));
+    if (loss_trace)
+      CK(cudaMemcpyAsync(loss_trace + (long long)done * c->B, c->trace,
+                         sizeof(double) * chunk * c->B, cudaMemcpyDefault, c->stream));
+    done += chunk;
+  }
+  return D2IP_OK;
+}
+
+d2ip_status stage_dv(d2ip_ctx* c, const float* dV, long long spitch) {
+  CK(copy_rows(c->dv, c->m, dV, spitch, c->m, c->B, sizeof(float), c->stream));
+  return D2IP_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+extern "C" {
+
+d2ip_status d2ip_create(d2ip_ctx** out, int device, void* stream) {
+  if (!out) return fail(nullptr, D2IP_ERR_BAD_ARG, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0)
+    return fail(nullptr, D2IP_ERR_CUDA, "no CUDA device available");
+  if (device < 0 || device >= ndev) return fail(nullptr, D2IP_ERR_BAD_ARG, "bad device index");
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) return fail(nullptr, D2IP_ERR_CUDA, cudaGetErrorString(e));
+  d2ip_ctx* c = new d2ip_ctx();
+  c->device = device;
+  if (stream) {
+    c->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete c;
+      return fail(nullptr, D2IP_ERR_CUDA, cudaGetErrorString(e));
+    }
+    c->own_stream = true;
+  }
+  e = prepare_pointwise_kernels();
+  if (e == cudaSuccess) e = bf16_prepare_kernels();
+  if (e != cudaSuccess) {
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return fail(nullptr, D2IP_ERR_CUDA, cudaGetErrorString(e));
+  }
+  *out = c;
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_destroy(d2ip_ctx* c) {
+  if (!c) return D2IP_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  free_arena(c);
+  if (c->J) cudaFree(c->J);
+  if (c->colnorm) cudaFree(c->colnorm);
+  if (c->r) cudaFree(c->r);
+  if (c->dv) cudaFree(c->dv);
+  if (c->seq_resid) cudaFree(c->seq_resid);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_set_grid(d2ip_ctx* c, int X, int Y, int Z) {
+  if (!c) return fail(nullptr, D2IP_ERR_BAD_ARG, "null context");
+  if (X <= 0 || Y <= 0 || Z <= 0 || (long long)X * Y * Z > (1LL << 30))
+    return fail(c, D2IP_ERR_BAD_SHAPE, "grid dimensions must be positive (at most 2^30 voxels)");
+  cudaSetDevice(c->device);
+  free_arena(c);
+  c->X = X;
+  c->Y = Y;
+  c->Z = Z;
+  c->j_ready = c->input_ready = false;
+  if (c->net_ready) build_plan(c);
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_set_network(d2ip_ctx* c, int levels, const int* widths, int c_in,
+                             int precision, int batch) {
+  if (!c) return fail(nullptr, D2IP_ERR_BAD_ARG, "null context");
+  if (!c->X) return fail(c, D2IP_ERR_STATE, "call d2ip_set_grid first");
+  if (levels < 1 || levels > 8 || !widths)
+    return fail(c, D2IP_ERR_BAD_ARG, "levels must be 1..8 with a widths array");
+  for (int l = 0; l < levels; ++l)
+    if (widths[l] <= 0 || widths[l] % 4 != 0 || widths[l] > 128)
+      return fail(c, D2IP_ERR_BAD_SHAPE, "each width must be a positive multiple of 4, <= 128");
+  if (c_in <= 0 || c_in > 256) return fail(c, D2IP_ERR_BAD_SHAPE, "c_in must be 1..256");
+  if (precision != D2IP_FP32 && precision != D2IP_BF16)
+    return fail(c, D2IP_ERR_BAD_ARG, "precision must be D2IP_FP32 or D2IP_BF16");
+  if (precision == D2IP_BF16 && !bf16_network_supported(levels, widths, c_in))
+    return fail(c, D2IP_ERR_BAD_SHAPE, "BF16 path needs c_in and widths that are multiples of 8");
+  if (batch < 1 || batch > 4096) return fail(c, D2IP_ERR_BAD_ARG, "batch must be 1..4096");
+  cudaSetDevice(c->device);
+  free_arena(c);
+  c->L = levels;
+  c->w.assign(widths, widths + levels);
+  c->c_in = c_in;
+  c->precision = precision;
+  c->B = batch;
+  c->net_ready = true;
+  c->j_ready = c->input_ready = false;
+  build_plan(c);
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_param_count(d2ip_ctx* c, long long* count) {
+  if (!c || !count) return fail(c, D2IP_ERR_BAD_ARG, "null argument");
+  if (!c->net_ready) return fail(c, D2IP_ERR_STATE, "network not set");
+  *count = c->P;
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_param_table(d2ip_ctx* c, long long* rows, int cap, int* n_rows) {
+  if (!c || !n_rows) return fail(c, D2IP_ERR_BAD_ARG, "null argument");
+  if (!c->net_ready) return fail(c, D2IP_ERR_STATE, "network not set");
+  const int n = (int)(c->table.size() / 4);
+  *n_rows = n;
+  if (rows)
+    for (int i = 0; i < std::min(n, cap) * 4; ++i) rows[i] = c->table[i];
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_load_J(d2ip_ctx* c, const float* J, int m, int n, int normalize_cols) {
+  if (!c || !J) return fail(c, D2IP_ERR_BAD_ARG, "null argument");
+  if (!c->net_ready) return fail(c, D2IP_ERR_STATE, "set grid and network first");
+  if (m <= 0 || (long long)n != c->n())
+    return fail(c, D2IP_ERR_BAD_SHAPE, "J must be m x (X*Y*Z)");
+  if ((size_t)8 * m * sizeof(float) > 200 * 1024)
+    return fail(c, D2IP_ERR_BAD_SHAPE, "m too large for the adjoint kernel (max 6400)");
+  CK(cudaSetDevice(c->device));
+  d2ip_status s = ensure_arena(c);
+  if (s) return s;
+  const size_t bytes = (size_t)m * n * sizeof(float);
+  if (bytes != c->j_bytes || m != c->m) {
+    drop_graphs(c);
+    if (c->J) cudaFree(c->J);
+    if (c->colnorm) cudaFree(c->colnorm);
+    if (c->r) cudaFree(c->r);
+    if (c->dv) cudaFree(c->dv);
+    c->J = nullptr;
+    c->colnorm = nullptr;
+    c->r = c->dv = nullptr;
+    c->j_bytes = 0;
+    if (cudaMalloc(&c->J, bytes) != cudaSuccess ||
+        cudaMalloc(&c->colnorm, sizeof(double) * n) != cudaSuccess ||
+        cudaMalloc(&c->r, sizeof(float) * m * c->B) != cudaSuccess ||
+        cudaMalloc(&c->dv, sizeof(float) * m * c->B) != cudaSuccess)
+      return fail(c, D2IP_ERR_OOM, "device allocation of J failed");
+    c->j_bytes = bytes;
+    c->m = m;
+  }
+  CK(cudaMemcpyAsync(c->J, J, bytes, cudaMemcpyDefault, c->stream));
+  if (normalize_cols) {
+    CK(normalize_columns_f64(c->J, c->colnorm, m, n, c->stream));
+  } else {
+    CK(cudaMemsetAsync(c->colnorm, 0, sizeof(double) * n, c->stream));
+  }
+  if (c->precision == D2IP_BF16) CK(bf16_set_J(c->bf, c->J, m, n, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->j_ready = true;
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_get_colnorms(d2ip_ctx* c, double* out) {
+  if (!c || !out) return fail(c, D2IP_ERR_BAD_ARG, "null argument");
+  if (!c->j_ready) return fail(c, D2IP_ERR_STATE, "J not loaded");
+  CK(cudaSetDevice(c->device));
+  CK(cudaMemcpyAsync(out, c->colnorm, sizeof(double) * c->n(), cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_set_input(d2ip_ctx* c, const float* Zin, const float* theta0) {
+  if (!c || !Zin || !theta0) return fail(c, D2IP_ERR_BAD_ARG, "null argument");
+  if (!c->net_ready) return fail(c, D2IP_ERR_STATE, "set grid and network first");
+  CK(cudaSetDevice(c->device));
+  d2ip_status s = ensure_arena(c);
+  if (s) return s;
+  CK(cudaMemcpyAsync(c->zin, Zin, sizeof(float) * c->B * c->n() * c->c_in, cudaMemcpyDefault,
+                     c->stream));
+  CK(copy_rows(c->theta, c->Pp, theta0, c->P, c->P, c->B, sizeof(float), c->stream));
+  s = reset_optimizer(c);
+  if (s) return s;
+  CK(cudaStreamSynchronize(c->stream));
+  c->input_ready = true;
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_set_optim(d2ip_ctx* c, double lr, double beta1, double beta2, double eps) {
+  if (!c) return fail(nullptr, D2IP_ERR_BAD_ARG, "null context");
+  if (!(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) ||
+      !(eps > 0.0))
+    return fail(c, D2IP_ERR_BAD_ARG, "need lr > 0, 0 <= beta < 1, eps > 0");
+  if (lr != c->lr || beta1 != c->beta1 || beta2 != c->beta2 || eps != c->eps) drop_graphs(c);
+  c->lr = lr;
+  c->beta1 = beta1;
+  c->beta2 = beta2;
+  c->eps = eps;
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_reset_optimizer(d2ip_ctx* c) {
+  if (!c) return fail(nullptr, D2IP_ERR_BAD_ARG, "null context");
+  if (!c->arena) return fail(c, D2IP_ERR_STATE, "network not set up");
+  CK(cudaSetDevice(c->device));
+  d2ip_status s = reset_optimizer(c);
+  if (s) return s;
+  CK(cudaStreamSynchronize(c->stream));
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_run_steps(d2ip_ctx* c, const float* dV, int n_steps, double* loss_trace) {
+  d2ip_status s = ready(c);
+  if (s) return s;
+  if (!dV || n_steps < 0) return fail(c, D2IP_ERR_BAD_ARG, "bad dV or n_steps");
+  s = stage_dv(c, dV, c->m);
+  if (s) return s;
+  s = run_steps(c, n_steps, loss_trace);
+  if (s) return s;
+  return check_status(c);
+}
+
+d2ip_status d2ip_forward(d2ip_ctx* c, float* dsigma_out) {
+  if (!c || !dsigma_out) return fail(c, D2IP_ERR_BAD_ARG, "null argument");
+  d2ip_status s = ready(c);
+  if (s) return s;
+  Launcher Lr{c};
+  Lr.forward();
+  if (Lr.e != cudaSuccess) return cuda_fail(c, Lr.e, "forward launch");
+  CK(cudaMemcpyAsync(dsigma_out, c->dsigma, sizeof(float) * c->B * c->n(), cudaMemcpyDefault,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_get_grad(d2ip_ctx* c, float* grad_out) {
+  if (!c || !grad_out) return fail(c, D2IP_ERR_BAD_ARG, "null argument");
+  if (!c->arena) return fail(c, D2IP_ERR_STATE, "network not set up");
+  CK(cudaSetDevice(c->device));
+  CK(copy_rows(grad_out, c->P, c->grad, c->Pp, c->P, c->B, sizeof(float), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_fit_frame(d2ip_ctx* c, const float* dV, int n_steps, float* dsigma_out,
+                           double* residual_out, double* loss_trace) {
+  d2ip_status s = ready(c);
+  if (s) return s;
+  if (!dV || n_steps < 0) return fail(c, D2IP_ERR_BAD_ARG, "bad dV or n_steps");
+  s = stage_dv(c, dV, c->m);
+  if (s) return s;
+  s = reset_optimizer(c);
+  if (s) return s;
+  s = run_steps(c, n_steps, loss_trace);
+  if (s) return s;
+  CK(cudaGraphLaunch(c->g_eval, c->stream));
+  if (dsigma_out)
+    CK(cudaMemcpyAsync(dsigma_out, c->dsigma, sizeof(float) * c->B * c->n(), cudaMemcpyDefault,
+                       c->stream));
+  if (residual_out)
+    CK(cudaMemcpyAsync(residual_out, c->resid, sizeof(double) * c->B, cudaMemcpyDefault,
+                       c->stream));
+  return check_status(c);
+}
+
+d2ip_status d2ip_fit_sequence(d2ip_ctx* c, const float* V, int T, const float* dV0,
+                              int upws_steps, int first_steps, int later_steps,
+                              float* Sigma_out, double* residual_out) {
+  d2ip_status s = ready(c);
+  if (s) return s;
+  if (!V || T < 1 || upws_steps < 0 || first_steps < 0 || later_steps < 0)
+    return fail(c, D2IP_ERR_BAD_ARG, "bad V, T or step counts");
+  if (T > c->seq_T_cap) {
+    if (c->seq_resid) cudaFree(c->seq_resid);
+    c->seq_resid = nullptr;
+    if (cudaMalloc(&c->seq_resid, sizeof(double) * T * c->B) != cudaSuccess)
+      return fail(c, D2IP_ERR_OOM, "residual buffer allocation failed");
+    c->seq_T_cap = T;
+  }
+  const long long m = c->m, n = c->n();
+  if (upws_steps > 0) {  // UPWS (Eqs. 5-7)
+    s = dV0 ? stage_dv(c, dV0, m) : stage_dv(c, V, (long long)T * m);
+    if (s) return s;
+    s = reset_optimizer(c);
+    if (s) return s;
+    s = run_steps(c, upws_steps, nullptr);
+    if (s) return s;
+  }
+  for (int i = 0; i < T; ++i) {  // TPP (Eqs. 8-9): theta carries over, Adam restarts
+    s = stage_dv(c, V + (long long)i * m, (long long)T * m);
+    if (s) return s;
+    s = reset_optimizer(c);
+    if (s) return s;
+    s = run_steps(c, i == 0 ? first_steps : later_steps, nullptr);
+    if (s) return s;
+    CK(cudaGraphLaunch(c->g_eval, c->stream));
+    if (Sigma_out)
+      CK(copy_rows(Sigma_out + (long long)i * n, (long long)T * n, c->dsigma, n, n, c->B,
+                   sizeof(float), c->stream));
+    CK(cudaMemcpy2DAsync(c->seq_resid + i, sizeof(double) * T, c->resid, sizeof(double),
+                         sizeof(double), c->B, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  if (residual_out)
+    CK(cudaMemcpyAsync(residual_out, c->seq_resid, sizeof(double) * T * c->B, cudaMemcpyDefault,
+                       c->stream));
+  return check_status(c);
+}
+
+d2ip_status d2ip_get_state(d2ip_ctx* c, float* theta, float* adam_m, float* adam_v,
+                           int* adam_t) {
+  if (!c) return fail(nullptr, D2IP_ERR_BAD_ARG, "null context");
+  if (!c->arena) return fail(c, D2IP_ERR_STATE, "network not set up");
+  CK(cudaSetDevice(c->device));
+  if (theta) CK(copy_rows(theta, c->P, c->theta, c->Pp, c->P, c->B, sizeof(float), c->stream));
+  if (adam_m) CK(copy_rows(adam_m, c->P, c->am, c->Pp, c->P, c->B, sizeof(float), c->stream));
+  if (adam_v) CK(copy_rows(adam_v, c->P, c->av, c->Pp, c->P, c->B, sizeof(float), c->stream));
+  int t = 0;
+  CK(cudaMemcpyAsync(&t, c->adam_t, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (adam_t) *adam_t = t;
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_set_state(d2ip_ctx* c, const float* theta, const float* adam_m,
+                           const float* adam_v, int adam_t) {
+  if (!c) return fail(nullptr, D2IP_ERR_BAD_ARG, "null context");
+  if (!c->net_ready) return fail(c, D2IP_ERR_STATE, "network not set");
+  if (adam_t < 0) return fail(c, D2IP_ERR_BAD_ARG, "adam_t must be >= 0");
+  CK(cudaSetDevice(c->device));
+  d2ip_status s = ensure_arena(c);
+  if (s) return s;
+  if (theta) CK(copy_rows(c->theta, c->Pp, theta, c->P, c->P, c->B, sizeof(float), c->stream));
+  if (adam_m) CK(copy_rows(c->am, c->Pp, adam_m, c->P, c->P, c->B, sizeof(float), c->stream));
+  if (adam_v) CK(copy_rows(c->av, c->Pp, adam_v, c->P, c->P, c->B, sizeof(float), c->stream));
+  CK(cudaMemcpyAsync(c->adam_t, &adam_t, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_err_ratio(d2ip_ctx* c, const float* est, const float* truth, double* out) {
+  if (!c || !est || !truth || !out) return fail(c, D2IP_ERR_BAD_ARG, "null argument");
+  if (!c->arena) return fail(c, D2IP_ERR_STATE, "network not set up");
+  CK(cudaSetDevice(c->device));
+  const long long n = c->n();
+  CK(cudaMemcpyAsync(c->stage, truth, sizeof(float) * c->B * n, cudaMemcpyDefault, c->stream));
+  CK(cudaMemcpyAsync(c->gds, est, sizeof(float) * c->B * n, cudaMemcpyDefault, c->stream));
+  CK(err_ratio_f64(c->gds, c->stage, c->resid, c->B, n, c->stream));
+  CK(cudaMemcpyAsync(out, c->resid, sizeof(double) * c->B, cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_profile_iterations(d2ip_ctx* c, const float* dV, int n_iters, double* ms,
+                                    double* work, long long* launches) {
+  d2ip_status s = ready(c);
+  if (s) return s;
+  if (!dV || n_iters < 1 || !ms || !work || !launches)
+    return fail(c, D2IP_ERR_BAD_ARG, "bad dV, n_iters or output arrays");
+  s = stage_dv(c, dV, c->m);
+  if (s) return s;
+  CK(cudaMemsetAsync(c->trace_pos, 0, sizeof(int), c->stream));
+  Tracer tr;
+  Launcher Lr{c, &tr};
+  for (int it = 0; it < n_iters && Lr.e == cudaSuccess; ++it) {
+    Lr.forward();
+    Lr.data_term(true);
+    Lr.backward();
+    Lr.adam();
+  }
+  cudaError_t e = Lr.e;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  for (int k = 0; k < D2IP_KCLASS_COUNT; ++k) {
+    ms[k] = 0.0;
+    work[k] = 0.0;
+    launches[k] = 0;
+  }
+  for (size_t i = 0; e == cudaSuccess && i < tr.cls.size(); ++i) {
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, tr.pool[2 * i], tr.pool[2 * i + 1]);
+    ms[tr.cls[i]] += t;
+    work[tr.cls[i]] += tr.work[i];
+    launches[tr.cls[i]] += 1;
+  }
+  tr.release();
+  if (e != cudaSuccess) return cuda_fail(c, e, "profiled iterations");
+  return check_status(c);
+}
+
+d2ip_status d2ip_sync(d2ip_ctx* c) {
+  if (!c) return fail(nullptr, D2IP_ERR_BAD_ARG, "null context");
+  CK(cudaSetDevice(c->device));
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaGetLastError());
+  return D2IP_OK;
+}
+
+const char* d2ip_last_error(d2ip_ctx* c) { return c ? c->err.c_str() : g_op_error.c_str(); }
+
+// ---------------------------------------------------------------------------------------
+// context-free ops
+// ---------------------------------------------------------------------------------------
+#define OPCK(call)                                                              \
+  do {                                                                          \
+    cudaError_t e_ = (call);                                                    \
+    if (e_ != cudaSuccess) return cuda_fail(nullptr, e_, #call);                \
+  } while (0)
+
+static bool bad_conv(int batch, int dz, int dy, int dx, int ci, int co, int k, int s) {
+  return batch < 1 || dz < 1 || dy < 1 || dx < 1 || ci < 1 || co < 1 || (k != 1 && k != 3) ||
+         (s != 1 && s != 2);
+}
+
+d2ip_status d2ip_conv3d_forward(const float* x, const float* W, const float* b, float* y,
+                                int batch, int dz, int dy, int dx, int ci, int co, int ksize,
+                                int stride, long long w_bs, void* stream) {
+  if (!x || !W || !b || !y) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
+  if (bad_conv(batch, dz, dy, dx, ci, co, ksize, stride))
+    return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad convolution shape");
+  const Dims3 din{dz, dy, dx};
+  const Dims3 dout = conv_out_dims(din, ksize, stride);
+  OPCK(conv3d_fwd_f32(x, W, b, y, batch, din, ci, co, ksize, stride, din.count() * ci,
+                      dout.count() * co, w_bs, (cudaStream_t)stream));
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_conv3d_dgrad(const float* dyp, const float* W, float* dxp, int batch, int dz,
+                              int dy, int dx, int ci, int co, int ksize, int stride,
+                              long long w_bs, int accumulate, void* stream) {
+  if (!dyp || !W || !dxp) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
+  if (bad_conv(batch, dz, dy, dx, ci, co, ksize, stride))
+    return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad convolution shape");
+  const Dims3 din{dz, dy, dx};
+  const Dims3 dout = conv_out_dims(din, ksize, stride);
+  OPCK(conv3d_dgrad_f32(dyp, W, dxp, batch, din, ci, co, ksize, stride, dout.count() * co,
+                        din.count() * ci, w_bs, accumulate, (cudaStream_t)stream));
+  return D2IP_OK;
+}
+
+long long d2ip_conv3d_wgrad_workspace(int batch, int dz, int dy, int dx, int ci, int co,
+                                      int ksize, int stride) {
+  if (bad_conv(batch, dz, dy, dx, ci, co, ksize, stride)) return -1;
+  const Dims3 din{dz, dy, dx};
+  return (long long)sizeof(float) * batch * conv3d_wgrad_chunks(din, ksize, stride) *
+         ((long long)co * ksize * ksize * ksize * ci + co);
+}
+
+d2ip_status d2ip_conv3d_wgrad(const float* x, const float* dyp, float* dWb, int batch, int dz,
+                              int dy, int dx, int ci, int co, int ksize, int stride,
+                              long long dw_bs, int accumulate, void* workspace,
+                              long long ws_bytes, void* stream) {
+  if (!x || !dyp || !dWb || !workspace) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
+  if (bad_conv(batch, dz, dy, dx, ci, co, ksize, stride))
+    return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad convolution shape");
+  if (ws_bytes < d2ip_conv3d_wgrad_workspace(batch, dz, dy, dx, ci, co, ksize, stride))
+    return fail(nullptr, D2IP_ERR_BAD_ARG, "workspace too small");
+  const Dims3 din{dz, dy, dx};
+  const Dims3 dout = conv_out_dims(din, ksize, stride);
+  float* part = static_cast<float*>(workspace);
+  OPCK(conv3d_wgrad_partial_f32(x, dyp, part, batch, din, ci, co, ksize, stride,
+                                din.count() * ci, dout.count() * co, (cudaStream_t)stream));
+  const long long row = (long long)co * ksize * ksize * ksize * ci + co;
+  OPCK(reduce_rows_f32(part, dWb, batch, conv3d_wgrad_chunks(din, ksize, stride), row,
+                       dw_bs ? dw_bs : row, accumulate, (cudaStream_t)stream));
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_layernorm_act_forward(const float* z, const float* gb, const float* resid,
+                                       float* y, float* xhat, float* rstd, int batch,
+                                       long long nvox, int c, int act, long long gb_bs,
+                                       void* stream) {
+  if (!z || !gb || !y || !xhat || !rstd) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
+  if (batch < 1 || nvox < 1 || c < 4 || c % 4 || c > 128 || (act != 0 && act != 1))
+    return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad LayerNorm shape (c multiple of 4, <= 128)");
+  OPCK(layernorm_act_fwd_f32(z, gb, resid, y, xhat, rstd, batch, nvox, c, act, gb_bs,
+                             (cudaStream_t)stream));
+  return D2IP_OK;
+}
+
+long long d2ip_layernorm_workspace(int batch, long long nvox, int c) {
+  if (batch < 1 || nvox < 1 || c < 4 || c % 4 || c > 128) return -1;
+  return (long long)sizeof(float) * batch * layernorm_bwd_blocks(nvox, c) * 2 * c;
+}
+
+d2ip_status d2ip_layernorm_act_backward(const float* dy, const float* act_out,
+                                        const float* xhat, const float* rstd, const float* gb,
+                                        float* dz, float* dt, float* dgb, int batch,
+                                        long long nvox, int c, long long gb_bs, int accumulate,
+                                        void* workspace, long long ws_bytes, void* stream) {
+  if (!dy || !xhat || !rstd || !gb || !dz || !dgb || !workspace)
+    return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
+  if (batch < 1 || nvox < 1 || c < 4 || c % 4 || c > 128)
+    return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad LayerNorm shape (c multiple of 4, <= 128)");
+  if (ws_bytes < d2ip_layernorm_workspace(batch, nvox, c))
+    return fail(nullptr, D2IP_ERR_BAD_ARG, "workspace too small");
+  float* part = static_cast<float*>(workspace);
+  OPCK(layernorm_act_bwd_f32(dy, act_out, xhat, rstd, gb, dz, dt, part, batch, nvox, c, gb_bs,
+                             (cudaStream_t)stream));
+  OPCK(reduce_rows_f32(part, dgb, batch, layernorm_bwd_blocks(nvox, c), 2 * c, 2 * c,
+                       accumulate, (cudaStream_t)stream));
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_upsample_concat_forward(const float* low, const float* skip, float* cat,
+                                         int batch, int lz, int ly, int lx, int oz, int oy,
+                                         int ox, int cu, int cs, void* stream) {
+  if (!low || !cat || (cs > 0 && !skip)) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
+  if (batch < 1 || lz < 1 || ly < 1 || lx < 1 || oz < 1 || oy < 1 || ox < 1 || cu < 1 || cs < 0)
+    return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad upsample shape");
+  OPCK(upsample_concat_fwd_f32(low, skip, cat, batch, Dims3{lz, ly, lx}, Dims3{oz, oy, ox}, cu,
+                               cs, (cudaStream_t)stream));
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_upsample_concat_backward(const float* dcat, float* dlow, float* dskip,
+                                          int batch, int lz, int ly, int lx, int oz, int oy,
+                                          int ox, int cu, int cs, void* stream) {
+  if (!dcat || !dlow) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
+  if (batch < 1 || lz < 1 || ly < 1 || lx < 1 || oz < 1 || oy < 1 || ox < 1 || cu < 1 || cs < 0)
+    return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad upsample shape");
+  // the gather visits at most 8 outputs per input and axis: needs out/in <= about 3
+  if (oz > 3 * lz || oy > 3 * ly || ox > 3 * lx)
+    return fail(nullptr, D2IP_ERR_BAD_SHAPE, "upsample factor above 3 not supported");
+  OPCK(upsample_concat_bwd_f32(dcat, dlow, dskip, batch, Dims3{lz, ly, lx}, Dims3{oz, oy, ox},
+                               cu, cs, (cudaStream_t)stream));
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_sensitivity_residual(const float* J, const float* x, const float* dv,
+                                      float* r, double* loss, int batch, int m, int n,
+                                      void* stream) {
+  if (!J || !x || !dv || !r) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
+  if (batch < 1 || m < 1 || n < 1) return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad J shape");
+  OPCK(jmul_residual_f32(J, x, dv, r, batch, m, n, n, (cudaStream_t)stream));
+  if (loss)
+    OPCK(residual_loss_f64(r, loss, nullptr, nullptr, nullptr, nullptr, batch, m,
+                           (cudaStream_t)stream));
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_sensitivity_adjoint(const float* J, const float* r, float* g, float scale,
+                                     int batch, int m, int n, void* stream) {
+  if (!J || !r || !g) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
+  if (batch < 1 || m < 1 || n < 1 || m > 6400)
+    return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad J shape (m <= 6400)");
+  OPCK(prepare_pointwise_kernels());
+  OPCK(jtmul_f32(J, r, g, scale, batch, m, n, n, (cudaStream_t)stream));
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_normalize_columns(float* J, double* colnorm, int m, int n, void* stream) {
+  if (!J || !colnorm) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
+  if (m < 1 || n < 1) return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad J shape");
+  OPCK(normalize_columns_f64(J, colnorm, m, n, (cudaStream_t)stream));
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_adam_update(float* theta, const float* g, float* m, float* v, long long count,
+                             double lr, double beta1, double beta2, double eps, int t,
+                             void* stream) {
+  if (!theta || !g || !m || !v) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
+  if (count < 1 || t < 1 || !(lr > 0.0) || !(eps > 0.0))
+    return fail(nullptr, D2IP_ERR_BAD_ARG, "bad Adam arguments");
+  OPCK(adam_step_f32(theta, g, m, v, count, lr, beta1, beta2, eps, nullptr, t,
+                     (cudaStream_t)stream));
+  return D2IP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,190 @@
+"""Parity of the full DIP iteration, frame fit and UPWS/TPP sequence (CUDA path through the
+C ABI) against the FP64 oracle.
+
+* teacher-forced iteration: the GPU starts from the oracle's state theta_k (and Adam
+  moments) and takes one step; Delta sigma, the loss, dL/dtheta (per tensor) and
+  theta_{k+1} must agree within 1e-5 norm-wise relative error (FP32 path);
+* index maps: the parameter table is bit-identical to the oracle's layout;
+* end to end: per-frame ERR within 1e-3 relative of the oracle's.
+"""
+import numpy as np
+import pytest
+
+from oracle import dip, network as onet
+from tests import problems
+from tests.problems import rel
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def _ctx(d2ip, pb, lr=1e-3, batch=1, precision=0):
+    s = pb.spec
+    c = d2ip.Context(s.grid, s.levels, s.widths, s.c_in, precision, batch)
+    c.load_J(pb.J)
+    c.set_input(np.tile(pb.Zin[None], (batch, 1, 1)), np.tile(pb.theta0[None], (batch, 1)))
+    c.set_optim(lr)
+    return c
+
+
+SHAPES = [((16, 16, 8), 1, 2, (8, 16)),          # single-frame workload
+          ((11, 9, 7), 1, 3, (8, 16, 32)),       # odd grid: ragged tiles, odd down/up sizes
+          ((32, 32, 16), 2, 3, (16, 32, 64))]    # 20-frame sequence workload
+
+
+@pytest.mark.parametrize("grid,rings,L,widths", SHAPES)
+def test_parameter_table_matches_oracle_layout(d2ip, grid, rings, L, widths):
+    pb = problems.make(grid, rings, L, widths)
+    c = d2ip.Context(grid, L, widths, 8)
+    tab = c.table()
+    ref = np.array(problems.oracle_table(pb.spec), dtype=np.int64)
+    np.testing.assert_array_equal(tab, ref)
+    assert c.P == onet.param_count(pb.spec)
+
+
+@pytest.mark.parametrize("grid,rings,L,widths", SHAPES)
+@pytest.mark.parametrize("k_pre", [0, 3])
+def test_teacher_forced_iteration(d2ip, grid, rings, L, widths, k_pre):
+    pb = problems.make(grid, rings, L, widths, seed=1)
+    lr = 1e-3
+    Z64 = pb.Zin.astype(np.float64)
+    dv = pb.V[0].astype(np.float64)
+    # oracle state after k_pre steps, rounded to float32 (what the GPU can hold)
+    th = pb.theta0.astype(np.float64)
+    st = dip.AdamState.fresh(th.size)
+    for _ in range(k_pre):
+        th = dip.dip_step(pb.spec, pb.Jn64, Z64, dv, th, st, lr).theta
+    th32, m32, v32 = (a.astype(np.float32) for a in (th, st.m, st.v))
+    st = dip.AdamState(m32.astype(np.float64), v32.astype(np.float64), st.t)
+    ref = dip.dip_step(pb.spec, pb.Jn64, Z64, dv, th32.astype(np.float64), st, lr)
+
+    c = _ctx(d2ip, pb, lr)
+    c.set_state(th32[None], m32[None], v32[None], k_pre)
+    ds = c.forward()[0]
+    tr = c.run_steps(pb.V[:1], 1, trace=True)
+    g = c.grad()[0]
+    th1, m1, v1, t1 = c.state()
+    assert rel(ds, ref.dsigma) < TOL
+    assert abs(tr[0, 0] - ref.loss) <= TOL * ref.loss
+    for name, shape, kind, fi, off, cnt in onet.param_layout(pb.spec):
+        assert rel(g[off:off + cnt], ref.grad[off:off + cnt]) < TOL, name
+    assert rel(th1[0], ref.theta) < TOL
+    assert rel(m1[0], st.m) < TOL and rel(v1[0], st.v) < TOL
+    assert t1 == k_pre + 1
+
+
+def test_single_frame_fit_matches_oracle_err(d2ip):
+    """Plain DIP on the 16x16x8 single-frame workload: 200 Adam steps, lr 1e-3."""
+    pb = problems.make((16, 16, 8), 1, 2, (8, 16), seed=0)
+    ref = dip.fit_frame(pb.spec, pb.Jn64, pb.Zin.astype(np.float64),
+                        pb.V[0].astype(np.float64), pb.theta0, 200, 1e-3)
+    c = _ctx(d2ip, pb, 1e-3)
+    ds, res, tr = c.fit_frame(pb.V[:1], 200, trace=True)
+    e_gpu = dip.err_ratio(ds[0], pb.truth[0])
+    e_ref = dip.err_ratio(ref.dsigma, pb.truth[0])
+    assert abs(e_gpu - e_ref) <= 1e-3 * e_ref
+    # the loss curve follows the oracle's (drift grows slowly with the iteration count)
+    assert rel(tr[:20, 0], ref.losses[:20]) < 1e-4
+    gpu_err = c.err_ratio(ds, pb.truth[:1].astype(np.float32))
+    assert abs(gpu_err[0] - e_gpu) < 1e-6
+    assert abs(res[0] - dip.data_term(pb.Jn64, ds[0].astype(np.float64),
+                                      pb.V[0].astype(np.float64))[1]) < 1e-5 * res[0]
+
+
+def test_sequence_matches_oracle_and_manual_chaining(d2ip):
+    """UPWS + TPP on a short 4-frame breathing sequence (16x16x8 grid, one ring)."""
+    pb = problems.make((16, 16, 8), 1, 2, (8, 16), seed=2, T=4)
+    lr, up, first, later = 1e-3, 30, 15, 10
+    ref = dip.fit_sequence(pb.spec, pb.Jn64, pb.Zin.astype(np.float64), pb.V, pb.theta0, up,
+                           first, later, lr)
+    c = _ctx(d2ip, pb, lr)
+    Sig, res = c.fit_sequence(pb.V[None], up, first, later)
+    for i in range(4):
+        if np.abs(pb.truth[i]).max() == 0:
+            continue
+        e_gpu = dip.err_ratio(Sig[0, i], pb.truth[i])
+        e_ref = dip.err_ratio(ref.Sigma[i], pb.truth[i])
+        assert abs(e_gpu - e_ref) <= 1e-3 * e_ref, i
+        # the residual is reported, not gated: it follows the trajectory's FP32 drift
+        assert abs(res[0, i] - ref.residuals[i]) <= 1e-2 * ref.residuals[i]
+    # the same schedule chained by hand through the frame API is bit-identical
+    c2 = _ctx(d2ip, pb, lr)
+    c2.run_steps(pb.V[:1], up)
+    for i in range(4):
+        ds, r, _ = c2.fit_frame(pb.V[i:i + 1], first if i == 0 else later)
+        np.testing.assert_array_equal(ds[0], Sig[0, i])
+        assert r[0] == res[0, i]
+
+
+def test_batch_equals_independent_problems(d2ip):
+    """B problems fitted in lockstep give bit-identical results to B separate contexts."""
+    pbs = [problems.make((11, 9, 7), 1, 2, (8, 16), seed=s) for s in (3, 4, 5)]
+    base = pbs[0]
+    J = base.J
+    B = 3
+    c = d2ip.Context(base.spec.grid, 2, (8, 16), 8, 0, B)
+    c.load_J(J)
+    c.set_input(np.stack([p.Zin for p in pbs]), np.stack([p.theta0 for p in pbs]))
+    c.set_optim(1e-3)
+    V = np.stack([p.V[0] for p in pbs])
+    ds, res, _ = c.fit_frame(V, 15)
+    for b, p in enumerate(pbs):
+        ci = d2ip.Context(base.spec.grid, 2, (8, 16), 8, 0, 1)
+        ci.load_J(J)
+        ci.set_input(p.Zin, p.theta0)
+        ci.set_optim(1e-3)
+        dsi, resi, _ = ci.fit_frame(p.V[:1], 15)
+        np.testing.assert_array_equal(ds[b], dsi[0])
+        assert res[b] == resi[0]
+
+
+def test_checkpoint_resume_is_exact(d2ip):
+    pb = problems.make((16, 16, 8), 1, 2, (8, 16), seed=6)
+    c = _ctx(d2ip, pb)
+    c.run_steps(pb.V[:1], 7)
+    th, m, v, t = c.state()
+    c.run_steps(pb.V[:1], 5)
+    a = c.forward()
+    c2 = _ctx(d2ip, pb)
+    c2.set_state(th, m, v, t)
+    c2.run_steps(pb.V[:1], 5)
+    np.testing.assert_array_equal(c2.forward(), a)
+
+
+def test_column_norms_fp64(d2ip):
+    pb = problems.make((16, 16, 8), 1, 2, (8, 16))
+    c = _ctx(d2ip, pb)
+    _, cn = dip.normalise_columns(pb.J)
+    np.testing.assert_allclose(c.colnorms(), cn, rtol=1e-13)
+
+
+def test_nonfinite_measurements_are_reported(d2ip):
+    pb = problems.make((16, 16, 8), 1, 2, (8, 16))
+    c = _ctx(d2ip, pb)
+    bad = pb.V[:1].copy()
+    bad[0, 3] = np.nan
+    with pytest.raises(d2ip.D2IPError) as e:
+        c.fit_frame(bad, 2)
+    assert e.value.status == -4
+
+
+def test_shape_and_order_errors(d2ip):
+    h = d2ip.d2ip_create(0)
+    try:
+        with pytest.raises(d2ip.D2IPError) as e:
+            d2ip.d2ip_set_network(h, 2, [8, 16], 8, 0, 1)
+        assert e.value.status == -7
+        d2ip.d2ip_set_grid(h, 16, 16, 8)
+        with pytest.raises(d2ip.D2IPError) as e:
+            d2ip.d2ip_set_network(h, 2, [8, 18], 8, 0, 1)
+        assert e.value.status == -2
+        d2ip.d2ip_set_network(h, 2, [8, 16], 8, 0, 1)
+        J = np.zeros((208, 100), np.float32)
+        with pytest.raises(d2ip.D2IPError) as e:
+            d2ip.d2ip_load_J(h, J, 208, 100, 1)
+        assert e.value.status == -2
+        with pytest.raises(d2ip.D2IPError) as e:
+            d2ip.d2ip_run_steps(h, np.zeros(208, np.float32), 1, None)
+        assert e.value.status == -7
+    finally:
+        d2ip.d2ip_destroy(h)
