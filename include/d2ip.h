@@ -194,6 +194,26 @@ d2ip_status d2ip_conv3d_wgrad(const float* x, const float* dy, float* dWb, int b
                               long long dw_batch_stride, int accumulate, void* workspace,
                               long long workspace_bytes, void* stream);
 
+/* The weight gradient above, for callers that cannot allocate device memory while they
+ * need it: a bedside monitoring loop that runs with a fixed device footprint and must not
+ * block or fail on the allocator mid-sequence, or a host application whose device memory is
+ * all owned by another allocator (a framework's caching pool), so it has no workspace to
+ * hand over.  This entry point allocates nothing (no cudaMalloc, cudaFree or allocating
+ * library call): its partial sums live in a 16 MiB static __device__ array that is part of
+ * the library on every GPU that loads it, until the process exits.  The paper has no
+ * counterpart; it is an interface convenience.
+ * Same arguments and result as d2ip_conv3d_wgrad without the workspace.  Sizes whose
+ * d2ip_conv3d_wgrad_workspace exceeds 16 MiB are rejected with D2IP_ERR_BAD_SHAPE.  The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current) and caches it; make that first call before any stream capture.
+ * All calls share the one array, and it keeps the last call's partial sums (each call
+ * writes every partial it reads, so nothing needs clearing): calls that overlap on the GPU
+ * (different streams, or different host threads) race and must not be issued. */
+d2ip_status d2ip_conv3d_wgrad_noalloc(const float* x, const float* dy, float* dWb, int batch,
+                                      int dz, int dy_, int dx_, int ci, int co, int ksize,
+                                      int stride, long long dw_batch_stride, int accumulate,
+                                      void* stream);
+
 /* y = act(gamma * xhat + beta (+ resid)), xhat = (z - mean)/sqrt(var + 1e-5) over the c
  * channels of each voxel; saves xhat ([batch][nvox][c]) and rstd ([batch][nvox]) for the
  * backward.  gamma_beta = [gamma[c], beta[c]] per problem.  act: 0 none, 1 LeakyReLU(0.2).

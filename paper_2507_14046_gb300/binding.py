@@ -61,6 +61,8 @@ _SIGS = {
     "d2ip_conv3d_dgrad": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _ll, _i, _vp],
     "d2ip_conv3d_wgrad": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _ll, _i, _vp, _ll,
                           _vp],
+    "d2ip_conv3d_wgrad_noalloc": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _ll, _i,
+                                  _vp],
     "d2ip_layernorm_act_forward": [_vp, _vp, _vp, _vp, _vp, _vp, _i, _ll, _i, _i, _ll, _vp],
     "d2ip_layernorm_act_backward": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _ll, _i, _ll,
                                     _i, _vp, _ll, _vp],
@@ -185,6 +187,7 @@ for _name in ("d2ip_set_grid", "d2ip_load_J", "d2ip_get_colnorms", "d2ip_set_inp
               "d2ip_err_ratio", "d2ip_sync", "d2ip_profile_iterations"):
     globals()[_name] = _wrap_ctx(_name)
 for _name in ("d2ip_conv3d_forward", "d2ip_conv3d_dgrad", "d2ip_conv3d_wgrad",
+              "d2ip_conv3d_wgrad_noalloc",
               "d2ip_layernorm_act_forward", "d2ip_layernorm_act_backward",
               "d2ip_upsample_concat_forward", "d2ip_upsample_concat_backward",
               "d2ip_sensitivity_residual", "d2ip_sensitivity_adjoint", "d2ip_normalize_columns",

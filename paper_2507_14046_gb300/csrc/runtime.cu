@@ -633,6 +633,11 @@ d2ip_status stage_dv(d2ip_ctx* c, const float* dV, long long spitch) {
 
 }  // namespace
 
+namespace d2ip {
+// Message for d2ip_last_error(NULL) from op entry points defined in other files.
+void record_op_error(const std::string& msg) { g_op_error = msg; }
+}  // namespace d2ip
+
 // =====================================================================================
 // C ABI
 // =====================================================================================
