@@ -184,6 +184,23 @@ d2ip_status d2ip_conv3d_forward(const float* x, const float* W, const float* b, 
 d2ip_status d2ip_conv3d_dgrad(const float* dy, const float* W, float* dx, int batch, int dz,
                               int dy_, int dx_, int ci, int co, int ksize, int stride,
                               long long w_batch_stride, int accumulate, void* stream);
+/* Tensor-core forms (tcgen05, sm_103a) of the two calls above: x (or dy) and W are rounded
+ * to BF16 (round to nearest even), products accumulate in FP32 in tensor memory; the
+ * bias is added in FP32.  Needs ci and co multiples of 16, co <= 256 (and, for the data
+ * gradient, stride 1).  `workspace` (device, d2ip_conv3d_tc_workspace bytes) receives the
+ * BF16 staging copies; the int at its first 1024-byte aligned address is an error word,
+ * non-zero after the call when a pipeline wait of the kernel gave up (about 1 s). */
+long long d2ip_conv3d_tc_workspace(int batch, int dz, int dy, int dx, int ci, int co,
+                                   int ksize, int stride);
+d2ip_status d2ip_conv3d_forward_tc(const float* x, const float* W, const float* b, float* y,
+                                   int batch, int dz, int dy, int dx, int ci, int co, int ksize,
+                                   int stride, long long w_batch_stride, void* workspace,
+                                   long long workspace_bytes, void* stream);
+d2ip_status d2ip_conv3d_dgrad_tc(const float* dy, const float* W, float* dx, int batch, int dz,
+                                 int dy_, int dx_, int ci, int co, int ksize, int stride,
+                                 long long w_batch_stride, int accumulate, void* workspace,
+                                 long long workspace_bytes, void* stream);
+
 /* Workspace bytes needed by d2ip_conv3d_wgrad for these sizes. */
 long long d2ip_conv3d_wgrad_workspace(int batch, int dz, int dy, int dx, int ci, int co,
                                       int ksize, int stride);

@@ -1,20 +1,523 @@
-// Tensor-core path (tcgen05).  Not enabled yet: every query reports "unsupported", so the
-// runtime rejects D2IP_BF16 at d2ip_set_network.
+// Implicit-GEMM 3D convolution on the 5th-generation tensor cores (tcgen05), sm_103a.
+//
+// GEMM view: D[M = output voxels][N = Co] = sum over taps t and input channels c of
+// A_t[voxel][c] * W[co][t][c], accumulated in FP32 in tensor memory (TMEM).
+//
+// * A tile: 128 output voxels = an 8 x 4 x 4 (x, y, z) box.  For tap t and channel chunk c0
+//   its im2col rows are exactly one TMA box of the channels-last input volume, shifted by
+//   the tap offset (and traversed with element stride 2 for the stride-2 convolutions); the
+//   zero padding of the convolution is TMA's out-of-bounds fill, so the halo costs nothing.
+//   The box lands in shared memory in the K-major swizzled layout the MMA reads (32/64/128-byte
+//   swizzle for 16/32/64-channel chunks).
+// * B tile: the [Co][chunk] weights of tap t, one TMA box of the BF16 weight copy.
+// * One thread of warp 1 issues tcgen05.mma (M 128, N Co, K 16) and commits each stage
+//   back to the producer; one thread of warp 0 issues the TMA loads into a 4-stage ring
+//   guarded by mbarriers; after the last MMA all four warps read their 32 TMEM lanes
+//   (thread = output voxel, registers = its Co channels) and write FP32 results.
+// Every wait on an mbarrier is bounded by a clock budget; on expiry the kernel records an
+// error code, lets the in-flight MMAs drain, frees its TMEM and returns.
+#include <cuda.h>
+
+#include <algorithm>
+
 #include "conv_bf16.cuh"
 
 namespace d2ip {
+namespace {
 
-bool bf16_network_supported(int, const int*, int) { return false; }
-bool bf16_conv_supported(int, int, int) { return false; }
-void bf16_layout(Bf16Net&, char*, size_t&, int, long long, long long, long long) {}
-cudaError_t bf16_prepare_kernels() { return cudaSuccess; }
-cudaError_t bf16_prepare_weights(Bf16Net&, const float*, int, long long, cudaStream_t) {
+constexpr int kBX = 8, kBY = 4, kBZ = 4;  // output voxel box of one 128-row tile
+constexpr int kBM = kBX * kBY * kBZ;
+constexpr int kStages = 4;
+constexpr long long kWaitCycles = 2000000000LL;  // about one second at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false when the budget ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, int c4, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
+      "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor, K-major, swizzled rows of CK bf16 (32/64/128 bytes),
+// consecutive rows, 8-row groups SBO = 8 * row bytes apart.
+template <int CK>
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  constexpr uint64_t kSwizzle = CK == 16 ? 6 : (CK == 32 ? 4 : 2);  // 32B / 64B / 128B
+  constexpr uint64_t kSbo = 8ull * CK * 2;
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= 1ull << 16;                  // leading byte offset: unused for swizzled K-major
+  d |= (kSbo >> 4) << 32;
+  d |= 1ull << 46;                  // descriptor version of tcgen05
+  d |= kSwizzle << 61;
+  return d;
+}
+
+// Instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t instr_desc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(kBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+constexpr int kErrProducer = 1, kErrMma = 2, kErrEpilogue = 4;
+
+template <int CK>
+__global__ void __launch_bounds__(128, 1)
+conv_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
+               const float* __restrict__ bias, float* __restrict__ out, Dims3 dout, int N,
+               int K, int S, int nchunks, int tiles_x, int tiles_y, long long out_bs,
+               long long bias_bs, int accumulate, int* __restrict__ err) {
+  constexpr uint32_t kABytes = kBM * CK * 2;
+  const uint32_t b_bytes = (uint32_t)N * CK * 2;
+  const uint32_t stage_bytes = kABytes + b_bytes;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
+  __shared__ uint32_t tmem_base_s;
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int b = blockIdx.z;
+  const int tile = blockIdx.x;
+  const int x0 = (tile % tiles_x) * kBX;
+  const int y0 = ((tile / tiles_x) % tiles_y) * kBY;
+  const int z0 = (tile / (tiles_x * tiles_y)) * kBZ;
+  const int T = K * K * K, pad = (K - 1) / 2;
+  const int ksteps = T * nchunks;
+  const uint32_t tmem_cols = N <= 32 ? 32u : N <= 64 ? 64u : N <= 128 ? 128u : 256u;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_u32(&done_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_s)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  if (warp == 0 && lane == 0) {  // TMA producer
+    for (int k = 0; k < ksteps; ++k) {
+      const int s = k % kStages, round = k / kStages;
+      if (round > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (round - 1) & 1)) {
+        atomicOr(err, kErrProducer);
+        break;
+      }
+      const int t = k / nchunks, c = k % nchunks;
+      const int kz = t / (K * K), ky = (t / K) % K, kx = t % K;
+      const uint32_t a_dst = smem_u32(smem + (size_t)s * stage_bytes);
+      const uint32_t fb = smem_u32(&full_bar[s]);
+      mbar_expect_tx(fb, stage_bytes);
+      tma_load_5d(a_dst, &tm_a, c * CK, x0 * S + kx - pad, y0 * S + ky - pad, z0 * S + kz - pad,
+                  b, fb);
+      tma_load_4d(a_dst + kABytes, &tm_b, c * CK, t, 0, b, fb);
+    }
+  } else if (warp == 1 && lane == 0) {  // MMA issuer
+    const uint32_t idesc = instr_desc(N);
+    for (int k = 0; k < ksteps; ++k) {
+      const int s = k % kStages;
+      if (!mbar_wait(smem_u32(&full_bar[s]), (k / kStages) & 1)) {
+        atomicOr(err, kErrMma);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a_addr = smem_u32(smem + (size_t)s * stage_bytes);
+      const uint32_t b_addr = a_addr + kABytes;
+#pragma unroll
+      for (int kk = 0; kk < CK / 16; ++kk)
+        mma_bf16(tmem, smem_desc<CK>(a_addr + kk * 32), smem_desc<CK>(b_addr + kk * 32), idesc,
+                 (k > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(smem_u32(&empty_bar[s]));
+    }
+    mma_commit(smem_u32(&done_bar));  // fires once every issued MMA has completed
+  }
+  __syncwarp();
+
+  const bool ok = mbar_wait(smem_u32(&done_bar), 0);
+  if (!ok && lane == 0) atomicOr(err, kErrEpilogue);
+  tc_fence_after();
+  if (ok) {
+    const int m = warp * 32 + lane;  // TMEM lane = tile row = voxel of the box
+    const int ox = x0 + m % kBX, oy = y0 + (m / kBX) % kBY, oz = z0 + m / (kBX * kBY);
+    const bool inside = ox < dout.x && oy < dout.y && oz < dout.z;
+    const long long vox = ((long long)oz * dout.y + oy) * dout.x + ox;
+    float* o = out + (long long)b * out_bs + vox * N;
+    const float* bb = bias ? bias + (long long)b * bias_bs : nullptr;
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+      if (inside) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          float v = __uint_as_float(r[j]) + (bb ? bb[c0 + j] : 0.f);
+          o[c0 + j] = accumulate ? o[c0 + j] + v : v;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(tmem_cols)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// staging kernels
+// ------------------------------------------------------------------------------------
+__global__ void f32_to_bf16_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ y,
+                                   long long n) {
+  const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (i + 3 < n) {
+    const float4 v = *reinterpret_cast<const float4*>(x + i);
+    __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), c = __floats2bfloat162_rn(v.z, v.w);
+    *reinterpret_cast<__nv_bfloat162*>(y + i) = a;
+    *reinterpret_cast<__nv_bfloat162*>(y + i + 2) = c;
+  } else {
+    for (long long j = i; j < n; ++j) y[j] = __float2bfloat16_rn(x[j]);
+  }
+}
+
+// Forward weights [co][t][ci] and data-gradient weights [ci][T-1-t][co] of one layer, for
+// every problem of the batch.
+__global__ void weights_bf16_kernel(const float* __restrict__ theta, __nv_bfloat16* __restrict__ wb,
+                                    long long Pp, long long wstride, long long w_off,
+                                    long long wf_off, long long wd_off, int ci, int co, int T,
+                                    int dgrad) {
+  const int b = blockIdx.y;
+  const long long n = (long long)co * T * ci;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const float v = theta[(long long)b * Pp + w_off + e];
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  __nv_bfloat16* base = wb + (long long)b * wstride;
+  base[wf_off + e] = h;
+  if (dgrad) {
+    const int c = (int)(e % ci);
+    const long long r = e / ci;
+    const int t = (int)(r % T), o = (int)(r / T);
+    base[wd_off + ((long long)c * T + (T - 1 - t)) * co + o] = h;
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+int chunk_for(int c) { return c % 64 == 0 ? 64 : (c % 32 == 0 ? 32 : 16); }
+
+CUtensorMapSwizzle swizzle_for(int ck) {
+  return ck == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                  : (ck == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+}
+
+// Channels-last BF16 activations [B][Z][Y][X][C] as a 5-D map, box = one tile's taps.
+cudaError_t encode_act(CUtensorMap* m, void* base, int B, Dims3 d, int C, int ck, int S) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)d.x, (cuuint64_t)d.y, (cuuint64_t)d.z,
+                              (cuuint64_t)B};
+  const cuuint64_t es = 2;
+  const cuuint64_t strides[4] = {C * es, C * es * d.x, C * es * d.x * d.y,
+                                 C * es * d.x * d.y * d.z};
+  const cuuint32_t box[5] = {(cuuint32_t)ck, (cuuint32_t)(kBX * S), (cuuint32_t)(kBY * S),
+                             (cuuint32_t)(kBZ * S), 1};
+  const cuuint32_t estr[5] = {1, (cuuint32_t)S, (cuuint32_t)S, (cuuint32_t)S, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(ck),
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Weights [B][Cout][T][Cin] (BF16) as a 4-D map (Cin, T, Cout, B), box = one tap's chunk.
+cudaError_t encode_w(CUtensorMap* m, void* base, int B, long long wstride, int cin, int T,
+                     int cout, int ck) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[4] = {(cuuint64_t)cin, (cuuint64_t)T, (cuuint64_t)cout, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {(cuuint64_t)cin * 2, (cuuint64_t)cin * T * 2,
+                                 (cuuint64_t)wstride * 2};
+  const cuuint32_t box[4] = {(cuuint32_t)ck, 1, (cuuint32_t)cout, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(ck),
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+size_t smem_bytes(int ck, int n) { return (size_t)kStages * (kBM + n) * ck * 2 + 1024; }
+
+cudaError_t launch_tc(const CUtensorMap& a, const CUtensorMap& w, int cin, const float* bias,
+                      float* out, Dims3 dout, int n, int K, int S, int B, long long out_bs,
+                      long long bias_bs, int acc, int* err, cudaStream_t st) {
+  const int ck = chunk_for(cin);
+  const int tx = (int)ceil_div(dout.x, kBX), ty = (int)ceil_div(dout.y, kBY),
+            tz = (int)ceil_div(dout.z, kBZ);
+  dim3 grid((unsigned)(tx * ty * tz), 1, B);
+  const size_t sm = smem_bytes(ck, n);
+  const int nch = cin / ck;
+  switch (ck) {
+    case 64:
+      conv_tc_kernel<64><<<grid, 128, sm, st>>>(a, w, bias, out, dout, n, K, S, nch, tx, ty,
+                                                 out_bs, bias_bs, acc, err);
+      break;
+    case 32:
+      conv_tc_kernel<32><<<grid, 128, sm, st>>>(a, w, bias, out, dout, n, K, S, nch, tx, ty,
+                                                 out_bs, bias_bs, acc, err);
+      break;
+    default:
+      conv_tc_kernel<16><<<grid, 128, sm, st>>>(a, w, bias, out, dout, n, K, S, nch, tx, ty,
+                                                 out_bs, bias_bs, acc, err);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool bf16_conv_supported(int ci, int co, int k) {
+  return ci % 16 == 0 && co % 16 == 0 && co >= 16 && co <= 256 && (k == 3 || k == 1);
+}
+
+bool bf16_network_supported(int levels, const int* widths, int) {
+  for (int l = 0; l < levels; ++l)
+    if (widths[l] % 16 != 0) return false;
+  return true;
+}
+
+int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long long w_off) {
+  if (!bf16_conv_supported(ci, co, k)) return -1;
+  TcLayer L;
+  L.ci = ci;
+  L.co = co;
+  L.k = k;
+  L.s = s;
+  L.din = din;
+  L.dout = conv_out_dims(din, k, s);
+  L.w_off = w_off;
+  L.dgrad = (s == 1) && bf16_conv_supported(co, ci, k);
+  const long long n = (long long)co * k * k * k * ci;
+  L.wf_off = bf.wstride;
+  bf.wstride += (n + 63) / 64 * 64;
+  if (L.dgrad) {
+    L.wd_off = bf.wstride;
+    bf.wstride += (n + 63) / 64 * 64;
+  }
+  bf.layers.push_back(L);
+  return (int)bf.layers.size() - 1;
+}
+
+void bf16_layout(Bf16Net& bf, char* base, size_t& used, int B, long long max_act) {
+  auto take = [&](size_t bytes) {
+    char* p = base ? base + used : nullptr;
+    used += (bytes + 1023) / 1024 * 1024;
+    return p;
+  };
+  bf.max_act = max_act;
+  bf.err = reinterpret_cast<int*>(take(sizeof(int)));
+  bf.xbf = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * max_act * 2));
+  bf.wbuf = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * bf.wstride * 2));
+}
+
+cudaError_t bf16_finalize(Bf16Net& bf, int B) {
+  for (TcLayer& L : bf.layers) {
+    const int T = L.k * L.k * L.k;
+    cudaError_t e = encode_act(&L.act_f, bf.xbf, B, L.din, L.ci, chunk_for(L.ci), L.s);
+    if (e == cudaSuccess)
+      e = encode_w(&L.w_f, bf.wbuf + L.wf_off, B, bf.wstride, L.ci, T, L.co, chunk_for(L.ci));
+    if (e == cudaSuccess && L.dgrad) {
+      e = encode_act(&L.act_d, bf.xbf, B, L.dout, L.co, chunk_for(L.co), 1);
+      if (e == cudaSuccess)
+        e = encode_w(&L.w_d, bf.wbuf + L.wd_off, B, bf.wstride, L.co, T, L.ci, chunk_for(L.co));
+    }
+    if (e != cudaSuccess) return e;
+  }
   return cudaSuccess;
 }
-cudaError_t bf16_set_J(Bf16Net&, const float*, int, int, cudaStream_t) { return cudaSuccess; }
-cudaError_t bf16_conv_fwd(Bf16Net&, const float*, long long, const float*, float*, int, Dims3,
-                          int, int, int, int, long long, long long, long long, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+cudaError_t bf16_prepare_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<64>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes(64, 256));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(conv_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes(32, 256));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(conv_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes(16, 256));
+  return e;
+}
+
+cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long long Pp,
+                                 cudaStream_t stream) {
+  for (const TcLayer& L : bf.layers) {
+    const int T = L.k * L.k * L.k;
+    const long long n = (long long)L.co * T * L.ci;
+    dim3 grid((unsigned)ceil_div(n, 256), B);
+    weights_bf16_kernel<<<grid, 256, 0, stream>>>(theta, bf.wbuf, Pp, bf.wstride, L.w_off,
+                                                  L.wf_off, L.wd_off, L.ci, L.co, T,
+                                                  L.dgrad ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+static cudaError_t stage_bf16(const float* x, __nv_bfloat16* y, long long n, cudaStream_t st) {
+  f32_to_bf16_kernel<<<(unsigned)ceil_div(ceil_div(n, 4), 256), 256, 0, st>>>(x, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t bf16_conv_fwd(Bf16Net& bf, int layer, const float* x, const float* bias, float* y,
+                          int B, long long bias_bs, cudaStream_t stream) {
+  const TcLayer& L = bf.layers[layer];
+  cudaError_t e = stage_bf16(x, bf.xbf, (long long)B * L.din.count() * L.ci, stream);
+  if (e != cudaSuccess) return e;
+  return launch_tc(L.act_f, L.w_f, L.ci, bias, y, L.dout, L.co, L.k, L.s, B,
+                   L.dout.count() * L.co, bias_bs, 0, bf.err, stream);
+}
+
+cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, int B,
+                            int accumulate, cudaStream_t stream) {
+  const TcLayer& L = bf.layers[layer];
+  if (!L.dgrad) return cudaErrorInvalidValue;
+  cudaError_t e = stage_bf16(dy, bf.xbf, (long long)B * L.dout.count() * L.co, stream);
+  if (e != cudaSuccess) return e;
+  return launch_tc(L.act_d, L.w_d, L.co, nullptr, dx, L.din, L.ci, L.k, 1, B,
+                   L.din.count() * L.ci, 0, accumulate, bf.err, stream);
+}
+
+long long bf16_op_workspace(int B, Dims3 din, int ci, int co, int k, int s) {
+  const Dims3 dout = conv_out_dims(din, k, s);
+  const long long T = (long long)k * k * k;
+  const long long act = std::max(din.count() * ci, dout.count() * co);
+  const long long w = 2 * ((co * T * ci + 63) / 64 * 64);
+  return 1024 + ((long long)B * act * 2 + 1023) / 1024 * 1024 +
+         ((long long)B * w * 2 + 1023) / 1024 * 1024 + 1024;
+}
+
+cudaError_t bf16_op_conv(bool dgrad, const float* in, const float* W, const float* bias,
+                         float* out, int B, Dims3 din, int ci, int co, int k, int s,
+                         long long w_bs, int accumulate, void* workspace, cudaStream_t st) {
+  cudaError_t e = bf16_prepare_kernels();  // opt-in shared memory size, once per device
+  if (e != cudaSuccess) return e;
+  Bf16Net bf;
+  const int idx = bf16_add_layer(bf, ci, co, k, s, din, 0);
+  if (idx < 0 || (dgrad && !bf.layers[idx].dgrad)) return cudaErrorInvalidValue;
+  // per-problem weight blocks are packed at wstride in the workspace copy
+  size_t used = 0;
+  char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(workspace) + 1023) &
+                                       ~(uintptr_t)1023);
+  const Dims3 dout = conv_out_dims(din, k, s);
+  bf16_layout(bf, base, used, B, std::max(din.count() * ci, dout.count() * co));
+  e = bf16_finalize(bf, B);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bf.err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = bf16_prepare_weights(bf, W, B, w_bs, st);
+  if (e != cudaSuccess) return e;
+  return dgrad ? bf16_conv_dgrad(bf, idx, in, out, B, accumulate, st)
+               : bf16_conv_fwd(bf, idx, in, bias, out, B, w_bs, st);
 }
 
 }  // namespace d2ip

@@ -1,31 +1,63 @@
-// Tensor-core (tcgen05, BF16 x BF16 -> FP32) path of the convolutions and J products.
+// Tensor-core path of the 3D convolutions: implicit GEMM on tcgen05 (BF16 x BF16 -> FP32 in
+// TMEM), operands staged by TMA.
 #pragma once
 
+#include <cuda.h>
+
 #include <cstddef>
+#include <vector>
 
 #include "common.cuh"
 
 namespace d2ip {
 
-// Device buffers of the BF16 path, carved from the context arena.
+// One convolution served by the tensor cores, with its TMA descriptors.
+struct TcLayer {
+  CUtensorMap act_f;  // forward input (BF16 staging buffer, this layer's dims and channels)
+  CUtensorMap w_f;    // forward weights [B][Co][T][Ci] (BF16)
+  CUtensorMap act_d;  // stride-1 data-gradient input (dy staged in BF16)
+  CUtensorMap w_d;    // data-gradient weights [B][Ci][T][Co], taps reversed (BF16)
+  int ci = 0, co = 0, k = 3, s = 1;
+  Dims3 din{}, dout{};
+  long long w_off = 0;            // weights of this conv in the FP32 theta arena
+  long long wf_off = 0, wd_off = 0;  // offsets in the per-problem BF16 weight block
+  bool dgrad = false;             // data gradient on the tensor cores too (stride 1)
+};
+
+// Device buffers of the BF16 path (carved from the context arena) and its layers.
 struct Bf16Net {
-  __nv_bfloat16* wbf = nullptr;   // BF16 copy of theta (per problem, padded stride)
-  __nv_bfloat16* xbf = nullptr;   // BF16 staging of a conv input
-  __nv_bfloat16* Jbf = nullptr;   // BF16 copy of J
-  long long Pp = 0;
+  __nv_bfloat16* xbf = nullptr;   // BF16 staging of one convolution input (or dy)
+  __nv_bfloat16* wbuf = nullptr;  // BF16 weights of every tensor-core layer, per problem
+  long long wstride = 0;          // elements per problem in wbuf
+  long long max_act = 0;          // elements per problem of the largest staged input
+  int* err = nullptr;             // device error word (bounded waits that ran out)
+  std::vector<TcLayer> layers;
 };
 
 bool bf16_network_supported(int levels, const int* widths, int c_in);
 bool bf16_conv_supported(int ci, int co, int k);
+// Register a convolution; returns its index in bf.layers or -1 when it stays on FP32 SIMT.
+int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long long w_off);
 // Reserve the BF16 buffers in the arena (base == nullptr: size only).
-void bf16_layout(Bf16Net& bf, char* base, size_t& used, int B, long long Pp, long long max_act,
-                 long long zin_count);
+void bf16_layout(Bf16Net& bf, char* base, size_t& used, int B, long long max_act);
+// Encode the TMA descriptors once the buffers have addresses.
+cudaError_t bf16_finalize(Bf16Net& bf, int B);
 cudaError_t bf16_prepare_kernels();
+// theta (FP32, [B][Pp]) -> BF16 forward and data-gradient weights of every layer.
 cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long long Pp,
                                  cudaStream_t stream);
-cudaError_t bf16_set_J(Bf16Net& bf, const float* J, int m, int n, cudaStream_t stream);
-cudaError_t bf16_conv_fwd(Bf16Net& bf, const float* theta, long long w_off, const float* x,
-                          float* y, int B, Dims3 din, int Ci, int Co, int K, int S,
-                          long long x_bs, long long y_bs, long long w_bs, cudaStream_t stream);
+// y = conv(x) + bias on the tensor cores (x FP32 is staged to BF16 first).
+cudaError_t bf16_conv_fwd(Bf16Net& bf, int layer, const float* x, const float* bias, float* y,
+                          int B, long long bias_bs, cudaStream_t stream);
+// dx (=|+=) data gradient of a stride-1 layer on the tensor cores.
+cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, int B,
+                            int accumulate, cudaStream_t stream);
+
+// Context-free form for the op entry points: one layer, staging buffers, BF16 weights and
+// the error word carved from a caller workspace of bf16_op_workspace() bytes.
+long long bf16_op_workspace(int B, Dims3 din, int ci, int co, int k, int s);
+cudaError_t bf16_op_conv(bool dgrad, const float* in, const float* W, const float* bias,
+                         float* out, int B, Dims3 din, int ci, int co, int k, int s,
+                         long long w_bs, int accumulate, void* workspace, cudaStream_t st);
 
 }  // namespace d2ip

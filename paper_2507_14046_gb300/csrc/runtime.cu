@@ -26,6 +26,7 @@ struct ConvL {
   int ci = 0, co = 0, k = 3, s = 1;
   Dims3 din{}, dout{};
   long long w_off = 0;  // bias follows at w_off + co*k^3*ci
+  int tc = -1;          // index of its tensor-core layer (BF16 precision), -1: FP32 SIMT
   long long wcount() const { return (long long)co * k * k * k * ci; }
 };
 
@@ -97,7 +98,7 @@ struct d2ip_ctx {
   double* colnorm = nullptr;
   size_t j_bytes = 0;
   int seq_T_cap = 0;
-  Bf16Net bf;  // tensor-core path state (BF16 copies of weights and activations)
+  Bf16Net bf;  // tensor-core path: BF16 staging buffers, weights, TMA descriptors
 
   // graphs
   cudaGraphExec_t g_step = nullptr, g_eval = nullptr;
@@ -136,7 +137,6 @@ void free_arena(d2ip_ctx* c) {
   if (c->arena) cudaFree(c->arena);
   c->arena = nullptr;
   c->arena_bytes = 0;
-  c->bf = Bf16Net{};
 }
 
 // ------------------------------------------------------------------------------------
@@ -154,6 +154,7 @@ struct Builder {
     L.din = c->dims[lvl_in];
     L.dout = conv_out_dims(L.din, k, s);
     L.w_off = off;
+    if (c->precision == D2IP_BF16) L.tc = bf16_add_layer(c->bf, ci, co, k, s, L.din, off);
     const long long fan = (long long)ci * k * k * k;
     c->table.insert(c->table.end(), {D2IP_PARAM_CONV_W, off, L.wcount(), fan});
     off += L.wcount();
@@ -189,6 +190,7 @@ void build_plan(d2ip_ctx* c) {
   c->dims[0] = Dims3{c->Z, c->Y, c->X};
   for (int l = 1; l < c->L; ++l) c->dims[l] = conv_out_dims(c->dims[l - 1], 3, 2);
   c->table.clear();
+  c->bf = Bf16Net{};
   Builder b{c};
   const auto& w = c->w;
   c->stem.conv = b.conv(c->c_in, w[0], 3, 1, 0);
@@ -319,8 +321,12 @@ void layout_buffers(d2ip_ctx* c, Carve& cv) {
   c->trace_pos = cv.take<int>(1);
   c->adam_t = cv.take<int>(1);
   c->status = cv.take<int>(1);
-  if (c->precision == D2IP_BF16)
-    bf16_layout(c->bf, cv.dry ? nullptr : cv.base, cv.used, B, c->Pp, maxz, nv(0) * c->c_in);
+  if (c->precision == D2IP_BF16) {
+    long long max_act = 0;
+    for (int l = 0; l < c->L; ++l)
+      max_act = std::max(max_act, nv(l) * (w[l] + (l + 1 < c->L ? w[l + 1] : 0)));
+    bf16_layout(c->bf, cv.dry ? nullptr : cv.base, cv.used, B, max_act);
+  }
 }
 
 d2ip_status ensure_arena(d2ip_ctx* c) {
@@ -335,6 +341,7 @@ d2ip_status ensure_arena(d2ip_ctx* c) {
   Carve real{static_cast<char*>(p), 0, false};
   layout_buffers(c, real);
   CK(cudaMemsetAsync(p, 0, dry.used, c->stream));
+  if (c->precision == D2IP_BF16) CK(bf16_finalize(c->bf, c->B));
   return D2IP_OK;
 }
 
@@ -393,9 +400,8 @@ struct Launcher {
 
   void conv_fwd(const ConvL& L, const float* x, float* y) {
     beg(D2IP_KCLASS_CONV_FWD, conv_flops(L));
-    if (c->precision == D2IP_BF16 && bf16_conv_supported(L.ci, L.co, L.k)) {
-      ok(bf16_conv_fwd(c->bf, c->theta, L.w_off, x, y, c->B, L.din, L.ci, L.co, L.k, L.s,
-                       L.din.count() * L.ci, L.dout.count() * L.co, c->Pp, c->stream));
+    if (L.tc >= 0) {
+      ok(bf16_conv_fwd(c->bf, L.tc, x, W(L) + L.wcount(), y, c->B, c->Pp, c->stream));
     } else {
       ok(conv3d_fwd_f32(x, W(L), W(L) + L.wcount(), y, c->B, L.din, L.ci, L.co, L.k, L.s,
                         L.din.count() * L.ci, L.dout.count() * L.co, c->Pp, c->stream));
@@ -404,8 +410,11 @@ struct Launcher {
   }
   void conv_dgrad(const ConvL& L, const float* dy, float* dx, int acc) {
     beg(D2IP_KCLASS_CONV_DGRAD, conv_flops(L));
-    ok(conv3d_dgrad_f32(dy, W(L), dx, c->B, L.din, L.ci, L.co, L.k, L.s, L.dout.count() * L.co,
-                        L.din.count() * L.ci, c->Pp, acc, c->stream));
+    if (L.tc >= 0 && c->bf.layers[L.tc].dgrad)
+      ok(bf16_conv_dgrad(c->bf, L.tc, dy, dx, c->B, acc, c->stream));
+    else
+      ok(conv3d_dgrad_f32(dy, W(L), dx, c->B, L.din, L.ci, L.co, L.k, L.s,
+                          L.dout.count() * L.co, L.din.count() * L.ci, c->Pp, acc, c->stream));
     fin();
   }
   void conv_wgrad(const ConvL& L, const float* x, const float* dy) {
@@ -588,9 +597,17 @@ d2ip_status ready(d2ip_ctx* c) {
 }
 
 d2ip_status check_status(d2ip_ctx* c) {
-  int st = 0;
+  int st = 0, tc = 0;
   CK(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  if (c->precision == D2IP_BF16 && c->bf.err)
+    CK(cudaMemcpyAsync(&tc, c->bf.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (tc) {
+    CK(cudaMemsetAsync(c->bf.err, 0, sizeof(int), c->stream));
+    return fail(c, D2IP_ERR_TIMEOUT,
+                "a tensor-core convolution gave up waiting on its pipeline (code " +
+                    std::to_string(tc) + ")");
+  }
   if (st & 1) {
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     return fail(c, D2IP_ERR_NONFINITE, "a loss or residual became NaN or Inf");
@@ -785,7 +802,6 @@ d2ip_status d2ip_load_J(d2ip_ctx* c, const float* J, int m, int n, int normalize
   } else {
     CK(cudaMemsetAsync(c->colnorm, 0, sizeof(double) * n, c->stream));
   }
-  if (c->precision == D2IP_BF16) CK(bf16_set_J(c->bf, c->J, m, n, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->j_ready = true;
   return D2IP_OK;
@@ -1064,6 +1080,48 @@ d2ip_status d2ip_conv3d_dgrad(const float* dyp, const float* W, float* dxp, int 
   OPCK(conv3d_dgrad_f32(dyp, W, dxp, batch, din, ci, co, ksize, stride, dout.count() * co,
                         din.count() * ci, w_bs, accumulate, (cudaStream_t)stream));
   return D2IP_OK;
+}
+
+long long d2ip_conv3d_tc_workspace(int batch, int dz, int dy, int dx, int ci, int co,
+                                   int ksize, int stride) {
+  if (bad_conv(batch, dz, dy, dx, ci, co, ksize, stride) || !bf16_conv_supported(ci, co, ksize))
+    return -1;
+  return bf16_op_workspace(batch, Dims3{dz, dy, dx}, ci, co, ksize, stride);
+}
+
+static d2ip_status tc_op(bool dgrad, const float* in, const float* W, const float* b,
+                         float* out, int batch, int dz, int dy, int dx, int ci, int co,
+                         int ksize, int stride, long long w_bs, int accumulate, void* ws,
+                         long long ws_bytes, void* stream) {
+  if (!in || !W || !out || !ws) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
+  if (bad_conv(batch, dz, dy, dx, ci, co, ksize, stride) || !bf16_conv_supported(ci, co, ksize) ||
+      (dgrad && (stride != 1 || !bf16_conv_supported(co, ci, ksize))))
+    return fail(nullptr, D2IP_ERR_BAD_SHAPE,
+                "tensor-core convolution needs ci, co multiples of 16 (co <= 256); data "
+                "gradient stride 1 only");
+  if (ws_bytes < d2ip_conv3d_tc_workspace(batch, dz, dy, dx, ci, co, ksize, stride))
+    return fail(nullptr, D2IP_ERR_BAD_ARG, "workspace too small");
+  const long long blk = (long long)co * ksize * ksize * ksize * ci + co;
+  OPCK(bf16_op_conv(dgrad, in, W, b, out, batch, Dims3{dz, dy, dx}, ci, co, ksize, stride,
+                    w_bs ? w_bs : blk, accumulate, ws, (cudaStream_t)stream));
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_conv3d_forward_tc(const float* x, const float* W, const float* b, float* y,
+                                   int batch, int dz, int dy, int dx, int ci, int co, int ksize,
+                                   int stride, long long w_bs, void* ws, long long ws_bytes,
+                                   void* stream) {
+  if (!b) return fail(nullptr, D2IP_ERR_BAD_ARG, "null bias");
+  return tc_op(false, x, W, b, y, batch, dz, dy, dx, ci, co, ksize, stride, w_bs, 0, ws,
+               ws_bytes, stream);
+}
+
+d2ip_status d2ip_conv3d_dgrad_tc(const float* dyp, const float* W, float* dxp, int batch,
+                                 int dz, int dy, int dx, int ci, int co, int ksize, int stride,
+                                 long long w_bs, int accumulate, void* ws, long long ws_bytes,
+                                 void* stream) {
+  return tc_op(true, dyp, W, nullptr, dxp, batch, dz, dy, dx, ci, co, ksize, stride, w_bs,
+               accumulate, ws, ws_bytes, stream);
 }
 
 long long d2ip_conv3d_wgrad_workspace(int batch, int dz, int dy, int dx, int ci, int co,
