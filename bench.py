@@ -31,7 +31,8 @@ from paper_2507_14046_gb300 import synth  # noqa: E402
 
 METRIC = "DIP iters/s and tsEIT frames/s at equal ERR; BF16 batched vs plain FP32"
 UNIT = "DIP iters/s"
-WORKLOADS = {"seq32": synth.SEQ_32, "single16": synth.SINGLE_16, "seq64": synth.SEQ_64}
+WORKLOADS = {"seq32": synth.SEQ_32, "single16": synth.SINGLE_16, "seq64": synth.SEQ_64,
+             "batch64": synth.SEQ_32}
 FP32_LANES_PER_SM = 128
 SMS = 152
 
@@ -54,13 +55,15 @@ def iters_per_step(w) -> int:
 # oracle (CPU baseline and the reference arm)
 # ------------------------------------------------------------------------------------------
 
-def oracle_leg(workload: str, iters: int) -> dict:
-    """Time ``iters`` FP64 oracle DIP iterations on the workload (first frame, from the
-    Kaiming weights); returns iterations/s."""
+def _oracle_rate(w, grid, rings, iters: int) -> float:
+    """Seconds per FP64 oracle DIP iteration of network ``w`` on one seeded problem."""
     from oracle import dip, network as onet
-    w = WORKLOADS[workload]
-    J, truth, V, Zin = synth.make_problem(w)
-    spec = onet.NetSpec(w.grid, w.levels, w.widths, w.c_in)
+    J = synth.sensitivity_raw(grid, rings, w.seed)
+    truth = synth.ellipsoid_phantom(grid, synth.lung_pair(grid))[None]
+    V = synth.measurements(J, truth, w.seed)
+    n = grid[0] * grid[1] * grid[2]
+    Zin = synth.input_noise(n, w.c_in, w.seed)
+    spec = onet.NetSpec(tuple(grid), w.levels, w.widths, w.c_in)
     table = [(k, o, c, f) for _, _, k, f, o, c in onet.param_layout(spec)]
     th = synth.kaiming_theta(table, w.seed).astype(np.float64)
     Jn, _ = dip.normalise_columns(J)
@@ -70,8 +73,34 @@ def oracle_leg(workload: str, iters: int) -> dict:
     t0 = time.perf_counter()
     for _ in range(iters):
         th = dip.dip_step(spec, Jn, Z64, dv, th, st, w.lr).theta
-    dt = time.perf_counter() - t0
-    return {"iters": iters, "seconds": dt, "iters_per_s": iters / dt}
+    return (time.perf_counter() - t0) / iters
+
+
+def oracle_leg(workload: str, iters: int) -> dict:
+    """Time FP64 oracle DIP iterations on the workload (first frame, from the Kaiming
+    weights); returns iterations/s.  For the batched workload every grid of the mix is timed
+    and weighted by its number of sequences."""
+    if workload == "batch64":
+        shapes = synth.batch_problem_shapes(64, 1)
+        w = synth.SEQ_32
+        per_grid = {g: (max(1, iters * 4 // 3) if g[0] == 16 else
+                        (max(1, iters // 3) if g[0] == 32 else max(1, iters // 6)))
+                    for g in synth.BATCH_GRIDS}
+        sec, total = 0.0, 0
+        for g in synth.BATCH_GRIDS:
+            cnt = sum(1 for gg, _ in shapes if gg == g)
+            spi = _oracle_rate(w, g, 2, per_grid[g])
+            sec += spi * per_grid[g]
+            total += per_grid[g]
+            per_grid[g] = (per_grid[g], spi, cnt)
+        wsec = sum(spi * cnt for _, spi, cnt in per_grid.values()) / 64.0
+        return {"iters": total, "seconds": sec, "iters_per_s": 1.0 / wsec,
+                "detail": {f"{g[0]}x{g[1]}x{g[2]}": {"iters": k, "s_per_iter": spi,
+                                                      "sequences": cnt}
+                           for g, (k, spi, cnt) in per_grid.items()}}
+    w = WORKLOADS[workload]
+    spi = _oracle_rate(w, w.grid, w.rings, iters)
+    return {"iters": iters, "seconds": spi * iters, "iters_per_s": 1.0 / spi}
 
 
 def run_oracle_subprocess(workload: str, iters: int) -> dict:
@@ -89,7 +118,7 @@ def run_oracle_subprocess(workload: str, iters: int) -> dict:
 
 def oracle_iters_for(workload: str) -> int:
     # about 10-30 s of host work per sample on a Grace host
-    return {"single16": 200, "seq32": 12, "seq64": 2}[workload]
+    return {"single16": 200, "seq32": 12, "seq64": 2, "batch64": 12}[workload]
 
 
 # ------------------------------------------------------------------------------------------
@@ -161,7 +190,8 @@ def run_gpu(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     J, truth, V, Zin = synth.make_problem(w)
     stream = torch.cuda.Stream(device=dev)
-    ctx = B.Context(w.grid, w.levels, w.widths, w.c_in, B.D2IP_FP32, 1, device=local_rank,
+    prec = B.D2IP_BF16 if args.precision == "bf16" else B.D2IP_FP32
+    ctx = B.Context(w.grid, w.levels, w.widths, w.c_in, prec, 1, device=local_rank,
                     stream=stream.cuda_stream)
     table = ctx.table()
     theta0 = synth.kaiming_theta([tuple(r) for r in table], w.seed)
@@ -220,28 +250,7 @@ def run_gpu(args, rank, world, local_rank):
     # roofline of the dominant kernel class, from CUDA events around every launch
     ctx.set_input(Zd, thd)
     prof = ctx.profile(Vd[0], 10)
-    peaks, kind = _peaks()
-    dom = max(prof, key=lambda k: prof[k][0])
-    ms, work, cnt = prof[dom]
-    avg_ms = ms / cnt
-    per_launch = work / cnt
-    if dom.startswith("conv"):
-        mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-        peak = SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": per_launch / (avg_ms * 1e-3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "traffic": None,
-                "peak_source": f"FP32 FFMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                               f"{mhz:.0f} MHz (median sampled SM clock)"}
-    else:
-        peak = peaks["hbm_gbs"]
-        roof = {"bound": "hbm", "achieved": per_launch / (avg_ms * 1e-3) / 1e9, "peak": peak,
-                "unit": "GB/s", "traffic": None, "peak_source": f"{kind} hbm_gbs"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = dom
-    roof["avg_launch_us"] = avg_ms * 1e3
-    roof["work_per_launch"] = per_launch
-    step_ms_total = sum(v[0] for v in prof.values())
-    roof["share_of_traced_time"] = ms / step_ms_total
+    roof = _roofline(prof, args, clk, 10)
     kpl = {"conv_wgrad": 2, "ln_bwd": 2, "up_bwd": 2}
     launches_per_iter = sum(v[2] * kpl.get(k, 1) for k, v in prof.items()) / 10.0
     fwd_launches = sum(prof[k][2] for k in ("conv_fwd", "ln_fwd", "up_fwd")) / 10.0 + 2
@@ -282,13 +291,216 @@ def run_gpu(args, rank, world, local_rank):
     }
 
 
+def run_batched(args, rank, world, local_rank):
+    """BF16 batched form: all 64 sequences, one context per (grid, rings) group, fitted
+    concurrently with d2ip_fit_batched.  Beside it, the plain FP32 single-problem form on a
+    sample of the same sequences (one per group), for frames/s at equal ERR."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2507_14046_gb300 import binding as B
+
+    w = synth.SEQ_32  # network and schedule of the 20-frame workload
+    T = w.frames
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    groups = synth.batch_workload(64, T, seed=1, c_in=w.c_in)
+    prec = B.D2IP_BF16 if args.precision == "bf16" else B.D2IP_FP32
+    ctxs, streams, dv = [], [], []
+    table = None
+    for g in groups:
+        st = torch.cuda.Stream(device=dev)
+        c = B.Context(g.grid, w.levels, w.widths, w.c_in, prec, len(g.problems),
+                      device=local_rank, stream=st.cuda_stream)
+        c.set_optim(w.lr)
+        table = c.table() if table is None else table
+        P = c.P
+        th = np.stack([synth.kaiming_theta([tuple(r) for r in table], 1, stream_offset=p * P)
+                       for p in g.problems])
+        n, m = g.J.shape[1], g.J.shape[0]
+        dv.append({"J": torch.from_numpy(g.J).to(dev), "Z": torch.from_numpy(g.Z).to(dev),
+                   "th": torch.from_numpy(th).to(dev),
+                   "V": torch.from_numpy(np.ascontiguousarray(g.V)).to(dev),
+                   "S": torch.zeros((len(g.problems), T, n), device=dev),
+                   "R": torch.zeros((len(g.problems), T), dtype=torch.float64, device=dev),
+                   "th_np": th, "m": m, "n": n})
+        ctxs.append(c)
+        streams.append(st)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    its = iters_per_step(w)
+    nseq = sum(len(g.problems) for g in groups)
+
+    def step(bufs):
+        for c, b in zip(ctxs, bufs):
+            B.d2ip_load_J(c.handle, b["J"], b["m"], b["n"], 1)
+            B.d2ip_set_input(c.handle, b["Z"], b["th"])
+        B.d2ip_fit_batched([c.handle for c in ctxs], [b["V"] for b in bufs], T, None,
+                           w.upws_steps, w.first_steps, w.later_steps, [b["S"] for b in bufs],
+                           [b["R"] for b in bufs])
+
+    for _ in range(args.warmup):
+        step(dv)
+        flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local_rank, os.path.join(ROOT, "gpurun_out", f"clocks_r{rank}.csv")
+                          if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                          else f"/tmp/d2ip_clocks_r{rank}.csv")
+    total_ms = 0.0
+    for _ in range(args.steps):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in streams]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in streams]
+        for e, st in zip(starts, streams):
+            e.record(st)
+        step(dv)
+        for e, st in zip(ends, streams):
+            e.record(st)
+        torch.cuda.synchronize()
+        total_ms += max(starts[0].elapsed_time(e) for e in ends)
+        flush.zero_()
+        torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps * nseq * its / (total_ms / 1e3)
+    frames_s = world * args.steps * nseq * T / (total_ms / 1e3)
+
+    # ERR of every sequence of the last step (frames with a zero truth excluded)
+    err_b = {}
+    for g, b in zip(groups, dv):
+        S = b["S"].cpu().numpy()
+        for i, p in enumerate(g.problems):
+            err_b[p] = [_err(S[i, t], g.truth[i, t]) for t in range(T)
+                        if np.abs(g.truth[i, t]).max() > 0]
+    # plain FP32 single-problem form on one sequence per group, at equal schedule
+    plain_s, plain_frames, err_p = 0.0, 0, {}
+    for g, b in zip(groups, dv):
+        i, p = 0, g.problems[0]
+        st = torch.cuda.Stream(device=dev)
+        c1 = B.Context(g.grid, w.levels, w.widths, w.c_in, B.D2IP_FP32, 1, device=local_rank,
+                       stream=st.cuda_stream)
+        c1.set_optim(w.lr)
+        S1 = torch.zeros((1, T, b["n"]), device=dev)
+        R1 = torch.zeros((1, T), dtype=torch.float64, device=dev)
+
+        def one():
+            B.d2ip_load_J(c1.handle, b["J"], b["m"], b["n"], 1)
+            B.d2ip_set_input(c1.handle, b["Z"][i:i + 1], b["th"][i:i + 1])
+            B.d2ip_fit_sequence(c1.handle, b["V"][i:i + 1], T, None, w.upws_steps,
+                                w.first_steps, w.later_steps, S1, R1)
+        one()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        one()
+        e1.record(st)
+        torch.cuda.synchronize()
+        plain_s += e0.elapsed_time(e1) / 1e3
+        plain_frames += T
+        S = S1.cpu().numpy()[0]
+        err_p[p] = [_err(S[t], g.truth[i, t]) for t in range(T) if np.abs(g.truth[i, t]).max() > 0]
+        c1.close()
+    sample = sorted(err_p)
+    eb = float(np.mean([np.mean(err_b[p]) for p in sample]))
+    ep = float(np.mean([np.mean(err_p[p]) for p in sample]))
+
+    # roofline of the dominant kernel class on the largest group
+    gi = max(range(len(groups)), key=lambda k: groups[k].J.shape[1] * len(groups[k].problems))
+    ctxs[gi].set_input(dv[gi]["Z"], dv[gi]["th"])
+    prof = ctxs[gi].profile(dv[gi]["V"][:, 0].contiguous(), 5)
+    roof = _roofline(prof, args, clk, 5)
+    kpl = {"conv_wgrad": 2, "ln_bwd": 2, "up_bwd": 2}
+    launches_per_iter = sum(v[2] * kpl.get(k, 1) for k, v in prof.items()) / 5.0
+    gpu_launches = int(args.steps * len(groups) * (its * launches_per_iter + T * 40 + 1))
+
+    # end to end through the C ABI from pinned host buffers
+    hb = []
+    for b in dv:
+        hb.append({"J": b["J"].cpu().pin_memory(), "Z": b["Z"].cpu().pin_memory(),
+                   "th": b["th"].cpu().pin_memory(), "V": b["V"].cpu().pin_memory(),
+                   "S": b["S"].cpu().pin_memory(), "R": b["R"].cpu().pin_memory(),
+                   "m": b["m"], "n": b["n"]})
+    step(hb)
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(hb)
+        e2e_s += time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = sum(b["J"].numel() * 4 + b["Z"].numel() * 4 + b["th"].numel() * 4 + b["V"].numel() * 4
+              for b in hb)
+    d2h = sum(b["S"].numel() * 4 + b["R"].numel() * 8 for b in hb)
+    for c in ctxs:
+        c.close()
+    return {
+        "value": value, "ms_per_step": total_ms / args.steps, "frames_per_s": frames_s,
+        "e2e": {"value": world * args.steps * nseq * its / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "frames_per_s": world * args.steps * nseq * T / e2e_s},
+        "roofline": roof, "clocks": clk, "gpu_launches": gpu_launches,
+        "err": {"mean": float(np.mean([np.mean(v) for v in err_b.values()])),
+                "sequences": len(err_b)},
+        "plain_fp32": {"frames_per_s": plain_frames / plain_s,
+                       "iters_per_s": len(sample) * its / plain_s,
+                       "sample": f"{len(sample)} sequences (one per grid/m group), one at a "
+                                 "time, FP32 single-problem contexts",
+                       "err_mean_sample": ep, "err_mean_batched_same_sequences": eb,
+                       "err_rel_diff": abs(eb - ep) / ep,
+                       "speedup_frames_per_s": frames_s / (plain_frames / plain_s)},
+        "groups": [{"grid": list(g.grid), "m": g.J.shape[0], "problems": len(g.problems)}
+                   for g in groups],
+        "profile_ms_per_iter": {k: round(v[0] / 5.0, 4) for k, v in prof.items()},
+    }
+
+
+def _roofline(prof, args, clk, iters):
+    peaks, kind = _peaks()
+    dom = max(prof, key=lambda k: prof[k][0])
+    ms, work, cnt = prof[dom]
+    avg_ms = ms / cnt
+    per_launch = work / cnt
+    if dom in ("conv_fwd", "conv_dgrad") and args.precision == "bf16":
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        roof = {"bound": "tensor", "achieved": per_launch / (avg_ms * 1e-3) / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "traffic": None,
+                "peak_source": f"{kind} bf16_tflops_sustained (kernel timed inside a long step); "
+                               "the class also holds the FP32 stem, down and tail convolutions"}
+    elif dom.startswith("conv"):
+        mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        peak = SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": per_launch / (avg_ms * 1e-3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "traffic": None,
+                "peak_source": f"FP32 FFMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                               f"{mhz:.0f} MHz (median sampled SM clock)"}
+    else:
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": per_launch / (avg_ms * 1e-3) / 1e9, "peak": peak,
+                "unit": "GB/s", "traffic": None, "peak_source": f"{kind} hbm_gbs"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dom
+    roof["avg_launch_us"] = avg_ms * 1e3
+    roof["work_per_launch"] = per_launch
+    roof["share_of_traced_time"] = ms / sum(v[0] for v in prof.values())
+    return roof
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="seq32", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="batch64", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-leg", default=None)
     ap.add_argument("--oracle-iters", type=int, default=5)
@@ -297,16 +509,19 @@ def main():
     if args.oracle_leg:
         print(json.dumps(oracle_leg(args.oracle_leg, args.oracle_iters)))
         return
+    if args.precision is None:
+        args.precision = "bf16" if args.workload == "batch64" else "fp32"
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     w = WORKLOADS[args.workload]
     its = iters_per_step(w)
-    config = {"workload": w.name + (", FP32" if args.impl == "ours" else ", FP64 oracle"),
+    config = {"workload": w.name + ((", " + args.precision.upper()) if args.impl == "ours"
+                                    else ", FP64 oracle"),
               "grid": list(w.grid), "m": w.m, "levels": w.levels, "widths": list(w.widths),
               "frames": w.frames, "schedule": [w.upws_steps, w.first_steps, w.later_steps],
-              "lr": w.lr, "iters_per_step": its, "precision": "fp32",
+              "lr": w.lr, "iters_per_step": its, "precision": args.precision,
               "l2": "512 MB buffer written between timed steps (working set < L2)",
               "parallelism": f"replicas x{args.gpus}"}
 
@@ -340,7 +555,17 @@ def main():
         import torch.distributed as dist
         import torch
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    out = run_gpu(args, rank, world, local_rank)
+    if args.workload == "batch64":
+        config["workload"] = ("64 independent 20-frame sequences (grids 16x16x8 / 32x32x16 / "
+                              f"48x48x24, m 208 / 416), L3(16,32,64), {args.precision.upper()} "
+                              "batched")
+        config["grid"] = "mixed"
+        config["m"] = "mixed"
+        config["iters_per_step"] = 64 * its
+        out = run_batched(args, rank, world, local_rank)
+        config["groups"] = out.pop("groups")
+    else:
+        out = run_gpu(args, rank, world, local_rank)
     if rank != 0:
         return
     cpu = None
@@ -348,15 +573,18 @@ def main():
         r = run_oracle_subprocess(args.workload, oracle_iters_for(args.workload))
         cpu = {"value": r["iters_per_s"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                "sample": f"{r['iters']} FP64 oracle DIP iterations (first frame of the same "
-                         f"workload) in {r['seconds']:.1f} s, NumPy/BLAS on {r['cores']} "
-                         "host threads"}
+                         f"workload{', every grid of the mix, weighted by its sequences' if args.workload == 'batch64' else ''}"
+                         f") in {r['seconds']:.1f} s, NumPy/BLAS on {r['cores']} host threads"}
     line = {"metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["ms_per_step"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if args.precision == "bf16" else "f32",
             "data": "synthetic", "config": config, "frames_per_s": out["frames_per_s"],
             "e2e": out["e2e"], "roofline": out["roofline"], "cpu_baseline": cpu,
             "clocks": out["clocks"], "gpu_launches": out["gpu_launches"], "err": out["err"],
             "profile_ms_per_iter": out["profile_ms_per_iter"]}
+    if "plain_fp32" in out:
+        line["plain_fp32"] = out["plain_fp32"]
     print(json.dumps(line))
 
 

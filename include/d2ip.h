@@ -131,6 +131,17 @@ d2ip_status d2ip_fit_sequence(d2ip_ctx* ctx, const float* V, int T, const float*
                               int upws_steps, int first_steps, int later_steps,
                               float* Sigma_out, double* residual_out);
 
+/* Batched form: `count` contexts (for example one per grid and measurement-count group of a
+ * set of independent sequences, each context holding its group's problems as its batch) fit
+ * their sequences concurrently, every context on its own stream, with the schedule of
+ * d2ip_fit_sequence.  V[i], dV0[i] (dV0 may be NULL, or entries NULL), Sigma_out[i] and
+ * residual_out[i] are context i's arrays exactly as in d2ip_fit_sequence.  Returns after
+ * all contexts finished; the first failing context's status is returned. */
+d2ip_status d2ip_fit_batched(d2ip_ctx* const* ctxs, int count, const float* const* V, int T,
+                             const float* const* dV0, int upws_steps, int first_steps,
+                             int later_steps, float* const* Sigma_out,
+                             double* const* residual_out);
+
 /* Checkpoint: theta, Adam m and v ([batch][P] each) and the Adam step count.  Any pointer
  * may be NULL to skip that part. */
 d2ip_status d2ip_get_state(d2ip_ctx* ctx, float* theta, float* adam_m, float* adam_v,

@@ -52,6 +52,7 @@ _SIGS = {
     "d2ip_get_grad": [_vp, _vp],
     "d2ip_fit_frame": [_vp, _vp, _i, _vp, _vp, _vp],
     "d2ip_fit_sequence": [_vp, _vp, _i, _vp, _i, _i, _i, _vp, _vp],
+    "d2ip_fit_batched": [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp, _vp],
     "d2ip_get_state": [_vp, _vp, _vp, _vp, C.POINTER(_i)],
     "d2ip_set_state": [_vp, _vp, _vp, _vp, _i],
     "d2ip_err_ratio": [_vp, _vp, _vp, _vp],
@@ -202,6 +203,23 @@ for _name in ("d2ip_conv3d_forward", "d2ip_conv3d_dgrad", "d2ip_conv3d_wgrad",
               "d2ip_sensitivity_residual", "d2ip_sensitivity_adjoint", "d2ip_normalize_columns",
               "d2ip_adam_update"):
     globals()[_name] = _wrap_op(_name)
+
+
+def _ptr_array(items):
+    arr = (_vp * len(items))(*[ptr(x) for x in items])
+    return C.cast(arr, _vp), arr
+
+
+def d2ip_fit_batched(ctxs, V, T, dV0, upws_steps, first_steps, later_steps, Sigma_out,
+                     residual_out):
+    """Lists of per-context handles and arrays (see d2ip.h)."""
+    hc, keep1 = _ptr_array(ctxs)
+    hv, keep2 = _ptr_array(V)
+    hd, keep3 = _ptr_array(dV0) if dV0 is not None else (None, None)
+    hs, keep4 = _ptr_array(Sigma_out) if Sigma_out is not None else (None, None)
+    hr, keep5 = _ptr_array(residual_out) if residual_out is not None else (None, None)
+    return _call("d2ip_fit_batched", ctxs[0], hc, len(ctxs), hv, T, hd, upws_steps,
+                 first_steps, later_steps, hs, hr)
 
 
 class Context:

@@ -78,10 +78,12 @@ cudaError_t jmul_residual_f32(const float* J, const float* x, const float* dv, f
 cudaError_t prepare_pointwise_kernels();
 cudaError_t jtmul_f32(const float* J, const float* r, float* g, float scale, int B, int m,
                       int n, long long g_bs, cudaStream_t stream);
-// loss[b] = (1/m) sum r^2 (FP64); optional trace slot; optional Adam step counter bump;
-// status bit 1 set when a loss is not finite.
+// loss[b] = (1/m) sum r^2 (FP64); optional trace ring (slot trace_pos % trace_cap, then
+// trace_pos += 1); optional Adam step counter bump; status bit 1 set when a loss is not
+// finite.
 cudaError_t residual_loss_f64(const float* r, double* loss, double* trace, int* trace_pos,
-                              int* adam_t, int* status, int B, int m, cudaStream_t stream);
+                              int trace_cap, int* adam_t, int* status, int B, int m,
+                              cudaStream_t stream);
 cudaError_t normalize_columns_f64(float* J, double* colnorm, int m, int n,
                                   cudaStream_t stream);
 cudaError_t err_ratio_f64(const float* est, const float* truth, double* out, int B,

@@ -328,10 +328,11 @@ jtmul_kernel(const float* __restrict__ J, const float* __restrict__ r, float* __
 
 __global__ void __launch_bounds__(256)
 loss_kernel(const float* __restrict__ r, double* __restrict__ loss, double* __restrict__ trace,
-            int* __restrict__ trace_pos, int* __restrict__ adam_t, int* __restrict__ status,
-            int B, int m) {
+            int* __restrict__ trace_pos, int trace_cap, int* __restrict__ adam_t,
+            int* __restrict__ status, int B, int m) {
   __shared__ double red[256];
   const int pos = trace_pos ? *trace_pos : 0;
+  const int slot = trace_cap > 0 ? pos % trace_cap : 0;
   bool bad = false;
   for (int b = 0; b < B; ++b) {
     double s = 0.0;
@@ -348,7 +349,7 @@ loss_kernel(const float* __restrict__ r, double* __restrict__ loss, double* __re
     if (threadIdx.x == 0) {
       const double L = red[0] / (double)m;
       loss[b] = L;
-      if (trace) trace[(long long)pos * B + b] = L;
+      if (trace) trace[(long long)slot * B + b] = L;
       if (!isfinite(L)) bad = true;
     }
     __syncthreads();
@@ -521,8 +522,10 @@ cudaError_t prepare_pointwise_kernels() {
 }
 
 cudaError_t residual_loss_f64(const float* r, double* loss, double* trace, int* trace_pos,
-                              int* adam_t, int* status, int B, int m, cudaStream_t stream) {
-  loss_kernel<<<1, 256, 0, stream>>>(r, loss, trace, trace_pos, adam_t, status, B, m);
+                              int trace_cap, int* adam_t, int* status, int B, int m,
+                              cudaStream_t stream) {
+  loss_kernel<<<1, 256, 0, stream>>>(r, loss, trace, trace_pos, trace_cap, adam_t, status, B,
+                                     m);
   return cudaGetLastError();
 }
 

@@ -486,10 +486,10 @@ struct Launcher {
     fin();
     beg(D2IP_KCLASS_LOSS, 4.0 * c->B * c->m);
     if (training) {
-      ok(residual_loss_f64(c->r, c->loss, c->trace, c->trace_pos, c->adam_t, c->status, c->B,
-                           c->m, c->stream));
+      ok(residual_loss_f64(c->r, c->loss, c->trace, c->trace_pos, kTraceCap, c->adam_t,
+                           c->status, c->B, c->m, c->stream));
     } else {
-      ok(residual_loss_f64(c->r, c->resid, nullptr, nullptr, nullptr, c->status, c->B, c->m,
+      ok(residual_loss_f64(c->r, c->resid, nullptr, nullptr, 0, nullptr, c->status, c->B, c->m,
                            c->stream));
     }
     fin();
@@ -645,6 +645,100 @@ d2ip_status run_steps(d2ip_ctx* c, int n_steps, double* loss_trace) {
 
 d2ip_status stage_dv(d2ip_ctx* c, const float* dV, long long spitch) {
   CK(copy_rows(c->dv, c->m, dV, spitch, c->m, c->B, sizeof(float), c->stream));
+  return D2IP_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// One context's sequence as a list of operations, issued a few graph launches at a time.
+struct SeqOp {
+  enum Kind { kStage, kReset, kSteps, kEval, kResiduals } kind;
+  int arg;                 // frame index (kStage: -1 = the UPWS frame), step count
+};
+
+struct SeqJob {
+  d2ip_ctx* c = nullptr;
+  const float* V = nullptr;
+  const float* dV0 = nullptr;
+  float* Sigma = nullptr;
+  double* resid = nullptr;
+  int T = 0;
+  std::vector<SeqOp> ops;
+  size_t pc = 0;
+  int done_steps = 0;      // of the current kSteps op
+};
+
+SeqJob make_sequence_job(d2ip_ctx* c, const float* V, int T, const float* dV0, int upws,
+                         int first, int later, float* Sigma, double* resid) {
+  SeqJob j;
+  j.c = c;
+  j.V = V;
+  j.T = T;
+  j.dV0 = dV0;
+  j.Sigma = Sigma;
+  j.resid = resid;
+  if (upws > 0) {  // UPWS (Eqs. 5-7): N_0 steps on one frame from the initial weights
+    j.ops.push_back({SeqOp::kStage, -1});
+    j.ops.push_back({SeqOp::kReset, 0});
+    j.ops.push_back({SeqOp::kSteps, upws});
+  }
+  for (int i = 0; i < T; ++i) {  // TPP (Eqs. 8-9): theta carries over, Adam restarts
+    j.ops.push_back({SeqOp::kStage, i});
+    j.ops.push_back({SeqOp::kReset, 0});
+    j.ops.push_back({SeqOp::kSteps, i == 0 ? first : later});
+    j.ops.push_back({SeqOp::kEval, i});
+  }
+  j.ops.push_back({SeqOp::kResiduals, 0});
+  return j;
+}
+
+// Issue the job's next operations, at most `budget` step graphs.
+d2ip_status issue(SeqJob& j, int budget) {
+  d2ip_ctx* c = j.c;
+  const long long m = c->m, n = c->n();
+  while (j.pc < j.ops.size()) {
+    const SeqOp& op = j.ops[j.pc];
+    switch (op.kind) {
+      case SeqOp::kStage: {
+        d2ip_status s = op.arg < 0 ? (j.dV0 ? stage_dv(c, j.dV0, m)
+                                            : stage_dv(c, j.V, (long long)j.T * m))
+                                   : stage_dv(c, j.V + (long long)op.arg * m, (long long)j.T * m);
+        if (s) return s;
+        break;
+      }
+      case SeqOp::kReset: {
+        d2ip_status s = reset_optimizer(c);
+        if (s) return s;
+        break;
+      }
+      case SeqOp::kSteps:
+        while (j.done_steps < op.arg && budget > 0) {
+          CK(cudaGraphLaunch(c->g_step, c->stream));
+          ++j.done_steps;
+          --budget;
+        }
+        if (j.done_steps < op.arg) return D2IP_OK;
+        j.done_steps = 0;
+        break;
+      case SeqOp::kEval:
+        CK(cudaGraphLaunch(c->g_eval, c->stream));
+        if (j.Sigma)
+          CK(copy_rows(j.Sigma + (long long)op.arg * n, (long long)j.T * n, c->dsigma, n, n,
+                       c->B, sizeof(float), c->stream));
+        CK(cudaMemcpy2DAsync(c->seq_resid + op.arg, sizeof(double) * j.T, c->resid,
+                             sizeof(double), sizeof(double), c->B, cudaMemcpyDeviceToDevice,
+                             c->stream));
+        break;
+      case SeqOp::kResiduals:
+        if (j.resid)
+          CK(cudaMemcpyAsync(j.resid, c->seq_resid, sizeof(double) * j.T * c->B,
+                             cudaMemcpyDefault, c->stream));
+        break;
+    }
+    ++j.pc;
+  }
   return D2IP_OK;
 }
 
@@ -912,44 +1006,54 @@ d2ip_status d2ip_fit_frame(d2ip_ctx* c, const float* dV, int n_steps, float* dsi
 d2ip_status d2ip_fit_sequence(d2ip_ctx* c, const float* V, int T, const float* dV0,
                               int upws_steps, int first_steps, int later_steps,
                               float* Sigma_out, double* residual_out) {
-  d2ip_status s = ready(c);
-  if (s) return s;
-  if (!V || T < 1 || upws_steps < 0 || first_steps < 0 || later_steps < 0)
-    return fail(c, D2IP_ERR_BAD_ARG, "bad V, T or step counts");
-  if (T > c->seq_T_cap) {
-    if (c->seq_resid) cudaFree(c->seq_resid);
-    c->seq_resid = nullptr;
-    if (cudaMalloc(&c->seq_resid, sizeof(double) * T * c->B) != cudaSuccess)
-      return fail(c, D2IP_ERR_OOM, "residual buffer allocation failed");
-    c->seq_T_cap = T;
+  d2ip_ctx* one[1] = {c};
+  const float* Vs[1] = {V};
+  const float* d0[1] = {dV0};
+  float* So[1] = {Sigma_out};
+  double* Ro[1] = {residual_out};
+  return d2ip_fit_batched(one, 1, Vs, T, d0, upws_steps, first_steps, later_steps, So, Ro);
+}
+
+d2ip_status d2ip_fit_batched(d2ip_ctx* const* ctxs, int count, const float* const* V, int T,
+                             const float* const* dV0, int upws_steps, int first_steps,
+                             int later_steps, float* const* Sigma_out,
+                             double* const* residual_out) {
+  if (!ctxs || count < 1 || !V) return fail(nullptr, D2IP_ERR_BAD_ARG, "bad context list");
+  if (T < 1 || upws_steps < 0 || first_steps < 0 || later_steps < 0)
+    return fail(ctxs[0], D2IP_ERR_BAD_ARG, "bad T or step counts");
+  std::vector<SeqJob> jobs(count);
+  for (int i = 0; i < count; ++i) {
+    d2ip_ctx* c = ctxs[i];
+    d2ip_status s = ready(c);
+    if (s) return s;
+    if (!V[i]) return fail(c, D2IP_ERR_BAD_ARG, "null V");
+    if (T > c->seq_T_cap) {
+      if (c->seq_resid) cudaFree(c->seq_resid);
+      c->seq_resid = nullptr;
+      if (cudaMalloc(&c->seq_resid, sizeof(double) * T * c->B) != cudaSuccess)
+        return fail(c, D2IP_ERR_OOM, "residual buffer allocation failed");
+      c->seq_T_cap = T;
+    }
+    jobs[i] = make_sequence_job(c, V[i], T, dV0 ? dV0[i] : nullptr, upws_steps, first_steps,
+                                later_steps, Sigma_out ? Sigma_out[i] : nullptr,
+                                residual_out ? residual_out[i] : nullptr);
   }
-  const long long m = c->m, n = c->n();
-  if (upws_steps > 0) {  // UPWS (Eqs. 5-7)
-    s = dV0 ? stage_dv(c, dV0, m) : stage_dv(c, V, (long long)T * m);
-    if (s) return s;
-    s = reset_optimizer(c);
-    if (s) return s;
-    s = run_steps(c, upws_steps, nullptr);
-    if (s) return s;
+  // issue a few graph launches per context in turn, so every context's stream keeps work
+  bool left = true;
+  while (left) {
+    left = false;
+    for (SeqJob& j : jobs) {
+      d2ip_status s = issue(j, 8);
+      if (s) return s;
+      left = left || j.pc < j.ops.size();
+    }
   }
-  for (int i = 0; i < T; ++i) {  // TPP (Eqs. 8-9): theta carries over, Adam restarts
-    s = stage_dv(c, V + (long long)i * m, (long long)T * m);
-    if (s) return s;
-    s = reset_optimizer(c);
-    if (s) return s;
-    s = run_steps(c, i == 0 ? first_steps : later_steps, nullptr);
-    if (s) return s;
-    CK(cudaGraphLaunch(c->g_eval, c->stream));
-    if (Sigma_out)
-      CK(copy_rows(Sigma_out + (long long)i * n, (long long)T * n, c->dsigma, n, n, c->B,
-                   sizeof(float), c->stream));
-    CK(cudaMemcpy2DAsync(c->seq_resid + i, sizeof(double) * T, c->resid, sizeof(double),
-                         sizeof(double), c->B, cudaMemcpyDeviceToDevice, c->stream));
+  d2ip_status first_err = D2IP_OK;
+  for (SeqJob& j : jobs) {
+    d2ip_status s = check_status(j.c);
+    if (s && !first_err) first_err = s;
   }
-  if (residual_out)
-    CK(cudaMemcpyAsync(residual_out, c->seq_resid, sizeof(double) * T * c->B, cudaMemcpyDefault,
-                       c->stream));
-  return check_status(c);
+  return first_err;
 }
 
 d2ip_status d2ip_get_state(d2ip_ctx* c, float* theta, float* adam_m, float* adam_v,
@@ -1220,7 +1324,7 @@ d2ip_status d2ip_sensitivity_residual(const float* J, const float* x, const floa
   if (batch < 1 || m < 1 || n < 1) return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad J shape");
   OPCK(jmul_residual_f32(J, x, dv, r, batch, m, n, n, (cudaStream_t)stream));
   if (loss)
-    OPCK(residual_loss_f64(r, loss, nullptr, nullptr, nullptr, nullptr, batch, m,
+    OPCK(residual_loss_f64(r, loss, nullptr, nullptr, 0, nullptr, nullptr, batch, m,
                            (cudaStream_t)stream));
   return D2IP_OK;
 }

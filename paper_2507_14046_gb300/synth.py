@@ -217,7 +217,7 @@ def column_normalised(J32: np.ndarray) -> np.ndarray:
 
 
 def measurements(J32: np.ndarray, truth: np.ndarray, seed: int, snr_db: float = 40.0,
-                 stream_offset: int = 0) -> np.ndarray:
+                 stream_offset: int = 0, Jn: np.ndarray | None = None) -> np.ndarray:
     """Delta v for each truth frame: J_n @ truth_t + noise (float32, shape (T, M)).
 
     ``truth`` is (T, V).  The noise standard deviation is 10^(-snr/20) times the RMS of the
@@ -225,7 +225,8 @@ def measurements(J32: np.ndarray, truth: np.ndarray, seed: int, snr_db: float = 
     i.i.d. per frame and measurement.
     """
     truth = np.atleast_2d(truth)
-    Jn = column_normalised(J32)
+    if Jn is None:
+        Jn = column_normalised(J32)
     clean = truth @ Jn.T                                   # (T, M)
     peak = int(np.argmax(np.abs(truth).sum(axis=1)))
     rms = math.sqrt(float(np.mean(clean[peak] ** 2)))
@@ -347,3 +348,46 @@ def batch_problem_shapes(count: int, seed: int) -> list[tuple[tuple[int, int, in
         r = BATCH_RINGS[min(1, int(u[2 * p + 1] * 2))]
         out.append((g, r))
     return out
+
+
+@dataclass
+class BatchGroup:
+    """Problems of the batched workload that share a grid and a measurement count (hence one
+    sensitivity matrix)."""
+    grid: tuple[int, int, int]
+    rings: int
+    J: np.ndarray                 # raw float32 (m, n)
+    problems: list[int]           # indices into the 64 sequences
+    truth: np.ndarray             # (B, T, n) float64
+    V: np.ndarray                 # (B, T, m) float32
+    Z: np.ndarray                 # (B, n, c_in) float32
+
+
+def batch_sensitivity_seed(grid, rings, seed: int = 1) -> int:
+    """J depends only on (grid, m), seeded from (seed, X, Y, Z, m)."""
+    X, Y, Z = grid
+    k = _key(seed, ((X * 1009 + Y) * 1013 + Z) * 4099 + rings * MEAS_PER_RING)
+    return int(k & np.uint64(0x7FFFFFFF))
+
+
+def batch_workload(count: int = 64, frames: int = 20, seed: int = 1, c_in: int = 8):
+    """The batched workload: ``count`` independent breathing sequences on random grids and
+    electrode counts with random ellipsoid pairs, grouped by (grid, rings)."""
+    shapes = batch_problem_shapes(count, seed)
+    keys = sorted(set(shapes), key=lambda k: (k[0][0], k[1]))
+    amp = breathing_amplitude(frames)
+    groups = []
+    for g, r in keys:
+        idx = [p for p, sh in enumerate(shapes) if sh == (g, r)]
+        J = sensitivity_raw(g, r, batch_sensitivity_seed(g, r, seed))
+        Jn = column_normalised(J)
+        n = g[0] * g[1] * g[2]
+        truths, Vs, Zs = [], [], []
+        for p in idx:
+            base = ellipsoid_phantom(g, random_ellipsoids(g, seed, p), -0.3)
+            t = amp[:, None] * base[None, :]
+            truths.append(t)
+            Vs.append(measurements(J, t, seed, stream_offset=p * 1_000_003, Jn=Jn))
+            Zs.append(input_noise(n, c_in, seed, stream_offset=p * 10_000_019))
+        groups.append(BatchGroup(g, r, J, idx, np.stack(truths), np.stack(Vs), np.stack(Zs)))
+    return groups

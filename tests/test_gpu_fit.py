@@ -188,3 +188,24 @@ def test_shape_and_order_errors(d2ip):
         assert e.value.status == -7
     finally:
         d2ip.d2ip_destroy(h)
+
+
+def test_fit_batched_equals_separate_sequences(d2ip):
+    """Two contexts of different grids fitted together by d2ip_fit_batched give exactly the
+    results of fitting each alone with d2ip_fit_sequence."""
+    pa = problems.make((16, 16, 8), 1, 2, (16, 32), seed=7, T=3)
+    pb = problems.make((12, 10, 6), 2, 2, (16, 32), seed=8, T=3)
+    up, first, later = 12, 6, 4
+    alone = []
+    for p in (pa, pb):
+        c = _ctx(d2ip, p, 1e-3)
+        alone.append(c.fit_sequence(p.V[None], up, first, later))
+    cs = [_ctx(d2ip, p, 1e-3) for p in (pa, pb)]
+    S = [np.zeros((1, 3, p.n), np.float32) for p in (pa, pb)]
+    R = [np.zeros((1, 3), np.float64) for p in (pa, pb)]
+    d2ip.d2ip_fit_batched([c.handle for c in cs], [np.ascontiguousarray(p.V[None])
+                                                   for p in (pa, pb)], 3, None, up, first,
+                          later, S, R)
+    for k in range(2):
+        np.testing.assert_array_equal(S[k], alone[k][0])
+        np.testing.assert_array_equal(R[k], alone[k][1])
