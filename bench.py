@@ -468,12 +468,12 @@ def _roofline(prof, args, clk, iters):
     ms, work, cnt = prof[dom]
     avg_ms = ms / cnt
     per_launch = work / cnt
-    if dom in ("conv_fwd", "conv_dgrad") and args.precision == "bf16":
+    if dom.startswith("conv") and args.precision == "bf16":
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
         roof = {"bound": "tensor", "achieved": per_launch / (avg_ms * 1e-3) / 1e12,
                 "peak": peak, "unit": "TFLOP/s", "traffic": None,
                 "peak_source": f"{kind} bf16_tflops_sustained (kernel timed inside a long step); "
-                               "the class also holds the FP32 stem, down and tail convolutions"}
+                               "the class also holds the FP32 SIMT stem, tail and stride-2 layers"}
     elif dom.startswith("conv"):
         mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
         peak = SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12

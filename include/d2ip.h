@@ -212,6 +212,16 @@ d2ip_status d2ip_conv3d_dgrad_tc(const float* dy, const float* W, float* dx, int
                                  long long w_batch_stride, int accumulate, void* workspace,
                                  long long workspace_bytes, void* stream);
 
+/* Tensor-core weight gradient of a 3x3x3 stride-1 convolution (tcgen05, x and dy rounded to
+ * BF16, FP32 accumulation; bias gradient in FP32): result as d2ip_conv3d_wgrad.  Needs ci and
+ * co multiples of 16, co dividing 128, ci <= 256.  Workspace: d2ip_conv3d_wgrad_tc_workspace
+ * bytes (device); the int at its first 1024-byte aligned address is the error word. */
+long long d2ip_conv3d_wgrad_tc_workspace(int batch, int dz, int dy, int dx, int ci, int co);
+d2ip_status d2ip_conv3d_wgrad_tc(const float* x, const float* dy, float* dWb, int batch,
+                                 int dz, int dy_, int dx_, int ci, int co,
+                                 long long dw_batch_stride, int accumulate, void* workspace,
+                                 long long workspace_bytes, void* stream);
+
 /* Workspace bytes needed by d2ip_conv3d_wgrad for these sizes. */
 long long d2ip_conv3d_wgrad_workspace(int batch, int dz, int dy, int dx, int ci, int co,
                                       int ksize, int stride);

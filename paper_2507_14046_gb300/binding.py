@@ -66,6 +66,7 @@ _SIGS = {
                                _ll, _vp],
     "d2ip_conv3d_dgrad_tc": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _ll, _i, _vp, _ll,
                              _vp],
+    "d2ip_conv3d_wgrad_tc": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _ll, _i, _vp, _ll, _vp],
     "d2ip_conv3d_wgrad_noalloc": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _ll, _i,
                                   _vp],
     "d2ip_layernorm_act_forward": [_vp, _vp, _vp, _vp, _vp, _vp, _i, _ll, _i, _i, _ll, _vp],
@@ -81,6 +82,7 @@ _SIGS = {
 _SIZE_FNS = {
     "d2ip_conv3d_wgrad_workspace": [_i] * 8,
     "d2ip_conv3d_tc_workspace": [_i] * 8,
+    "d2ip_conv3d_wgrad_tc_workspace": [_i] * 6,
     "d2ip_layernorm_workspace": [_i, _ll, _i],
 }
 
@@ -187,6 +189,10 @@ def d2ip_conv3d_tc_workspace(*args) -> int:
     return int(_lib.d2ip_conv3d_tc_workspace(*args))
 
 
+def d2ip_conv3d_wgrad_tc_workspace(*args) -> int:
+    return int(_lib.d2ip_conv3d_wgrad_tc_workspace(*args))
+
+
 def d2ip_layernorm_workspace(*args) -> int:
     return int(_lib.d2ip_layernorm_workspace(*args))
 
@@ -198,6 +204,7 @@ for _name in ("d2ip_set_grid", "d2ip_load_J", "d2ip_get_colnorms", "d2ip_set_inp
     globals()[_name] = _wrap_ctx(_name)
 for _name in ("d2ip_conv3d_forward", "d2ip_conv3d_dgrad", "d2ip_conv3d_wgrad",
               "d2ip_conv3d_wgrad_noalloc", "d2ip_conv3d_forward_tc", "d2ip_conv3d_dgrad_tc",
+              "d2ip_conv3d_wgrad_tc",
               "d2ip_layernorm_act_forward", "d2ip_layernorm_act_backward",
               "d2ip_upsample_concat_forward", "d2ip_upsample_concat_backward",
               "d2ip_sensitivity_residual", "d2ip_sensitivity_adjoint", "d2ip_normalize_columns",

@@ -218,7 +218,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__
   }
   __syncwarp();
 
-  const bool ok = mbar_wait(smem_u32(&done_bar), 0);
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&done_bar), 0));
   if (!ok && lane == 0) atomicOr(err, kErrEpilogue);
   tc_fence_after();
   if (ok) {
@@ -239,6 +239,172 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__
         }
       }
     }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(tmem_cols)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// weight gradient on the tensor cores (stride-1 layers)
+//
+// With u = v + offset(t), dW[co][t][ci] = sum_u dy[u - offset(t)][co] x[u][ci]: the tap
+// shift moves to dy, whose out-of-grid values are zero (TMA fill), exactly like x's padding.
+// One CTA: M = 128 rows = TG taps x Co (TG = 128 / Co), N = Ci, K = the voxels of a chunk of
+// 8 x 4 x 4 tiles.  Per K tile: TG shifted dy boxes and the unshifted x box, both
+// channels-last, which the MMA reads as MN-major operands (channels contiguous in 16/32/64-
+// channel swizzle atoms, voxels along K in 8-row groups).  The epilogue writes each CTA's
+// partial sums; a fixed-order sum over chunks follows.
+// ------------------------------------------------------------------------------------
+constexpr int kWgMaxStages = 4;
+
+// MN-major descriptor: MN-blocks of CK elements (CK*2 bytes, the swizzle width) at LBO,
+// 8-row K groups at SBO = 8 * CK * 2.
+template <int CK>
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t addr, uint32_t lbo) {
+  constexpr uint64_t kSwizzle = CK == 16 ? 6 : (CK == 32 ? 4 : 2);
+  constexpr uint64_t kSbo = 8ull * CK * 2;
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (kSbo >> 4) << 32;
+  d |= 1ull << 46;
+  d |= kSwizzle << 61;
+  return d;
+}
+
+// D FP32, A and B BF16, both MN-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t instr_desc_mn(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+
+template <int CKA, int CKB>
+__global__ void __launch_bounds__(128, 1)
+wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant__ CUtensorMap tm_x,
+                float* __restrict__ part, Dims3 d, int Co, int Ci, int tg, int tiles_per_chunk,
+                int ntiles, int tiles_x, int tiles_y, int nchunks, int nst,
+                int* __restrict__ err) {
+  constexpr int KT = kBM;                       // voxels per K tile (8 x 4 x 4 box)
+  const int ablocks = Co / CKA;                 // A boxes per tap
+  const uint32_t a_box = KT * CKA * 2;          // bytes of one A box
+  const uint32_t a_bytes = (uint32_t)kBM * KT * 2;  // the whole 128-row A tile
+  const uint32_t b_box = KT * CKB * 2;
+  const uint32_t b_bytes = (uint32_t)Ci * KT * 2;         // loaded by TMA
+  const uint32_t stage_bytes = a_bytes + b_bytes + b_box;  // + one block of ones
+  const int n_mma = Ci + CKB;  // the ones block makes column Ci the bias partial
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[kWgMaxStages], empty_bar[kWgMaxStages], done_bar;
+  __shared__ uint32_t tmem_base_s;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int chunk = blockIdx.x, grp = blockIdx.y, b = blockIdx.z;
+  const int t0 = grp * tg;
+  const int ntap = 27 - t0 < tg ? 27 - t0 : tg;
+  const int tile0 = chunk * tiles_per_chunk;
+  const int tile1 = tile0 + tiles_per_chunk < ntiles ? tile0 + tiles_per_chunk : ntiles;
+  const int ksteps = tile1 - tile0;
+  const uint32_t tmem_cols = n_mma <= 32 ? 32u : n_mma <= 64 ? 64u : n_mma <= 128 ? 128u : 256u;
+  const uint32_t tx_bytes = (uint32_t)ntap * ablocks * a_box + b_bytes;
+  // the ones block of every stage (BF16 1.0 = 0x3F80); any swizzle of ones is ones
+  for (int s = 0; s < nst; ++s) {
+    uint32_t* ones = reinterpret_cast<uint32_t*>(smem + (size_t)s * stage_bytes + a_bytes + b_bytes);
+    for (int i = threadIdx.x; i < (int)(b_box / 4); i += blockDim.x) ones[i] = 0x3F803F80u;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nst; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_u32(&done_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_s)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  if (warp == 0 && lane == 0) {  // TMA producer
+    for (int k = 0; k < ksteps; ++k) {
+      const int s = k % nst, round = k / nst;
+      if (round > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (round - 1) & 1)) {
+        atomicOr(err, kErrProducer);
+        break;
+      }
+      const int tile = tile0 + k;
+      const int x0 = (tile % tiles_x) * kBX, y0 = ((tile / tiles_x) % tiles_y) * kBY,
+                z0 = (tile / (tiles_x * tiles_y)) * kBZ;
+      const uint32_t base = smem_u32(smem + (size_t)s * stage_bytes);
+      const uint32_t fb = smem_u32(&full_bar[s]);
+      mbar_expect_tx(fb, tx_bytes);
+      for (int q = 0; q < ntap; ++q) {
+        const int t = t0 + q, kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
+        for (int a = 0; a < ablocks; ++a)
+          tma_load_5d(base + (uint32_t)(q * ablocks + a) * a_box, &tm_dy, a * CKA,
+                      x0 - (kx - 1), y0 - (ky - 1), z0 - (kz - 1), b, fb);
+      }
+      for (int c = 0; c < Ci / CKB; ++c)
+        tma_load_5d(base + a_bytes + (uint32_t)c * b_box, &tm_x, c * CKB, x0, y0, z0, b, fb);
+    }
+  } else if (warp == 1 && lane == 0) {  // MMA issuer
+    const uint32_t idesc = instr_desc_mn(n_mma);
+    for (int k = 0; k < ksteps; ++k) {
+      const int s = k % nst;
+      if (!mbar_wait(smem_u32(&full_bar[s]), (k / nst) & 1)) {
+        atomicOr(err, kErrMma);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a_addr = smem_u32(smem + (size_t)s * stage_bytes);
+      const uint32_t b_addr = a_addr + a_bytes;
+#pragma unroll
+      for (int kk = 0; kk < KT / 16; ++kk)  // K = 16 voxels = two 8-row groups per MMA
+        mma_bf16(tmem, smem_desc_mn<CKA>(a_addr + kk * 2 * 8 * CKA * 2, a_box),
+                 smem_desc_mn<CKB>(b_addr + kk * 2 * 8 * CKB * 2, b_box), idesc,
+                 (k > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(smem_u32(&empty_bar[s]));
+    }
+    mma_commit(smem_u32(&done_bar));
+  }
+  __syncwarp();
+
+  const bool waited = ksteps > 0 ? mbar_wait(smem_u32(&done_bar), 0) : false;
+  const bool ok = __all_sync(0xffffffffu, waited);
+  if (!ok && ksteps > 0 && lane == 0) atomicOr(err, kErrEpilogue);
+  tc_fence_after();
+  const int m = warp * 32 + lane;       // TMEM lane = A row = (tap in group, co)
+  const int q = m / Co, co = m % Co;
+  const int t = t0 + q;
+  const long long row = (long long)Co * 27 * Ci + Co;
+  float* prow = part + ((long long)b * nchunks + chunk) * row;
+  float* out = prow + ((long long)co * 27 + t) * Ci;
+  for (int c0 = 0; c0 < Ci; c0 += 16) {
+    uint32_t r[16];
+    if (ok) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+    if (q < ntap) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) out[c0 + j] = ok ? __uint_as_float(r[j]) : 0.f;
+    }
+  }
+  {  // column Ci: sum of the row's dy over the chunk; the centre tap's is the bias partial
+    uint32_t r[16];
+    if (ok) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)Ci, r);
+    if (q < ntap && t == 13) prow[(long long)Co * 27 * Ci + co] = ok ? __uint_as_float(r[0]) : 0.f;
   }
   tc_fence_before();
   __syncthreads();
@@ -398,6 +564,7 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
   L.dout = conv_out_dims(din, k, s);
   L.w_off = w_off;
   L.dgrad = (s == 1) && bf16_conv_supported(co, ci, k);
+  L.wgrad = s == 1 && k == 3 && co <= 128 && 128 % co == 0 && ci + chunk_for(ci) <= 256;
   const long long n = (long long)co * k * k * k * ci;
   L.wf_off = bf.wstride;
   bf.wstride += (n + 63) / 64 * 64;
@@ -418,6 +585,7 @@ void bf16_layout(Bf16Net& bf, char* base, size_t& used, int B, long long max_act
   bf.max_act = max_act;
   bf.err = reinterpret_cast<int*>(take(sizeof(int)));
   bf.xbf = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * max_act * 2));
+  bf.ybf = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * max_act * 2));
   bf.wbuf = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * bf.wstride * 2));
 }
 
@@ -432,9 +600,81 @@ cudaError_t bf16_finalize(Bf16Net& bf, int B) {
       if (e == cudaSuccess)
         e = encode_w(&L.w_d, bf.wbuf + L.wd_off, B, bf.wstride, L.co, T, L.ci, chunk_for(L.co));
     }
+    if (e == cudaSuccess && L.wgrad)
+      e = encode_act(&L.act_wy, bf.ybf, B, L.dout, L.co, chunk_for(L.co), 1);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+static cudaError_t stage_bf16(const float* x, __nv_bfloat16* y, long long n, cudaStream_t st);
+
+namespace {
+
+struct WgPlan {
+  int tg, groups, tiles_x, tiles_y, ntiles, tiles_per_chunk, chunks, nst;
+  size_t smem;
+};
+
+WgPlan wgrad_plan(const TcLayer& L, int B) {
+  WgPlan p;
+  p.tiles_x = (int)ceil_div(L.dout.x, kBX);
+  p.tiles_y = (int)ceil_div(L.dout.y, kBY);
+  p.ntiles = p.tiles_x * p.tiles_y * (int)ceil_div(L.dout.z, kBZ);
+  p.tg = kBM / L.co;
+  p.groups = (int)ceil_div(27, p.tg);
+  const long long want = std::max(1LL, ceil_div(2 * 152, (long long)p.groups * B));
+  const int chunks0 = (int)std::min<long long>(p.ntiles, want);
+  p.tiles_per_chunk = (int)ceil_div(p.ntiles, chunks0);
+  p.chunks = (int)ceil_div(p.ntiles, p.tiles_per_chunk);
+  const size_t stage = (size_t)kBM * kBM * 2 + (size_t)(L.ci + chunk_for(L.ci)) * kBM * 2;
+  p.nst = (int)std::min<size_t>(kWgMaxStages, (200 * 1024) / stage);
+  p.smem = (size_t)p.nst * stage + 1024;
+  return p;
+}
+
+constexpr int kWgSmemMax = 210 * 1024;
+
+template <int CKA, int CKB>
+cudaError_t wgrad_attr() {
+  return cudaFuncSetAttribute(wgrad_tc_kernel<CKA, CKB>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmemMax);
+}
+
+template <int CKA, int CKB>
+void launch_wgrad_tc(dim3 grid, size_t smem, const TcLayer& L, float* part, const WgPlan& p,
+                     int* err, cudaStream_t st) {
+  wgrad_tc_kernel<CKA, CKB><<<grid, 128, smem, st>>>(
+      L.act_wy, L.act_f, part, L.dout, L.co, L.ci, p.tg, p.tiles_per_chunk, p.ntiles,
+      p.tiles_x, p.tiles_y, p.chunks, p.nst, err);
+}
+
+}  // namespace
+
+long long bf16_wgrad_chunks(const Bf16Net& bf, int layer, int B) {
+  return wgrad_plan(bf.layers[layer], B).chunks;
+}
+
+cudaError_t bf16_conv_wgrad(Bf16Net& bf, int layer, const float* x, const float* dy,
+                            float* part, int B, cudaStream_t stream) {
+  const TcLayer& L = bf.layers[layer];
+  if (!L.wgrad) return cudaErrorInvalidValue;
+  const WgPlan p = wgrad_plan(L, B);
+  cudaError_t e = stage_bf16(x, bf.xbf, (long long)B * L.din.count() * L.ci, stream);
+  if (e == cudaSuccess) e = stage_bf16(dy, bf.ybf, (long long)B * L.dout.count() * L.co, stream);
+  if (e != cudaSuccess) return e;
+  dim3 grid(p.chunks, p.groups, B);
+  const int cka = chunk_for(L.co), ckb = chunk_for(L.ci);
+#define D2IP_WGT(A_, B_) launch_wgrad_tc<A_, B_>(grid, p.smem, L, part, p, bf.err, stream)
+  if (cka == 16) {
+    if (ckb == 16) D2IP_WGT(16, 16); else if (ckb == 32) D2IP_WGT(16, 32); else D2IP_WGT(16, 64);
+  } else if (cka == 32) {
+    if (ckb == 16) D2IP_WGT(32, 16); else if (ckb == 32) D2IP_WGT(32, 32); else D2IP_WGT(32, 64);
+  } else {
+    if (ckb == 16) D2IP_WGT(64, 16); else if (ckb == 32) D2IP_WGT(64, 32); else D2IP_WGT(64, 64);
+  }
+#undef D2IP_WGT
+  return cudaGetLastError();
 }
 
 cudaError_t bf16_prepare_kernels() {
@@ -447,6 +687,15 @@ cudaError_t bf16_prepare_kernels() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(conv_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes(16, 256));
+  if (e == cudaSuccess) e = wgrad_attr<16, 16>();
+  if (e == cudaSuccess) e = wgrad_attr<16, 32>();
+  if (e == cudaSuccess) e = wgrad_attr<16, 64>();
+  if (e == cudaSuccess) e = wgrad_attr<32, 16>();
+  if (e == cudaSuccess) e = wgrad_attr<32, 32>();
+  if (e == cudaSuccess) e = wgrad_attr<32, 64>();
+  if (e == cudaSuccess) e = wgrad_attr<64, 16>();
+  if (e == cudaSuccess) e = wgrad_attr<64, 32>();
+  if (e == cudaSuccess) e = wgrad_attr<64, 64>();
   return e;
 }
 
@@ -494,7 +743,7 @@ long long bf16_op_workspace(int B, Dims3 din, int ci, int co, int k, int s) {
   const long long T = (long long)k * k * k;
   const long long act = std::max(din.count() * ci, dout.count() * co);
   const long long w = 2 * ((co * T * ci + 63) / 64 * 64);
-  return 1024 + ((long long)B * act * 2 + 1023) / 1024 * 1024 +
+  return 1024 + 2 * (((long long)B * act * 2 + 1023) / 1024 * 1024) +
          ((long long)B * w * 2 + 1023) / 1024 * 1024 + 1024;
 }
 
@@ -518,6 +767,36 @@ cudaError_t bf16_op_conv(bool dgrad, const float* in, const float* W, const floa
   if (e != cudaSuccess) return e;
   return dgrad ? bf16_conv_dgrad(bf, idx, in, out, B, accumulate, st)
                : bf16_conv_fwd(bf, idx, in, bias, out, B, w_bs, st);
+}
+
+long long bf16_op_wgrad_workspace(int B, Dims3 din, int ci, int co) {
+  Bf16Net bf;
+  const int idx = bf16_add_layer(bf, ci, co, 3, 1, din, 0);
+  if (idx < 0 || !bf.layers[idx].wgrad) return -1;
+  const long long rows = bf16_wgrad_chunks(bf, idx, B);
+  return bf16_op_workspace(B, din, ci, co, 3, 1) +
+         (long long)B * rows * ((long long)co * 27 * ci + co) * 4 + 1024;
+}
+
+cudaError_t bf16_op_wgrad(const float* x, const float* dy, float* dWb, int B, Dims3 din, int ci,
+                          int co, long long dw_bs, int accumulate, void* workspace,
+                          cudaStream_t st) {
+  cudaError_t e = bf16_prepare_kernels();
+  if (e != cudaSuccess) return e;
+  Bf16Net bf;
+  const int idx = bf16_add_layer(bf, ci, co, 3, 1, din, 0);
+  if (idx < 0 || !bf.layers[idx].wgrad) return cudaErrorInvalidValue;
+  size_t used = 0;
+  char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(workspace) + 1023) &
+                                       ~(uintptr_t)1023);
+  bf16_layout(bf, base, used, B, std::max(din.count() * ci, din.count() * co));
+  float* part = reinterpret_cast<float*>(base + used);
+  e = bf16_finalize(bf, B);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bf.err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = bf16_conv_wgrad(bf, idx, x, dy, part, B, st);
+  if (e != cudaSuccess) return e;
+  const long long row = (long long)co * 27 * ci + co;
+  return reduce_rows_f32(part, dWb, B, bf16_wgrad_chunks(bf, idx, B), row, dw_bs, accumulate, st);
 }
 
 }  // namespace d2ip

@@ -17,16 +17,19 @@ struct TcLayer {
   CUtensorMap w_f;    // forward weights [B][Co][T][Ci] (BF16)
   CUtensorMap act_d;  // stride-1 data-gradient input (dy staged in BF16)
   CUtensorMap w_d;    // data-gradient weights [B][Ci][T][Co], taps reversed (BF16)
+  CUtensorMap act_wy; // weight-gradient dy (second BF16 staging buffer)
   int ci = 0, co = 0, k = 3, s = 1;
   Dims3 din{}, dout{};
   long long w_off = 0;            // weights of this conv in the FP32 theta arena
   long long wf_off = 0, wd_off = 0;  // offsets in the per-problem BF16 weight block
   bool dgrad = false;             // data gradient on the tensor cores too (stride 1)
+  bool wgrad = false;             // weight gradient on the tensor cores too (3x3x3, stride 1)
 };
 
 // Device buffers of the BF16 path (carved from the context arena) and its layers.
 struct Bf16Net {
   __nv_bfloat16* xbf = nullptr;   // BF16 staging of one convolution input (or dy)
+  __nv_bfloat16* ybf = nullptr;   // BF16 staging of dy for the weight gradient
   __nv_bfloat16* wbuf = nullptr;  // BF16 weights of every tensor-core layer, per problem
   long long wstride = 0;          // elements per problem in wbuf
   long long max_act = 0;          // elements per problem of the largest staged input
@@ -53,11 +56,23 @@ cudaError_t bf16_conv_fwd(Bf16Net& bf, int layer, const float* x, const float* b
 cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, int B,
                             int accumulate, cudaStream_t stream);
 
+// Partial-sum rows (chunks of output voxels) of a tensor-core weight gradient.
+long long bf16_wgrad_chunks(const Bf16Net& bf, int layer, int B);
+// Per-chunk partial sums part[b][chunk][Co*27*Ci + Co] (weights, then bias) of a layer with
+// .wgrad set; the caller adds the chunks (reduce_rows_f32).
+cudaError_t bf16_conv_wgrad(Bf16Net& bf, int layer, const float* x, const float* dy,
+                            float* part, int B, cudaStream_t stream);
+
 // Context-free form for the op entry points: one layer, staging buffers, BF16 weights and
 // the error word carved from a caller workspace of bf16_op_workspace() bytes.
 long long bf16_op_workspace(int B, Dims3 din, int ci, int co, int k, int s);
 cudaError_t bf16_op_conv(bool dgrad, const float* in, const float* W, const float* bias,
                          float* out, int B, Dims3 din, int ci, int co, int k, int s,
                          long long w_bs, int accumulate, void* workspace, cudaStream_t st);
+
+long long bf16_op_wgrad_workspace(int B, Dims3 din, int ci, int co);
+cudaError_t bf16_op_wgrad(const float* x, const float* dy, float* dWb, int B, Dims3 din, int ci,
+                          int co, long long dw_bs, int accumulate, void* workspace,
+                          cudaStream_t st);
 
 }  // namespace d2ip

@@ -119,16 +119,32 @@ wgrad_brick_kernel(const float* __restrict__ x, const float* __restrict__ dy,
   }
 }
 
-__global__ void reduce_rows_kernel(const float* __restrict__ part, float* __restrict__ out,
-                                   long long R, long long N, long long out_bs, int accumulate) {
+// out[b][j] (=|+=) sum_r part[b][r][j].  A block covers 32 columns with 8 row groups; each
+// thread sums the rows r = g, g + 8, ... of its column, then the 8 group sums are added in a
+// fixed order (deterministic).
+constexpr int kRedCols = 32, kRedGroups = 8;
+
+__global__ void __launch_bounds__(kRedCols * kRedGroups)
+reduce_rows_kernel(const float* __restrict__ part, float* __restrict__ out, long long R,
+                   long long N, long long out_bs, int accumulate) {
+  __shared__ float red[kRedGroups][kRedCols];
   const int b = blockIdx.y;
-  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= N) return;
-  const float* p = part + (long long)b * R * N + j;
+  const int col = threadIdx.x % kRedCols, g = threadIdx.x / kRedCols;
+  const long long j = (long long)blockIdx.x * kRedCols + col;
   float sum = 0.f;
-  for (long long r = 0; r < R; ++r) sum += p[r * N];
-  float* o = out + (long long)b * out_bs + j;
-  *o = accumulate ? *o + sum : sum;
+  if (j < N) {
+    const float* p = part + (long long)b * R * N + j;
+    for (long long r = g; r < R; r += kRedGroups) sum += p[r * N];
+  }
+  red[g][col] = sum;
+  __syncthreads();
+  if (g == 0 && j < N) {
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < kRedGroups; ++q) s += red[q][col];
+    float* o = out + (long long)b * out_bs + j;
+    *o = accumulate ? *o + s : s;
+  }
 }
 
 // Output brick: 2 x 8 x 8 voxels for stride 1, 1 x 4 x 8 for stride 2 (keeps the stride-2
@@ -178,8 +194,9 @@ cudaError_t conv3d_wgrad_partial_f32(const float* x, const float* dy, float* par
 
 cudaError_t reduce_rows_f32(const float* part, float* out, int B, long long R, long long N,
                             long long out_bs, int accumulate, cudaStream_t stream) {
-  dim3 grid((unsigned)ceil_div(N, 256), B);
-  reduce_rows_kernel<<<grid, 256, 0, stream>>>(part, out, R, N, out_bs, accumulate);
+  dim3 grid((unsigned)ceil_div(N, kRedCols), B);
+  reduce_rows_kernel<<<grid, kRedCols * kRedGroups, 0, stream>>>(part, out, R, N, out_bs,
+                                                                  accumulate);
   return cudaGetLastError();
 }
 

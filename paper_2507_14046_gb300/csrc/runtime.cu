@@ -229,8 +229,13 @@ struct Carve {
   }
 };
 
+long long wgrad_rows(const d2ip_ctx* c, const ConvL& L) {
+  if (L.tc >= 0 && c->bf.layers[L.tc].wgrad) return bf16_wgrad_chunks(c->bf, L.tc, c->B);
+  return conv3d_wgrad_chunks(L.din, L.k, L.s);
+}
+
 long long conv_ws_floats(const d2ip_ctx* c, const ConvL& L) {
-  return (long long)c->B * conv3d_wgrad_chunks(L.din, L.k, L.s) * (L.wcount() + L.co);
+  return (long long)c->B * wgrad_rows(c, L) * (L.wcount() + L.co);
 }
 long long ln_ws_floats(const d2ip_ctx* c, const LnL& L, int lvl) {
   return (long long)c->B * layernorm_bwd_blocks(c->dims[lvl].count(), L.c) * 2 * L.c;
@@ -419,10 +424,13 @@ struct Launcher {
   }
   void conv_wgrad(const ConvL& L, const float* x, const float* dy) {
     beg(D2IP_KCLASS_CONV_WGRAD, conv_flops(L));
-    ok(conv3d_wgrad_partial_f32(x, dy, c->ws, c->B, L.din, L.ci, L.co, L.k, L.s,
-                                L.din.count() * L.ci, L.dout.count() * L.co, c->stream));
-    ok(reduce_rows_f32(c->ws, G(L.w_off), c->B, conv3d_wgrad_chunks(L.din, L.k, L.s),
-                       L.wcount() + L.co, c->Pp, 0, c->stream));
+    if (L.tc >= 0 && c->bf.layers[L.tc].wgrad)
+      ok(bf16_conv_wgrad(c->bf, L.tc, x, dy, c->ws, c->B, c->stream));
+    else
+      ok(conv3d_wgrad_partial_f32(x, dy, c->ws, c->B, L.din, L.ci, L.co, L.k, L.s,
+                                  L.din.count() * L.ci, L.dout.count() * L.co, c->stream));
+    ok(reduce_rows_f32(c->ws, G(L.w_off), c->B, wgrad_rows(c, L), L.wcount() + L.co, c->Pp, 0,
+                       c->stream));
     fin();
   }
   void ln_fwd(const LnL& L, int lvl, const float* z, const float* resid, float* y, float* xh,
@@ -1226,6 +1234,29 @@ d2ip_status d2ip_conv3d_dgrad_tc(const float* dyp, const float* W, float* dxp, i
                                  void* stream) {
   return tc_op(true, dyp, W, nullptr, dxp, batch, dz, dy, dx, ci, co, ksize, stride, w_bs,
                accumulate, ws, ws_bytes, stream);
+}
+
+long long d2ip_conv3d_wgrad_tc_workspace(int batch, int dz, int dy, int dx, int ci, int co) {
+  if (bad_conv(batch, dz, dy, dx, ci, co, 3, 1) || !bf16_conv_supported(ci, co, 3) || co > 128 ||
+      128 % co != 0)
+    return -1;
+  return bf16_op_wgrad_workspace(batch, Dims3{dz, dy, dx}, ci, co);
+}
+
+d2ip_status d2ip_conv3d_wgrad_tc(const float* x, const float* dyp, float* dWb, int batch, int dz,
+                                 int dy, int dx, int ci, int co, long long dw_bs, int accumulate,
+                                 void* ws, long long ws_bytes, void* stream) {
+  if (!x || !dyp || !dWb || !ws) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
+  const long long need = d2ip_conv3d_wgrad_tc_workspace(batch, dz, dy, dx, ci, co);
+  if (need < 0)
+    return fail(nullptr, D2IP_ERR_BAD_SHAPE,
+                "tensor-core weight gradient: 3x3x3 stride 1, ci and co multiples of 16, co "
+                "dividing 128");
+  if (ws_bytes < need) return fail(nullptr, D2IP_ERR_BAD_ARG, "workspace too small");
+  const long long row = (long long)co * 27 * ci + co;
+  OPCK(bf16_op_wgrad(x, dyp, dWb, batch, Dims3{dz, dy, dx}, ci, co, dw_bs ? dw_bs : row,
+                     accumulate, ws, (cudaStream_t)stream));
+  return D2IP_OK;
 }
 
 long long d2ip_conv3d_wgrad_workspace(int batch, int dz, int dy, int dx, int ci, int co,

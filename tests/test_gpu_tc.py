@@ -79,3 +79,32 @@ def test_tc_rejects_unsupported_shapes(d2ip):
     with pytest.raises(d2ip.D2IPError) as e:
         d2ip.d2ip_conv3d_dgrad_tc(1, 1, 1, 1, 4, 4, 4, 16, 16, 3, 2, 0, 0, 1, 1 << 20, None)
     assert e.value.status == -2
+
+
+WG_CASES = [((16, 8, 8), 16, 16), ((7, 9, 11), 32, 16), ((4, 8, 8), 64, 64), ((16, 16, 8), 48, 16),
+            ((8, 16, 16), 16, 32), ((5, 6, 7), 192, 64), ((8, 8, 8), 128, 128), ((6, 5, 9), 96, 32)]
+
+
+@pytest.mark.parametrize("din,ci,co", WG_CASES)
+def test_tc_weight_gradient(d2ip, din, ci, co):
+    rng = np.random.default_rng(ci * 7 + co)
+    B = 2
+    stream = torch.cuda.current_stream().cuda_stream
+    x = bf16_round(rng.standard_normal((B, *din, ci)).astype(np.float32))
+    dy = bf16_round(rng.standard_normal((B, *din, co)).astype(np.float32))
+    nw = co * 27 * ci
+    wsb = d2ip.d2ip_conv3d_wgrad_tc_workspace(B, *din, ci, co)
+    ws = torch.zeros(wsb, dtype=torch.uint8, device="cuda")
+    out = torch.full((B, nw + co), float("nan"), device="cuda")
+    d2ip.d2ip_conv3d_wgrad_tc(_dev(x), _dev(dy), out, B, *din, ci, co, nw + co, 0, ws, wsb,
+                              stream)
+    torch.cuda.synchronize()
+    assert _err_word(ws) == 0
+    W0 = np.zeros((co, 3, 3, 3, ci))
+    for b in range(B):
+        _, gW, gb = onet.conv3d_backward(x[b].astype(np.float64), W0, 1, dy[b].astype(np.float64))
+        o = out[b].cpu().numpy()
+        e = rel(o[:nw], gW.reshape(-1))
+        print("tc wgrad rel err", e)
+        assert e < TOL
+        assert rel(o[nw:], gb) < 1e-5
