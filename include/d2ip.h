@@ -273,7 +273,8 @@ d2ip_status d2ip_layernorm_act_backward(const float* dy, const float* act_out,
                                         void* stream);
 
 /* cat[:, :cu] = trilinear(low (lz,ly,lx) -> (oz,oy,ox)), half-pixel centres, source index
- * clamped at 0 (PyTorch align_corners=False with an explicit size); cat[:, cu:] = skip. */
+ * clamped at 0 (PyTorch align_corners=False with an explicit size); cat[:, cu:] = skip.
+ * cu and cs are multiples of 4 (cs may be 0). */
 d2ip_status d2ip_upsample_concat_forward(const float* low, const float* skip, float* cat,
                                          int batch, int lz, int ly, int lx, int oz, int oy,
                                          int ox, int cu, int cs, void* stream);
@@ -284,9 +285,12 @@ d2ip_status d2ip_upsample_concat_backward(const float* dcat, float* dlow, float*
                                           int ox, int cu, int cs, void* stream);
 
 /* Data term of Eq. 4: r[b] = J x[b] - dv[b] (FP32, x [batch][n]) and, when loss is not NULL,
- * loss[b] = |r[b]|^2 / m accumulated in FP64 (device memory). */
+ * loss[b] = |r[b]|^2 / m accumulated in FP64 (device memory).  The products are summed in
+ * fixed-order column chunks held in `workspace` (d2ip_sensitivity_workspace bytes). */
+long long d2ip_sensitivity_workspace(int batch, int m, int n);
 d2ip_status d2ip_sensitivity_residual(const float* J, const float* x, const float* dv,
                                       float* r, double* loss, int batch, int m, int n,
+                                      void* workspace, long long workspace_bytes,
                                       void* stream);
 /* g[b] = scale * J^T r[b]  (scale = 2/m gives the gradient of the mean-square data term). */
 d2ip_status d2ip_sensitivity_adjoint(const float* J, const float* r, float* g, float scale,

@@ -74,7 +74,7 @@ _SIGS = {
                                     _i, _vp, _ll, _vp],
     "d2ip_upsample_concat_forward": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _i, _vp],
     "d2ip_upsample_concat_backward": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _i, _vp],
-    "d2ip_sensitivity_residual": [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _vp],
+    "d2ip_sensitivity_residual": [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _vp, _ll, _vp],
     "d2ip_sensitivity_adjoint": [_vp, _vp, _vp, _f, _i, _i, _i, _vp],
     "d2ip_normalize_columns": [_vp, _vp, _i, _i, _vp],
     "d2ip_adam_update": [_vp, _vp, _vp, _vp, _ll, _d, _d, _d, _d, _i, _vp],
@@ -84,6 +84,7 @@ _SIZE_FNS = {
     "d2ip_conv3d_tc_workspace": [_i] * 8,
     "d2ip_conv3d_wgrad_tc_workspace": [_i] * 6,
     "d2ip_layernorm_workspace": [_i, _ll, _i],
+    "d2ip_sensitivity_workspace": [_i, _i, _i],
 }
 
 for _name, _args in _SIGS.items():
@@ -191,6 +192,10 @@ def d2ip_conv3d_tc_workspace(*args) -> int:
 
 def d2ip_conv3d_wgrad_tc_workspace(*args) -> int:
     return int(_lib.d2ip_conv3d_wgrad_tc_workspace(*args))
+
+
+def d2ip_sensitivity_workspace(*args) -> int:
+    return int(_lib.d2ip_sensitivity_workspace(*args))
 
 
 def d2ip_layernorm_workspace(*args) -> int:

@@ -72,8 +72,11 @@ cudaError_t upsample_concat_bwd_f32(const float* dcat, float* dlow, float* dskip
 cudaError_t add_inplace_f32(float* y, const float* x, long long count, cudaStream_t stream);
 
 // Data term.  r[b] = J x[b] - dv[b];  g[b] = scale * J^T r[b];  loss in FP64.
+// part: workspace of jmul_chunks(n) * B * m floats (deterministic column-chunk partials).
+int jmul_chunks(int n);
 cudaError_t jmul_residual_f32(const float* J, const float* x, const float* dv, float* r,
-                              int B, int m, int n, long long x_bs, cudaStream_t stream);
+                              float* part, int B, int m, int n, long long x_bs,
+                              cudaStream_t stream);
 // Per-device kernel attributes (opt-in shared memory); call once per device before launches.
 cudaError_t prepare_pointwise_kernels();
 cudaError_t jtmul_f32(const float* J, const float* r, float* g, float scale, int B, int m,

@@ -152,58 +152,67 @@ struct AxisW {
 };
 
 // src = ((2o+1) s_in - s_out) / (2 s_out), clamped at 0: integer form, exact index map.
+// Sizes stay far below 2^15, so 32-bit arithmetic is exact.
 __device__ __forceinline__ AxisW axis_map(int o, int s_in, int s_out) {
-  long long num = (long long)(2 * o + 1) * s_in - s_out;
+  int num = (2 * o + 1) * s_in - s_out;
   if (num < 0) num = 0;
-  const long long den = 2LL * s_out;
+  const int den = 2 * s_out;
   AxisW a;
-  a.i0 = (int)(num / den);
-  a.w1 = (float)(num - (long long)a.i0 * den) / (float)den;
+  a.i0 = num / den;
+  a.w1 = (float)(num - a.i0 * den) / (float)den;
   a.i1 = a.i0 + 1 < s_in ? a.i0 + 1 : s_in - 1;
   return a;
 }
 
+// One thread per (output voxel, group of 4 channels) of cat = [up(low), skip].
 __global__ void up_concat_fwd_kernel(const float* __restrict__ low,
                                      const float* __restrict__ skip, float* __restrict__ cat,
                                      Dims3 dl, Dims3 dout, int Cu, int Cs) {
   const int b = blockIdx.y;
-  const int Ct = Cu + Cs;
+  const int Ct = Cu + Cs, G = Ct / 4;
   const long long nout = dout.count();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nout * Ct) return;
-  const long long vox = e / Ct;
-  const int c = (int)(e % Ct);
-  float val;
+  if (e >= nout * G) return;
+  const long long vox = e / G;
+  const int c = (int)(e % G) * 4;
+  float4 val;
   if (c >= Cu) {
-    val = skip[((long long)b * nout + vox) * Cs + (c - Cu)];
+    val = *reinterpret_cast<const float4*>(skip + ((long long)b * nout + vox) * Cs + (c - Cu));
   } else {
     const int ox = (int)(vox % dout.x);
-    const long long r = vox / dout.x;
-    const int oy = (int)(r % dout.y), oz = (int)(r / dout.y);
+    const int r = (int)(vox / dout.x);
+    const int oy = r % dout.y, oz = r / dout.y;
     const AxisW az = axis_map(oz, dl.z, dout.z), ay = axis_map(oy, dl.y, dout.y),
                 ax = axis_map(ox, dl.x, dout.x);
     const float* L = low + (long long)b * dl.count() * Cu + c;
     const int zs[2] = {az.i0, az.i1}, ys[2] = {ay.i0, ay.i1}, xs[2] = {ax.i0, ax.i1};
     const float wz[2] = {1.f - az.w1, az.w1}, wy[2] = {1.f - ay.w1, ay.w1},
                 wx[2] = {1.f - ax.w1, ax.w1};
-    val = 0.f;
+    val = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int j = 0; j < 2; ++j)
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
-          val += wz[i] * wy[j] * wx[k] *
-                 L[(((long long)zs[i] * dl.y + ys[j]) * dl.x + xs[k]) * Cu];
+        for (int k = 0; k < 2; ++k) {
+          const float w = wz[i] * wy[j] * wx[k];
+          const float4 v = *reinterpret_cast<const float4*>(
+              L + (((long long)zs[i] * dl.y + ys[j]) * dl.x + xs[k]) * Cu);
+          val.x += w * v.x;
+          val.y += w * v.y;
+          val.z += w * v.z;
+          val.w += w * v.w;
+        }
   }
-  cat[((long long)b * nout + vox) * Ct + c] = val;
+  *reinterpret_cast<float4*>(cat + ((long long)b * nout + vox) * Ct + c) = val;
 }
 
 // Output positions along one axis that read input index i, with their weights.
 __device__ __forceinline__ int axis_sources(int i, int s_in, int s_out, int* os, float* ws) {
-  const double r = (double)s_out / (double)s_in;
-  int lo = (int)floor((i - 0.5) * r - 0.5) - 1;
-  int hi = (int)ceil((i + 1.5) * r - 0.5) + 1;
+  // outputs o with i0(o) or i1(o) == i satisfy (i - 1/2) r - 1/2 < o < (i + 3/2) r - 1/2,
+  // r = s_out / s_in; scan that window (widened by one) with the exact map
+  int lo = ((2 * i - 1) * s_out - s_in) / (2 * s_in) - 1;
+  int hi = ((2 * i + 3) * s_out - s_in) / (2 * s_in) + 1;
   if (lo < 0) lo = 0;
   if (hi > s_out - 1) hi = s_out - 1;
   int n = 0;
@@ -221,31 +230,38 @@ __device__ __forceinline__ int axis_sources(int i, int s_in, int s_out, int* os,
   return n;
 }
 
+// One thread per (low voxel, group of 4 up-sampled channels): gather of the adjoint.
 __global__ void up_bwd_kernel(const float* __restrict__ dcat, float* __restrict__ dlow,
                               Dims3 dl, Dims3 dout, int Cu, int Cs) {
   const int b = blockIdx.y;
-  const int Ct = Cu + Cs;
+  const int Ct = Cu + Cs, G = Cu / 4;
   const long long nl = dl.count();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nl * Cu) return;
-  const long long vox = e / Cu;
-  const int c = (int)(e % Cu);
+  if (e >= nl * G) return;
+  const long long vox = e / G;
+  const int c = (int)(e % G) * 4;
   const int ix = (int)(vox % dl.x);
-  const long long r = vox / dl.x;
-  const int iy = (int)(r % dl.y), iz = (int)(r / dl.y);
+  const int r = (int)(vox / dl.x);
+  const int iy = r % dl.y, iz = r / dl.y;
   int oz[8], oy[8], ox[8];
   float wz[8], wy[8], wx[8];
   const int nz = axis_sources(iz, dl.z, dout.z, oz, wz);
   const int ny = axis_sources(iy, dl.y, dout.y, oy, wy);
   const int nx = axis_sources(ix, dl.x, dout.x, ox, wx);
   const float* D = dcat + (long long)b * dout.count() * Ct + c;
-  float acc = 0.f;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int a = 0; a < nz; ++a)
     for (int q = 0; q < ny; ++q)
-      for (int k = 0; k < nx; ++k)
-        acc += wz[a] * wy[q] * wx[k] *
-               D[(((long long)oz[a] * dout.y + oy[q]) * dout.x + ox[k]) * Ct];
-  dlow[((long long)b * nl + vox) * Cu + c] = acc;
+      for (int k = 0; k < nx; ++k) {
+        const float w = wz[a] * wy[q] * wx[k];
+        const float4 v = *reinterpret_cast<const float4*>(
+            D + (((long long)oz[a] * dout.y + oy[q]) * dout.x + ox[k]) * Ct);
+        acc.x += w * v.x;
+        acc.y += w * v.y;
+        acc.z += w * v.z;
+        acc.w += w * v.w;
+      }
+  *reinterpret_cast<float4*>(dlow + ((long long)b * nl + vox) * Cu + c) = acc;
 }
 
 __global__ void split_skip_kernel(const float* __restrict__ dcat, float* __restrict__ dskip,
@@ -270,38 +286,76 @@ __global__ void add_kernel(float* __restrict__ y, const float* __restrict__ x, l
 constexpr int kJB = 8;  // problems per block in the J kernels
 constexpr int kJtmulMaxSmem = 200 * 1024;
 
+// r[b][i] = sum_j J[i][j] x[b][j] - dv[b][i], in two deterministic stages.  Stage 1: a block
+// takes 1024 columns (4 per thread, float4) of kJRows rows for kJB problems and writes the
+// block's partial sums; stage 2 adds the column chunks in order and subtracts dv.
+constexpr int kJRows = 4;
+constexpr int kJCols = 1024;
+
 __global__ void __launch_bounds__(256)
-jmul_kernel(const float* __restrict__ J, const float* __restrict__ x,
-            const float* __restrict__ dv, float* __restrict__ r, int B, int m, int n,
-            long long x_bs) {
-  __shared__ float red[kJB][8];
-  const int i = blockIdx.x;
-  const int b0 = blockIdx.y * kJB;
+jmul_part_kernel(const float* __restrict__ J, const float* __restrict__ x,
+                 float* __restrict__ part, int B, int m, int n, long long x_bs) {
+  __shared__ float red[8][kJRows * kJB];
+  const int chunk = blockIdx.x;
+  const int i0 = blockIdx.y * kJRows;
+  const int b0 = blockIdx.z * kJB;
   const int nb = B - b0 < kJB ? B - b0 : kJB;
-  const float* row = J + (long long)i * n;
-  float acc[kJB];
+  const int nr = m - i0 < kJRows ? m - i0 : kJRows;
+  float acc[kJRows][kJB];
 #pragma unroll
-  for (int q = 0; q < kJB; ++q) acc[q] = 0.f;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const float a = row[j];
+  for (int r = 0; r < kJRows; ++r)
+#pragma unroll
+    for (int q = 0; q < kJB; ++q) acc[r][q] = 0.f;
+  const int j = chunk * kJCols + threadIdx.x * 4;
+  if (j + 3 < n && (n & 3) == 0) {
+    float4 xv[kJB];
 #pragma unroll
     for (int q = 0; q < kJB; ++q)
-      if (q < nb) acc[q] = fmaf(a, x[(long long)(b0 + q) * x_bs + j], acc[q]);
+      xv[q] = q < nb ? *reinterpret_cast<const float4*>(x + (long long)(b0 + q) * x_bs + j)
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < kJRows; ++r) {
+      if (r >= nr) break;
+      const float4 a = *reinterpret_cast<const float4*>(J + (long long)(i0 + r) * n + j);
+#pragma unroll
+      for (int q = 0; q < kJB; ++q)
+        acc[r][q] = fmaf(a.x, xv[q].x, fmaf(a.y, xv[q].y, fmaf(a.z, xv[q].z,
+                                                            fmaf(a.w, xv[q].w, acc[r][q]))));
+    }
+  } else {
+    for (int jj = j; jj < j + 4 && jj < n; ++jj)
+      for (int r = 0; r < nr; ++r) {
+        const float a = J[(long long)(i0 + r) * n + jj];
+        for (int q = 0; q < nb; ++q) acc[r][q] = fmaf(a, x[(long long)(b0 + q) * x_bs + jj], acc[r][q]);
+      }
   }
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
 #pragma unroll
-  for (int q = 0; q < kJB; ++q) {
-    float v = acc[q];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (l == 0) red[q][w] = v;
-  }
+  for (int r = 0; r < kJRows; ++r)
+#pragma unroll
+    for (int q = 0; q < kJB; ++q) {
+      float v = acc[r][q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (l == 0) red[w][r * kJB + q] = v;
+    }
   __syncthreads();
-  if (threadIdx.x < nb) {
-    const int q = threadIdx.x;
-    float s = 0.f;
-    for (int k = 0; k < 8; ++k) s += red[q][k];
-    r[(long long)(b0 + q) * m + i] = s - dv[(long long)(b0 + q) * m + i];
+  if (threadIdx.x < kJRows * kJB) {
+    const int r = threadIdx.x / kJB, q = threadIdx.x % kJB;
+    if (r < nr && q < nb) {
+      float v = 0.f;
+      for (int k = 0; k < 8; ++k) v += red[k][threadIdx.x];
+      part[((long long)chunk * B + b0 + q) * m + i0 + r] = v;
+    }
   }
+}
+
+__global__ void jmul_final_kernel(const float* __restrict__ part, const float* __restrict__ dv,
+                                  float* __restrict__ r, int B, int m, int nchunks) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)B * m) return;
+  float s = 0.f;
+  for (int c = 0; c < nchunks; ++c) s += part[(long long)c * B * m + e];
+  r[e] = s - dv[e];
 }
 
 __global__ void __launch_bounds__(256)
@@ -477,7 +531,8 @@ cudaError_t layernorm_act_bwd_f32(const float* dy, const float* act_out, const f
 cudaError_t upsample_concat_fwd_f32(const float* low, const float* skip, float* cat, int B,
                                     Dims3 dlow, Dims3 dout, int Cu, int Cs,
                                     cudaStream_t stream) {
-  const long long total = dout.count() * (Cu + Cs);
+  if (Cu % 4 || Cs % 4) return cudaErrorInvalidValue;
+  const long long total = dout.count() * ((Cu + Cs) / 4);
   dim3 grid((unsigned)ceil_div(total, 256), B);
   up_concat_fwd_kernel<<<grid, 256, 0, stream>>>(low, skip, cat, dlow, dout, Cu, Cs);
   return cudaGetLastError();
@@ -486,7 +541,8 @@ cudaError_t upsample_concat_fwd_f32(const float* low, const float* skip, float* 
 cudaError_t upsample_concat_bwd_f32(const float* dcat, float* dlow, float* dskip, int B,
                                     Dims3 dlow_dims, Dims3 dout, int Cu, int Cs,
                                     cudaStream_t stream) {
-  dim3 g1((unsigned)ceil_div(dlow_dims.count() * Cu, 256), B);
+  if (Cu % 4 || Cs % 4) return cudaErrorInvalidValue;
+  dim3 g1((unsigned)ceil_div(dlow_dims.count() * (Cu / 4), 256), B);
   up_bwd_kernel<<<g1, 256, 0, stream>>>(dcat, dlow, dlow_dims, dout, Cu, Cs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !dskip || Cs == 0) return e;
@@ -500,10 +556,18 @@ cudaError_t add_inplace_f32(float* y, const float* x, long long count, cudaStrea
   return cudaGetLastError();
 }
 
+int jmul_chunks(int n) { return (int)ceil_div(n, kJCols); }
+
 cudaError_t jmul_residual_f32(const float* J, const float* x, const float* dv, float* r,
-                              int B, int m, int n, long long x_bs, cudaStream_t stream) {
-  dim3 grid(m, (unsigned)ceil_div(B, kJB));
-  jmul_kernel<<<grid, 256, 0, stream>>>(J, x, dv, r, B, m, n, x_bs);
+                              float* part, int B, int m, int n, long long x_bs,
+                              cudaStream_t stream) {
+  const int nch = jmul_chunks(n);
+  dim3 grid(nch, (unsigned)ceil_div(m, kJRows), (unsigned)ceil_div(B, kJB));
+  jmul_part_kernel<<<grid, 256, 0, stream>>>(J, x, part, B, m, n, x_bs);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  jmul_final_kernel<<<(unsigned)ceil_div((long long)B * m, 256), 256, 0, stream>>>(part, dv, r, B,
+                                                                                  m, nch);
   return cudaGetLastError();
 }
 

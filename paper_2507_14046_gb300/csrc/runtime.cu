@@ -95,6 +95,7 @@ struct d2ip_ctx {
   double *loss = nullptr, *resid = nullptr, *trace = nullptr, *seq_resid = nullptr;
   int *trace_pos = nullptr, *adam_t = nullptr, *status = nullptr;
   float* J = nullptr;
+  float* jpart = nullptr;  // column-chunk partial sums of J x
   double* colnorm = nullptr;
   size_t j_bytes = 0;
   int seq_T_cap = 0;
@@ -490,7 +491,8 @@ struct Launcher {
     const long long n = c->n();
     const double jb = 4.0 * c->m * (double)n, vb = 4.0 * c->B * ((double)n + 2.0 * c->m);
     beg(D2IP_KCLASS_JMUL, jb + vb);
-    ok(jmul_residual_f32(c->J, c->dsigma, c->dv, c->r, c->B, c->m, (int)n, n, c->stream));
+    ok(jmul_residual_f32(c->J, c->dsigma, c->dv, c->r, c->jpart, c->B, c->m, (int)n, n,
+                         c->stream));
     fin();
     beg(D2IP_KCLASS_LOSS, 4.0 * c->B * c->m);
     if (training) {
@@ -804,6 +806,7 @@ d2ip_status d2ip_destroy(d2ip_ctx* c) {
   if (c->colnorm) cudaFree(c->colnorm);
   if (c->r) cudaFree(c->r);
   if (c->dv) cudaFree(c->dv);
+  if (c->jpart) cudaFree(c->jpart);
   if (c->seq_resid) cudaFree(c->seq_resid);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -886,14 +889,16 @@ d2ip_status d2ip_load_J(d2ip_ctx* c, const float* J, int m, int n, int normalize
     if (c->colnorm) cudaFree(c->colnorm);
     if (c->r) cudaFree(c->r);
     if (c->dv) cudaFree(c->dv);
+    if (c->jpart) cudaFree(c->jpart);
     c->J = nullptr;
     c->colnorm = nullptr;
-    c->r = c->dv = nullptr;
+    c->r = c->dv = c->jpart = nullptr;
     c->j_bytes = 0;
     if (cudaMalloc(&c->J, bytes) != cudaSuccess ||
         cudaMalloc(&c->colnorm, sizeof(double) * n) != cudaSuccess ||
         cudaMalloc(&c->r, sizeof(float) * m * c->B) != cudaSuccess ||
-        cudaMalloc(&c->dv, sizeof(float) * m * c->B) != cudaSuccess)
+        cudaMalloc(&c->dv, sizeof(float) * m * c->B) != cudaSuccess ||
+        cudaMalloc(&c->jpart, sizeof(float) * jmul_chunks(n) * (size_t)m * c->B) != cudaSuccess)
       return fail(c, D2IP_ERR_OOM, "device allocation of J failed");
     c->j_bytes = bytes;
     c->m = m;
@@ -1327,8 +1332,9 @@ d2ip_status d2ip_upsample_concat_forward(const float* low, const float* skip, fl
                                          int batch, int lz, int ly, int lx, int oz, int oy,
                                          int ox, int cu, int cs, void* stream) {
   if (!low || !cat || (cs > 0 && !skip)) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
-  if (batch < 1 || lz < 1 || ly < 1 || lx < 1 || oz < 1 || oy < 1 || ox < 1 || cu < 1 || cs < 0)
-    return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad upsample shape");
+  if (batch < 1 || lz < 1 || ly < 1 || lx < 1 || oz < 1 || oy < 1 || ox < 1 || cu < 4 || cs < 0 ||
+      cu % 4 || cs % 4)
+    return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad upsample shape (cu, cs multiples of 4)");
   OPCK(upsample_concat_fwd_f32(low, skip, cat, batch, Dims3{lz, ly, lx}, Dims3{oz, oy, ox}, cu,
                                cs, (cudaStream_t)stream));
   return D2IP_OK;
@@ -1338,8 +1344,9 @@ d2ip_status d2ip_upsample_concat_backward(const float* dcat, float* dlow, float*
                                           int batch, int lz, int ly, int lx, int oz, int oy,
                                           int ox, int cu, int cs, void* stream) {
   if (!dcat || !dlow) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
-  if (batch < 1 || lz < 1 || ly < 1 || lx < 1 || oz < 1 || oy < 1 || ox < 1 || cu < 1 || cs < 0)
-    return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad upsample shape");
+  if (batch < 1 || lz < 1 || ly < 1 || lx < 1 || oz < 1 || oy < 1 || ox < 1 || cu < 4 || cs < 0 ||
+      cu % 4 || cs % 4)
+    return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad upsample shape (cu, cs multiples of 4)");
   // the gather visits at most 8 outputs per input and axis: needs out/in <= about 3
   if (oz > 3 * lz || oy > 3 * ly || ox > 3 * lx)
     return fail(nullptr, D2IP_ERR_BAD_SHAPE, "upsample factor above 3 not supported");
@@ -1348,12 +1355,21 @@ d2ip_status d2ip_upsample_concat_backward(const float* dcat, float* dlow, float*
   return D2IP_OK;
 }
 
+long long d2ip_sensitivity_workspace(int batch, int m, int n) {
+  if (batch < 1 || m < 1 || n < 1) return -1;
+  return (long long)sizeof(float) * jmul_chunks(n) * m * batch;
+}
+
 d2ip_status d2ip_sensitivity_residual(const float* J, const float* x, const float* dv,
                                       float* r, double* loss, int batch, int m, int n,
+                                      void* workspace, long long workspace_bytes,
                                       void* stream) {
-  if (!J || !x || !dv || !r) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
+  if (!J || !x || !dv || !r || !workspace) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
   if (batch < 1 || m < 1 || n < 1) return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad J shape");
-  OPCK(jmul_residual_f32(J, x, dv, r, batch, m, n, n, (cudaStream_t)stream));
+  if (workspace_bytes < d2ip_sensitivity_workspace(batch, m, n))
+    return fail(nullptr, D2IP_ERR_BAD_ARG, "workspace too small");
+  OPCK(jmul_residual_f32(J, x, dv, r, static_cast<float*>(workspace), batch, m, n, n,
+                         (cudaStream_t)stream));
   if (loss)
     OPCK(residual_loss_f64(r, loss, nullptr, nullptr, 0, nullptr, nullptr, batch, m,
                            (cudaStream_t)stream));

@@ -143,7 +143,8 @@ def test_upsample_constant_field_exact(d2ip):
     np.testing.assert_array_equal(cat.cpu().numpy(), 0.625)
 
 
-@pytest.mark.parametrize("m,n,B", [(208, 2048, 1), (416, 16384, 3), (624, 4999, 9)])
+@pytest.mark.parametrize("m,n,B", [(208, 2048, 1), (416, 16384, 3), (624, 4999, 9),
+                                   (416, 55296, 13), (3, 1030, 17)])
 def test_sensitivity_products_and_normalisation(d2ip, m, n, B):
     rng = np.random.default_rng(m + n)
     J = rng.standard_normal((m, n)).astype(np.float32) * 3
@@ -155,7 +156,9 @@ def test_sensitivity_products_and_normalisation(d2ip, m, n, B):
     dv = rng.standard_normal((B, m)).astype(np.float32)
     r = torch.zeros((B, m), device="cuda")
     loss = torch.zeros(B, dtype=torch.float64, device="cuda")
-    d2ip.d2ip_sensitivity_residual(Jd, _dev(x), _dev(dv), r, loss, B, m, n, _stream())
+    wsb = d2ip.d2ip_sensitivity_workspace(B, m, n)
+    ws = torch.empty(wsb // 4 + 1, device="cuda")
+    d2ip.d2ip_sensitivity_residual(Jd, _dev(x), _dev(dv), r, loss, B, m, n, ws, wsb, _stream())
     g = torch.zeros((B, n), device="cuda")
     d2ip.d2ip_sensitivity_adjoint(Jd, r, g, 2.0 / m, B, m, n, _stream())
     torch.cuda.synchronize()
