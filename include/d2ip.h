@@ -197,8 +197,9 @@ d2ip_status d2ip_conv3d_dgrad(const float* dy, const float* W, float* dx, int ba
                               long long w_batch_stride, int accumulate, void* stream);
 /* Tensor-core forms (tcgen05, sm_103a) of the two calls above: x (or dy) and W are rounded
  * to BF16 (round to nearest even), products accumulate in FP32 in tensor memory; the
- * bias is added in FP32.  Needs ci and co multiples of 16, co <= 256 (and, for the data
- * gradient, stride 1).  `workspace` (device, d2ip_conv3d_tc_workspace bytes) receives the
+ * bias is added in FP32.  Needs ci and co multiples of 16, co <= 256 (ci <= 256 too for the
+ * data gradient; its stride-2 form runs as 8 output-parity classes of 1 to 8 taps on the
+ * coarse grid).  `workspace` (device, d2ip_conv3d_tc_workspace bytes) receives the
  * BF16 staging copies; the int at its first 1024-byte aligned address is an error word,
  * non-zero after the call when a pipeline wait of the kernel gave up (about 1 s). */
 long long d2ip_conv3d_tc_workspace(int batch, int dz, int dy, int dx, int ci, int co,
@@ -212,13 +213,15 @@ d2ip_status d2ip_conv3d_dgrad_tc(const float* dy, const float* W, float* dx, int
                                  long long w_batch_stride, int accumulate, void* workspace,
                                  long long workspace_bytes, void* stream);
 
-/* Tensor-core weight gradient of a 3x3x3 stride-1 convolution (tcgen05, x and dy rounded to
- * BF16, FP32 accumulation; bias gradient in FP32): result as d2ip_conv3d_wgrad.  Needs ci and
- * co multiples of 16, co dividing 128, ci <= 256.  Workspace: d2ip_conv3d_wgrad_tc_workspace
- * bytes (device); the int at its first 1024-byte aligned address is the error word. */
-long long d2ip_conv3d_wgrad_tc_workspace(int batch, int dz, int dy, int dx, int ci, int co);
+/* Tensor-core weight gradient of a stride-1 convolution (3x3x3 or 1x1x1; tcgen05, x and dy
+ * rounded to BF16, FP32 accumulation, the bias gradient from the same MMAs): result as
+ * d2ip_conv3d_wgrad.  Needs ci and co multiples of 16, co dividing 128, ci + min(64, ci) <= 256.
+ * Workspace: d2ip_conv3d_wgrad_tc_workspace bytes (device); the int at its first 1024-byte
+ * aligned address is the error word. */
+long long d2ip_conv3d_wgrad_tc_workspace(int batch, int dz, int dy, int dx, int ci, int co,
+                                         int ksize);
 d2ip_status d2ip_conv3d_wgrad_tc(const float* x, const float* dy, float* dWb, int batch,
-                                 int dz, int dy_, int dx_, int ci, int co,
+                                 int dz, int dy_, int dx_, int ci, int co, int ksize,
                                  long long dw_batch_stride, int accumulate, void* workspace,
                                  long long workspace_bytes, void* stream);
 

@@ -66,7 +66,8 @@ _SIGS = {
                                _ll, _vp],
     "d2ip_conv3d_dgrad_tc": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _ll, _i, _vp, _ll,
                              _vp],
-    "d2ip_conv3d_wgrad_tc": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _ll, _i, _vp, _ll, _vp],
+    "d2ip_conv3d_wgrad_tc": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _ll, _i, _vp, _ll,
+                             _vp],
     "d2ip_conv3d_wgrad_noalloc": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _ll, _i,
                                   _vp],
     "d2ip_layernorm_act_forward": [_vp, _vp, _vp, _vp, _vp, _vp, _i, _ll, _i, _i, _ll, _vp],
@@ -82,7 +83,7 @@ _SIGS = {
 _SIZE_FNS = {
     "d2ip_conv3d_wgrad_workspace": [_i] * 8,
     "d2ip_conv3d_tc_workspace": [_i] * 8,
-    "d2ip_conv3d_wgrad_tc_workspace": [_i] * 6,
+    "d2ip_conv3d_wgrad_tc_workspace": [_i] * 7,
     "d2ip_layernorm_workspace": [_i, _ll, _i],
     "d2ip_sensitivity_workspace": [_i, _i, _i],
 }

@@ -135,12 +135,28 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 
 constexpr int kErrProducer = 1, kErrMma = 2, kErrEpilogue = 4;
 
+// Taps of one launch: the input box of tap j starts at origin * s_in + off[j] (x, y, z), its
+// weights are tap widx[j] of the weight tensor, and the tile's output voxel q is written at
+// q * s_out + r.  A forward convolution is one class of 27 (or 1) taps; the stride-2 data
+// gradient is 8 classes, one per output parity, of 1, 2, 4 or 8 taps.
+struct TapClass {
+  int n;
+  int8_t off[27][3];
+  uint8_t widx[27];
+  int8_t r[3];
+};
+struct TapPlan {
+  int s_in, s_out;
+  TapClass cls[8];
+};
+
 template <int CK>
 __global__ void __launch_bounds__(128, 1)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
-               const float* __restrict__ bias, float* __restrict__ out, Dims3 dout, int N,
-               int K, int S, int nchunks, int tiles_x, int tiles_y, long long out_bs,
-               long long bias_bs, int accumulate, int* __restrict__ err) {
+               const __grid_constant__ TapPlan plan, const float* __restrict__ bias,
+               float* __restrict__ out, Dims3 dout, int N, int nchunks, int tiles_x,
+               int tiles_y, long long out_bs, long long bias_bs, int accumulate,
+               int* __restrict__ err) {
   constexpr uint32_t kABytes = kBM * CK * 2;
   const uint32_t b_bytes = (uint32_t)N * CK * 2;
   const uint32_t stage_bytes = kABytes + b_bytes;
@@ -156,8 +172,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__
   const int x0 = (tile % tiles_x) * kBX;
   const int y0 = ((tile / tiles_x) % tiles_y) * kBY;
   const int z0 = (tile / (tiles_x * tiles_y)) * kBZ;
-  const int T = K * K * K, pad = (K - 1) / 2;
-  const int ksteps = T * nchunks;
+  const TapClass& cls = plan.cls[blockIdx.y];
+  const int ksteps = cls.n * nchunks;
   const uint32_t tmem_cols = N <= 32 ? 32u : N <= 64 ? 64u : N <= 128 ? 128u : 256u;
 
   if (threadIdx.x == 0) {
@@ -188,14 +204,13 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__
         atomicOr(err, kErrProducer);
         break;
       }
-      const int t = k / nchunks, c = k % nchunks;
-      const int kz = t / (K * K), ky = (t / K) % K, kx = t % K;
+      const int j = k / nchunks, c = k % nchunks;
       const uint32_t a_dst = smem_u32(smem + (size_t)s * stage_bytes);
       const uint32_t fb = smem_u32(&full_bar[s]);
       mbar_expect_tx(fb, stage_bytes);
-      tma_load_5d(a_dst, &tm_a, c * CK, x0 * S + kx - pad, y0 * S + ky - pad, z0 * S + kz - pad,
-                  b, fb);
-      tma_load_4d(a_dst + kABytes, &tm_b, c * CK, t, 0, b, fb);
+      tma_load_5d(a_dst, &tm_a, c * CK, x0 * plan.s_in + cls.off[j][0],
+                  y0 * plan.s_in + cls.off[j][1], z0 * plan.s_in + cls.off[j][2], b, fb);
+      tma_load_4d(a_dst + kABytes, &tm_b, c * CK, cls.widx[j], 0, b, fb);
     }
   } else if (warp == 1 && lane == 0) {  // MMA issuer
     const uint32_t idesc = instr_desc(N);
@@ -223,7 +238,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__
   tc_fence_after();
   if (ok) {
     const int m = warp * 32 + lane;  // TMEM lane = tile row = voxel of the box
-    const int ox = x0 + m % kBX, oy = y0 + (m / kBX) % kBY, oz = z0 + m / (kBX * kBY);
+    const int ox = (x0 + m % kBX) * plan.s_out + cls.r[0],
+              oy = (y0 + (m / kBX) % kBY) * plan.s_out + cls.r[1],
+              oz = (z0 + m / (kBX * kBY)) * plan.s_out + cls.r[2];
     const bool inside = ox < dout.x && oy < dout.y && oz < dout.z;
     const long long vox = ((long long)oz * dout.y + oy) * dout.x + ox;
     float* o = out + (long long)b * out_bs + vox * N;
@@ -286,8 +303,8 @@ __device__ __forceinline__ uint32_t instr_desc_mn(int n) {
 template <int CKA, int CKB>
 __global__ void __launch_bounds__(128, 1)
 wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant__ CUtensorMap tm_x,
-                float* __restrict__ part, Dims3 d, int Co, int Ci, int tg, int tiles_per_chunk,
-                int ntiles, int tiles_x, int tiles_y, int nchunks, int nst,
+                float* __restrict__ part, Dims3 d, int Co, int Ci, int K, int tg,
+                int tiles_per_chunk, int ntiles, int tiles_x, int tiles_y, int nchunks, int nst,
                 int* __restrict__ err) {
   constexpr int KT = kBM;                       // voxels per K tile (8 x 4 x 4 box)
   const int ablocks = Co / CKA;                 // A boxes per tap
@@ -304,8 +321,9 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant
   __shared__ uint32_t tmem_base_s;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int chunk = blockIdx.x, grp = blockIdx.y, b = blockIdx.z;
+  const int T = K * K * K, pad = (K - 1) / 2, centre = T / 2;
   const int t0 = grp * tg;
-  const int ntap = 27 - t0 < tg ? 27 - t0 : tg;
+  const int ntap = T - t0 < tg ? T - t0 : tg;
   const int tile0 = chunk * tiles_per_chunk;
   const int tile1 = tile0 + tiles_per_chunk < ntiles ? tile0 + tiles_per_chunk : ntiles;
   const int ksteps = tile1 - tile0;
@@ -353,10 +371,10 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant
       const uint32_t fb = smem_u32(&full_bar[s]);
       mbar_expect_tx(fb, tx_bytes);
       for (int q = 0; q < ntap; ++q) {
-        const int t = t0 + q, kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
+        const int t = t0 + q, kz = t / (K * K), ky = (t / K) % K, kx = t % K;
         for (int a = 0; a < ablocks; ++a)
           tma_load_5d(base + (uint32_t)(q * ablocks + a) * a_box, &tm_dy, a * CKA,
-                      x0 - (kx - 1), y0 - (ky - 1), z0 - (kz - 1), b, fb);
+                      x0 - (kx - pad), y0 - (ky - pad), z0 - (kz - pad), b, fb);
       }
       for (int c = 0; c < Ci / CKB; ++c)
         tma_load_5d(base + a_bytes + (uint32_t)c * b_box, &tm_x, c * CKB, x0, y0, z0, b, fb);
@@ -390,9 +408,9 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant
   const int m = warp * 32 + lane;       // TMEM lane = A row = (tap in group, co)
   const int q = m / Co, co = m % Co;
   const int t = t0 + q;
-  const long long row = (long long)Co * 27 * Ci + Co;
+  const long long row = (long long)Co * T * Ci + Co;
   float* prow = part + ((long long)b * nchunks + chunk) * row;
-  float* out = prow + ((long long)co * 27 + t) * Ci;
+  float* out = prow + ((long long)co * T + t) * Ci;
   for (int c0 = 0; c0 < Ci; c0 += 16) {
     uint32_t r[16];
     if (ok) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
@@ -404,7 +422,7 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant
   {  // column Ci: sum of the row's dy over the chunk; the centre tap's is the bias partial
     uint32_t r[16];
     if (ok) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)Ci, r);
-    if (q < ntap && t == 13) prow[(long long)Co * 27 * Ci + co] = ok ? __uint_as_float(r[0]) : 0.f;
+    if (q < ntap && t == centre) prow[(long long)Co * T * Ci + co] = ok ? __uint_as_float(r[0]) : 0.f;
   }
   tc_fence_before();
   __syncthreads();
@@ -515,26 +533,75 @@ cudaError_t encode_w(CUtensorMap* m, void* base, int B, long long wstride, int c
 
 size_t smem_bytes(int ck, int n) { return (size_t)kStages * (kBM + n) * ck * 2 + 1024; }
 
-cudaError_t launch_tc(const CUtensorMap& a, const CUtensorMap& w, int cin, const float* bias,
-                      float* out, Dims3 dout, int n, int K, int S, int B, long long out_bs,
-                      long long bias_bs, int acc, int* err, cudaStream_t st) {
+// Forward (and stride-1 data-gradient) taps: offset k - pad, weight tap t, stride S.
+TapPlan conv_plan(int K, int S) {
+  TapPlan p{};
+  p.s_in = S;
+  p.s_out = 1;
+  TapClass& c = p.cls[0];
+  const int pad = (K - 1) / 2;
+  c.n = K * K * K;
+  for (int t = 0; t < c.n; ++t) {
+    c.off[t][0] = (int8_t)(t % K - pad);
+    c.off[t][1] = (int8_t)((t / K) % K - pad);
+    c.off[t][2] = (int8_t)(t / (K * K) - pad);
+    c.widx[t] = (uint8_t)t;
+  }
+  return p;
+}
+
+// Stride-2 3x3x3 data gradient as 8 parity classes on the coarse grid.  Per axis, an even
+// input position 2q takes tap k = 1 from dy[q]; an odd one 2q + 1 takes k = 0 from dy[q + 1]
+// and k = 2 from dy[q].  The weights are the tap-reversed copy (index 26 - t).
+TapPlan dgrad_s2_plan() {
+  TapPlan p{};
+  p.s_in = 1;
+  p.s_out = 2;
+  const int ks[2][2] = {{1, -1}, {0, 2}}, ds[2][2] = {{0, 0}, {1, 0}}, nk[2] = {1, 2};
+  for (int cl = 0; cl < 8; ++cl) {
+    const int rx = cl & 1, ry = (cl >> 1) & 1, rz = (cl >> 2) & 1;
+    TapClass& c = p.cls[cl];
+    c.r[0] = (int8_t)rx;
+    c.r[1] = (int8_t)ry;
+    c.r[2] = (int8_t)rz;
+    c.n = 0;
+    for (int a = 0; a < nk[rz]; ++a)
+      for (int bb = 0; bb < nk[ry]; ++bb)
+        for (int e = 0; e < nk[rx]; ++e) {
+          const int kz = ks[rz][a], ky = ks[ry][bb], kx = ks[rx][e];
+          const int t = (kz * 3 + ky) * 3 + kx;
+          c.off[c.n][0] = (int8_t)ds[rx][e];
+          c.off[c.n][1] = (int8_t)ds[ry][bb];
+          c.off[c.n][2] = (int8_t)ds[rz][a];
+          c.widx[c.n] = (uint8_t)(26 - t);
+          ++c.n;
+        }
+  }
+  return p;
+}
+
+// qdims: extent of the tile grid (output voxels for s_out = 1, coarse positions for 2).
+cudaError_t launch_tc(const CUtensorMap& a, const CUtensorMap& w, const TapPlan& plan,
+                      int nclass, int cin, const float* bias, float* out, Dims3 dout,
+                      Dims3 qdims, int n, int B, long long out_bs, long long bias_bs, int acc,
+                      int* err, cudaStream_t st) {
   const int ck = chunk_for(cin);
-  const int tx = (int)ceil_div(dout.x, kBX), ty = (int)ceil_div(dout.y, kBY),
-            tz = (int)ceil_div(dout.z, kBZ);
-  dim3 grid((unsigned)(tx * ty * tz), 1, B);
+  const int tx = (int)ceil_div(qdims.x, kBX), ty = (int)ceil_div(qdims.y, kBY),
+            tz = (int)ceil_div(qdims.z, kBZ);
+  dim3 grid((unsigned)(tx * ty * tz), nclass, B);
   const size_t sm = smem_bytes(ck, n);
   const int nch = cin / ck;
   switch (ck) {
     case 64:
-      conv_tc_kernel<64><<<grid, 128, sm, st>>>(a, w, bias, out, dout, n, K, S, nch, tx, ty,
+      conv_tc_kernel<64><<<grid, 128, sm, st>>>(a, w, plan, bias, out, dout, n, nch, tx, ty,
                                                  out_bs, bias_bs, acc, err);
       break;
     case 32:
-      conv_tc_kernel<32><<<grid, 128, sm, st>>>(a, w, bias, out, dout, n, K, S, nch, tx, ty,
+      conv_tc_kernel<32><<<grid, 128, sm, st>>>(a, w, plan, bias, out, dout, n, nch, tx, ty,
                                                  out_bs, bias_bs, acc, err);
       break;
     default:
-      conv_tc_kernel<16><<<grid, 128, sm, st>>>(a, w, bias, out, dout, n, K, S, nch, tx, ty,
+      conv_tc_kernel<16><<<grid, 128, sm, st>>>(a, w, plan, bias, out, dout, n, nch, tx, ty,
                                                  out_bs, bias_bs, acc, err);
       break;
   }
@@ -563,8 +630,8 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
   L.din = din;
   L.dout = conv_out_dims(din, k, s);
   L.w_off = w_off;
-  L.dgrad = (s == 1) && bf16_conv_supported(co, ci, k);
-  L.wgrad = s == 1 && k == 3 && co <= 128 && 128 % co == 0 && ci + chunk_for(ci) <= 256;
+  L.dgrad = (s == 1 || k == 3) && bf16_conv_supported(co, ci, k);
+  L.wgrad = s == 1 && co <= 128 && 128 % co == 0 && ci + chunk_for(ci) <= 256;
   const long long n = (long long)co * k * k * k * ci;
   L.wf_off = bf.wstride;
   bf.wstride += (n + 63) / 64 * 64;
@@ -621,8 +688,9 @@ WgPlan wgrad_plan(const TcLayer& L, int B) {
   p.tiles_x = (int)ceil_div(L.dout.x, kBX);
   p.tiles_y = (int)ceil_div(L.dout.y, kBY);
   p.ntiles = p.tiles_x * p.tiles_y * (int)ceil_div(L.dout.z, kBZ);
-  p.tg = kBM / L.co;
-  p.groups = (int)ceil_div(27, p.tg);
+  const int T = L.k * L.k * L.k;
+  p.tg = std::min(kBM / L.co, T);
+  p.groups = (int)ceil_div(T, p.tg);
   const long long want = std::max(1LL, ceil_div(2 * 152, (long long)p.groups * B));
   const int chunks0 = (int)std::min<long long>(p.ntiles, want);
   p.tiles_per_chunk = (int)ceil_div(p.ntiles, chunks0);
@@ -645,7 +713,7 @@ template <int CKA, int CKB>
 void launch_wgrad_tc(dim3 grid, size_t smem, const TcLayer& L, float* part, const WgPlan& p,
                      int* err, cudaStream_t st) {
   wgrad_tc_kernel<CKA, CKB><<<grid, 128, smem, st>>>(
-      L.act_wy, L.act_f, part, L.dout, L.co, L.ci, p.tg, p.tiles_per_chunk, p.ntiles,
+      L.act_wy, L.act_f, part, L.dout, L.co, L.ci, L.k, p.tg, p.tiles_per_chunk, p.ntiles,
       p.tiles_x, p.tiles_y, p.chunks, p.nst, err);
 }
 
@@ -724,7 +792,8 @@ cudaError_t bf16_conv_fwd(Bf16Net& bf, int layer, const float* x, const float* b
   const TcLayer& L = bf.layers[layer];
   cudaError_t e = stage_bf16(x, bf.xbf, (long long)B * L.din.count() * L.ci, stream);
   if (e != cudaSuccess) return e;
-  return launch_tc(L.act_f, L.w_f, L.ci, bias, y, L.dout, L.co, L.k, L.s, B,
+  const TapPlan plan = conv_plan(L.k, L.s);
+  return launch_tc(L.act_f, L.w_f, plan, 1, L.ci, bias, y, L.dout, L.dout, L.co, B,
                    L.dout.count() * L.co, bias_bs, 0, bf.err, stream);
 }
 
@@ -734,8 +803,13 @@ cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, 
   if (!L.dgrad) return cudaErrorInvalidValue;
   cudaError_t e = stage_bf16(dy, bf.xbf, (long long)B * L.dout.count() * L.co, stream);
   if (e != cudaSuccess) return e;
-  return launch_tc(L.act_d, L.w_d, L.co, nullptr, dx, L.din, L.ci, L.k, 1, B,
-                   L.din.count() * L.ci, 0, accumulate, bf.err, stream);
+  if (L.s == 2) {
+    const Dims3 q{(L.din.z + 1) / 2, (L.din.y + 1) / 2, (L.din.x + 1) / 2};
+    return launch_tc(L.act_d, L.w_d, dgrad_s2_plan(), 8, L.co, nullptr, dx, L.din, q, L.ci, B,
+                     L.din.count() * L.ci, 0, accumulate, bf.err, stream);
+  }
+  return launch_tc(L.act_d, L.w_d, conv_plan(L.k, 1), 1, L.co, nullptr, dx, L.din, L.din, L.ci,
+                   B, L.din.count() * L.ci, 0, accumulate, bf.err, stream);
 }
 
 long long bf16_op_workspace(int B, Dims3 din, int ci, int co, int k, int s) {
@@ -769,22 +843,22 @@ cudaError_t bf16_op_conv(bool dgrad, const float* in, const float* W, const floa
                : bf16_conv_fwd(bf, idx, in, bias, out, B, w_bs, st);
 }
 
-long long bf16_op_wgrad_workspace(int B, Dims3 din, int ci, int co) {
+long long bf16_op_wgrad_workspace(int B, Dims3 din, int ci, int co, int k) {
   Bf16Net bf;
-  const int idx = bf16_add_layer(bf, ci, co, 3, 1, din, 0);
+  const int idx = bf16_add_layer(bf, ci, co, k, 1, din, 0);
   if (idx < 0 || !bf.layers[idx].wgrad) return -1;
   const long long rows = bf16_wgrad_chunks(bf, idx, B);
-  return bf16_op_workspace(B, din, ci, co, 3, 1) +
-         (long long)B * rows * ((long long)co * 27 * ci + co) * 4 + 1024;
+  return bf16_op_workspace(B, din, ci, co, k, 1) +
+         (long long)B * rows * ((long long)co * k * k * k * ci + co) * 4 + 1024;
 }
 
 cudaError_t bf16_op_wgrad(const float* x, const float* dy, float* dWb, int B, Dims3 din, int ci,
-                          int co, long long dw_bs, int accumulate, void* workspace,
+                          int co, int k, long long dw_bs, int accumulate, void* workspace,
                           cudaStream_t st) {
   cudaError_t e = bf16_prepare_kernels();
   if (e != cudaSuccess) return e;
   Bf16Net bf;
-  const int idx = bf16_add_layer(bf, ci, co, 3, 1, din, 0);
+  const int idx = bf16_add_layer(bf, ci, co, k, 1, din, 0);
   if (idx < 0 || !bf.layers[idx].wgrad) return cudaErrorInvalidValue;
   size_t used = 0;
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(workspace) + 1023) &
@@ -795,7 +869,7 @@ cudaError_t bf16_op_wgrad(const float* x, const float* dy, float* dWb, int B, Di
   if (e == cudaSuccess) e = cudaMemsetAsync(bf.err, 0, sizeof(int), st);
   if (e == cudaSuccess) e = bf16_conv_wgrad(bf, idx, x, dy, part, B, st);
   if (e != cudaSuccess) return e;
-  const long long row = (long long)co * 27 * ci + co;
+  const long long row = (long long)co * k * k * k * ci + co;
   return reduce_rows_f32(part, dWb, B, bf16_wgrad_chunks(bf, idx, B), row, dw_bs, accumulate, st);
 }
 

@@ -70,9 +70,9 @@ cudaError_t bf16_op_conv(bool dgrad, const float* in, const float* W, const floa
                          float* out, int B, Dims3 din, int ci, int co, int k, int s,
                          long long w_bs, int accumulate, void* workspace, cudaStream_t st);
 
-long long bf16_op_wgrad_workspace(int B, Dims3 din, int ci, int co);
+long long bf16_op_wgrad_workspace(int B, Dims3 din, int ci, int co, int k);
 cudaError_t bf16_op_wgrad(const float* x, const float* dy, float* dWb, int B, Dims3 din, int ci,
-                          int co, long long dw_bs, int accumulate, void* workspace,
+                          int co, int k, long long dw_bs, int accumulate, void* workspace,
                           cudaStream_t st);
 
 }  // namespace d2ip

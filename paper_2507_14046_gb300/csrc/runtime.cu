@@ -230,8 +230,15 @@ struct Carve {
   }
 };
 
+// Weight gradients of 3x3x3 layers use the tensor cores; 1x1x1 ones stay on the SIMT kernel,
+// which is faster there (only Co of the 128 MMA rows would carry work while the A tile still
+// takes 32 KB of shared memory per stage, leaving one CTA per SM).
+bool tc_wgrad(const d2ip_ctx* c, const ConvL& L) {
+  return L.tc >= 0 && L.k == 3 && c->bf.layers[L.tc].wgrad;
+}
+
 long long wgrad_rows(const d2ip_ctx* c, const ConvL& L) {
-  if (L.tc >= 0 && c->bf.layers[L.tc].wgrad) return bf16_wgrad_chunks(c->bf, L.tc, c->B);
+  if (tc_wgrad(c, L)) return bf16_wgrad_chunks(c->bf, L.tc, c->B);
   return conv3d_wgrad_chunks(L.din, L.k, L.s);
 }
 
@@ -425,7 +432,7 @@ struct Launcher {
   }
   void conv_wgrad(const ConvL& L, const float* x, const float* dy) {
     beg(D2IP_KCLASS_CONV_WGRAD, conv_flops(L));
-    if (L.tc >= 0 && c->bf.layers[L.tc].wgrad)
+    if (tc_wgrad(c, L))
       ok(bf16_conv_wgrad(c->bf, L.tc, x, dy, c->ws, c->B, c->stream));
     else
       ok(conv3d_wgrad_partial_f32(x, dy, c->ws, c->B, L.din, L.ci, L.co, L.k, L.s,
@@ -1212,10 +1219,10 @@ static d2ip_status tc_op(bool dgrad, const float* in, const float* W, const floa
                          long long ws_bytes, void* stream) {
   if (!in || !W || !out || !ws) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
   if (bad_conv(batch, dz, dy, dx, ci, co, ksize, stride) || !bf16_conv_supported(ci, co, ksize) ||
-      (dgrad && (stride != 1 || !bf16_conv_supported(co, ci, ksize))))
+      (dgrad && !bf16_conv_supported(co, ci, ksize)))
     return fail(nullptr, D2IP_ERR_BAD_SHAPE,
-                "tensor-core convolution needs ci, co multiples of 16 (co <= 256); data "
-                "gradient stride 1 only");
+                "tensor-core convolution needs ci, co multiples of 16 (both <= 256 for the data "
+                "gradient, co <= 256 for the forward)");
   if (ws_bytes < d2ip_conv3d_tc_workspace(batch, dz, dy, dx, ci, co, ksize, stride))
     return fail(nullptr, D2IP_ERR_BAD_ARG, "workspace too small");
   const long long blk = (long long)co * ksize * ksize * ksize * ci + co;
@@ -1241,25 +1248,25 @@ d2ip_status d2ip_conv3d_dgrad_tc(const float* dyp, const float* W, float* dxp, i
                accumulate, ws, ws_bytes, stream);
 }
 
-long long d2ip_conv3d_wgrad_tc_workspace(int batch, int dz, int dy, int dx, int ci, int co) {
-  if (bad_conv(batch, dz, dy, dx, ci, co, 3, 1) || !bf16_conv_supported(ci, co, 3) || co > 128 ||
-      128 % co != 0)
+long long d2ip_conv3d_wgrad_tc_workspace(int batch, int dz, int dy, int dx, int ci, int co,
+                                         int ksize) {
+  if (bad_conv(batch, dz, dy, dx, ci, co, ksize, 1) || !bf16_conv_supported(ci, co, ksize))
     return -1;
-  return bf16_op_wgrad_workspace(batch, Dims3{dz, dy, dx}, ci, co);
+  return bf16_op_wgrad_workspace(batch, Dims3{dz, dy, dx}, ci, co, ksize);
 }
 
 d2ip_status d2ip_conv3d_wgrad_tc(const float* x, const float* dyp, float* dWb, int batch, int dz,
-                                 int dy, int dx, int ci, int co, long long dw_bs, int accumulate,
-                                 void* ws, long long ws_bytes, void* stream) {
+                                 int dy, int dx, int ci, int co, int ksize, long long dw_bs,
+                                 int accumulate, void* ws, long long ws_bytes, void* stream) {
   if (!x || !dyp || !dWb || !ws) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
-  const long long need = d2ip_conv3d_wgrad_tc_workspace(batch, dz, dy, dx, ci, co);
+  const long long need = d2ip_conv3d_wgrad_tc_workspace(batch, dz, dy, dx, ci, co, ksize);
   if (need < 0)
     return fail(nullptr, D2IP_ERR_BAD_SHAPE,
-                "tensor-core weight gradient: 3x3x3 stride 1, ci and co multiples of 16, co "
-                "dividing 128");
+                "tensor-core weight gradient: stride 1, ci and co multiples of 16, co dividing "
+                "128, ci + min(64, ci) <= 256");
   if (ws_bytes < need) return fail(nullptr, D2IP_ERR_BAD_ARG, "workspace too small");
-  const long long row = (long long)co * 27 * ci + co;
-  OPCK(bf16_op_wgrad(x, dyp, dWb, batch, Dims3{dz, dy, dx}, ci, co, dw_bs ? dw_bs : row,
+  const long long row = (long long)co * ksize * ksize * ksize * ci + co;
+  OPCK(bf16_op_wgrad(x, dyp, dWb, batch, Dims3{dz, dy, dx}, ci, co, ksize, dw_bs ? dw_bs : row,
                      accumulate, ws, (cudaStream_t)stream));
   return D2IP_OK;
 }

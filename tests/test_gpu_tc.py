@@ -33,7 +33,8 @@ def _err_word(ws):
 
 TC_CASES = [((16, 8, 8), 16, 16, 3, 1), ((7, 9, 11), 32, 16, 3, 1), ((4, 8, 8), 64, 64, 3, 1),
             ((6, 9, 5), 16, 32, 3, 2), ((16, 16, 8), 48, 16, 3, 1), ((8, 8, 8), 96, 32, 1, 1),
-            ((8, 16, 16), 128, 128, 3, 1), ((5, 6, 7), 192, 64, 3, 1), ((8, 8, 8), 64, 128, 3, 2)]
+            ((8, 16, 16), 128, 128, 3, 1), ((5, 6, 7), 192, 64, 3, 1), ((8, 8, 8), 64, 128, 3, 2),
+            ((16, 32, 32), 16, 32, 3, 2), ((9, 7, 11), 32, 64, 3, 2)]
 
 
 @pytest.mark.parametrize("din,ci,co,k,s", TC_CASES)
@@ -60,7 +61,7 @@ def test_tc_conv_forward_and_dgrad(d2ip, din, ci, co, k, s):
     errs = [rel(y[b].cpu().numpy(), ref[b]) for b in range(B)]
     print("tc forward rel err", errs)
     assert max(errs) < TOL
-    if s != 1:
+    if k == 1 and s != 1:
         return
     dy = bf16_round(rng.standard_normal((B, *dout, co)).astype(np.float32))
     dx = torch.zeros_like(xd)
@@ -77,30 +78,32 @@ def test_tc_conv_forward_and_dgrad(d2ip, din, ci, co, k, s):
 def test_tc_rejects_unsupported_shapes(d2ip):
     assert d2ip.d2ip_conv3d_tc_workspace(1, 4, 4, 4, 8, 16, 3, 1) == -1
     with pytest.raises(d2ip.D2IPError) as e:
-        d2ip.d2ip_conv3d_dgrad_tc(1, 1, 1, 1, 4, 4, 4, 16, 16, 3, 2, 0, 0, 1, 1 << 20, None)
+        d2ip.d2ip_conv3d_dgrad_tc(1, 1, 1, 1, 4, 4, 4, 16, 24, 3, 1, 0, 0, 1, 1 << 20, None)
     assert e.value.status == -2
 
 
-WG_CASES = [((16, 8, 8), 16, 16), ((7, 9, 11), 32, 16), ((4, 8, 8), 64, 64), ((16, 16, 8), 48, 16),
-            ((8, 16, 16), 16, 32), ((5, 6, 7), 192, 64), ((8, 8, 8), 128, 128), ((6, 5, 9), 96, 32)]
+WG_CASES = [((16, 8, 8), 16, 16, 3), ((7, 9, 11), 32, 16, 3), ((4, 8, 8), 64, 64, 3),
+            ((16, 16, 8), 48, 16, 3), ((8, 16, 16), 16, 32, 3), ((5, 6, 7), 192, 64, 3),
+            ((8, 8, 8), 128, 128, 3), ((6, 5, 9), 96, 32, 3), ((9, 7, 11), 48, 16, 1),
+            ((8, 8, 8), 96, 32, 1), ((4, 8, 16), 192, 64, 1)]
 
 
-@pytest.mark.parametrize("din,ci,co", WG_CASES)
-def test_tc_weight_gradient(d2ip, din, ci, co):
-    rng = np.random.default_rng(ci * 7 + co)
+@pytest.mark.parametrize("din,ci,co,k", WG_CASES)
+def test_tc_weight_gradient(d2ip, din, ci, co, k):
+    rng = np.random.default_rng(ci * 7 + co + k)
     B = 2
     stream = torch.cuda.current_stream().cuda_stream
     x = bf16_round(rng.standard_normal((B, *din, ci)).astype(np.float32))
     dy = bf16_round(rng.standard_normal((B, *din, co)).astype(np.float32))
-    nw = co * 27 * ci
-    wsb = d2ip.d2ip_conv3d_wgrad_tc_workspace(B, *din, ci, co)
+    nw = co * k ** 3 * ci
+    wsb = d2ip.d2ip_conv3d_wgrad_tc_workspace(B, *din, ci, co, k)
     ws = torch.zeros(wsb, dtype=torch.uint8, device="cuda")
     out = torch.full((B, nw + co), float("nan"), device="cuda")
-    d2ip.d2ip_conv3d_wgrad_tc(_dev(x), _dev(dy), out, B, *din, ci, co, nw + co, 0, ws, wsb,
+    d2ip.d2ip_conv3d_wgrad_tc(_dev(x), _dev(dy), out, B, *din, ci, co, k, nw + co, 0, ws, wsb,
                               stream)
     torch.cuda.synchronize()
     assert _err_word(ws) == 0
-    W0 = np.zeros((co, 3, 3, 3, ci))
+    W0 = np.zeros((co, k, k, k, ci))
     for b in range(B):
         _, gW, gb = onet.conv3d_backward(x[b].astype(np.float64), W0, 1, dy[b].astype(np.float64))
         o = out[b].cpu().numpy()
