@@ -48,7 +48,8 @@ typedef int d2ip_status;
 #define D2IP_ERR_STATE (-7)     /* call out of order (e.g. fit before d2ip_load_J)        */
 
 #define D2IP_FP32 0 /* convolutions and J products in FP32 (SIMT), FP32 accumulation      */
-#define D2IP_BF16 1 /* convolutions on tcgen05 tensor cores, BF16 x BF16 -> FP32            */
+#define D2IP_BF16 1 /* convolutions on tcgen05 tensor cores and J products from a BF16 copy
+                       of J, FP32 accumulation; J column norms and the residual stay FP64    */
 
 /* parameter-table kinds */
 #define D2IP_PARAM_CONV_W 0
@@ -103,6 +104,16 @@ d2ip_status d2ip_set_input(d2ip_ctx* ctx, const float* Z, const float* theta0);
 /* Adam hyperparameters (Sec. III-A; defaults lr 1e-3, 0.9, 0.999, 1e-8).  Given in double:
  * (1 - beta) is formed in double before rounding to the float the kernels use. */
 d2ip_status d2ip_set_optim(d2ip_ctx* ctx, double lr, double beta1, double beta2, double eps);
+/* 4D-TV regulariser of Sec. III-E added to the data term (Eq. 13): lambda_tv * (lambda_s *
+ * R_spatial + lambda_t * R_temporal); the paper uses 0.002, 1 and 0.1 (Sec. IV-D).  R_spatial
+ * = (1/V) sum_voxels sqrt(dx^2 + dy^2 + dz^2 + eps) with forward differences (0 past the far
+ * face); R_temporal = (1/sum a) sum_j a_j sum_voxels sqrt((s - s_j)^2 + eps) over the earlier
+ * frames j of the sequence, a_j = exp(-(i - j)).  lambda_tv = 0 (the default) turns it off.
+ * d2ip_fit_sequence/batched keep the earlier outputs on the device; d2ip_fit_frame and
+ * d2ip_run_steps see no earlier frame (spatial term only).  The loss trace includes it;
+ * residual_out stays the data term alone. */
+d2ip_status d2ip_set_regularizer(d2ip_ctx* ctx, double lambda_tv, double lambda_s,
+                                 double lambda_t, double eps);
 /* Zero the Adam moments and step count (done at the start of every fitted frame). */
 d2ip_status d2ip_reset_optimizer(d2ip_ctx* ctx);
 
@@ -298,6 +309,14 @@ d2ip_status d2ip_sensitivity_residual(const float* J, const float* x, const floa
 /* g[b] = scale * J^T r[b]  (scale = 2/m gives the gradient of the mean-square data term). */
 d2ip_status d2ip_sensitivity_adjoint(const float* J, const float* r, float* g, float scale,
                                      int batch, int m, int n, void* stream);
+/* The 4D-TV regulariser alone: grad[b] += its gradient at dsigma[b] ([batch][n]) given
+ * n_previous earlier outputs previous[b][j][n]; value_host[b] (host, may be NULL) receives
+ * its value (a synchronising copy).  Workspace: d2ip_tv4d_workspace bytes (device). */
+long long d2ip_tv4d_workspace(int batch, int dz, int dy, int dx);
+d2ip_status d2ip_tv4d(const float* dsigma, const float* previous, int n_previous, float* grad,
+                      double* value_host, int batch, int dz, int dy, int dx, double lambda_tv,
+                      double lambda_s, double lambda_t, double eps, void* workspace,
+                      long long workspace_bytes, void* stream);
 /* In place: J[:, j] /= |J[:, j]|_2 with the norm in FP64; colnorm[j] receives it. */
 d2ip_status d2ip_normalize_columns(float* J, double* colnorm, int m, int n, void* stream);
 /* One Adam step (bias-corrected, step number t >= 1) over `count` parameters. */

@@ -47,6 +47,7 @@ _SIGS = {
     "d2ip_set_input": [_vp, _vp, _vp],
     "d2ip_set_optim": [_vp, _d, _d, _d, _d],
     "d2ip_reset_optimizer": [_vp],
+    "d2ip_set_regularizer": [_vp, _d, _d, _d, _d],
     "d2ip_run_steps": [_vp, _vp, _i, _vp],
     "d2ip_forward": [_vp, _vp],
     "d2ip_get_grad": [_vp, _vp],
@@ -78,6 +79,7 @@ _SIGS = {
     "d2ip_sensitivity_residual": [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _vp, _ll, _vp],
     "d2ip_sensitivity_adjoint": [_vp, _vp, _vp, _f, _i, _i, _i, _vp],
     "d2ip_normalize_columns": [_vp, _vp, _i, _i, _vp],
+    "d2ip_tv4d": [_vp, _vp, _i, _vp, _vp, _i, _i, _i, _i, _d, _d, _d, _d, _vp, _ll, _vp],
     "d2ip_adam_update": [_vp, _vp, _vp, _vp, _ll, _d, _d, _d, _d, _i, _vp],
 }
 _SIZE_FNS = {
@@ -86,6 +88,7 @@ _SIZE_FNS = {
     "d2ip_conv3d_wgrad_tc_workspace": [_i] * 7,
     "d2ip_layernorm_workspace": [_i, _ll, _i],
     "d2ip_sensitivity_workspace": [_i, _i, _i],
+    "d2ip_tv4d_workspace": [_i, _i, _i, _i],
 }
 
 for _name, _args in _SIGS.items():
@@ -199,12 +202,17 @@ def d2ip_sensitivity_workspace(*args) -> int:
     return int(_lib.d2ip_sensitivity_workspace(*args))
 
 
+def d2ip_tv4d_workspace(*args) -> int:
+    return int(_lib.d2ip_tv4d_workspace(*args))
+
+
 def d2ip_layernorm_workspace(*args) -> int:
     return int(_lib.d2ip_layernorm_workspace(*args))
 
 
 for _name in ("d2ip_set_grid", "d2ip_load_J", "d2ip_get_colnorms", "d2ip_set_input",
-              "d2ip_set_optim", "d2ip_reset_optimizer", "d2ip_run_steps", "d2ip_forward",
+              "d2ip_set_optim", "d2ip_set_regularizer", "d2ip_reset_optimizer",
+              "d2ip_run_steps", "d2ip_forward",
               "d2ip_get_grad", "d2ip_fit_frame", "d2ip_fit_sequence", "d2ip_set_state",
               "d2ip_err_ratio", "d2ip_sync", "d2ip_profile_iterations"):
     globals()[_name] = _wrap_ctx(_name)
@@ -214,6 +222,7 @@ for _name in ("d2ip_conv3d_forward", "d2ip_conv3d_dgrad", "d2ip_conv3d_wgrad",
               "d2ip_layernorm_act_forward", "d2ip_layernorm_act_backward",
               "d2ip_upsample_concat_forward", "d2ip_upsample_concat_backward",
               "d2ip_sensitivity_residual", "d2ip_sensitivity_adjoint", "d2ip_normalize_columns",
+              "d2ip_tv4d",
               "d2ip_adam_update"):
     globals()[_name] = _wrap_op(_name)
 
@@ -268,6 +277,10 @@ class Context:
 
     def set_optim(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         d2ip_set_optim(self.handle, float(lr), float(beta1), float(beta2), float(eps))
+
+    def set_regularizer(self, lambda_tv=0.002, lambda_s=1.0, lambda_t=0.1, eps=1e-8):
+        d2ip_set_regularizer(self.handle, float(lambda_tv), float(lambda_s), float(lambda_t),
+                             float(eps))
 
     def run_steps(self, dV, n_steps, trace=False):
         tr = np.zeros((n_steps, self.batch), dtype=np.float64) if trace else None

@@ -77,6 +77,13 @@ int jmul_chunks(int n);
 cudaError_t jmul_residual_f32(const float* J, const float* x, const float* dv, float* r,
                               float* part, int B, int m, int n, long long x_bs,
                               cudaStream_t stream);
+// The same products reading a BF16 copy of J (FP32 accumulation).
+cudaError_t jmul_residual_bf16(const __nv_bfloat16* J, const float* x, const float* dv, float* r,
+                               float* part, int B, int m, int n, long long x_bs,
+                               cudaStream_t stream);
+cudaError_t jtmul_bf16(const __nv_bfloat16* J, const float* r, float* g, float scale, int B,
+                       int m, int n, long long g_bs, cudaStream_t stream);
+cudaError_t convert_bf16(const float* x, __nv_bfloat16* y, long long n, cudaStream_t stream);
 // Per-device kernel attributes (opt-in shared memory); call once per device before launches.
 cudaError_t prepare_pointwise_kernels();
 cudaError_t jtmul_f32(const float* J, const float* r, float* g, float scale, int B, int m,
@@ -84,9 +91,18 @@ cudaError_t jtmul_f32(const float* J, const float* r, float* g, float scale, int
 // loss[b] = (1/m) sum r^2 (FP64); optional trace ring (slot trace_pos % trace_cap, then
 // trace_pos += 1); optional Adam step counter bump; status bit 1 set when a loss is not
 // finite.
+// reg_part (optional): [B][reg_blocks] regulariser partial sums added to each loss.
 cudaError_t residual_loss_f64(const float* r, double* loss, double* trace, int* trace_pos,
                               int trace_cap, int* adam_t, int* status, int B, int m,
-                              cudaStream_t stream);
+                              cudaStream_t stream, const double* reg_part = nullptr,
+                              int reg_blocks = 0);
+// 4D-TV value (per-block FP64 partials [B][tv4d_blocks]) and gradient added into g; hist holds
+// the previous outputs [B][frames][n] (batch stride hist_bs), *nprev_dev of them in use.
+int tv4d_blocks(long long n);
+cudaError_t set_device_int(int* p, int v, cudaStream_t stream);  // graph-capturable store
+cudaError_t tv4d_f32(const float* ds, const float* hist, const int* nprev_dev, float* g,
+                     double* part, int B, Dims3 d, long long hist_bs, float lam_s, float lam_t,
+                     float eps, cudaStream_t stream);
 cudaError_t normalize_columns_f64(float* J, double* colnorm, int m, int n,
                                   cudaStream_t stream);
 cudaError_t err_ratio_f64(const float* est, const float* truth, double* out, int B,

@@ -292,8 +292,22 @@ constexpr int kJtmulMaxSmem = 200 * 1024;
 constexpr int kJRows = 4;
 constexpr int kJCols = 1024;
 
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float4 load4(const float* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+__device__ __forceinline__ float4 load4(const __nv_bfloat16* p) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&u.x);
+  const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&u.y);
+  const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+  return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
+template <typename JT>
 __global__ void __launch_bounds__(256)
-jmul_part_kernel(const float* __restrict__ J, const float* __restrict__ x,
+jmul_part_kernel(const JT* __restrict__ J, const float* __restrict__ x,
                  float* __restrict__ part, int B, int m, int n, long long x_bs) {
   __shared__ float red[8][kJRows * kJB];
   const int chunk = blockIdx.x;
@@ -316,7 +330,7 @@ jmul_part_kernel(const float* __restrict__ J, const float* __restrict__ x,
 #pragma unroll
     for (int r = 0; r < kJRows; ++r) {
       if (r >= nr) break;
-      const float4 a = *reinterpret_cast<const float4*>(J + (long long)(i0 + r) * n + j);
+      const float4 a = load4(J + (long long)(i0 + r) * n + j);
 #pragma unroll
       for (int q = 0; q < kJB; ++q)
         acc[r][q] = fmaf(a.x, xv[q].x, fmaf(a.y, xv[q].y, fmaf(a.z, xv[q].z,
@@ -325,7 +339,7 @@ jmul_part_kernel(const float* __restrict__ J, const float* __restrict__ x,
   } else {
     for (int jj = j; jj < j + 4 && jj < n; ++jj)
       for (int r = 0; r < nr; ++r) {
-        const float a = J[(long long)(i0 + r) * n + jj];
+        const float a = to_f32(J[(long long)(i0 + r) * n + jj]);
         for (int q = 0; q < nb; ++q) acc[r][q] = fmaf(a, x[(long long)(b0 + q) * x_bs + jj], acc[r][q]);
       }
   }
@@ -358,8 +372,9 @@ __global__ void jmul_final_kernel(const float* __restrict__ part, const float* _
   r[e] = s - dv[e];
 }
 
+template <typename JT>
 __global__ void __launch_bounds__(256)
-jtmul_kernel(const float* __restrict__ J, const float* __restrict__ r, float* __restrict__ g,
+jtmul_kernel(const JT* __restrict__ J, const float* __restrict__ r, float* __restrict__ g,
              float scale, int B, int m, int n, long long g_bs) {
   extern __shared__ float rs[];  // [kJB][m]
   const int b0 = blockIdx.y * kJB;
@@ -372,7 +387,7 @@ jtmul_kernel(const float* __restrict__ J, const float* __restrict__ r, float* __
 #pragma unroll
   for (int q = 0; q < kJB; ++q) acc[q] = 0.f;
   for (int i = 0; i < m; ++i) {
-    const float a = J[(long long)i * n + j];
+    const float a = to_f32(J[(long long)i * n + j]);
 #pragma unroll
     for (int q = 0; q < kJB; ++q)
       if (q < nb) acc[q] = fmaf(a, rs[q * m + i], acc[q]);
@@ -383,7 +398,8 @@ jtmul_kernel(const float* __restrict__ J, const float* __restrict__ r, float* __
 __global__ void __launch_bounds__(256)
 loss_kernel(const float* __restrict__ r, double* __restrict__ loss, double* __restrict__ trace,
             int* __restrict__ trace_pos, int trace_cap, int* __restrict__ adam_t,
-            int* __restrict__ status, int B, int m) {
+            int* __restrict__ status, int B, int m, const double* __restrict__ reg_part,
+            int reg_blocks) {
   __shared__ double red[256];
   const int pos = trace_pos ? *trace_pos : 0;
   const int slot = trace_cap > 0 ? pos % trace_cap : 0;
@@ -401,7 +417,9 @@ loss_kernel(const float* __restrict__ r, double* __restrict__ loss, double* __re
       __syncthreads();
     }
     if (threadIdx.x == 0) {
-      const double L = red[0] / (double)m;
+      double L = red[0] / (double)m;
+      if (reg_part)
+        for (int k = 0; k < reg_blocks; ++k) L += reg_part[(long long)b * reg_blocks + k];
       loss[b] = L;
       if (trace) trace[(long long)slot * B + b] = L;
       if (!isfinite(L)) bad = true;
@@ -413,6 +431,78 @@ loss_kernel(const float* __restrict__ r, double* __restrict__ loss, double* __re
     if (adam_t) *adam_t += 1;
     if (bad && status) *status |= 1;
   }
+}
+
+// 4D-TV regulariser (Sec. III-E).  Per voxel v of frame i (previous outputs h_0..h_{i-1}):
+//   spatial  (1/V) sqrt(d_x^2 + d_y^2 + d_z^2 + eps), forward differences, 0 past the far face;
+//   temporal (1/sum a) sum_j a_j sqrt((s - h_j)^2 + eps), a_j = exp(-(i - j)).
+// g[v] += lam_s' dR_s/ds[v] + lam_t' dR_t/ds[v] with lam_s' = lam*lam_s, lam_t' = lam*lam_t;
+// part[b][block] = the block's share of lam_s' R_s + lam_t' R_t (FP64, fixed order).
+__device__ __forceinline__ float tv_mag(const float* s, int x, int y, int z, Dims3 d, float eps,
+                                        float* dxo, float* dyo, float* dzo) {
+  const long long v = ((long long)z * d.y + y) * d.x + x;
+  const float c = s[v];
+  const float dx = x + 1 < d.x ? s[v + 1] - c : 0.f;
+  const float dy = y + 1 < d.y ? s[v + d.x] - c : 0.f;
+  const float dz = z + 1 < d.z ? s[v + (long long)d.x * d.y] - c : 0.f;
+  *dxo = dx;
+  *dyo = dy;
+  *dzo = dz;
+  return sqrtf(dx * dx + dy * dy + dz * dz + eps);
+}
+
+// d mag(u) / d s[u + e_axis] = (its forward difference along axis) / mag(u).
+__device__ __forceinline__ float bx_over(const float* s, int x, int y, int z, Dims3 d, float eps,
+                                         int axis) {
+  float dx, dy, dz;
+  const float m = tv_mag(s, x, y, z, d, eps, &dx, &dy, &dz);
+  return (axis == 0 ? dx : axis == 1 ? dy : dz) / m;
+}
+
+__global__ void __launch_bounds__(256)
+tv4d_kernel(const float* __restrict__ ds, const float* __restrict__ hist,
+            const int* __restrict__ nprev_dev, float* __restrict__ g, double* __restrict__ part,
+            Dims3 d, long long hist_bs, float lam_s, float lam_t, float eps) {
+  __shared__ double red[256];
+  const int b = blockIdx.y;
+  const long long n = d.count();
+  const float* s = ds + (long long)b * n;
+  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double val = 0.0;
+  if (v < n) {
+    const int x = (int)(v % d.x), y = (int)((v / d.x) % d.y), z = (int)(v / ((long long)d.x * d.y));
+    float ax, ay, az;
+    const float mag = tv_mag(s, x, y, z, d, eps, &ax, &ay, &az);
+    float grad = -(ax + ay + az) / mag;  // d mag(v) / d s[v]
+    // the backward neighbours' magnitudes also contain s[v]
+    if (x > 0) grad += bx_over(s, x - 1, y, z, d, eps, 0);
+    if (y > 0) grad += bx_over(s, x, y - 1, z, d, eps, 1);
+    if (z > 0) grad += bx_over(s, x, y, z - 1, d, eps, 2);
+    float gt = 0.f, vt = 0.f;
+    const int np = nprev_dev ? *nprev_dev : 0;
+    if (np > 0) {
+      float asum = 0.f;
+      for (int j = 0; j < np; ++j) {
+        const float a = expf(-(float)(np - j));
+        const float diff = s[v] - hist[(long long)b * hist_bs + (long long)j * n + v];
+        const float q = sqrtf(diff * diff + eps);
+        asum += a;
+        vt += a * q;
+        gt += a * diff / q;
+      }
+      gt /= asum;
+      vt /= asum;
+    }
+    g[(long long)b * n + v] += lam_s * grad + lam_t * gt;
+    val = (double)lam_s * mag + (double)lam_t * vt;
+  }
+  red[threadIdx.x] = val;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(long long)b * gridDim.x + blockIdx.x] = red[0];
 }
 
 __global__ void colnorm_kernel(float* __restrict__ J, double* __restrict__ cn, int m, int n) {
@@ -479,6 +569,24 @@ adam_kernel(float* __restrict__ theta, const float* __restrict__ g, float* __res
 }
 
 }  // namespace
+
+int tv4d_blocks(long long n) { return (int)ceil_div(n, 256); }
+
+__global__ void set_int_kernel(int* p, int v) { *p = v; }
+
+cudaError_t set_device_int(int* p, int v, cudaStream_t stream) {
+  set_int_kernel<<<1, 1, 0, stream>>>(p, v);
+  return cudaGetLastError();
+}
+
+cudaError_t tv4d_f32(const float* ds, const float* hist, const int* nprev_dev, float* g,
+                     double* part, int B, Dims3 d, long long hist_bs, float lam_s, float lam_t,
+                     float eps, cudaStream_t stream) {
+  dim3 grid((unsigned)tv4d_blocks(d.count()), B);
+  tv4d_kernel<<<grid, 256, 0, stream>>>(ds, hist, nprev_dev, g, part, d, hist_bs, lam_s, lam_t,
+                                        eps);
+  return cudaGetLastError();
+}
 
 int layernorm_bwd_blocks(long long nvox, int C) {
   const int gp = lanes_for(C);
@@ -558,12 +666,12 @@ cudaError_t add_inplace_f32(float* y, const float* x, long long count, cudaStrea
 
 int jmul_chunks(int n) { return (int)ceil_div(n, kJCols); }
 
-cudaError_t jmul_residual_f32(const float* J, const float* x, const float* dv, float* r,
-                              float* part, int B, int m, int n, long long x_bs,
-                              cudaStream_t stream) {
+template <typename JT>
+cudaError_t jmul_impl(const JT* J, const float* x, const float* dv, float* r, float* part, int B,
+                      int m, int n, long long x_bs, cudaStream_t stream) {
   const int nch = jmul_chunks(n);
   dim3 grid(nch, (unsigned)ceil_div(m, kJRows), (unsigned)ceil_div(B, kJB));
-  jmul_part_kernel<<<grid, 256, 0, stream>>>(J, x, part, B, m, n, x_bs);
+  jmul_part_kernel<JT><<<grid, 256, 0, stream>>>(J, x, part, B, m, n, x_bs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   jmul_final_kernel<<<(unsigned)ceil_div((long long)B * m, 256), 256, 0, stream>>>(part, dv, r, B,
@@ -571,25 +679,62 @@ cudaError_t jmul_residual_f32(const float* J, const float* x, const float* dv, f
   return cudaGetLastError();
 }
 
-cudaError_t jtmul_f32(const float* J, const float* r, float* g, float scale, int B, int m,
-                      int n, long long g_bs, cudaStream_t stream) {
+cudaError_t jmul_residual_f32(const float* J, const float* x, const float* dv, float* r,
+                              float* part, int B, int m, int n, long long x_bs,
+                              cudaStream_t stream) {
+  return jmul_impl(J, x, dv, r, part, B, m, n, x_bs, stream);
+}
+
+cudaError_t jmul_residual_bf16(const __nv_bfloat16* J, const float* x, const float* dv, float* r,
+                               float* part, int B, int m, int n, long long x_bs,
+                               cudaStream_t stream) {
+  return jmul_impl(J, x, dv, r, part, B, m, n, x_bs, stream);
+}
+
+template <typename JT>
+cudaError_t jtmul_impl(const JT* J, const float* r, float* g, float scale, int B, int m, int n,
+                       long long g_bs, cudaStream_t stream) {
   const size_t smem = (size_t)kJB * m * sizeof(float);
   if (smem > (size_t)kJtmulMaxSmem) return cudaErrorInvalidValue;
   dim3 grid((unsigned)ceil_div(n, 256), (unsigned)ceil_div(B, kJB));
-  jtmul_kernel<<<grid, 256, smem, stream>>>(J, r, g, scale, B, m, n, g_bs);
+  jtmul_kernel<JT><<<grid, 256, smem, stream>>>(J, r, g, scale, B, m, n, g_bs);
+  return cudaGetLastError();
+}
+
+cudaError_t jtmul_f32(const float* J, const float* r, float* g, float scale, int B, int m,
+                      int n, long long g_bs, cudaStream_t stream) {
+  return jtmul_impl(J, r, g, scale, B, m, n, g_bs, stream);
+}
+
+cudaError_t jtmul_bf16(const __nv_bfloat16* J, const float* r, float* g, float scale, int B,
+                       int m, int n, long long g_bs, cudaStream_t stream) {
+  return jtmul_impl(J, r, g, scale, B, m, n, g_bs, stream);
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ y,
+                               long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = __float2bfloat16_rn(x[i]);
+}
+
+cudaError_t convert_bf16(const float* x, __nv_bfloat16* y, long long n, cudaStream_t stream) {
+  to_bf16_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, stream>>>(x, y, n);
   return cudaGetLastError();
 }
 
 cudaError_t prepare_pointwise_kernels() {
-  return cudaFuncSetAttribute(jtmul_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kJtmulMaxSmem);
+  cudaError_t e = cudaFuncSetAttribute(jtmul_kernel<float>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kJtmulMaxSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(jtmul_kernel<__nv_bfloat16>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, kJtmulMaxSmem);
 }
 
 cudaError_t residual_loss_f64(const float* r, double* loss, double* trace, int* trace_pos,
                               int trace_cap, int* adam_t, int* status, int B, int m,
-                              cudaStream_t stream) {
+                              cudaStream_t stream, const double* reg_part, int reg_blocks) {
   loss_kernel<<<1, 256, 0, stream>>>(r, loss, trace, trace_pos, trace_cap, adam_t, status, B,
-                                     m);
+                                     m, reg_part, reg_blocks);
   return cudaGetLastError();
 }
 

@@ -74,6 +74,8 @@ struct d2ip_ctx {
   int m = 0;
   bool j_ready = false, input_ready = false;
   double lr = 1e-3, beta1 = 0.9, beta2 = 0.999, eps = 1e-8;
+  // 4D-TV regulariser (off when lam_tv == 0)
+  double lam_tv = 0.0, lam_s = 1.0, lam_t = 0.1, tv_eps = 1e-8;
 
   // plan
   std::vector<Dims3> dims;
@@ -93,8 +95,12 @@ struct d2ip_ctx {
   float *zin = nullptr, *dsigma = nullptr, *r = nullptr, *gds = nullptr, *dv = nullptr;
   float *ztmp = nullptr, *ptmp = nullptr, *ws = nullptr, *stage = nullptr;
   double *loss = nullptr, *resid = nullptr, *trace = nullptr, *seq_resid = nullptr;
-  int *trace_pos = nullptr, *adam_t = nullptr, *status = nullptr;
+  int *trace_pos = nullptr, *adam_t = nullptr, *status = nullptr, *nprev = nullptr;
+  double* reg_part = nullptr;  // [B][tv4d_blocks] regulariser partial sums
+  float* hist = nullptr;       // previous frames' outputs [B][hist_cap][n]
+  int hist_cap = 0;
   float* J = nullptr;
+  __nv_bfloat16* Jbf = nullptr;  // BF16 copy of the normalised J (BF16 precision)
   float* jpart = nullptr;  // column-chunk partial sums of J x
   double* colnorm = nullptr;
   size_t j_bytes = 0;
@@ -334,6 +340,8 @@ void layout_buffers(d2ip_ctx* c, Carve& cv) {
   c->trace_pos = cv.take<int>(1);
   c->adam_t = cv.take<int>(1);
   c->status = cv.take<int>(1);
+  c->nprev = cv.take<int>(1);
+  c->reg_part = cv.take<double>((long long)B * tv4d_blocks(nv(0)));
   if (c->precision == D2IP_BF16) {
     long long max_act = 0;
     for (int l = 0; l < c->L; ++l)
@@ -496,25 +504,44 @@ struct Launcher {
   }
   void data_term(bool training) {
     const long long n = c->n();
-    const double jb = 4.0 * c->m * (double)n, vb = 4.0 * c->B * ((double)n + 2.0 * c->m);
+    const bool jb16 = c->precision == D2IP_BF16;
+    const double jb = (jb16 ? 2.0 : 4.0) * c->m * (double)n,
+                 vb = 4.0 * c->B * ((double)n + 2.0 * c->m);
     beg(D2IP_KCLASS_JMUL, jb + vb);
-    ok(jmul_residual_f32(c->J, c->dsigma, c->dv, c->r, c->jpart, c->B, c->m, (int)n, n,
-                         c->stream));
+    if (jb16)
+      ok(jmul_residual_bf16(c->Jbf, c->dsigma, c->dv, c->r, c->jpart, c->B, c->m, (int)n, n,
+                            c->stream));
+    else
+      ok(jmul_residual_f32(c->J, c->dsigma, c->dv, c->r, c->jpart, c->B, c->m, (int)n, n,
+                           c->stream));
     fin();
+    if (training) {
+      beg(D2IP_KCLASS_JTMUL, jb + vb);
+      if (jb16)
+        ok(jtmul_bf16(c->Jbf, c->r, c->gds, 2.0f / (float)c->m, c->B, c->m, (int)n, n,
+                      c->stream));
+      else
+        ok(jtmul_f32(c->J, c->r, c->gds, 2.0f / (float)c->m, c->B, c->m, (int)n, n, c->stream));
+      fin();
+    }
+    const bool reg = training && c->lam_tv != 0.0;
+    if (reg) {  // 4D-TV (Sec. III-E): value into the loss, gradient into dL/d dsigma
+      beg(D2IP_KCLASS_MISC, 4.0 * c->B * (double)n * 8);
+      ok(tv4d_f32(c->dsigma, c->hist, c->nprev, c->gds, c->reg_part, c->B, c->dims[0],
+                  (long long)c->hist_cap * n, (float)(c->lam_tv * c->lam_s / (double)n),
+                  (float)(c->lam_tv * c->lam_t), (float)c->tv_eps, c->stream));
+      fin();
+    }
     beg(D2IP_KCLASS_LOSS, 4.0 * c->B * c->m);
     if (training) {
       ok(residual_loss_f64(c->r, c->loss, c->trace, c->trace_pos, kTraceCap, c->adam_t,
-                           c->status, c->B, c->m, c->stream));
+                           c->status, c->B, c->m, c->stream, reg ? c->reg_part : nullptr,
+                           reg ? tv4d_blocks(n) : 0));
     } else {
       ok(residual_loss_f64(c->r, c->resid, nullptr, nullptr, 0, nullptr, c->status, c->B, c->m,
                            c->stream));
     }
     fin();
-    if (training) {
-      beg(D2IP_KCLASS_JTMUL, jb + vb);
-      ok(jtmul_f32(c->J, c->r, c->gds, 2.0f / (float)c->m, c->B, c->m, (int)n, n, c->stream));
-      fin();
-    }
   }
   // dout: gradient of R.out; writes dx (gradient of R.x)
   void res_bwd(Res& R, const float* dout, float* dx) {
@@ -671,7 +698,7 @@ namespace {
 
 // One context's sequence as a list of operations, issued a few graph launches at a time.
 struct SeqOp {
-  enum Kind { kStage, kReset, kSteps, kEval, kResiduals } kind;
+  enum Kind { kStage, kReset, kSteps, kEval, kResiduals, kPrev, kSave } kind;
   int arg;                 // frame index (kStage: -1 = the UPWS frame), step count
 };
 
@@ -696,6 +723,8 @@ SeqJob make_sequence_job(d2ip_ctx* c, const float* V, int T, const float* dV0, i
   j.dV0 = dV0;
   j.Sigma = Sigma;
   j.resid = resid;
+  const bool reg = c->lam_tv != 0.0;
+  if (reg) j.ops.push_back({SeqOp::kPrev, 0});
   if (upws > 0) {  // UPWS (Eqs. 5-7): N_0 steps on one frame from the initial weights
     j.ops.push_back({SeqOp::kStage, -1});
     j.ops.push_back({SeqOp::kReset, 0});
@@ -706,6 +735,10 @@ SeqJob make_sequence_job(d2ip_ctx* c, const float* V, int T, const float* dV0, i
     j.ops.push_back({SeqOp::kReset, 0});
     j.ops.push_back({SeqOp::kSteps, i == 0 ? first : later});
     j.ops.push_back({SeqOp::kEval, i});
+    if (reg) {  // the temporal term of frame i + 1 sees frames 0..i
+      j.ops.push_back({SeqOp::kSave, i});
+      j.ops.push_back({SeqOp::kPrev, i + 1});
+    }
   }
   j.ops.push_back({SeqOp::kResiduals, 0});
   return j;
@@ -747,6 +780,13 @@ d2ip_status issue(SeqJob& j, int budget) {
         CK(cudaMemcpy2DAsync(c->seq_resid + op.arg, sizeof(double) * j.T, c->resid,
                              sizeof(double), sizeof(double), c->B, cudaMemcpyDeviceToDevice,
                              c->stream));
+        break;
+      case SeqOp::kPrev:
+        CK(set_device_int(c->nprev, op.arg, c->stream));
+        break;
+      case SeqOp::kSave:
+        CK(copy_rows(c->hist + (long long)op.arg * n, (long long)c->hist_cap * n, c->dsigma, n,
+                     n, c->B, sizeof(float), c->stream));
         break;
       case SeqOp::kResiduals:
         if (j.resid)
@@ -814,7 +854,9 @@ d2ip_status d2ip_destroy(d2ip_ctx* c) {
   if (c->r) cudaFree(c->r);
   if (c->dv) cudaFree(c->dv);
   if (c->jpart) cudaFree(c->jpart);
+  if (c->Jbf) cudaFree(c->Jbf);
   if (c->seq_resid) cudaFree(c->seq_resid);
+  if (c->hist) cudaFree(c->hist);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return D2IP_OK;
@@ -897,6 +939,8 @@ d2ip_status d2ip_load_J(d2ip_ctx* c, const float* J, int m, int n, int normalize
     if (c->r) cudaFree(c->r);
     if (c->dv) cudaFree(c->dv);
     if (c->jpart) cudaFree(c->jpart);
+    if (c->Jbf) cudaFree(c->Jbf);
+    c->Jbf = nullptr;
     c->J = nullptr;
     c->colnorm = nullptr;
     c->r = c->dv = c->jpart = nullptr;
@@ -905,7 +949,9 @@ d2ip_status d2ip_load_J(d2ip_ctx* c, const float* J, int m, int n, int normalize
         cudaMalloc(&c->colnorm, sizeof(double) * n) != cudaSuccess ||
         cudaMalloc(&c->r, sizeof(float) * m * c->B) != cudaSuccess ||
         cudaMalloc(&c->dv, sizeof(float) * m * c->B) != cudaSuccess ||
-        cudaMalloc(&c->jpart, sizeof(float) * jmul_chunks(n) * (size_t)m * c->B) != cudaSuccess)
+        cudaMalloc(&c->jpart, sizeof(float) * jmul_chunks(n) * (size_t)m * c->B) != cudaSuccess ||
+        (c->precision == D2IP_BF16 &&
+         cudaMalloc(&c->Jbf, sizeof(__nv_bfloat16) * (size_t)m * n) != cudaSuccess))
       return fail(c, D2IP_ERR_OOM, "device allocation of J failed");
     c->j_bytes = bytes;
     c->m = m;
@@ -916,6 +962,7 @@ d2ip_status d2ip_load_J(d2ip_ctx* c, const float* J, int m, int n, int normalize
   } else {
     CK(cudaMemsetAsync(c->colnorm, 0, sizeof(double) * n, c->stream));
   }
+  if (c->precision == D2IP_BF16) CK(convert_bf16(c->J, c->Jbf, (long long)m * n, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->j_ready = true;
   return D2IP_OK;
@@ -956,6 +1003,19 @@ d2ip_status d2ip_set_optim(d2ip_ctx* c, double lr, double beta1, double beta2, d
   c->beta1 = beta1;
   c->beta2 = beta2;
   c->eps = eps;
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_set_regularizer(d2ip_ctx* c, double lambda_tv, double lambda_s,
+                                 double lambda_t, double eps) {
+  if (!c) return fail(nullptr, D2IP_ERR_BAD_ARG, "null context");
+  if (!(lambda_tv >= 0.0) || !(lambda_s >= 0.0) || !(lambda_t >= 0.0) || !(eps > 0.0))
+    return fail(c, D2IP_ERR_BAD_ARG, "need lambdas >= 0 and eps > 0");
+  drop_graphs(c);
+  c->lam_tv = lambda_tv;
+  c->lam_s = lambda_s;
+  c->lam_t = lambda_t;
+  c->tv_eps = eps;
   return D2IP_OK;
 }
 
@@ -1011,6 +1071,7 @@ d2ip_status d2ip_fit_frame(d2ip_ctx* c, const float* dV, int n_steps, float* dsi
   if (s) return s;
   s = reset_optimizer(c);
   if (s) return s;
+  if (c->lam_tv != 0.0) CK(set_device_int(c->nprev, 0, c->stream));  // no earlier frames
   s = run_steps(c, n_steps, loss_trace);
   if (s) return s;
   CK(cudaGraphLaunch(c->g_eval, c->stream));
@@ -1053,6 +1114,17 @@ d2ip_status d2ip_fit_batched(d2ip_ctx* const* ctxs, int count, const float* cons
       if (cudaMalloc(&c->seq_resid, sizeof(double) * T * c->B) != cudaSuccess)
         return fail(c, D2IP_ERR_OOM, "residual buffer allocation failed");
       c->seq_T_cap = T;
+    }
+    if (c->lam_tv != 0.0 && T > c->hist_cap) {
+      if (c->hist) cudaFree(c->hist);
+      c->hist = nullptr;
+      c->hist_cap = 0;
+      drop_graphs(c);  // the step graph holds the history's address and stride
+      if (cudaMalloc(&c->hist, sizeof(float) * (size_t)T * c->B * c->n()) != cudaSuccess)
+        return fail(c, D2IP_ERR_OOM, "frame history allocation failed");
+      c->hist_cap = T;
+      s = ready(c);
+      if (s) return s;
     }
     jobs[i] = make_sequence_job(c, V[i], T, dV0 ? dV0[i] : nullptr, upws_steps, first_steps,
                                 later_steps, Sigma_out ? Sigma_out[i] : nullptr,
@@ -1390,6 +1462,44 @@ d2ip_status d2ip_sensitivity_adjoint(const float* J, const float* r, float* g, f
     return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad J shape (m <= 6400)");
   OPCK(prepare_pointwise_kernels());
   OPCK(jtmul_f32(J, r, g, scale, batch, m, n, n, (cudaStream_t)stream));
+  return D2IP_OK;
+}
+
+long long d2ip_tv4d_workspace(int batch, int dz, int dy, int dx) {
+  if (batch < 1 || dz < 1 || dy < 1 || dx < 1) return -1;
+  return 256 + (long long)sizeof(double) * batch * tv4d_blocks((long long)dz * dy * dx);
+}
+
+d2ip_status d2ip_tv4d(const float* dsigma, const float* previous, int n_previous, float* grad,
+                      double* value_host, int batch, int dz, int dy, int dx, double lambda_tv,
+                      double lambda_s, double lambda_t, double eps, void* workspace,
+                      long long workspace_bytes, void* stream) {
+  if (!dsigma || !grad || !workspace || (n_previous > 0 && !previous))
+    return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
+  if (batch < 1 || dz < 1 || dy < 1 || dx < 1 || n_previous < 0 || !(eps > 0.0))
+    return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad 4D-TV arguments");
+  if (workspace_bytes < d2ip_tv4d_workspace(batch, dz, dy, dx))
+    return fail(nullptr, D2IP_ERR_BAD_ARG, "workspace too small");
+  const Dims3 d{dz, dy, dx};
+  const long long n = d.count();
+  int* np = static_cast<int*>(workspace);
+  double* part = reinterpret_cast<double*>(static_cast<char*>(workspace) + 256);
+  const cudaStream_t st = (cudaStream_t)stream;
+  OPCK(set_device_int(np, n_previous, st));
+  OPCK(tv4d_f32(dsigma, previous, np, grad, part, batch, d, (long long)n_previous * n,
+                (float)(lambda_tv * lambda_s / (double)n), (float)(lambda_tv * lambda_t),
+                (float)eps, st));
+  if (value_host) {
+    const int nb = tv4d_blocks(n);
+    std::vector<double> h((size_t)batch * nb);
+    OPCK(cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
+    OPCK(cudaStreamSynchronize(st));
+    for (int b = 0; b < batch; ++b) {
+      double v = 0.0;
+      for (int k = 0; k < nb; ++k) v += h[(size_t)b * nb + k];
+      value_host[b] = v;
+    }
+  }
   return D2IP_OK;
 }
 
