@@ -210,7 +210,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__
       mbar_expect_tx(fb, stage_bytes);
       tma_load_5d(a_dst, &tm_a, c * CK, x0 * plan.s_in + cls.off[j][0],
                   y0 * plan.s_in + cls.off[j][1], z0 * plan.s_in + cls.off[j][2], b, fb);
-      tma_load_4d(a_dst + kABytes, &tm_b, c * CK, cls.widx[j], 0, b, fb);
+      tma_load_4d(a_dst + kABytes, &tm_b, c * CK, 0, cls.widx[j], b, fb);
     }
   } else if (warp == 1 && lane == 0) {  // MMA issuer
     const uint32_t idesc = instr_desc(N);
@@ -252,6 +252,135 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           float v = __uint_as_float(r[j]) + (bb ? bb[c0 + j] : 0.f);
+          o[c0 + j] = accumulate ? o[c0 + j] + v : v;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(tmem_cols)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// 3x3x3 stride-1 convolution with halo boxes.  Tile = 8 x 16 x 1 output voxels (row m =
+// y * 8 + x).  Per stage (channel chunk, x tap kx) one TMA box of 8 x 18 x 3 voxels holds the
+// input shifted by kx - 1 in x with a one-voxel halo in y and z; the nine (ky, kz) taps are
+// windows of it that start (kz * 18 + ky) * 8 rows in -- whole swizzle atoms, so each is an
+// ordinary K-major operand.  The stage's B box holds the nine taps t = kx + 3 q (TMA element
+// stride 3 along the tap axis of the tap-major weights).  Three boxes per channel chunk
+// replace the per-tap kernel's 27.
+// ------------------------------------------------------------------------------------
+constexpr int kH3Rows = 8 * 18 * 3;  // rows of one halo box
+constexpr int kT3Max = 4;            // pipeline stages (at most)
+
+template <int CK>
+__global__ void __launch_bounds__(128, 1)
+conv_tc3_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
+                const float* __restrict__ bias, float* __restrict__ out, Dims3 dout, int N,
+                int nchunks, int tiles_x, int tiles_y, long long out_bs, long long bias_bs,
+                int accumulate, int nst, int* __restrict__ err) {
+  constexpr uint32_t kABytes = kH3Rows * CK * 2;
+  constexpr uint32_t kRowB = CK * 2;
+  const uint32_t b_tap = (uint32_t)N * CK * 2;
+  const uint32_t stage_bytes = kABytes + 9 * b_tap;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[kT3Max], empty_bar[kT3Max], done_bar;
+  __shared__ uint32_t tmem_base_s;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int b = blockIdx.z;
+  const int tile = blockIdx.x;
+  const int x0 = (tile % tiles_x) * 8;
+  const int y0 = ((tile / tiles_x) % tiles_y) * 16;
+  const int z0 = tile / (tiles_x * tiles_y);
+  const int ksteps = nchunks * 3;
+  const uint32_t tmem_cols = N <= 32 ? 32u : N <= 64 ? 64u : N <= 128 ? 128u : 256u;
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < nst; ++q) {
+      mbar_init(smem_u32(&full_bar[q]), 1);
+      mbar_init(smem_u32(&empty_bar[q]), 1);
+    }
+    mbar_init(smem_u32(&done_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_s)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  if (warp == 0 && lane == 0) {  // TMA producer
+    for (int k = 0; k < ksteps; ++k) {
+      const int st = k % nst, round = k / nst;
+      if (round > 0 && !mbar_wait(smem_u32(&empty_bar[st]), (round - 1) & 1)) {
+        atomicOr(err, kErrProducer);
+        break;
+      }
+      const int c = k / 3, kx = k % 3;
+      const uint32_t dst = smem_u32(smem + (size_t)st * stage_bytes);
+      const uint32_t fb = smem_u32(&full_bar[st]);
+      mbar_expect_tx(fb, stage_bytes);
+      tma_load_5d(dst, &tm_a, c * CK, x0 + kx - 1, y0 - 1, z0 - 1, b, fb);
+      tma_load_4d(dst + kABytes, &tm_b, c * CK, 0, kx, b, fb);
+    }
+  } else if (warp == 1 && lane == 0) {  // MMA issuer
+    const uint32_t idesc = instr_desc(N);
+    for (int k = 0; k < ksteps; ++k) {
+      const int st = k % nst;
+      if (!mbar_wait(smem_u32(&full_bar[st]), (k / nst) & 1)) {
+        atomicOr(err, kErrMma);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a_addr = smem_u32(smem + (size_t)st * stage_bytes);
+      const uint32_t b_addr = a_addr + kABytes;
+#pragma unroll 1
+      for (int q = 0; q < 9; ++q) {  // tap t = kx + 3 q: kz = q / 3, ky = q % 3
+        const uint32_t a_win = a_addr + (uint32_t)(((q / 3) * 18 + (q % 3)) * 8) * kRowB;
+        const uint32_t b_win = b_addr + (uint32_t)q * b_tap;
+#pragma unroll
+        for (int kk = 0; kk < CK / 16; ++kk)
+          mma_bf16(tmem, smem_desc<CK>(a_win + kk * 32), smem_desc<CK>(b_win + kk * 32), idesc,
+                   (k > 0 || q > 0 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(smem_u32(&empty_bar[st]));
+    }
+    mma_commit(smem_u32(&done_bar));
+  }
+  __syncwarp();
+
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&done_bar), 0));
+  if (!ok && lane == 0) atomicOr(err, kErrEpilogue);
+  tc_fence_after();
+  if (ok) {
+    const int m = warp * 32 + lane;
+    const int ox = x0 + m % 8, oy = y0 + m / 8, oz = z0;
+    const bool inside = ox < dout.x && oy < dout.y && oz < dout.z;
+    const long long vox = ((long long)oz * dout.y + oy) * dout.x + ox;
+    float* o = out + (long long)b * out_bs + vox * N;
+    const float* bb = bias ? bias + (long long)b * bias_bs : nullptr;
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+      if (inside) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float v = __uint_as_float(r[j]) + (bb ? bb[c0 + j] : 0.f);
           o[c0 + j] = accumulate ? o[c0 + j] + v : v;
         }
       }
@@ -450,8 +579,8 @@ __global__ void f32_to_bf16_kernel(const float* __restrict__ x, __nv_bfloat16* _
   }
 }
 
-// Forward weights [co][t][ci] and data-gradient weights [ci][T-1-t][co] of one layer, for
-// every problem of the batch.
+// Forward weights [t][co][ci] and data-gradient weights [T-1-t][ci][co] of one layer (tap
+// major), for every problem of the batch.
 __global__ void weights_bf16_kernel(const float* __restrict__ theta, __nv_bfloat16* __restrict__ wb,
                                     long long Pp, long long wstride, long long w_off,
                                     long long wf_off, long long wd_off, int ci, int co, int T,
@@ -460,16 +589,14 @@ __global__ void weights_bf16_kernel(const float* __restrict__ theta, __nv_bfloat
   const long long n = (long long)co * T * ci;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
-  const float v = theta[(long long)b * Pp + w_off + e];
+  const float v = theta[(long long)b * Pp + w_off + e];  // W[o][t][c]
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
   __nv_bfloat16* base = wb + (long long)b * wstride;
-  base[wf_off + e] = h;
-  if (dgrad) {
-    const int c = (int)(e % ci);
-    const long long r = e / ci;
-    const int t = (int)(r % T), o = (int)(r / T);
-    base[wd_off + ((long long)c * T + (T - 1 - t)) * co + o] = h;
-  }
+  const int c = (int)(e % ci);
+  const long long r = e / ci;
+  const int t = (int)(r % T), o = (int)(r / T);
+  base[wf_off + ((long long)t * co + o) * ci + c] = h;                     // [t][co][ci]
+  if (dgrad) base[wd_off + ((long long)(T - 1 - t) * ci + c) * co + o] = h;  // [26-t][ci][co]
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -515,23 +642,81 @@ cudaError_t encode_act(CUtensorMap* m, void* base, int B, Dims3 d, int C, int ck
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// Weights [B][Cout][T][Cin] (BF16) as a 4-D map (Cin, T, Cout, B), box = one tap's chunk.
+// Tap-major weights [B][T][Cout][Cin] (BF16) as a 4-D map (Cin, Cout, T, B); the box holds
+// one channel chunk of `taps` taps spaced `tap_stride` apart (one tap, or the 9 taps sharing
+// an x offset).
 cudaError_t encode_w(CUtensorMap* m, void* base, int B, long long wstride, int cin, int T,
-                     int cout, int ck) {
+                     int cout, int ck, int taps, int tap_stride) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
-  const cuuint64_t dims[4] = {(cuuint64_t)cin, (cuuint64_t)T, (cuuint64_t)cout, (cuuint64_t)B};
-  const cuuint64_t strides[3] = {(cuuint64_t)cin * 2, (cuuint64_t)cin * T * 2,
+  const cuuint64_t dims[4] = {(cuuint64_t)cin, (cuuint64_t)cout, (cuuint64_t)T, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {(cuuint64_t)cin * 2, (cuuint64_t)cin * cout * 2,
                                  (cuuint64_t)wstride * 2};
-  const cuuint32_t box[4] = {(cuuint32_t)ck, 1, (cuuint32_t)cout, 1};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const cuuint32_t box[4] = {(cuuint32_t)ck, (cuuint32_t)cout,
+                             (cuuint32_t)(taps * tap_stride), 1};
+  const cuuint32_t estr[4] = {1, 1, (cuuint32_t)tap_stride, 1};
   const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(ck),
                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// Channels-last activations with an 8 x 18 x 3 box: the x-shifted halo of an 8 x 16 x 1 tile
+// for the three (y, z) offsets of every tap.
+cudaError_t encode_act_halo(CUtensorMap* m, void* base, int B, Dims3 d, int C, int ck) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)d.x, (cuuint64_t)d.y, (cuuint64_t)d.z,
+                              (cuuint64_t)B};
+  const cuuint64_t es = 2;
+  const cuuint64_t strides[4] = {C * es, C * es * d.x, C * es * d.x * d.y,
+                                 C * es * d.x * d.y * d.z};
+  const cuuint32_t box[5] = {(cuuint32_t)ck, 8, 18, 3, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(ck),
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 size_t smem_bytes(int ck, int n) { return (size_t)kStages * (kBM + n) * ck * 2 + 1024; }
+
+size_t tc3_stage(int ck, int n) { return (size_t)kH3Rows * ck * 2 + (size_t)9 * n * ck * 2; }
+
+// Largest channel chunk (64, 32, 16) dividing cin whose halo stage stays within 100 KB.
+int tc3_chunk(int cin, int n) {
+  for (int ck : {64, 32, 16})
+    if (cin % ck == 0 && tc3_stage(ck, n) <= 100 * 1024) return ck;
+  return 0;
+}
+
+constexpr size_t kTc3SmemMax = 210 * 1024;
+
+cudaError_t launch_tc3(const CUtensorMap& a, const CUtensorMap& w, int cin, int ck,
+                       const float* bias, float* out, Dims3 dout, int n, int B, long long out_bs,
+                       long long bias_bs, int acc, int* err, cudaStream_t st) {
+  const int tx = (int)ceil_div(dout.x, 8), ty = (int)ceil_div(dout.y, 16);
+  dim3 grid((unsigned)(tx * ty * dout.z), 1, B);
+  const size_t stage = tc3_stage(ck, n);
+  const int nst = (int)std::min<size_t>(kT3Max, (kTc3SmemMax - 1024) / stage);
+  const size_t sm = (size_t)nst * stage + 1024;
+  const int nch = cin / ck;
+  switch (ck) {
+    case 64:
+      conv_tc3_kernel<64><<<grid, 128, sm, st>>>(a, w, bias, out, dout, n, nch, tx, ty, out_bs,
+                                                  bias_bs, acc, nst, err);
+      break;
+    case 32:
+      conv_tc3_kernel<32><<<grid, 128, sm, st>>>(a, w, bias, out, dout, n, nch, tx, ty, out_bs,
+                                                  bias_bs, acc, nst, err);
+      break;
+    default:
+      conv_tc3_kernel<16><<<grid, 128, sm, st>>>(a, w, bias, out, dout, n, nch, tx, ty, out_bs,
+                                                  bias_bs, acc, nst, err);
+      break;
+  }
+  return cudaGetLastError();
+}
 
 // Forward (and stride-1 data-gradient) taps: offset k - pad, weight tap t, stride S.
 TapPlan conv_plan(int K, int S) {
@@ -631,6 +816,8 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
   L.dout = conv_out_dims(din, k, s);
   L.w_off = w_off;
   L.dgrad = (s == 1 || k == 3) && bf16_conv_supported(co, ci, k);
+  L.ck3f = (k == 3 && s == 1) ? tc3_chunk(ci, co) : 0;
+  L.ck3d = (k == 3 && s == 1 && L.dgrad) ? tc3_chunk(co, ci) : 0;
   L.wgrad = s == 1 && co <= 128 && 128 % co == 0 && ci + chunk_for(ci) <= 256;
   const long long n = (long long)co * k * k * k * ci;
   L.wf_off = bf.wstride;
@@ -661,14 +848,26 @@ cudaError_t bf16_finalize(Bf16Net& bf, int B) {
     const int T = L.k * L.k * L.k;
     cudaError_t e = encode_act(&L.act_f, bf.xbf, B, L.din, L.ci, chunk_for(L.ci), L.s);
     if (e == cudaSuccess)
-      e = encode_w(&L.w_f, bf.wbuf + L.wf_off, B, bf.wstride, L.ci, T, L.co, chunk_for(L.ci));
+      e = encode_w(&L.w_f, bf.wbuf + L.wf_off, B, bf.wstride, L.ci, T, L.co, chunk_for(L.ci), 1,
+                   1);
     if (e == cudaSuccess && L.dgrad) {
       e = encode_act(&L.act_d, bf.xbf, B, L.dout, L.co, chunk_for(L.co), 1);
       if (e == cudaSuccess)
-        e = encode_w(&L.w_d, bf.wbuf + L.wd_off, B, bf.wstride, L.co, T, L.ci, chunk_for(L.co));
+        e = encode_w(&L.w_d, bf.wbuf + L.wd_off, B, bf.wstride, L.co, T, L.ci, chunk_for(L.co), 1,
+                     1);
     }
     if (e == cudaSuccess && L.wgrad)
       e = encode_act(&L.act_wy, bf.ybf, B, L.dout, L.co, chunk_for(L.co), 1);
+    if (e == cudaSuccess && L.ck3f) {
+      e = encode_act_halo(&L.act_f3, bf.xbf, B, L.din, L.ci, L.ck3f);
+      if (e == cudaSuccess)
+        e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, L.ci, T, L.co, L.ck3f, 9, 3);
+    }
+    if (e == cudaSuccess && L.ck3d) {
+      e = encode_act_halo(&L.act_d3, bf.xbf, B, L.dout, L.co, L.ck3d);
+      if (e == cudaSuccess)
+        e = encode_w(&L.w_d3, bf.wbuf + L.wd_off, B, bf.wstride, L.co, T, L.ci, L.ck3d, 9, 3);
+    }
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -755,6 +954,15 @@ cudaError_t bf16_prepare_kernels() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(conv_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes(16, 256));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(conv_tc3_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTc3SmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(conv_tc3_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTc3SmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(conv_tc3_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTc3SmemMax);
   if (e == cudaSuccess) e = wgrad_attr<16, 16>();
   if (e == cudaSuccess) e = wgrad_attr<16, 32>();
   if (e == cudaSuccess) e = wgrad_attr<16, 64>();
@@ -792,6 +1000,9 @@ cudaError_t bf16_conv_fwd(Bf16Net& bf, int layer, const float* x, const float* b
   const TcLayer& L = bf.layers[layer];
   cudaError_t e = stage_bf16(x, bf.xbf, (long long)B * L.din.count() * L.ci, stream);
   if (e != cudaSuccess) return e;
+  if (L.ck3f)
+    return launch_tc3(L.act_f3, L.w_f3, L.ci, L.ck3f, bias, y, L.dout, L.co, B,
+                      L.dout.count() * L.co, bias_bs, 0, bf.err, stream);
   const TapPlan plan = conv_plan(L.k, L.s);
   return launch_tc(L.act_f, L.w_f, plan, 1, L.ci, bias, y, L.dout, L.dout, L.co, B,
                    L.dout.count() * L.co, bias_bs, 0, bf.err, stream);
@@ -808,6 +1019,9 @@ cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, 
     return launch_tc(L.act_d, L.w_d, dgrad_s2_plan(), 8, L.co, nullptr, dx, L.din, q, L.ci, B,
                      L.din.count() * L.ci, 0, accumulate, bf.err, stream);
   }
+  if (L.ck3d)
+    return launch_tc3(L.act_d3, L.w_d3, L.co, L.ck3d, nullptr, dx, L.din, L.ci, B,
+                      L.din.count() * L.ci, 0, accumulate, bf.err, stream);
   return launch_tc(L.act_d, L.w_d, conv_plan(L.k, 1), 1, L.co, nullptr, dx, L.din, L.din, L.ci,
                    B, L.din.count() * L.ci, 0, accumulate, bf.err, stream);
 }

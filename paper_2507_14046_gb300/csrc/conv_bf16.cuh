@@ -18,12 +18,14 @@ struct TcLayer {
   CUtensorMap act_d;  // stride-1 data-gradient input (dy staged in BF16)
   CUtensorMap w_d;    // data-gradient weights [B][Ci][T][Co], taps reversed (BF16)
   CUtensorMap act_wy; // weight-gradient dy (second BF16 staging buffer)
+  CUtensorMap act_f3, w_f3, act_d3, w_d3;  // halo-box forms (3x3x3 stride 1)
   int ci = 0, co = 0, k = 3, s = 1;
   Dims3 din{}, dout{};
   long long w_off = 0;            // weights of this conv in the FP32 theta arena
   long long wf_off = 0, wd_off = 0;  // offsets in the per-problem BF16 weight block
   bool dgrad = false;             // data gradient on the tensor cores too (stride 1)
   bool wgrad = false;             // weight gradient on the tensor cores too (3x3x3, stride 1)
+  int ck3f = 0, ck3d = 0;         // channel chunk of the halo-box kernel (0: per-tap kernel)
 };
 
 // Device buffers of the BF16 path (carved from the context arena) and its layers.

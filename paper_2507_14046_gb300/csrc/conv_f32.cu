@@ -73,39 +73,55 @@ wgrad_brick_kernel(const float* __restrict__ x, const float* __restrict__ dy,
   const long long row = (long long)Co * T * Ci + Co;
   float* out = part + ((long long)b * nbricks + blockIdx.x) * row;
   const int ntask = (t_hi - t_lo) * NG * NG;
-  for (int task = threadIdx.x; task < ntask; task += kWThreads) {
-    const int gi = task % NG;
-    const int r = task / NG;
-    const int go = r % NG;
-    const int t = t_lo + r / NG;
-    const int kz = t / (K * K), ky = (t / K) % K, kx = t % K;
+  // 1x1x1 layers have only 16 tasks per block: 8 threads share one task's voxels and their
+  // 4 x 4 tiles are added in a fixed order through shared memory.  The split depends on the
+  // layer alone, so a problem's sums do not depend on the batch it is fitted in.
+  constexpr int lanes = K == 1 ? kWThreads / 16 : 1;
+  __shared__ float lane_red[K == 1 ? kWThreads : 1][16];
+  for (int base = 0; base < ntask * lanes; base += kWThreads) {  // uniform trip count
+    const int slot = base + threadIdx.x;
+    const int task = slot / lanes, lane = slot % lanes;
+    const bool active = task < ntask;
     float acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    for (int vz = 0; vz < BZ; ++vz)
-      for (int vy = 0; vy < BY; ++vy)
-#pragma unroll 4
-        for (int vx = 0; vx < kWBX; ++vx) {
-          const int v = (vz * BY + vy) * kWBX + vx;
-          const int h = ((vz * S + kz) * HY + (vy * S + ky)) * HX + (vx * S + kx);
-          const float4 g = sdy[v * NG + go];
-          const float4 a = sx[h * NG + gi];
-          const float gg[4] = {g.x, g.y, g.z, g.w}, aa[4] = {a.x, a.y, a.z, a.w};
+    const int gi = task % NG, go = (task / NG) % NG, t = t_lo + task / (NG * NG);
+    if (active) {
+      const int kz = t / (K * K), ky = (t / K) % K, kx = t % K;
+      for (int v = lane; v < BV; v += lanes) {
+        const int vx = v % kWBX, vy = (v / kWBX) % BY, vz = v / (kWBX * BY);
+        const int h = ((vz * S + kz) * HY + (vy * S + ky)) * HX + (vx * S + kx);
+        const float4 g = sdy[v * NG + go];
+        const float4 a = sx[h * NG + gi];
+        const float gg[4] = {g.x, g.y, g.z, g.w}, aa[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(gg[i], aa[j], acc[i][j]);
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(gg[i], aa[j], acc[i][j]);
+      }
+    }
+    if constexpr (lanes > 1) {
+#pragma unroll
+      for (int e = 0; e < 16; ++e) lane_red[threadIdx.x][e] = acc[e / 4][e % 4];
+      __syncthreads();
+      if (active && lane == 0)
+        for (int q = 1; q < lanes; ++q)
+#pragma unroll
+          for (int e = 0; e < 16; ++e) acc[e / 4][e % 4] += lane_red[threadIdx.x + q][e];
+      __syncthreads();
+    }
+    if (active && lane == 0) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int co = co0 + go * 4 + i;
+        if (co >= Co) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int ci = ci0 + gi * 4 + j;
+          if (ci < Ci) out[((long long)co * T + t) * Ci + ci] = acc[i][j];
         }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int co = co0 + go * 4 + i;
-      if (co >= Co) continue;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int ci = ci0 + gi * 4 + j;
-        if (ci < Ci) out[((long long)co * T + t) * Ci + ci] = acc[i][j];
       }
     }
   }
