@@ -210,7 +210,8 @@ d2ip_status d2ip_conv3d_dgrad(const float* dy, const float* W, float* dx, int ba
  * to BF16 (round to nearest even), products accumulate in FP32 in tensor memory; the
  * bias is added in FP32.  Needs ci and co multiples of 16, co <= 256 (ci <= 256 too for the
  * data gradient; its stride-2 form runs as 8 output-parity classes of 1 to 8 taps on the
- * coarse grid).  `workspace` (device, d2ip_conv3d_tc_workspace bytes) receives the
+ * coarse grid).  x (or dy) and y (or dx) must be 16-byte aligned (D2IP_ERR_BAD_ARG
+ * otherwise).  `workspace` (device, d2ip_conv3d_tc_workspace bytes) receives the
  * BF16 staging copies; the int at its first 1024-byte aligned address is an error word,
  * non-zero after the call when a pipeline wait of the kernel gave up (about 1 s). */
 long long d2ip_conv3d_tc_workspace(int batch, int dz, int dy, int dx, int ci, int co,

@@ -268,40 +268,47 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__
 }
 
 // ------------------------------------------------------------------------------------
-// 3x3x3 stride-1 convolution with halo boxes.  Tile = 8 x 16 x 1 output voxels (row m =
-// y * 8 + x).  Per stage (channel chunk, x tap kx) one TMA box of 8 x 18 x 3 voxels holds the
-// input shifted by kx - 1 in x with a one-voxel halo in y and z; the nine (ky, kz) taps are
-// windows of it that start (kz * 18 + ky) * 8 rows in -- whole swizzle atoms, so each is an
-// ordinary K-major operand.  The stage's B box holds the nine taps t = kx + 3 q (TMA element
-// stride 3 along the tap axis of the tap-major weights).  Three boxes per channel chunk
-// replace the per-tap kernel's 27.
+// 3x3x3 stride-1 convolution with halo boxes.  Tile = 8 x 16 x TZ output voxels (TZ = 1, 2
+// or 4 z slices of 128 rows, row m = y * 8 + x).  Per stage (channel chunk, x tap kx) one TMA
+// box of 8 x 18 x (TZ + 2) voxels holds the input shifted by kx - 1 in x with a one-voxel
+// halo in y and z; tap (ky, kz) of slice zz is the window that starts ((zz + kz) * 18 + ky) * 8
+// rows in -- whole swizzle atoms, so each is an ordinary K-major operand.  The stage's B box
+// holds the nine taps t = kx + 3 q (TMA element stride 3 along the tap axis of the tap-major
+// weights).  Slice zz accumulates in TMEM columns [zz N, zz N + N).  The epilogue moves each
+// slice through shared memory (rows padded to N + 4 floats: conflict-free 16-byte writes) and
+// stores it with coalesced 16-byte accesses.
 // ------------------------------------------------------------------------------------
-constexpr int kH3Rows = 8 * 18 * 3;  // rows of one halo box
-constexpr int kT3Max = 4;            // pipeline stages (at most)
+constexpr int kT3Max = 4;  // pipeline stages (at most)
 
 template <int CK>
 __global__ void __launch_bounds__(128, 1)
 conv_tc3_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
                 const float* __restrict__ bias, float* __restrict__ out, Dims3 dout, int N,
-                int nchunks, int tiles_x, int tiles_y, long long out_bs, long long bias_bs,
-                int accumulate, int nst, int* __restrict__ err) {
-  constexpr uint32_t kABytes = kH3Rows * CK * 2;
+                int nchunks, int tiles_x, int tiles_y, int TZ, long long out_bs,
+                long long bias_bs, int accumulate, int nst, int* __restrict__ err) {
   constexpr uint32_t kRowB = CK * 2;
+  const uint32_t a_bytes = (uint32_t)(8 * 18 * (TZ + 2)) * kRowB;
   const uint32_t b_tap = (uint32_t)N * CK * 2;
-  const uint32_t stage_bytes = kABytes + 9 * b_tap;
+  const uint32_t stage_bytes = a_bytes + 9 * b_tap;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[kT3Max], empty_bar[kT3Max], done_bar;
   __shared__ uint32_t tmem_base_s;
+  __shared__ __align__(16) float sbias[256];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int b = blockIdx.z;
-  const int tile = blockIdx.x;
+  for (int c = threadIdx.x; c < N; c += blockDim.x)
+    sbias[c] = bias ? bias[(long long)b * bias_bs + c] : 0.f;
+  int tile = blockIdx.x;
   const int x0 = (tile % tiles_x) * 8;
-  const int y0 = ((tile / tiles_x) % tiles_y) * 16;
-  const int z0 = tile / (tiles_x * tiles_y);
+  tile /= tiles_x;
+  const int y0 = (tile % tiles_y) * 16;
+  const int z0 = (tile / tiles_y) * TZ;
   const int ksteps = nchunks * 3;
-  const uint32_t tmem_cols = N <= 32 ? 32u : N <= 64 ? 64u : N <= 128 ? 128u : 256u;
+  const int cols = TZ * N;
+  const uint32_t tmem_cols = cols <= 32 ? 32u : cols <= 64 ? 64u : cols <= 128 ? 128u
+                                                : cols <= 256 ? 256u : 512u;
 
   if (threadIdx.x == 0) {
     for (int q = 0; q < nst; ++q) {
@@ -336,7 +343,7 @@ conv_tc3_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant_
       const uint32_t fb = smem_u32(&full_bar[st]);
       mbar_expect_tx(fb, stage_bytes);
       tma_load_5d(dst, &tm_a, c * CK, x0 + kx - 1, y0 - 1, z0 - 1, b, fb);
-      tma_load_4d(dst + kABytes, &tm_b, c * CK, 0, kx, b, fb);
+      tma_load_4d(dst + a_bytes, &tm_b, c * CK, 0, kx, b, fb);
     }
   } else if (warp == 1 && lane == 0) {  // MMA issuer
     const uint32_t idesc = instr_desc(N);
@@ -347,16 +354,21 @@ conv_tc3_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant_
         break;
       }
       tc_fence_after();
+      // descriptors are linear in the address (start >> 4 in the low field): offset a base
       const uint32_t a_addr = smem_u32(smem + (size_t)st * stage_bytes);
-      const uint32_t b_addr = a_addr + kABytes;
+      const uint64_t a0 = smem_desc<CK>(a_addr), b0 = smem_desc<CK>(a_addr + a_bytes);
 #pragma unroll 1
       for (int q = 0; q < 9; ++q) {  // tap t = kx + 3 q: kz = q / 3, ky = q % 3
-        const uint32_t a_win = a_addr + (uint32_t)(((q / 3) * 18 + (q % 3)) * 8) * kRowB;
-        const uint32_t b_win = b_addr + (uint32_t)q * b_tap;
+        const uint64_t bq = b0 + ((q * b_tap) >> 4);
+        const uint32_t acc = (k > 0 || q > 0) ? 1u : 0u;
+#pragma unroll 1
+        for (int zz = 0; zz < TZ; ++zz) {
+          const uint64_t aq = a0 + ((((zz + q / 3) * 18 + (q % 3)) * 8 * kRowB) >> 4);
 #pragma unroll
-        for (int kk = 0; kk < CK / 16; ++kk)
-          mma_bf16(tmem, smem_desc<CK>(a_win + kk * 32), smem_desc<CK>(b_win + kk * 32), idesc,
-                   (k > 0 || q > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < CK / 16; ++kk)
+            mma_bf16(tmem + (uint32_t)(zz * N), aq + kk * 2, bq + kk * 2, idesc,
+                     (acc | kk) ? 1u : 0u);
+        }
       }
       mma_commit(smem_u32(&empty_bar[st]));
     }
@@ -367,23 +379,45 @@ conv_tc3_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant_
   const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&done_bar), 0));
   if (!ok && lane == 0) atomicOr(err, kErrEpilogue);
   tc_fence_after();
-  if (ok) {
+  // every warp reached done_bar: all loads were consumed and all MMAs completed, so the
+  // pipeline buffers are free for the output staging
+  const int okall = __syncthreads_and(ok ? 1 : 0);
+  if (okall) {
     const int m = warp * 32 + lane;
-    const int ox = x0 + m % 8, oy = y0 + m / 8, oz = z0;
-    const bool inside = ox < dout.x && oy < dout.y && oz < dout.z;
-    const long long vox = ((long long)oz * dout.y + oy) * dout.x + ox;
-    float* o = out + (long long)b * out_bs + vox * N;
-    const float* bb = bias ? bias + (long long)b * bias_bs : nullptr;
-    for (int c0 = 0; c0 < N; c0 += 16) {
-      uint32_t r[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-      if (inside) {
+    const int ld = N + 4;  // padded staging row (floats)
+    float* stg = reinterpret_cast<float*>(smem);
+    const int n4 = N / 4;
+    for (int zz = 0; zz < TZ; ++zz) {
+      for (int c0 = 0; c0 < N; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(zz * N + c0), r);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const float v = __uint_as_float(r[j]) + (bb ? bb[c0 + j] : 0.f);
-          o[c0 + j] = accumulate ? o[c0 + j] + v : v;
+        for (int j = 0; j < 16; j += 4) {
+          float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                 __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+          const float4 bv = *reinterpret_cast<const float4*>(sbias + c0 + j);
+          v.x += bv.x, v.y += bv.y, v.z += bv.z, v.w += bv.w;
+          *reinterpret_cast<float4*>(stg + m * ld + c0 + j) = v;
         }
       }
+      __syncthreads();
+      const int oz = z0 + zz;
+      if (oz < dout.z) {
+        for (int i = threadIdx.x; i < 128 * n4; i += blockDim.x) {
+          const int mv = i / n4, c4 = i % n4;
+          const int ox = x0 + mv % 8, oy = y0 + mv / 8;
+          if (ox >= dout.x || oy >= dout.y) continue;
+          float4 v = *reinterpret_cast<const float4*>(stg + mv * ld + c4 * 4);
+          float4* o = reinterpret_cast<float4*>(
+              out + (long long)b * out_bs + (((long long)oz * dout.y + oy) * dout.x + ox) * N) + c4;
+          if (accumulate) {
+            const float4 p = *o;
+            v.x += p.x, v.y += p.y, v.z += p.z, v.w += p.w;
+          }
+          *o = v;
+        }
+      }
+      __syncthreads();
     }
   }
   tc_fence_before();
@@ -564,6 +598,188 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant
 }
 
 // ------------------------------------------------------------------------------------
+// Weight gradient of a 3x3x3 stride-1 layer with halo boxes.  K tile = one column of
+// 8 x 1 x TZ input voxels u (rows g * 8 + x, g = z offset).  With dy shifted by the tap,
+// dW[co][t][ci] = sum_u dy[u + 1 - k_t][co] x[u][ci]; for one x tap kx the dy values of all
+// nine (ky, kz) taps lie in one TMA box of 8 x 3 x (TZ + 2) voxels.  Stored [z][y][x], the
+// window of tap (ky, kz) starts p = 8 - 3 kz - ky swizzle atoms (8 rows) into the box and
+// steps 3 atoms per z, so an M block of one tap's Co channels is an MN-major operand with
+// block stride = 1 atom and 8-row K-group stride = 3 atoms.  One MMA (M = 128) covers
+// TPM = 128 / Co consecutive windows; G = ceil(9 / TPM) MMAs per x tap (the last one
+// overlaps its predecessor and only its new rows are kept).  B = the unshifted x column
+// plus a block of ones, whose column gives sum(dy) per window: the centre tap's is the bias
+// partial.  A CTA adds the products of a run of tiles for NKX x taps (all three when the
+// accumulators fit in TMEM, else one per grid row) and writes one partial-sum row.
+// ------------------------------------------------------------------------------------
+constexpr int kWg3MaxStages = 6;
+
+// MN-major descriptor with explicit MN-block stride (lbo) and 8-row K-group stride (sbo).
+template <int CK>
+__device__ __forceinline__ uint64_t smem_desc_mn2(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  constexpr uint64_t kSwizzle = CK == 16 ? 6 : (CK == 32 ? 4 : 2);
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= 1ull << 46;
+  d |= kSwizzle << 61;
+  return d;
+}
+
+struct Wg3Geom {
+  int tz, nkx, tiles_x, tiles_z, ntiles, tiles_per_chunk, nchunks, nst;
+  uint32_t a_box, b_box, b_off, ones_off, stage, tmem_cols;
+};
+
+template <int CKA, int CKB>
+__global__ void __launch_bounds__(128, 1)
+wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant__ CUtensorMap tm_x,
+                 float* __restrict__ part, Dims3 d, int Ci, int ci_out,
+                 const __grid_constant__ Wg3Geom gm, int* __restrict__ err) {
+  constexpr int kTpm = 128 / CKA;                  // taps per MMA
+  constexpr int kG = (9 + kTpm - 1) / kTpm;        // MMAs per x tap
+  constexpr uint32_t kAtomA = 8 * CKA * 2;         // 8 rows of dy
+  constexpr uint32_t kAtomB = 8 * CKB * 2;
+  const int N = Ci + CKB;                          // + the ones block
+  const int nb = Ci / CKB;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[kWg3MaxStages], empty_bar[kWg3MaxStages], done_bar;
+  __shared__ uint32_t tmem_base_s;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int chunk = blockIdx.x, kx0 = blockIdx.y * gm.nkx, b = blockIdx.z;
+  const int tile0 = chunk * gm.tiles_per_chunk;
+  const int tile1 = min(tile0 + gm.tiles_per_chunk, gm.ntiles);
+  const int ksteps = max(tile1 - tile0, 0);
+  const int nst = gm.nst;
+  for (int s = 0; s < nst; ++s) {
+    uint32_t* ones = reinterpret_cast<uint32_t*>(smem + (size_t)s * gm.stage + gm.ones_off);
+    for (int i = threadIdx.x; i < (int)(gm.b_box / 4); i += blockDim.x) ones[i] = 0x3F803F80u;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nst; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_u32(&done_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_s)),
+                 "r"(gm.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  if (warp == 0 && lane == 0) {  // TMA producer
+    const uint32_t tx_bytes = (uint32_t)gm.nkx * gm.a_box + (uint32_t)nb * gm.b_box;
+    for (int k = 0; k < ksteps; ++k) {
+      const int s = k % nst, round = k / nst;
+      if (round > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (round - 1) & 1)) {
+        atomicOr(err, kErrProducer);
+        break;
+      }
+      const int tile = tile0 + k;
+      const int x0 = (tile % gm.tiles_x) * 8;
+      const int y0 = (tile / gm.tiles_x) % d.y;
+      const int z0 = (tile / (gm.tiles_x * d.y)) * gm.tz;
+      const uint32_t base = smem_u32(smem + (size_t)s * gm.stage);
+      const uint32_t fb = smem_u32(&full_bar[s]);
+      mbar_expect_tx(fb, tx_bytes);
+      for (int q = 0; q < gm.nkx; ++q)
+        tma_load_5d(base + (uint32_t)q * gm.a_box, &tm_dy, 0, x0 + 1 - (kx0 + q), y0 - 1, z0 - 1,
+                    b, fb);
+      for (int c = 0; c < nb; ++c)
+        tma_load_5d(base + gm.b_off + (uint32_t)c * gm.b_box, &tm_x, c * CKB, x0, y0, z0, b, fb);
+    }
+  } else if (warp == 1 && lane == 0) {  // MMA issuer
+    const uint32_t idesc = instr_desc_mn(N);
+    for (int k = 0; k < ksteps; ++k) {
+      const int s = k % nst;
+      if (!mbar_wait(smem_u32(&full_bar[s]), (k / nst) & 1)) {
+        atomicOr(err, kErrMma);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = smem_u32(smem + (size_t)s * gm.stage);
+      // descriptors are linear in the address (start >> 4 in the low field): offset a base
+      const uint64_t a0 = smem_desc_mn2<CKA>(base, kAtomA, 3 * kAtomA);
+      const uint64_t b0 = smem_desc_mn2<CKB>(base + gm.b_off, gm.b_box, kAtomB);
+      for (int kk = 0; kk < gm.tz / 2; ++kk) {  // K = 16 voxels = z offsets 2kk, 2kk + 1
+        const uint64_t db = b0 + ((kk * 2 * kAtomB) >> 4);
+        const uint64_t ak = a0 + ((kk * 6 * kAtomA) >> 4);
+        const uint32_t acc = (k > 0 || kk > 0) ? 1u : 0u;
+        for (int q = 0; q < gm.nkx; ++q) {
+          const uint64_t aq = ak + ((q * gm.a_box) >> 4);
+#pragma unroll
+          for (int g = 0; g < kG; ++g) {
+            constexpr int kLast = 9 - kTpm;
+            const int s0 = g * kTpm < kLast ? g * kTpm : kLast;
+            mma_bf16(tmem + (uint32_t)((q * kG + g) * N), aq + ((s0 * kAtomA) >> 4), db, idesc,
+                     acc);
+          }
+        }
+      }
+      mma_commit(smem_u32(&empty_bar[s]));
+    }
+    mma_commit(smem_u32(&done_bar));
+  }
+  __syncwarp();
+
+  const bool waited = ksteps > 0 ? mbar_wait(smem_u32(&done_bar), 0) : false;
+  const bool ok = __all_sync(0xffffffffu, waited);
+  if (!ok && ksteps > 0 && lane == 0) atomicOr(err, kErrEpilogue);
+  tc_fence_after();
+  const int Co = CKA;
+  const int m = warp * 32 + lane;  // TMEM lane = (window in the MMA, co)
+  const int pl = m / Co, co = m % Co;
+  const long long row = (long long)Co * 27 * ci_out + Co;  // the first ci_out channels
+  float* prow = part + ((long long)b * gm.nchunks + chunk) * row;
+  for (int q = 0; q < gm.nkx; ++q)
+    for (int g = 0; g < kG; ++g) {
+      const int s0 = g * kTpm < 9 - kTpm ? g * kTpm : 9 - kTpm;
+      const int p = s0 + pl;                      // window p <-> tap 3 kz + ky = 8 - p
+      const bool keep = p >= g * kTpm && p < 9;   // rows new to this MMA
+      const int tq = 8 - p, kz = tq / 3, ky = tq % 3, kx = kx0 + q;
+      const int t = kz * 9 + ky * 3 + kx;
+      float* out = prow + ((long long)co * 27 + t) * ci_out;
+      const uint32_t col = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((q * kG + g) * N);
+      for (int c0 = 0; c0 < Ci; c0 += 16) {
+        uint32_t r[16];
+        if (ok) tmem_ld16(col + (uint32_t)c0, r);
+        if (keep) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4)
+            if (c0 + j < ci_out)
+              *reinterpret_cast<float4*>(out + c0 + j) =
+                ok ? make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                 __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]))
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+      uint32_t r[16];
+      if (ok) tmem_ld16(col + (uint32_t)Ci, r);
+      if (keep && t == 13)
+        prow[(long long)Co * 27 * ci_out + co] = ok ? __uint_as_float(r[0]) : 0.f;
+    }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(gm.tmem_cols)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------------------------
 // staging kernels
 // ------------------------------------------------------------------------------------
 __global__ void f32_to_bf16_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ y,
@@ -583,18 +799,18 @@ __global__ void f32_to_bf16_kernel(const float* __restrict__ x, __nv_bfloat16* _
 // major), for every problem of the batch.
 __global__ void weights_bf16_kernel(const float* __restrict__ theta, __nv_bfloat16* __restrict__ wb,
                                     long long Pp, long long wstride, long long w_off,
-                                    long long wf_off, long long wd_off, int ci, int co, int T,
-                                    int dgrad) {
+                                    long long wf_off, long long wd_off, int ci, int ci_real,
+                                    int co, int T, int dgrad) {
   const int b = blockIdx.y;
-  const long long n = (long long)co * T * ci;
+  const long long n = (long long)co * T * ci;  // padded input channels
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
-  const float v = theta[(long long)b * Pp + w_off + e];  // W[o][t][c]
-  const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  __nv_bfloat16* base = wb + (long long)b * wstride;
   const int c = (int)(e % ci);
   const long long r = e / ci;
   const int t = (int)(r % T), o = (int)(r / T);
+  const float v = c < ci_real ? theta[(long long)b * Pp + w_off + r * ci_real + c] : 0.f;
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);  // W[o][t][c]
+  __nv_bfloat16* base = wb + (long long)b * wstride;
   base[wf_off + ((long long)t * co + o) * ci + c] = h;                     // [t][co][ci]
   if (dgrad) base[wd_off + ((long long)(T - 1 - t) * ci + c) * co + o] = h;  // [26-t][ci][co]
 }
@@ -618,6 +834,9 @@ EncodeTiledFn encode_fn() {
 }
 
 int chunk_for(int c) { return c % 64 == 0 ? 64 : (c % 32 == 0 ? 32 : 16); }
+
+int wg3_tz(int Z);
+Wg3Geom wg3_geom(const TcLayer& L, int B);
 
 CUtensorMapSwizzle swizzle_for(int ck) {
   return ck == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
@@ -661,9 +880,9 @@ cudaError_t encode_w(CUtensorMap* m, void* base, int B, long long wstride, int c
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// Channels-last activations with an 8 x 18 x 3 box: the x-shifted halo of an 8 x 16 x 1 tile
-// for the three (y, z) offsets of every tap.
-cudaError_t encode_act_halo(CUtensorMap* m, void* base, int B, Dims3 d, int C, int ck) {
+// Channels-last activations [B][Z][Y][X][C] with a bx x by x bz box of ck channels.
+cudaError_t encode_box(CUtensorMap* m, void* base, int B, Dims3 d, int C, int ck, int bx, int by,
+                       int bz) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   const cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)d.x, (cuuint64_t)d.y, (cuuint64_t)d.z,
@@ -671,7 +890,25 @@ cudaError_t encode_act_halo(CUtensorMap* m, void* base, int B, Dims3 d, int C, i
   const cuuint64_t es = 2;
   const cuuint64_t strides[4] = {C * es, C * es * d.x, C * es * d.x * d.y,
                                  C * es * d.x * d.y * d.z};
-  const cuuint32_t box[5] = {(cuuint32_t)ck, 8, 18, 3, 1};
+  const cuuint32_t box[5] = {(cuuint32_t)ck, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(ck),
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Channels-last activations with an 8 x 18 x (tz + 2) box: the x-shifted halo of an
+// 8 x 16 x tz tile for the (y, z) offsets of every tap.
+cudaError_t encode_act_halo(CUtensorMap* m, void* base, int B, Dims3 d, int C, int ck, int tz) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)d.x, (cuuint64_t)d.y, (cuuint64_t)d.z,
+                              (cuuint64_t)B};
+  const cuuint64_t es = 2;
+  const cuuint64_t strides[4] = {C * es, C * es * d.x, C * es * d.x * d.y,
+                                 C * es * d.x * d.y * d.z};
+  const cuuint32_t box[5] = {(cuuint32_t)ck, 8, 18, (cuuint32_t)(tz + 2), 1};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(ck),
@@ -681,7 +918,9 @@ cudaError_t encode_act_halo(CUtensorMap* m, void* base, int B, Dims3 d, int C, i
 
 size_t smem_bytes(int ck, int n) { return (size_t)kStages * (kBM + n) * ck * 2 + 1024; }
 
-size_t tc3_stage(int ck, int n) { return (size_t)kH3Rows * ck * 2 + (size_t)9 * n * ck * 2; }
+size_t tc3_stage(int ck, int n, int tz = 1) {
+  return (size_t)8 * 18 * (tz + 2) * ck * 2 + (size_t)9 * n * ck * 2;
+}
 
 // Largest channel chunk (64, 32, 16) dividing cin whose halo stage stays within 100 KB.
 int tc3_chunk(int cin, int n) {
@@ -692,27 +931,44 @@ int tc3_chunk(int cin, int n) {
 
 constexpr size_t kTc3SmemMax = 210 * 1024;
 
+// z slices per halo-box tile: the z extent in {1, 2, 4} that loads the fewest halo rows per
+// z column (ceil(Z / tz) boxes of tz + 2 planes; ties: the smaller), among those whose stage
+// stays within 72 KB and whose accumulators within 256 TMEM columns.
+int tc3_tz(int ck, int n, int Z) {
+  int best = 1;
+  long long best_cost = 3LL * Z;
+  for (int tz : {2, 4}) {
+    if (tc3_stage(ck, n, tz) > 72 * 1024 || tz * n > 256) continue;
+    const long long cost = ceil_div(Z, tz) * (tz + 2);
+    if (cost < best_cost) best = tz, best_cost = cost;
+  }
+  return best;
+}
+
 cudaError_t launch_tc3(const CUtensorMap& a, const CUtensorMap& w, int cin, int ck,
                        const float* bias, float* out, Dims3 dout, int n, int B, long long out_bs,
                        long long bias_bs, int acc, int* err, cudaStream_t st) {
+  const int tz = tc3_tz(ck, n, dout.z);
   const int tx = (int)ceil_div(dout.x, 8), ty = (int)ceil_div(dout.y, 16);
-  dim3 grid((unsigned)(tx * ty * dout.z), 1, B);
-  const size_t stage = tc3_stage(ck, n);
-  const int nst = (int)std::min<size_t>(kT3Max, (kTc3SmemMax - 1024) / stage);
-  const size_t sm = (size_t)nst * stage + 1024;
+  dim3 grid((unsigned)(tx * ty * ceil_div(dout.z, tz)), 1, B);
+  const size_t stage = tc3_stage(ck, n, tz);
   const int nch = cin / ck;
+  const int nst = (int)std::min<size_t>({(size_t)kT3Max, (kTc3SmemMax - 1024) / stage,
+                                         (size_t)nch * 3});
+  // the epilogue stages one 128 x (N + 4) FP32 slice in the pipeline buffers
+  const size_t sm = std::max((size_t)nst * stage, (size_t)128 * (n + 4) * 4) + 1024;
   switch (ck) {
     case 64:
-      conv_tc3_kernel<64><<<grid, 128, sm, st>>>(a, w, bias, out, dout, n, nch, tx, ty, out_bs,
-                                                  bias_bs, acc, nst, err);
+      conv_tc3_kernel<64><<<grid, 128, sm, st>>>(a, w, bias, out, dout, n, nch, tx, ty, tz,
+                                                  out_bs, bias_bs, acc, nst, err);
       break;
     case 32:
-      conv_tc3_kernel<32><<<grid, 128, sm, st>>>(a, w, bias, out, dout, n, nch, tx, ty, out_bs,
-                                                  bias_bs, acc, nst, err);
+      conv_tc3_kernel<32><<<grid, 128, sm, st>>>(a, w, bias, out, dout, n, nch, tx, ty, tz,
+                                                  out_bs, bias_bs, acc, nst, err);
       break;
     default:
-      conv_tc3_kernel<16><<<grid, 128, sm, st>>>(a, w, bias, out, dout, n, nch, tx, ty, out_bs,
-                                                  bias_bs, acc, nst, err);
+      conv_tc3_kernel<16><<<grid, 128, sm, st>>>(a, w, bias, out, dout, n, nch, tx, ty, tz,
+                                                  out_bs, bias_bs, acc, nst, err);
       break;
   }
   return cudaGetLastError();
@@ -809,6 +1065,7 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
   if (!bf16_conv_supported(ci, co, k)) return -1;
   TcLayer L;
   L.ci = ci;
+  L.ci_real = ci;
   L.co = co;
   L.k = k;
   L.s = s;
@@ -819,6 +1076,7 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
   L.ck3f = (k == 3 && s == 1) ? tc3_chunk(ci, co) : 0;
   L.ck3d = (k == 3 && s == 1 && L.dgrad) ? tc3_chunk(co, ci) : 0;
   L.wgrad = s == 1 && co <= 128 && 128 % co == 0 && ci + chunk_for(ci) <= 256;
+  L.wg3 = L.wgrad && wg3_geom(L, 1).nst > 0;
   const long long n = (long long)co * k * k * k * ci;
   L.wf_off = bf.wstride;
   bf.wstride += (n + 63) / 64 * 64;
@@ -826,6 +1084,28 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
     L.wd_off = bf.wstride;
     bf.wstride += (n + 63) / 64 * 64;
   }
+  bf.layers.push_back(L);
+  return (int)bf.layers.size() - 1;
+}
+
+int bf16_add_input_layer(Bf16Net& bf, int ci_real, int co, Dims3 din, long long w_off) {
+  if (ci_real < 1 || ci_real > 16 || ci_real % 4 != 0) return -1;
+  TcLayer L;
+  L.ci = 16;
+  L.ci_real = ci_real;
+  L.co = co;
+  L.k = 3;
+  L.s = 1;
+  L.din = din;
+  L.dout = din;
+  L.w_off = w_off;
+  L.input_layer = true;
+  L.ck3f = bf16_conv_supported(16, co, 3) ? tc3_chunk(16, co) : 0;
+  L.wgrad = L.wg3 = wg3_geom(L, 1).nst > 0;
+  if (!L.ck3f || !L.wg3) return -1;
+  L.wf_off = bf.wstride;
+  bf.wstride += ((long long)co * 27 * 16 + 63) / 64 * 64;
+  bf.zcount = din.count() * 16;
   bf.layers.push_back(L);
   return (int)bf.layers.size() - 1;
 }
@@ -841,11 +1121,23 @@ void bf16_layout(Bf16Net& bf, char* base, size_t& used, int B, long long max_act
   bf.xbf = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * max_act * 2));
   bf.ybf = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * max_act * 2));
   bf.wbuf = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * bf.wstride * 2));
+  bf.zbf = bf.zcount ? reinterpret_cast<__nv_bfloat16*>(take((size_t)B * bf.zcount * 2)) : nullptr;
 }
 
 cudaError_t bf16_finalize(Bf16Net& bf, int B) {
   for (TcLayer& L : bf.layers) {
     const int T = L.k * L.k * L.k;
+    if (L.input_layer) {  // halo-box forward and weight gradient over zbf only
+      cudaError_t e =
+          encode_act_halo(&L.act_f3, bf.zbf, B, L.din, 16, L.ck3f, tc3_tz(L.ck3f, L.co, L.dout.z));
+      if (e == cudaSuccess)
+        e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, 16, T, L.co, L.ck3f, 9, 3);
+      const int tz = wg3_tz(L.dout.z);
+      if (e == cudaSuccess) e = encode_box(&L.wg_dy3, bf.ybf, B, L.dout, L.co, L.co, 8, 3, tz + 2);
+      if (e == cudaSuccess) e = encode_box(&L.wg_x3, bf.zbf, B, L.din, 16, 16, 8, 1, tz);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     cudaError_t e = encode_act(&L.act_f, bf.xbf, B, L.din, L.ci, chunk_for(L.ci), L.s);
     if (e == cudaSuccess)
       e = encode_w(&L.w_f, bf.wbuf + L.wf_off, B, bf.wstride, L.ci, T, L.co, chunk_for(L.ci), 1,
@@ -858,13 +1150,21 @@ cudaError_t bf16_finalize(Bf16Net& bf, int B) {
     }
     if (e == cudaSuccess && L.wgrad)
       e = encode_act(&L.act_wy, bf.ybf, B, L.dout, L.co, chunk_for(L.co), 1);
+    if (e == cudaSuccess && L.wg3) {
+      const int tz = wg3_tz(L.dout.z);
+      e = encode_box(&L.wg_dy3, bf.ybf, B, L.dout, L.co, L.co, 8, 3, tz + 2);
+      if (e == cudaSuccess)
+        e = encode_box(&L.wg_x3, bf.xbf, B, L.din, L.ci, chunk_for(L.ci), 8, 1, tz);
+    }
     if (e == cudaSuccess && L.ck3f) {
-      e = encode_act_halo(&L.act_f3, bf.xbf, B, L.din, L.ci, L.ck3f);
+      e = encode_act_halo(&L.act_f3, bf.xbf, B, L.din, L.ci, L.ck3f,
+                          tc3_tz(L.ck3f, L.co, L.dout.z));
       if (e == cudaSuccess)
         e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, L.ci, T, L.co, L.ck3f, 9, 3);
     }
     if (e == cudaSuccess && L.ck3d) {
-      e = encode_act_halo(&L.act_d3, bf.xbf, B, L.dout, L.co, L.ck3d);
+      e = encode_act_halo(&L.act_d3, bf.xbf, B, L.dout, L.co, L.ck3d,
+                          tc3_tz(L.ck3d, L.ci, L.din.z));
       if (e == cudaSuccess)
         e = encode_w(&L.w_d3, bf.wbuf + L.wd_off, B, bf.wstride, L.co, T, L.ci, L.ck3d, 9, 3);
     }
@@ -916,10 +1216,87 @@ void launch_wgrad_tc(dim3 grid, size_t smem, const TcLayer& L, float* part, cons
       p.tiles_x, p.tiles_y, p.chunks, p.nst, err);
 }
 
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 152;
+  }
+  return n;
+}
+
+constexpr size_t kWg3SmemMax = 210 * 1024;
+
+// z extent of the halo weight-gradient column: the even tz <= 16 with the least padding of Z.
+int wg3_tz(int Z) {
+  int best = 16;
+  long long best_pad = ceil_div(Z, 16) * 16;
+  for (int tz = 14; tz >= 2; tz -= 2) {
+    const long long pad = ceil_div(Z, tz) * tz;
+    if (pad < best_pad) best = tz, best_pad = pad;
+  }
+  return best;
+}
+
+// Geometry of the halo weight gradient; nst == 0 when the layer does not fit it.
+Wg3Geom wg3_geom(const TcLayer& L, int B) {
+  Wg3Geom g{};
+  if (L.k != 3 || L.s != 1 || (L.co != 16 && L.co != 32 && L.co != 64)) return g;
+  const int ckb = chunk_for(L.ci);
+  const int tpm = 128 / L.co, G = (9 + tpm - 1) / tpm, N = L.ci + ckb;
+  if (N > 256) return g;
+  auto pow2 = [](int c) {
+    int t = 32;
+    while (t < c) t *= 2;
+    return t;
+  };
+  g.nkx = 3 * G * N <= 512 ? 3 : 1;
+  if (G * N > 512) return g;
+  g.tmem_cols = (uint32_t)pow2(g.nkx * G * N);
+  g.tz = wg3_tz(L.dout.z);
+  g.a_box = (uint32_t)(8 * 3 * (g.tz + 2) * L.co * 2);
+  g.b_box = (uint32_t)(8 * g.tz * ckb * 2);
+  g.b_off = (uint32_t)((g.nkx * g.a_box + 1023) / 1024 * 1024);
+  g.ones_off = g.b_off + (uint32_t)(L.ci / ckb) * g.b_box;
+  g.stage = (g.ones_off + g.b_box + 1023) / 1024 * 1024;
+  const int nst = (int)std::min<size_t>(kWg3MaxStages, (kWg3SmemMax - 1024) / g.stage);
+  if (nst < 2) return g;
+  g.tiles_x = (int)ceil_div(L.dout.x, 8);
+  g.tiles_z = (int)ceil_div(L.dout.z, g.tz);
+  g.ntiles = g.tiles_x * L.dout.y * g.tiles_z;
+  const size_t smem = (size_t)nst * g.stage + 1024;
+  const int cps = std::max(1, std::min((int)(233472 / (smem + 1024)), (int)(512 / g.tmem_cols)));
+  const long long slots = (long long)sm_count() * cps;
+  const long long want = std::max(1LL, slots / ((3 / g.nkx) * (long long)B));
+  g.tiles_per_chunk = (int)ceil_div(g.ntiles, std::min<long long>(want, g.ntiles));
+  g.nchunks = (int)ceil_div(g.ntiles, g.tiles_per_chunk);
+  g.nst = nst;
+  return g;
+}
+
+template <int CKA, int CKB>
+cudaError_t wg3_attr() {
+  return cudaFuncSetAttribute(wgrad_tc3_kernel<CKA, CKB>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWg3SmemMax);
+}
+
+template <int CKA, int CKB>
+void launch_wg3(const TcLayer& L, const Wg3Geom& g, float* part, int B, int* err,
+                cudaStream_t st) {
+  dim3 grid((unsigned)g.nchunks, (unsigned)(3 / g.nkx), (unsigned)B);
+  const size_t smem = (size_t)g.nst * g.stage + 1024;
+  wgrad_tc3_kernel<CKA, CKB><<<grid, 128, smem, st>>>(L.wg_dy3, L.wg_x3, part, L.dout, L.ci,
+                                                      L.ci_real, g, err);
+}
+
 }  // namespace
 
 long long bf16_wgrad_chunks(const Bf16Net& bf, int layer, int B) {
-  return wgrad_plan(bf.layers[layer], B).chunks;
+  const TcLayer& L = bf.layers[layer];
+  if (L.wg3) return wg3_geom(L, B).nchunks;
+  return wgrad_plan(L, B).chunks;
 }
 
 cudaError_t bf16_conv_wgrad(Bf16Net& bf, int layer, const float* x, const float* dy,
@@ -927,9 +1304,24 @@ cudaError_t bf16_conv_wgrad(Bf16Net& bf, int layer, const float* x, const float*
   const TcLayer& L = bf.layers[layer];
   if (!L.wgrad) return cudaErrorInvalidValue;
   const WgPlan p = wgrad_plan(L, B);
-  cudaError_t e = stage_bf16(x, bf.xbf, (long long)B * L.din.count() * L.ci, stream);
+  cudaError_t e =
+      L.input_layer ? cudaSuccess : stage_bf16(x, bf.xbf, (long long)B * L.din.count() * L.ci, stream);
   if (e == cudaSuccess) e = stage_bf16(dy, bf.ybf, (long long)B * L.dout.count() * L.co, stream);
   if (e != cudaSuccess) return e;
+  if (L.wg3) {
+    const Wg3Geom g = wg3_geom(L, B);
+    const int ckb = chunk_for(L.ci);
+#define D2IP_WG3(A_, B_) launch_wg3<A_, B_>(L, g, part, B, bf.err, stream)
+    if (L.co == 16) {
+      if (ckb == 16) D2IP_WG3(16, 16); else if (ckb == 32) D2IP_WG3(16, 32); else D2IP_WG3(16, 64);
+    } else if (L.co == 32) {
+      if (ckb == 16) D2IP_WG3(32, 16); else if (ckb == 32) D2IP_WG3(32, 32); else D2IP_WG3(32, 64);
+    } else {
+      if (ckb == 16) D2IP_WG3(64, 16); else if (ckb == 32) D2IP_WG3(64, 32); else D2IP_WG3(64, 64);
+    }
+#undef D2IP_WG3
+    return cudaGetLastError();
+  }
   dim3 grid(p.chunks, p.groups, B);
   const int cka = chunk_for(L.co), ckb = chunk_for(L.ci);
 #define D2IP_WGT(A_, B_) launch_wgrad_tc<A_, B_>(grid, p.smem, L, part, p, bf.err, stream)
@@ -972,6 +1364,15 @@ cudaError_t bf16_prepare_kernels() {
   if (e == cudaSuccess) e = wgrad_attr<64, 16>();
   if (e == cudaSuccess) e = wgrad_attr<64, 32>();
   if (e == cudaSuccess) e = wgrad_attr<64, 64>();
+  if (e == cudaSuccess) e = wg3_attr<16, 16>();
+  if (e == cudaSuccess) e = wg3_attr<16, 32>();
+  if (e == cudaSuccess) e = wg3_attr<16, 64>();
+  if (e == cudaSuccess) e = wg3_attr<32, 16>();
+  if (e == cudaSuccess) e = wg3_attr<32, 32>();
+  if (e == cudaSuccess) e = wg3_attr<32, 64>();
+  if (e == cudaSuccess) e = wg3_attr<64, 16>();
+  if (e == cudaSuccess) e = wg3_attr<64, 32>();
+  if (e == cudaSuccess) e = wg3_attr<64, 64>();
   return e;
 }
 
@@ -982,7 +1383,7 @@ cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long lo
     const long long n = (long long)L.co * T * L.ci;
     dim3 grid((unsigned)ceil_div(n, 256), B);
     weights_bf16_kernel<<<grid, 256, 0, stream>>>(theta, bf.wbuf, Pp, bf.wstride, L.w_off,
-                                                  L.wf_off, L.wd_off, L.ci, L.co, T,
+                                                  L.wf_off, L.wd_off, L.ci, L.ci_real, L.co, T,
                                                   L.dgrad ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -995,10 +1396,32 @@ static cudaError_t stage_bf16(const float* x, __nv_bfloat16* y, long long n, cud
   return cudaGetLastError();
 }
 
+namespace {
+// z [v][cr] FP32 -> zp [v][16] BF16, channels cr..15 zero; one thread per (voxel, channel).
+__global__ void pad_input_kernel(const float* __restrict__ z, __nv_bfloat16* __restrict__ zp,
+                                 long long nvox, int cr) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nvox * 16) return;
+  const long long v = i / 16;
+  const int c = (int)(i % 16);
+  zp[i] = __float2bfloat16_rn(c < cr ? z[v * cr + c] : 0.f);
+}
+}  // namespace
+
+cudaError_t bf16_stage_input(Bf16Net& bf, int layer, const float* z, int B, cudaStream_t stream) {
+  const TcLayer& L = bf.layers[layer];
+  if (!L.input_layer || !bf.zbf) return cudaErrorInvalidValue;
+  const long long nvox = (long long)B * L.din.count();
+  pad_input_kernel<<<(unsigned)ceil_div(nvox * 16, 256), 256, 0, stream>>>(z, bf.zbf, nvox,
+                                                                          L.ci_real);
+  return cudaGetLastError();
+}
+
 cudaError_t bf16_conv_fwd(Bf16Net& bf, int layer, const float* x, const float* bias, float* y,
                           int B, long long bias_bs, cudaStream_t stream) {
   const TcLayer& L = bf.layers[layer];
-  cudaError_t e = stage_bf16(x, bf.xbf, (long long)B * L.din.count() * L.ci, stream);
+  cudaError_t e =
+      L.input_layer ? cudaSuccess : stage_bf16(x, bf.xbf, (long long)B * L.din.count() * L.ci, stream);
   if (e != cudaSuccess) return e;
   if (L.ck3f)
     return launch_tc3(L.act_f3, L.w_f3, L.ci, L.ck3f, bias, y, L.dout, L.co, B,

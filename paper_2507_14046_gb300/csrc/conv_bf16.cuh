@@ -19,6 +19,7 @@ struct TcLayer {
   CUtensorMap w_d;    // data-gradient weights [B][Ci][T][Co], taps reversed (BF16)
   CUtensorMap act_wy; // weight-gradient dy (second BF16 staging buffer)
   CUtensorMap act_f3, w_f3, act_d3, w_d3;  // halo-box forms (3x3x3 stride 1)
+  CUtensorMap wg_dy3, wg_x3;  // halo-box weight gradient: dy (8 x 3 x tz+2), x (8 x 1 x tz)
   int ci = 0, co = 0, k = 3, s = 1;
   Dims3 din{}, dout{};
   long long w_off = 0;            // weights of this conv in the FP32 theta arena
@@ -26,6 +27,9 @@ struct TcLayer {
   bool dgrad = false;             // data gradient on the tensor cores too (stride 1)
   bool wgrad = false;             // weight gradient on the tensor cores too (3x3x3, stride 1)
   int ck3f = 0, ck3d = 0;         // channel chunk of the halo-box kernel (0: per-tap kernel)
+  bool wg3 = false;               // weight gradient by the halo-box kernel
+  int ci_real = 0;                // input channels of the model (ci is padded up to 16)
+  bool input_layer = false;       // reads the padded BF16 copy of the network input (zbf)
 };
 
 // Device buffers of the BF16 path (carved from the context arena) and its layers.
@@ -33,6 +37,8 @@ struct Bf16Net {
   __nv_bfloat16* xbf = nullptr;   // BF16 staging of one convolution input (or dy)
   __nv_bfloat16* ybf = nullptr;   // BF16 staging of dy for the weight gradient
   __nv_bfloat16* wbuf = nullptr;  // BF16 weights of every tensor-core layer, per problem
+  __nv_bfloat16* zbf = nullptr;   // network input, BF16, channels padded to 16 (input layer)
+  long long zcount = 0;           // elements per problem of zbf
   long long wstride = 0;          // elements per problem in wbuf
   long long max_act = 0;          // elements per problem of the largest staged input
   int* err = nullptr;             // device error word (bounded waits that ran out)
@@ -43,6 +49,12 @@ bool bf16_network_supported(int levels, const int* widths, int c_in);
 bool bf16_conv_supported(int ci, int co, int k);
 // Register a convolution; returns its index in bf.layers or -1 when it stays on FP32 SIMT.
 int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long long w_off);
+// Register the first convolution, whose input (ci_real <= 16 channels) is fixed per problem:
+// it reads a BF16 copy padded to 16 channels, staged once by bf16_stage_input, and has no
+// data gradient.  Returns -1 when the halo-box kernels do not fit it.
+int bf16_add_input_layer(Bf16Net& bf, int ci_real, int co, Dims3 din, long long w_off);
+// z [B][n][ci_real] FP32 -> zbf [B][n][16] BF16 (zero channels ci_real..15).
+cudaError_t bf16_stage_input(Bf16Net& bf, int layer, const float* z, int B, cudaStream_t stream);
 // Reserve the BF16 buffers in the arena (base == nullptr: size only).
 void bf16_layout(Bf16Net& bf, char* base, size_t& used, int B, long long max_act);
 // Encode the TMA descriptors once the buffers have addresses.

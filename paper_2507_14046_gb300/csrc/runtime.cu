@@ -152,7 +152,7 @@ void free_arena(d2ip_ctx* c) {
 struct Builder {
   d2ip_ctx* c;
   long long off = 0;
-  ConvL conv(int ci, int co, int k, int s, int lvl_in) {
+  ConvL conv(int ci, int co, int k, int s, int lvl_in, bool input = false) {
     ConvL L;
     L.ci = ci;
     L.co = co;
@@ -161,7 +161,9 @@ struct Builder {
     L.din = c->dims[lvl_in];
     L.dout = conv_out_dims(L.din, k, s);
     L.w_off = off;
-    if (c->precision == D2IP_BF16) L.tc = bf16_add_layer(c->bf, ci, co, k, s, L.din, off);
+    if (c->precision == D2IP_BF16)
+      L.tc = input && ci < 16 ? bf16_add_input_layer(c->bf, ci, co, L.din, off)
+                              : bf16_add_layer(c->bf, ci, co, k, s, L.din, off);
     const long long fan = (long long)ci * k * k * k;
     c->table.insert(c->table.end(), {D2IP_PARAM_CONV_W, off, L.wcount(), fan});
     off += L.wcount();
@@ -200,7 +202,7 @@ void build_plan(d2ip_ctx* c) {
   c->bf = Bf16Net{};
   Builder b{c};
   const auto& w = c->w;
-  c->stem.conv = b.conv(c->c_in, w[0], 3, 1, 0);
+  c->stem.conv = b.conv(c->c_in, w[0], 3, 1, 0, /*input=*/true);
   c->stem.ln = b.ln(w[0]);
   c->stem.lvl_in = c->stem.lvl_out = 0;
   c->enc.assign(c->L, Res{});
@@ -985,6 +987,8 @@ d2ip_status d2ip_set_input(d2ip_ctx* c, const float* Zin, const float* theta0) {
   if (s) return s;
   CK(cudaMemcpyAsync(c->zin, Zin, sizeof(float) * c->B * c->n() * c->c_in, cudaMemcpyDefault,
                      c->stream));
+  if (c->stem.conv.tc >= 0 && c->bf.layers[c->stem.conv.tc].input_layer)
+    CK(bf16_stage_input(c->bf, c->stem.conv.tc, c->zin, c->B, c->stream));
   CK(copy_rows(c->theta, c->Pp, theta0, c->P, c->P, c->B, sizeof(float), c->stream));
   s = reset_optimizer(c);
   if (s) return s;
@@ -1297,6 +1301,8 @@ static d2ip_status tc_op(bool dgrad, const float* in, const float* W, const floa
                 "gradient, co <= 256 for the forward)");
   if (ws_bytes < d2ip_conv3d_tc_workspace(batch, dz, dy, dx, ci, co, ksize, stride))
     return fail(nullptr, D2IP_ERR_BAD_ARG, "workspace too small");
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15)
+    return fail(nullptr, D2IP_ERR_BAD_ARG, "input and output must be 16-byte aligned");
   const long long blk = (long long)co * ksize * ksize * ksize * ci + co;
   OPCK(bf16_op_conv(dgrad, in, W, b, out, batch, Dims3{dz, dy, dx}, ci, co, ksize, stride,
                     w_bs ? w_bs : blk, accumulate, ws, (cudaStream_t)stream));
