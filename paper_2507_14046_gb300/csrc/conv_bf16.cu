@@ -116,6 +116,33 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b
       : "memory");
 }
 
+// MMA with descriptors given as (low, high) words.  The low word holds the start address
+// >> 4 in its low 14 bits, so a shared-memory offset is added to it alone (no carry: every
+// operand lies below 256 KB); with the offsets known at compile time the issuing thread
+// spends about one add per operand on each MMA.  acc: accumulate into D (else overwrite).
+__device__ __forceinline__ void mma_lh(uint32_t tmem_d, uint32_t alo, uint32_t ahi, uint32_t blo,
+                                       uint32_t bhi, uint32_t idesc) {
+  asm volatile(
+      "{\n\t.reg .b64 a, b;\n\t"
+      "mov.b64 a, {%1, %2};\n\t"
+      "mov.b64 b, {%3, %4};\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %5, 1;\n\t}" ::"r"(tmem_d),
+      "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_lh_p(uint32_t tmem_d, uint32_t alo, uint32_t ahi,
+                                         uint32_t blo, uint32_t bhi, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .b64 a, b;\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %6, 0;\n\t"
+      "mov.b64 a, {%1, %2};\n\t"
+      "mov.b64 b, {%3, %4};\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %5, p;\n\t}" ::"r"(tmem_d),
+      "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -431,6 +458,255 @@ conv_tc3_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant_
 }
 
 // ------------------------------------------------------------------------------------
+// Persistent, warp-specialised form of the halo-box convolution.  One CTA per SM walks the
+// tiles blockIdx.x, blockIdx.x + gridDim.x, ... of all problems.  Warp 0 (one thread) keeps
+// the TMA ring full across tile boundaries, warp 1 (one thread) issues the MMAs of tile i
+// into TMEM accumulator buffer i % 2, and warps 2..5 drain the other buffer (TMEM -> bias ->
+// shared-memory staging -> coalesced global stores) while the next tile is multiplied.
+// Barriers: full/empty per ring stage (TMA <-> MMA), tfull/tempty per accumulator buffer
+// (MMA <-> epilogue).  Every wait is bounded; a wait that runs out records an error bit and
+// its role stops, the others then run out too, and before TMEM is freed the MMA thread's
+// last commit and the producer's last loads are awaited (bounded).
+// ------------------------------------------------------------------------------------
+constexpr int kP3Max = 4;
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void epi_sync() {  // the four epilogue warps only
+  asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+
+// true on every epilogue thread iff p holds on all 128 of them (named barrier 1)
+__device__ __forceinline__ bool epi_all(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred a, q;\n\t"
+      "setp.ne.u32 a, %1, 0;\n\t"
+      "bar.red.and.pred q, 1, 128, a;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(p ? 1u : 0u)
+      : "memory");
+  return r != 0;
+}
+
+template <int CK, int TZ>
+__global__ void __launch_bounds__(192, 1)
+conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
+                 const float* __restrict__ bias, float* __restrict__ out, Dims3 dout, int N,
+                 int nchunks, int tiles_x, int tiles_y, int tiles_z, int B,
+                 long long out_bs, long long bias_bs, int accumulate, int nst, uint32_t ring_bytes,
+                 int* __restrict__ err) {
+  constexpr uint32_t kRowB = CK * 2;
+  const uint32_t a_bytes = (uint32_t)(8 * 18 * (TZ + 2)) * kRowB;
+  const uint32_t b_tap = (uint32_t)N * CK * 2;
+  const uint32_t stage_bytes = a_bytes + 9 * b_tap;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  float* stg = reinterpret_cast<float*>(smem + ring_bytes);  // epilogue staging slice
+  __shared__ __align__(8) uint64_t full_bar[kP3Max], empty_bar[kP3Max], tfull[2], tempty[2],
+      done_bar;
+  __shared__ uint32_t tmem_base_s;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int per_b = tiles_x * tiles_y * tiles_z;
+  const int total = per_b * B;
+  const int ntile = blockIdx.x < total ? (total - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int ksteps = nchunks * 3;
+  const int acc_cols = TZ * N;
+  const int cols = 2 * acc_cols;
+  const uint32_t tmem_cols = cols <= 32 ? 32u : cols <= 64 ? 64u : cols <= 128 ? 128u
+                                                : cols <= 256 ? 256u : 512u;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < nst; ++q) {
+      mbar_init(smem_u32(&full_bar[q]), 1);
+      mbar_init(smem_u32(&empty_bar[q]), 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(smem_u32(&tfull[q]), 1);
+      mbar_init(smem_u32(&tempty[q]), 128);
+    }
+    mbar_init(smem_u32(&done_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_s)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      int k = 0;      // ring position, continuous over tiles
+      bool good = true;
+      for (int i = 0; i < ntile && good; ++i) {
+        int tile = blockIdx.x + i * gridDim.x;
+        const int b = tile / per_b;
+        tile %= per_b;
+        const int x0 = (tile % tiles_x) * 8;
+        tile /= tiles_x;
+        const int y0 = (tile % tiles_y) * 16;
+        const int z0 = (tile / tiles_y) * TZ;
+        for (int j = 0; j < ksteps; ++j, ++k) {
+          const int st = k % nst, round = k / nst;
+          if (round > 0 && !mbar_wait(smem_u32(&empty_bar[st]), (round - 1) & 1)) {
+            atomicOr(err, kErrProducer);
+            good = false;
+            break;
+          }
+          const int c = j / 3, kx = j % 3;
+          const uint32_t dst = smem_u32(smem + (size_t)st * stage_bytes);
+          const uint32_t fb = smem_u32(&full_bar[st]);
+          mbar_expect_tx(fb, stage_bytes);
+          tma_load_5d(dst, &tm_a, c * CK, x0 + kx - 1, y0 - 1, z0 - 1, b, fb);
+          tma_load_4d(dst + a_bytes, &tm_b, c * CK, 0, kx, b, fb);
+        }
+      }
+      // the last loads issued into each stage have landed before the CTA may exit
+      for (int q = 0; q < nst && q < k; ++q) {
+        const int last = k - 1 - ((k - 1 - q) % nst + nst) % nst;  // last k with k % nst == q
+        if (!mbar_wait(smem_u32(&full_bar[q]), (last / nst) & 1)) atomicOr(err, kErrProducer);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      const uint32_t idesc = instr_desc(N);
+      int k = 0;
+      bool good = true;
+      for (int i = 0; i < ntile && good; ++i) {
+        const int buf = i & 1;
+        if (i >= 2 && !mbar_wait(smem_u32(&tempty[buf]), ((i >> 1) - 1) & 1)) {
+          atomicOr(err, kErrMma);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dbase = tmem + (uint32_t)(buf * acc_cols);
+        for (int j = 0; j < ksteps; ++j, ++k) {
+          const int st = k % nst;
+          if (!mbar_wait(smem_u32(&full_bar[st]), (k / nst) & 1)) {
+            atomicOr(err, kErrMma);
+            good = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_addr = smem_u32(smem + (size_t)st * stage_bytes);
+          const uint64_t a0 = smem_desc<CK>(a_addr), b0 = smem_desc<CK>(a_addr + a_bytes);
+          const uint32_t alo = (uint32_t)a0, ahi = (uint32_t)(a0 >> 32);
+          const uint32_t blo = (uint32_t)b0, bhi = (uint32_t)(b0 >> 32);
+          const uint32_t bt = b_tap >> 4;
+          // tap t = kx + 3 q (kz = q / 3, ky = q % 3), slice zz, K step kk: all offsets but
+          // the weight tap stride are compile-time constants
+#pragma unroll
+          for (int q = 0; q < 9; ++q)
+#pragma unroll
+            for (int zz = 0; zz < TZ; ++zz)
+#pragma unroll
+              for (int kk = 0; kk < CK / 16; ++kk) {
+                constexpr uint32_t kAtom = 8 * kRowB >> 4;
+                const uint32_t ao = (uint32_t)(((zz + q / 3) * 18 + (q % 3)) * kAtom + kk * 2);
+                const uint32_t bo = (uint32_t)q * bt + (uint32_t)(kk * 2);
+                const uint32_t d = dbase + (uint32_t)(zz * N);
+                if (q == 0 && kk == 0)
+                  mma_lh_p(d, alo + ao, ahi, blo + bo, bhi, idesc, j > 0 ? 1u : 0u);
+                else
+                  mma_lh(d, alo + ao, ahi, blo + bo, bhi, idesc);
+              }
+          mma_commit(smem_u32(&empty_bar[st]));
+        }
+        if (good) mma_commit(smem_u32(&tfull[buf]));
+      }
+      mma_commit(smem_u32(&done_bar));  // fires once every issued MMA has completed
+    }
+  } else {  // epilogue warps 2..5: TMEM lane quadrant warp % 4
+    const int quad = warp & 3;
+    const int m = quad * 32 + lane;  // tile row = y * 8 + x
+    const int tid = threadIdx.x - 64;
+    const int ld = N + 4;
+    const int n4 = N / 4;
+    for (int i = 0; i < ntile; ++i) {
+      const int buf = i & 1;
+      const bool ok = epi_all(mbar_wait(smem_u32(&tfull[buf]), (i >> 1) & 1));
+      if (!ok) {  // uniform over the four warps, so none is left at a named barrier
+        if (tid == 0) atomicOr(err, kErrEpilogue);
+        break;
+      }
+      tc_fence_after();
+      int tile = blockIdx.x + i * gridDim.x;
+      const int b = tile / per_b;
+      tile %= per_b;
+      const int x0 = (tile % tiles_x) * 8;
+      tile /= tiles_x;
+      const int y0 = (tile % tiles_y) * 16;
+      const int z0 = (tile / tiles_y) * TZ;
+      const float* bb = bias ? bias + (long long)b * bias_bs : nullptr;
+      for (int zz = 0; zz < TZ; ++zz) {
+        for (int c0 = 0; c0 < N; c0 += 16) {
+          uint32_t r[16];
+          tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * acc_cols + zz * N + c0),
+                    r);
+#pragma unroll
+          for (int j = 0; j < 16; j += 4) {
+            float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                   __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+            if (bb) {
+              v.x += __ldg(bb + c0 + j), v.y += __ldg(bb + c0 + j + 1);
+              v.z += __ldg(bb + c0 + j + 2), v.w += __ldg(bb + c0 + j + 3);
+            }
+            *reinterpret_cast<float4*>(stg + m * ld + c0 + j) = v;
+          }
+        }
+        if (zz == TZ - 1) {  // all of this buffer is in registers/shared: hand it back
+          tc_fence_before();
+          mbar_arrive(smem_u32(&tempty[buf]));
+        }
+        epi_sync();
+        const int oz = z0 + zz;
+        if (oz < dout.z) {
+          for (int e = tid; e < 128 * n4; e += 128) {
+            const int mv = e / n4, c4 = e % n4;
+            const int ox = x0 + mv % 8, oy = y0 + mv / 8;
+            if (ox >= dout.x || oy >= dout.y) continue;
+            float4 v = *reinterpret_cast<const float4*>(stg + mv * ld + c4 * 4);
+            float4* o = reinterpret_cast<float4*>(
+                            out + (long long)b * out_bs +
+                            (((long long)oz * dout.y + oy) * dout.x + ox) * N) + c4;
+            if (accumulate) {
+              const float4 p = *o;
+              v.x += p.x, v.y += p.y, v.z += p.z, v.w += p.w;
+            }
+            *o = v;
+          }
+        }
+        epi_sync();
+      }
+    }
+  }
+  __syncwarp();
+  // TMEM is freed only after every issued MMA has completed
+  if (warp == 1) {
+    const bool fin = __all_sync(0xffffffffu, mbar_wait(smem_u32(&done_bar), 0));
+    if (!fin && lane == 0) atomicOr(err, kErrEpilogue);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(tmem_cols)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------------------------
 // weight gradient on the tensor cores (stride-1 layers)
 //
 // With u = v + offset(t), dW[co][t][ci] = sum_u dy[u - offset(t)][co] x[u][ci]: the tap
@@ -630,7 +906,7 @@ struct Wg3Geom {
   uint32_t a_box, b_box, b_off, ones_off, stage, tmem_cols;
 };
 
-template <int CKA, int CKB>
+template <int CKA, int CKB, int NKX>
 __global__ void __launch_bounds__(128, 1)
 wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant__ CUtensorMap tm_x,
                  float* __restrict__ part, Dims3 d, int Ci, int ci_out,
@@ -647,7 +923,7 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
   __shared__ __align__(8) uint64_t full_bar[kWg3MaxStages], empty_bar[kWg3MaxStages], done_bar;
   __shared__ uint32_t tmem_base_s;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int chunk = blockIdx.x, kx0 = blockIdx.y * gm.nkx, b = blockIdx.z;
+  const int chunk = blockIdx.x, kx0 = blockIdx.y * NKX, b = blockIdx.z;
   const int tile0 = chunk * gm.tiles_per_chunk;
   const int tile1 = min(tile0 + gm.tiles_per_chunk, gm.ntiles);
   const int ksteps = max(tile1 - tile0, 0);
@@ -679,7 +955,7 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
   const uint32_t tmem = tmem_base_s;
 
   if (warp == 0 && lane == 0) {  // TMA producer
-    const uint32_t tx_bytes = (uint32_t)gm.nkx * gm.a_box + (uint32_t)nb * gm.b_box;
+    const uint32_t tx_bytes = (uint32_t)NKX * gm.a_box + (uint32_t)nb * gm.b_box;
     for (int k = 0; k < ksteps; ++k) {
       const int s = k % nst, round = k / nst;
       if (round > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (round - 1) & 1)) {
@@ -693,7 +969,7 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
       const uint32_t base = smem_u32(smem + (size_t)s * gm.stage);
       const uint32_t fb = smem_u32(&full_bar[s]);
       mbar_expect_tx(fb, tx_bytes);
-      for (int q = 0; q < gm.nkx; ++q)
+      for (int q = 0; q < NKX; ++q)
         tma_load_5d(base + (uint32_t)q * gm.a_box, &tm_dy, 0, x0 + 1 - (kx0 + q), y0 - 1, z0 - 1,
                     b, fb);
       for (int c = 0; c < nb; ++c)
@@ -709,23 +985,28 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
       }
       tc_fence_after();
       const uint32_t base = smem_u32(smem + (size_t)s * gm.stage);
-      // descriptors are linear in the address (start >> 4 in the low field): offset a base
+      // descriptors are linear in the address (start >> 4 in the low word): offset a base
       const uint64_t a0 = smem_desc_mn2<CKA>(base, kAtomA, 3 * kAtomA);
       const uint64_t b0 = smem_desc_mn2<CKB>(base + gm.b_off, gm.b_box, kAtomB);
+      const uint32_t ahi = (uint32_t)(a0 >> 32), bhi = (uint32_t)(b0 >> 32);
+      const uint32_t abx = gm.a_box >> 4;
+      uint32_t alo = (uint32_t)a0, blo = (uint32_t)b0;
       for (int kk = 0; kk < gm.tz / 2; ++kk) {  // K = 16 voxels = z offsets 2kk, 2kk + 1
-        const uint64_t db = b0 + ((kk * 2 * kAtomB) >> 4);
-        const uint64_t ak = a0 + ((kk * 6 * kAtomA) >> 4);
-        const uint32_t acc = (k > 0 || kk > 0) ? 1u : 0u;
-        for (int q = 0; q < gm.nkx; ++q) {
-          const uint64_t aq = ak + ((q * gm.a_box) >> 4);
+#pragma unroll
+        for (int q = 0; q < NKX; ++q)
 #pragma unroll
           for (int g = 0; g < kG; ++g) {
             constexpr int kLast = 9 - kTpm;
             const int s0 = g * kTpm < kLast ? g * kTpm : kLast;
-            mma_bf16(tmem + (uint32_t)((q * kG + g) * N), aq + ((s0 * kAtomA) >> 4), db, idesc,
-                     acc);
+            const uint32_t ao = (uint32_t)q * abx + (uint32_t)((s0 * kAtomA) >> 4);
+            const uint32_t d = tmem + (uint32_t)((q * kG + g) * N);
+            if (kk == 0)
+              mma_lh_p(d, alo + ao, ahi, blo, bhi, idesc, k > 0 ? 1u : 0u);
+            else
+              mma_lh(d, alo + ao, ahi, blo, bhi, idesc);
           }
-        }
+        alo += (6 * kAtomA) >> 4;  // next two z offsets: 6 dy atoms, 2 x atoms
+        blo += (2 * kAtomB) >> 4;
       }
       mma_commit(smem_u32(&empty_bar[s]));
     }
@@ -742,7 +1023,7 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
   const int pl = m / Co, co = m % Co;
   const long long row = (long long)Co * 27 * ci_out + Co;  // the first ci_out channels
   float* prow = part + ((long long)b * gm.nchunks + chunk) * row;
-  for (int q = 0; q < gm.nkx; ++q)
+  for (int q = 0; q < NKX; ++q)
     for (int g = 0; g < kG; ++g) {
       const int s0 = g * kTpm < 9 - kTpm ? g * kTpm : 9 - kTpm;
       const int p = s0 + pl;                      // window p <-> tap 3 kz + ky = 8 - p
@@ -945,10 +1226,35 @@ int tc3_tz(int ck, int n, int Z) {
   return best;
 }
 
+int sm_count();
+
+// Persistent form when two ring stages and the staging slice fit; else one tile per CTA.
 cudaError_t launch_tc3(const CUtensorMap& a, const CUtensorMap& w, int cin, int ck,
                        const float* bias, float* out, Dims3 dout, int n, int B, long long out_bs,
                        long long bias_bs, int acc, int* err, cudaStream_t st) {
   const int tz = tc3_tz(ck, n, dout.z);
+  {
+    const size_t stage = tc3_stage(ck, n, tz), staging = (size_t)128 * (n + 4) * 4;
+    const int nst = (int)std::min<size_t>(kP3Max, (kTc3SmemMax - 1024 - staging) / stage);
+    if (nst >= 2) {
+      const int tx = (int)ceil_div(dout.x, 8), ty = (int)ceil_div(dout.y, 16),
+                tzn = (int)ceil_div(dout.z, tz);
+      const long long total = (long long)tx * ty * tzn * B;
+      const int grid = (int)std::min<long long>(total, sm_count());
+      const uint32_t ring = (uint32_t)(nst * stage);
+      const size_t sm = ring + staging + 1024;
+      const int nch = cin / ck;
+#define D2IP_P3(CK_, TZ_)                                                                  \
+  conv_tc3p_kernel<CK_, TZ_><<<grid, 192, sm, st>>>(a, w, bias, out, dout, n, nch, tx, ty, tzn, \
+                                                    B, out_bs, bias_bs, acc, nst, ring, err)
+#define D2IP_P3Z(CK_) \
+  if (tz == 4) D2IP_P3(CK_, 4); else if (tz == 2) D2IP_P3(CK_, 2); else D2IP_P3(CK_, 1)
+      if (ck == 64) { D2IP_P3Z(64); } else if (ck == 32) { D2IP_P3Z(32); } else { D2IP_P3Z(16); }
+#undef D2IP_P3Z
+#undef D2IP_P3
+      return cudaGetLastError();
+    }
+  }
   const int tx = (int)ceil_div(dout.x, 8), ty = (int)ceil_div(dout.y, 16);
   dim3 grid((unsigned)(tx * ty * ceil_div(dout.z, tz)), 1, B);
   const size_t stage = tc3_stage(ck, n, tz);
@@ -1278,8 +1584,13 @@ Wg3Geom wg3_geom(const TcLayer& L, int B) {
 
 template <int CKA, int CKB>
 cudaError_t wg3_attr() {
-  return cudaFuncSetAttribute(wgrad_tc3_kernel<CKA, CKB>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWg3SmemMax);
+  cudaError_t e = cudaFuncSetAttribute(wgrad_tc3_kernel<CKA, CKB, 1>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kWg3SmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(wgrad_tc3_kernel<CKA, CKB, 3>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWg3SmemMax);
+  return e;
 }
 
 template <int CKA, int CKB>
@@ -1287,8 +1598,12 @@ void launch_wg3(const TcLayer& L, const Wg3Geom& g, float* part, int B, int* err
                 cudaStream_t st) {
   dim3 grid((unsigned)g.nchunks, (unsigned)(3 / g.nkx), (unsigned)B);
   const size_t smem = (size_t)g.nst * g.stage + 1024;
-  wgrad_tc3_kernel<CKA, CKB><<<grid, 128, smem, st>>>(L.wg_dy3, L.wg_x3, part, L.dout, L.ci,
-                                                      L.ci_real, g, err);
+  if (g.nkx == 3)
+    wgrad_tc3_kernel<CKA, CKB, 3><<<grid, 128, smem, st>>>(L.wg_dy3, L.wg_x3, part, L.dout, L.ci,
+                                                           L.ci_real, g, err);
+  else
+    wgrad_tc3_kernel<CKA, CKB, 1><<<grid, 128, smem, st>>>(L.wg_dy3, L.wg_x3, part, L.dout, L.ci,
+                                                           L.ci_real, g, err);
 }
 
 }  // namespace
@@ -1355,6 +1670,13 @@ cudaError_t bf16_prepare_kernels() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(conv_tc3_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kTc3SmemMax);
+#define D2IP_P3A(CK_, TZ_)                                                          \
+  if (e == cudaSuccess)                                                             \
+    e = cudaFuncSetAttribute(conv_tc3p_kernel<CK_, TZ_>,                            \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc3SmemMax);
+  D2IP_P3A(64, 1) D2IP_P3A(64, 2) D2IP_P3A(64, 4) D2IP_P3A(32, 1) D2IP_P3A(32, 2)
+  D2IP_P3A(32, 4) D2IP_P3A(16, 1) D2IP_P3A(16, 2) D2IP_P3A(16, 4)
+#undef D2IP_P3A
   if (e == cudaSuccess) e = wgrad_attr<16, 16>();
   if (e == cudaSuccess) e = wgrad_attr<16, 32>();
   if (e == cudaSuccess) e = wgrad_attr<16, 64>();
