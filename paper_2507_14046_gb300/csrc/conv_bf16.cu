@@ -492,30 +492,48 @@ __device__ __forceinline__ bool epi_all(bool p) {
   return r != 0;
 }
 
+// Launch arguments of the persistent halo convolution.  mode 0: y = conv(x) + bias.
+// mode 1 (forward of a block with a 1x1 projection of the same input): also
+// y_p = W_p x + bias_p, from one more MMA per slice on the centre window of the kx = 1 stage.
+// mode 2 (data gradient of such a block): dx = conv^T(dz) + W_p^T dz_p, the second term from
+// one more stage per channel chunk (the dz_p box of the tile, no halo).
+struct P3Args {
+  const float* bias;
+  float* out;
+  const float* bias_p;
+  float* out_p;
+  int* err;
+  Dims3 dout;
+  int N, Np, nchunks, tiles_x, tiles_y, tiles_z, B, accumulate, nst, mode;
+  uint32_t ring_bytes, stage_bytes;
+  long long out_bs, bias_bs, outp_bs, biasp_bs;
+};
+
 template <int CK, int TZ>
 __global__ void __launch_bounds__(192, 1)
 conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
-                 const float* __restrict__ bias, float* __restrict__ out, Dims3 dout, int N,
-                 int nchunks, int tiles_x, int tiles_y, int tiles_z, int B,
-                 long long out_bs, long long bias_bs, int accumulate, int nst, uint32_t ring_bytes,
-                 int* __restrict__ err) {
+                 const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorMap tm_a2,
+                 const __grid_constant__ P3Args g) {
   constexpr uint32_t kRowB = CK * 2;
-  const uint32_t a_bytes = (uint32_t)(8 * 18 * (TZ + 2)) * kRowB;
+  constexpr uint32_t a_bytes = (uint32_t)(8 * 18 * (TZ + 2)) * kRowB;
+  const int N = g.N, Np = g.mode == 1 ? g.Np : 0;
   const uint32_t b_tap = (uint32_t)N * CK * 2;
-  const uint32_t stage_bytes = a_bytes + 9 * b_tap;
+  const uint32_t stage_bytes = g.stage_bytes;
+  const int spc = g.mode == 2 ? 4 : 3;  // stages per channel chunk
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  float* stg = reinterpret_cast<float*>(smem + ring_bytes);  // epilogue staging slice
+  float* stg = reinterpret_cast<float*>(smem + g.ring_bytes);  // epilogue staging slice
   __shared__ __align__(8) uint64_t full_bar[kP3Max], empty_bar[kP3Max], tfull[2], tempty[2],
       done_bar;
   __shared__ uint32_t tmem_base_s;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int per_b = tiles_x * tiles_y * tiles_z;
-  const int total = per_b * B;
+  const int per_b = g.tiles_x * g.tiles_y * g.tiles_z;
+  const int total = per_b * g.B;
   const int ntile = blockIdx.x < total ? (total - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const int ksteps = nchunks * 3;
-  const int acc_cols = TZ * N;
+  const int ksteps = g.nchunks * spc;
+  const int nst = g.nst;
+  const int acc_cols = TZ * (N + Np);  // one accumulator buffer: TZ slices of N (+ Np)
   const int cols = 2 * acc_cols;
   const uint32_t tmem_cols = cols <= 32 ? 32u : cols <= 64 ? 64u : cols <= 128 ? 128u
                                                 : cols <= 256 ? 256u : 512u;
@@ -548,44 +566,54 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
     if (lane == 0) {  // TMA producer
       int k = 0;      // ring position, continuous over tiles
       bool good = true;
+      const uint32_t wp_bytes = (uint32_t)Np * CK * 2;
+      const uint32_t a2_bytes = (uint32_t)(128 * TZ) * kRowB + b_tap;
       for (int i = 0; i < ntile && good; ++i) {
         int tile = blockIdx.x + i * gridDim.x;
         const int b = tile / per_b;
         tile %= per_b;
-        const int x0 = (tile % tiles_x) * 8;
-        tile /= tiles_x;
-        const int y0 = (tile % tiles_y) * 16;
-        const int z0 = (tile / tiles_y) * TZ;
+        const int x0 = (tile % g.tiles_x) * 8;
+        tile /= g.tiles_x;
+        const int y0 = (tile % g.tiles_y) * 16;
+        const int z0 = (tile / g.tiles_y) * TZ;
         for (int j = 0; j < ksteps; ++j, ++k) {
           const int st = k % nst, round = k / nst;
           if (round > 0 && !mbar_wait(smem_u32(&empty_bar[st]), (round - 1) & 1)) {
-            atomicOr(err, kErrProducer);
+            atomicOr(g.err, kErrProducer);
             good = false;
             break;
           }
-          const int c = j / 3, kx = j % 3;
+          const int c = j / spc, kx = j % spc;
           const uint32_t dst = smem_u32(smem + (size_t)st * stage_bytes);
           const uint32_t fb = smem_u32(&full_bar[st]);
-          mbar_expect_tx(fb, stage_bytes);
-          tma_load_5d(dst, &tm_a, c * CK, x0 + kx - 1, y0 - 1, z0 - 1, b, fb);
-          tma_load_4d(dst + a_bytes, &tm_b, c * CK, 0, kx, b, fb);
+          if (kx == 3) {  // mode 2: dz_p box of the tile and W_p^T chunk c
+            mbar_expect_tx(fb, a2_bytes);
+            tma_load_5d(dst, &tm_a2, c * CK, x0, y0, z0, b, fb);
+            tma_load_4d(dst + (uint32_t)(128 * TZ) * kRowB, &tm_p, c * CK, 0, 0, b, fb);
+          } else {
+            const bool wp = Np > 0 && kx == 1;
+            mbar_expect_tx(fb, a_bytes + 9 * b_tap + (wp ? wp_bytes : 0u));
+            tma_load_5d(dst, &tm_a, c * CK, x0 + kx - 1, y0 - 1, z0 - 1, b, fb);
+            tma_load_4d(dst + a_bytes, &tm_b, c * CK, 0, kx, b, fb);
+            if (wp) tma_load_4d(dst + a_bytes + 9 * b_tap, &tm_p, c * CK, 0, 0, b, fb);
+          }
         }
       }
       // the last loads issued into each stage have landed before the CTA may exit
       for (int q = 0; q < nst && q < k; ++q) {
         const int last = k - 1 - ((k - 1 - q) % nst + nst) % nst;  // last k with k % nst == q
-        if (!mbar_wait(smem_u32(&full_bar[q]), (last / nst) & 1)) atomicOr(err, kErrProducer);
+        if (!mbar_wait(smem_u32(&full_bar[q]), (last / nst) & 1)) atomicOr(g.err, kErrProducer);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
-      const uint32_t idesc = instr_desc(N);
+      const uint32_t idesc = instr_desc(N), idesc_p = instr_desc(Np > 0 ? Np : 16);
       int k = 0;
       bool good = true;
       for (int i = 0; i < ntile && good; ++i) {
         const int buf = i & 1;
         if (i >= 2 && !mbar_wait(smem_u32(&tempty[buf]), ((i >> 1) - 1) & 1)) {
-          atomicOr(err, kErrMma);
+          atomicOr(g.err, kErrMma);
           break;
         }
         tc_fence_after();
@@ -593,33 +621,64 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
         for (int j = 0; j < ksteps; ++j, ++k) {
           const int st = k % nst;
           if (!mbar_wait(smem_u32(&full_bar[st]), (k / nst) & 1)) {
-            atomicOr(err, kErrMma);
+            atomicOr(g.err, kErrMma);
             good = false;
             break;
           }
           tc_fence_after();
+          const int kx = j % spc;
           const uint32_t a_addr = smem_u32(smem + (size_t)st * stage_bytes);
-          const uint64_t a0 = smem_desc<CK>(a_addr), b0 = smem_desc<CK>(a_addr + a_bytes);
+          const uint64_t a0 = smem_desc<CK>(a_addr);
           const uint32_t alo = (uint32_t)a0, ahi = (uint32_t)(a0 >> 32);
-          const uint32_t blo = (uint32_t)b0, bhi = (uint32_t)(b0 >> 32);
-          const uint32_t bt = b_tap >> 4;
-          // tap t = kx + 3 q (kz = q / 3, ky = q % 3), slice zz, K step kk: all offsets but
-          // the weight tap stride are compile-time constants
-#pragma unroll
-          for (int q = 0; q < 9; ++q)
+          if (kx == 3) {  // W_p^T dz_p: slice zz is rows [128 zz, 128 zz + 128) of the box
+            const uint64_t b0 = smem_desc<CK>(a_addr + (uint32_t)(128 * TZ) * kRowB);
+            const uint32_t blo = (uint32_t)b0, bhi = (uint32_t)(b0 >> 32);
 #pragma unroll
             for (int zz = 0; zz < TZ; ++zz)
 #pragma unroll
-              for (int kk = 0; kk < CK / 16; ++kk) {
-                constexpr uint32_t kAtom = 8 * kRowB >> 4;
-                const uint32_t ao = (uint32_t)(((zz + q / 3) * 18 + (q % 3)) * kAtom + kk * 2);
-                const uint32_t bo = (uint32_t)q * bt + (uint32_t)(kk * 2);
-                const uint32_t d = dbase + (uint32_t)(zz * N);
-                if (q == 0 && kk == 0)
-                  mma_lh_p(d, alo + ao, ahi, blo + bo, bhi, idesc, j > 0 ? 1u : 0u);
-                else
-                  mma_lh(d, alo + ao, ahi, blo + bo, bhi, idesc);
-              }
+              for (int kk = 0; kk < CK / 16; ++kk)
+                mma_lh(dbase + (uint32_t)(zz * N),
+                       alo + (uint32_t)(zz * 16 * (8 * kRowB >> 4) + kk * 2), ahi,
+                       blo + (uint32_t)(kk * 2), bhi, idesc);
+          } else {
+            const uint64_t b0 = smem_desc<CK>(a_addr + a_bytes);
+            const uint32_t blo = (uint32_t)b0, bhi = (uint32_t)(b0 >> 32);
+            const uint32_t bt = b_tap >> 4;
+            const uint32_t first = j >= spc ? 1u : 0u;  // a later chunk accumulates
+            // tap t = kx + 3 q (kz = q / 3, ky = q % 3), slice zz, K step kk: all offsets but
+            // the weight tap stride are compile-time constants
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+#pragma unroll
+              for (int zz = 0; zz < TZ; ++zz)
+#pragma unroll
+                for (int kk = 0; kk < CK / 16; ++kk) {
+                  constexpr uint32_t kAtom = 8 * kRowB >> 4;
+                  const uint32_t ao = (uint32_t)(((zz + q / 3) * 18 + (q % 3)) * kAtom + kk * 2);
+                  const uint32_t bo = (uint32_t)q * bt + (uint32_t)(kk * 2);
+                  const uint32_t d = dbase + (uint32_t)(zz * N);
+                  if (q == 0 && kk == 0)
+                    mma_lh_p(d, alo + ao, ahi, blo + bo, bhi, idesc, (j > 0) ? 1u : 0u);
+                  else
+                    mma_lh(d, alo + ao, ahi, blo + bo, bhi, idesc);
+                }
+            if (Np > 0 && kx == 1) {  // projection: the centre window (q = 4) of each slice
+              const uint64_t p0 = smem_desc<CK>(a_addr + a_bytes + 9 * b_tap);
+              const uint32_t plo = (uint32_t)p0, phi = (uint32_t)(p0 >> 32);
+#pragma unroll
+              for (int zz = 0; zz < TZ; ++zz)
+#pragma unroll
+                for (int kk = 0; kk < CK / 16; ++kk) {
+                  constexpr uint32_t kAtom = 8 * kRowB >> 4;
+                  const uint32_t ao = (uint32_t)(((zz + 1) * 18 + 1) * kAtom + kk * 2);
+                  const uint32_t d = dbase + (uint32_t)(TZ * N + zz * Np);
+                  if (kk == 0)
+                    mma_lh_p(d, alo + ao, ahi, plo, phi, idesc_p, first);
+                  else
+                    mma_lh(d, alo + ao, ahi, plo + (uint32_t)(kk * 2), phi, idesc_p);
+                }
+            }
+          }
           mma_commit(smem_u32(&empty_bar[st]));
         }
         if (good) mma_commit(smem_u32(&tfull[buf]));
@@ -630,63 +689,69 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
     const int quad = warp & 3;
     const int m = quad * 32 + lane;  // tile row = y * 8 + x
     const int tid = threadIdx.x - 64;
-    const int ld = N + 4;
-    const int n4 = N / 4;
+    const Dims3 dout = g.dout;
     for (int i = 0; i < ntile; ++i) {
       const int buf = i & 1;
       const bool ok = epi_all(mbar_wait(smem_u32(&tfull[buf]), (i >> 1) & 1));
       if (!ok) {  // uniform over the four warps, so none is left at a named barrier
-        if (tid == 0) atomicOr(err, kErrEpilogue);
+        if (tid == 0) atomicOr(g.err, kErrEpilogue);
         break;
       }
       tc_fence_after();
       int tile = blockIdx.x + i * gridDim.x;
       const int b = tile / per_b;
       tile %= per_b;
-      const int x0 = (tile % tiles_x) * 8;
-      tile /= tiles_x;
-      const int y0 = (tile % tiles_y) * 16;
-      const int z0 = (tile / tiles_y) * TZ;
-      const float* bb = bias ? bias + (long long)b * bias_bs : nullptr;
-      for (int zz = 0; zz < TZ; ++zz) {
-        for (int c0 = 0; c0 < N; c0 += 16) {
-          uint32_t r[16];
-          tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * acc_cols + zz * N + c0),
-                    r);
+      const int x0 = (tile % g.tiles_x) * 8;
+      tile /= g.tiles_x;
+      const int y0 = (tile % g.tiles_y) * 16;
+      const int z0 = (tile / g.tiles_y) * TZ;
+      for (int part = 0; part < (Np > 0 ? 2 : 1); ++part) {
+        const int nc = part ? Np : N;
+        const int ld = nc + 4;  // padded staging row (floats)
+        const int n4 = nc / 4;
+        const float* bb = part ? (g.bias_p ? g.bias_p + (long long)b * g.biasp_bs : nullptr)
+                               : (g.bias ? g.bias + (long long)b * g.bias_bs : nullptr);
+        float* dst = part ? g.out_p + (long long)b * g.outp_bs : g.out + (long long)b * g.out_bs;
+        const int accum = part ? 0 : g.accumulate;
+        for (int zz = 0; zz < TZ; ++zz) {
+          const int col0 = buf * acc_cols + (part ? TZ * N + zz * Np : zz * N);
+          for (int c0 = 0; c0 < nc; c0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(col0 + c0), r);
 #pragma unroll
-          for (int j = 0; j < 16; j += 4) {
-            float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                   __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-            if (bb) {
-              v.x += __ldg(bb + c0 + j), v.y += __ldg(bb + c0 + j + 1);
-              v.z += __ldg(bb + c0 + j + 2), v.w += __ldg(bb + c0 + j + 3);
+            for (int j = 0; j < 16; j += 4) {
+              float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                     __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+              if (bb) {
+                v.x += __ldg(bb + c0 + j), v.y += __ldg(bb + c0 + j + 1);
+                v.z += __ldg(bb + c0 + j + 2), v.w += __ldg(bb + c0 + j + 3);
+              }
+              *reinterpret_cast<float4*>(stg + m * ld + c0 + j) = v;
             }
-            *reinterpret_cast<float4*>(stg + m * ld + c0 + j) = v;
           }
-        }
-        if (zz == TZ - 1) {  // all of this buffer is in registers/shared: hand it back
-          tc_fence_before();
-          mbar_arrive(smem_u32(&tempty[buf]));
-        }
-        epi_sync();
-        const int oz = z0 + zz;
-        if (oz < dout.z) {
-          for (int e = tid; e < 128 * n4; e += 128) {
-            const int mv = e / n4, c4 = e % n4;
-            const int ox = x0 + mv % 8, oy = y0 + mv / 8;
-            if (ox >= dout.x || oy >= dout.y) continue;
-            float4 v = *reinterpret_cast<const float4*>(stg + mv * ld + c4 * 4);
-            float4* o = reinterpret_cast<float4*>(
-                            out + (long long)b * out_bs +
-                            (((long long)oz * dout.y + oy) * dout.x + ox) * N) + c4;
-            if (accumulate) {
-              const float4 p = *o;
-              v.x += p.x, v.y += p.y, v.z += p.z, v.w += p.w;
+          if (zz == TZ - 1 && part == (Np > 0 ? 1 : 0)) {  // buffer fully read: hand it back
+            tc_fence_before();
+            mbar_arrive(smem_u32(&tempty[buf]));
+          }
+          epi_sync();
+          const int oz = z0 + zz;
+          if (oz < dout.z) {
+            for (int e = tid; e < 128 * n4; e += 128) {
+              const int mv = e / n4, c4 = e % n4;
+              const int ox = x0 + mv % 8, oy = y0 + mv / 8;
+              if (ox >= dout.x || oy >= dout.y) continue;
+              float4 v = *reinterpret_cast<const float4*>(stg + mv * ld + c4 * 4);
+              float4* o = reinterpret_cast<float4*>(
+                              dst + (((long long)oz * dout.y + oy) * dout.x + ox) * nc) + c4;
+              if (accum) {
+                const float4 p = *o;
+                v.x += p.x, v.y += p.y, v.z += p.z, v.w += p.w;
+              }
+              *o = v;
             }
-            *o = v;
           }
+          epi_sync();
         }
-        epi_sync();
       }
     }
   }
@@ -694,7 +759,7 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
   // TMEM is freed only after every issued MMA has completed
   if (warp == 1) {
     const bool fin = __all_sync(0xffffffffu, mbar_wait(smem_u32(&done_bar), 0));
-    if (!fin && lane == 0) atomicOr(err, kErrEpilogue);
+    if (!fin && lane == 0) atomicOr(g.err, kErrEpilogue);
   }
   tc_fence_before();
   __syncthreads();
@@ -1228,33 +1293,76 @@ int tc3_tz(int ck, int n, int Z) {
 
 int sm_count();
 
-// Persistent form when two ring stages and the staging slice fit; else one tile per CTA.
-cudaError_t launch_tc3(const CUtensorMap& a, const CUtensorMap& w, int cin, int ck,
-                       const float* bias, float* out, Dims3 dout, int n, int B, long long out_bs,
-                       long long bias_bs, int acc, int* err, cudaStream_t st) {
-  const int tz = tc3_tz(ck, n, dout.z);
-  {
-    const size_t stage = tc3_stage(ck, n, tz), staging = (size_t)128 * (n + 4) * 4;
-    const int nst = (int)std::min<size_t>(kP3Max, (kTc3SmemMax - 1024 - staging) / stage);
-    if (nst >= 2) {
-      const int tx = (int)ceil_div(dout.x, 8), ty = (int)ceil_div(dout.y, 16),
-                tzn = (int)ceil_div(dout.z, tz);
-      const long long total = (long long)tx * ty * tzn * B;
-      const int grid = (int)std::min<long long>(total, sm_count());
-      const uint32_t ring = (uint32_t)(nst * stage);
-      const size_t sm = ring + staging + 1024;
-      const int nch = cin / ck;
-#define D2IP_P3(CK_, TZ_)                                                                  \
-  conv_tc3p_kernel<CK_, TZ_><<<grid, 192, sm, st>>>(a, w, bias, out, dout, n, nch, tx, ty, tzn, \
-                                                    B, out_bs, bias_bs, acc, nst, ring, err)
-#define D2IP_P3Z(CK_) \
-  if (tz == 4) D2IP_P3(CK_, 4); else if (tz == 2) D2IP_P3(CK_, 2); else D2IP_P3(CK_, 1)
-      if (ck == 64) { D2IP_P3Z(64); } else if (ck == 32) { D2IP_P3Z(32); } else { D2IP_P3Z(16); }
-#undef D2IP_P3Z
-#undef D2IP_P3
-      return cudaGetLastError();
+// Halo-box launch geometry.  The persistent kernel is planned first: over z depths tz in
+// {4, 2, 1} (accumulators of both TMEM buffers within 512 columns) and channel chunks ck
+// dividing cin, with at least two ring stages besides the epilogue staging slice, pick the
+// least TMA time per output voxel -- rows loaded per z column (halo box of tz + 2 planes per
+// x tap, plus the weight boxes) over the TMA line rate (one 32-byte row per clock for ck = 16,
+// 64 bytes for wider chunks).  Otherwise one tile per CTA (np must be 0 then).
+struct Tc3Plan {
+  int ck = 0, tz = 1, nst = 0;
+  size_t stage = 0, staging = 0;
+  bool persistent = false;
+};
+
+Tc3Plan tc3_plan(int cin, int n, int np, int Z) {
+  Tc3Plan best;
+  double best_cost = 1e300;
+  const size_t staging = (size_t)128 * (std::max(n, np) + 4) * 4;
+  for (int tz : {4, 2, 1}) {
+    if (tz * (n + np) > 256) continue;
+    for (int ck : {64, 32, 16}) {
+      if (cin % ck) continue;
+      const size_t stage = tc3_stage(ck, n, tz) + (size_t)np * ck * 2;
+      if (stage > 100 * 1024 || staging + 2 * stage + 1024 > kTc3SmemMax) continue;
+      const int nst = (int)std::min<size_t>(kP3Max, (kTc3SmemMax - 1024 - staging) / stage);
+      const double cost = (double)ceil_div(Z, tz) * (3.0 * 144 * (tz + 2) + 9.0 * n + np) /
+                          std::min(32, ck);
+      if (cost < best_cost * (1 - 1e-9) || (cost <= best_cost * (1 + 1e-9) && nst > best.nst)) {
+        best_cost = cost;
+        best.ck = ck, best.tz = tz, best.nst = nst, best.stage = stage, best.staging = staging;
+        best.persistent = true;
+      }
     }
   }
+  if (best.persistent || np) return best;
+  best.ck = tc3_chunk(cin, n);
+  if (best.ck) best.tz = tc3_tz(best.ck, n, Z);
+  return best;
+}
+
+// Persistent form when the plan has it; else one tile per CTA.
+cudaError_t launch_tc3(const CUtensorMap& a, const CUtensorMap& w, int cin, int ck, int tz,
+                       const float* bias, float* out, Dims3 dout, int n, int B, long long out_bs,
+                       long long bias_bs, int acc, int* err, cudaStream_t st,
+                       int mode = 0, const CUtensorMap* wp = nullptr,
+                       const CUtensorMap* a2 = nullptr, int np = 0, const float* bias_p = nullptr,
+                       float* out_p = nullptr, long long outp_bs = 0) {
+  const Tc3Plan pl = tc3_plan(cin, n, mode == 1 ? np : 0, dout.z);
+  if (pl.persistent && pl.ck == ck && pl.tz == tz) {
+    P3Args g{};
+    g.bias = bias, g.out = out, g.bias_p = bias_p, g.out_p = out_p, g.err = err;
+    g.dout = dout;
+    g.N = n, g.Np = np, g.nchunks = cin / ck;
+    g.tiles_x = (int)ceil_div(dout.x, 8), g.tiles_y = (int)ceil_div(dout.y, 16);
+    g.tiles_z = (int)ceil_div(dout.z, tz);
+    g.B = B, g.accumulate = acc, g.nst = pl.nst, g.mode = mode;
+    g.stage_bytes = (uint32_t)pl.stage, g.ring_bytes = (uint32_t)(pl.nst * pl.stage);
+    g.out_bs = out_bs, g.bias_bs = bias_bs, g.outp_bs = outp_bs, g.biasp_bs = bias_bs;
+    const long long total = (long long)g.tiles_x * g.tiles_y * g.tiles_z * B;
+    const int grid = (int)std::min<long long>(total, sm_count());
+    const size_t sm = g.ring_bytes + pl.staging + 1024;
+    const CUtensorMap& mp = wp ? *wp : w;
+    const CUtensorMap& m2 = a2 ? *a2 : a;
+#define D2IP_P3(CK_, TZ_) conv_tc3p_kernel<CK_, TZ_><<<grid, 192, sm, st>>>(a, w, mp, m2, g)
+#define D2IP_P3Z(CK_) \
+  if (tz == 4) D2IP_P3(CK_, 4); else if (tz == 2) D2IP_P3(CK_, 2); else D2IP_P3(CK_, 1)
+    if (ck == 64) { D2IP_P3Z(64); } else if (ck == 32) { D2IP_P3Z(32); } else { D2IP_P3Z(16); }
+#undef D2IP_P3Z
+#undef D2IP_P3
+    return cudaGetLastError();
+  }
+  if (mode != 0) return cudaErrorInvalidValue;
   const int tx = (int)ceil_div(dout.x, 8), ty = (int)ceil_div(dout.y, 16);
   dim3 grid((unsigned)(tx * ty * ceil_div(dout.z, tz)), 1, B);
   const size_t stage = tc3_stage(ck, n, tz);
@@ -1379,8 +1487,14 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
   L.dout = conv_out_dims(din, k, s);
   L.w_off = w_off;
   L.dgrad = (s == 1 || k == 3) && bf16_conv_supported(co, ci, k);
-  L.ck3f = (k == 3 && s == 1) ? tc3_chunk(ci, co) : 0;
-  L.ck3d = (k == 3 && s == 1 && L.dgrad) ? tc3_chunk(co, ci) : 0;
+  if (k == 3 && s == 1) {
+    const Tc3Plan pf = tc3_plan(ci, co, 0, L.dout.z);
+    L.ck3f = pf.ck, L.tz3f = pf.tz;
+    if (L.dgrad) {
+      const Tc3Plan pd = tc3_plan(co, ci, 0, L.din.z);
+      L.ck3d = pd.ck, L.tz3d = pd.tz;
+    }
+  }
   L.wgrad = s == 1 && co <= 128 && 128 % co == 0 && ci + chunk_for(ci) <= 256;
   L.wg3 = L.wgrad && wg3_geom(L, 1).nst > 0;
   const long long n = (long long)co * k * k * k * ci;
@@ -1406,7 +1520,10 @@ int bf16_add_input_layer(Bf16Net& bf, int ci_real, int co, Dims3 din, long long 
   L.dout = din;
   L.w_off = w_off;
   L.input_layer = true;
-  L.ck3f = bf16_conv_supported(16, co, 3) ? tc3_chunk(16, co) : 0;
+  if (bf16_conv_supported(16, co, 3)) {
+    const Tc3Plan pf = tc3_plan(16, co, 0, din.z);
+    L.ck3f = pf.ck, L.tz3f = pf.tz;
+  }
   L.wgrad = L.wg3 = wg3_geom(L, 1).nst > 0;
   if (!L.ck3f || !L.wg3) return -1;
   L.wf_off = bf.wstride;
@@ -1426,6 +1543,9 @@ void bf16_layout(Bf16Net& bf, char* base, size_t& used, int B, long long max_act
   bf.err = reinterpret_cast<int*>(take(sizeof(int)));
   bf.xbf = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * max_act * 2));
   bf.ybf = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * max_act * 2));
+  bool any_proj = false;
+  for (const TcLayer& L : bf.layers) any_proj |= L.projd;
+  bf.pbf = any_proj ? reinterpret_cast<__nv_bfloat16*>(take((size_t)B * max_act * 2)) : nullptr;
   bf.wbuf = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * bf.wstride * 2));
   bf.zbf = bf.zcount ? reinterpret_cast<__nv_bfloat16*>(take((size_t)B * bf.zcount * 2)) : nullptr;
 }
@@ -1435,7 +1555,7 @@ cudaError_t bf16_finalize(Bf16Net& bf, int B) {
     const int T = L.k * L.k * L.k;
     if (L.input_layer) {  // halo-box forward and weight gradient over zbf only
       cudaError_t e =
-          encode_act_halo(&L.act_f3, bf.zbf, B, L.din, 16, L.ck3f, tc3_tz(L.ck3f, L.co, L.dout.z));
+          encode_act_halo(&L.act_f3, bf.zbf, B, L.din, 16, L.ck3f, L.tz3f);
       if (e == cudaSuccess)
         e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, 16, T, L.co, L.ck3f, 9, 3);
       const int tz = wg3_tz(L.dout.z);
@@ -1463,16 +1583,24 @@ cudaError_t bf16_finalize(Bf16Net& bf, int B) {
         e = encode_box(&L.wg_x3, bf.xbf, B, L.din, L.ci, chunk_for(L.ci), 8, 1, tz);
     }
     if (e == cudaSuccess && L.ck3f) {
-      e = encode_act_halo(&L.act_f3, bf.xbf, B, L.din, L.ci, L.ck3f,
-                          tc3_tz(L.ck3f, L.co, L.dout.z));
+      e = encode_act_halo(&L.act_f3, bf.xbf, B, L.din, L.ci, L.ck3f, L.tz3f);
       if (e == cudaSuccess)
         e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, L.ci, T, L.co, L.ck3f, 9, 3);
     }
     if (e == cudaSuccess && L.ck3d) {
-      e = encode_act_halo(&L.act_d3, bf.xbf, B, L.dout, L.co, L.ck3d,
-                          tc3_tz(L.ck3d, L.ci, L.din.z));
+      e = encode_act_halo(&L.act_d3, bf.xbf, B, L.dout, L.co, L.ck3d, L.tz3d);
       if (e == cudaSuccess)
         e = encode_w(&L.w_d3, bf.wbuf + L.wd_off, B, bf.wstride, L.co, T, L.ci, L.ck3d, 9, 3);
+    }
+    if (e == cudaSuccess && L.projf) {  // W_p [1][co][ci] in chunks of this layer's ck
+      const TcLayer& P = bf.layers[L.proj];
+      e = encode_w(&L.pw_f, bf.wbuf + P.wf_off, B, bf.wstride, P.ci, 1, P.co, L.ck3f, 1, 1);
+    }
+    if (e == cudaSuccess && L.projd) {  // W_p^T [1][ci][co] and the dz_p tile box
+      const TcLayer& P = bf.layers[L.proj];
+      e = encode_w(&L.pw_d, bf.wbuf + P.wd_off, B, bf.wstride, P.co, 1, P.ci, L.ck3d, 1, 1);
+      if (e == cudaSuccess)
+        e = encode_box(&L.pa_d, bf.pbf, B, L.dout, L.co, L.ck3d, 8, 16, L.tz3d);
     }
     if (e != cudaSuccess) return e;
   }
@@ -1730,6 +1858,47 @@ __global__ void pad_input_kernel(const float* __restrict__ z, __nv_bfloat16* __r
 }
 }  // namespace
 
+int bf16_fuse_proj(Bf16Net& bf, int la, int lp) {
+  TcLayer& A = bf.layers[la];
+  const TcLayer& P = bf.layers[lp];
+  if (A.k != 3 || A.s != 1 || P.k != 1 || P.ci != A.ci || P.co != A.co || A.input_layer)
+    return 0;
+  A.proj = lp;
+  if (A.ck3f) {
+    const Tc3Plan pf = tc3_plan(A.ci, A.co, P.co, A.dout.z);
+    if (pf.persistent) A.projf = true, A.ck3f = pf.ck, A.tz3f = pf.tz;
+  }
+  if (A.ck3d && P.dgrad) {
+    const Tc3Plan pd = tc3_plan(A.co, A.ci, 0, A.din.z);
+    A.projd = pd.persistent && pd.ck == A.ck3d && pd.tz == A.tz3d;
+  }
+  return (A.projf ? 1 : 0) | (A.projd ? 2 : 0);
+}
+
+cudaError_t bf16_conv_fwd_proj(Bf16Net& bf, int la, const float* x, const float* bias_a,
+                               float* y_a, const float* bias_p, float* y_p, int B,
+                               long long bias_bs, cudaStream_t stream) {
+  const TcLayer& L = bf.layers[la];
+  if (!L.projf) return cudaErrorInvalidValue;
+  cudaError_t e = stage_bf16(x, bf.xbf, (long long)B * L.din.count() * L.ci, stream);
+  if (e != cudaSuccess) return e;
+  return launch_tc3(L.act_f3, L.w_f3, L.ci, L.ck3f, L.tz3f, bias_a, y_a, L.dout, L.co, B,
+                    L.dout.count() * L.co, bias_bs, 0, bf.err, stream, 1, &L.pw_f, nullptr,
+                    L.co, bias_p, y_p, L.dout.count() * L.co);
+}
+
+cudaError_t bf16_conv_dgrad_proj(Bf16Net& bf, int la, const float* dz_a, const float* dz_p,
+                                 float* dx, int B, cudaStream_t stream) {
+  const TcLayer& L = bf.layers[la];
+  if (!L.projd) return cudaErrorInvalidValue;
+  const long long n = (long long)B * L.dout.count() * L.co;
+  cudaError_t e = stage_bf16(dz_a, bf.xbf, n, stream);
+  if (e == cudaSuccess) e = stage_bf16(dz_p, bf.pbf, n, stream);
+  if (e != cudaSuccess) return e;
+  return launch_tc3(L.act_d3, L.w_d3, L.co, L.ck3d, L.tz3d, nullptr, dx, L.din, L.ci, B,
+                    L.din.count() * L.ci, 0, 0, bf.err, stream, 2, &L.pw_d, &L.pa_d);
+}
+
 cudaError_t bf16_stage_input(Bf16Net& bf, int layer, const float* z, int B, cudaStream_t stream) {
   const TcLayer& L = bf.layers[layer];
   if (!L.input_layer || !bf.zbf) return cudaErrorInvalidValue;
@@ -1746,7 +1915,7 @@ cudaError_t bf16_conv_fwd(Bf16Net& bf, int layer, const float* x, const float* b
       L.input_layer ? cudaSuccess : stage_bf16(x, bf.xbf, (long long)B * L.din.count() * L.ci, stream);
   if (e != cudaSuccess) return e;
   if (L.ck3f)
-    return launch_tc3(L.act_f3, L.w_f3, L.ci, L.ck3f, bias, y, L.dout, L.co, B,
+    return launch_tc3(L.act_f3, L.w_f3, L.ci, L.ck3f, L.tz3f, bias, y, L.dout, L.co, B,
                       L.dout.count() * L.co, bias_bs, 0, bf.err, stream);
   const TapPlan plan = conv_plan(L.k, L.s);
   return launch_tc(L.act_f, L.w_f, plan, 1, L.ci, bias, y, L.dout, L.dout, L.co, B,
@@ -1765,7 +1934,7 @@ cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, 
                      L.din.count() * L.ci, 0, accumulate, bf.err, stream);
   }
   if (L.ck3d)
-    return launch_tc3(L.act_d3, L.w_d3, L.co, L.ck3d, nullptr, dx, L.din, L.ci, B,
+    return launch_tc3(L.act_d3, L.w_d3, L.co, L.ck3d, L.tz3d, nullptr, dx, L.din, L.ci, B,
                       L.din.count() * L.ci, 0, accumulate, bf.err, stream);
   return launch_tc(L.act_d, L.w_d, conv_plan(L.k, 1), 1, L.co, nullptr, dx, L.din, L.din, L.ci,
                    B, L.din.count() * L.ci, 0, accumulate, bf.err, stream);

@@ -27,6 +27,10 @@ struct TcLayer {
   bool dgrad = false;             // data gradient on the tensor cores too (stride 1)
   bool wgrad = false;             // weight gradient on the tensor cores too (3x3x3, stride 1)
   int ck3f = 0, ck3d = 0;         // channel chunk of the halo-box kernel (0: per-tap kernel)
+  int tz3f = 1, tz3d = 1;         // z slices per halo-box tile
+  int proj = -1;                  // layer index of a 1x1 projection of the same input, fused
+  bool projf = false, projd = false;  // ... into this layer's forward / data gradient
+  CUtensorMap pw_f, pw_d, pa_d;   // projection: W_p, W_p^T and the dz_p tile box
   bool wg3 = false;               // weight gradient by the halo-box kernel
   int ci_real = 0;                // input channels of the model (ci is padded up to 16)
   bool input_layer = false;       // reads the padded BF16 copy of the network input (zbf)
@@ -36,6 +40,7 @@ struct TcLayer {
 struct Bf16Net {
   __nv_bfloat16* xbf = nullptr;   // BF16 staging of one convolution input (or dy)
   __nv_bfloat16* ybf = nullptr;   // BF16 staging of dy for the weight gradient
+  __nv_bfloat16* pbf = nullptr;   // BF16 staging of a fused projection's dy
   __nv_bfloat16* wbuf = nullptr;  // BF16 weights of every tensor-core layer, per problem
   __nv_bfloat16* zbf = nullptr;   // network input, BF16, channels padded to 16 (input layer)
   long long zcount = 0;           // elements per problem of zbf
@@ -55,6 +60,17 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
 int bf16_add_input_layer(Bf16Net& bf, int ci_real, int co, Dims3 din, long long w_off);
 // z [B][n][ci_real] FP32 -> zbf [B][n][16] BF16 (zero channels ci_real..15).
 cudaError_t bf16_stage_input(Bf16Net& bf, int layer, const float* z, int B, cudaStream_t stream);
+// Fuse the 1x1 projection lp (same input, same output channels) into the 3x3x3 stride-1
+// layer la: its forward and data gradient then run in la's halo-box launches.  Returns
+// whether the forward (bit 0) and the data gradient (bit 1) were fused.
+int bf16_fuse_proj(Bf16Net& bf, int la, int lp);
+// y_a = conv_a(x) + bias_a and y_p = W_p x + bias_p in one launch (layer la with projf).
+cudaError_t bf16_conv_fwd_proj(Bf16Net& bf, int la, const float* x, const float* bias_a,
+                               float* y_a, const float* bias_p, float* y_p, int B,
+                               long long bias_bs, cudaStream_t stream);
+// dx = conv_a^T(dz_a) + W_p^T dz_p in one launch (layer la with projd).
+cudaError_t bf16_conv_dgrad_proj(Bf16Net& bf, int la, const float* dz_a, const float* dz_p,
+                                 float* dx, int B, cudaStream_t stream);
 // Reserve the BF16 buffers in the arena (base == nullptr: size only).
 void bf16_layout(Bf16Net& bf, char* base, size_t& used, int B, long long max_act);
 // Encode the TMA descriptors once the buffers have addresses.

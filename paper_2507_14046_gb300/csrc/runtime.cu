@@ -47,6 +47,7 @@ struct Res {  // act(LN_b(conv_b(act(LN_a(conv_a(x))))) + P(x))
   ConvL a, b, p;
   LnL lna, lnb;
   bool proj = false;
+  bool fuse_f = false, fuse_d = false;  // projection fused into conv a's launches (BF16)
   int lvl = 0;
   const float* x = nullptr;
   float *xh_a = nullptr, *rs_a = nullptr, *h1 = nullptr, *xh_b = nullptr, *rs_b = nullptr,
@@ -190,6 +191,11 @@ struct Builder {
     R.lnb = ln(co);
     R.proj = ci != co;
     if (R.proj) R.p = conv(ci, co, 1, 1, lvl);
+    if (R.proj && R.a.tc >= 0 && R.p.tc >= 0) {
+      const int f = bf16_fuse_proj(c->bf, R.a.tc, R.p.tc);
+      R.fuse_f = (f & 1) != 0;
+      R.fuse_d = (f & 2) != 0;
+    }
     return R;
   }
 };
@@ -475,9 +481,16 @@ struct Launcher {
     ln_fwd(u.ln, u.lvl_out, c->ztmp, nullptr, u.a, u.xh, u.rs);
   }
   void res_fwd(Res& R) {
-    conv_fwd(R.a, R.x, c->ztmp);
+    if (R.fuse_f) {  // conv a and the projection in one launch
+      beg(D2IP_KCLASS_CONV_FWD, conv_flops(R.a) + conv_flops(R.p));
+      ok(bf16_conv_fwd_proj(c->bf, R.a.tc, R.x, W(R.a) + R.a.wcount(), c->ztmp,
+                            W(R.p) + R.p.wcount(), c->ptmp, c->B, c->Pp, c->stream));
+      fin();
+    } else {
+      conv_fwd(R.a, R.x, c->ztmp);
+    }
     ln_fwd(R.lna, R.lvl, c->ztmp, nullptr, R.h1, R.xh_a, R.rs_a);
-    if (R.proj) conv_fwd(R.p, R.x, c->ptmp);
+    if (R.proj && !R.fuse_f) conv_fwd(R.p, R.x, c->ptmp);
     conv_fwd(R.b, R.h1, c->ztmp);
     ln_fwd(R.lnb, R.lvl, c->ztmp, R.proj ? c->ptmp : R.x, R.out, R.xh_b, R.rs_b);
   }
@@ -552,10 +565,16 @@ struct Launcher {
     conv_dgrad(R.b, T.tz, T.th, 0);
     conv_wgrad(R.b, R.h1, T.tz);
     ln_bwd(R.lna, R.lvl, T.th, R.h1, R.xh_a, R.rs_a, T.tz, nullptr);
-    conv_dgrad(R.a, T.tz, dx, 0);
+    if (R.fuse_d) {  // dx = conv_a^T(dz_a) + W_p^T dz_p in one launch
+      beg(D2IP_KCLASS_CONV_DGRAD, conv_flops(R.a) + conv_flops(R.p));
+      ok(bf16_conv_dgrad_proj(c->bf, R.a.tc, T.tz, T.tt, dx, c->B, c->stream));
+      fin();
+    } else {
+      conv_dgrad(R.a, T.tz, dx, 0);
+    }
     conv_wgrad(R.a, R.x, T.tz);
     if (R.proj) {
-      conv_dgrad(R.p, T.tt, dx, 1);
+      if (!R.fuse_d) conv_dgrad(R.p, T.tt, dx, 1);
       conv_wgrad(R.p, R.x, T.tt);
     } else {
       const long long cnt = c->B * c->dims[R.lvl].count() * R.lna.c;
