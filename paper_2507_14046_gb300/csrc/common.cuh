@@ -114,4 +114,16 @@ cudaError_t adam_step_f32(float* theta, const float* g, float* m, float* v, long
                           double lr, double beta1, double beta2, double eps, const int* t_dev,
                           int t_host, cudaStream_t stream);
 
+
+// 1x1x1 convolution to one output channel (C input channels, weights [C] then bias, per
+// problem at w_bs): y = b + w . h, and its backward dh (=|+=) w g with per-block weight
+// partials part[b][blk][C + 1] (conv1x1_co1_blocks rows; add them with reduce_rows_f32).
+bool conv1x1_co1_supported(int C);
+long long conv1x1_co1_blocks(long long nvox);
+cudaError_t conv1x1_co1_fwd_f32(const float* h, const float* wb, float* y, int B, long long nvox,
+                                int C, long long w_bs, cudaStream_t stream);
+cudaError_t conv1x1_co1_bwd_f32(const float* h, const float* g, const float* wb, float* dh,
+                                float* part, int B, long long nvox, int C, long long w_bs,
+                                int accumulate, cudaStream_t stream);
+
 }  // namespace d2ip

@@ -969,12 +969,15 @@ __device__ __forceinline__ uint64_t smem_desc_mn2(uint32_t addr, uint32_t lbo, u
 struct Wg3Geom {
   int tz, nkx, tiles_x, tiles_z, ntiles, tiles_per_chunk, nchunks, nst;
   uint32_t a_box, b_box, b_off, ones_off, stage, tmem_cols;
+  int proj;        // also the weight gradient of a fused 1x1 projection (its dz_p: p_box)
+  uint32_t p_off, p_box;
 };
 
 template <int CKA, int CKB, int NKX>
 __global__ void __launch_bounds__(128, 1)
 wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant__ CUtensorMap tm_x,
-                 float* __restrict__ part, Dims3 d, int Ci, int ci_out,
+                 const __grid_constant__ CUtensorMap tm_p, float* __restrict__ part,
+                 float* __restrict__ part_p, Dims3 d, int Ci, int ci_out,
                  const __grid_constant__ Wg3Geom gm, int* __restrict__ err) {
   constexpr int kTpm = 128 / CKA;                  // taps per MMA
   constexpr int kG = (9 + kTpm - 1) / kTpm;        // MMAs per x tap
@@ -993,6 +996,9 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
   const int tile1 = min(tile0 + gm.tiles_per_chunk, gm.ntiles);
   const int ksteps = max(tile1 - tile0, 0);
   const int nst = gm.nst;
+  // the projection's products go with the centre x tap: D_p[co][ci] = sum_u dz_p[u][co] x[u][ci]
+  const bool proj = gm.proj && kx0 <= 1 && 1 < kx0 + NKX;
+  const uint32_t pcol = (uint32_t)(NKX * kG * N);  // its accumulator
   for (int s = 0; s < nst; ++s) {
     uint32_t* ones = reinterpret_cast<uint32_t*>(smem + (size_t)s * gm.stage + gm.ones_off);
     for (int i = threadIdx.x; i < (int)(gm.b_box / 4); i += blockDim.x) ones[i] = 0x3F803F80u;
@@ -1020,7 +1026,8 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
   const uint32_t tmem = tmem_base_s;
 
   if (warp == 0 && lane == 0) {  // TMA producer
-    const uint32_t tx_bytes = (uint32_t)NKX * gm.a_box + (uint32_t)nb * gm.b_box;
+    const uint32_t tx_bytes =
+        (uint32_t)NKX * gm.a_box + (uint32_t)nb * gm.b_box + (proj ? gm.p_box : 0u);
     for (int k = 0; k < ksteps; ++k) {
       const int s = k % nst, round = k / nst;
       if (round > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (round - 1) & 1)) {
@@ -1039,6 +1046,7 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
                     b, fb);
       for (int c = 0; c < nb; ++c)
         tma_load_5d(base + gm.b_off + (uint32_t)c * gm.b_box, &tm_x, c * CKB, x0, y0, z0, b, fb);
+      if (proj) tma_load_5d(base + gm.p_off, &tm_p, 0, x0, y0, z0, b, fb);
     }
   } else if (warp == 1 && lane == 0) {  // MMA issuer
     const uint32_t idesc = instr_desc_mn(N);
@@ -1056,6 +1064,10 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
       const uint32_t ahi = (uint32_t)(a0 >> 32), bhi = (uint32_t)(b0 >> 32);
       const uint32_t abx = gm.a_box >> 4;
       uint32_t alo = (uint32_t)a0, blo = (uint32_t)b0;
+      // dz_p column: every M block reads the same Co rows (block stride 0), K groups adjacent
+      const uint64_t p0 = smem_desc_mn2<CKA>(base + gm.p_off, 0, kAtomA);
+      uint32_t plo = (uint32_t)p0;
+      const uint32_t phi = (uint32_t)(p0 >> 32);
       for (int kk = 0; kk < gm.tz / 2; ++kk) {  // K = 16 voxels = z offsets 2kk, 2kk + 1
 #pragma unroll
         for (int q = 0; q < NKX; ++q)
@@ -1070,8 +1082,15 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
             else
               mma_lh(d, alo + ao, ahi, blo, bhi, idesc);
           }
+        if (proj) {
+          if (kk == 0)
+            mma_lh_p(tmem + pcol, plo, phi, blo, bhi, idesc, k > 0 ? 1u : 0u);
+          else
+            mma_lh(tmem + pcol, plo, phi, blo, bhi, idesc);
+        }
         alo += (6 * kAtomA) >> 4;  // next two z offsets: 6 dy atoms, 2 x atoms
         blo += (2 * kAtomB) >> 4;
+        plo += (2 * kAtomA) >> 4;
       }
       mma_commit(smem_u32(&empty_bar[s]));
     }
@@ -1115,6 +1134,26 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
       if (keep && t == 13)
         prow[(long long)Co * 27 * ci_out + co] = ok ? __uint_as_float(r[0]) : 0.f;
     }
+  if (proj && warp * 32 < Co) {  // rows co < Co of the projection accumulator
+    const long long prow_n = (long long)Co * Ci + Co;
+    float* pp = part_p + ((long long)b * gm.nchunks + chunk) * prow_n;
+    const uint32_t col = tmem + ((uint32_t)(warp * 32) << 16) + pcol;
+    for (int c0 = 0; c0 < Ci; c0 += 16) {
+      uint32_t r[16];
+      if (ok) tmem_ld16(col + (uint32_t)c0, r);
+      if (m < Co) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4*>(pp + (long long)m * Ci + c0 + j) =
+              ok ? make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                               __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]))
+                 : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    uint32_t r[16];
+    if (ok) tmem_ld16(col + (uint32_t)Ci, r);
+    if (m < Co) pp[(long long)Co * Ci + m] = ok ? __uint_as_float(r[0]) : 0.f;
+  }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -1182,7 +1221,7 @@ EncodeTiledFn encode_fn() {
 int chunk_for(int c) { return c % 64 == 0 ? 64 : (c % 32 == 0 ? 32 : 16); }
 
 int wg3_tz(int Z);
-Wg3Geom wg3_geom(const TcLayer& L, int B);
+Wg3Geom wg3_geom(const TcLayer& L, int B, bool proj = false);
 
 CUtensorMapSwizzle swizzle_for(int ck) {
   return ck == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
@@ -1544,7 +1583,7 @@ void bf16_layout(Bf16Net& bf, char* base, size_t& used, int B, long long max_act
   bf.xbf = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * max_act * 2));
   bf.ybf = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * max_act * 2));
   bool any_proj = false;
-  for (const TcLayer& L : bf.layers) any_proj |= L.projd;
+  for (const TcLayer& L : bf.layers) any_proj |= L.projd || L.projw;
   bf.pbf = any_proj ? reinterpret_cast<__nv_bfloat16*>(take((size_t)B * max_act * 2)) : nullptr;
   bf.wbuf = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * bf.wstride * 2));
   bf.zbf = bf.zcount ? reinterpret_cast<__nv_bfloat16*>(take((size_t)B * bf.zcount * 2)) : nullptr;
@@ -1596,6 +1635,8 @@ cudaError_t bf16_finalize(Bf16Net& bf, int B) {
       const TcLayer& P = bf.layers[L.proj];
       e = encode_w(&L.pw_f, bf.wbuf + P.wf_off, B, bf.wstride, P.ci, 1, P.co, L.ck3f, 1, 1);
     }
+    if (e == cudaSuccess && L.projw)  // dz_p column of the halo weight gradient
+      e = encode_box(&L.wg_p3, bf.pbf, B, L.dout, L.co, L.co, 8, 1, wg3_tz(L.dout.z));
     if (e == cudaSuccess && L.projd) {  // W_p^T [1][ci][co] and the dz_p tile box
       const TcLayer& P = bf.layers[L.proj];
       e = encode_w(&L.pw_d, bf.wbuf + P.wd_off, B, bf.wstride, P.co, 1, P.ci, L.ck3d, 1, 1);
@@ -1675,7 +1716,7 @@ int wg3_tz(int Z) {
 }
 
 // Geometry of the halo weight gradient; nst == 0 when the layer does not fit it.
-Wg3Geom wg3_geom(const TcLayer& L, int B) {
+Wg3Geom wg3_geom(const TcLayer& L, int B, bool proj) {
   Wg3Geom g{};
   if (L.k != 3 || L.s != 1 || (L.co != 16 && L.co != 32 && L.co != 64)) return g;
   const int ckb = chunk_for(L.ci);
@@ -1686,15 +1727,19 @@ Wg3Geom wg3_geom(const TcLayer& L, int B) {
     while (t < c) t *= 2;
     return t;
   };
-  g.nkx = 3 * G * N <= 512 ? 3 : 1;
-  if (G * N > 512) return g;
-  g.tmem_cols = (uint32_t)pow2(g.nkx * G * N);
+  const int extra = proj ? 1 : 0;  // the projection's accumulator
+  g.nkx = (3 * G + extra) * N <= 512 ? 3 : 1;
+  if ((G + extra) * N > 512) return g;
+  g.proj = extra;
+  g.tmem_cols = (uint32_t)pow2((g.nkx * G + extra) * N);
   g.tz = wg3_tz(L.dout.z);
   g.a_box = (uint32_t)(8 * 3 * (g.tz + 2) * L.co * 2);
   g.b_box = (uint32_t)(8 * g.tz * ckb * 2);
   g.b_off = (uint32_t)((g.nkx * g.a_box + 1023) / 1024 * 1024);
   g.ones_off = g.b_off + (uint32_t)(L.ci / ckb) * g.b_box;
-  g.stage = (g.ones_off + g.b_box + 1023) / 1024 * 1024;
+  g.p_box = proj ? (uint32_t)(8 * g.tz * L.co * 2) : 0u;
+  g.p_off = (g.ones_off + g.b_box + 1023) / 1024 * 1024;
+  g.stage = (g.p_off + g.p_box + 1023) / 1024 * 1024;
   const int nst = (int)std::min<size_t>(kWg3MaxStages, (kWg3SmemMax - 1024) / g.stage);
   if (nst < 2) return g;
   g.tiles_x = (int)ceil_div(L.dout.x, 8);
@@ -1722,39 +1767,46 @@ cudaError_t wg3_attr() {
 }
 
 template <int CKA, int CKB>
-void launch_wg3(const TcLayer& L, const Wg3Geom& g, float* part, int B, int* err,
+void launch_wg3(const TcLayer& L, const Wg3Geom& g, float* part, float* part_p, int B, int* err,
                 cudaStream_t st) {
   dim3 grid((unsigned)g.nchunks, (unsigned)(3 / g.nkx), (unsigned)B);
   const size_t smem = (size_t)g.nst * g.stage + 1024;
+  const CUtensorMap& mp = g.proj ? L.wg_p3 : L.wg_dy3;
   if (g.nkx == 3)
-    wgrad_tc3_kernel<CKA, CKB, 3><<<grid, 128, smem, st>>>(L.wg_dy3, L.wg_x3, part, L.dout, L.ci,
-                                                           L.ci_real, g, err);
+    wgrad_tc3_kernel<CKA, CKB, 3><<<grid, 128, smem, st>>>(L.wg_dy3, L.wg_x3, mp, part, part_p,
+                                                           L.dout, L.ci, L.ci_real, g, err);
   else
-    wgrad_tc3_kernel<CKA, CKB, 1><<<grid, 128, smem, st>>>(L.wg_dy3, L.wg_x3, part, L.dout, L.ci,
-                                                           L.ci_real, g, err);
+    wgrad_tc3_kernel<CKA, CKB, 1><<<grid, 128, smem, st>>>(L.wg_dy3, L.wg_x3, mp, part, part_p,
+                                                           L.dout, L.ci, L.ci_real, g, err);
 }
 
 }  // namespace
 
 long long bf16_wgrad_chunks(const Bf16Net& bf, int layer, int B) {
   const TcLayer& L = bf.layers[layer];
-  if (L.wg3) return wg3_geom(L, B).nchunks;
+  if (L.wg3) return wg3_geom(L, B, L.projw).nchunks;
   return wgrad_plan(L, B).chunks;
 }
 
 cudaError_t bf16_conv_wgrad(Bf16Net& bf, int layer, const float* x, const float* dy,
-                            float* part, int B, cudaStream_t stream) {
+                            float* part, int B, cudaStream_t stream, const float* dz_p,
+                            float* part_p) {
   const TcLayer& L = bf.layers[layer];
-  if (!L.wgrad) return cudaErrorInvalidValue;
+  if (!L.wgrad || (dz_p && !L.projw)) return cudaErrorInvalidValue;
   const WgPlan p = wgrad_plan(L, B);
   cudaError_t e =
       L.input_layer ? cudaSuccess : stage_bf16(x, bf.xbf, (long long)B * L.din.count() * L.ci, stream);
   if (e == cudaSuccess) e = stage_bf16(dy, bf.ybf, (long long)B * L.dout.count() * L.co, stream);
   if (e != cudaSuccess) return e;
   if (L.wg3) {
-    const Wg3Geom g = wg3_geom(L, B);
+    const Wg3Geom g = wg3_geom(L, B, L.projw);
+    if (L.projw) {  // the fused projection needs its dz_p staged (kept from the data gradient)
+      if (!dz_p || !part_p) return cudaErrorInvalidValue;
+      if (!L.projd) e = stage_bf16(dz_p, bf.pbf, (long long)B * L.dout.count() * L.co, stream);
+      if (e != cudaSuccess) return e;
+    }
     const int ckb = chunk_for(L.ci);
-#define D2IP_WG3(A_, B_) launch_wg3<A_, B_>(L, g, part, B, bf.err, stream)
+#define D2IP_WG3(A_, B_) launch_wg3<A_, B_>(L, g, part, part_p, B, bf.err, stream)
     if (L.co == 16) {
       if (ckb == 16) D2IP_WG3(16, 16); else if (ckb == 32) D2IP_WG3(16, 32); else D2IP_WG3(16, 64);
     } else if (L.co == 32) {
@@ -1872,7 +1924,8 @@ int bf16_fuse_proj(Bf16Net& bf, int la, int lp) {
     const Tc3Plan pd = tc3_plan(A.co, A.ci, 0, A.din.z);
     A.projd = pd.persistent && pd.ck == A.ck3d && pd.tz == A.tz3d;
   }
-  return (A.projf ? 1 : 0) | (A.projd ? 2 : 0);
+  A.projw = A.wg3 && wg3_geom(A, 1, true).nst > 0;
+  return (A.projf ? 1 : 0) | (A.projd ? 2 : 0) | (A.projw ? 4 : 0);
 }
 
 cudaError_t bf16_conv_fwd_proj(Bf16Net& bf, int la, const float* x, const float* bias_a,

@@ -29,8 +29,9 @@ struct TcLayer {
   int ck3f = 0, ck3d = 0;         // channel chunk of the halo-box kernel (0: per-tap kernel)
   int tz3f = 1, tz3d = 1;         // z slices per halo-box tile
   int proj = -1;                  // layer index of a 1x1 projection of the same input, fused
-  bool projf = false, projd = false;  // ... into this layer's forward / data gradient
+  bool projf = false, projd = false, projw = false;  // ... into forward / dgrad / wgrad
   CUtensorMap pw_f, pw_d, pa_d;   // projection: W_p, W_p^T and the dz_p tile box
+  CUtensorMap wg_p3;              // projection: dz_p column of the halo weight gradient
   bool wg3 = false;               // weight gradient by the halo-box kernel
   int ci_real = 0;                // input channels of the model (ci is padded up to 16)
   bool input_layer = false;       // reads the padded BF16 copy of the network input (zbf)
@@ -62,7 +63,8 @@ int bf16_add_input_layer(Bf16Net& bf, int ci_real, int co, Dims3 din, long long 
 cudaError_t bf16_stage_input(Bf16Net& bf, int layer, const float* z, int B, cudaStream_t stream);
 // Fuse the 1x1 projection lp (same input, same output channels) into the 3x3x3 stride-1
 // layer la: its forward and data gradient then run in la's halo-box launches.  Returns
-// whether the forward (bit 0) and the data gradient (bit 1) were fused.
+// whether the forward (bit 0), the data gradient (bit 1) and the weight gradient (bit 2)
+// were fused.
 int bf16_fuse_proj(Bf16Net& bf, int la, int lp);
 // y_a = conv_a(x) + bias_a and y_p = W_p x + bias_p in one launch (layer la with projf).
 cudaError_t bf16_conv_fwd_proj(Bf16Net& bf, int la, const float* x, const float* bias_a,
@@ -90,8 +92,11 @@ cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, 
 long long bf16_wgrad_chunks(const Bf16Net& bf, int layer, int B);
 // Per-chunk partial sums part[b][chunk][Co*27*Ci + Co] (weights, then bias) of a layer with
 // .wgrad set; the caller adds the chunks (reduce_rows_f32).
+// With dz_p (layer with projw): also the projection's partial sums
+// part_p[b][chunk][Co*Ci + Co] (its dz_p is staged here unless the fused data gradient did).
 cudaError_t bf16_conv_wgrad(Bf16Net& bf, int layer, const float* x, const float* dy,
-                            float* part, int B, cudaStream_t stream);
+                            float* part, int B, cudaStream_t stream,
+                            const float* dz_p = nullptr, float* part_p = nullptr);
 
 // Context-free form for the op entry points: one layer, staging buffers, BF16 weights and
 // the error word carved from a caller workspace of bf16_op_workspace() bytes.

@@ -761,3 +761,123 @@ cudaError_t adam_step_f32(float* theta, const float* g, float* m, float* v, long
 }
 
 }  // namespace d2ip
+
+// ------------------------------------------------------------------------------------
+// 1x1x1 convolution to a single output channel (the network's last layer):
+// y[v] = b + sum_c w[c] h[v][c]; backward dh[v][c] = w[c] g[v] with the weight partials
+// sum_v g[v] h[v][c] and sum_v g[v] per block of kOneVox voxels (fixed-order sums).
+// ------------------------------------------------------------------------------------
+namespace d2ip {
+namespace {
+
+constexpr int kOneThreads = 256, kOneVpt = 8, kOneVox = kOneThreads * kOneVpt;
+
+template <int C>
+__global__ void __launch_bounds__(kOneThreads)
+co1_fwd_kernel(const float* __restrict__ h, const float* __restrict__ wb, float* __restrict__ y,
+               long long nvox, long long w_bs) {
+  const int b = blockIdx.y;
+  const long long v = (long long)blockIdx.x * kOneThreads + threadIdx.x;
+  if (v >= nvox) return;
+  const float* w = wb + (long long)b * w_bs;
+  const float4* hv = reinterpret_cast<const float4*>(h + ((long long)b * nvox + v) * C);
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < C / 4; ++c) {
+    const float4 a = hv[c];
+    s = fmaf(a.x, __ldg(w + 4 * c), s);
+    s = fmaf(a.y, __ldg(w + 4 * c + 1), s);
+    s = fmaf(a.z, __ldg(w + 4 * c + 2), s);
+    s = fmaf(a.w, __ldg(w + 4 * c + 3), s);
+  }
+  y[(long long)b * nvox + v] = s + __ldg(w + C);
+}
+
+template <int C>
+__global__ void __launch_bounds__(kOneThreads)
+co1_bwd_kernel(const float* __restrict__ h, const float* __restrict__ g,
+               const float* __restrict__ wb, float* __restrict__ dh, float* __restrict__ part,
+               long long nvox, long long w_bs, int nblk, int accumulate) {
+  __shared__ float red[kOneThreads][C + 1];
+  const int b = blockIdx.y;
+  const float* w = wb + (long long)b * w_bs;
+  float wr[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) wr[c] = __ldg(w + c);
+  float acc[C + 1];
+#pragma unroll
+  for (int c = 0; c <= C; ++c) acc[c] = 0.f;
+  const long long v0 = (long long)blockIdx.x * kOneVox;
+  for (int i = 0; i < kOneVpt; ++i) {
+    const long long v = v0 + (long long)i * kOneThreads + threadIdx.x;
+    if (v >= nvox) break;
+    const long long o = (long long)b * nvox + v;
+    const float gv = g[o];
+    const float4* hv = reinterpret_cast<const float4*>(h + o * C);
+    float4* dv = reinterpret_cast<float4*>(dh + o * C);
+#pragma unroll
+    for (int c = 0; c < C / 4; ++c) {
+      const float4 a = hv[c];
+      acc[4 * c] = fmaf(gv, a.x, acc[4 * c]);
+      acc[4 * c + 1] = fmaf(gv, a.y, acc[4 * c + 1]);
+      acc[4 * c + 2] = fmaf(gv, a.z, acc[4 * c + 2]);
+      acc[4 * c + 3] = fmaf(gv, a.w, acc[4 * c + 3]);
+      float4 d = make_float4(wr[4 * c] * gv, wr[4 * c + 1] * gv, wr[4 * c + 2] * gv,
+                             wr[4 * c + 3] * gv);
+      if (accumulate) {
+        const float4 p = dv[c];
+        d.x += p.x, d.y += p.y, d.z += p.z, d.w += p.w;
+      }
+      dv[c] = d;
+    }
+    acc[C] += gv;
+  }
+#pragma unroll
+  for (int c = 0; c <= C; ++c) red[threadIdx.x][c] = acc[c];
+  __syncthreads();
+  if (threadIdx.x <= C) {
+    float s = 0.f;
+    for (int t = 0; t < kOneThreads; ++t) s += red[t][threadIdx.x];
+    part[((long long)b * nblk + blockIdx.x) * (C + 1) + threadIdx.x] = s;
+  }
+}
+
+}  // namespace
+
+bool conv1x1_co1_supported(int C) { return C == 4 || C == 8 || C == 16 || C == 32; }
+
+long long conv1x1_co1_blocks(long long nvox) { return ceil_div(nvox, kOneVox); }
+
+cudaError_t conv1x1_co1_fwd_f32(const float* h, const float* wb, float* y, int B, long long nvox,
+                                int C, long long w_bs, cudaStream_t stream) {
+  dim3 grid((unsigned)ceil_div(nvox, kOneThreads), B);
+  switch (C) {
+    case 4: co1_fwd_kernel<4><<<grid, kOneThreads, 0, stream>>>(h, wb, y, nvox, w_bs); break;
+    case 8: co1_fwd_kernel<8><<<grid, kOneThreads, 0, stream>>>(h, wb, y, nvox, w_bs); break;
+    case 16: co1_fwd_kernel<16><<<grid, kOneThreads, 0, stream>>>(h, wb, y, nvox, w_bs); break;
+    case 32: co1_fwd_kernel<32><<<grid, kOneThreads, 0, stream>>>(h, wb, y, nvox, w_bs); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t conv1x1_co1_bwd_f32(const float* h, const float* g, const float* wb, float* dh,
+                                float* part, int B, long long nvox, int C, long long w_bs,
+                                int accumulate, cudaStream_t stream) {
+  const int nblk = (int)conv1x1_co1_blocks(nvox);
+  dim3 grid((unsigned)nblk, B);
+#define D2IP_CO1B(C_)                                                                  \
+  co1_bwd_kernel<C_><<<grid, kOneThreads, 0, stream>>>(h, g, wb, dh, part, nvox, w_bs, nblk, \
+                                                       accumulate)
+  switch (C) {
+    case 4: D2IP_CO1B(4); break;
+    case 8: D2IP_CO1B(8); break;
+    case 16: D2IP_CO1B(16); break;
+    case 32: D2IP_CO1B(32); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef D2IP_CO1B
+  return cudaGetLastError();
+}
+
+}  // namespace d2ip

@@ -47,7 +47,7 @@ struct Res {  // act(LN_b(conv_b(act(LN_a(conv_a(x))))) + P(x))
   ConvL a, b, p;
   LnL lna, lnb;
   bool proj = false;
-  bool fuse_f = false, fuse_d = false;  // projection fused into conv a's launches (BF16)
+  bool fuse_f = false, fuse_d = false, fuse_w = false;  // projection fused into conv a (BF16)
   int lvl = 0;
   const float* x = nullptr;
   float *xh_a = nullptr, *rs_a = nullptr, *h1 = nullptr, *xh_b = nullptr, *rs_b = nullptr,
@@ -195,6 +195,7 @@ struct Builder {
       const int f = bf16_fuse_proj(c->bf, R.a.tc, R.p.tc);
       R.fuse_f = (f & 1) != 0;
       R.fuse_d = (f & 2) != 0;
+      R.fuse_w = (f & 4) != 0;
     }
     return R;
   }
@@ -251,7 +252,13 @@ bool tc_wgrad(const d2ip_ctx* c, const ConvL& L) {
   return L.tc >= 0 && L.k == 3 && c->bf.layers[L.tc].wgrad;
 }
 
+// The last layer (1x1x1 to one channel) has its own memory-bound kernels.
+bool co1_layer(const ConvL& L) {
+  return L.k == 1 && L.s == 1 && L.co == 1 && conv1x1_co1_supported(L.ci);
+}
+
 long long wgrad_rows(const d2ip_ctx* c, const ConvL& L) {
+  if (co1_layer(L)) return conv1x1_co1_blocks(L.din.count());
   if (tc_wgrad(c, L)) return bf16_wgrad_chunks(c->bf, L.tc, c->B);
   return conv3d_wgrad_chunks(L.din, L.k, L.s);
 }
@@ -326,6 +333,9 @@ void layout_buffers(d2ip_ctx* c, Carve& cv) {
   ws = std::max(ws, ln_ws_floats(c, c->stem.ln, 0));
   auto res_ws = [&](const Res& R) {
     ws = std::max(ws, conv_ws_floats(c, R.a));
+    if (R.fuse_w)
+      ws = std::max(ws, conv_ws_floats(c, R.a) +
+                            (long long)c->B * wgrad_rows(c, R.a) * (R.p.wcount() + R.p.co));
     ws = std::max(ws, conv_ws_floats(c, R.b));
     if (R.proj) ws = std::max(ws, conv_ws_floats(c, R.p));
     ws = std::max(ws, ln_ws_floats(c, R.lna, R.lvl));
@@ -515,7 +525,14 @@ struct Launcher {
       res_fwd(c->dec[l]);
       cur = c->dec[l].out;
     }
-    conv_fwd(c->tail, cur, c->dsigma);
+    if (co1_layer(c->tail)) {
+      beg(D2IP_KCLASS_CONV_FWD, conv_flops(c->tail));
+      ok(conv1x1_co1_fwd_f32(cur, W(c->tail), c->dsigma, c->B, c->tail.din.count(), c->tail.ci,
+                             c->Pp, c->stream));
+      fin();
+    } else {
+      conv_fwd(c->tail, cur, c->dsigma);
+    }
   }
   void data_term(bool training) {
     const long long n = c->n();
@@ -572,10 +589,22 @@ struct Launcher {
     } else {
       conv_dgrad(R.a, T.tz, dx, 0);
     }
-    conv_wgrad(R.a, R.x, T.tz);
+    if (R.fuse_w) {  // weight gradients of conv a and the projection in one launch
+      const long long rows = wgrad_rows(c, R.a);
+      float* part_p = c->ws + (long long)c->B * rows * (R.a.wcount() + R.a.co);
+      beg(D2IP_KCLASS_CONV_WGRAD, conv_flops(R.a) + conv_flops(R.p));
+      ok(bf16_conv_wgrad(c->bf, R.a.tc, R.x, T.tz, c->ws, c->B, c->stream, T.tt, part_p));
+      ok(reduce_rows_f32(c->ws, G(R.a.w_off), c->B, rows, R.a.wcount() + R.a.co, c->Pp, 0,
+                         c->stream));
+      ok(reduce_rows_f32(part_p, G(R.p.w_off), c->B, rows, R.p.wcount() + R.p.co, c->Pp, 0,
+                         c->stream));
+      fin();
+    } else {
+      conv_wgrad(R.a, R.x, T.tz);
+    }
     if (R.proj) {
       if (!R.fuse_d) conv_dgrad(R.p, T.tt, dx, 1);
-      conv_wgrad(R.p, R.x, T.tt);
+      if (!R.fuse_w) conv_wgrad(R.p, R.x, T.tt);
     } else {
       const long long cnt = c->B * c->dims[R.lvl].count() * R.lna.c;
       beg(D2IP_KCLASS_MISC, 12.0 * cnt);
@@ -592,8 +621,18 @@ struct Launcher {
   void backward() {
     const int L = c->L;
     const float* tail_in = L > 1 ? c->dec[0].out : c->enc[0].out;
-    conv_dgrad(c->tail, c->gds, c->lb[0].g1, 0);
-    conv_wgrad(c->tail, tail_in, c->gds);
+    if (co1_layer(c->tail)) {  // data and weight gradients of the last layer in one pass
+      const ConvL& T = c->tail;
+      beg(D2IP_KCLASS_CONV_WGRAD, 2.0 * conv_flops(T));
+      ok(conv1x1_co1_bwd_f32(tail_in, c->gds, W(T), c->lb[0].g1, c->ws, c->B, T.din.count(), T.ci,
+                             c->Pp, 0, c->stream));
+      ok(reduce_rows_f32(c->ws, G(T.w_off), c->B, wgrad_rows(c, T), T.wcount() + T.co, c->Pp, 0,
+                         c->stream));
+      fin();
+    } else {
+      conv_dgrad(c->tail, c->gds, c->lb[0].g1, 0);
+      conv_wgrad(c->tail, tail_in, c->gds);
+    }
     for (int l = 0; l + 1 < L; ++l) {
       res_bwd(c->dec[l], c->lb[l].g1, c->lb[l].g2);
       const double bytes = 4.0 * c->B *
