@@ -1200,6 +1200,37 @@ __global__ void weights_bf16_kernel(const float* __restrict__ theta, __nv_bfloat
   if (dgrad) base[wd_off + ((long long)(T - 1 - t) * ci + c) * co + o] = h;  // [26-t][ci][co]
 }
 
+// All layers' weights in one launch: a block belongs to the layer whose block range holds
+// blockIdx.x (ranges from a prefix table of at most kWMaxLayers layers).
+constexpr int kWMaxLayers = 48;
+struct WTable {
+  int nl;
+  int blk0[kWMaxLayers + 1];
+  long long w_off[kWMaxLayers], wf_off[kWMaxLayers], wd_off[kWMaxLayers];
+  int ci[kWMaxLayers], ci_real[kWMaxLayers], co[kWMaxLayers], T[kWMaxLayers],
+      dgrad[kWMaxLayers];
+};
+
+__global__ void weights_all_bf16_kernel(const float* __restrict__ theta,
+                                        __nv_bfloat16* __restrict__ wb, long long Pp,
+                                        long long wstride, const __grid_constant__ WTable t) {
+  int l = 0;
+  while (l + 1 < t.nl && (int)blockIdx.x >= t.blk0[l + 1]) ++l;
+  const int b = blockIdx.y;
+  const int ci = t.ci[l], cr = t.ci_real[l], co = t.co[l], T = t.T[l];
+  const long long n = (long long)co * T * ci;
+  const long long e = (long long)(blockIdx.x - t.blk0[l]) * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int c = (int)(e % ci);
+  const long long r = e / ci;
+  const int tap = (int)(r % T), o = (int)(r / T);
+  const float v = c < cr ? theta[(long long)b * Pp + t.w_off[l] + r * cr + c] : 0.f;
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);  // W[o][tap][c]
+  __nv_bfloat16* base = wb + (long long)b * wstride;
+  base[t.wf_off[l] + ((long long)tap * co + o) * ci + c] = h;                     // [t][co][ci]
+  if (t.dgrad[l]) base[t.wd_off[l] + ((long long)(T - 1 - tap) * ci + c) * co + o] = h;
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -1587,6 +1618,14 @@ void bf16_layout(Bf16Net& bf, char* base, size_t& used, int B, long long max_act
   bf.pbf = any_proj ? reinterpret_cast<__nv_bfloat16*>(take((size_t)B * max_act * 2)) : nullptr;
   bf.wbuf = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * bf.wstride * 2));
   bf.zbf = bf.zcount ? reinterpret_cast<__nv_bfloat16*>(take((size_t)B * bf.zcount * 2)) : nullptr;
+  for (TcLayer& L : bf.layers) {
+    if (L.input_layer)
+      L.xin = bf.zbf;
+    else if (bf.keep_inputs)
+      L.xin = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * L.din.count() * L.ci * 2));
+    else
+      L.xin = bf.xbf;
+  }
 }
 
 cudaError_t bf16_finalize(Bf16Net& bf, int B) {
@@ -1603,12 +1642,12 @@ cudaError_t bf16_finalize(Bf16Net& bf, int B) {
       if (e != cudaSuccess) return e;
       continue;
     }
-    cudaError_t e = encode_act(&L.act_f, bf.xbf, B, L.din, L.ci, chunk_for(L.ci), L.s);
+    cudaError_t e = encode_act(&L.act_f, L.xin, B, L.din, L.ci, chunk_for(L.ci), L.s);
     if (e == cudaSuccess)
       e = encode_w(&L.w_f, bf.wbuf + L.wf_off, B, bf.wstride, L.ci, T, L.co, chunk_for(L.ci), 1,
                    1);
     if (e == cudaSuccess && L.dgrad) {
-      e = encode_act(&L.act_d, bf.xbf, B, L.dout, L.co, chunk_for(L.co), 1);
+      e = encode_act(&L.act_d, bf.ybf, B, L.dout, L.co, chunk_for(L.co), 1);
       if (e == cudaSuccess)
         e = encode_w(&L.w_d, bf.wbuf + L.wd_off, B, bf.wstride, L.co, T, L.ci, chunk_for(L.co), 1,
                      1);
@@ -1619,15 +1658,15 @@ cudaError_t bf16_finalize(Bf16Net& bf, int B) {
       const int tz = wg3_tz(L.dout.z);
       e = encode_box(&L.wg_dy3, bf.ybf, B, L.dout, L.co, L.co, 8, 3, tz + 2);
       if (e == cudaSuccess)
-        e = encode_box(&L.wg_x3, bf.xbf, B, L.din, L.ci, chunk_for(L.ci), 8, 1, tz);
+        e = encode_box(&L.wg_x3, L.xin, B, L.din, L.ci, chunk_for(L.ci), 8, 1, tz);
     }
     if (e == cudaSuccess && L.ck3f) {
-      e = encode_act_halo(&L.act_f3, bf.xbf, B, L.din, L.ci, L.ck3f, L.tz3f);
+      e = encode_act_halo(&L.act_f3, L.xin, B, L.din, L.ci, L.ck3f, L.tz3f);
       if (e == cudaSuccess)
         e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, L.ci, T, L.co, L.ck3f, 9, 3);
     }
     if (e == cudaSuccess && L.ck3d) {
-      e = encode_act_halo(&L.act_d3, bf.xbf, B, L.dout, L.co, L.ck3d, L.tz3d);
+      e = encode_act_halo(&L.act_d3, bf.ybf, B, L.dout, L.co, L.ck3d, L.tz3d);
       if (e == cudaSuccess)
         e = encode_w(&L.w_d3, bf.wbuf + L.wd_off, B, bf.wstride, L.co, T, L.ci, L.ck3d, 9, 3);
     }
@@ -1790,13 +1829,15 @@ long long bf16_wgrad_chunks(const Bf16Net& bf, int layer, int B) {
 
 cudaError_t bf16_conv_wgrad(Bf16Net& bf, int layer, const float* x, const float* dy,
                             float* part, int B, cudaStream_t stream, const float* dz_p,
-                            float* part_p) {
+                            float* part_p, bool x_staged, bool dy_staged) {
   const TcLayer& L = bf.layers[layer];
   if (!L.wgrad || (dz_p && !L.projw)) return cudaErrorInvalidValue;
   const WgPlan p = wgrad_plan(L, B);
-  cudaError_t e =
-      L.input_layer ? cudaSuccess : stage_bf16(x, bf.xbf, (long long)B * L.din.count() * L.ci, stream);
-  if (e == cudaSuccess) e = stage_bf16(dy, bf.ybf, (long long)B * L.dout.count() * L.co, stream);
+  cudaError_t e = L.input_layer || (x_staged && bf.keep_inputs)
+                      ? cudaSuccess
+                      : stage_bf16(x, L.xin, (long long)B * L.din.count() * L.ci, stream);
+  if (e == cudaSuccess && !dy_staged)
+    e = stage_bf16(dy, bf.ybf, (long long)B * L.dout.count() * L.co, stream);
   if (e != cudaSuccess) return e;
   if (L.wg3) {
     const Wg3Geom g = wg3_geom(L, B, L.projw);
@@ -1880,6 +1921,24 @@ cudaError_t bf16_prepare_kernels() {
 
 cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long long Pp,
                                  cudaStream_t stream) {
+  if (bf.layers.size() <= (size_t)kWMaxLayers && !bf.layers.empty()) {
+    WTable t{};
+    t.nl = (int)bf.layers.size();
+    int blk = 0;
+    for (int i = 0; i < t.nl; ++i) {
+      const TcLayer& L = bf.layers[i];
+      const int T = L.k * L.k * L.k;
+      t.blk0[i] = blk;
+      blk += (int)ceil_div((long long)L.co * T * L.ci, 256);
+      t.w_off[i] = L.w_off, t.wf_off[i] = L.wf_off, t.wd_off[i] = L.wd_off;
+      t.ci[i] = L.ci, t.ci_real[i] = L.ci_real, t.co[i] = L.co, t.T[i] = T;
+      t.dgrad[i] = L.dgrad ? 1 : 0;
+    }
+    t.blk0[t.nl] = blk;
+    weights_all_bf16_kernel<<<dim3((unsigned)blk, B), 256, 0, stream>>>(theta, bf.wbuf, Pp,
+                                                                         bf.wstride, t);
+    return cudaGetLastError();
+  }
   for (const TcLayer& L : bf.layers) {
     const int T = L.k * L.k * L.k;
     const long long n = (long long)L.co * T * L.ci;
@@ -1933,7 +1992,7 @@ cudaError_t bf16_conv_fwd_proj(Bf16Net& bf, int la, const float* x, const float*
                                long long bias_bs, cudaStream_t stream) {
   const TcLayer& L = bf.layers[la];
   if (!L.projf) return cudaErrorInvalidValue;
-  cudaError_t e = stage_bf16(x, bf.xbf, (long long)B * L.din.count() * L.ci, stream);
+  cudaError_t e = stage_bf16(x, L.xin, (long long)B * L.din.count() * L.ci, stream);
   if (e != cudaSuccess) return e;
   return launch_tc3(L.act_f3, L.w_f3, L.ci, L.ck3f, L.tz3f, bias_a, y_a, L.dout, L.co, B,
                     L.dout.count() * L.co, bias_bs, 0, bf.err, stream, 1, &L.pw_f, nullptr,
@@ -1945,7 +2004,7 @@ cudaError_t bf16_conv_dgrad_proj(Bf16Net& bf, int la, const float* dz_a, const f
   const TcLayer& L = bf.layers[la];
   if (!L.projd) return cudaErrorInvalidValue;
   const long long n = (long long)B * L.dout.count() * L.co;
-  cudaError_t e = stage_bf16(dz_a, bf.xbf, n, stream);
+  cudaError_t e = stage_bf16(dz_a, bf.ybf, n, stream);
   if (e == cudaSuccess) e = stage_bf16(dz_p, bf.pbf, n, stream);
   if (e != cudaSuccess) return e;
   return launch_tc3(L.act_d3, L.w_d3, L.co, L.ck3d, L.tz3d, nullptr, dx, L.din, L.ci, B,
@@ -1965,7 +2024,7 @@ cudaError_t bf16_conv_fwd(Bf16Net& bf, int layer, const float* x, const float* b
                           int B, long long bias_bs, cudaStream_t stream) {
   const TcLayer& L = bf.layers[layer];
   cudaError_t e =
-      L.input_layer ? cudaSuccess : stage_bf16(x, bf.xbf, (long long)B * L.din.count() * L.ci, stream);
+      L.input_layer ? cudaSuccess : stage_bf16(x, L.xin, (long long)B * L.din.count() * L.ci, stream);
   if (e != cudaSuccess) return e;
   if (L.ck3f)
     return launch_tc3(L.act_f3, L.w_f3, L.ci, L.ck3f, L.tz3f, bias, y, L.dout, L.co, B,
@@ -1979,7 +2038,7 @@ cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, 
                             int accumulate, cudaStream_t stream) {
   const TcLayer& L = bf.layers[layer];
   if (!L.dgrad) return cudaErrorInvalidValue;
-  cudaError_t e = stage_bf16(dy, bf.xbf, (long long)B * L.dout.count() * L.co, stream);
+  cudaError_t e = stage_bf16(dy, bf.ybf, (long long)B * L.dout.count() * L.co, stream);
   if (e != cudaSuccess) return e;
   if (L.s == 2) {
     const Dims3 q{(L.din.z + 1) / 2, (L.din.y + 1) / 2, (L.din.x + 1) / 2};

@@ -33,6 +33,7 @@ struct TcLayer {
   CUtensorMap pw_f, pw_d, pa_d;   // projection: W_p, W_p^T and the dz_p tile box
   CUtensorMap wg_p3;              // projection: dz_p column of the halo weight gradient
   bool wg3 = false;               // weight gradient by the halo-box kernel
+  __nv_bfloat16* xin = nullptr;   // BF16 copy of the forward input (kept for the weight gradient)
   int ci_real = 0;                // input channels of the model (ci is padded up to 16)
   bool input_layer = false;       // reads the padded BF16 copy of the network input (zbf)
 };
@@ -48,6 +49,7 @@ struct Bf16Net {
   long long wstride = 0;          // elements per problem in wbuf
   long long max_act = 0;          // elements per problem of the largest staged input
   int* err = nullptr;             // device error word (bounded waits that ran out)
+  bool keep_inputs = false;       // a BF16 input copy per layer (else all share xbf)
   std::vector<TcLayer> layers;
 };
 
@@ -94,9 +96,12 @@ long long bf16_wgrad_chunks(const Bf16Net& bf, int layer, int B);
 // .wgrad set; the caller adds the chunks (reduce_rows_f32).
 // With dz_p (layer with projw): also the projection's partial sums
 // part_p[b][chunk][Co*Ci + Co] (its dz_p is staged here unless the fused data gradient did).
+// x_staged: the layer's forward has staged x into its kept input copy (keep_inputs) since x
+// last changed; dy_staged: its data gradient has just staged this dy (both skip a staging).
 cudaError_t bf16_conv_wgrad(Bf16Net& bf, int layer, const float* x, const float* dy,
                             float* part, int B, cudaStream_t stream,
-                            const float* dz_p = nullptr, float* part_p = nullptr);
+                            const float* dz_p = nullptr, float* part_p = nullptr,
+                            bool x_staged = false, bool dy_staged = false);
 
 // Context-free form for the op entry points: one layer, staging buffers, BF16 weights and
 // the error word carved from a caller workspace of bf16_op_workspace() bytes.

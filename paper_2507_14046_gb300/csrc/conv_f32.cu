@@ -163,6 +163,70 @@ reduce_rows_kernel(const float* __restrict__ part, float* __restrict__ out, long
   }
 }
 
+// out[b][j] (=|+=) sum_r part[b][r][j] for few rows and many columns: a thread owns four
+// adjacent columns and adds the rows in order (four independent loads in flight).
+__global__ void __launch_bounds__(256)
+reduce_wide_kernel(const float* __restrict__ part, float* __restrict__ out, long long R,
+                   long long N, long long out_bs, int accumulate) {
+  const int b = blockIdx.y;
+  const long long j = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (j >= N) return;
+  const float* p = part + (long long)b * R * N + j;
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  long long r = 0;
+  for (; r + 4 <= R; r += 4) {
+    const float4 v0 = *reinterpret_cast<const float4*>(p + r * N);
+    const float4 v1 = *reinterpret_cast<const float4*>(p + (r + 1) * N);
+    const float4 v2 = *reinterpret_cast<const float4*>(p + (r + 2) * N);
+    const float4 v3 = *reinterpret_cast<const float4*>(p + (r + 3) * N);
+    s.x += v0.x, s.y += v0.y, s.z += v0.z, s.w += v0.w;
+    s.x += v1.x, s.y += v1.y, s.z += v1.z, s.w += v1.w;
+    s.x += v2.x, s.y += v2.y, s.z += v2.z, s.w += v2.w;
+    s.x += v3.x, s.y += v3.y, s.z += v3.z, s.w += v3.w;
+  }
+  for (; r < R; ++r) {
+    const float4 v = *reinterpret_cast<const float4*>(p + r * N);
+    s.x += v.x, s.y += v.y, s.z += v.z, s.w += v.w;
+  }
+  float4* o = reinterpret_cast<float4*>(out + (long long)b * out_bs + j);
+  if (accumulate) {
+    const float4 q = *o;
+    s.x += q.x, s.y += q.y, s.z += q.z, s.w += q.w;
+  }
+  *o = s;
+}
+
+// Few columns, many rows (LayerNorm partials): 32 row groups per column, combined in order.
+constexpr int kNarrowGroups = 32;
+
+__global__ void __launch_bounds__(kRedCols * kNarrowGroups)
+reduce_narrow_kernel(const float* __restrict__ part, float* __restrict__ out, long long R,
+                     long long N, long long out_bs, int accumulate) {
+  __shared__ float red[kNarrowGroups][kRedCols + 1];
+  const int b = blockIdx.y;
+  const int col = threadIdx.x % kRedCols, g = threadIdx.x / kRedCols;
+  const long long j = (long long)blockIdx.x * kRedCols + col;
+  float s0 = 0.f, s1 = 0.f;
+  if (j < N) {
+    const float* p = part + (long long)b * R * N + j;
+    long long r = g;
+    for (; r + kNarrowGroups < R; r += 2 * kNarrowGroups) {
+      s0 += p[r * N];
+      s1 += p[(r + kNarrowGroups) * N];
+    }
+    if (r < R) s0 += p[r * N];
+  }
+  red[g][col] = s0 + s1;
+  __syncthreads();
+  if (g == 0 && j < N) {
+    float s = 0.f;
+#pragma unroll 8
+    for (int q = 0; q < kNarrowGroups; ++q) s += red[q][col];
+    float* o = out + (long long)b * out_bs + j;
+    *o = accumulate ? *o + s : s;
+  }
+}
+
 // Output brick: 2 x 8 x 8 voxels for stride 1, 1 x 4 x 8 for stride 2 (keeps the stride-2
 // halo within static shared memory).
 int wgrad_bz(int S) { return S == 1 ? 2 : 1; }
@@ -210,9 +274,20 @@ cudaError_t conv3d_wgrad_partial_f32(const float* x, const float* dy, float* par
 
 cudaError_t reduce_rows_f32(const float* part, float* out, int B, long long R, long long N,
                             long long out_bs, int accumulate, cudaStream_t stream) {
-  dim3 grid((unsigned)ceil_div(N, kRedCols), B);
-  reduce_rows_kernel<<<grid, kRedCols * kRedGroups, 0, stream>>>(part, out, R, N, out_bs,
-                                                                  accumulate);
+  const bool vec = N % 4 == 0 && out_bs % 4 == 0 &&
+                   ((reinterpret_cast<uintptr_t>(part) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+  if (vec && N >= 1024 && R <= 64) {  // wide: one thread per 4 columns, rows in order
+    dim3 grid((unsigned)ceil_div(N / 4, 256), B);
+    reduce_wide_kernel<<<grid, 256, 0, stream>>>(part, out, R, N, out_bs, accumulate);
+  } else if (N <= 256) {  // narrow: 32 row groups per column
+    dim3 grid((unsigned)ceil_div(N, kRedCols), B);
+    reduce_narrow_kernel<<<grid, kRedCols * kNarrowGroups, 0, stream>>>(part, out, R, N, out_bs,
+                                                                        accumulate);
+  } else {
+    dim3 grid((unsigned)ceil_div(N, kRedCols), B);
+    reduce_rows_kernel<<<grid, kRedCols * kRedGroups, 0, stream>>>(part, out, R, N, out_bs,
+                                                                    accumulate);
+  }
   return cudaGetLastError();
 }
 

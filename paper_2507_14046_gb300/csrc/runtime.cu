@@ -207,6 +207,7 @@ void build_plan(d2ip_ctx* c) {
   for (int l = 1; l < c->L; ++l) c->dims[l] = conv_out_dims(c->dims[l - 1], 3, 2);
   c->table.clear();
   c->bf = Bf16Net{};
+  c->bf.keep_inputs = true;  // layer inputs stay staged in BF16 from forward to backward
   Builder b{c};
   const auto& w = c->w;
   c->stem.conv = b.conv(c->c_in, w[0], 3, 1, 0, /*input=*/true);
@@ -456,10 +457,13 @@ struct Launcher {
                           L.dout.count() * L.co, L.din.count() * L.ci, c->Pp, acc, c->stream));
     fin();
   }
-  void conv_wgrad(const ConvL& L, const float* x, const float* dy) {
+  // dy_staged: this layer's data gradient has just staged dy (BF16); the forward of this
+  // iteration staged x.
+  void conv_wgrad(const ConvL& L, const float* x, const float* dy, bool dy_staged = false) {
     beg(D2IP_KCLASS_CONV_WGRAD, conv_flops(L));
     if (tc_wgrad(c, L))
-      ok(bf16_conv_wgrad(c->bf, L.tc, x, dy, c->ws, c->B, c->stream));
+      ok(bf16_conv_wgrad(c->bf, L.tc, x, dy, c->ws, c->B, c->stream, nullptr, nullptr, true,
+                         dy_staged && c->bf.layers[L.tc].dgrad));
     else
       ok(conv3d_wgrad_partial_f32(x, dy, c->ws, c->B, L.din, L.ci, L.co, L.k, L.s,
                                   L.din.count() * L.ci, L.dout.count() * L.co, c->stream));
@@ -580,7 +584,7 @@ struct Launcher {
     LevelBufs& T = c->lb[R.lvl];
     ln_bwd(R.lnb, R.lvl, dout, R.out, R.xh_b, R.rs_b, T.tz, T.tt);
     conv_dgrad(R.b, T.tz, T.th, 0);
-    conv_wgrad(R.b, R.h1, T.tz);
+    conv_wgrad(R.b, R.h1, T.tz, true);
     ln_bwd(R.lna, R.lvl, T.th, R.h1, R.xh_a, R.rs_a, T.tz, nullptr);
     if (R.fuse_d) {  // dx = conv_a^T(dz_a) + W_p^T dz_p in one launch
       beg(D2IP_KCLASS_CONV_DGRAD, conv_flops(R.a) + conv_flops(R.p));
@@ -593,14 +597,15 @@ struct Launcher {
       const long long rows = wgrad_rows(c, R.a);
       float* part_p = c->ws + (long long)c->B * rows * (R.a.wcount() + R.a.co);
       beg(D2IP_KCLASS_CONV_WGRAD, conv_flops(R.a) + conv_flops(R.p));
-      ok(bf16_conv_wgrad(c->bf, R.a.tc, R.x, T.tz, c->ws, c->B, c->stream, T.tt, part_p));
+      ok(bf16_conv_wgrad(c->bf, R.a.tc, R.x, T.tz, c->ws, c->B, c->stream, T.tt, part_p, true,
+                         true));
       ok(reduce_rows_f32(c->ws, G(R.a.w_off), c->B, rows, R.a.wcount() + R.a.co, c->Pp, 0,
                          c->stream));
       ok(reduce_rows_f32(part_p, G(R.p.w_off), c->B, rows, R.p.wcount() + R.p.co, c->Pp, 0,
                          c->stream));
       fin();
     } else {
-      conv_wgrad(R.a, R.x, T.tz);
+      conv_wgrad(R.a, R.x, T.tz, true);
     }
     if (R.proj) {
       if (!R.fuse_d) conv_dgrad(R.p, T.tt, dx, 1);
@@ -616,7 +621,7 @@ struct Launcher {
     float* tz = c->lb[u.lvl_out].tz;
     ln_bwd(u.ln, u.lvl_out, da, u.a, u.xh, u.rs, tz, nullptr);
     if (dgrad) conv_dgrad(u.conv, tz, dx, acc);
-    conv_wgrad(u.conv, u.x, tz);
+    conv_wgrad(u.conv, u.x, tz, dgrad);
   }
   void backward() {
     const int L = c->L;
