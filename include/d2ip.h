@@ -92,7 +92,8 @@ d2ip_status d2ip_param_table(d2ip_ctx* ctx, long long* rows, int cap, int* n_row
 
 /* Copy J (m x n, n = X*Y*Z) into the context.  normalize_cols != 0 scales every column to
  * unit l2 norm with the norm accumulated in FP64 (Eq. 1, "normalized" sensitivity); a zero
- * column is left as is.  J may be host or device memory. */
+ * column is left as is.  J may be host or device memory.  m <= 6400; with D2IP_BF16 also m a
+ * multiple of 4 and at most 1024 (D2IP_ERR_BAD_SHAPE otherwise). */
 d2ip_status d2ip_load_J(d2ip_ctx* ctx, const float* J, int m, int n, int normalize_cols);
 /* The FP64 column norms used by the last d2ip_load_J (n values; host or device memory). */
 d2ip_status d2ip_get_colnorms(d2ip_ctx* ctx, double* out);

@@ -84,6 +84,8 @@ cudaError_t jmul_residual_bf16(const __nv_bfloat16* J, const float* x, const flo
 cudaError_t jtmul_bf16(const __nv_bfloat16* J, const float* r, float* g, float scale, int B,
                        int m, int n, long long g_bs, cudaStream_t stream);
 cudaError_t convert_bf16(const float* x, __nv_bfloat16* y, long long n, cudaStream_t stream);
+// The BF16 forms of the J products take J transposed: Jt[n][m] (BF16), m a multiple of 4.
+cudaError_t transpose_bf16(const float* J, __nv_bfloat16* Jt, int m, int n, cudaStream_t stream);
 // Per-device kernel attributes (opt-in shared memory); call once per device before launches.
 cudaError_t prepare_pointwise_kernels();
 cudaError_t jtmul_f32(const float* J, const float* r, float* g, float scale, int B, int m,

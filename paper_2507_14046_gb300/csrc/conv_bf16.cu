@@ -939,6 +939,146 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant
 }
 
 // ------------------------------------------------------------------------------------
+// Weight gradient of a 3x3x3 stride-2 layer.  dW[co][t][ci] = sum_v x[2 v + k_t - 1][ci]
+// dy[v][co]: M = TG taps x Ci (one M block per tap: the input box of an 8 x 4 x 4 output tile
+// traversed with element stride 2, i.e. the forward's own strided map), N = Co (the dy tile),
+// K = output voxels.  The group that holds the last taps also gets a block of ones in A, whose
+// rows give sum_v dy[v][co] (the bias partial).  A CTA takes one tap group and a chunk of
+// tiles; per-chunk partial rows follow the layout [co][t][ci], then the bias.
+// ------------------------------------------------------------------------------------
+template <int CKA, int CKB>
+__global__ void __launch_bounds__(128, 1)
+wgrad_s2_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_dy,
+                   float* __restrict__ part, Dims3 dout, int Co, int tiles_per_chunk, int ntiles,
+                   int tiles_x, int tiles_y, int nchunks, int nst, int* __restrict__ err) {
+  constexpr int kTpm = 128 / CKA;               // M blocks (taps) per MMA
+  constexpr uint32_t a_box = kBM * CKA * 2;     // one tap's box: 128 voxels x Ci
+  constexpr uint32_t a_bytes = kTpm * a_box;    // the whole 128-row A tile
+  const uint32_t b_box = kBM * CKB * 2;
+  const uint32_t stage_bytes = a_bytes + (uint32_t)(Co / CKB) * b_box;
+  const int Ci = CKA;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[kWgMaxStages], empty_bar[kWgMaxStages], done_bar;
+  __shared__ uint32_t tmem_base_s;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int chunk = blockIdx.x, grp = blockIdx.y, b = blockIdx.z;
+  const int t0 = grp * kTpm;
+  const int ntap = 27 - t0 < kTpm ? 27 - t0 : kTpm;  // taps of this group
+  const bool ones = ntap < kTpm;                     // block ntap holds ones
+  const int tile0 = chunk * tiles_per_chunk;
+  const int tile1 = tile0 + tiles_per_chunk < ntiles ? tile0 + tiles_per_chunk : ntiles;
+  const int ksteps = tile1 > tile0 ? tile1 - tile0 : 0;
+  const uint32_t tmem_cols = Co <= 32 ? 32u : Co <= 64 ? 64u : Co <= 128 ? 128u : 256u;
+  if (ones) {  // the ones block of every stage (BF16 1.0); rows past it stay unused
+    for (int s = 0; s < nst; ++s) {
+      uint32_t* o = reinterpret_cast<uint32_t*>(smem + (size_t)s * stage_bytes + ntap * a_box);
+      for (int i = threadIdx.x; i < (int)(a_box / 4); i += blockDim.x) o[i] = 0x3F803F80u;
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nst; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_u32(&done_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_s)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  if (warp == 0 && lane == 0) {  // TMA producer
+    const uint32_t tx_bytes = (uint32_t)ntap * a_box + (uint32_t)(Co / CKB) * b_box;
+    for (int k = 0; k < ksteps; ++k) {
+      const int s = k % nst, round = k / nst;
+      if (round > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (round - 1) & 1)) {
+        atomicOr(err, kErrProducer);
+        break;
+      }
+      const int tile = tile0 + k;
+      const int x0 = (tile % tiles_x) * kBX, y0 = ((tile / tiles_x) % tiles_y) * kBY,
+                z0 = (tile / (tiles_x * tiles_y)) * kBZ;
+      const uint32_t base = smem_u32(smem + (size_t)s * stage_bytes);
+      const uint32_t fb = smem_u32(&full_bar[s]);
+      mbar_expect_tx(fb, tx_bytes);
+      for (int q = 0; q < ntap; ++q) {
+        const int t = t0 + q, kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
+        tma_load_5d(base + (uint32_t)q * a_box, &tm_x, 0, 2 * x0 + kx - 1, 2 * y0 + ky - 1,
+                    2 * z0 + kz - 1, b, fb);
+      }
+      for (int c = 0; c < Co / CKB; ++c)
+        tma_load_5d(base + a_bytes + (uint32_t)c * b_box, &tm_dy, c * CKB, x0, y0, z0, b, fb);
+    }
+  } else if (warp == 1 && lane == 0) {  // MMA issuer
+    const uint32_t idesc = instr_desc_mn(Co);
+    for (int k = 0; k < ksteps; ++k) {
+      const int s = k % nst;
+      if (!mbar_wait(smem_u32(&full_bar[s]), (k / nst) & 1)) {
+        atomicOr(err, kErrMma);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = smem_u32(smem + (size_t)s * stage_bytes);
+      const uint64_t a0 = smem_desc_mn<CKA>(base, a_box);
+      const uint64_t b0 = smem_desc_mn<CKB>(base + a_bytes, b_box);
+      const uint32_t alo = (uint32_t)a0, ahi = (uint32_t)(a0 >> 32);
+      const uint32_t blo = (uint32_t)b0, bhi = (uint32_t)(b0 >> 32);
+      mma_lh_p(tmem, alo, ahi, blo, bhi, idesc, k > 0 ? 1u : 0u);
+#pragma unroll
+      for (int kk = 1; kk < kBM / 16; ++kk)  // K = 16 voxels = two 8-row groups per MMA
+        mma_lh(tmem, alo + (uint32_t)((kk * 2 * 8 * CKA * 2) >> 4), ahi,
+               blo + (uint32_t)((kk * 2 * 8 * CKB * 2) >> 4), bhi, idesc);
+      mma_commit(smem_u32(&empty_bar[s]));
+    }
+    mma_commit(smem_u32(&done_bar));
+  }
+  __syncwarp();
+
+  const bool waited = ksteps > 0 ? mbar_wait(smem_u32(&done_bar), 0) : false;
+  const bool ok = __all_sync(0xffffffffu, waited);
+  if (!ok && ksteps > 0 && lane == 0) atomicOr(err, kErrEpilogue);
+  tc_fence_after();
+  const int m = warp * 32 + lane;  // TMEM lane = A row = (tap in group, ci)
+  const int q = m / Ci, ci = m % Ci;
+  const int t = t0 + q;
+  const long long row = (long long)Co * 27 * Ci + Co;
+  float* prow = part + ((long long)b * nchunks + chunk) * row;
+  for (int c0 = 0; c0 < Co; c0 += 16) {
+    uint32_t r[16];
+    if (ok) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+    if (q < ntap) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        prow[((long long)(c0 + j) * 27 + t) * Ci + ci] = ok ? __uint_as_float(r[j]) : 0.f;
+    } else if (ones && q == ntap && ci == 0) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        prow[(long long)Co * 27 * Ci + c0 + j] = ok ? __uint_as_float(r[j]) : 0.f;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(tmem_cols)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------------------------
 // Weight gradient of a 3x3x3 stride-1 layer with halo boxes.  K tile = one column of
 // 8 x 1 x TZ input voxels u (rows g * 8 + x, g = z offset).  With dy shifted by the tap,
 // dW[co][t][ci] = sum_u dy[u + 1 - k_t][co] x[u][ci]; for one x tap kx the dy values of all
@@ -1567,6 +1707,8 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
   }
   L.wgrad = s == 1 && co <= 128 && 128 % co == 0 && ci + chunk_for(ci) <= 256;
   L.wg3 = L.wgrad && wg3_geom(L, 1).nst > 0;
+  if (k == 3 && s == 2 && (ci == 16 || ci == 32 || ci == 64) && co % 16 == 0 && co <= 256)
+    L.wgrad = L.wgs2 = true;
   const long long n = (long long)co * k * k * k * ci;
   L.wf_off = bf.wstride;
   bf.wstride += (n + 63) / 64 * 64;
@@ -1819,10 +1961,47 @@ void launch_wg3(const TcLayer& L, const Wg3Geom& g, float* part, float* part_p, 
                                                            L.dout, L.ci, L.ci_real, g, err);
 }
 
+struct S2Plan {
+  int groups, tiles_x, tiles_y, ntiles, tiles_per_chunk, chunks, nst;
+  size_t stage, smem;
+};
+
+S2Plan wgs2_plan(const TcLayer& L, int B) {
+  S2Plan p{};
+  const int tpm = 128 / L.ci;
+  p.groups = (27 + 1 + tpm - 1) / tpm;  // 27 taps and the ones block
+  p.tiles_x = (int)ceil_div(L.dout.x, kBX);
+  p.tiles_y = (int)ceil_div(L.dout.y, kBY);
+  p.ntiles = p.tiles_x * p.tiles_y * (int)ceil_div(L.dout.z, kBZ);
+  const long long want = std::max(1LL, (long long)sm_count() / ((long long)p.groups * B));
+  p.tiles_per_chunk = (int)ceil_div(p.ntiles, std::min<long long>(want, p.ntiles));
+  p.chunks = (int)ceil_div(p.ntiles, p.tiles_per_chunk);
+  p.stage = (size_t)tpm * kBM * L.ci * 2 + (size_t)kBM * L.co * 2;
+  p.nst = (int)std::min<size_t>(kWgMaxStages, (200 * 1024) / p.stage);
+  p.smem = (size_t)p.nst * p.stage + 1024;
+  return p;
+}
+
+template <int CKA, int CKB>
+cudaError_t wgs2_attr() {
+  return cudaFuncSetAttribute(wgrad_s2_tc_kernel<CKA, CKB>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmemMax);
+}
+
+template <int CKA, int CKB>
+void launch_wgs2(const TcLayer& L, const S2Plan& p, float* part, int B, int* err,
+                 cudaStream_t st) {
+  dim3 grid((unsigned)p.chunks, (unsigned)p.groups, (unsigned)B);
+  wgrad_s2_tc_kernel<CKA, CKB><<<grid, 128, p.smem, st>>>(L.act_f, L.act_wy, part, L.dout, L.co,
+                                                          p.tiles_per_chunk, p.ntiles, p.tiles_x,
+                                                          p.tiles_y, p.chunks, p.nst, err);
+}
+
 }  // namespace
 
 long long bf16_wgrad_chunks(const Bf16Net& bf, int layer, int B) {
   const TcLayer& L = bf.layers[layer];
+  if (L.wgs2) return wgs2_plan(L, B).chunks;
   if (L.wg3) return wg3_geom(L, B, L.projw).nchunks;
   return wgrad_plan(L, B).chunks;
 }
@@ -1839,6 +2018,20 @@ cudaError_t bf16_conv_wgrad(Bf16Net& bf, int layer, const float* x, const float*
   if (e == cudaSuccess && !dy_staged)
     e = stage_bf16(dy, bf.ybf, (long long)B * L.dout.count() * L.co, stream);
   if (e != cudaSuccess) return e;
+  if (L.wgs2) {
+    const S2Plan p2 = wgs2_plan(L, B);
+    const int ckb = chunk_for(L.co);
+#define D2IP_WS2(A_, B_) launch_wgs2<A_, B_>(L, p2, part, B, bf.err, stream)
+    if (L.ci == 16) {
+      if (ckb == 16) D2IP_WS2(16, 16); else if (ckb == 32) D2IP_WS2(16, 32); else D2IP_WS2(16, 64);
+    } else if (L.ci == 32) {
+      if (ckb == 16) D2IP_WS2(32, 16); else if (ckb == 32) D2IP_WS2(32, 32); else D2IP_WS2(32, 64);
+    } else {
+      if (ckb == 16) D2IP_WS2(64, 16); else if (ckb == 32) D2IP_WS2(64, 32); else D2IP_WS2(64, 64);
+    }
+#undef D2IP_WS2
+    return cudaGetLastError();
+  }
   if (L.wg3) {
     const Wg3Geom g = wg3_geom(L, B, L.projw);
     if (L.projw) {  // the fused projection needs its dz_p staged (kept from the data gradient)
@@ -1907,6 +2100,15 @@ cudaError_t bf16_prepare_kernels() {
   if (e == cudaSuccess) e = wgrad_attr<64, 16>();
   if (e == cudaSuccess) e = wgrad_attr<64, 32>();
   if (e == cudaSuccess) e = wgrad_attr<64, 64>();
+  if (e == cudaSuccess) e = wgs2_attr<16, 16>();
+  if (e == cudaSuccess) e = wgs2_attr<16, 32>();
+  if (e == cudaSuccess) e = wgs2_attr<16, 64>();
+  if (e == cudaSuccess) e = wgs2_attr<32, 16>();
+  if (e == cudaSuccess) e = wgs2_attr<32, 32>();
+  if (e == cudaSuccess) e = wgs2_attr<32, 64>();
+  if (e == cudaSuccess) e = wgs2_attr<64, 16>();
+  if (e == cudaSuccess) e = wgs2_attr<64, 32>();
+  if (e == cudaSuccess) e = wgs2_attr<64, 64>();
   if (e == cudaSuccess) e = wg3_attr<16, 16>();
   if (e == cudaSuccess) e = wg3_attr<16, 32>();
   if (e == cudaSuccess) e = wg3_attr<16, 64>();

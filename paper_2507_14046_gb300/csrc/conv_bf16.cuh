@@ -25,7 +25,7 @@ struct TcLayer {
   long long w_off = 0;            // weights of this conv in the FP32 theta arena
   long long wf_off = 0, wd_off = 0;  // offsets in the per-problem BF16 weight block
   bool dgrad = false;             // data gradient on the tensor cores too (stride 1)
-  bool wgrad = false;             // weight gradient on the tensor cores too (3x3x3, stride 1)
+  bool wgrad = false;             // weight gradient on the tensor cores too (3x3x3)
   int ck3f = 0, ck3d = 0;         // channel chunk of the halo-box kernel (0: per-tap kernel)
   int tz3f = 1, tz3d = 1;         // z slices per halo-box tile
   int proj = -1;                  // layer index of a 1x1 projection of the same input, fused
@@ -33,6 +33,7 @@ struct TcLayer {
   CUtensorMap pw_f, pw_d, pa_d;   // projection: W_p, W_p^T and the dz_p tile box
   CUtensorMap wg_p3;              // projection: dz_p column of the halo weight gradient
   bool wg3 = false;               // weight gradient by the halo-box kernel
+  bool wgs2 = false;              // stride-2 weight gradient on the tensor cores
   __nv_bfloat16* xin = nullptr;   // BF16 copy of the forward input (kept for the weight gradient)
   int ci_real = 0;                // input channels of the model (ci is padded up to 16)
   bool input_layer = false;       // reads the padded BF16 copy of the network input (zbf)

@@ -291,18 +291,11 @@ constexpr int kJtmulMaxSmem = 200 * 1024;
 // block's partial sums; stage 2 adds the column chunks in order and subtracts dv.
 constexpr int kJRows = 4;
 constexpr int kJCols = 1024;
+constexpr int kTCols = 64, kTB = 16;  // transposed-J (BF16) forms: columns per block, problems
 
 __device__ __forceinline__ float to_f32(float v) { return v; }
-__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ float4 load4(const float* p) {
   return *reinterpret_cast<const float4*>(p);
-}
-__device__ __forceinline__ float4 load4(const __nv_bfloat16* p) {
-  const uint2 u = *reinterpret_cast<const uint2*>(p);
-  const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&u.x);
-  const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&u.y);
-  const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-  return make_float4(fa.x, fa.y, fb.x, fb.y);
 }
 
 template <typename JT>
@@ -363,14 +356,33 @@ jmul_part_kernel(const JT* __restrict__ J, const float* __restrict__ x,
   }
 }
 
-__global__ void jmul_final_kernel(const float* __restrict__ part, const float* __restrict__ dv,
-                                  float* __restrict__ r, int B, int m, int nchunks) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long long)B * m) return;
-  float s = 0.f;
-  for (int c = 0; c < nchunks; ++c) s += part[(long long)c * B * m + e];
-  r[e] = s - dv[e];
+// r[e] = sum_c part[c][e] - dv[e]: 32 columns x 8 chunk groups per block, the groups' sums
+// added in order.
+__global__ void __launch_bounds__(256)
+jmul_final_many_kernel(const float* __restrict__ part, const float* __restrict__ dv,
+                       float* __restrict__ r, long long N, int nchunks) {
+  __shared__ float red[8][33];
+  const int col = threadIdx.x % 32, grp = threadIdx.x / 32;
+  const long long e = (long long)blockIdx.x * 32 + col;
+  float s0 = 0.f, s1 = 0.f;
+  if (e < N) {
+    int c = grp;
+    for (; c + 8 < nchunks; c += 16) {
+      s0 += part[(long long)c * N + e];
+      s1 += part[(long long)(c + 8) * N + e];
+    }
+    if (c < nchunks) s0 += part[(long long)c * N + e];
+  }
+  red[grp][col] = s0 + s1;
+  __syncthreads();
+  if (grp == 0 && e < N) {
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += red[q][col];
+    r[e] = s - dv[e];
+  }
 }
+
 
 template <typename JT>
 __global__ void __launch_bounds__(256)
@@ -664,7 +676,10 @@ cudaError_t add_inplace_f32(float* y, const float* x, long long count, cudaStrea
   return cudaGetLastError();
 }
 
-int jmul_chunks(int n) { return (int)ceil_div(n, kJCols); }
+int jmul_chunks(int n) {
+  const long long a = ceil_div(n, kJCols), b = ceil_div(n, kTCols);
+  return (int)(a > b ? a : b);
+}
 
 template <typename JT>
 cudaError_t jmul_impl(const JT* J, const float* x, const float* dv, float* r, float* part, int B,
@@ -674,8 +689,8 @@ cudaError_t jmul_impl(const JT* J, const float* x, const float* dv, float* r, fl
   jmul_part_kernel<JT><<<grid, 256, 0, stream>>>(J, x, part, B, m, n, x_bs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  jmul_final_kernel<<<(unsigned)ceil_div((long long)B * m, 256), 256, 0, stream>>>(part, dv, r, B,
-                                                                                  m, nch);
+  jmul_final_many_kernel<<<(unsigned)ceil_div((long long)B * m, 32), 256, 0, stream>>>(
+      part, dv, r, (long long)B * m, nch);
   return cudaGetLastError();
 }
 
@@ -685,10 +700,139 @@ cudaError_t jmul_residual_f32(const float* J, const float* x, const float* dv, f
   return jmul_impl(J, x, dv, r, part, B, m, n, x_bs, stream);
 }
 
-cudaError_t jmul_residual_bf16(const __nv_bfloat16* J, const float* x, const float* dv, float* r,
+// ---- BF16 path: J stored transposed, Jt[n][m] (BF16) -------------------------------
+// r[b][i] = sum_j Jt[j][i] x[b][j] - dv[b][i]: a block takes kTCols columns j for up to kTB
+// problems; thread t owns the row pairs i = 2 p, 2 p + 1 (p = t + 256 s) and adds j in order;
+// per-block partial sums, then the chunks in order (jmul_final_kernel).
+template <int SLOTS>
+__global__ void __launch_bounds__(256)
+jmul_t_kernel(const __nv_bfloat16* __restrict__ Jt, const float* __restrict__ x,
+              float* __restrict__ part, int B, int m, int n, long long x_bs) {
+  __shared__ float xs[kTB][kTCols];
+  const int chunk = blockIdx.x, b0 = blockIdx.y * kTB;
+  const int nb = B - b0 < kTB ? B - b0 : kTB;
+  const int j0 = chunk * kTCols;
+  const int nj = n - j0 < kTCols ? n - j0 : kTCols;
+  for (int e = threadIdx.x; e < kTB * kTCols; e += blockDim.x) {
+    const int q = e / kTCols, jj = e % kTCols;
+    xs[q][jj] = (q < nb && jj < nj) ? x[(long long)(b0 + q) * x_bs + j0 + jj] : 0.f;
+  }
+  __syncthreads();
+  float acc[SLOTS][2][kTB];
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s)
+#pragma unroll
+    for (int q = 0; q < kTB; ++q) acc[s][0][q] = acc[s][1][q] = 0.f;
+  const int np = m / 2;
+#pragma unroll 8
+  for (int jj = 0; jj < nj; ++jj) {
+    const __nv_bfloat162* row =
+        reinterpret_cast<const __nv_bfloat162*>(Jt + (long long)(j0 + jj) * m);
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const int pi = threadIdx.x + 256 * s;
+      if (pi >= np) break;
+      const float2 a = __bfloat1622float2(row[pi]);
+#pragma unroll
+      for (int q = 0; q < kTB; ++q) {
+        const float xv = xs[q][jj];
+        acc[s][0][q] = fmaf(a.x, xv, acc[s][0][q]);
+        acc[s][1][q] = fmaf(a.y, xv, acc[s][1][q]);
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s) {
+    const int pi = threadIdx.x + 256 * s;
+    if (pi >= np) break;
+#pragma unroll
+    for (int q = 0; q < kTB; ++q)
+      if (q < nb) {
+        float* o = part + ((long long)chunk * B + b0 + q) * m + 2 * pi;
+        o[0] = acc[s][0][q];
+        o[1] = acc[s][1][q];
+      }
+  }
+}
+
+// g[b][j] = scale sum_i Jt[j][i] r[b][i]: a thread per column j (kJtRows per block) keeps
+// the kTB problems' sums; the block stages r and, chunk by chunk along i, a tile of Jt rows
+// (coalesced) in shared memory; i is added in order.
+constexpr int kJtRows = 128, kJtChunk = 64;
+
+__global__ void __launch_bounds__(kJtRows)
+jtmul_t_kernel(const __nv_bfloat16* __restrict__ Jt, const float* __restrict__ r,
+               float* __restrict__ g, float scale, int B, int m, int n, long long g_bs) {
+  extern __shared__ float rs[];  // [kTB][m], then the Jt tile
+  __nv_bfloat16* jt = reinterpret_cast<__nv_bfloat16*>(rs + kTB * m);  // [kJtRows][kJtChunk + 8]
+  constexpr int kLd = kJtChunk + 8;  // padded row (bf16): 144 bytes
+  const int b0 = blockIdx.y * kTB;
+  const int nb = B - b0 < kTB ? B - b0 : kTB;
+  for (int e = threadIdx.x; e < kTB * m; e += blockDim.x)
+    rs[e] = e < nb * m ? r[(long long)b0 * m + e] : 0.f;
+  const long long j0 = (long long)blockIdx.x * kJtRows;
+  const long long j = j0 + threadIdx.x;
+  float acc[kTB];
+#pragma unroll
+  for (int q = 0; q < kTB; ++q) acc[q] = 0.f;
+  for (int i0 = 0; i0 < m; i0 += kJtChunk) {
+    const int ni = m - i0 < kJtChunk ? m - i0 : kJtChunk;  // a multiple of 4
+    __syncthreads();
+    // tile: rows j0 .. j0 + 127, columns i0 .. i0 + ni - 1, 8-byte pieces
+    for (int e = threadIdx.x; e < kJtRows * (kJtChunk / 4); e += blockDim.x) {
+      const int row = e / (kJtChunk / 4), c4 = (e % (kJtChunk / 4)) * 4;
+      uint2 v = make_uint2(0u, 0u);
+      if (j0 + row < n && c4 < ni)
+        v = *reinterpret_cast<const uint2*>(Jt + (j0 + row) * m + i0 + c4);
+      *reinterpret_cast<uint2*>(jt + row * kLd + c4) = v;
+    }
+    __syncthreads();
+    for (int c = 0; c < ni; c += 4) {
+      const uint2 u = *reinterpret_cast<const uint2*>(jt + threadIdx.x * kLd + c);
+      const float2 a01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+      const float2 a23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+#pragma unroll
+      for (int q = 0; q < kTB; ++q) {
+        const float4 rv = *reinterpret_cast<const float4*>(rs + q * m + i0 + c);
+        acc[q] = fmaf(a01.x, rv.x, fmaf(a01.y, rv.y, fmaf(a23.x, rv.z, fmaf(a23.y, rv.w, acc[q]))));
+      }
+    }
+  }
+  if (j < n)
+    for (int q = 0; q < nb; ++q) g[(long long)(b0 + q) * g_bs + j] = scale * acc[q];
+}
+
+// J [m][n] FP32 -> Jt [n][m] BF16 through 32 x 32 shared-memory tiles.
+__global__ void transpose_bf16_kernel(const float* __restrict__ J, __nv_bfloat16* __restrict__ Jt,
+                                      int m, int n) {
+  __shared__ float t[32][33];
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int i = i0 + k, j = j0 + threadIdx.x;
+    t[k][threadIdx.x] = (i < m && j < n) ? J[(long long)i * n + j] : 0.f;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int j = j0 + k, i = i0 + threadIdx.x;
+    if (i < m && j < n) Jt[(long long)j * m + i] = __float2bfloat16_rn(t[threadIdx.x][k]);
+  }
+}
+
+cudaError_t jmul_residual_bf16(const __nv_bfloat16* Jt, const float* x, const float* dv, float* r,
                                float* part, int B, int m, int n, long long x_bs,
                                cudaStream_t stream) {
-  return jmul_impl(J, x, dv, r, part, B, m, n, x_bs, stream);
+  if (m % 4 || m > 1024) return cudaErrorInvalidValue;
+  const int nch = (int)ceil_div(n, kTCols);
+  dim3 grid((unsigned)nch, (unsigned)ceil_div(B, kTB));
+  if (m / 2 <= 256)
+    jmul_t_kernel<1><<<grid, 256, 0, stream>>>(Jt, x, part, B, m, n, x_bs);
+  else
+    jmul_t_kernel<2><<<grid, 256, 0, stream>>>(Jt, x, part, B, m, n, x_bs);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  jmul_final_many_kernel<<<(unsigned)ceil_div((long long)B * m, 32), 256, 0, stream>>>(
+      part, dv, r, (long long)B * m, nch);
+  return cudaGetLastError();
 }
 
 template <typename JT>
@@ -706,9 +850,19 @@ cudaError_t jtmul_f32(const float* J, const float* r, float* g, float scale, int
   return jtmul_impl(J, r, g, scale, B, m, n, g_bs, stream);
 }
 
-cudaError_t jtmul_bf16(const __nv_bfloat16* J, const float* r, float* g, float scale, int B,
+cudaError_t jtmul_bf16(const __nv_bfloat16* Jt, const float* r, float* g, float scale, int B,
                        int m, int n, long long g_bs, cudaStream_t stream) {
-  return jtmul_impl(J, r, g, scale, B, m, n, g_bs, stream);
+  const size_t smem = (size_t)kTB * m * sizeof(float) + (size_t)kJtRows * (kJtChunk + 8) * 2;
+  if (m % 4 || smem > (size_t)kJtmulMaxSmem) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)ceil_div(n, kJtRows), (unsigned)ceil_div(B, kTB));
+  jtmul_t_kernel<<<grid, kJtRows, smem, stream>>>(Jt, r, g, scale, B, m, n, g_bs);
+  return cudaGetLastError();
+}
+
+cudaError_t transpose_bf16(const float* J, __nv_bfloat16* Jt, int m, int n, cudaStream_t stream) {
+  dim3 grid((unsigned)ceil_div(n, 32), (unsigned)ceil_div(m, 32));
+  transpose_bf16_kernel<<<grid, dim3(32, 8), 0, stream>>>(J, Jt, m, n);
+  return cudaGetLastError();
 }
 
 __global__ void to_bf16_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ y,
@@ -726,8 +880,8 @@ cudaError_t prepare_pointwise_kernels() {
   cudaError_t e = cudaFuncSetAttribute(jtmul_kernel<float>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kJtmulMaxSmem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(jtmul_kernel<__nv_bfloat16>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, kJtmulMaxSmem);
+  return cudaFuncSetAttribute(jtmul_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kJtmulMaxSmem);
 }
 
 cudaError_t residual_loss_f64(const float* r, double* loss, double* trace, int* trace_pos,

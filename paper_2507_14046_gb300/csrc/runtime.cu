@@ -101,7 +101,7 @@ struct d2ip_ctx {
   float* hist = nullptr;       // previous frames' outputs [B][hist_cap][n]
   int hist_cap = 0;
   float* J = nullptr;
-  __nv_bfloat16* Jbf = nullptr;  // BF16 copy of the normalised J (BF16 precision)
+  __nv_bfloat16* Jbf = nullptr;  // BF16 copy of the normalised J, transposed [n][m] (BF16)
   float* jpart = nullptr;  // column-chunk partial sums of J x
   double* colnorm = nullptr;
   size_t j_bytes = 0;
@@ -993,6 +993,8 @@ d2ip_status d2ip_load_J(d2ip_ctx* c, const float* J, int m, int n, int normalize
     return fail(c, D2IP_ERR_BAD_SHAPE, "J must be m x (X*Y*Z)");
   if ((size_t)8 * m * sizeof(float) > 200 * 1024)
     return fail(c, D2IP_ERR_BAD_SHAPE, "m too large for the adjoint kernel (max 6400)");
+  if (c->precision == D2IP_BF16 && (m % 4 != 0 || m > 1024))
+    return fail(c, D2IP_ERR_BAD_SHAPE, "the BF16 path needs m a multiple of 4, at most 1024");
   CK(cudaSetDevice(c->device));
   d2ip_status s = ensure_arena(c);
   if (s) return s;
@@ -1027,7 +1029,7 @@ d2ip_status d2ip_load_J(d2ip_ctx* c, const float* J, int m, int n, int normalize
   } else {
     CK(cudaMemsetAsync(c->colnorm, 0, sizeof(double) * n, c->stream));
   }
-  if (c->precision == D2IP_BF16) CK(convert_bf16(c->J, c->Jbf, (long long)m * n, c->stream));
+  if (c->precision == D2IP_BF16) CK(transpose_bf16(c->J, c->Jbf, m, (int)n, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->j_ready = true;
   return D2IP_OK;
