@@ -207,6 +207,87 @@ __global__ void up_concat_fwd_kernel(const float* __restrict__ low,
   *reinterpret_cast<float4*>(cat + ((long long)b * nout + vox) * Ct + c) = val;
 }
 
+// Factor-2 form (every output extent twice the input's): a thread takes one input voxel i
+// and one group of 4 channels and writes the 2 x 2 x 2 outputs 2i + a.  Along an axis output
+// 2i reads (i - 1, i) with weights (1/4, 3/4) and 2i + 1 reads (i, i + 1) with (3/4, 1/4);
+// the neighbours are loaded with clamped indices, which reproduces the clamped map at the
+// borders.  Groups past Cu copy the skip channels of the 8 outputs.
+__global__ void __launch_bounds__(256)
+up2_concat_fwd_kernel(const float* __restrict__ low, const float* __restrict__ skip,
+                      float* __restrict__ cat, Dims3 dl, Dims3 dout, int Cu, int Cs) {
+  const int b = blockIdx.y;
+  const int Ct = Cu + Cs, G = Ct / 4;
+  const long long nl = dl.count();
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nl * G) return;
+  const long long vox = e / G;
+  const int c = (int)(e % G) * 4;
+  const int ix = (int)(vox % dl.x);
+  const int rr = (int)(vox / dl.x);
+  const int iy = rr % dl.y, iz = rr / dl.y;
+  const long long nout = dout.count();
+  float* C = cat + (long long)b * nout * Ct + c;
+  auto out_at = [&](int a, int bb, int cc) -> float4* {
+    const long long o = ((long long)(2 * iz + a) * dout.y + (2 * iy + bb)) * dout.x + (2 * ix + cc);
+    return reinterpret_cast<float4*>(C + o * Ct);
+  };
+  if (c >= Cu) {  // skip channels of the 8 outputs
+    const float* S = skip + (long long)b * nout * Cs + (c - Cu);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const long long o =
+              ((long long)(2 * iz + a) * dout.y + (2 * iy + bb)) * dout.x + (2 * ix + cc);
+          *out_at(a, bb, cc) = *reinterpret_cast<const float4*>(S + o * Cs);
+        }
+    return;
+  }
+  const float* L = low + (long long)b * nl * Cu + c;
+  const int zs[3] = {iz > 0 ? iz - 1 : 0, iz, iz + 1 < dl.z ? iz + 1 : dl.z - 1};
+  const int ys[3] = {iy > 0 ? iy - 1 : 0, iy, iy + 1 < dl.y ? iy + 1 : dl.y - 1};
+  const int xs[3] = {ix > 0 ? ix - 1 : 0, ix, ix + 1 < dl.x ? ix + 1 : dl.x - 1};
+  // along x first: for each (z, y) neighbour row the two x outputs
+  float4 rx[3][3][2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float4 v[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        v[i] = *reinterpret_cast<const float4*>(
+            L + (((long long)zs[k] * dl.y + ys[j]) * dl.x + xs[i]) * Cu);
+      rx[k][j][0] = make_float4(0.25f * v[0].x + 0.75f * v[1].x, 0.25f * v[0].y + 0.75f * v[1].y,
+                                0.25f * v[0].z + 0.75f * v[1].z, 0.25f * v[0].w + 0.75f * v[1].w);
+      rx[k][j][1] = make_float4(0.75f * v[1].x + 0.25f * v[2].x, 0.75f * v[1].y + 0.25f * v[2].y,
+                                0.75f * v[1].z + 0.25f * v[2].z, 0.75f * v[1].w + 0.25f * v[2].w);
+    }
+  const float w[2][2] = {{0.25f, 0.75f}, {0.75f, 0.25f}};  // [output parity][first, second]
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc) {
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+          for (int dy = 0; dy < 2; ++dy) {
+            const float wv = w[a][dz] * w[bb][dy];
+            const float4 t = rx[a + dz][bb + dy][cc];
+            o.x = fmaf(wv, t.x, o.x);
+            o.y = fmaf(wv, t.y, o.y);
+            o.z = fmaf(wv, t.z, o.z);
+            o.w = fmaf(wv, t.w, o.w);
+          }
+        *out_at(a, bb, cc) = o;
+      }
+}
+
 // Output positions along one axis that read input index i, with their weights.
 __device__ __forceinline__ int axis_sources(int i, int s_in, int s_out, int* os, float* ws) {
   // outputs o with i0(o) or i1(o) == i satisfy (i - 1/2) r - 1/2 < o < (i + 3/2) r - 1/2,
@@ -654,6 +735,11 @@ cudaError_t upsample_concat_fwd_f32(const float* low, const float* skip, float* 
   if (Cu % 4 || Cs % 4) return cudaErrorInvalidValue;
   const long long total = dout.count() * ((Cu + Cs) / 4);
   dim3 grid((unsigned)ceil_div(total, 256), B);
+  if (dout.x == 2 * dlow.x && dout.y == 2 * dlow.y && dout.z == 2 * dlow.z) {
+    dim3 g2((unsigned)ceil_div(dlow.count() * ((Cu + Cs) / 4), 256), B);
+    up2_concat_fwd_kernel<<<g2, 256, 0, stream>>>(low, skip, cat, dlow, dout, Cu, Cs);
+    return cudaGetLastError();
+  }
   up_concat_fwd_kernel<<<grid, 256, 0, stream>>>(low, skip, cat, dlow, dout, Cu, Cs);
   return cudaGetLastError();
 }
@@ -708,7 +794,7 @@ template <int SLOTS>
 __global__ void __launch_bounds__(256)
 jmul_t_kernel(const __nv_bfloat16* __restrict__ Jt, const float* __restrict__ x,
               float* __restrict__ part, int B, int m, int n, long long x_bs) {
-  __shared__ float xs[kTB][kTCols];
+  __shared__ __align__(16) float xs[kTB][kTCols];
   const int chunk = blockIdx.x, b0 = blockIdx.y * kTB;
   const int nb = B - b0 < kTB ? B - b0 : kTB;
   const int j0 = chunk * kTCols;
@@ -724,20 +810,27 @@ jmul_t_kernel(const __nv_bfloat16* __restrict__ Jt, const float* __restrict__ x,
 #pragma unroll
     for (int q = 0; q < kTB; ++q) acc[s][0][q] = acc[s][1][q] = 0.f;
   const int np = m / 2;
-#pragma unroll 8
-  for (int jj = 0; jj < nj; ++jj) {
-    const __nv_bfloat162* row =
-        reinterpret_cast<const __nv_bfloat162*>(Jt + (long long)(j0 + jj) * m);
+  // four columns per step: their J pairs from global memory, x from shared memory as float4
+  // (columns past n carry x = 0 and read row n - 1, which exists)
+  for (int jj = 0; jj < nj; jj += 4) {
+    const __nv_bfloat162* rows[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int jr = j0 + jj + u < n ? j0 + jj + u : n - 1;
+      rows[u] = reinterpret_cast<const __nv_bfloat162*>(Jt + (long long)jr * m);
+    }
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
       const int pi = threadIdx.x + 256 * s;
       if (pi >= np) break;
-      const float2 a = __bfloat1622float2(row[pi]);
+      float2 a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = __bfloat1622float2(rows[u][pi]);
 #pragma unroll
       for (int q = 0; q < kTB; ++q) {
-        const float xv = xs[q][jj];
-        acc[s][0][q] = fmaf(a.x, xv, acc[s][0][q]);
-        acc[s][1][q] = fmaf(a.y, xv, acc[s][1][q]);
+        const float4 xv = *reinterpret_cast<const float4*>(&xs[q][jj]);
+        acc[s][0][q] = fmaf(a[3].x, xv.w, fmaf(a[2].x, xv.z, fmaf(a[1].x, xv.y, fmaf(a[0].x, xv.x, acc[s][0][q]))));
+        acc[s][1][q] = fmaf(a[3].y, xv.w, fmaf(a[2].y, xv.z, fmaf(a[1].y, xv.y, fmaf(a[0].y, xv.x, acc[s][1][q]))));
       }
     }
   }
@@ -798,8 +891,11 @@ jtmul_t_kernel(const __nv_bfloat16* __restrict__ Jt, const float* __restrict__ r
       }
     }
   }
-  if (j < n)
-    for (int q = 0; q < nb; ++q) g[(long long)(b0 + q) * g_bs + j] = scale * acc[q];
+  if (j < n) {
+#pragma unroll
+    for (int q = 0; q < kTB; ++q)
+      if (q < nb) g[(long long)(b0 + q) * g_bs + j] = scale * acc[q];
+  }
 }
 
 // J [m][n] FP32 -> Jt [n][m] BF16 through 32 x 32 shared-memory tiles.
