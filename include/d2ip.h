@@ -186,6 +186,11 @@ d2ip_status d2ip_err_ratio(d2ip_ctx* ctx, const float* est, const float* truth, 
 d2ip_status d2ip_profile_iterations(d2ip_ctx* ctx, const float* dV, int n_iters, double* ms,
                                     double* work, long long* launches);
 
+/* Kernel launches of one training iteration (the captured step graph: forward, data term,
+ * backward, Adam) and of one evaluation (forward and data term), counted as the kernel
+ * nodes of the CUDA graphs the context replays (captured here if not yet). */
+d2ip_status d2ip_graph_kernels(d2ip_ctx* ctx, long long* step_kernels, long long* eval_kernels);
+
 /* Wait for the context's stream; report asynchronous CUDA errors. */
 d2ip_status d2ip_sync(d2ip_ctx* ctx);
 /* Message of the last failure of `ctx` (NULL: of the calling thread's op calls). */

@@ -59,6 +59,7 @@ _SIGS = {
     "d2ip_err_ratio": [_vp, _vp, _vp, _vp],
     "d2ip_sync": [_vp],
     "d2ip_profile_iterations": [_vp, _vp, _i, _vp, _vp, _vp],
+    "d2ip_graph_kernels": [_vp, _vp, _vp],
     "d2ip_conv3d_forward": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _ll, _vp],
     "d2ip_conv3d_dgrad": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _ll, _i, _vp],
     "d2ip_conv3d_wgrad": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _ll, _i, _vp, _ll,
@@ -214,7 +215,7 @@ for _name in ("d2ip_set_grid", "d2ip_load_J", "d2ip_get_colnorms", "d2ip_set_inp
               "d2ip_set_optim", "d2ip_set_regularizer", "d2ip_reset_optimizer",
               "d2ip_run_steps", "d2ip_forward",
               "d2ip_get_grad", "d2ip_fit_frame", "d2ip_fit_sequence", "d2ip_set_state",
-              "d2ip_err_ratio", "d2ip_sync", "d2ip_profile_iterations"):
+              "d2ip_err_ratio", "d2ip_sync", "d2ip_profile_iterations", "d2ip_graph_kernels"):
     globals()[_name] = _wrap_ctx(_name)
 for _name in ("d2ip_conv3d_forward", "d2ip_conv3d_dgrad", "d2ip_conv3d_wgrad",
               "d2ip_conv3d_wgrad_noalloc", "d2ip_conv3d_forward_tc", "d2ip_conv3d_dgrad_tc",
@@ -330,6 +331,12 @@ class Context:
         cnt = np.zeros(k, dtype=np.int64)
         d2ip_profile_iterations(self.handle, dV, n_iters, ms, work, cnt)
         return {name: (ms[i], work[i], int(cnt[i])) for i, name in enumerate(KCLASSES)}
+
+    def graph_kernels(self):
+        """Kernel launches of one training iteration and of one evaluation (graph nodes)."""
+        st, ev = np.zeros(1, dtype=np.int64), np.zeros(1, dtype=np.int64)
+        d2ip_graph_kernels(self.handle, st, ev)
+        return int(st[0]), int(ev[0])
 
     def err_ratio(self, est, truth):
         out = np.zeros(self.batch, dtype=np.float64)

@@ -110,6 +110,7 @@ struct d2ip_ctx {
 
   // graphs
   cudaGraphExec_t g_step = nullptr, g_eval = nullptr;
+  long long step_kernels = 0, eval_kernels = 0;  // kernel nodes of the captured graphs
 
   long long n() const { return (long long)X * Y * Z; }
 };
@@ -682,6 +683,23 @@ d2ip_status capture(d2ip_ctx* c, bool step, cudaGraphExec_t* out) {
     return cuda_fail(c, Lr.e, "kernel launch during capture");
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+  size_t nn = 0;
+  e = cudaGraphGetNodes(g, nullptr, &nn);
+  long long nk = 0;
+  if (e == cudaSuccess && nn) {
+    std::vector<cudaGraphNode_t> nodes(nn);
+    e = cudaGraphGetNodes(g, nodes.data(), &nn);
+    for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
+      cudaGraphNodeType t;
+      e = cudaGraphNodeGetType(nodes[i], &t);
+      if (e == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+    }
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(c, e, "cudaGraphGetNodes");
+  }
+  (step ? c->step_kernels : c->eval_kernels) = nk;
   e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
@@ -1295,6 +1313,15 @@ d2ip_status d2ip_profile_iterations(d2ip_ctx* c, const float* dV, int n_iters, d
   tr.release();
   if (e != cudaSuccess) return cuda_fail(c, e, "profiled iterations");
   return check_status(c);
+}
+
+d2ip_status d2ip_graph_kernels(d2ip_ctx* c, long long* step_kernels, long long* eval_kernels) {
+  d2ip_status s = ready(c);
+  if (s) return s;
+  if (!step_kernels || !eval_kernels) return fail(c, D2IP_ERR_BAD_ARG, "null output");
+  *step_kernels = c->step_kernels;
+  *eval_kernels = c->eval_kernels;
+  return D2IP_OK;
 }
 
 d2ip_status d2ip_sync(d2ip_ctx* c) {
