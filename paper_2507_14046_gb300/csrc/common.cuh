@@ -52,19 +52,22 @@ cudaError_t reduce_rows_f32(const float* part, float* out, int B, long long R, l
 
 // LayerNorm over channels (+ residual) (+ LeakyReLU).
 int layernorm_bwd_blocks(long long nvox, int C);
+// ybf (optional): a BF16 copy of y (the next tensor-core convolution's staged input).
 cudaError_t layernorm_act_fwd_f32(const float* z, const float* gamma, const float* resid,
                                   float* y, float* xhat, float* rstd, int B, long long nvox,
-                                  int C, int act, long long g_bs, cudaStream_t stream);
-// part: [B][blocks][2C] partial (dgamma, dbeta).
+                                  int C, int act, long long g_bs, cudaStream_t stream,
+                                  __nv_bfloat16* ybf = nullptr);
+// part: [B][blocks][2C] partial (dgamma, dbeta); dzbf, dtbf (optional): BF16 copies of dz, dt.
 cudaError_t layernorm_act_bwd_f32(const float* dy, const float* act_out, const float* xhat,
                                   const float* rstd, const float* gamma, float* dz, float* dt,
                                   float* part, int B, long long nvox, int C, long long g_bs,
-                                  cudaStream_t stream);
+                                  cudaStream_t stream, __nv_bfloat16* dzbf = nullptr,
+                                  __nv_bfloat16* dtbf = nullptr);
 
-// cat[:, :Cu] = trilinear(low -> dout), cat[:, Cu:] = skip.
+// cat[:, :Cu] = trilinear(low -> dout), cat[:, Cu:] = skip; catbf (optional): a BF16 copy.
 cudaError_t upsample_concat_fwd_f32(const float* low, const float* skip, float* cat, int B,
                                     Dims3 dlow, Dims3 dout, int Cu, int Cs,
-                                    cudaStream_t stream);
+                                    cudaStream_t stream, __nv_bfloat16* catbf = nullptr);
 // dlow = adjoint of the upsample applied to dcat[:, :Cu]; dskip = dcat[:, Cu:].
 cudaError_t upsample_concat_bwd_f32(const float* dcat, float* dlow, float* dskip, int B,
                                     Dims3 dlow_dims, Dims3 dout, int Cu, int Cs,

@@ -2191,10 +2191,12 @@ int bf16_fuse_proj(Bf16Net& bf, int la, int lp) {
 
 cudaError_t bf16_conv_fwd_proj(Bf16Net& bf, int la, const float* x, const float* bias_a,
                                float* y_a, const float* bias_p, float* y_p, int B,
-                               long long bias_bs, cudaStream_t stream) {
+                               long long bias_bs, cudaStream_t stream, bool x_staged) {
   const TcLayer& L = bf.layers[la];
   if (!L.projf) return cudaErrorInvalidValue;
-  cudaError_t e = stage_bf16(x, L.xin, (long long)B * L.din.count() * L.ci, stream);
+  cudaError_t e = x_staged && bf.keep_inputs
+                      ? cudaSuccess
+                      : stage_bf16(x, L.xin, (long long)B * L.din.count() * L.ci, stream);
   if (e != cudaSuccess) return e;
   return launch_tc3(L.act_f3, L.w_f3, L.ci, L.ck3f, L.tz3f, bias_a, y_a, L.dout, L.co, B,
                     L.dout.count() * L.co, bias_bs, 0, bf.err, stream, 1, &L.pw_f, nullptr,
@@ -2202,12 +2204,13 @@ cudaError_t bf16_conv_fwd_proj(Bf16Net& bf, int la, const float* x, const float*
 }
 
 cudaError_t bf16_conv_dgrad_proj(Bf16Net& bf, int la, const float* dz_a, const float* dz_p,
-                                 float* dx, int B, cudaStream_t stream) {
+                                 float* dx, int B, cudaStream_t stream, bool dza_staged,
+                                 bool dzp_staged) {
   const TcLayer& L = bf.layers[la];
   if (!L.projd) return cudaErrorInvalidValue;
   const long long n = (long long)B * L.dout.count() * L.co;
-  cudaError_t e = stage_bf16(dz_a, bf.ybf, n, stream);
-  if (e == cudaSuccess) e = stage_bf16(dz_p, bf.pbf, n, stream);
+  cudaError_t e = dza_staged ? cudaSuccess : stage_bf16(dz_a, bf.ybf, n, stream);
+  if (e == cudaSuccess && !dzp_staged) e = stage_bf16(dz_p, bf.pbf, n, stream);
   if (e != cudaSuccess) return e;
   return launch_tc3(L.act_d3, L.w_d3, L.co, L.ck3d, L.tz3d, nullptr, dx, L.din, L.ci, B,
                     L.din.count() * L.ci, 0, 0, bf.err, stream, 2, &L.pw_d, &L.pa_d);
@@ -2222,11 +2225,17 @@ cudaError_t bf16_stage_input(Bf16Net& bf, int layer, const float* z, int B, cuda
   return cudaGetLastError();
 }
 
-cudaError_t bf16_conv_fwd(Bf16Net& bf, int layer, const float* x, const float* bias, float* y,
-                          int B, long long bias_bs, cudaStream_t stream) {
+__nv_bfloat16* bf16_input_buffer(const Bf16Net& bf, int layer) {
   const TcLayer& L = bf.layers[layer];
-  cudaError_t e =
-      L.input_layer ? cudaSuccess : stage_bf16(x, L.xin, (long long)B * L.din.count() * L.ci, stream);
+  return bf.keep_inputs && !L.input_layer ? L.xin : nullptr;
+}
+
+cudaError_t bf16_conv_fwd(Bf16Net& bf, int layer, const float* x, const float* bias, float* y,
+                          int B, long long bias_bs, cudaStream_t stream, bool x_staged) {
+  const TcLayer& L = bf.layers[layer];
+  cudaError_t e = L.input_layer || (x_staged && bf.keep_inputs)
+                      ? cudaSuccess
+                      : stage_bf16(x, L.xin, (long long)B * L.din.count() * L.ci, stream);
   if (e != cudaSuccess) return e;
   if (L.ck3f)
     return launch_tc3(L.act_f3, L.w_f3, L.ci, L.ck3f, L.tz3f, bias, y, L.dout, L.co, B,
@@ -2237,10 +2246,11 @@ cudaError_t bf16_conv_fwd(Bf16Net& bf, int layer, const float* x, const float* b
 }
 
 cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, int B,
-                            int accumulate, cudaStream_t stream) {
+                            int accumulate, cudaStream_t stream, bool dy_staged) {
   const TcLayer& L = bf.layers[layer];
   if (!L.dgrad) return cudaErrorInvalidValue;
-  cudaError_t e = stage_bf16(dy, bf.ybf, (long long)B * L.dout.count() * L.co, stream);
+  cudaError_t e =
+      dy_staged ? cudaSuccess : stage_bf16(dy, bf.ybf, (long long)B * L.dout.count() * L.co, stream);
   if (e != cudaSuccess) return e;
   if (L.s == 2) {
     const Dims3 q{(L.din.z + 1) / 2, (L.din.y + 1) / 2, (L.din.x + 1) / 2};

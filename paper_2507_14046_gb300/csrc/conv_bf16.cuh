@@ -72,10 +72,12 @@ int bf16_fuse_proj(Bf16Net& bf, int la, int lp);
 // y_a = conv_a(x) + bias_a and y_p = W_p x + bias_p in one launch (layer la with projf).
 cudaError_t bf16_conv_fwd_proj(Bf16Net& bf, int la, const float* x, const float* bias_a,
                                float* y_a, const float* bias_p, float* y_p, int B,
-                               long long bias_bs, cudaStream_t stream);
-// dx = conv_a^T(dz_a) + W_p^T dz_p in one launch (layer la with projd).
+                               long long bias_bs, cudaStream_t stream, bool x_staged = false);
+// dx = conv_a^T(dz_a) + W_p^T dz_p in one launch (layer la with projd); dz_a is staged into
+// bf.ybf and dz_p into bf.pbf unless their producer already wrote them there.
 cudaError_t bf16_conv_dgrad_proj(Bf16Net& bf, int la, const float* dz_a, const float* dz_p,
-                                 float* dx, int B, cudaStream_t stream);
+                                 float* dx, int B, cudaStream_t stream, bool dza_staged = false,
+                                 bool dzp_staged = false);
 // Reserve the BF16 buffers in the arena (base == nullptr: size only).
 void bf16_layout(Bf16Net& bf, char* base, size_t& used, int B, long long max_act);
 // Encode the TMA descriptors once the buffers have addresses.
@@ -84,12 +86,16 @@ cudaError_t bf16_prepare_kernels();
 // theta (FP32, [B][Pp]) -> BF16 forward and data-gradient weights of every layer.
 cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long long Pp,
                                  cudaStream_t stream);
-// y = conv(x) + bias on the tensor cores (x FP32 is staged to BF16 first).
+// The layer's kept BF16 input copy, when a producer may write it directly (keep_inputs);
+// else nullptr.
+__nv_bfloat16* bf16_input_buffer(const Bf16Net& bf, int layer);
+// y = conv(x) + bias on the tensor cores (x FP32 is staged to BF16 first unless x_staged:
+// its producer already wrote bf16_input_buffer).
 cudaError_t bf16_conv_fwd(Bf16Net& bf, int layer, const float* x, const float* bias, float* y,
-                          int B, long long bias_bs, cudaStream_t stream);
-// dx (=|+=) data gradient of a stride-1 layer on the tensor cores.
+                          int B, long long bias_bs, cudaStream_t stream, bool x_staged = false);
+// dx (=|+=) data gradient on the tensor cores (dy staged into bf.ybf unless dy_staged).
 cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, int B,
-                            int accumulate, cudaStream_t stream);
+                            int accumulate, cudaStream_t stream, bool dy_staged = false);
 
 // Partial-sum rows (chunks of output voxels) of a tensor-core weight gradient.
 long long bf16_wgrad_chunks(const Bf16Net& bf, int layer, int B);

@@ -423,6 +423,26 @@ struct Launcher {
   d2ip_ctx* c;
   Tracer* tr = nullptr;
   cudaError_t e = cudaSuccess;
+  // BF16 staging done by producers (BF16 precision): layers whose kept input copy the
+  // producing kernel wrote this pass, the layer whose dy sits in the dy staging buffer, and
+  // the block whose projection dy sits in the projection staging buffer.
+  std::vector<const ConvL*> staged_x;
+  const ConvL* ybf_owner = nullptr;
+  const void* pbf_owner = nullptr;
+  __nv_bfloat16* bf_in(const ConvL* L) {
+    return L && L->tc >= 0 && c->precision == D2IP_BF16 ? bf16_input_buffer(c->bf, L->tc)
+                                                        : nullptr;
+  }
+  bool take_staged(const ConvL& L) {
+    auto it = std::find(staged_x.begin(), staged_x.end(), &L);
+    if (it == staged_x.end()) return false;
+    staged_x.erase(it);
+    return true;
+  }
+  bool tc_dy_consumer(const ConvL* L) {
+    return L && L->tc >= 0 && c->precision == D2IP_BF16 &&
+           (c->bf.layers[L->tc].dgrad || c->bf.layers[L->tc].wgrad);
+  }
   void ok(cudaError_t x) {
     if (e == cudaSuccess) e = x;
   }
@@ -442,7 +462,8 @@ struct Launcher {
   void conv_fwd(const ConvL& L, const float* x, float* y) {
     beg(D2IP_KCLASS_CONV_FWD, conv_flops(L));
     if (L.tc >= 0) {
-      ok(bf16_conv_fwd(c->bf, L.tc, x, W(L) + L.wcount(), y, c->B, c->Pp, c->stream));
+      ok(bf16_conv_fwd(c->bf, L.tc, x, W(L) + L.wcount(), y, c->B, c->Pp, c->stream,
+                       take_staged(L)));
     } else {
       ok(conv3d_fwd_f32(x, W(L), W(L) + L.wcount(), y, c->B, L.din, L.ci, L.co, L.k, L.s,
                         L.din.count() * L.ci, L.dout.count() * L.co, c->Pp, c->stream));
@@ -451,20 +472,20 @@ struct Launcher {
   }
   void conv_dgrad(const ConvL& L, const float* dy, float* dx, int acc) {
     beg(D2IP_KCLASS_CONV_DGRAD, conv_flops(L));
-    if (L.tc >= 0 && c->bf.layers[L.tc].dgrad)
-      ok(bf16_conv_dgrad(c->bf, L.tc, dy, dx, c->B, acc, c->stream));
-    else
+    if (L.tc >= 0 && c->bf.layers[L.tc].dgrad) {
+      ok(bf16_conv_dgrad(c->bf, L.tc, dy, dx, c->B, acc, c->stream, ybf_owner == &L));
+      ybf_owner = &L;  // dy now sits in the staging buffer
+    } else
       ok(conv3d_dgrad_f32(dy, W(L), dx, c->B, L.din, L.ci, L.co, L.k, L.s,
                           L.dout.count() * L.co, L.din.count() * L.ci, c->Pp, acc, c->stream));
     fin();
   }
-  // dy_staged: this layer's data gradient has just staged dy (BF16); the forward of this
-  // iteration staged x.
-  void conv_wgrad(const ConvL& L, const float* x, const float* dy, bool dy_staged = false) {
+  // x: the forward of this iteration staged it; dy: staged when this layer owns the buffer
+  void conv_wgrad(const ConvL& L, const float* x, const float* dy) {
     beg(D2IP_KCLASS_CONV_WGRAD, conv_flops(L));
     if (tc_wgrad(c, L))
       ok(bf16_conv_wgrad(c->bf, L.tc, x, dy, c->ws, c->B, c->stream, nullptr, nullptr, true,
-                         dy_staged && c->bf.layers[L.tc].dgrad));
+                         ybf_owner == &L));
     else
       ok(conv3d_wgrad_partial_f32(x, dy, c->ws, c->B, L.din, L.ci, L.co, L.k, L.s,
                                   L.din.count() * L.ci, L.dout.count() * L.co, c->stream));
@@ -472,50 +493,63 @@ struct Launcher {
                        c->stream));
     fin();
   }
+  // consumer: the tensor-core convolution that reads y next (its BF16 input is written here)
   void ln_fwd(const LnL& L, int lvl, const float* z, const float* resid, float* y, float* xh,
-              float* rs) {
+              float* rs, const ConvL* consumer = nullptr) {
     const double nv = (double)c->dims[lvl].count() * c->B;
     beg(D2IP_KCLASS_LN_FWD, 4.0 * nv * (L.c * (resid ? 4 : 3) + 1));
+    __nv_bfloat16* ybf = bf_in(consumer);
     ok(layernorm_act_fwd_f32(z, c->theta + L.g_off, resid, y, xh, rs, c->B,
-                             c->dims[lvl].count(), L.c, 1, c->Pp, c->stream));
+                             c->dims[lvl].count(), L.c, 1, c->Pp, c->stream, ybf));
+    if (ybf) staged_x.push_back(consumer);
     fin();
   }
+  // dz_consumer: the convolution whose output gradient dz is (dz also goes to the dy staging
+  // buffer); dt_owner: the block whose fused projection reads dt (dt also goes to its buffer)
   void ln_bwd(const LnL& L, int lvl, const float* dy, const float* aout, const float* xh,
-              const float* rs, float* dz, float* dt) {
+              const float* rs, float* dz, float* dt, const ConvL* dz_consumer = nullptr,
+              const void* dt_owner = nullptr) {
     const long long nv = c->dims[lvl].count();
     beg(D2IP_KCLASS_LN_BWD, 4.0 * c->B * nv * (L.c * (dt ? 5 : 4) + 1));
+    __nv_bfloat16* dzbf = tc_dy_consumer(dz_consumer) ? c->bf.ybf : nullptr;
+    __nv_bfloat16* dtbf = dt && dt_owner && c->bf.pbf ? c->bf.pbf : nullptr;
     ok(layernorm_act_bwd_f32(dy, aout, xh, rs, c->theta + L.g_off, dz, dt, c->ws, c->B, nv,
-                             L.c, c->Pp, c->stream));
+                             L.c, c->Pp, c->stream, dzbf, dtbf));
+    if (dzbf) ybf_owner = dz_consumer;
+    if (dtbf) pbf_owner = dt_owner;
     ok(reduce_rows_f32(c->ws, G(L.g_off), c->B, layernorm_bwd_blocks(nv, L.c), 2 * L.c, c->Pp,
                        0, c->stream));
     fin();
   }
 
-  void unit_fwd(Unit& u) {
+  // next: the convolution that reads the unit's (block's) output
+  void unit_fwd(Unit& u, const ConvL* next) {
     conv_fwd(u.conv, u.x, c->ztmp);
-    ln_fwd(u.ln, u.lvl_out, c->ztmp, nullptr, u.a, u.xh, u.rs);
+    ln_fwd(u.ln, u.lvl_out, c->ztmp, nullptr, u.a, u.xh, u.rs, next);
   }
-  void res_fwd(Res& R) {
+  void res_fwd(Res& R, const ConvL* next) {
     if (R.fuse_f) {  // conv a and the projection in one launch
       beg(D2IP_KCLASS_CONV_FWD, conv_flops(R.a) + conv_flops(R.p));
       ok(bf16_conv_fwd_proj(c->bf, R.a.tc, R.x, W(R.a) + R.a.wcount(), c->ztmp,
-                            W(R.p) + R.p.wcount(), c->ptmp, c->B, c->Pp, c->stream));
+                            W(R.p) + R.p.wcount(), c->ptmp, c->B, c->Pp, c->stream,
+                            take_staged(R.a)));
       fin();
     } else {
       conv_fwd(R.a, R.x, c->ztmp);
     }
-    ln_fwd(R.lna, R.lvl, c->ztmp, nullptr, R.h1, R.xh_a, R.rs_a);
+    ln_fwd(R.lna, R.lvl, c->ztmp, nullptr, R.h1, R.xh_a, R.rs_a, &R.b);
     if (R.proj && !R.fuse_f) conv_fwd(R.p, R.x, c->ptmp);
     conv_fwd(R.b, R.h1, c->ztmp);
-    ln_fwd(R.lnb, R.lvl, c->ztmp, R.proj ? c->ptmp : R.x, R.out, R.xh_b, R.rs_b);
+    ln_fwd(R.lnb, R.lvl, c->ztmp, R.proj ? c->ptmp : R.x, R.out, R.xh_b, R.rs_b, next);
   }
   void forward() {
     if (c->precision == D2IP_BF16) ok(bf16_prepare_weights(c->bf, c->theta, c->B, c->Pp, c->stream));
-    unit_fwd(c->stem);
-    res_fwd(c->enc[0]);
+    staged_x.clear();
+    unit_fwd(c->stem, &c->enc[0].a);
+    res_fwd(c->enc[0], c->L > 1 ? &c->down[1].conv : nullptr);
     for (int l = 1; l < c->L; ++l) {
-      unit_fwd(c->down[l]);
-      res_fwd(c->enc[l]);
+      unit_fwd(c->down[l], &c->enc[l].a);
+      res_fwd(c->enc[l], l + 1 < c->L ? &c->down[l + 1].conv : nullptr);
     }
     const float* cur = c->enc[c->L - 1].out;
     for (int l = c->L - 2; l >= 0; --l) {
@@ -524,10 +558,12 @@ struct Launcher {
                             2.0 * c->dims[l].count() * c->w[l] +
                             (double)c->dims[l].count() * c->w[l + 1]);
       beg(D2IP_KCLASS_UP_FWD, bytes);
+      __nv_bfloat16* catbf = bf_in(&c->dec[l].a);
       ok(upsample_concat_fwd_f32(cur, c->enc[l].out, c->lb[l].cat, c->B, c->dims[l + 1],
-                                 c->dims[l], c->w[l + 1], c->w[l], c->stream));
+                                 c->dims[l], c->w[l + 1], c->w[l], c->stream, catbf));
+      if (catbf) staged_x.push_back(&c->dec[l].a);
       fin();
-      res_fwd(c->dec[l]);
+      res_fwd(c->dec[l], nullptr);
       cur = c->dec[l].out;
     }
     if (co1_layer(c->tail)) {
@@ -583,13 +619,17 @@ struct Launcher {
   // dout: gradient of R.out; writes dx (gradient of R.x)
   void res_bwd(Res& R, const float* dout, float* dx) {
     LevelBufs& T = c->lb[R.lvl];
-    ln_bwd(R.lnb, R.lvl, dout, R.out, R.xh_b, R.rs_b, T.tz, T.tt);
+    ln_bwd(R.lnb, R.lvl, dout, R.out, R.xh_b, R.rs_b, T.tz, T.tt, &R.b,
+           R.fuse_d || R.fuse_w ? &R : nullptr);
     conv_dgrad(R.b, T.tz, T.th, 0);
-    conv_wgrad(R.b, R.h1, T.tz, true);
-    ln_bwd(R.lna, R.lvl, T.th, R.h1, R.xh_a, R.rs_a, T.tz, nullptr);
+    conv_wgrad(R.b, R.h1, T.tz);
+    ln_bwd(R.lna, R.lvl, T.th, R.h1, R.xh_a, R.rs_a, T.tz, nullptr, &R.a);
     if (R.fuse_d) {  // dx = conv_a^T(dz_a) + W_p^T dz_p in one launch
       beg(D2IP_KCLASS_CONV_DGRAD, conv_flops(R.a) + conv_flops(R.p));
-      ok(bf16_conv_dgrad_proj(c->bf, R.a.tc, T.tz, T.tt, dx, c->B, c->stream));
+      ok(bf16_conv_dgrad_proj(c->bf, R.a.tc, T.tz, T.tt, dx, c->B, c->stream,
+                              ybf_owner == &R.a, pbf_owner == &R));
+      ybf_owner = &R.a;
+      pbf_owner = &R;
       fin();
     } else {
       conv_dgrad(R.a, T.tz, dx, 0);
@@ -599,14 +639,14 @@ struct Launcher {
       float* part_p = c->ws + (long long)c->B * rows * (R.a.wcount() + R.a.co);
       beg(D2IP_KCLASS_CONV_WGRAD, conv_flops(R.a) + conv_flops(R.p));
       ok(bf16_conv_wgrad(c->bf, R.a.tc, R.x, T.tz, c->ws, c->B, c->stream, T.tt, part_p, true,
-                         true));
+                         ybf_owner == &R.a));
       ok(reduce_rows_f32(c->ws, G(R.a.w_off), c->B, rows, R.a.wcount() + R.a.co, c->Pp, 0,
                          c->stream));
       ok(reduce_rows_f32(part_p, G(R.p.w_off), c->B, rows, R.p.wcount() + R.p.co, c->Pp, 0,
                          c->stream));
       fin();
     } else {
-      conv_wgrad(R.a, R.x, T.tz, true);
+      conv_wgrad(R.a, R.x, T.tz);
     }
     if (R.proj) {
       if (!R.fuse_d) conv_dgrad(R.p, T.tt, dx, 1);
@@ -620,11 +660,13 @@ struct Launcher {
   }
   void unit_bwd(Unit& u, const float* da, float* dx, int acc, bool dgrad) {
     float* tz = c->lb[u.lvl_out].tz;
-    ln_bwd(u.ln, u.lvl_out, da, u.a, u.xh, u.rs, tz, nullptr);
+    ln_bwd(u.ln, u.lvl_out, da, u.a, u.xh, u.rs, tz, nullptr, &u.conv);
     if (dgrad) conv_dgrad(u.conv, tz, dx, acc);
-    conv_wgrad(u.conv, u.x, tz, dgrad);
+    conv_wgrad(u.conv, u.x, tz);
   }
   void backward() {
+    ybf_owner = nullptr;
+    pbf_owner = nullptr;
     const int L = c->L;
     const float* tail_in = L > 1 ? c->dec[0].out : c->enc[0].out;
     if (co1_layer(c->tail)) {  // data and weight gradients of the last layer in one pass
