@@ -1351,24 +1351,38 @@ struct WTable {
       dgrad[kWMaxLayers];
 };
 
-__global__ void weights_all_bf16_kernel(const float* __restrict__ theta,
-                                        __nv_bfloat16* __restrict__ wb, long long Pp,
-                                        long long wstride, const __grid_constant__ WTable t) {
+// A block takes one (layer, tap, chunk of 32 output channels): it reads W[o][tap][0..ci) rows
+// (coalesced, zero past ci_real) into shared memory, writes the forward rows [tap][o][ci]
+// and, through the shared tile, the data-gradient rows [T-1-tap][ci][o] (32 o per row piece).
+constexpr int kWOc = 32;
+
+__global__ void __launch_bounds__(256)
+weights_all_bf16_kernel(const float* __restrict__ theta, __nv_bfloat16* __restrict__ wb,
+                        long long Pp, long long wstride, const __grid_constant__ WTable t) {
+  __shared__ __nv_bfloat16 tile[kWOc][256 + 2];
   int l = 0;
   while (l + 1 < t.nl && (int)blockIdx.x >= t.blk0[l + 1]) ++l;
   const int b = blockIdx.y;
   const int ci = t.ci[l], cr = t.ci_real[l], co = t.co[l], T = t.T[l];
-  const long long n = (long long)co * T * ci;
-  const long long e = (long long)(blockIdx.x - t.blk0[l]) * blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  const int c = (int)(e % ci);
-  const long long r = e / ci;
-  const int tap = (int)(r % T), o = (int)(r / T);
-  const float v = c < cr ? theta[(long long)b * Pp + t.w_off[l] + r * cr + c] : 0.f;
-  const __nv_bfloat16 h = __float2bfloat16_rn(v);  // W[o][tap][c]
+  const int nch = (co + kWOc - 1) / kWOc;
+  const int q = blockIdx.x - t.blk0[l];
+  const int tap = q / nch, o0 = (q % nch) * kWOc;
+  const int no = co - o0 < kWOc ? co - o0 : kWOc;
+  const float* src = theta + (long long)b * Pp + t.w_off[l];
   __nv_bfloat16* base = wb + (long long)b * wstride;
-  base[t.wf_off[l] + ((long long)tap * co + o) * ci + c] = h;                     // [t][co][ci]
-  if (t.dgrad[l]) base[t.wd_off[l] + ((long long)(T - 1 - tap) * ci + c) * co + o] = h;
+  for (int e = threadIdx.x; e < no * ci; e += blockDim.x) {
+    const int ol = e / ci, c = e % ci;
+    const float v = c < cr ? src[((long long)(o0 + ol) * T + tap) * cr + c] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    tile[ol][c] = h;
+    base[t.wf_off[l] + ((long long)tap * co + o0 + ol) * ci + c] = h;  // [t][co][ci]
+  }
+  if (!t.dgrad[l]) return;
+  __syncthreads();
+  for (int e = threadIdx.x; e < no * ci; e += blockDim.x) {
+    const int ol = e % no, c = e / no;
+    base[t.wd_off[l] + ((long long)(T - 1 - tap) * ci + c) * co + o0 + ol] = tile[ol][c];
+  }
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -2123,7 +2137,9 @@ cudaError_t bf16_prepare_kernels() {
 
 cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long long Pp,
                                  cudaStream_t stream) {
-  if (bf.layers.size() <= (size_t)kWMaxLayers && !bf.layers.empty()) {
+  bool fits = bf.layers.size() <= (size_t)kWMaxLayers && !bf.layers.empty();
+  for (const TcLayer& L : bf.layers) fits = fits && L.ci <= 256;
+  if (fits) {
     WTable t{};
     t.nl = (int)bf.layers.size();
     int blk = 0;
@@ -2131,7 +2147,7 @@ cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long lo
       const TcLayer& L = bf.layers[i];
       const int T = L.k * L.k * L.k;
       t.blk0[i] = blk;
-      blk += (int)ceil_div((long long)L.co * T * L.ci, 256);
+      blk += T * (int)ceil_div(L.co, kWOc);
       t.w_off[i] = L.w_off, t.wf_off[i] = L.wf_off, t.wd_off[i] = L.wd_off;
       t.ci[i] = L.ci, t.ci_real[i] = L.ci_real, t.co[i] = L.co, t.T[i] = T;
       t.dgrad[i] = L.dgrad ? 1 : 0;

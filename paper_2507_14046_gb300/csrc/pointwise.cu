@@ -506,41 +506,41 @@ jtmul_kernel(const JT* __restrict__ J, const float* __restrict__ r, float* __res
   for (int q = 0; q < nb; ++q) g[(long long)(b0 + q) * g_bs + j] = scale * acc[q];
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024)
 loss_kernel(const float* __restrict__ r, double* __restrict__ loss, double* __restrict__ trace,
             int* __restrict__ trace_pos, int trace_cap, int* __restrict__ adam_t,
             int* __restrict__ status, int B, int m, const double* __restrict__ reg_part,
             int reg_blocks) {
-  __shared__ double red[256];
+  // one warp per problem (problems w, w + nw, ...): lanes add i = lane, lane + 32, ... in
+  // order, then a fixed butterfly over the lanes
+  __shared__ int bad_s;
   const int pos = trace_pos ? *trace_pos : 0;
   const int slot = trace_cap > 0 ? pos % trace_cap : 0;
-  bool bad = false;
-  for (int b = 0; b < B; ++b) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  if (threadIdx.x == 0) bad_s = 0;
+  __syncthreads();
+  for (int b = warp; b < B; b += nw) {
     double s = 0.0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    for (int i = lane; i < m; i += 32) {
       const double v = (double)r[(long long)b * m + i];
       s += v * v;
     }
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      double L = red[0] / (double)m;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      double L = s / (double)m;
       if (reg_part)
         for (int k = 0; k < reg_blocks; ++k) L += reg_part[(long long)b * reg_blocks + k];
       loss[b] = L;
       if (trace) trace[(long long)slot * B + b] = L;
-      if (!isfinite(L)) bad = true;
+      if (!isfinite(L)) atomicOr(&bad_s, 1);
     }
-    __syncthreads();
   }
+  __syncthreads();
   if (threadIdx.x == 0) {
     if (trace_pos) *trace_pos = pos + 1;
     if (adam_t) *adam_t += 1;
-    if (bad && status) *status |= 1;
+    if (bad_s && status) *status |= 1;
   }
 }
 
@@ -1004,8 +1004,9 @@ cudaError_t prepare_pointwise_kernels() {
 cudaError_t residual_loss_f64(const float* r, double* loss, double* trace, int* trace_pos,
                               int trace_cap, int* adam_t, int* status, int B, int m,
                               cudaStream_t stream, const double* reg_part, int reg_blocks) {
-  loss_kernel<<<1, 256, 0, stream>>>(r, loss, trace, trace_pos, trace_cap, adam_t, status, B,
-                                     m, reg_part, reg_blocks);
+  const int threads = 32 * (B < 32 ? (B > 0 ? B : 1) : 32);
+  loss_kernel<<<1, threads, 0, stream>>>(r, loss, trace, trace_pos, trace_cap, adam_t, status, B,
+                                         m, reg_part, reg_blocks);
   return cudaGetLastError();
 }
 
@@ -1024,6 +1025,7 @@ cudaError_t err_ratio_f64(const float* est, const float* truth, double* out, int
 cudaError_t adam_step_f32(float* theta, const float* g, float* m, float* v, long long count,
                           double lr, double beta1, double beta2, double eps, const int* t_dev,
                           int t_host, cudaStream_t stream) {
+  // capped grid: every block forms the FP64 bias corrections once (FP64 is slow here)
   long long blocks = ceil_div(count, 256);
   if (blocks > 152 * 8) blocks = 152 * 8;
   adam_kernel<<<(unsigned)blocks, 256, 0, stream>>>(theta, g, m, v, count, (float)lr, beta1,
