@@ -1406,6 +1406,7 @@ EncodeTiledFn encode_fn() {
 int chunk_for(int c) { return c % 64 == 0 ? 64 : (c % 32 == 0 ? 32 : 16); }
 
 int wg3_tz(int Z);
+int wg3_tz_fit(const TcLayer& L);
 Wg3Geom wg3_geom(const TcLayer& L, int B, bool proj = false);
 
 CUtensorMapSwizzle swizzle_for(int ck) {
@@ -1533,7 +1534,7 @@ Tc3Plan tc3_plan(int cin, int n, int np, int Z) {
   Tc3Plan best;
   double best_cost = 1e300;
   const size_t staging = (size_t)128 * (std::max(n, np) + 4) * 4;
-  for (int tz : {4, 2, 1}) {
+  for (int tz : {8, 4, 2, 1}) {
     if (tz * (n + np) > 256) continue;
     for (int ck : {64, 32, 16}) {
       if (cin % ck) continue;
@@ -1580,7 +1581,8 @@ cudaError_t launch_tc3(const CUtensorMap& a, const CUtensorMap& w, int cin, int 
     const CUtensorMap& m2 = a2 ? *a2 : a;
 #define D2IP_P3(CK_, TZ_) conv_tc3p_kernel<CK_, TZ_><<<grid, 192, sm, st>>>(a, w, mp, m2, g)
 #define D2IP_P3Z(CK_) \
-  if (tz == 4) D2IP_P3(CK_, 4); else if (tz == 2) D2IP_P3(CK_, 2); else D2IP_P3(CK_, 1)
+  if (tz == 8) D2IP_P3(CK_, 8); else if (tz == 4) D2IP_P3(CK_, 4); \
+  else if (tz == 2) D2IP_P3(CK_, 2); else D2IP_P3(CK_, 1)
     if (ck == 64) { D2IP_P3Z(64); } else if (ck == 32) { D2IP_P3Z(32); } else { D2IP_P3Z(16); }
 #undef D2IP_P3Z
 #undef D2IP_P3
@@ -1720,6 +1722,7 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
     }
   }
   L.wgrad = s == 1 && co <= 128 && 128 % co == 0 && ci + chunk_for(ci) <= 256;
+  if (k == 3 && s == 1) L.wg_tz = wg3_tz_fit(L);
   L.wg3 = L.wgrad && wg3_geom(L, 1).nst > 0;
   if (k == 3 && s == 2 && (ci == 16 || ci == 32 || ci == 64) && co % 16 == 0 && co <= 256)
     L.wgrad = L.wgs2 = true;
@@ -1750,6 +1753,7 @@ int bf16_add_input_layer(Bf16Net& bf, int ci_real, int co, Dims3 din, long long 
     const Tc3Plan pf = tc3_plan(16, co, 0, din.z);
     L.ck3f = pf.ck, L.tz3f = pf.tz;
   }
+  L.wg_tz = wg3_tz_fit(L);
   L.wgrad = L.wg3 = wg3_geom(L, 1).nst > 0;
   if (!L.ck3f || !L.wg3) return -1;
   L.wf_off = bf.wstride;
@@ -1792,7 +1796,7 @@ cudaError_t bf16_finalize(Bf16Net& bf, int B) {
           encode_act_halo(&L.act_f3, bf.zbf, B, L.din, 16, L.ck3f, L.tz3f);
       if (e == cudaSuccess)
         e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, 16, T, L.co, L.ck3f, 9, 3);
-      const int tz = wg3_tz(L.dout.z);
+      const int tz = L.wg_tz;
       if (e == cudaSuccess) e = encode_box(&L.wg_dy3, bf.ybf, B, L.dout, L.co, L.co, 8, 3, tz + 2);
       if (e == cudaSuccess) e = encode_box(&L.wg_x3, bf.zbf, B, L.din, 16, 16, 8, 1, tz);
       if (e != cudaSuccess) return e;
@@ -1811,7 +1815,7 @@ cudaError_t bf16_finalize(Bf16Net& bf, int B) {
     if (e == cudaSuccess && L.wgrad)
       e = encode_act(&L.act_wy, bf.ybf, B, L.dout, L.co, chunk_for(L.co), 1);
     if (e == cudaSuccess && L.wg3) {
-      const int tz = wg3_tz(L.dout.z);
+      const int tz = L.wg_tz;
       e = encode_box(&L.wg_dy3, bf.ybf, B, L.dout, L.co, L.co, 8, 3, tz + 2);
       if (e == cudaSuccess)
         e = encode_box(&L.wg_x3, L.xin, B, L.din, L.ci, chunk_for(L.ci), 8, 1, tz);
@@ -1831,7 +1835,7 @@ cudaError_t bf16_finalize(Bf16Net& bf, int B) {
       e = encode_w(&L.pw_f, bf.wbuf + P.wf_off, B, bf.wstride, P.ci, 1, P.co, L.ck3f, 1, 1);
     }
     if (e == cudaSuccess && L.projw)  // dz_p column of the halo weight gradient
-      e = encode_box(&L.wg_p3, bf.pbf, B, L.dout, L.co, L.co, 8, 1, wg3_tz(L.dout.z));
+      e = encode_box(&L.wg_p3, bf.pbf, B, L.dout, L.co, L.co, 8, 1, L.wg_tz);
     if (e == cudaSuccess && L.projd) {  // W_p^T [1][ci][co] and the dz_p tile box
       const TcLayer& P = bf.layers[L.proj];
       e = encode_w(&L.pw_d, bf.wbuf + P.wd_off, B, bf.wstride, P.co, 1, P.ci, L.ck3d, 1, 1);
@@ -1899,7 +1903,24 @@ int sm_count() {
 
 constexpr size_t kWg3SmemMax = 210 * 1024;
 
-// z extent of the halo weight-gradient column: the even tz <= 16 with the least padding of Z.
+// z extent of the halo weight-gradient column: among even tz <= 32, the least padding of Z,
+// then the longest column (more MMAs per pipeline stage), whose stage (with room for a fused
+// projection) still leaves two stages in shared memory.
+int wg3_tz_fit(const TcLayer& L) {
+  const int Z = L.dout.z, ckb = chunk_for(L.ci);
+  int best = 0;
+  long long best_pad = 0;
+  for (int tz = 32; tz >= 2; tz -= 2) {
+    const size_t a_box = (size_t)8 * 3 * (tz + 2) * L.co * 2, b_box = (size_t)8 * tz * ckb * 2;
+    const size_t stage = (3 * a_box + 1023) / 1024 * 1024 + (L.ci / ckb + 2) * b_box +
+                         (size_t)8 * tz * L.co * 2 + 2048;
+    if (2 * stage + 1024 > kWg3SmemMax) continue;
+    const long long pad = ceil_div(Z, tz) * tz;
+    if (!best || pad < best_pad) best = tz, best_pad = pad;
+  }
+  return best ? best : 2;
+}
+
 int wg3_tz(int Z) {
   int best = 16;
   long long best_pad = ceil_div(Z, 16) * 16;
@@ -1927,7 +1948,7 @@ Wg3Geom wg3_geom(const TcLayer& L, int B, bool proj) {
   if ((G + extra) * N > 512) return g;
   g.proj = extra;
   g.tmem_cols = (uint32_t)pow2((g.nkx * G + extra) * N);
-  g.tz = wg3_tz(L.dout.z);
+  g.tz = L.wg_tz > 0 ? L.wg_tz : wg3_tz(L.dout.z);
   g.a_box = (uint32_t)(8 * 3 * (g.tz + 2) * L.co * 2);
   g.b_box = (uint32_t)(8 * g.tz * ckb * 2);
   g.b_off = (uint32_t)((g.nkx * g.a_box + 1023) / 1024 * 1024);
@@ -2102,8 +2123,9 @@ cudaError_t bf16_prepare_kernels() {
   if (e == cudaSuccess)                                                             \
     e = cudaFuncSetAttribute(conv_tc3p_kernel<CK_, TZ_>,                            \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc3SmemMax);
-  D2IP_P3A(64, 1) D2IP_P3A(64, 2) D2IP_P3A(64, 4) D2IP_P3A(32, 1) D2IP_P3A(32, 2)
-  D2IP_P3A(32, 4) D2IP_P3A(16, 1) D2IP_P3A(16, 2) D2IP_P3A(16, 4)
+  D2IP_P3A(64, 1) D2IP_P3A(64, 2) D2IP_P3A(64, 4) D2IP_P3A(64, 8) D2IP_P3A(32, 1)
+  D2IP_P3A(32, 2) D2IP_P3A(32, 4) D2IP_P3A(32, 8) D2IP_P3A(16, 1) D2IP_P3A(16, 2)
+  D2IP_P3A(16, 4) D2IP_P3A(16, 8)
 #undef D2IP_P3A
   if (e == cudaSuccess) e = wgrad_attr<16, 16>();
   if (e == cudaSuccess) e = wgrad_attr<16, 32>();

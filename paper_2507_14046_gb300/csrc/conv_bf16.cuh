@@ -33,6 +33,7 @@ struct TcLayer {
   CUtensorMap pw_f, pw_d, pa_d;   // projection: W_p, W_p^T and the dz_p tile box
   CUtensorMap wg_p3;              // projection: dz_p column of the halo weight gradient
   bool wg3 = false;               // weight gradient by the halo-box kernel
+  int wg_tz = 0;                  // its column depth (z voxels per K tile)
   bool wgs2 = false;              // stride-2 weight gradient on the tensor cores
   __nv_bfloat16* xin = nullptr;   // BF16 copy of the forward input (kept for the weight gradient)
   int ci_real = 0;                // input channels of the model (ci is padded up to 16)
