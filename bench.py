@@ -572,17 +572,31 @@ def main():
     rank, world, local_rank = replicas.world()
     w = WORKLOADS[args.workload]
     its = iters_per_step(w)
-    config = {"workload": w.name + ((", " + args.precision.upper()) if args.impl == "ours"
-                                    else ", FP64 oracle"),
+    config = {"workload": w.name + ", " + args.precision.upper(),
               "grid": list(w.grid), "m": w.m, "levels": w.levels, "widths": list(w.widths),
               "frames": w.frames, "schedule": [w.upws_steps, w.first_steps, w.later_steps],
               "lr": w.lr, "iters_per_step": its, "precision": args.precision,
               "l2": "512 MB buffer written between timed steps (working set < L2)",
               "parallelism": f"replicas x{args.gpus}"}
 
+    if args.workload == "batch64":
+        config["workload"] = ("64 independent 20-frame sequences (grids 16x16x8 / 32x32x16 / "
+                              f"48x48x24, m 208 / 416), L3(16,32,64), {args.precision.upper()} "
+                              "batched")
+        config["grid"] = "mixed"
+        config["m"] = "mixed"
+        config["iters_per_step"] = 64 * its
+
     if args.impl == "reference":
         if rank != 0:
             return
+        if args.workload == "batch64":  # the same groups as the batched arm reports
+            cnt = {}
+            for g, r in synth.batch_problem_shapes(64, 1):
+                cnt[(g, r)] = cnt.get((g, r), 0) + 1
+            config["groups"] = [{"grid": list(g), "m": 208 * r, "problems": cnt[(g, r)]}
+                                for g in synth.BATCH_GRIDS for r in synth.BATCH_RINGS
+                                if (g, r) in cnt]
         per = oracle_iters_for(args.workload)
         per = max(1, per // 4)
         for _ in range(args.warmup):
@@ -608,12 +622,6 @@ def main():
 
     replicas.init()
     if args.workload == "batch64":
-        config["workload"] = ("64 independent 20-frame sequences (grids 16x16x8 / 32x32x16 / "
-                              f"48x48x24, m 208 / 416), L3(16,32,64), {args.precision.upper()} "
-                              "batched")
-        config["grid"] = "mixed"
-        config["m"] = "mixed"
-        config["iters_per_step"] = 64 * its
         out = run_batched(args, rank, world, local_rank)
         config["groups"] = out.pop("groups")
     else:
