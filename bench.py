@@ -7,6 +7,8 @@ data term, adjoint, backward and Adam.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload seq32|single16]
     python bench.py --impl reference ...     (the FP64 oracle on the host cores)
+    python bench.py --study 3000 [--workload seq32] [--study-out curves.npz]
+                                             (convergence ablation of UPWS / TPP)
 
 Multi-GPU: replicas only.  Every rank fits its own copy of the workload (weak scaling);
 there is no collective on the data path, only a barrier and a max over ranks of the time.
@@ -544,6 +546,27 @@ def run_probe(args):
     c.close()
 
 
+def run_study(args):
+    """Convergence ablation (plain DIP, + 4D-TV, UPWS, full D²IP) on the second frame of a
+    sequence workload; prints one JSON summary line, and the curves to --study-out (.npz)."""
+    import torch
+
+    from paper_2507_14046_gb300 import study
+
+    w = WORKLOADS["seq32" if args.workload == "batch64" else args.workload]
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    res = study.run(w, iters=args.study, precision=args.precision or "fp32")
+    secs = time.time() - t0
+    summ = study.summarise(res)
+    if args.study_out:
+        np.savez_compressed(args.study_out, err_iters=res["err_iters"],
+                            **{f"loss_{a}": res["loss"][a] for a in study.ARMS},
+                            **{f"err_{a}": res["err"][a] for a in study.ARMS})
+    print(json.dumps({"study": "acceleration ablation, frame 2", "workload": w.name,
+                      "schedule": res["schedule"], "seconds": round(secs, 1), **summ}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -558,7 +581,13 @@ def main():
     ap.add_argument("--probe", type=int, default=0,
                     help="trace this many iterations of the largest batched group and exit")
     ap.add_argument("--probe-problems", type=int, default=0)
+    ap.add_argument("--study", type=int, default=0,
+                    help="run the convergence ablation for this many iterations and exit")
+    ap.add_argument("--study-out", default=None)
     args = ap.parse_args()
+    if args.study:
+        run_study(args)
+        return
     if args.probe:
         run_probe(args)
         return

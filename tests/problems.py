@@ -33,9 +33,13 @@ def oracle_table(spec):
     return [(k, o, c, f) for _, _, k, f, o, c in onet.param_layout(spec)]
 
 
-def make(grid, rings, levels, widths, c_in=8, seed=0, T=1, random_phantom=False):
+def make(grid, rings, levels, widths, c_in=8, seed=0, T=1, random_phantom=False, m=None):
+    """m: keep the first m rows of J (a measurement count other than 208 per ring, e.g. the
+    328 of the paper's 32-electrode, two-layer protocol, reproduced as a shape only)."""
     from oracle import dip
     J = synth.sensitivity_raw(grid, rings, seed)
+    if m is not None:
+        J = np.ascontiguousarray(J[:m])
     if random_phantom:
         base = synth.ellipsoid_phantom(grid, synth.random_ellipsoids(grid, seed, 0))
     else:

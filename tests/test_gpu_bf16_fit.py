@@ -1,8 +1,8 @@
 """The BF16 tensor-core precision of the whole DIP iteration against the FP64 oracle.
 
 Convolutions whose channel counts are multiples of 16 run on tcgen05 with BF16 operands and
-FP32 accumulation (the stem, with 8 input channels, and the 1-channel tail stay FP32); every
-other step is FP32.  BF16 rounds each operand to 8 significant bits (relative 2^-9), so the
+FP32 accumulation (the stem's 8 input channels are zero-padded to 16; the 1-channel tail
+stays FP32); J products read a BF16 copy of J; every other step is FP32.  BF16 rounds each operand to 8 significant bits (relative 2^-9), so the
 per-iteration agreement is about 1e-2, not the FP32 path's 1e-5; the reconstruction error
 (ERR) of a fitted frame is compared with the oracle's."""
 import numpy as np

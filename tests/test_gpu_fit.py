@@ -73,6 +73,25 @@ def test_teacher_forced_iteration(d2ip, grid, rings, L, widths, k_pre):
     assert t1 == k_pre + 1
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_protocol_shape_m328(d2ip, precision):
+    """The measurement count of the paper's 32-electrode, two-layer protocol (m = 328, as a
+    shape: the first 328 rows of a two-ring J), one teacher-forced step, FP32 and BF16."""
+    pb = problems.make((16, 16, 8), 2, 2, (16, 32), seed=3, m=328)
+    assert pb.J.shape[0] == 328 and pb.V.shape[1] == 328
+    Z64, dv = pb.Zin.astype(np.float64), pb.V[0].astype(np.float64)
+    st = dip.AdamState.fresh(pb.theta0.size)
+    ref = dip.dip_step(pb.spec, pb.Jn64, Z64, dv, pb.theta0.astype(np.float64), st, 1e-3)
+    c = _ctx(d2ip, pb, 1e-3, precision=precision)
+    ds = c.forward()[0]
+    tr = c.run_steps(pb.V[:1], 1, trace=True)
+    g = c.grad()[0]
+    tol_ds, tol_l, tol_g = (TOL, TOL, TOL) if precision == 0 else (2e-2, 4e-2, 5e-2)
+    assert rel(ds, ref.dsigma) < tol_ds
+    assert abs(tr[0, 0] - ref.loss) <= tol_l * ref.loss
+    assert rel(g, ref.grad) < tol_g
+
+
 def test_single_frame_fit_matches_oracle_err(d2ip):
     """Plain DIP on the 16x16x8 single-frame workload: 200 Adam steps, lr 1e-3."""
     pb = problems.make((16, 16, 8), 1, 2, (8, 16), seed=0)

@@ -1,0 +1,50 @@
+"""Host logic of the convergence ablation: running minimum, iterations to a target, plateau
+detection and the summary over synthetic curves with known answers."""
+import numpy as np
+
+from paper_2507_14046_gb300 import study
+
+
+def test_running_min_and_targets():
+    x = np.array([5.0, 3.0, 4.0, 2.0, 2.5, 1.0])
+    np.testing.assert_array_equal(study.running_min(x), [5, 3, 3, 2, 2, 1])
+    assert study.iters_to_reach(x, 3.0) == 2
+    assert study.iters_to_reach(x, 2.0) == 4
+    assert study.iters_to_reach(x, 0.5) is None
+    # labelled samples (ERR every 10 iterations)
+    assert study.iters_to_reach(x, 2.0, np.arange(10, 70, 10)) == 40
+    # within 10 % of the minimum 1.0: only the last sample
+    assert study.plateau_iter(x, 0.1) == 6
+    # within 100 %: 2.0 reached at the fourth sample
+    assert study.plateau_iter(x, 1.0) == 4
+
+
+def test_oscillating_curve_credited_at_first_reach():
+    k = np.arange(1, 1001)
+    x = np.exp(-k / 100.0) * (1.0 + 0.5 * np.sin(k))
+    t = 0.05
+    got = study.iters_to_reach(x, t)
+    assert x[got - 1] <= t and np.all(x[:got - 1] > t)
+
+
+def test_summarise_orders_arms_by_decay_rate():
+    n, every = 600, 10
+    k = np.arange(1, n + 1)
+    it = np.arange(every, n + 1, every)
+    rates = {"dip": 400.0, "dip_reg": 300.0, "upws": 60.0, "d2ip": 30.0}
+    res = {"loss": {a: 1e-3 + np.exp(-k / r) for a, r in rates.items()},
+           "err": {a: 0.3 + np.exp(-it / r) for a, r in rates.items()},
+           "err_iters": it}
+    s = study.summarise(res, budget=250)
+    assert s["targets"]["budget"] == 250
+    a = s["arms"]
+    assert a["d2ip"]["iters_to_loss_target"] <= 250
+    assert a["d2ip"]["iters_to_err_target"] <= 250
+    assert a["dip_reg"]["iters_to_loss_target"] is None
+    assert a["upws"]["iters_to_err_target"] > a["d2ip"]["iters_to_err_target"]
+    assert a["dip"]["iters_to_err_target"] is None or \
+        a["dip"]["iters_to_err_target"] > a["upws"]["iters_to_err_target"]
+    assert a["d2ip"]["loss_plateau_iter"] < a["upws"]["loss_plateau_iter"] < \
+        a["dip"]["loss_plateau_iter"]
+    assert a["dip"]["loss_at"][50] == res["loss"]["dip"][49]
+    assert a["dip"]["err_at"][100] == res["err"]["dip"][9]
