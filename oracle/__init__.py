@@ -10,6 +10,8 @@ Modules:
   dip     -- the data term of Eq. 4 with the l2 norm, its gradient through J^T, Adam,
              the per-frame fit, UPWS (Eqs. 5-7), TPP (Eqs. 8-9) and ERR.
   tv4d    -- the 4D-TV regulariser (Eqs. 10-13) and its gradient.
+  fastres -- the paper-form 3D-FastResUNet (Sec. III-D) as a flagged variant: PyTorch CPU
+             float64 forward, gradient by reverse-mode differentiation.
 
 Each function cites the passage it follows.  Pins (brute-force loops, closed forms,
 finite differences, library special cases) live in tests/test_oracle_*.py.

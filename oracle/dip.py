@@ -25,6 +25,13 @@ from . import network
 BETA1, BETA2, ADAM_EPS = 0.9, 0.999, 1e-8
 
 
+def _net(spec):
+    """The network module of a spec: the paper-form variant for a FastSpec, else the
+    residual U-Net."""
+    from . import fastres
+    return fastres if isinstance(spec, fastres.FastSpec) else network
+
+
 def normalise_columns(J) -> tuple[np.ndarray, np.ndarray]:
     """Column-normalised J (Eq. 1) and the column norms c_j = ||J[:, j]||_2."""
     J = np.asarray(J, dtype=np.float64)
@@ -75,14 +82,15 @@ class StepResult:
 def dip_step(spec, J, Zin, dv, theta, st: AdamState, lr, reg=None) -> StepResult:
     """One DIP iteration: forward phi, data term (+ optional regulariser callback
     ``reg(dsigma) -> (value, gradient)``), backward through J^T and phi, Adam."""
-    ds, kept = network.forward(spec, theta, Zin, keep=True)
+    net = _net(spec)
+    ds, kept = net.forward(spec, theta, Zin, keep=True)
     r, loss = data_term(J, ds, dv)
     gds = data_term_grad(J, r)
     if reg is not None:
         rv, rg = reg(ds)
         loss += rv
         gds = gds + rg
-    g = network.backward(spec, kept, gds)
+    g = net.backward(spec, kept, gds)
     return StepResult(ds, loss, g, adam_step(np.asarray(theta, np.float64), g, st, lr))
 
 
@@ -104,7 +112,7 @@ def fit_frame(spec, J, Zin, dv, theta0, n_steps, lr, reg=None, state=None) -> Fr
         res = dip_step(spec, J, Zin, dv, theta, st, lr, reg)
         losses.append(res.loss)
         theta = res.theta
-    ds = network.forward(spec, theta, Zin)
+    ds = _net(spec).forward(spec, theta, Zin)
     _, resid = data_term(J, ds, dv)
     return FrameResult(theta, ds, resid, losses)
 
