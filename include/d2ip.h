@@ -84,6 +84,31 @@ d2ip_status d2ip_set_grid(d2ip_ctx* ctx, int X, int Y, int Z);
 d2ip_status d2ip_set_network(d2ip_ctx* ctx, int levels, const int* widths, int c_in,
                              int precision, int batch);
 
+/* The paper-form 3D-FastResUNet of Sec. III-D as a network variant (the section names its
+ * parts but gives no sizes; this is one reading of them).  `levels` encoder stages of widths
+ * widths[levels] (multiples of 8, 8..128), `c_in` 1..256, precision D2IP_FP32 only (the
+ * depthwise and pointwise kernels are FP32 SIMT), `batch` problems as in d2ip_set_network.
+ * Layout, in parameter order:
+ *   stem act(LN(conv3(c_in -> w0)));
+ *   per stage l: SE then ResConv3D(-> w_l, stride 1 for l = 0 else 2), where
+ *     SE(C) = x * sigmoid(FC2(relu(FC1(mean over voxels of x)))), FC1: C -> max(C/4, 1);
+ *     ResConv3D(ci -> co, s) = act(LN_b(DWSep_b(act(LN_a(DWSep_a(x, s))))) + P x),
+ *     DWSep = depthwise 3x3x3 (stride s) then pointwise 1x1x1, P a 1x1x1 convolution with
+ *     stride s when ci != co or s != 1, else the identity;
+ *   bottleneck: act(LN(DWSep(stride 2))) then ASPP: branches 1x1x1, depthwise dilation 2
+ *     and 3 each then 1x1x1, and the global mean through 1x1x1 broadcast back, each of
+ *     width max(C/2, 1) with LeakyReLU, concatenated in that order, 1x1x1 back to C,
+ *     act(LN);
+ *   decoder l = L-1..0: attention gate on the skip e_l, e_l * sigmoid(psi(relu(Wx e_l +
+ *     Up(Wg g)))) with max(w_l/2, 1) inner channels, then ResConv3D([Up(g), gated skip] ->
+ *     w_l); g is the coarser decoder output (the ASPP output for l = L-1);
+ *   tail sigmoid(conv1(w0 -> 1)).
+ * Weights: dense W[co][kz][ky][kx][ci] then b[co]; depthwise W[c][kz][ky][kx] then b[c]
+ * (kind D2IP_PARAM_CONV_W/B, fan_in 27); LayerNorm gamma then beta.  Every other call
+ * (J, input, optimiser, fits, state, tracing) works on it unchanged. */
+d2ip_status d2ip_set_network_fastres(d2ip_ctx* ctx, int levels, const int* widths, int c_in,
+                                     int precision, int batch);
+
 /* Number of parameters P of one problem's theta. */
 d2ip_status d2ip_param_count(d2ip_ctx* ctx, long long* count);
 /* Parameter table: row r = {kind, offset, count, fan_in} (kind: D2IP_PARAM_*), written to

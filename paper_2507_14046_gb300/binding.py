@@ -40,6 +40,7 @@ _SIGS = {
     "d2ip_destroy": [_vp],
     "d2ip_set_grid": [_vp, _i, _i, _i],
     "d2ip_set_network": [_vp, _i, _vp, _i, _i, _i],
+    "d2ip_set_network_fastres": [_vp, _i, _vp, _i, _i, _i],
     "d2ip_param_count": [_vp, C.POINTER(_ll)],
     "d2ip_param_table": [_vp, _vp, _i, C.POINTER(_i)],
     "d2ip_load_J": [_vp, _vp, _i, _i, _i],
@@ -167,6 +168,12 @@ def d2ip_set_network(ctx, levels, widths, c_in, precision, batch):
     return _call("d2ip_set_network", ctx, ctx, levels, C.cast(w, _vp), c_in, precision, batch)
 
 
+def d2ip_set_network_fastres(ctx, levels, widths, c_in, precision, batch):
+    w = (C.c_int * levels)(*widths)
+    return _call("d2ip_set_network_fastres", ctx, ctx, levels, C.cast(w, _vp), c_in, precision,
+                 batch)
+
+
 def d2ip_param_count(ctx) -> int:
     v = _ll()
     _call("d2ip_param_count", ctx, ctx, C.byref(v))
@@ -250,12 +257,18 @@ class Context:
     calls of the same name without the ``d2ip_`` prefix."""
 
     def __init__(self, grid, levels, widths, c_in=8, precision=D2IP_FP32, batch=1, device=0,
-                 stream=None):
+                 stream=None, net="resunet"):
+        """net: "resunet" (d2ip_set_network) or "fastres" (d2ip_set_network_fastres)."""
         self.handle = d2ip_create(device, stream)
         self.grid, self.batch, self.c_in = tuple(grid), batch, c_in
         X, Y, Z = grid
         d2ip_set_grid(self.handle, X, Y, Z)
-        d2ip_set_network(self.handle, levels, list(widths), c_in, precision, batch)
+        if net == "fastres":
+            d2ip_set_network_fastres(self.handle, levels, list(widths), c_in, precision, batch)
+        elif net == "resunet":
+            d2ip_set_network(self.handle, levels, list(widths), c_in, precision, batch)
+        else:
+            raise ValueError(f"unknown network {net!r}")
         self.P = d2ip_param_count(self.handle)
         self.n = X * Y * Z
         self.m = 0

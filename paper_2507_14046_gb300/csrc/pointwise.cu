@@ -24,6 +24,12 @@ __device__ __forceinline__ float group_sum(float v) {
   return v;
 }
 
+// Four consecutive floats from an address that need not be 16-byte aligned (LayerNorm
+// parameters sit at arbitrary offsets of the parameter arena).
+__device__ __forceinline__ float4 ld4_any(const float* p) {
+  return make_float4(__ldg(p), __ldg(p + 1), __ldg(p + 2), __ldg(p + 3));
+}
+
 template <int GP>
 __global__ void __launch_bounds__(256)
 ln_fwd_kernel(const float* __restrict__ z, const float* __restrict__ gamma,
@@ -47,8 +53,8 @@ ln_fwd_kernel(const float* __restrict__ z, const float* __restrict__ gamma,
   const float var = group_sum<GP>(d.x * d.x + d.y * d.y + d.z * d.z + d.w * d.w) * inv_c;
   const float rs = 1.0f / sqrtf(var + kLnEps);
   if (!on) return;
-  const float4 g = *reinterpret_cast<const float4*>(gamma + c);
-  const float4 be = *reinterpret_cast<const float4*>(beta + c);
+  const float4 g = ld4_any(gamma + c);
+  const float4 be = ld4_any(beta + c);
   float4 xh = make_float4(d.x * rs, d.y * rs, d.z * rs, d.w * rs);
   float4 o = make_float4(fmaf(xh.x, g.x, be.x), fmaf(xh.y, g.y, be.y), fmaf(xh.z, g.z, be.z),
                          fmaf(xh.w, g.w, be.w));
@@ -90,7 +96,7 @@ ln_bwd_kernel(const float* __restrict__ dy, const float* __restrict__ act_out,
   const int c = lane * 4;
   const bool con = c < C;
   float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (con) g = *reinterpret_cast<const float4*>(gamma + c);
+  if (con) g = ld4_any(gamma + c);
   const float inv_c = 1.0f / (float)C;
   float ag[4] = {0.f, 0.f, 0.f, 0.f}, ab[4] = {0.f, 0.f, 0.f, 0.f};
   const long long step = (long long)gridDim.x * kGroups;

@@ -10,6 +10,7 @@
 #include "../../include/d2ip.h"
 #include "common.cuh"
 #include "conv_bf16.cuh"
+#include "fastres.cuh"
 
 using namespace d2ip;
 
@@ -70,6 +71,7 @@ struct d2ip_ctx {
   // configuration
   int X = 0, Y = 0, Z = 0;
   int L = 0, c_in = 0, precision = D2IP_FP32, B = 1;
+  int arch = 0;  // 0: residual U-Net; 1: paper-form 3D-FastResUNet variant (node list fr)
   std::vector<int> w;
   bool net_ready = false;
   int m = 0;
@@ -107,6 +109,7 @@ struct d2ip_ctx {
   size_t j_bytes = 0;
   int seq_T_cap = 0;
   Bf16Net bf;  // tensor-core path: BF16 staging buffers, weights, TMA descriptors
+  FastNet fr;  // the FastResUNet variant's nodes and buffers (arch 1)
 
   // graphs
   cudaGraphExec_t g_step = nullptr, g_eval = nullptr;
@@ -203,6 +206,17 @@ struct Builder {
 };
 
 void build_plan(d2ip_ctx* c) {
+  if (c->arch == 1) {
+    c->bf = Bf16Net{};
+    c->stem = Unit{};
+    c->down.clear();
+    c->enc.clear();
+    c->dec.clear();
+    c->fr.build(Dims3{c->Z, c->Y, c->X}, c->L, c->w, c->c_in, c->table, c->P);
+    c->dims.assign(c->fr.dims.begin(), c->fr.dims.end() - 1);
+    c->Pp = round_up(c->P, kAlign);
+    return;
+  }
   c->dims.assign(c->L, Dims3{});
   c->dims[0] = Dims3{c->Z, c->Y, c->X};
   for (int l = 1; l < c->L; ++l) c->dims[l] = conv_out_dims(c->dims[l - 1], 3, 2);
@@ -284,76 +298,83 @@ void layout_buffers(d2ip_ctx* c, Carve& cv) {
   c->dsigma = cv.take<float>(B * nv(0));
   c->gds = cv.take<float>(B * nv(0));
   c->stage = cv.take<float>(B * nv(0));
-  long long maxz = 0;
-  for (int l = 0; l < c->L; ++l) maxz = std::max(maxz, nv(l) * w[l]);
-  c->ztmp = cv.take<float>(B * maxz);
-  c->ptmp = cv.take<float>(B * maxz);
-  auto unit_bufs = [&](Unit& u) {
-    const long long n = nv(u.lvl_out);
-    u.xh = cv.take<float>(B * n * u.ln.c);
-    u.rs = cv.take<float>(B * n);
-    u.a = cv.take<float>(B * n * u.ln.c);
-  };
-  auto res_bufs = [&](Res& R) {
-    const long long n = nv(R.lvl);
-    const int co = R.lna.c;
-    R.xh_a = cv.take<float>(B * n * co);
-    R.rs_a = cv.take<float>(B * n);
-    R.h1 = cv.take<float>(B * n * co);
-    R.xh_b = cv.take<float>(B * n * co);
-    R.rs_b = cv.take<float>(B * n);
-    R.out = cv.take<float>(B * n * co);
-  };
-  unit_bufs(c->stem);
-  for (int l = 0; l < c->L; ++l) {
-    if (l > 0) unit_bufs(c->down[l]);
-    res_bufs(c->enc[l]);
-  }
-  for (int l = 0; l + 1 < c->L; ++l) res_bufs(c->dec[l]);
-  c->lb.assign(c->L, LevelBufs{});
-  for (int l = 0; l < c->L; ++l) {
-    const long long cmax = w[l] + (l + 1 < c->L ? w[l + 1] : 0);
-    LevelBufs& L = c->lb[l];
-    L.g1 = cv.take<float>(B * nv(l) * cmax);
-    L.g2 = cv.take<float>(B * nv(l) * cmax);
-    L.tz = cv.take<float>(B * nv(l) * w[l]);
-    L.tt = cv.take<float>(B * nv(l) * w[l]);
-    L.th = cv.take<float>(B * nv(l) * w[l]);
-    L.de = cv.take<float>(B * nv(l) * w[l]);
-    if (l + 1 < c->L) L.cat = cv.take<float>(B * nv(l) * cmax);
-  }
-  // wiring of block inputs
-  c->stem.x = c->zin;
-  c->enc[0].x = c->stem.a;
-  for (int l = 1; l < c->L; ++l) {
-    c->down[l].x = c->enc[l - 1].out;
-    c->enc[l].x = c->down[l].a;
-  }
-  for (int l = 0; l + 1 < c->L; ++l) c->dec[l].x = c->lb[l].cat;
-  // workspace: the largest split-K / LayerNorm partial buffer of any layer
-  long long ws = conv_ws_floats(c, c->stem.conv);
-  ws = std::max(ws, ln_ws_floats(c, c->stem.ln, 0));
-  auto res_ws = [&](const Res& R) {
-    ws = std::max(ws, conv_ws_floats(c, R.a));
-    if (R.fuse_w)
-      ws = std::max(ws, conv_ws_floats(c, R.a) +
-                            (long long)c->B * wgrad_rows(c, R.a) * (R.p.wcount() + R.p.co));
-    ws = std::max(ws, conv_ws_floats(c, R.b));
-    if (R.proj) ws = std::max(ws, conv_ws_floats(c, R.p));
-    ws = std::max(ws, ln_ws_floats(c, R.lna, R.lvl));
-    ws = std::max(ws, ln_ws_floats(c, R.lnb, R.lvl));
-  };
-  for (int l = 0; l < c->L; ++l) {
-    res_ws(c->enc[l]);
-    if (l > 0) {
-      ws = std::max(ws, conv_ws_floats(c, c->down[l].conv));
-      ws = std::max(ws, ln_ws_floats(c, c->down[l].ln, l));
+  if (c->arch == 1) {
+    float* frm = cv.take<float>(c->fr.arena_floats(B));
+    if (!cv.dry) c->fr.bind(frm, B, c->zin, c->dsigma, c->gds);
+    c->ws = nullptr;
+    c->ws_floats = 0;
+  } else {
+    long long maxz = 0;
+    for (int l = 0; l < c->L; ++l) maxz = std::max(maxz, nv(l) * w[l]);
+    c->ztmp = cv.take<float>(B * maxz);
+    c->ptmp = cv.take<float>(B * maxz);
+    auto unit_bufs = [&](Unit& u) {
+      const long long n = nv(u.lvl_out);
+      u.xh = cv.take<float>(B * n * u.ln.c);
+      u.rs = cv.take<float>(B * n);
+      u.a = cv.take<float>(B * n * u.ln.c);
+    };
+    auto res_bufs = [&](Res& R) {
+      const long long n = nv(R.lvl);
+      const int co = R.lna.c;
+      R.xh_a = cv.take<float>(B * n * co);
+      R.rs_a = cv.take<float>(B * n);
+      R.h1 = cv.take<float>(B * n * co);
+      R.xh_b = cv.take<float>(B * n * co);
+      R.rs_b = cv.take<float>(B * n);
+      R.out = cv.take<float>(B * n * co);
+    };
+    unit_bufs(c->stem);
+    for (int l = 0; l < c->L; ++l) {
+      if (l > 0) unit_bufs(c->down[l]);
+      res_bufs(c->enc[l]);
     }
+    for (int l = 0; l + 1 < c->L; ++l) res_bufs(c->dec[l]);
+    c->lb.assign(c->L, LevelBufs{});
+    for (int l = 0; l < c->L; ++l) {
+      const long long cmax = w[l] + (l + 1 < c->L ? w[l + 1] : 0);
+      LevelBufs& L = c->lb[l];
+      L.g1 = cv.take<float>(B * nv(l) * cmax);
+      L.g2 = cv.take<float>(B * nv(l) * cmax);
+      L.tz = cv.take<float>(B * nv(l) * w[l]);
+      L.tt = cv.take<float>(B * nv(l) * w[l]);
+      L.th = cv.take<float>(B * nv(l) * w[l]);
+      L.de = cv.take<float>(B * nv(l) * w[l]);
+      if (l + 1 < c->L) L.cat = cv.take<float>(B * nv(l) * cmax);
+    }
+    // wiring of block inputs
+    c->stem.x = c->zin;
+    c->enc[0].x = c->stem.a;
+    for (int l = 1; l < c->L; ++l) {
+      c->down[l].x = c->enc[l - 1].out;
+      c->enc[l].x = c->down[l].a;
+    }
+    for (int l = 0; l + 1 < c->L; ++l) c->dec[l].x = c->lb[l].cat;
+    // workspace: the largest split-K / LayerNorm partial buffer of any layer
+    long long ws = conv_ws_floats(c, c->stem.conv);
+    ws = std::max(ws, ln_ws_floats(c, c->stem.ln, 0));
+    auto res_ws = [&](const Res& R) {
+      ws = std::max(ws, conv_ws_floats(c, R.a));
+      if (R.fuse_w)
+        ws = std::max(ws, conv_ws_floats(c, R.a) +
+                              (long long)c->B * wgrad_rows(c, R.a) * (R.p.wcount() + R.p.co));
+      ws = std::max(ws, conv_ws_floats(c, R.b));
+      if (R.proj) ws = std::max(ws, conv_ws_floats(c, R.p));
+      ws = std::max(ws, ln_ws_floats(c, R.lna, R.lvl));
+      ws = std::max(ws, ln_ws_floats(c, R.lnb, R.lvl));
+    };
+    for (int l = 0; l < c->L; ++l) {
+      res_ws(c->enc[l]);
+      if (l > 0) {
+        ws = std::max(ws, conv_ws_floats(c, c->down[l].conv));
+        ws = std::max(ws, ln_ws_floats(c, c->down[l].ln, l));
+      }
+    }
+    for (int l = 0; l + 1 < c->L; ++l) res_ws(c->dec[l]);
+    ws = std::max(ws, conv_ws_floats(c, c->tail));
+    c->ws_floats = ws;
+    c->ws = cv.take<float>(ws);
   }
-  for (int l = 0; l + 1 < c->L; ++l) res_ws(c->dec[l]);
-  ws = std::max(ws, conv_ws_floats(c, c->tail));
-  c->ws_floats = ws;
-  c->ws = cv.take<float>(ws);
   c->loss = cv.take<double>(B);
   c->resid = cv.take<double>(B);
   c->trace = cv.take<double>((long long)kTraceCap * B);
@@ -542,7 +563,22 @@ struct Launcher {
     conv_fwd(R.b, R.h1, c->ztmp);
     ln_fwd(R.lnb, R.lvl, c->ztmp, R.proj ? c->ptmp : R.x, R.out, R.xh_b, R.rs_b, next);
   }
+  static void tr_beg(void* u, int k, double w) { static_cast<Launcher*>(u)->beg(k, w); }
+  static void tr_fin(void* u) { static_cast<Launcher*>(u)->fin(); }
+  FrRun fr_run() {
+    FrRun r{c->theta, c->grad, c->Pp, c->stream};
+    if (tr) {
+      r.beg = tr_beg;
+      r.fin = tr_fin;
+      r.user = this;
+    }
+    return r;
+  }
   void forward() {
+    if (c->arch == 1) {
+      ok(c->fr.forward(fr_run()));
+      return;
+    }
     if (c->precision == D2IP_BF16) ok(bf16_prepare_weights(c->bf, c->theta, c->B, c->Pp, c->stream));
     staged_x.clear();
     unit_fwd(c->stem, &c->enc[0].a);
@@ -665,6 +701,10 @@ struct Launcher {
     conv_wgrad(u.conv, u.x, tz);
   }
   void backward() {
+    if (c->arch == 1) {
+      ok(c->fr.backward(fr_run()));
+      return;
+    }
     ybf_owner = nullptr;
     pbf_owner = nullptr;
     const int L = c->L;
@@ -1023,6 +1063,33 @@ d2ip_status d2ip_set_network(d2ip_ctx* c, int levels, const int* widths, int c_i
   c->c_in = c_in;
   c->precision = precision;
   c->B = batch;
+  c->arch = 0;
+  c->net_ready = true;
+  c->j_ready = c->input_ready = false;
+  build_plan(c);
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_set_network_fastres(d2ip_ctx* c, int levels, const int* widths, int c_in,
+                                     int precision, int batch) {
+  if (!c) return fail(nullptr, D2IP_ERR_BAD_ARG, "null context");
+  if (!c->X) return fail(c, D2IP_ERR_STATE, "call d2ip_set_grid first");
+  if (levels < 1 || levels > 6 || !widths)
+    return fail(c, D2IP_ERR_BAD_ARG, "levels must be 1..6 with a widths array");
+  if (!fastres_supported(levels, widths, c_in))
+    return fail(c, D2IP_ERR_BAD_SHAPE,
+                "each width must be a multiple of 8 in 8..128 and c_in 1..256");
+  if (precision != D2IP_FP32)
+    return fail(c, D2IP_ERR_BAD_ARG, "the FastResUNet variant runs in D2IP_FP32");
+  if (batch < 1 || batch > 4096) return fail(c, D2IP_ERR_BAD_ARG, "batch must be 1..4096");
+  cudaSetDevice(c->device);
+  free_arena(c);
+  c->L = levels;
+  c->w.assign(widths, widths + levels);
+  c->c_in = c_in;
+  c->precision = precision;
+  c->B = batch;
+  c->arch = 1;
   c->net_ready = true;
   c->j_ready = c->input_ready = false;
   build_plan(c);
