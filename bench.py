@@ -58,16 +58,20 @@ def iters_per_step(w) -> int:
 # oracle (CPU baseline and the reference arm)
 # ------------------------------------------------------------------------------------------
 
-def _oracle_rate(w, grid, rings, iters: int) -> float:
+def _oracle_rate(w, grid, rings, iters: int, net: str = "resunet") -> float:
     """Seconds per FP64 oracle DIP iteration of network ``w`` on one seeded problem."""
-    from oracle import dip, network as onet
+    from oracle import dip, fastres as ofr, network as onet
     J = synth.sensitivity_raw(grid, rings, w.seed)
     truth = synth.ellipsoid_phantom(grid, synth.lung_pair(grid))[None]
     V = synth.measurements(J, truth, w.seed)
     n = grid[0] * grid[1] * grid[2]
     Zin = synth.input_noise(n, w.c_in, w.seed)
-    spec = onet.NetSpec(tuple(grid), w.levels, w.widths, w.c_in)
-    table = [(k, o, c, f) for _, _, k, f, o, c in onet.param_layout(spec)]
+    if net == "fastres":
+        spec = ofr.FastSpec(tuple(grid), w.levels, w.widths, w.c_in)
+        table = ofr.table(spec)
+    else:
+        spec = onet.NetSpec(tuple(grid), w.levels, w.widths, w.c_in)
+        table = [(k, o, c, f) for _, _, k, f, o, c in onet.param_layout(spec)]
     th = synth.kaiming_theta(table, w.seed).astype(np.float64)
     Jn, _ = dip.normalise_columns(J)
     Z64, dv = Zin.astype(np.float64), V[0].astype(np.float64)
@@ -79,7 +83,7 @@ def _oracle_rate(w, grid, rings, iters: int) -> float:
     return (time.perf_counter() - t0) / iters
 
 
-def oracle_leg(workload: str, iters: int) -> dict:
+def oracle_leg(workload: str, iters: int, net: str = "resunet") -> dict:
     """Time FP64 oracle DIP iterations on the workload (first frame, from the Kaiming
     weights); returns iterations/s.  For the batched workload every grid of the mix is timed
     and weighted by its number of sequences."""
@@ -102,17 +106,18 @@ def oracle_leg(workload: str, iters: int) -> dict:
                                                       "sequences": cnt}
                            for g, (k, spi, cnt) in per_grid.items()}}
     w = WORKLOADS[workload]
-    spi = _oracle_rate(w, w.grid, w.rings, iters)
+    spi = _oracle_rate(w, w.grid, w.rings, iters, net)
     return {"iters": iters, "seconds": spi * iters, "iters_per_s": 1.0 / spi}
 
 
-def run_oracle_subprocess(workload: str, iters: int) -> dict:
+def run_oracle_subprocess(workload: str, iters: int, net: str = "resunet") -> dict:
     cores = os.cpu_count() or 1
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(cores)
     out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-leg", workload,
-                          "--oracle-iters", str(iters)], capture_output=True, text=True,
+                          "--oracle-iters", str(iters), "--net", net], capture_output=True,
+                         text=True,
                          env=env, check=True)
     res = json.loads(out.stdout.strip().splitlines()[-1])
     res["cores"] = cores
@@ -194,7 +199,7 @@ def run_gpu(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     prec = B.D2IP_BF16 if args.precision == "bf16" else B.D2IP_FP32
     ctx = B.Context(w.grid, w.levels, w.widths, w.c_in, prec, 1, device=local_rank,
-                    stream=stream.cuda_stream)
+                    stream=stream.cuda_stream, net=args.net)
     table = ctx.table()
     theta0 = synth.kaiming_theta([tuple(r) for r in table], w.seed)
     m, n, T = J.shape[0], J.shape[1], w.frames
@@ -249,10 +254,8 @@ def run_gpu(args, rank, world, local_rank):
     ctx.set_input(Zd, thd)
     prof = ctx.profile(Vd[0], 10)
     roof = _roofline(prof, args, clk, 10)
-    kpl = {"conv_wgrad": 2, "ln_bwd": 2, "up_bwd": 2}
-    launches_per_iter = sum(v[2] * kpl.get(k, 1) for k, v in prof.items()) / 10.0
-    fwd_launches = sum(prof[k][2] for k in ("conv_fwd", "ln_fwd", "up_fwd")) / 10.0 + 2
-    gpu_launches = int(args.steps * (its * launches_per_iter + T * fwd_launches + 1))
+    nk_step, nk_eval = ctx.graph_kernels()
+    gpu_launches = int(args.steps * (its * nk_step + T * nk_eval))
 
     # end to end through the C ABI with pinned host buffers
     Jh = torch.from_numpy(J).pin_memory()
@@ -467,10 +470,17 @@ def _source_digest():
     return h.hexdigest()
 
 
-def _traffic(cls):
+TRAFFIC_FILES = {("batch64", "resunet", "bf16"): "roofline_traffic_batch64_bf16.txt",
+                 ("seq32", "fastres", "fp32"): "roofline_traffic_seq32_fastres_fp32.txt"}
+
+
+def _traffic(cls, args):
     """DRAM bytes per launch of the class from the committed ncu summary, when it was taken on
-    the kernels as they are now (same CUDA sources); else None."""
-    path = os.path.join(ROOT, "profiles", "roofline_traffic_batch64_bf16.txt")
+    the kernels as they are now (same CUDA sources) and on this workload; else None."""
+    name = TRAFFIC_FILES.get((args.workload, args.net, args.precision))
+    if name is None:
+        return None
+    path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as fh:
             t = json.load(fh)
@@ -491,7 +501,7 @@ def _roofline(prof, args, clk, iters):
     if dom.startswith("conv") and args.precision == "bf16":
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
         roof = {"bound": "tensor", "achieved": per_launch / (avg_ms * 1e-3) / 1e12,
-                "peak": peak, "unit": "TFLOP/s", "traffic": _traffic(dom),
+                "peak": peak, "unit": "TFLOP/s", "traffic": _traffic(dom, args),
                 "peak_source": f"{kind} bf16_tflops_sustained (kernel timed inside a long step); "
                                "the class also holds its BF16 staging, the partial-sum "
                                "reductions and the 1x1x1 single-channel last layer (FP32)"}
@@ -499,13 +509,13 @@ def _roofline(prof, args, clk, iters):
         mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
         peak = SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": per_launch / (avg_ms * 1e-3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "traffic": _traffic(dom),
+                "unit": "TFLOP/s", "traffic": _traffic(dom, args),
                 "peak_source": f"FP32 FFMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                                f"{mhz:.0f} MHz (median sampled SM clock)"}
     else:
         peak = peaks["hbm_gbs"]
         roof = {"bound": "hbm", "achieved": per_launch / (avg_ms * 1e-3) / 1e9, "peak": peak,
-                "unit": "GB/s", "traffic": _traffic(dom), "peak_source": f"{kind} hbm_gbs"}
+                "unit": "GB/s", "traffic": _traffic(dom, args), "peak_source": f"{kind} hbm_gbs"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dom
     roof["avg_launch_us"] = avg_ms * 1e3
@@ -523,6 +533,24 @@ def run_probe(args):
     from paper_2507_14046_gb300 import binding as B
 
     w = synth.SEQ_32
+    if args.net == "fastres":  # the variant on the 20-frame sequence's first frame, FP32
+        J, truth, V, Zin = synth.make_problem(w)
+        c = B.Context(w.grid, w.levels, w.widths, w.c_in, B.D2IP_FP32, 1, net="fastres")
+        th = synth.kaiming_theta([tuple(r) for r in c.table()], w.seed)
+        c.load_J(J)
+        c.set_input(Zin, th)
+        c.set_optim(w.lr)
+        c.run_steps(V[:1], args.warmup)
+        torch.cuda.synchronize()
+        prof = c.profile(V[0], args.probe)
+        nk_step, nk_eval = c.graph_kernels()
+        print(json.dumps({"probe": f"FastResUNet variant, grid {list(w.grid)}, FP32",
+                          "iters": args.probe, "step_graph_kernels": nk_step,
+                          "profile_ms_per_iter": {k: round(v[0] / args.probe, 4)
+                                                  for k, v in prof.items()},
+                          "launches_per_iter": {k: v[2] / args.probe for k, v in prof.items()}}))
+        c.close()
+        return
     groups = synth.batch_workload(64, w.frames, seed=1, c_in=w.c_in)
     g = max(groups, key=lambda q: q.J.shape[1] * len(q.problems))
     nprob = min(args.probe_problems or len(g.problems), len(g.problems))
@@ -584,6 +612,9 @@ def main():
     ap.add_argument("--study", type=int, default=0,
                     help="run the convergence ablation for this many iterations and exit")
     ap.add_argument("--study-out", default=None)
+    ap.add_argument("--net", default="resunet", choices=["resunet", "fastres"],
+                    help="network: the residual U-Net, or the paper-form FastResUNet variant "
+                         "(FP32, single-sequence workloads)")
     args = ap.parse_args()
     if args.study:
         run_study(args)
@@ -593,8 +624,13 @@ def main():
         return
 
     if args.oracle_leg:
-        print(json.dumps(oracle_leg(args.oracle_leg, args.oracle_iters)))
+        print(json.dumps(oracle_leg(args.oracle_leg, args.oracle_iters, args.net)))
         return
+    if args.net == "fastres":
+        if args.workload == "batch64":
+            args.workload = "seq32"
+        if args.precision == "bf16":
+            ap.error("the FastResUNet variant runs in FP32")
     if args.precision is None:
         args.precision = "bf16" if args.workload == "batch64" else "fp32"
 
@@ -607,6 +643,10 @@ def main():
               "lr": w.lr, "iters_per_step": its, "precision": args.precision,
               "l2": "512 MB buffer written between timed steps (working set < L2)",
               "parallelism": f"replicas x{args.gpus}"}
+    if args.net == "fastres":
+        config["workload"] = (w.name.replace("L3(16,32,64)", "FastResUNet(16,32,64)")
+                              + ", FP32 (paper-form network variant)")
+        config["net"] = "fastres"
 
     if args.workload == "batch64":
         config["workload"] = ("64 independent 20-frame sequences (grids 16x16x8 / 32x32x16 / "
@@ -629,10 +669,10 @@ def main():
         per = oracle_iters_for(args.workload)
         per = max(1, per // 4)
         for _ in range(args.warmup):
-            oracle_leg(args.workload, 1)
+            oracle_leg(args.workload, 1, args.net)
         tot_it, tot_s = 0, 0.0
         for _ in range(args.steps):
-            r = oracle_leg(args.workload, per)
+            r = oracle_leg(args.workload, per, args.net)
             tot_it += r["iters"]
             tot_s += r["seconds"]
         v = tot_it / tot_s
@@ -659,7 +699,7 @@ def main():
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        r = run_oracle_subprocess(args.workload, oracle_iters_for(args.workload))
+        r = run_oracle_subprocess(args.workload, oracle_iters_for(args.workload), args.net)
         cpu = {"value": r["iters_per_s"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                "sample": f"{r['iters']} FP64 oracle DIP iterations (first frame of the same "
                          f"workload{', every grid of the mix, weighted by its sequences' if args.workload == 'batch64' else ''}"

@@ -14,10 +14,17 @@ namespace d2ip {
 namespace {
 
 constexpr int kPwV = 32;       // voxels per pointwise forward / data-gradient block
-constexpr int kPwWV = 256;     // voxels per pointwise weight-gradient partial row
+constexpr int kPwK = 32;       // input channels per staged weight tile of the forward
 constexpr int kPwPairs = 4096; // (co, ci) pairs per weight-gradient block (16 per thread)
-constexpr int kDwWV = 512;     // voxels per depthwise weight-gradient partial row
-constexpr int kSumV = 1024;    // voxels per voxel-sum partial row
+constexpr int kSumV = 256;     // voxels per voxel-sum partial row
+constexpr int kRowTarget = 608;  // partial rows aimed at per weight gradient (4 per SM)
+
+// Voxels per partial row of a weight gradient: a multiple of 32 between 32 and `cap`, chosen
+// so that about kRowTarget rows (blocks) cover the volume.
+long long wgrad_chunk(long long nout, long long cap) {
+  long long c = ceil_div(ceil_div(nout, kRowTarget), 32) * 32;
+  return c < 32 ? 32 : (c > cap ? cap : c);
+}
 
 __device__ __forceinline__ long long strided_voxel(long long q, Dims3 dout, Dims3 din, int s) {
   if (s == 1) return q;
@@ -28,34 +35,64 @@ __device__ __forceinline__ long long strided_voxel(long long q, Dims3 dout, Dims
   return ((long long)(s * qz) * din.y + s * qy) * din.x + s * qx;
 }
 
-// y[q][o] (=|+=) b[o] + sum_i W[o][i] x[in(q)][i], in(q) the voxel s*q of din.
+// y[q][o] (=|+=) b[o] + sum_i W[o][i] x[in(q)][i], in(q) the voxel s*q of din.  The block
+// stages its vb input rows (row stride ci + 1: no bank conflicts between voxels) and the
+// weights transposed, kPwK input channels at a time, so a warp reads consecutive outputs'
+// weights.  vb * co <= 1024: each thread keeps the sums of up to 4 (voxel, output) pairs;
+// the channel sum runs in order.
 __global__ void __launch_bounds__(256) pw_fwd_kernel(const float* __restrict__ x,
                                                      const float* __restrict__ W, float* y,
                                                      Dims3 din, Dims3 dout, int ci, int co, int s,
-                                                     long long w_bs, int acc) {
-  extern __shared__ float xs[];  // [kPwV][ci]
+                                                     long long w_bs, int acc, int vb) {
+  extern __shared__ float sm[];  // xs[vb][ci + 1], wt[kPwK][co]
+  float* xs = sm;
+  float* wt = sm + vb * (ci + 1);
   const int b = blockIdx.y;
-  const long long nout = dout.count(), q0 = (long long)blockIdx.x * kPwV;
+  const long long nout = dout.count(), q0 = (long long)blockIdx.x * vb;
   x += (long long)b * din.count() * ci;
   y += (long long)b * nout * co;
   W += (long long)b * w_bs;
   const float* bias = W + (long long)co * ci;
-  for (int i = threadIdx.x; i < kPwV * ci; i += blockDim.x) {
+  for (int i = threadIdx.x; i < vb * ci; i += blockDim.x) {
     const int v = i / ci, c = i - v * ci;
     const long long q = q0 + v;
-    xs[i] = q < nout ? x[strided_voxel(q, dout, din, s) * ci + c] : 0.f;
+    xs[v * (ci + 1) + c] = q < nout ? x[strided_voxel(q, dout, din, s) * ci + c] : 0.f;
   }
-  __syncthreads();
-  for (int o = threadIdx.x; o < kPwV * co; o += blockDim.x) {
+  const int npair = vb * co;
+  float a[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int o = threadIdx.x + 256 * j;
+    a[j] = o < npair ? bias[o % co] : 0.f;
+  }
+  for (int k0 = 0; k0 < ci; k0 += kPwK) {
+    const int kn = min(kPwK, ci - k0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kn * co; i += blockDim.x) {
+      const int k = i / co, c = i - k * co;
+      wt[i] = W[(long long)c * ci + k0 + k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int o = threadIdx.x + 256 * j;
+      if (o >= npair) continue;
+      const int v = o / co, c = o - v * co;
+      const float* xv = xs + v * (ci + 1) + k0;
+      float t = a[j];
+      for (int k = 0; k < kn; ++k) t = fmaf(wt[k * co + c], xv[k], t);
+      a[j] = t;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int o = threadIdx.x + 256 * j;
+    if (o >= npair) continue;
     const int v = o / co, c = o - v * co;
     const long long q = q0 + v;
     if (q >= nout) continue;
-    const float* w = W + (long long)c * ci;
-    const float* xv = xs + v * ci;
-    float a = bias[c];
-    for (int k = 0; k < ci; ++k) a = fmaf(w[k], xv[k], a);
     float* d = y + q * co + c;
-    *d = acc ? *d + a : a;
+    *d = acc ? *d + a[j] : a[j];
   }
 }
 
@@ -94,7 +131,7 @@ __global__ void __launch_bounds__(256) pw_dgrad_kernel(const float* __restrict__
 __global__ void __launch_bounds__(256) pw_wgrad_kernel(const float* __restrict__ x,
                                                        const float* __restrict__ dy, float* part,
                                                        Dims3 din, Dims3 dout, int ci, int co,
-                                                       int s, long long rows) {
+                                                       int s, long long rows, long long chv) {
   extern __shared__ float sm[];  // xs[kPwV][ci] then dys[kPwV][co]
   float* xs = sm;
   float* dys = sm + kPwV * ci;
@@ -107,8 +144,8 @@ __global__ void __launch_bounds__(256) pw_wgrad_kernel(const float* __restrict__
   float a[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) a[j] = 0.f;
-  const long long v_end = min(nout, (chunk + 1) * kPwWV);
-  for (long long t0 = chunk * kPwWV; t0 < v_end; t0 += kPwV) {
+  const long long v_end = min(nout, (chunk + 1) * chv);
+  for (long long t0 = chunk * chv; t0 < v_end; t0 += kPwV) {
     __syncthreads();
     for (int i = threadIdx.x; i < kPwV * ci; i += blockDim.x) {
       const long long q = t0 + i / ci;
@@ -220,12 +257,12 @@ __global__ void __launch_bounds__(256) dw_dgrad_kernel(const float* __restrict__
   *o = acc ? *o + a : a;
 }
 
-// part[b][chunk][28 C]: per chunk of kDwWV output voxels, W part [c][27] then bias [c].
+// part[b][chunk][28 C]: per chunk of chv output voxels, W part [c][27] then bias [c].
 // Thread (channel c, voxel lane vl) sums its voxels; lanes are then added in order.
 __global__ void __launch_bounds__(256) dw_wgrad_kernel(const float* __restrict__ x,
                                                        const float* __restrict__ dy, float* part,
                                                        Dims3 din, Dims3 dout, int C, int s, int d,
-                                                       long long rows) {
+                                                       long long rows, long long chv) {
   __shared__ float red[256 * 28];
   const int b = blockIdx.y;
   const long long chunk = blockIdx.x, nout = dout.count();
@@ -238,8 +275,8 @@ __global__ void __launch_bounds__(256) dw_wgrad_kernel(const float* __restrict__
   for (int t = 0; t < 28; ++t) a[t] = 0.f;
   if (vl < nvl) {
     const long long yx = (long long)dout.y * dout.x;
-    const long long v_end = min(nout, (chunk + 1) * kDwWV);
-    for (long long q = chunk * kDwWV + vl; q < v_end; q += nvl) {
+    const long long v_end = min(nout, (chunk + 1) * chv);
+    for (long long q = chunk * chv + vl; q < v_end; q += nvl) {
       const int oz = (int)(q / yx), oy = (int)((q - oz * yx) / dout.x),
                 ox = (int)(q - oz * yx - (long long)oy * dout.x);
       const float g = dy[q * C + c];
@@ -395,17 +432,23 @@ unsigned blocks(long long n) { return (unsigned)ceil_div(n, 256); }
 
 }  // namespace
 
+// voxels per pointwise forward block: vb * co <= 1024 (4 sums per thread), at most kPwV
+int pw_vb(int co) { return co >= 1024 ? 1 : (1024 / co < kPwV ? 1024 / co : kPwV); }
+
 bool pw_supported(int ci, int co) {
-  return ci >= 1 && co >= 1 && (long long)kPwV * (ci + co) * 4 <= 48 * 1024;
+  return ci >= 1 && co >= 1 && co <= 1024 &&
+         ((long long)pw_vb(co) * (ci + 1) + (long long)kPwK * co) * 4 <= 48 * 1024 &&
+         (long long)kPwV * (ci + co) * 4 <= 48 * 1024;
 }
 
 cudaError_t pw_fwd_f32(const float* x, const float* W, float* y, int B, Dims3 din, int ci,
                        int co, int s, long long w_bs, int acc, cudaStream_t st) {
   if (!pw_supported(ci, co) || (s != 1 && s != 2)) return cudaErrorInvalidValue;
   const Dims3 dout = conv_out_dims(din, 1, s);
-  dim3 grid((unsigned)ceil_div(dout.count(), kPwV), B);
-  pw_fwd_kernel<<<grid, 256, kPwV * ci * sizeof(float), st>>>(x, W, y, din, dout, ci, co, s,
-                                                                w_bs, acc);
+  const int vb = pw_vb(co);
+  dim3 grid((unsigned)ceil_div(dout.count(), vb), B);
+  const size_t smem = ((size_t)vb * (ci + 1) + (size_t)kPwK * co) * sizeof(float);
+  pw_fwd_kernel<<<grid, 256, smem, st>>>(x, W, y, din, dout, ci, co, s, w_bs, acc, vb);
   return cudaGetLastError();
 }
 
@@ -425,7 +468,8 @@ cudaError_t pw_dgrad_f32(const float* dy, const float* W, float* dx, int B, Dims
 }
 
 long long pw_wgrad_rows(Dims3 din, int s) {
-  return ceil_div(conv_out_dims(din, 1, s).count(), kPwWV);
+  const long long n = conv_out_dims(din, 1, s).count();
+  return ceil_div(n, wgrad_chunk(n, 256));
 }
 
 cudaError_t pw_wgrad_partial_f32(const float* x, const float* dy, float* part, int B, Dims3 din,
@@ -433,10 +477,11 @@ cudaError_t pw_wgrad_partial_f32(const float* x, const float* dy, float* part, i
   if (!pw_supported(ci, co) || (s != 1 && s != 2)) return cudaErrorInvalidValue;
   const Dims3 dout = conv_out_dims(din, 1, s);
   const long long rows = pw_wgrad_rows(din, s);
+  const long long chv = wgrad_chunk(dout.count(), 256);
   const long long npairs = (long long)co * ci + co;
   dim3 grid((unsigned)rows, (unsigned)ceil_div(npairs, kPwPairs), B);
   pw_wgrad_kernel<<<grid, 256, kPwV * (ci + co) * sizeof(float), st>>>(x, dy, part, din, dout,
-                                                                         ci, co, s, rows);
+                                                                         ci, co, s, rows, chv);
   return cudaGetLastError();
 }
 
@@ -459,7 +504,8 @@ cudaError_t dw_dgrad_f32(const float* dy, const float* W, float* dx, int B, Dims
 }
 
 long long dw_wgrad_rows(Dims3 din, int s) {
-  return ceil_div(conv_out_dims(din, 3, s).count(), kDwWV);
+  const long long n = conv_out_dims(din, 3, s).count();
+  return ceil_div(n, wgrad_chunk(n, 512));
 }
 
 cudaError_t dw_wgrad_partial_f32(const float* x, const float* dy, float* part, int B, Dims3 din,
@@ -468,7 +514,8 @@ cudaError_t dw_wgrad_partial_f32(const float* x, const float* dy, float* part, i
   const Dims3 dout = conv_out_dims(din, 3, s);
   const long long rows = dw_wgrad_rows(din, s);
   dim3 grid((unsigned)rows, B);
-  dw_wgrad_kernel<<<grid, 256, 0, st>>>(x, dy, part, din, dout, C, s, d, rows);
+  dw_wgrad_kernel<<<grid, 256, 0, st>>>(x, dy, part, din, dout, C, s, d, rows,
+                                        wgrad_chunk(dout.count(), 512));
   return cudaGetLastError();
 }
 
