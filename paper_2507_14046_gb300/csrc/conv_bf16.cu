@@ -735,19 +735,39 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
           }
           epi_sync();
           const int oz = z0 + zz;
-          if (oz < dout.z) {
+          if (oz < dout.z && !accum) {
             for (int e = tid; e < 128 * n4; e += 128) {
               const int mv = e / n4, c4 = e % n4;
               const int ox = x0 + mv % 8, oy = y0 + mv / 8;
               if (ox >= dout.x || oy >= dout.y) continue;
-              float4 v = *reinterpret_cast<const float4*>(stg + mv * ld + c4 * 4);
-              float4* o = reinterpret_cast<float4*>(
-                              dst + (((long long)oz * dout.y + oy) * dout.x + ox) * nc) + c4;
-              if (accum) {
-                const float4 p = *o;
-                v.x += p.x, v.y += p.y, v.z += p.z, v.w += p.w;
+              const float4 v = *reinterpret_cast<const float4*>(stg + mv * ld + c4 * 4);
+              *(reinterpret_cast<float4*>(
+                    dst + (((long long)oz * dout.y + oy) * dout.x + ox) * nc) + c4) = v;
+            }
+          } else if (oz < dout.z) {  // accumulate: four loads of the old values in flight
+            for (int e0 = tid; e0 < 128 * n4; e0 += 4 * 128) {
+              float4 v[4], p[4];
+              float4* o[4];
+              bool on[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int e = e0 + 128 * u;
+                const int mv = e / n4, c4 = e % n4;
+                const int ox = x0 + mv % 8, oy = y0 + mv / 8;
+                on[u] = e < 128 * n4 && ox < dout.x && oy < dout.y;
+                o[u] = reinterpret_cast<float4*>(
+                           dst + (((long long)oz * dout.y + oy) * dout.x + ox) * nc) + c4;
+                if (on[u]) {
+                  v[u] = *reinterpret_cast<const float4*>(stg + mv * ld + c4 * 4);
+                  p[u] = *o[u];
+                }
               }
-              *o = v;
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                if (!on[u]) continue;
+                v[u].x += p[u].x, v[u].y += p[u].y, v[u].z += p[u].z, v[u].w += p[u].w;
+                *o[u] = v[u];
+              }
             }
           }
           epi_sync();

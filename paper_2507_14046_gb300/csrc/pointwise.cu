@@ -369,6 +369,78 @@ __global__ void up_bwd_kernel(const float* __restrict__ dcat, float* __restrict_
   *reinterpret_cast<float4*>(dlow + ((long long)b * nl + vox) * Cu + c) = acc;
 }
 
+// Factor-2 form of the adjoint (every output extent twice the low one).  Along an axis low
+// index i receives from the outputs 2i-1, 2i, 2i+1, 2i+2 with weights 1/4, 3/4, 3/4, 1/4
+// (the transpose of the forward's 1/4-3/4 stencil); at the borders the clamped neighbour
+// folds the outer weight onto the inner one (i = 0: 2i gets 1; i = n-1: 2i+1 gets 1) and the
+// taps past the edge get 0.  A thread takes two neighbouring low voxels along x (six output
+// columns instead of eight) and one group of 4 channels; taps are unrolled.
+__global__ void __launch_bounds__(256) up2_bwd_kernel(const float* __restrict__ dcat,
+                                                      float* __restrict__ dlow, Dims3 dl,
+                                                      Dims3 dout, int Cu, int Cs) {
+  const int b = blockIdx.y;
+  const int Ct = Cu + Cs, G = Cu / 4;
+  const int hx = (dl.x + 1) / 2;  // pairs along x
+  const long long npair = (long long)dl.z * dl.y * hx;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= npair * G) return;
+  const long long pr = e / G;
+  const int c = (int)(e % G) * 4;
+  const int px = (int)(pr % hx);
+  const int r = (int)(pr / hx);
+  const int iy = r % dl.y, iz = r / dl.y;
+  const int ix0 = 2 * px;
+  auto axis = [](int i, int n, float* w) {
+    w[0] = i >= 1 ? 0.25f : 0.f;
+    w[1] = i == 0 ? 1.f : 0.75f;
+    w[2] = i == n - 1 ? 1.f : 0.75f;
+    w[3] = i <= n - 2 ? 0.25f : 0.f;
+  };
+  float wz[4], wy[4], wa[4], wb[4];
+  axis(iz, dl.z, wz);
+  axis(iy, dl.y, wy);
+  axis(ix0, dl.x, wa);
+  const bool two = ix0 + 1 < dl.x;
+  axis(ix0 + 1, dl.x, wb);
+  // output x columns 2*ix0 - 1 .. 2*ix0 + 4: the first voxel uses columns 0..3, the second 2..5
+  float wxa[6] = {wa[0], wa[1], wa[2], wa[3], 0.f, 0.f};
+  float wxb[6] = {0.f, 0.f, wb[0], wb[1], wb[2], wb[3]};
+  const float* D = dcat + (long long)b * dout.count() * Ct + c;
+  float4 A = make_float4(0.f, 0.f, 0.f, 0.f), Bv = A;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int oz = 2 * iz - 1 + a;
+    if (wz[a] == 0.f) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int oy = 2 * iy - 1 + q;
+      if (wy[q] == 0.f) continue;
+      const float wzy = wz[a] * wy[q];
+      const float* row = D + ((long long)oz * dout.y + oy) * dout.x * Ct;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const int ox = 2 * ix0 - 1 + k;
+        if (ox < 0 || ox >= dout.x) continue;
+        const float ka = wxa[k], kb = two ? wxb[k] : 0.f;
+        if (ka == 0.f && kb == 0.f) continue;
+        const float4 v = *reinterpret_cast<const float4*>(row + (long long)ox * Ct);
+        const float fa = wzy * ka, fb = wzy * kb;
+        A.x += fa * v.x;
+        A.y += fa * v.y;
+        A.z += fa * v.z;
+        A.w += fa * v.w;
+        Bv.x += fb * v.x;
+        Bv.y += fb * v.y;
+        Bv.z += fb * v.z;
+        Bv.w += fb * v.w;
+      }
+    }
+  }
+  float* O = dlow + ((long long)b * dl.count() + ((long long)iz * dl.y + iy) * dl.x + ix0) * Cu + c;
+  *reinterpret_cast<float4*>(O) = A;
+  if (two) *reinterpret_cast<float4*>(O + Cu) = Bv;
+}
+
 __global__ void split_skip_kernel(const float* __restrict__ dcat, float* __restrict__ dskip,
                                   long long nout, int Cu, int Cs) {
   const int b = blockIdx.y;
@@ -674,14 +746,37 @@ adam_kernel(float* __restrict__ theta, const float* __restrict__ g, float* __res
   __syncthreads();
   const float ibc1 = bc[0], ibc2 = bc[1];
   const float b1f = (float)b1, b2f = (float)b2, o1 = (float)(1.0 - b1), o2 = (float)(1.0 - b2);
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-       i += (long long)gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = fmaf(b1f, m[i], o1 * gi);
-    const float vi = fmaf(b2f, v[i], o2 * gi * gi);
+  auto upd = [&](float gi, float& mi, float& vi, float& th) {
+    mi = fmaf(b1f, mi, o1 * gi);
+    vi = fmaf(b2f, vi, o2 * gi * gi);
+    th -= lr * (mi * ibc1) / (sqrtf(vi * ibc2) + eps);
+  };
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool vec = (count & 3) == 0 &&
+                   ((reinterpret_cast<uintptr_t>(theta) | reinterpret_cast<uintptr_t>(g) |
+                     reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
+  if (vec) {  // four parameters per thread and step, the same arithmetic per element
+    for (long long i = i0; i < count / 4; i += stride) {
+      const float4 gi = reinterpret_cast<const float4*>(g)[i];
+      float4 mi = reinterpret_cast<float4*>(m)[i], vi = reinterpret_cast<float4*>(v)[i],
+             th = reinterpret_cast<float4*>(theta)[i];
+      upd(gi.x, mi.x, vi.x, th.x);
+      upd(gi.y, mi.y, vi.y, th.y);
+      upd(gi.z, mi.z, vi.z, th.z);
+      upd(gi.w, mi.w, vi.w, th.w);
+      reinterpret_cast<float4*>(m)[i] = mi;
+      reinterpret_cast<float4*>(v)[i] = vi;
+      reinterpret_cast<float4*>(theta)[i] = th;
+    }
+    return;
+  }
+  for (long long i = i0; i < count; i += stride) {
+    float mi = m[i], vi = v[i], th = theta[i];
+    upd(g[i], mi, vi, th);
     m[i] = mi;
     v[i] = vi;
-    theta[i] -= lr * (mi * ibc1) / (sqrtf(vi * ibc2) + eps);
+    theta[i] = th;
   }
 }
 
@@ -775,8 +870,14 @@ cudaError_t upsample_concat_bwd_f32(const float* dcat, float* dlow, float* dskip
                                     Dims3 dlow_dims, Dims3 dout, int Cu, int Cs,
                                     cudaStream_t stream) {
   if (Cu % 4 || Cs % 4) return cudaErrorInvalidValue;
-  dim3 g1((unsigned)ceil_div(dlow_dims.count() * (Cu / 4), 256), B);
-  up_bwd_kernel<<<g1, 256, 0, stream>>>(dcat, dlow, dlow_dims, dout, Cu, Cs);
+  if (dout.x == 2 * dlow_dims.x && dout.y == 2 * dlow_dims.y && dout.z == 2 * dlow_dims.z) {
+    const long long pairs = (long long)dlow_dims.z * dlow_dims.y * ((dlow_dims.x + 1) / 2);
+    dim3 g2((unsigned)ceil_div(pairs * (Cu / 4), 256), B);
+    up2_bwd_kernel<<<g2, 256, 0, stream>>>(dcat, dlow, dlow_dims, dout, Cu, Cs);
+  } else {
+    dim3 g1((unsigned)ceil_div(dlow_dims.count() * (Cu / 4), 256), B);
+    up_bwd_kernel<<<g1, 256, 0, stream>>>(dcat, dlow, dlow_dims, dout, Cu, Cs);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !dskip || Cs == 0) return e;
   dim3 g2((unsigned)ceil_div(dout.count() * Cs, 256), B);

@@ -652,10 +652,11 @@ struct Launcher {
     }
     fin();
   }
-  // dout: gradient of R.out; writes dx (gradient of R.x)
+  // dout: gradient of R.out; writes dx (gradient of R.x).  Without a projection the residual
+  // gradient dt goes straight into dx and conv a's data gradient adds onto it.
   void res_bwd(Res& R, const float* dout, float* dx) {
     LevelBufs& T = c->lb[R.lvl];
-    ln_bwd(R.lnb, R.lvl, dout, R.out, R.xh_b, R.rs_b, T.tz, T.tt, &R.b,
+    ln_bwd(R.lnb, R.lvl, dout, R.out, R.xh_b, R.rs_b, T.tz, R.proj ? T.tt : dx, &R.b,
            R.fuse_d || R.fuse_w ? &R : nullptr);
     conv_dgrad(R.b, T.tz, T.th, 0);
     conv_wgrad(R.b, R.h1, T.tz);
@@ -668,7 +669,7 @@ struct Launcher {
       pbf_owner = &R;
       fin();
     } else {
-      conv_dgrad(R.a, T.tz, dx, 0);
+      conv_dgrad(R.a, T.tz, dx, R.proj ? 0 : 1);
     }
     if (R.fuse_w) {  // weight gradients of conv a and the projection in one launch
       const long long rows = wgrad_rows(c, R.a);
@@ -687,11 +688,6 @@ struct Launcher {
     if (R.proj) {
       if (!R.fuse_d) conv_dgrad(R.p, T.tt, dx, 1);
       if (!R.fuse_w) conv_wgrad(R.p, R.x, T.tt);
-    } else {
-      const long long cnt = c->B * c->dims[R.lvl].count() * R.lna.c;
-      beg(D2IP_KCLASS_MISC, 12.0 * cnt);
-      ok(add_inplace_f32(dx, T.tt, cnt, c->stream));
-      fin();
     }
   }
   void unit_bwd(Unit& u, const float* da, float* dx, int acc, bool dgrad) {

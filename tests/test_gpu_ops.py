@@ -111,7 +111,8 @@ def test_layernorm_act_forward_backward(d2ip, nvox, c, resid):
                                            ((3, 2, 4), (5, 4, 7), 8, 4),
                                            ((1, 2, 3), (2, 3, 5), 4, 0),
                                            ((16, 32, 32), (32, 64, 64), 32, 16),
-                                           ((1, 3, 5), (2, 6, 10), 8, 8)])
+                                           ((1, 3, 5), (2, 6, 10), 8, 8),
+                                           ((3, 5, 7), (6, 10, 14), 12, 0)])
 def test_upsample_concat(d2ip, low, out, cu, cs):
     rng = np.random.default_rng(sum(low))
     B = 2
