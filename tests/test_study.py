@@ -1,6 +1,7 @@
 """Host logic of the convergence ablation: running minimum, iterations to a target, plateau
 detection and the summary over synthetic curves with known answers."""
 import numpy as np
+import pytest
 
 from paper_2507_14046_gb300 import study
 
@@ -48,3 +49,18 @@ def test_summarise_orders_arms_by_decay_rate():
         a["dip"]["loss_plateau_iter"]
     assert a["dip"]["loss_at"][50] == res["loss"]["dip"][49]
     assert a["dip"]["err_at"][100] == res["err"]["dip"][9]
+
+
+@pytest.mark.gpu
+def test_acceleration_ordering_on_the_sequence(d2ip):
+    """On frame 2 of the 20-frame 32x32x16 sequence (the paper's schedule: 1800 UPWS
+    iterations, 450 on frame 1), the full method starts lowest, UPWS alone next and the
+    Kaiming start last, in data loss and in ERR (the ordering of the paper's ablation)."""
+    from paper_2507_14046_gb300 import synth
+    res = study.run(synth.SEQ_32, iters=200, every=50)
+    L, E = res["loss"], res["err"]
+    for k in (50, 100, 200):
+        assert L["d2ip"][k - 1] < L["upws"][k - 1] < L["dip"][k - 1], k
+    assert E["d2ip"][-1] < E["upws"][-1] < E["dip"][-1]
+    # the regulariser is small at lambda_tv = 0.002: its fit stays close to plain DIP
+    assert abs(L["dip_reg"][-1] - L["dip"][-1]) < 0.05 * L["dip"][-1]
