@@ -460,33 +460,45 @@ def run_batched(args, rank, world, local_rank):
     }
 
 
-def _source_digest():
+def _source_digest(files=None):
+    """sha1 over the named CUDA sources (default: every .cu/.cuh of the library)."""
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2507_14046_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(f.encode() + fh.read())
+    names = sorted(files) if files else sorted(f for f in os.listdir(csrc)
+                                               if f.endswith((".cu", ".cuh")))
+    for f in names:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
     return h.hexdigest()
 
 
-TRAFFIC_FILES = {("batch64", "resunet", "bf16"): "roofline_traffic_batch64_bf16.txt",
-                 ("seq32", "fastres", "fp32"): "roofline_traffic_seq32_fastres_fp32.txt"}
+# per (workload, network, precision): the ncu traffic summary and the sources that hold the
+# roofline class's kernels and their launch sequence (a change there voids the figure)
+TRAFFIC_FILES = {
+    ("batch64", "resunet", "bf16"): (
+        "roofline_traffic_batch64_bf16.txt",
+        ("common.cuh", "conv_bf16.cu", "conv_bf16.cuh", "conv_f32.cu", "pointwise.cu",
+         "runtime.cu")),
+    ("seq32", "fastres", "fp32"): (
+        "roofline_traffic_seq32_fastres_fp32.txt",
+        ("common.cuh", "conv_f32.cu", "fastres.cu", "fastres.cuh", "fastres_ops.cu")),
+}
 
 
 def _traffic(cls, args):
     """DRAM bytes per launch of the class from the committed ncu summary, when it was taken on
     the kernels as they are now (same CUDA sources) and on this workload; else None."""
-    name = TRAFFIC_FILES.get((args.workload, args.net, args.precision))
-    if name is None:
+    entry = TRAFFIC_FILES.get((args.workload, args.net, args.precision))
+    if entry is None:
         return None
+    name, sources = entry
     path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as fh:
             t = json.load(fh)
     except (OSError, ValueError):
         return None
-    if t.get("source_sha1") != _source_digest():
+    if t.get("source_sha1") != _source_digest(sources):
         return None
     v = t.get("bytes_per_launch", {}).get(cls)
     return float(v) if v is not None else None
