@@ -101,7 +101,9 @@ def test_layernorm_act_function(d2ip, c, resid, act):
             assert rel(T.grad[b].cpu().numpy(), dpre) < 1e-5
     f = lambda a, gg: AG.layernorm_act(a, gg, T.detach() if resid else None, act) * _dev(w)  # noqa
     d = torch.randn_like(Z)
-    fd = _fd(f, (Z.detach(), G.detach()), 0, d, 1e-2)
+    # step 2e-3: LeakyReLU kinks crossed by the step bias the difference by O(h); FP32
+    # rounding of the sum grows as 1/h
+    fd = _fd(f, (Z.detach(), G.detach()), 0, d, 2e-3)
     assert abs(fd - (Z.grad.double() * d.double()).sum().item()) <= 2e-2 * max(1.0, abs(fd))
 
 
