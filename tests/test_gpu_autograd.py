@@ -4,8 +4,9 @@ and against the FP64 oracle's gradient; and a stem block (conv -> LayerNorm -> L
 composed by autograd against the oracle's backward of the same block.
 
 Finite differences: the convolution, the up-sampling and the J product are linear in each
-argument, so a central difference with a unit step is exact up to rounding; LayerNorm is
-checked with a small step in FP32 at a correspondingly looser bar.
+argument, so a central difference with a unit step is exact up to rounding; LayerNorm
+without the activation is smooth and is checked with a small step in FP32 at a looser bar
+(with LeakyReLU the comparison with the oracle's backward stands alone).
 """
 import numpy as np
 import pytest
@@ -99,12 +100,13 @@ def test_layernorm_act_function(d2ip, c, resid, act):
         assert rel(G.grad[b, c:].cpu().numpy(), dbeta) < 1e-5
         if resid:
             assert rel(T.grad[b].cpu().numpy(), dpre) < 1e-5
+    if act:  # a finite difference across LeakyReLU kinks measures the step, not the gradient
+        return
     f = lambda a, gg: AG.layernorm_act(a, gg, T.detach() if resid else None, act) * _dev(w)  # noqa
-    d = torch.randn_like(Z)
-    # step 2e-3: LeakyReLU kinks crossed by the step bias the difference by O(h); FP32
-    # rounding of the sum grows as 1/h
-    fd = _fd(f, (Z.detach(), G.detach()), 0, d, 2e-3)
-    assert abs(fd - (Z.grad.double() * d.double()).sum().item()) <= 2e-2 * max(1.0, abs(fd))
+    for i, g in ((0, Z.grad), (1, G.grad)):
+        d = torch.randn_like(g)
+        fd = _fd(f, (Z.detach(), G.detach()), i, d, 1e-2)
+        assert abs(fd - (g.double() * d.double()).sum().item()) <= 2e-2 * max(1.0, abs(fd))
 
 
 @pytest.mark.parametrize("low,out,cu,cs", [((3, 4, 5), (6, 8, 10), 8, 4), ((3, 2, 4), (5, 4, 7), 4, 0)])
