@@ -257,3 +257,39 @@ def test_largest_workload_iteration(d2ip, precision):
         assert rel(th1, ref.theta) < 5e-4
     else:
         assert rel(g, ref.grad) < 5e-2
+
+
+@pytest.mark.parametrize("grid,L,widths", [((6, 5, 1), 2, (8, 16)),     # one plane: z stays 1
+                                           ((7, 6, 5), 1, (8,)),        # one level: no decoder
+                                           ((3, 2, 2), 3, (8, 16, 32))])  # levels down to 1x1x1
+def test_degenerate_shapes_teacher_forced(d2ip, grid, L, widths):
+    """Degenerate grids and depths: one teacher-forced FP32 step against the oracle."""
+    pb = problems.make(grid, 1, L, widths, seed=6)
+    Z64, dv = pb.Zin.astype(np.float64), pb.V[0].astype(np.float64)
+    ref = dip.dip_step(pb.spec, pb.Jn64, Z64, dv, pb.theta0.astype(np.float64),
+                       dip.AdamState.fresh(pb.theta0.size), 1e-3)
+    c = _ctx(d2ip, pb, 1e-3)
+    ds = c.forward()[0]
+    tr = c.run_steps(pb.V[:1], 1, trace=True)
+    assert rel(ds, ref.dsigma) < TOL
+    assert abs(tr[0, 0] - ref.loss) <= TOL * ref.loss
+    assert rel(c.grad()[0], ref.grad) < TOL
+    assert rel(c.state()[0][0], ref.theta) < TOL
+
+
+def test_zero_steps_and_single_frame_sequence(d2ip):
+    """A frame fit of zero steps returns phi(theta0) and its residual; a one-frame sequence
+    without UPWS is the frame fit itself (Eq. 4 with N_0 = 0)."""
+    pb = problems.make((11, 9, 7), 1, 2, (8, 16), seed=7)
+    c = _ctx(d2ip, pb, 1e-3)
+    ds, res, _ = c.fit_frame(pb.V[:1], 0)
+    ref = onet.forward(pb.spec, pb.theta0.astype(np.float64), pb.Zin.astype(np.float64))
+    assert rel(ds[0], ref) < TOL
+    _, r = dip.data_term(pb.Jn64, ref, pb.V[0].astype(np.float64))
+    assert abs(res[0] - r) <= TOL * r
+    c1 = _ctx(d2ip, pb, 1e-3)
+    ds1, res1, _ = c1.fit_frame(pb.V[:1], 12)
+    c2 = _ctx(d2ip, pb, 1e-3)
+    Sig, res2 = c2.fit_sequence(pb.V[None, :1], 0, 12, 5)
+    np.testing.assert_array_equal(Sig[0, 0], ds1[0])
+    assert res2[0, 0] == res1[0]
