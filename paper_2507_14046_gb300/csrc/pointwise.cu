@@ -1,5 +1,7 @@
 // LayerNorm(+residual)(+LeakyReLU) forward/backward, trilinear up + concat and its adjoint,
 // the data term (J x - dv, J^T r, FP64 loss), FP64 column normalisation of J, ERR, Adam.
+#include <cmath>
+
 #include "common.cuh"
 
 namespace d2ip {
@@ -733,19 +735,14 @@ __global__ void err_kernel(const float* __restrict__ est, const float* __restric
 
 __global__ void __launch_bounds__(256)
 adam_kernel(float* __restrict__ theta, const float* __restrict__ g, float* __restrict__ m,
-            float* __restrict__ v, long long count, float lr, double b1, double b2, float eps,
-            const int* __restrict__ t_dev, int t_host) {
-  // beta and (1 - beta) are rounded to float from double so that (1 - 0.999) keeps full
-  // float precision; the bias corrections 1 - beta^t are formed in double.
-  __shared__ float bc[2];
-  if (threadIdx.x == 0) {
-    const int t = t_dev ? *t_dev : t_host;
-    bc[0] = (float)(1.0 / (1.0 - pow(b1, (double)t)));
-    bc[1] = (float)(1.0 / (1.0 - pow(b2, (double)t)));
-  }
-  __syncthreads();
-  const float ibc1 = bc[0], ibc2 = bc[1];
-  const float b1f = (float)b1, b2f = (float)b2, o1 = (float)(1.0 - b1), o2 = (float)(1.0 - b2);
+            float* __restrict__ v, long long count, float lr, float b1f, float b2f, float o1,
+            float o2, float lnb1, float lnb2, float eps, const int* __restrict__ t_dev,
+            int t_host) {
+  // beta and (1 - beta) come rounded to float from double, so (1 - 0.999) keeps full float
+  // precision.  The bias corrections 1 - beta^t = -expm1(t ln beta), with ln beta formed in
+  // double on the host: about 2e-7 relative error, with no FP64 work on the device.
+  const float tf = (float)(t_dev ? *t_dev : t_host);
+  const float ibc1 = -1.f / expm1f(tf * lnb1), ibc2 = -1.f / expm1f(tf * lnb2);
   auto upd = [&](float gi, float& mi, float& vi, float& th) {
     mi = fmaf(b1f, mi, o1 * gi);
     vi = fmaf(b2f, vi, o2 * gi * gi);
@@ -984,9 +981,10 @@ constexpr int kJtRows = 128, kJtChunk = 64;
 __global__ void __launch_bounds__(kJtRows)
 jtmul_t_kernel(const __nv_bfloat16* __restrict__ Jt, const float* __restrict__ r,
                float* __restrict__ g, float scale, int B, int m, int n, long long g_bs) {
-  extern __shared__ float rs[];  // [kTB][m], then the Jt tile
-  __nv_bfloat16* jt = reinterpret_cast<__nv_bfloat16*>(rs + kTB * m);  // [kJtRows][kJtChunk + 8]
+  extern __shared__ float rs[];  // [kTB][m], then two Jt tiles
   constexpr int kLd = kJtChunk + 8;  // padded row (bf16): 144 bytes
+  constexpr int kPer = kJtRows * (kJtChunk / 4) / kJtRows;  // 8-byte pieces per thread
+  __nv_bfloat16* jt0 = reinterpret_cast<__nv_bfloat16*>(rs + kTB * m);  // [2][kJtRows][kLd]
   const int b0 = blockIdx.y * kTB;
   const int nb = B - b0 < kTB ? B - b0 : kTB;
   for (int e = threadIdx.x; e < kTB * m; e += blockDim.x)
@@ -996,18 +994,36 @@ jtmul_t_kernel(const __nv_bfloat16* __restrict__ Jt, const float* __restrict__ r
   float acc[kTB];
 #pragma unroll
   for (int q = 0; q < kTB; ++q) acc[q] = 0.f;
+  // tile of chunk i0: rows j0 .. j0 + 127, columns i0 .. i0 + 63, 8-byte pieces; the next
+  // chunk's pieces are loaded into registers while the current tile is used
+  uint2 pre[kPer];
+  auto load = [&](int i0) {
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int e = threadIdx.x + kJtRows * k;
+      const int row = e / (kJtChunk / 4), c4 = (e % (kJtChunk / 4)) * 4;
+      pre[k] = (j0 + row < n && i0 + c4 < m)
+                   ? *reinterpret_cast<const uint2*>(Jt + (j0 + row) * m + i0 + c4)
+                   : make_uint2(0u, 0u);
+    }
+  };
+  auto store = [&](__nv_bfloat16* jt) {
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int e = threadIdx.x + kJtRows * k;
+      const int row = e / (kJtChunk / 4), c4 = (e % (kJtChunk / 4)) * 4;
+      *reinterpret_cast<uint2*>(jt + row * kLd + c4) = pre[k];
+    }
+  };
+  load(0);
+  store(jt0);
+  int buf = 0;
   for (int i0 = 0; i0 < m; i0 += kJtChunk) {
     const int ni = m - i0 < kJtChunk ? m - i0 : kJtChunk;  // a multiple of 4
-    __syncthreads();
-    // tile: rows j0 .. j0 + 127, columns i0 .. i0 + ni - 1, 8-byte pieces
-    for (int e = threadIdx.x; e < kJtRows * (kJtChunk / 4); e += blockDim.x) {
-      const int row = e / (kJtChunk / 4), c4 = (e % (kJtChunk / 4)) * 4;
-      uint2 v = make_uint2(0u, 0u);
-      if (j0 + row < n && c4 < ni)
-        v = *reinterpret_cast<const uint2*>(Jt + (j0 + row) * m + i0 + c4);
-      *reinterpret_cast<uint2*>(jt + row * kLd + c4) = v;
-    }
-    __syncthreads();
+    __syncthreads();  // tile `buf` complete; the other one no longer read
+    const bool more = i0 + kJtChunk < m;
+    if (more) load(i0 + kJtChunk);
+    const __nv_bfloat16* jt = jt0 + buf * (kJtRows * kLd);
     for (int c = 0; c < ni; c += 4) {
       const uint2 u = *reinterpret_cast<const uint2*>(jt + threadIdx.x * kLd + c);
       const float2 a01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
@@ -1018,6 +1034,8 @@ jtmul_t_kernel(const __nv_bfloat16* __restrict__ Jt, const float* __restrict__ r
         acc[q] = fmaf(a01.x, rv.x, fmaf(a01.y, rv.y, fmaf(a23.x, rv.z, fmaf(a23.y, rv.w, acc[q]))));
       }
     }
+    if (more) store(jt0 + (buf ^ 1) * (kJtRows * kLd));
+    buf ^= 1;
   }
   if (j < n) {
 #pragma unroll
@@ -1076,7 +1094,7 @@ cudaError_t jtmul_f32(const float* J, const float* r, float* g, float scale, int
 
 cudaError_t jtmul_bf16(const __nv_bfloat16* Jt, const float* r, float* g, float scale, int B,
                        int m, int n, long long g_bs, cudaStream_t stream) {
-  const size_t smem = (size_t)kTB * m * sizeof(float) + (size_t)kJtRows * (kJtChunk + 8) * 2;
+  const size_t smem = (size_t)kTB * m * sizeof(float) + 2 * (size_t)kJtRows * (kJtChunk + 8) * 2;
   if (m % 4 || smem > (size_t)kJtmulMaxSmem) return cudaErrorInvalidValue;
   dim3 grid((unsigned)ceil_div(n, kJtRows), (unsigned)ceil_div(B, kTB));
   jtmul_t_kernel<<<grid, kJtRows, smem, stream>>>(Jt, r, g, scale, B, m, n, g_bs);
@@ -1132,11 +1150,13 @@ cudaError_t err_ratio_f64(const float* est, const float* truth, double* out, int
 cudaError_t adam_step_f32(float* theta, const float* g, float* m, float* v, long long count,
                           double lr, double beta1, double beta2, double eps, const int* t_dev,
                           int t_host, cudaStream_t stream) {
-  // capped grid: every block forms the FP64 bias corrections once (FP64 is slow here)
-  long long blocks = ceil_div(count, 256);
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  adam_kernel<<<(unsigned)blocks, 256, 0, stream>>>(theta, g, m, v, count, (float)lr, beta1,
-                                                    beta2, (float)eps, t_dev, t_host);
+  // four parameters per thread when aligned; a grid-stride loop past 16 blocks per SM
+  long long blocks = ceil_div(ceil_div(count, 4), 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  adam_kernel<<<(unsigned)blocks, 256, 0, stream>>>(
+      theta, g, m, v, count, (float)lr, (float)beta1, (float)beta2, (float)(1.0 - beta1),
+      (float)(1.0 - beta2), (float)std::log(beta1), (float)std::log(beta2), (float)eps, t_dev,
+      t_host);
   return cudaGetLastError();
 }
 
