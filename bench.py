@@ -187,6 +187,13 @@ def _err(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
+def _clocks_path(args, rank):
+    """Where the nvidia-smi samples of the timed region go (--clocks-dir, else the temp dir)."""
+    d = args.clocks_dir or os.environ.get("TMPDIR", "/tmp")
+    os.makedirs(d, exist_ok=True)
+    return os.path.join(d, f"d2ip_clocks_r{rank}.csv")
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
 
@@ -225,9 +232,7 @@ def run_gpu(args, rank, world, local_rank):
             flush.zero_()
     torch.cuda.synchronize()
     replicas.barrier()
-    clocks = ClockSampler(local_rank, os.path.join(ROOT, "gpurun_out", f"clocks_r{rank}.csv")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                          else f"/tmp/d2ip_clocks_r{rank}.csv")
+    clocks = ClockSampler(local_rank, _clocks_path(args, rank))
     total_ms = 0.0
     for _ in range(args.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -343,9 +348,7 @@ def run_batched(args, rank, world, local_rank):
         flush.zero_()
     torch.cuda.synchronize()
     replicas.barrier()
-    clocks = ClockSampler(local_rank, os.path.join(ROOT, "gpurun_out", f"clocks_r{rank}.csv")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                          else f"/tmp/d2ip_clocks_r{rank}.csv")
+    clocks = ClockSampler(local_rank, _clocks_path(args, rank))
     total_ms = 0.0
     for _ in range(args.steps):
         starts = [torch.cuda.Event(enable_timing=True) for _ in streams]
@@ -624,6 +627,8 @@ def main():
     ap.add_argument("--study", type=int, default=0,
                     help="run the convergence ablation for this many iterations and exit")
     ap.add_argument("--study-out", default=None)
+    ap.add_argument("--clocks-dir", default=None,
+                    help="directory for the raw nvidia-smi samples of the timed region")
     ap.add_argument("--net", default="resunet", choices=["resunet", "fastres"],
                     help="network: the residual U-Net, or the paper-form FastResUNet variant "
                          "(FP32, single-sequence workloads)")
