@@ -114,6 +114,14 @@ d2ip_status d2ip_param_count(d2ip_ctx* ctx, long long* count);
 /* Parameter table: row r = {kind, offset, count, fan_in} (kind: D2IP_PARAM_*), written to
  * rows[4*r .. 4*r+3] (host memory) for r < cap; *n_rows receives the number of rows. */
 d2ip_status d2ip_param_table(d2ip_ctx* ctx, long long* rows, int cap, int* n_rows);
+/* The same table without a context or a device: the plan of network `net` (0 the residual
+ * U-Net of d2ip_set_network, 1 the FastResUNet variant of d2ip_set_network_fastres) on an
+ * X x Y x Z grid, for host code that lays out or initialises theta before any GPU call.
+ * rows as above (host memory); *count (may be NULL) receives P.  Shapes are checked as in
+ * the two set-network calls (D2IP_ERR_BAD_ARG / D2IP_ERR_BAD_SHAPE). */
+d2ip_status d2ip_plan_param_table(int net, int X, int Y, int Z, int levels, const int* widths,
+                                  int c_in, long long* rows, int cap, int* n_rows,
+                                  long long* count);
 
 /* Copy J (m x n, n = X*Y*Z) into the context.  normalize_cols != 0 scales every column to
  * unit l2 norm with the norm accumulated in FP64 (Eq. 1, "normalized" sensitivity); a zero

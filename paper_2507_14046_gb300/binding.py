@@ -41,6 +41,8 @@ _SIGS = {
     "d2ip_set_grid": [_vp, _i, _i, _i],
     "d2ip_set_network": [_vp, _i, _vp, _i, _i, _i],
     "d2ip_set_network_fastres": [_vp, _i, _vp, _i, _i, _i],
+    "d2ip_plan_param_table": [_i, _i, _i, _i, _i, _vp, _i, _vp, _i, C.POINTER(_i),
+                              C.POINTER(_ll)],
     "d2ip_param_count": [_vp, C.POINTER(_ll)],
     "d2ip_param_table": [_vp, _vp, _i, C.POINTER(_i)],
     "d2ip_load_J": [_vp, _vp, _i, _i, _i],
@@ -172,6 +174,21 @@ def d2ip_set_network_fastres(ctx, levels, widths, c_in, precision, batch):
     w = (C.c_int * levels)(*widths)
     return _call("d2ip_set_network_fastres", ctx, ctx, levels, C.cast(w, _vp), c_in, precision,
                  batch)
+
+
+def d2ip_plan_param_table(net, grid, levels, widths, c_in=8):
+    """(rows [n, 4] int64, P) of a network's parameter table, without a context or device.
+    net: "resunet" or "fastres"; grid (X, Y, Z)."""
+    code = {"resunet": 0, "fastres": 1}[net]
+    X, Y, Z = grid
+    w = (C.c_int * levels)(*widths)
+    n, P = _i(), _ll()
+    _call("d2ip_plan_param_table", None, code, X, Y, Z, levels, C.cast(w, _vp), c_in, None, 0,
+          C.byref(n), C.byref(P))
+    rows = np.zeros((n.value, 4), dtype=np.int64)
+    _call("d2ip_plan_param_table", None, code, X, Y, Z, levels, C.cast(w, _vp), c_in,
+          rows.ctypes.data, n.value, C.byref(n), C.byref(P))
+    return rows, P.value
 
 
 def d2ip_param_count(ctx) -> int:

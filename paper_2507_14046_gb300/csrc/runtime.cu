@@ -1109,6 +1109,40 @@ d2ip_status d2ip_param_table(d2ip_ctx* c, long long* rows, int cap, int* n_rows)
   return D2IP_OK;
 }
 
+d2ip_status d2ip_plan_param_table(int net, int X, int Y, int Z, int levels, const int* widths,
+                                  int c_in, long long* rows, int cap, int* n_rows,
+                                  long long* count) {
+  if (!n_rows || !widths || (net != 0 && net != 1))
+    return fail(nullptr, D2IP_ERR_BAD_ARG, "null argument or unknown network");
+  if (X <= 0 || Y <= 0 || Z <= 0 || (long long)X * Y * Z > (1LL << 30))
+    return fail(nullptr, D2IP_ERR_BAD_SHAPE, "grid dimensions must be positive");
+  if (net == 0) {
+    if (levels < 1 || levels > 8 || c_in <= 0 || c_in > 256)
+      return fail(nullptr, D2IP_ERR_BAD_ARG, "levels must be 1..8 and c_in 1..256");
+    for (int l = 0; l < levels; ++l)
+      if (widths[l] <= 0 || widths[l] % 4 != 0 || widths[l] > 128)
+        return fail(nullptr, D2IP_ERR_BAD_SHAPE,
+                    "each width must be a positive multiple of 4, <= 128");
+  } else if (levels < 1 || levels > 6 || !fastres_supported(levels, widths, c_in)) {
+    return fail(nullptr, D2IP_ERR_BAD_SHAPE,
+                "levels 1..6, each width a multiple of 8 in 8..128, c_in 1..256");
+  }
+  d2ip_ctx t;  // host-side plan only: nothing here touches a device
+  t.X = X, t.Y = Y, t.Z = Z;
+  t.L = levels;
+  t.w.assign(widths, widths + levels);
+  t.c_in = c_in;
+  t.precision = D2IP_FP32;
+  t.arch = net;
+  build_plan(&t);
+  const int n = (int)(t.table.size() / 4);
+  *n_rows = n;
+  if (rows)
+    for (int i = 0; i < std::min(n, cap) * 4; ++i) rows[i] = t.table[i];
+  if (count) *count = t.P;
+  return D2IP_OK;
+}
+
 d2ip_status d2ip_load_J(d2ip_ctx* c, const float* J, int m, int n, int normalize_cols) {
   if (!c || !J) return fail(c, D2IP_ERR_BAD_ARG, "null argument");
   if (!c->net_ready) return fail(c, D2IP_ERR_STATE, "set grid and network first");
