@@ -364,6 +364,15 @@ d2ip_status d2ip_adam_update(float* theta, const float* g, float* m, float* v,
                              long long count, double lr, double beta1, double beta2,
                              double eps, int t, void* stream);
 
+/* Self-test of the bounded-wait error path on `device`: a one-thread kernel waits on a
+ * device flag for at most spin_limit polls (1..2^26, about 64 ns apart), as the tensor-core
+ * kernels wait on their pipeline barriers.  set_flag = 0 leaves the flag unset, so the wait
+ * runs out; the kernel then writes code 2 to its status word instead of hanging or trapping,
+ * and the call returns D2IP_ERR_TIMEOUT.  set_flag = 1 sets the flag first and the call
+ * returns D2IP_OK.  *status_out receives the status word (0 or 2).  Synchronous; leaves
+ * the device usable. */
+d2ip_status d2ip_wait_selftest(int device, long long spin_limit, int set_flag, int* status_out);
+
 #ifdef __cplusplus
 }
 #endif

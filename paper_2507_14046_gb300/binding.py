@@ -41,6 +41,7 @@ _SIGS = {
     "d2ip_set_grid": [_vp, _i, _i, _i],
     "d2ip_set_network": [_vp, _i, _vp, _i, _i, _i],
     "d2ip_set_network_fastres": [_vp, _i, _vp, _i, _i, _i],
+    "d2ip_wait_selftest": [_i, _ll, _i, C.POINTER(_i)],
     "d2ip_plan_param_table": [_i, _i, _i, _i, _i, _vp, _i, _vp, _i, C.POINTER(_i),
                               C.POINTER(_ll)],
     "d2ip_param_count": [_vp, C.POINTER(_ll)],
@@ -189,6 +190,14 @@ def d2ip_plan_param_table(net, grid, levels, widths, c_in=8):
     _call("d2ip_plan_param_table", None, code, X, Y, Z, levels, C.cast(w, _vp), c_in,
           rows.ctypes.data, n.value, C.byref(n), C.byref(P))
     return rows, P.value
+
+
+def d2ip_wait_selftest(device=0, spin_limit=20000, set_flag=0):
+    """Runs the bounded-wait self-test; returns the status word (raises D2IPError with
+    D2IP_ERR_TIMEOUT when the wait ran out, as it does with set_flag=0)."""
+    st = _i(-1)
+    _call("d2ip_wait_selftest", None, device, spin_limit, set_flag, C.byref(st))
+    return st.value
 
 
 def d2ip_param_count(ctx) -> int:

@@ -293,3 +293,18 @@ def test_zero_steps_and_single_frame_sequence(d2ip):
     Sig, res2 = c2.fit_sequence(pb.V[None, :1], 0, 12, 5)
     np.testing.assert_array_equal(Sig[0, 0], ds1[0])
     assert res2[0, 0] == res1[0]
+
+
+def test_bounded_wait_reports_timeout_and_device_stays_usable(d2ip):
+    """Failure detection without a fault: a device wait on a flag that nothing sets runs out
+    of its iteration limit, the kernel records the failure in its status word and the call
+    returns D2IP_ERR_TIMEOUT; the same wait with the flag set succeeds, and a fit runs
+    normally afterwards."""
+    with pytest.raises(d2ip.D2IPError) as e:
+        d2ip.d2ip_wait_selftest(0, 20000, 0)
+    assert d2ip.STATUS[e.value.status] == "TIMEOUT"
+    assert d2ip.d2ip_wait_selftest(0, 20000, 1) == 0
+    pb = problems.make((16, 16, 8), 1, 2, (8, 16), seed=1)
+    c = _ctx(d2ip, pb, 1e-3)
+    tr = c.run_steps(pb.V[:1], 2, trace=True)
+    assert np.all(np.isfinite(tr))
