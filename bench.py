@@ -110,8 +110,9 @@ def oracle_leg(workload: str, iters: int, net: str = "resunet") -> dict:
     return {"iters": iters, "seconds": spi * iters, "iters_per_s": 1.0 / spi}
 
 
-def run_oracle_subprocess(workload: str, iters: int, net: str = "resunet") -> dict:
-    cores = os.cpu_count() or 1
+def run_oracle_subprocess(workload: str, iters: int, net: str = "resunet",
+                          threads: int | None = None) -> dict:
+    cores = threads or os.cpu_count() or 1
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(cores)
@@ -721,6 +722,11 @@ def main():
                "sample": f"{r['iters']} FP64 oracle DIP iterations (first frame of the same "
                          f"workload{', every grid of the mix, weighted by its sequences' if args.workload == 'batch64' else ''}"
                          f") in {r['seconds']:.1f} s, NumPy/BLAS on {r['cores']} host threads"}
+        r1 = run_oracle_subprocess(args.workload, max(1, oracle_iters_for(args.workload) // 4),
+                                   args.net, threads=1)
+        cpu["single_core"] = {"value": r1["iters_per_s"], "unit": UNIT, "cores": 1,
+                              "sample": f"{r1['iters']} iterations in {r1['seconds']:.1f} s, "
+                                        "one host thread"}
     line = {"metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
