@@ -224,3 +224,24 @@ def test_dip_step_uses_the_variant():
     np.testing.assert_array_equal(res.dsigma, ds)
     r = Jn @ ds - dv
     assert res.loss == pytest.approx(r @ r / 16, rel=1e-14)
+
+
+@pytest.mark.parametrize("grid,L,widths", [((4, 3, 5), 1, (8,)), ((6, 5, 4), 3, (8, 16, 16))])
+def test_gradient_matches_finite_differences_other_depths(grid, L, widths):
+    """One stage (the bottleneck one level below the stem's) and three stages (levels down to
+    one voxel): the gradient is the derivative of the forward at these depths too."""
+    spec = fr.FastSpec(grid, L, widths, 2)
+    th = _theta(spec, 4)
+    n = grid[0] * grid[1] * grid[2]
+    Z = R.normal(size=(n, 2))
+    w = R.normal(size=n)
+    out, kept = fr.forward(spec, th, Z, keep=True)
+    assert out.shape == (n,) and np.all((out > 0) & (out < 1))
+    g = fr.backward(spec, kept, w)
+    d = R.normal(size=th.size)
+    h = 1e-7
+    fd = (w @ fr.forward(spec, th + h * d, Z) - w @ fr.forward(spec, th - h * d, Z)) / (2 * h)
+    assert abs(fd - g @ d) <= 1e-6 * max(1.0, abs(fd))
+    names = [e[0] for e in fr.param_layout(spec)]
+    assert sum(nm.endswith(".a.dw.W") for nm in names) == 2 * L   # L encoder + L decoder blocks
+    assert sum(nm.endswith(".psi.W") for nm in names) == L
