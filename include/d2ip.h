@@ -50,6 +50,12 @@ typedef int d2ip_status;
 #define D2IP_FP32 0 /* convolutions and J products in FP32 (SIMT), FP32 accumulation      */
 #define D2IP_BF16 1 /* convolutions on tcgen05 tensor cores and J products from a BF16 copy
                        of J, FP32 accumulation; J column norms and the residual stay FP64    */
+#define D2IP_BF16X3 2 /* split BF16: convolutions on tcgen05 tensor cores with every operand
+                       v carried as two BF16 numbers hi = bf16(v), lo = bf16(v - hi) (16
+                       significant bits); each product sums hi*hi + lo*hi + hi*lo in FP32
+                       (three times the MMAs of D2IP_BF16).  J products in FP32 from the FP32
+                       J.  Plain BF16 operands (8 bits) and TF32 (11) both carry the Adam
+                       trajectory of a 100-step fit away from the FP64 one; 16 bits follow it */
 
 /* parameter-table kinds */
 #define D2IP_PARAM_CONV_W 0
@@ -74,7 +80,8 @@ d2ip_status d2ip_destroy(d2ip_ctx* ctx);
 d2ip_status d2ip_set_grid(d2ip_ctx* ctx, int X, int Y, int Z);
 
 /* Residual 3D U-Net of `levels` levels with channel widths[levels] (each a multiple of 4,
- * at most 128), `c_in` input channels of Z, `precision` D2IP_FP32 or D2IP_BF16, and `batch`
+ * at most 128; multiples of 16 for the BF16 precisions), `c_in` input channels of Z,
+ * `precision` D2IP_FP32, D2IP_BF16 or D2IP_BF16X3, and `batch`
  * independent problems (each with its own theta, Adam state, Z and measurements; all share
  * the grid and J).  Layout: stem act(LN(conv3(c_in->w0))); per level a ResBlock, preceded
  * for l > 0 by act(LN(conv3 stride 2)); decoder Up(trilinear) + concat(skip) + ResBlock with

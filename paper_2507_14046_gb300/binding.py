@@ -15,7 +15,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libd2ip.so")
 
-D2IP_FP32, D2IP_BF16 = 0, 1
+D2IP_FP32, D2IP_BF16, D2IP_BF16X3 = 0, 1, 2
 KCLASSES = ("conv_fwd", "conv_dgrad", "conv_wgrad", "ln_fwd", "ln_bwd", "up_fwd", "up_bwd",
             "jmul", "loss", "jtmul", "adam", "misc")
 STATUS = {0: "OK", -1: "BAD_ARG", -2: "BAD_SHAPE", -3: "OOM", -4: "NONFINITE", -5: "TIMEOUT",

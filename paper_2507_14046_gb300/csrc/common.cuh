@@ -22,6 +22,30 @@ __host__ __device__ inline Dims3 conv_out_dims(Dims3 in, int K, int S) {
 
 inline long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
 
+// Store four consecutive channels c..c+3 (c % 4 == 0) of one voxel into its BF16 staging
+// row (`row` = the voxel's first staged element, C channels per block).  sp 1: bf16(v).
+// sp 3: the split form of the BF16x3 precision, three C-channel blocks [hi | lo | hi] with
+// hi = bf16(v) and lo = bf16(v - hi) (v - hi is exact in FP32), so hi + lo holds 16
+// significant bits; a convolution whose weights are staged [hi | hi | lo] over the same
+// channel blocks then sums x_hi w_hi + x_lo w_hi + x_hi w_lo in one K loop.
+__device__ __forceinline__ void stage_bf16x4(__nv_bfloat16* row, int C, int c, float4 v,
+                                             int sp) {
+  const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+  uint2 hu;
+  hu.x = *reinterpret_cast<const uint32_t*>(&h01);
+  hu.y = *reinterpret_cast<const uint32_t*>(&h23);
+  *reinterpret_cast<uint2*>(row + c) = hu;
+  if (sp == 1) return;
+  const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+  const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y),
+                       l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+  uint2 lu;
+  lu.x = *reinterpret_cast<const uint32_t*>(&l01);
+  lu.y = *reinterpret_cast<const uint32_t*>(&l23);
+  *reinterpret_cast<uint2*>(row + C + c) = lu;
+  *reinterpret_cast<uint2*>(row + 2 * C + c) = hu;
+}
+
 constexpr float kLeakySlope = 0.2f;
 constexpr float kLnEps = 1e-5f;
 
@@ -52,22 +76,26 @@ cudaError_t reduce_rows_f32(const float* part, float* out, int B, long long R, l
 
 // LayerNorm over channels (+ residual) (+ LeakyReLU).
 int layernorm_bwd_blocks(long long nvox, int C);
-// ybf (optional): a BF16 copy of y (the next tensor-core convolution's staged input).
+// ybf (optional): a BF16 copy of y (the next tensor-core convolution's staged input), in sp
+// blocks per voxel (stage_bf16x4).
 cudaError_t layernorm_act_fwd_f32(const float* z, const float* gamma, const float* resid,
                                   float* y, float* xhat, float* rstd, int B, long long nvox,
                                   int C, int act, long long g_bs, cudaStream_t stream,
-                                  __nv_bfloat16* ybf = nullptr);
-// part: [B][blocks][2C] partial (dgamma, dbeta); dzbf, dtbf (optional): BF16 copies of dz, dt.
+                                  __nv_bfloat16* ybf = nullptr, int sp = 1);
+// part: [B][blocks][2C] partial (dgamma, dbeta); dzbf, dtbf (optional): BF16 copies of dz, dt
+// in sp blocks per voxel.
 cudaError_t layernorm_act_bwd_f32(const float* dy, const float* act_out, const float* xhat,
                                   const float* rstd, const float* gamma, float* dz, float* dt,
                                   float* part, int B, long long nvox, int C, long long g_bs,
                                   cudaStream_t stream, __nv_bfloat16* dzbf = nullptr,
-                                  __nv_bfloat16* dtbf = nullptr);
+                                  __nv_bfloat16* dtbf = nullptr, int sp = 1);
 
-// cat[:, :Cu] = trilinear(low -> dout), cat[:, Cu:] = skip; catbf (optional): a BF16 copy.
+// cat[:, :Cu] = trilinear(low -> dout), cat[:, Cu:] = skip; catbf (optional): a BF16 copy in
+// sp blocks per voxel.
 cudaError_t upsample_concat_fwd_f32(const float* low, const float* skip, float* cat, int B,
                                     Dims3 dlow, Dims3 dout, int Cu, int Cs,
-                                    cudaStream_t stream, __nv_bfloat16* catbf = nullptr);
+                                    cudaStream_t stream, __nv_bfloat16* catbf = nullptr,
+                                    int sp = 1);
 // dlow = adjoint of the upsample applied to dcat[:, :Cu]; dskip = dcat[:, Cu:].
 cudaError_t upsample_concat_bwd_f32(const float* dcat, float* dlow, float* dskip, int B,
                                     Dims3 dlow_dims, Dims3 dout, int Cu, int Cs,

@@ -162,6 +162,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 
 constexpr int kErrProducer = 1, kErrMma = 2, kErrEpilogue = 4;
 
+// After the producer's last issue, or an early stop: wait (bounded) for the last load issued
+// into each of the nst ring stages, k loads in all, so that no TMA write into this CTA's
+// shared memory is still in flight when the CTA may exit.
+__device__ __forceinline__ void drain_loads(const uint64_t* full_bar, int nst, int k, int* err) {
+  for (int q = 0; q < nst && q < k; ++q) {
+    const int last = k - 1 - ((k - 1 - q) % nst + nst) % nst;  // last k' < k with k' % nst == q
+    if (!mbar_wait(smem_u32(&full_bar[q]), (last / nst) & 1)) atomicOr(err, kErrProducer);
+  }
+}
+
 // Taps of one launch: the input box of tap j starts at origin * s_in + off[j] (x, y, z), its
 // weights are tap widx[j] of the weight tensor, and the tile's output voxel q is written at
 // q * s_out + r.  A forward convolution is one class of 27 (or 1) taps; the stride-2 data
@@ -225,7 +235,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__
   const uint32_t tmem = tmem_base_s;
 
   if (warp == 0 && lane == 0) {  // TMA producer
-    for (int k = 0; k < ksteps; ++k) {
+    int k = 0;
+    for (; k < ksteps; ++k) {
       const int s = k % kStages, round = k / kStages;
       if (round > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (round - 1) & 1)) {
         atomicOr(err, kErrProducer);
@@ -239,6 +250,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__
                   y0 * plan.s_in + cls.off[j][1], z0 * plan.s_in + cls.off[j][2], b, fb);
       tma_load_4d(a_dst + kABytes, &tm_b, c * CK, 0, cls.widx[j], b, fb);
     }
+    drain_loads(full_bar, kStages, k, err);
   } else if (warp == 1 && lane == 0) {  // MMA issuer
     const uint32_t idesc = instr_desc(N);
     for (int k = 0; k < ksteps; ++k) {
@@ -285,8 +297,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__
     }
   }
   tc_fence_before();
-  __syncthreads();
-  if (warp == 1) {
+  // TMEM is freed only once the last commit showed every issued MMA complete; otherwise the
+  // error word is set and the columns stay allocated
+  const int drained = __syncthreads_and(ok ? 1 : 0);
+  if (warp == 1 && drained) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(tmem_cols)
@@ -359,7 +373,8 @@ conv_tc3_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant_
   const uint32_t tmem = tmem_base_s;
 
   if (warp == 0 && lane == 0) {  // TMA producer
-    for (int k = 0; k < ksteps; ++k) {
+    int k = 0;
+    for (; k < ksteps; ++k) {
       const int st = k % nst, round = k / nst;
       if (round > 0 && !mbar_wait(smem_u32(&empty_bar[st]), (round - 1) & 1)) {
         atomicOr(err, kErrProducer);
@@ -372,6 +387,7 @@ conv_tc3_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant_
       tma_load_5d(dst, &tm_a, c * CK, x0 + kx - 1, y0 - 1, z0 - 1, b, fb);
       tma_load_4d(dst + a_bytes, &tm_b, c * CK, 0, kx, b, fb);
     }
+    drain_loads(full_bar, nst, k, err);
   } else if (warp == 1 && lane == 0) {  // MMA issuer
     const uint32_t idesc = instr_desc(N);
     for (int k = 0; k < ksteps; ++k) {
@@ -449,7 +465,7 @@ conv_tc3_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant_
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 1) {
+  if (warp == 1 && okall) {  // TMEM is freed only after the last commit showed the MMAs done
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(tmem_cols)
@@ -776,14 +792,16 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
     }
   }
   __syncwarp();
-  // TMEM is freed only after every issued MMA has completed
+  // TMEM is freed only after the MMA thread's last commit showed every issued MMA complete;
+  // otherwise the error word is set and the columns stay allocated
+  bool fin = true;
   if (warp == 1) {
-    const bool fin = __all_sync(0xffffffffu, mbar_wait(smem_u32(&done_bar), 0));
+    fin = __all_sync(0xffffffffu, mbar_wait(smem_u32(&done_bar), 0));
     if (!fin && lane == 0) atomicOr(g.err, kErrEpilogue);
   }
   tc_fence_before();
-  __syncthreads();
-  if (warp == 1) {
+  const int drained = __syncthreads_and(fin ? 1 : 0);
+  if (warp == 1 && drained) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(tmem_cols)
@@ -828,8 +846,8 @@ template <int CKA, int CKB>
 __global__ void __launch_bounds__(128, 1)
 wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant__ CUtensorMap tm_x,
                 float* __restrict__ part, Dims3 d, int Co, int Ci, int K, int tg,
-                int tiles_per_chunk, int ntiles, int tiles_x, int tiles_y, int nchunks, int nst,
-                int* __restrict__ err) {
+                int tiles_per_chunk, int ntiles, int tiles_x, int tiles_y, int rows_b, int nst,
+                int bias_on, int* __restrict__ err) {
   constexpr int KT = kBM;                       // voxels per K tile (8 x 4 x 4 box)
   const int ablocks = Co / CKA;                 // A boxes per tap
   const uint32_t a_box = KT * CKA * 2;          // bytes of one A box
@@ -882,7 +900,8 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant
   const uint32_t tmem = tmem_base_s;
 
   if (warp == 0 && lane == 0) {  // TMA producer
-    for (int k = 0; k < ksteps; ++k) {
+    int k = 0;
+    for (; k < ksteps; ++k) {
       const int s = k % nst, round = k / nst;
       if (round > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (round - 1) & 1)) {
         atomicOr(err, kErrProducer);
@@ -903,6 +922,7 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant
       for (int c = 0; c < Ci / CKB; ++c)
         tma_load_5d(base + a_bytes + (uint32_t)c * b_box, &tm_x, c * CKB, x0, y0, z0, b, fb);
     }
+    drain_loads(full_bar, nst, k, err);
   } else if (warp == 1 && lane == 0) {  // MMA issuer
     const uint32_t idesc = instr_desc_mn(n_mma);
     for (int k = 0; k < ksteps; ++k) {
@@ -925,15 +945,15 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant
   }
   __syncwarp();
 
-  const bool waited = ksteps > 0 ? mbar_wait(smem_u32(&done_bar), 0) : false;
-  const bool ok = __all_sync(0xffffffffu, waited);
-  if (!ok && ksteps > 0 && lane == 0) atomicOr(err, kErrEpilogue);
+  const bool drained = __all_sync(0xffffffffu, mbar_wait(smem_u32(&done_bar), 0));
+  const bool ok = drained && ksteps > 0;
+  if (!drained && lane == 0) atomicOr(err, kErrEpilogue);
   tc_fence_after();
   const int m = warp * 32 + lane;       // TMEM lane = A row = (tap in group, co)
   const int q = m / Co, co = m % Co;
   const int t = t0 + q;
   const long long row = (long long)Co * T * Ci + Co;
-  float* prow = part + ((long long)b * nchunks + chunk) * row;
+  float* prow = part + ((long long)b * rows_b + chunk) * row;
   float* out = prow + ((long long)co * T + t) * Ci;
   for (int c0 = 0; c0 < Ci; c0 += 16) {
     uint32_t r[16];
@@ -946,11 +966,13 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant
   {  // column Ci: sum of the row's dy over the chunk; the centre tap's is the bias partial
     uint32_t r[16];
     if (ok) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)Ci, r);
-    if (q < ntap && t == centre) prow[(long long)Co * T * Ci + co] = ok ? __uint_as_float(r[0]) : 0.f;
+    if (q < ntap && t == centre)
+      prow[(long long)Co * T * Ci + co] = ok && bias_on ? __uint_as_float(r[0]) : 0.f;
   }
   tc_fence_before();
-  __syncthreads();
-  if (warp == 1) {
+  // TMEM is freed only once the last commit showed every issued MMA complete
+  const int all_drained = __syncthreads_and(drained ? 1 : 0);
+  if (warp == 1 && all_drained) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(tmem_cols)
@@ -970,7 +992,8 @@ template <int CKA, int CKB>
 __global__ void __launch_bounds__(128, 1)
 wgrad_s2_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_dy,
                    float* __restrict__ part, Dims3 dout, int Co, int tiles_per_chunk, int ntiles,
-                   int tiles_x, int tiles_y, int nchunks, int nst, int* __restrict__ err) {
+                   int tiles_x, int tiles_y, int rows_b, int nst, int bias_on,
+                   int* __restrict__ err) {
   constexpr int kTpm = 128 / CKA;               // M blocks (taps) per MMA
   constexpr uint32_t a_box = kBM * CKA * 2;     // one tap's box: 128 voxels x Ci
   constexpr uint32_t a_bytes = kTpm * a_box;    // the whole 128-row A tile
@@ -1021,7 +1044,8 @@ wgrad_s2_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
 
   if (warp == 0 && lane == 0) {  // TMA producer
     const uint32_t tx_bytes = (uint32_t)ntap * a_box + (uint32_t)(Co / CKB) * b_box;
-    for (int k = 0; k < ksteps; ++k) {
+    int k = 0;
+    for (; k < ksteps; ++k) {
       const int s = k % nst, round = k / nst;
       if (round > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (round - 1) & 1)) {
         atomicOr(err, kErrProducer);
@@ -1041,6 +1065,7 @@ wgrad_s2_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
       for (int c = 0; c < Co / CKB; ++c)
         tma_load_5d(base + a_bytes + (uint32_t)c * b_box, &tm_dy, c * CKB, x0, y0, z0, b, fb);
     }
+    drain_loads(full_bar, nst, k, err);
   } else if (warp == 1 && lane == 0) {  // MMA issuer
     const uint32_t idesc = instr_desc_mn(Co);
     for (int k = 0; k < ksteps; ++k) {
@@ -1066,15 +1091,15 @@ wgrad_s2_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
   }
   __syncwarp();
 
-  const bool waited = ksteps > 0 ? mbar_wait(smem_u32(&done_bar), 0) : false;
-  const bool ok = __all_sync(0xffffffffu, waited);
-  if (!ok && ksteps > 0 && lane == 0) atomicOr(err, kErrEpilogue);
+  const bool drained = __all_sync(0xffffffffu, mbar_wait(smem_u32(&done_bar), 0));
+  const bool ok = drained && ksteps > 0;
+  if (!drained && lane == 0) atomicOr(err, kErrEpilogue);
   tc_fence_after();
   const int m = warp * 32 + lane;  // TMEM lane = A row = (tap in group, ci)
   const int q = m / Ci, ci = m % Ci;
   const int t = t0 + q;
   const long long row = (long long)Co * 27 * Ci + Co;
-  float* prow = part + ((long long)b * nchunks + chunk) * row;
+  float* prow = part + ((long long)b * rows_b + chunk) * row;
   for (int c0 = 0; c0 < Co; c0 += 16) {
     uint32_t r[16];
     if (ok) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
@@ -1085,12 +1110,13 @@ wgrad_s2_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
     } else if (ones && q == ntap && ci == 0) {
 #pragma unroll
       for (int j = 0; j < 16; ++j)
-        prow[(long long)Co * 27 * Ci + c0 + j] = ok ? __uint_as_float(r[j]) : 0.f;
+        prow[(long long)Co * 27 * Ci + c0 + j] = ok && bias_on ? __uint_as_float(r[j]) : 0.f;
     }
   }
   tc_fence_before();
-  __syncthreads();
-  if (warp == 1) {
+  // TMEM is freed only once the last commit showed every issued MMA complete
+  const int all_drained = __syncthreads_and(drained ? 1 : 0);
+  if (warp == 1 && all_drained) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(tmem_cols)
@@ -1128,6 +1154,8 @@ __device__ __forceinline__ uint64_t smem_desc_mn2(uint32_t addr, uint32_t lbo, u
 
 struct Wg3Geom {
   int tz, nkx, tiles_x, tiles_z, ntiles, tiles_per_chunk, nchunks, nst;
+  int rows_b;      // partial-sum rows per problem (nchunks times the operand passes)
+  int bias_on;     // write the ones column's sums (else zeros: a pass that repeats them)
   uint32_t a_box, b_box, b_off, ones_off, stage, tmem_cols;
   int proj;        // also the weight gradient of a fused 1x1 projection (its dz_p: p_box)
   uint32_t p_off, p_box;
@@ -1188,7 +1216,8 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
   if (warp == 0 && lane == 0) {  // TMA producer
     const uint32_t tx_bytes =
         (uint32_t)NKX * gm.a_box + (uint32_t)nb * gm.b_box + (proj ? gm.p_box : 0u);
-    for (int k = 0; k < ksteps; ++k) {
+    int k = 0;
+    for (; k < ksteps; ++k) {
       const int s = k % nst, round = k / nst;
       if (round > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (round - 1) & 1)) {
         atomicOr(err, kErrProducer);
@@ -1208,6 +1237,7 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
         tma_load_5d(base + gm.b_off + (uint32_t)c * gm.b_box, &tm_x, c * CKB, x0, y0, z0, b, fb);
       if (proj) tma_load_5d(base + gm.p_off, &tm_p, 0, x0, y0, z0, b, fb);
     }
+    drain_loads(full_bar, nst, k, err);
   } else if (warp == 1 && lane == 0) {  // MMA issuer
     const uint32_t idesc = instr_desc_mn(N);
     for (int k = 0; k < ksteps; ++k) {
@@ -1258,15 +1288,15 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
   }
   __syncwarp();
 
-  const bool waited = ksteps > 0 ? mbar_wait(smem_u32(&done_bar), 0) : false;
-  const bool ok = __all_sync(0xffffffffu, waited);
-  if (!ok && ksteps > 0 && lane == 0) atomicOr(err, kErrEpilogue);
+  const bool drained = __all_sync(0xffffffffu, mbar_wait(smem_u32(&done_bar), 0));
+  const bool ok = drained && ksteps > 0;
+  if (!drained && lane == 0) atomicOr(err, kErrEpilogue);
   tc_fence_after();
   const int Co = CKA;
   const int m = warp * 32 + lane;  // TMEM lane = (window in the MMA, co)
   const int pl = m / Co, co = m % Co;
   const long long row = (long long)Co * 27 * ci_out + Co;  // the first ci_out channels
-  float* prow = part + ((long long)b * gm.nchunks + chunk) * row;
+  float* prow = part + ((long long)b * gm.rows_b + chunk) * row;
   for (int q = 0; q < NKX; ++q)
     for (int g = 0; g < kG; ++g) {
       const int s0 = g * kTpm < 9 - kTpm ? g * kTpm : 9 - kTpm;
@@ -1292,11 +1322,11 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
       uint32_t r[16];
       if (ok) tmem_ld16(col + (uint32_t)Ci, r);
       if (keep && t == 13)
-        prow[(long long)Co * 27 * ci_out + co] = ok ? __uint_as_float(r[0]) : 0.f;
+        prow[(long long)Co * 27 * ci_out + co] = ok && gm.bias_on ? __uint_as_float(r[0]) : 0.f;
     }
   if (proj && warp * 32 < Co) {  // rows co < Co of the projection accumulator
     const long long prow_n = (long long)Co * Ci + Co;
-    float* pp = part_p + ((long long)b * gm.nchunks + chunk) * prow_n;
+    float* pp = part_p + ((long long)b * gm.rows_b + chunk) * prow_n;
     const uint32_t col = tmem + ((uint32_t)(warp * 32) << 16) + pcol;
     for (int c0 = 0; c0 < Ci; c0 += 16) {
       uint32_t r[16];
@@ -1312,11 +1342,12 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
     }
     uint32_t r[16];
     if (ok) tmem_ld16(col + (uint32_t)Ci, r);
-    if (m < Co) pp[(long long)Co * Ci + m] = ok ? __uint_as_float(r[0]) : 0.f;
+    if (m < Co) pp[(long long)Co * Ci + m] = ok && gm.bias_on ? __uint_as_float(r[0]) : 0.f;
   }
   tc_fence_before();
-  __syncthreads();
-  if (warp == 1) {
+  // TMEM is freed only once the last commit showed every issued MMA complete
+  const int all_drained = __syncthreads_and(drained ? 1 : 0);
+  if (warp == 1 && all_drained) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(gm.tmem_cols)
@@ -1338,6 +1369,18 @@ __global__ void f32_to_bf16_kernel(const float* __restrict__ x, __nv_bfloat16* _
   } else {
     for (long long j = i; j < n; ++j) y[j] = __float2bfloat16_rn(x[j]);
   }
+}
+
+// x [v][C] FP32 -> y [v][sp * C] BF16 staging rows (stage_bf16x4); a thread per 4 channels.
+__global__ void f32_to_bf16_rows_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ y,
+                                        long long nvox, int C, int sp) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = C / 4;
+  if (e >= nvox * g) return;
+  const long long v = e / g;
+  const int c = (int)(e % g) * 4;
+  const float4 val = *reinterpret_cast<const float4*>(x + v * C + c);
+  stage_bf16x4(y + v * C * sp, C, c, val, sp);
 }
 
 // Forward weights [t][co][ci] and data-gradient weights [T-1-t][ci][co] of one layer (tap
@@ -1384,7 +1427,7 @@ weights_all_bf16_kernel(const float* __restrict__ theta, __nv_bfloat16* __restri
   while (l + 1 < t.nl && (int)blockIdx.x >= t.blk0[l + 1]) ++l;
   const int b = blockIdx.y;
   const int ci = t.ci[l], cr = t.ci_real[l], co = t.co[l], T = t.T[l];
-  const int nch = (co + kWOc - 1) / kWOc;
+  const int nch = (co + kWOc - 1) / kWOc;  // (blocks of 32 output channels per tap)
   const int q = blockIdx.x - t.blk0[l];
   const int tap = q / nch, o0 = (q % nch) * kWOc;
   const int no = co - o0 < kWOc ? co - o0 : kWOc;
@@ -1402,6 +1445,34 @@ weights_all_bf16_kernel(const float* __restrict__ theta, __nv_bfloat16* __restri
   for (int e = threadIdx.x; e < no * ci; e += blockDim.x) {
     const int ol = e % no, c = e / no;
     base[t.wd_off[l] + ((long long)(T - 1 - tap) * ci + c) * co + o0 + ol] = tile[ol][c];
+  }
+}
+
+// Split weights of every layer (BF16x3): forward rows [t][co][3 ci] = [hi | hi | lo] over ci
+// and data-gradient rows [T-1-t][ci][3 co] = [hi | hi | lo] over co, hi = bf16(w),
+// lo = bf16(w - hi); a thread per (layer element, problem).  Blocks are ranged per layer as
+// in weights_all_bf16_kernel, each covering 256 elements [o][t][c] of its layer.
+__global__ void __launch_bounds__(256)
+weights_split_bf16_kernel(const float* __restrict__ theta, __nv_bfloat16* __restrict__ wb,
+                          long long Pp, long long wstride, const __grid_constant__ WTable t) {
+  int l = 0;
+  while (l + 1 < t.nl && (int)blockIdx.x >= t.blk0[l + 1]) ++l;
+  const int b = blockIdx.y;
+  const int ci = t.ci[l], cr = t.ci_real[l], co = t.co[l], T = t.T[l];
+  const long long e = (long long)(blockIdx.x - t.blk0[l]) * blockDim.x + threadIdx.x;
+  if (e >= (long long)co * T * ci) return;
+  const int c = (int)(e % ci);
+  const long long r = e / ci;
+  const int tap = (int)(r % T), o = (int)(r / T);
+  const float v = c < cr ? theta[(long long)b * Pp + t.w_off[l] + r * cr + c] : 0.f;
+  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+  const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+  __nv_bfloat16* base = wb + (long long)b * wstride;
+  __nv_bfloat16* f = base + t.wf_off[l] + ((long long)tap * co + o) * 3 * ci;
+  f[c] = hi, f[ci + c] = hi, f[2 * ci + c] = lo;
+  if (t.dgrad[l]) {
+    __nv_bfloat16* d = base + t.wd_off[l] + ((long long)(T - 1 - tap) * ci + c) * 3 * co;
+    d[o] = hi, d[co + o] = hi, d[2 * co + o] = lo;
   }
 }
 
@@ -1434,15 +1505,18 @@ CUtensorMapSwizzle swizzle_for(int ck) {
                   : (ck == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
 }
 
-// Channels-last BF16 activations [B][Z][Y][X][C] as a 5-D map, box = one tile's taps.
-cudaError_t encode_act(CUtensorMap* m, void* base, int B, Dims3 d, int C, int ck, int S) {
+// Channels-last BF16 activations [B][Z][Y][X][row] as a 5-D map over C channels of each
+// row (row = 0: row = C; else a C-channel block of a wider staged row, `base` at the block),
+// box = one tile's taps.
+cudaError_t encode_act(CUtensorMap* m, void* base, int B, Dims3 d, int C, int ck, int S,
+                       int row = 0) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   const cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)d.x, (cuuint64_t)d.y, (cuuint64_t)d.z,
                               (cuuint64_t)B};
-  const cuuint64_t es = 2;
-  const cuuint64_t strides[4] = {C * es, C * es * d.x, C * es * d.x * d.y,
-                                 C * es * d.x * d.y * d.z};
+  const cuuint64_t es = 2, R = (cuuint64_t)(row ? row : C);
+  const cuuint64_t strides[4] = {R * es, R * es * d.x, R * es * d.x * d.y,
+                                 R * es * d.x * d.y * d.z};
   const cuuint32_t box[5] = {(cuuint32_t)ck, (cuuint32_t)(kBX * S), (cuuint32_t)(kBY * S),
                              (cuuint32_t)(kBZ * S), 1};
   const cuuint32_t estr[5] = {1, (cuuint32_t)S, (cuuint32_t)S, (cuuint32_t)S, 1};
@@ -1471,16 +1545,17 @@ cudaError_t encode_w(CUtensorMap* m, void* base, int B, long long wstride, int c
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// Channels-last activations [B][Z][Y][X][C] with a bx x by x bz box of ck channels.
+// Channels-last activations [B][Z][Y][X][row] (C channels of each row, as encode_act) with a
+// bx x by x bz box of ck channels.
 cudaError_t encode_box(CUtensorMap* m, void* base, int B, Dims3 d, int C, int ck, int bx, int by,
-                       int bz) {
+                       int bz, int row = 0) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   const cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)d.x, (cuuint64_t)d.y, (cuuint64_t)d.z,
                               (cuuint64_t)B};
-  const cuuint64_t es = 2;
-  const cuuint64_t strides[4] = {C * es, C * es * d.x, C * es * d.x * d.y,
-                                 C * es * d.x * d.y * d.z};
+  const cuuint64_t es = 2, R = (cuuint64_t)(row ? row : C);
+  const cuuint64_t strides[4] = {R * es, R * es * d.x, R * es * d.x * d.y,
+                                 R * es * d.x * d.y * d.z};
   const cuuint32_t box[5] = {(cuuint32_t)ck, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box, estr,
@@ -1732,12 +1807,14 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
   L.din = din;
   L.dout = conv_out_dims(din, k, s);
   L.w_off = w_off;
+  L.kf = bf.sp * ci;
+  L.kd = bf.sp * co;
   L.dgrad = (s == 1 || k == 3) && bf16_conv_supported(co, ci, k);
   if (k == 3 && s == 1) {
-    const Tc3Plan pf = tc3_plan(ci, co, 0, L.dout.z);
+    const Tc3Plan pf = tc3_plan(L.kf, co, 0, L.dout.z);
     L.ck3f = pf.ck, L.tz3f = pf.tz;
     if (L.dgrad) {
-      const Tc3Plan pd = tc3_plan(co, ci, 0, L.din.z);
+      const Tc3Plan pd = tc3_plan(L.kd, ci, 0, L.din.z);
       L.ck3d = pd.ck, L.tz3d = pd.tz;
     }
   }
@@ -1746,7 +1823,7 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
   L.wg3 = L.wgrad && wg3_geom(L, 1).nst > 0;
   if (k == 3 && s == 2 && (ci == 16 || ci == 32 || ci == 64) && co % 16 == 0 && co <= 256)
     L.wgrad = L.wgs2 = true;
-  const long long n = (long long)co * k * k * k * ci;
+  const long long n = (long long)co * k * k * k * ci * bf.sp;
   L.wf_off = bf.wstride;
   bf.wstride += (n + 63) / 64 * 64;
   if (L.dgrad) {
@@ -1768,17 +1845,19 @@ int bf16_add_input_layer(Bf16Net& bf, int ci_real, int co, Dims3 din, long long 
   L.din = din;
   L.dout = din;
   L.w_off = w_off;
+  L.kf = 16 * bf.sp;
+  L.kd = co * bf.sp;
   L.input_layer = true;
   if (bf16_conv_supported(16, co, 3)) {
-    const Tc3Plan pf = tc3_plan(16, co, 0, din.z);
+    const Tc3Plan pf = tc3_plan(L.kf, co, 0, din.z);
     L.ck3f = pf.ck, L.tz3f = pf.tz;
   }
   L.wg_tz = wg3_tz_fit(L);
   L.wgrad = L.wg3 = wg3_geom(L, 1).nst > 0;
   if (!L.ck3f || !L.wg3) return -1;
   L.wf_off = bf.wstride;
-  bf.wstride += ((long long)co * 27 * 16 + 63) / 64 * 64;
-  bf.zcount = din.count() * 16;
+  bf.wstride += ((long long)co * 27 * L.kf + 63) / 64 * 64;
+  bf.zcount = din.count() * L.kf;
   bf.layers.push_back(L);
   return (int)bf.layers.size() - 1;
 }
@@ -1790,84 +1869,101 @@ void bf16_layout(Bf16Net& bf, char* base, size_t& used, int B, long long max_act
     return p;
   };
   bf.max_act = max_act;
+  const size_t act_bytes = (size_t)B * max_act * 2 * bf.sp;
   bf.err = reinterpret_cast<int*>(take(sizeof(int)));
-  bf.xbf = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * max_act * 2));
-  bf.ybf = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * max_act * 2));
+  bf.xbf = reinterpret_cast<__nv_bfloat16*>(take(act_bytes));
+  bf.ybf = reinterpret_cast<__nv_bfloat16*>(take(act_bytes));
   bool any_proj = false;
   for (const TcLayer& L : bf.layers) any_proj |= L.projd || L.projw;
-  bf.pbf = any_proj ? reinterpret_cast<__nv_bfloat16*>(take((size_t)B * max_act * 2)) : nullptr;
+  bf.pbf = any_proj ? reinterpret_cast<__nv_bfloat16*>(take(act_bytes)) : nullptr;
   bf.wbuf = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * bf.wstride * 2));
   bf.zbf = bf.zcount ? reinterpret_cast<__nv_bfloat16*>(take((size_t)B * bf.zcount * 2)) : nullptr;
   for (TcLayer& L : bf.layers) {
     if (L.input_layer)
       L.xin = bf.zbf;
     else if (bf.keep_inputs)
-      L.xin = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * L.din.count() * L.ci * 2));
+      L.xin = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * L.din.count() * L.kf * 2));
     else
       L.xin = bf.xbf;
   }
+}
+
+// Weight-gradient operand maps of one layer for channel block `blk` (0: hi, 1: lo) of the
+// staged dy (ybf, co channels per block) and x (the layer input, ci per block), in the box
+// form of the kernel that runs it; a fused projection's dz_p column (pbf) likewise.
+cudaError_t encode_wgrad_maps(TcLayer& L, const Bf16Net& bf, int B, int blk) {
+  const int sp = bf.sp;
+  __nv_bfloat16* y = bf.ybf + (size_t)blk * L.co;
+  __nv_bfloat16* x = L.xin + (size_t)blk * L.ci;
+  const int yrow = sp * L.co, xrow = sp * L.ci;
+  cudaError_t e = cudaSuccess;
+  if (L.wg3) {
+    const int tz = L.wg_tz;
+    e = encode_box(&L.wgy[blk], y, B, L.dout, L.co, L.co, 8, 3, tz + 2, yrow);
+    if (e == cudaSuccess)
+      e = encode_box(&L.wgx[blk], x, B, L.din, L.ci, chunk_for(L.ci), 8, 1, tz, xrow);
+    if (e == cudaSuccess && L.projw)
+      e = encode_box(&L.wgp[blk], bf.pbf + (size_t)blk * L.co, B, L.dout, L.co, L.co, 8, 1, tz,
+                     yrow);
+  } else {  // per-tap and stride-2 kernels: dy tile boxes, x tile boxes (strided for s = 2)
+    e = encode_act(&L.wgy[blk], y, B, L.dout, L.co, chunk_for(L.co), 1, yrow);
+    if (e == cudaSuccess)
+      e = encode_act(&L.wgx[blk], x, B, L.din, L.ci, chunk_for(L.ci), L.s, xrow);
+  }
+  return e;
 }
 
 cudaError_t bf16_finalize(Bf16Net& bf, int B) {
   for (TcLayer& L : bf.layers) {
     const int T = L.k * L.k * L.k;
     if (L.input_layer) {  // halo-box forward and weight gradient over zbf only
-      cudaError_t e =
-          encode_act_halo(&L.act_f3, bf.zbf, B, L.din, 16, L.ck3f, L.tz3f);
+      cudaError_t e = encode_act_halo(&L.act_f3, bf.zbf, B, L.din, L.kf, L.ck3f, L.tz3f);
       if (e == cudaSuccess)
-        e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, 16, T, L.co, L.ck3f, 9, 3);
-      const int tz = L.wg_tz;
-      if (e == cudaSuccess) e = encode_box(&L.wg_dy3, bf.ybf, B, L.dout, L.co, L.co, 8, 3, tz + 2);
-      if (e == cudaSuccess) e = encode_box(&L.wg_x3, bf.zbf, B, L.din, 16, 16, 8, 1, tz);
+        e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, L.kf, T, L.co, L.ck3f, 9, 3);
+      for (int blk = 0; blk < (bf.sp > 1 ? 2 : 1) && e == cudaSuccess; ++blk)
+        e = encode_wgrad_maps(L, bf, B, blk);
       if (e != cudaSuccess) return e;
       continue;
     }
-    cudaError_t e = encode_act(&L.act_f, L.xin, B, L.din, L.ci, chunk_for(L.ci), L.s);
+    cudaError_t e = encode_act(&L.act_f, L.xin, B, L.din, L.kf, chunk_for(L.kf), L.s);
     if (e == cudaSuccess)
-      e = encode_w(&L.w_f, bf.wbuf + L.wf_off, B, bf.wstride, L.ci, T, L.co, chunk_for(L.ci), 1,
+      e = encode_w(&L.w_f, bf.wbuf + L.wf_off, B, bf.wstride, L.kf, T, L.co, chunk_for(L.kf), 1,
                    1);
     if (e == cudaSuccess && L.dgrad) {
-      e = encode_act(&L.act_d, bf.ybf, B, L.dout, L.co, chunk_for(L.co), 1);
+      e = encode_act(&L.act_d, bf.ybf, B, L.dout, L.kd, chunk_for(L.kd), 1);
       if (e == cudaSuccess)
-        e = encode_w(&L.w_d, bf.wbuf + L.wd_off, B, bf.wstride, L.co, T, L.ci, chunk_for(L.co), 1,
+        e = encode_w(&L.w_d, bf.wbuf + L.wd_off, B, bf.wstride, L.kd, T, L.ci, chunk_for(L.kd), 1,
                      1);
     }
-    if (e == cudaSuccess && L.wgrad)
-      e = encode_act(&L.act_wy, bf.ybf, B, L.dout, L.co, chunk_for(L.co), 1);
-    if (e == cudaSuccess && L.wg3) {
-      const int tz = L.wg_tz;
-      e = encode_box(&L.wg_dy3, bf.ybf, B, L.dout, L.co, L.co, 8, 3, tz + 2);
-      if (e == cudaSuccess)
-        e = encode_box(&L.wg_x3, L.xin, B, L.din, L.ci, chunk_for(L.ci), 8, 1, tz);
-    }
+    for (int blk = 0; L.wgrad && blk < (bf.sp > 1 ? 2 : 1) && e == cudaSuccess; ++blk)
+      e = encode_wgrad_maps(L, bf, B, blk);
     if (e == cudaSuccess && L.ck3f) {
-      e = encode_act_halo(&L.act_f3, L.xin, B, L.din, L.ci, L.ck3f, L.tz3f);
+      e = encode_act_halo(&L.act_f3, L.xin, B, L.din, L.kf, L.ck3f, L.tz3f);
       if (e == cudaSuccess)
-        e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, L.ci, T, L.co, L.ck3f, 9, 3);
+        e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, L.kf, T, L.co, L.ck3f, 9, 3);
     }
     if (e == cudaSuccess && L.ck3d) {
-      e = encode_act_halo(&L.act_d3, bf.ybf, B, L.dout, L.co, L.ck3d, L.tz3d);
+      e = encode_act_halo(&L.act_d3, bf.ybf, B, L.dout, L.kd, L.ck3d, L.tz3d);
       if (e == cudaSuccess)
-        e = encode_w(&L.w_d3, bf.wbuf + L.wd_off, B, bf.wstride, L.co, T, L.ci, L.ck3d, 9, 3);
+        e = encode_w(&L.w_d3, bf.wbuf + L.wd_off, B, bf.wstride, L.kd, T, L.ci, L.ck3d, 9, 3);
     }
-    if (e == cudaSuccess && L.projf) {  // W_p [1][co][ci] in chunks of this layer's ck
+    if (e == cudaSuccess && L.projf) {  // W_p [1][co][kf] in chunks of this layer's ck
       const TcLayer& P = bf.layers[L.proj];
-      e = encode_w(&L.pw_f, bf.wbuf + P.wf_off, B, bf.wstride, P.ci, 1, P.co, L.ck3f, 1, 1);
+      e = encode_w(&L.pw_f, bf.wbuf + P.wf_off, B, bf.wstride, P.kf, 1, P.co, L.ck3f, 1, 1);
     }
-    if (e == cudaSuccess && L.projw)  // dz_p column of the halo weight gradient
-      e = encode_box(&L.wg_p3, bf.pbf, B, L.dout, L.co, L.co, 8, 1, L.wg_tz);
-    if (e == cudaSuccess && L.projd) {  // W_p^T [1][ci][co] and the dz_p tile box
+    if (e == cudaSuccess && L.projd) {  // W_p^T [1][ci][kd] and the dz_p tile box
       const TcLayer& P = bf.layers[L.proj];
-      e = encode_w(&L.pw_d, bf.wbuf + P.wd_off, B, bf.wstride, P.co, 1, P.ci, L.ck3d, 1, 1);
+      e = encode_w(&L.pw_d, bf.wbuf + P.wd_off, B, bf.wstride, P.kd, 1, P.ci, L.ck3d, 1, 1);
       if (e == cudaSuccess)
-        e = encode_box(&L.pa_d, bf.pbf, B, L.dout, L.co, L.ck3d, 8, 16, L.tz3d);
+        e = encode_box(&L.pa_d, bf.pbf, B, L.dout, L.kd, L.ck3d, 8, 16, L.tz3d);
     }
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-static cudaError_t stage_bf16(const float* x, __nv_bfloat16* y, long long n, cudaStream_t st);
+static cudaError_t stage_rows(const float* x, __nv_bfloat16* y, long long nvox, int C, int sp,
+                              cudaStream_t st);
 
 namespace {
 
@@ -1903,11 +1999,12 @@ cudaError_t wgrad_attr() {
 }
 
 template <int CKA, int CKB>
-void launch_wgrad_tc(dim3 grid, size_t smem, const TcLayer& L, float* part, const WgPlan& p,
-                     int* err, cudaStream_t st) {
+void launch_wgrad_tc(dim3 grid, size_t smem, const TcLayer& L, const CUtensorMap& my,
+                     const CUtensorMap& mx, float* part, const WgPlan& p, int rows_b,
+                     int bias_on, int* err, cudaStream_t st) {
   wgrad_tc_kernel<CKA, CKB><<<grid, 128, smem, st>>>(
-      L.act_wy, L.act_f, part, L.dout, L.co, L.ci, L.k, p.tg, p.tiles_per_chunk, p.ntiles,
-      p.tiles_x, p.tiles_y, p.chunks, p.nst, err);
+      my, mx, part, L.dout, L.co, L.ci, L.k, p.tg, p.tiles_per_chunk, p.ntiles, p.tiles_x,
+      p.tiles_y, rows_b, p.nst, bias_on, err);
 }
 
 int sm_count() {
@@ -2003,17 +2100,17 @@ cudaError_t wg3_attr() {
 }
 
 template <int CKA, int CKB>
-void launch_wg3(const TcLayer& L, const Wg3Geom& g, float* part, float* part_p, int B, int* err,
+void launch_wg3(const TcLayer& L, const Wg3Geom& g, const CUtensorMap& my, const CUtensorMap& mx,
+                const CUtensorMap& mp, float* part, float* part_p, int B, int* err,
                 cudaStream_t st) {
   dim3 grid((unsigned)g.nchunks, (unsigned)(3 / g.nkx), (unsigned)B);
   const size_t smem = (size_t)g.nst * g.stage + 1024;
-  const CUtensorMap& mp = g.proj ? L.wg_p3 : L.wg_dy3;
   if (g.nkx == 3)
-    wgrad_tc3_kernel<CKA, CKB, 3><<<grid, 128, smem, st>>>(L.wg_dy3, L.wg_x3, mp, part, part_p,
-                                                           L.dout, L.ci, L.ci_real, g, err);
+    wgrad_tc3_kernel<CKA, CKB, 3><<<grid, 128, smem, st>>>(my, mx, mp, part, part_p, L.dout,
+                                                           L.ci, L.ci_real, g, err);
   else
-    wgrad_tc3_kernel<CKA, CKB, 1><<<grid, 128, smem, st>>>(L.wg_dy3, L.wg_x3, mp, part, part_p,
-                                                           L.dout, L.ci, L.ci_real, g, err);
+    wgrad_tc3_kernel<CKA, CKB, 1><<<grid, 128, smem, st>>>(my, mx, mp, part, part_p, L.dout,
+                                                           L.ci, L.ci_real, g, err);
 }
 
 struct S2Plan {
@@ -2044,12 +2141,12 @@ cudaError_t wgs2_attr() {
 }
 
 template <int CKA, int CKB>
-void launch_wgs2(const TcLayer& L, const S2Plan& p, float* part, int B, int* err,
-                 cudaStream_t st) {
+void launch_wgs2(const TcLayer& L, const S2Plan& p, const CUtensorMap& mx, const CUtensorMap& my,
+                 float* part, int rows_b, int bias_on, int B, int* err, cudaStream_t st) {
   dim3 grid((unsigned)p.chunks, (unsigned)p.groups, (unsigned)B);
-  wgrad_s2_tc_kernel<CKA, CKB><<<grid, 128, p.smem, st>>>(L.act_f, L.act_wy, part, L.dout, L.co,
+  wgrad_s2_tc_kernel<CKA, CKB><<<grid, 128, p.smem, st>>>(mx, my, part, L.dout, L.co,
                                                           p.tiles_per_chunk, p.ntiles, p.tiles_x,
-                                                          p.tiles_y, p.chunks, p.nst, err);
+                                                          p.tiles_y, rows_b, p.nst, bias_on, err);
 }
 
 }  // namespace
@@ -2061,6 +2158,15 @@ long long bf16_wgrad_chunks(const Bf16Net& bf, int layer, int B) {
   return wgrad_plan(L, B).chunks;
 }
 
+int bf16_wgrad_passes(const Bf16Net& bf, int layer) {
+  return bf.layers[layer].wgrad && bf.sp > 1 ? 3 : 1;
+}
+
+// Operand blocks (dy, x) of weight-gradient pass p: (hi, hi), (lo, hi), (hi, lo).  The ones
+// column sums dy, so the bias partial is kept in the passes that see dy_hi once and dy_lo
+// once (the first two).
+constexpr int kPassY[3] = {0, 1, 0}, kPassX[3] = {0, 0, 1}, kPassBias[3] = {1, 1, 0};
+
 cudaError_t bf16_conv_wgrad(Bf16Net& bf, int layer, const float* x, const float* dy,
                             float* part, int B, cudaStream_t stream, const float* dz_p,
                             float* part_p, bool x_staged, bool dy_staged) {
@@ -2069,54 +2175,79 @@ cudaError_t bf16_conv_wgrad(Bf16Net& bf, int layer, const float* x, const float*
   const WgPlan p = wgrad_plan(L, B);
   cudaError_t e = L.input_layer || (x_staged && bf.keep_inputs)
                       ? cudaSuccess
-                      : stage_bf16(x, L.xin, (long long)B * L.din.count() * L.ci, stream);
+                      : stage_rows(x, L.xin, (long long)B * L.din.count(), L.ci, bf.sp, stream);
   if (e == cudaSuccess && !dy_staged)
-    e = stage_bf16(dy, bf.ybf, (long long)B * L.dout.count() * L.co, stream);
+    e = stage_rows(dy, bf.ybf, (long long)B * L.dout.count(), L.co, bf.sp, stream);
   if (e != cudaSuccess) return e;
+  const int passes = bf16_wgrad_passes(bf, layer);
+  // partial-row length as the kernels write it: the input layer keeps its real channels
+  const long long row =
+      (long long)L.co * L.k * L.k * L.k * (L.input_layer ? L.ci_real : L.ci) + L.co;
   if (L.wgs2) {
     const S2Plan p2 = wgs2_plan(L, B);
     const int ckb = chunk_for(L.co);
-#define D2IP_WS2(A_, B_) launch_wgs2<A_, B_>(L, p2, part, B, bf.err, stream)
-    if (L.ci == 16) {
-      if (ckb == 16) D2IP_WS2(16, 16); else if (ckb == 32) D2IP_WS2(16, 32); else D2IP_WS2(16, 64);
-    } else if (L.ci == 32) {
-      if (ckb == 16) D2IP_WS2(32, 16); else if (ckb == 32) D2IP_WS2(32, 32); else D2IP_WS2(32, 64);
-    } else {
-      if (ckb == 16) D2IP_WS2(64, 16); else if (ckb == 32) D2IP_WS2(64, 32); else D2IP_WS2(64, 64);
-    }
+    for (int q = 0; q < passes; ++q) {
+      float* pq = part + (long long)q * p2.chunks * row;
+      const int rows_b = passes * p2.chunks;
+      const CUtensorMap &mx = L.wgx[kPassX[q]], &my = L.wgy[kPassY[q]];
+#define D2IP_WS2(A_, B_) launch_wgs2<A_, B_>(L, p2, mx, my, pq, rows_b, kPassBias[q], B, bf.err, stream)
+      if (L.ci == 16) {
+        if (ckb == 16) D2IP_WS2(16, 16); else if (ckb == 32) D2IP_WS2(16, 32); else D2IP_WS2(16, 64);
+      } else if (L.ci == 32) {
+        if (ckb == 16) D2IP_WS2(32, 16); else if (ckb == 32) D2IP_WS2(32, 32); else D2IP_WS2(32, 64);
+      } else {
+        if (ckb == 16) D2IP_WS2(64, 16); else if (ckb == 32) D2IP_WS2(64, 32); else D2IP_WS2(64, 64);
+      }
 #undef D2IP_WS2
+    }
     return cudaGetLastError();
   }
   if (L.wg3) {
-    const Wg3Geom g = wg3_geom(L, B, L.projw);
+    Wg3Geom g = wg3_geom(L, B, L.projw);
     if (L.projw) {  // the fused projection needs its dz_p staged (kept from the data gradient)
       if (!dz_p || !part_p) return cudaErrorInvalidValue;
-      if (!L.projd) e = stage_bf16(dz_p, bf.pbf, (long long)B * L.dout.count() * L.co, stream);
+      if (!L.projd)
+        e = stage_rows(dz_p, bf.pbf, (long long)B * L.dout.count(), L.co, bf.sp, stream);
       if (e != cudaSuccess) return e;
     }
+    const long long prow = (long long)L.co * L.ci + L.co;
+    g.rows_b = passes * g.nchunks;
     const int ckb = chunk_for(L.ci);
-#define D2IP_WG3(A_, B_) launch_wg3<A_, B_>(L, g, part, part_p, B, bf.err, stream)
-    if (L.co == 16) {
-      if (ckb == 16) D2IP_WG3(16, 16); else if (ckb == 32) D2IP_WG3(16, 32); else D2IP_WG3(16, 64);
-    } else if (L.co == 32) {
-      if (ckb == 16) D2IP_WG3(32, 16); else if (ckb == 32) D2IP_WG3(32, 32); else D2IP_WG3(32, 64);
-    } else {
-      if (ckb == 16) D2IP_WG3(64, 16); else if (ckb == 32) D2IP_WG3(64, 32); else D2IP_WG3(64, 64);
-    }
+    for (int q = 0; q < passes; ++q) {
+      g.bias_on = kPassBias[q];
+      float* pq = part + (long long)q * g.nchunks * row;
+      float* ppq = part_p ? part_p + (long long)q * g.nchunks * prow : nullptr;
+      const CUtensorMap &my = L.wgy[kPassY[q]], &mx = L.wgx[kPassX[q]];
+      const CUtensorMap& mp = g.proj ? L.wgp[kPassY[q]] : my;
+#define D2IP_WG3(A_, B_) launch_wg3<A_, B_>(L, g, my, mx, mp, pq, ppq, B, bf.err, stream)
+      if (L.co == 16) {
+        if (ckb == 16) D2IP_WG3(16, 16); else if (ckb == 32) D2IP_WG3(16, 32); else D2IP_WG3(16, 64);
+      } else if (L.co == 32) {
+        if (ckb == 16) D2IP_WG3(32, 16); else if (ckb == 32) D2IP_WG3(32, 32); else D2IP_WG3(32, 64);
+      } else {
+        if (ckb == 16) D2IP_WG3(64, 16); else if (ckb == 32) D2IP_WG3(64, 32); else D2IP_WG3(64, 64);
+      }
 #undef D2IP_WG3
+    }
     return cudaGetLastError();
   }
   dim3 grid(p.chunks, p.groups, B);
   const int cka = chunk_for(L.co), ckb = chunk_for(L.ci);
-#define D2IP_WGT(A_, B_) launch_wgrad_tc<A_, B_>(grid, p.smem, L, part, p, bf.err, stream)
-  if (cka == 16) {
-    if (ckb == 16) D2IP_WGT(16, 16); else if (ckb == 32) D2IP_WGT(16, 32); else D2IP_WGT(16, 64);
-  } else if (cka == 32) {
-    if (ckb == 16) D2IP_WGT(32, 16); else if (ckb == 32) D2IP_WGT(32, 32); else D2IP_WGT(32, 64);
-  } else {
-    if (ckb == 16) D2IP_WGT(64, 16); else if (ckb == 32) D2IP_WGT(64, 32); else D2IP_WGT(64, 64);
-  }
+  for (int q = 0; q < passes; ++q) {
+    float* pq = part + (long long)q * p.chunks * row;
+    const int rows_b = passes * p.chunks;
+    const CUtensorMap &my = L.wgy[kPassY[q]], &mx = L.wgx[kPassX[q]];
+#define D2IP_WGT(A_, B_) \
+  launch_wgrad_tc<A_, B_>(grid, p.smem, L, my, mx, pq, p, rows_b, kPassBias[q], bf.err, stream)
+    if (cka == 16) {
+      if (ckb == 16) D2IP_WGT(16, 16); else if (ckb == 32) D2IP_WGT(16, 32); else D2IP_WGT(16, 64);
+    } else if (cka == 32) {
+      if (ckb == 16) D2IP_WGT(32, 16); else if (ckb == 32) D2IP_WGT(32, 32); else D2IP_WGT(32, 64);
+    } else {
+      if (ckb == 16) D2IP_WGT(64, 16); else if (ckb == 32) D2IP_WGT(64, 32); else D2IP_WGT(64, 64);
+    }
 #undef D2IP_WGT
+  }
   return cudaGetLastError();
 }
 
@@ -2179,6 +2310,25 @@ cudaError_t bf16_prepare_kernels() {
 
 cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long long Pp,
                                  cudaStream_t stream) {
+  if (bf.sp > 1) {  // split weights: one launch, a thread per (layer element, problem)
+    if (bf.layers.empty() || bf.layers.size() > (size_t)kWMaxLayers) return cudaErrorInvalidValue;
+    WTable t{};
+    t.nl = (int)bf.layers.size();
+    int blk = 0;
+    for (int i = 0; i < t.nl; ++i) {
+      const TcLayer& L = bf.layers[i];
+      const int T = L.k * L.k * L.k;
+      t.blk0[i] = blk;
+      blk += (int)ceil_div((long long)L.co * T * L.ci, 256);
+      t.w_off[i] = L.w_off, t.wf_off[i] = L.wf_off, t.wd_off[i] = L.wd_off;
+      t.ci[i] = L.ci, t.ci_real[i] = L.ci_real, t.co[i] = L.co, t.T[i] = T;
+      t.dgrad[i] = L.dgrad ? 1 : 0;
+    }
+    t.blk0[t.nl] = blk;
+    weights_split_bf16_kernel<<<dim3((unsigned)blk, B), 256, 0, stream>>>(theta, bf.wbuf, Pp,
+                                                                           bf.wstride, t);
+    return cudaGetLastError();
+  }
   bool fits = bf.layers.size() <= (size_t)kWMaxLayers && !bf.layers.empty();
   for (const TcLayer& L : bf.layers) fits = fits && L.ci <= 256;
   if (fits) {
@@ -2212,20 +2362,35 @@ cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long lo
   return cudaSuccess;
 }
 
-static cudaError_t stage_bf16(const float* x, __nv_bfloat16* y, long long n, cudaStream_t st) {
-  f32_to_bf16_kernel<<<(unsigned)ceil_div(ceil_div(n, 4), 256), 256, 0, st>>>(x, y, n);
+static cudaError_t stage_rows(const float* x, __nv_bfloat16* y, long long nvox, int C, int sp,
+                              cudaStream_t st) {
+  if (sp == 1) {
+    const long long n = nvox * C;
+    f32_to_bf16_kernel<<<(unsigned)ceil_div(ceil_div(n, 4), 256), 256, 0, st>>>(x, y, n);
+  } else {
+    f32_to_bf16_rows_kernel<<<(unsigned)ceil_div(nvox * (C / 4), 256), 256, 0, st>>>(x, y, nvox,
+                                                                                    C, sp);
+  }
   return cudaGetLastError();
 }
 
 namespace {
-// z [v][cr] FP32 -> zp [v][16] BF16, channels cr..15 zero; one thread per (voxel, channel).
+// z [v][cr] FP32 -> zp [v][16 sp] BF16, channels cr..15 of each block zero (sp 3: blocks
+// [hi | lo | hi]); one thread per (voxel, channel).
 __global__ void pad_input_kernel(const float* __restrict__ z, __nv_bfloat16* __restrict__ zp,
-                                 long long nvox, int cr) {
+                                 long long nvox, int cr, int sp) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nvox * 16) return;
   const long long v = i / 16;
   const int c = (int)(i % 16);
-  zp[i] = __float2bfloat16_rn(c < cr ? z[v * cr + c] : 0.f);
+  const float x = c < cr ? z[v * cr + c] : 0.f;
+  const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+  __nv_bfloat16* row = zp + v * 16 * sp;
+  row[c] = hi;
+  if (sp > 1) {
+    row[16 + c] = __float2bfloat16_rn(x - __bfloat162float(hi));
+    row[32 + c] = hi;
+  }
 }
 }  // namespace
 
@@ -2236,11 +2401,11 @@ int bf16_fuse_proj(Bf16Net& bf, int la, int lp) {
     return 0;
   A.proj = lp;
   if (A.ck3f) {
-    const Tc3Plan pf = tc3_plan(A.ci, A.co, P.co, A.dout.z);
+    const Tc3Plan pf = tc3_plan(A.kf, A.co, P.co, A.dout.z);
     if (pf.persistent) A.projf = true, A.ck3f = pf.ck, A.tz3f = pf.tz;
   }
   if (A.ck3d && P.dgrad) {
-    const Tc3Plan pd = tc3_plan(A.co, A.ci, 0, A.din.z);
+    const Tc3Plan pd = tc3_plan(A.kd, A.ci, 0, A.din.z);
     A.projd = pd.persistent && pd.ck == A.ck3d && pd.tz == A.tz3d;
   }
   A.projw = A.wg3 && wg3_geom(A, 1, true).nst > 0;
@@ -2254,9 +2419,9 @@ cudaError_t bf16_conv_fwd_proj(Bf16Net& bf, int la, const float* x, const float*
   if (!L.projf) return cudaErrorInvalidValue;
   cudaError_t e = x_staged && bf.keep_inputs
                       ? cudaSuccess
-                      : stage_bf16(x, L.xin, (long long)B * L.din.count() * L.ci, stream);
+                      : stage_rows(x, L.xin, (long long)B * L.din.count(), L.ci, bf.sp, stream);
   if (e != cudaSuccess) return e;
-  return launch_tc3(L.act_f3, L.w_f3, L.ci, L.ck3f, L.tz3f, bias_a, y_a, L.dout, L.co, B,
+  return launch_tc3(L.act_f3, L.w_f3, L.kf, L.ck3f, L.tz3f, bias_a, y_a, L.dout, L.co, B,
                     L.dout.count() * L.co, bias_bs, 0, bf.err, stream, 1, &L.pw_f, nullptr,
                     L.co, bias_p, y_p, L.dout.count() * L.co);
 }
@@ -2266,11 +2431,11 @@ cudaError_t bf16_conv_dgrad_proj(Bf16Net& bf, int la, const float* dz_a, const f
                                  bool dzp_staged) {
   const TcLayer& L = bf.layers[la];
   if (!L.projd) return cudaErrorInvalidValue;
-  const long long n = (long long)B * L.dout.count() * L.co;
-  cudaError_t e = dza_staged ? cudaSuccess : stage_bf16(dz_a, bf.ybf, n, stream);
-  if (e == cudaSuccess && !dzp_staged) e = stage_bf16(dz_p, bf.pbf, n, stream);
+  const long long nv = (long long)B * L.dout.count();
+  cudaError_t e = dza_staged ? cudaSuccess : stage_rows(dz_a, bf.ybf, nv, L.co, bf.sp, stream);
+  if (e == cudaSuccess && !dzp_staged) e = stage_rows(dz_p, bf.pbf, nv, L.co, bf.sp, stream);
   if (e != cudaSuccess) return e;
-  return launch_tc3(L.act_d3, L.w_d3, L.co, L.ck3d, L.tz3d, nullptr, dx, L.din, L.ci, B,
+  return launch_tc3(L.act_d3, L.w_d3, L.kd, L.ck3d, L.tz3d, nullptr, dx, L.din, L.ci, B,
                     L.din.count() * L.ci, 0, 0, bf.err, stream, 2, &L.pw_d, &L.pa_d);
 }
 
@@ -2279,7 +2444,7 @@ cudaError_t bf16_stage_input(Bf16Net& bf, int layer, const float* z, int B, cuda
   if (!L.input_layer || !bf.zbf) return cudaErrorInvalidValue;
   const long long nvox = (long long)B * L.din.count();
   pad_input_kernel<<<(unsigned)ceil_div(nvox * 16, 256), 256, 0, stream>>>(z, bf.zbf, nvox,
-                                                                          L.ci_real);
+                                                                          L.ci_real, bf.sp);
   return cudaGetLastError();
 }
 
@@ -2293,13 +2458,13 @@ cudaError_t bf16_conv_fwd(Bf16Net& bf, int layer, const float* x, const float* b
   const TcLayer& L = bf.layers[layer];
   cudaError_t e = L.input_layer || (x_staged && bf.keep_inputs)
                       ? cudaSuccess
-                      : stage_bf16(x, L.xin, (long long)B * L.din.count() * L.ci, stream);
+                      : stage_rows(x, L.xin, (long long)B * L.din.count(), L.ci, bf.sp, stream);
   if (e != cudaSuccess) return e;
   if (L.ck3f)
-    return launch_tc3(L.act_f3, L.w_f3, L.ci, L.ck3f, L.tz3f, bias, y, L.dout, L.co, B,
+    return launch_tc3(L.act_f3, L.w_f3, L.kf, L.ck3f, L.tz3f, bias, y, L.dout, L.co, B,
                       L.dout.count() * L.co, bias_bs, 0, bf.err, stream);
   const TapPlan plan = conv_plan(L.k, L.s);
-  return launch_tc(L.act_f, L.w_f, plan, 1, L.ci, bias, y, L.dout, L.dout, L.co, B,
+  return launch_tc(L.act_f, L.w_f, plan, 1, L.kf, bias, y, L.dout, L.dout, L.co, B,
                    L.dout.count() * L.co, bias_bs, 0, bf.err, stream);
 }
 
@@ -2308,17 +2473,18 @@ cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, 
   const TcLayer& L = bf.layers[layer];
   if (!L.dgrad) return cudaErrorInvalidValue;
   cudaError_t e =
-      dy_staged ? cudaSuccess : stage_bf16(dy, bf.ybf, (long long)B * L.dout.count() * L.co, stream);
+      dy_staged ? cudaSuccess
+                : stage_rows(dy, bf.ybf, (long long)B * L.dout.count(), L.co, bf.sp, stream);
   if (e != cudaSuccess) return e;
   if (L.s == 2) {
     const Dims3 q{(L.din.z + 1) / 2, (L.din.y + 1) / 2, (L.din.x + 1) / 2};
-    return launch_tc(L.act_d, L.w_d, dgrad_s2_plan(), 8, L.co, nullptr, dx, L.din, q, L.ci, B,
+    return launch_tc(L.act_d, L.w_d, dgrad_s2_plan(), 8, L.kd, nullptr, dx, L.din, q, L.ci, B,
                      L.din.count() * L.ci, 0, accumulate, bf.err, stream);
   }
   if (L.ck3d)
-    return launch_tc3(L.act_d3, L.w_d3, L.co, L.ck3d, L.tz3d, nullptr, dx, L.din, L.ci, B,
+    return launch_tc3(L.act_d3, L.w_d3, L.kd, L.ck3d, L.tz3d, nullptr, dx, L.din, L.ci, B,
                       L.din.count() * L.ci, 0, accumulate, bf.err, stream);
-  return launch_tc(L.act_d, L.w_d, conv_plan(L.k, 1), 1, L.co, nullptr, dx, L.din, L.din, L.ci,
+  return launch_tc(L.act_d, L.w_d, conv_plan(L.k, 1), 1, L.kd, nullptr, dx, L.din, L.din, L.ci,
                    B, L.din.count() * L.ci, 0, accumulate, bf.err, stream);
 }
 

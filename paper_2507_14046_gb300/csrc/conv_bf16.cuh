@@ -17,10 +17,15 @@ struct TcLayer {
   CUtensorMap w_f;    // forward weights [B][Co][T][Ci] (BF16)
   CUtensorMap act_d;  // stride-1 data-gradient input (dy staged in BF16)
   CUtensorMap w_d;    // data-gradient weights [B][Ci][T][Co], taps reversed (BF16)
-  CUtensorMap act_wy; // weight-gradient dy (second BF16 staging buffer)
   CUtensorMap act_f3, w_f3, act_d3, w_d3;  // halo-box forms (3x3x3 stride 1)
-  CUtensorMap wg_dy3, wg_x3;  // halo-box weight gradient: dy (8 x 3 x tz+2), x (8 x 1 x tz)
+  // Weight-gradient operands in the box form of the kernel that runs the layer (halo box:
+  // dy 8 x 3 x tz+2, x 8 x 1 x tz; stride 2: x strided tile, dy tile; per tap: dy and x
+  // tiles) for the hi (index 0) and lo (index 1, split precision only) channel blocks of the
+  // staged dy and x, and a fused projection's dz_p column.
+  CUtensorMap wgy[2], wgx[2], wgp[2];
   int ci = 0, co = 0, k = 3, s = 1;
+  int kf = 0, kd = 0;             // K channels of the forward and data-gradient operands:
+                                  // ci and co times the operand blocks (Bf16Net::sp)
   Dims3 din{}, dout{};
   long long w_off = 0;            // weights of this conv in the FP32 theta arena
   long long wf_off = 0, wd_off = 0;  // offsets in the per-problem BF16 weight block
@@ -31,7 +36,6 @@ struct TcLayer {
   int proj = -1;                  // layer index of a 1x1 projection of the same input, fused
   bool projf = false, projd = false, projw = false;  // ... into forward / dgrad / wgrad
   CUtensorMap pw_f, pw_d, pa_d;   // projection: W_p, W_p^T and the dz_p tile box
-  CUtensorMap wg_p3;              // projection: dz_p column of the halo weight gradient
   bool wg3 = false;               // weight gradient by the halo-box kernel
   int wg_tz = 0;                  // its column depth (z voxels per K tile)
   bool wgs2 = false;              // stride-2 weight gradient on the tensor cores
@@ -52,6 +56,12 @@ struct Bf16Net {
   long long max_act = 0;          // elements per problem of the largest staged input
   int* err = nullptr;             // device error word (bounded waits that ran out)
   bool keep_inputs = false;       // a BF16 input copy per layer (else all share xbf)
+  // Operand blocks per staged value: 1 for BF16; 3 for the split BF16x3 precision, where a
+  // staged activation or gradient holds [hi | lo | hi] and the weights [hi | hi | lo] (each a
+  // block of the channel count), so the forward and data-gradient K loops add up
+  // x_hi w_hi + x_lo w_hi + x_hi w_lo, and the weight gradient runs three passes over the
+  // (dy, x) block pairs (hi, hi), (lo, hi), (hi, lo).
+  int sp = 1;
   std::vector<TcLayer> layers;
 };
 
@@ -98,12 +108,15 @@ cudaError_t bf16_conv_fwd(Bf16Net& bf, int layer, const float* x, const float* b
 cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, int B,
                             int accumulate, cudaStream_t stream, bool dy_staged = false);
 
-// Partial-sum rows (chunks of output voxels) of a tensor-core weight gradient.
+// Partial-sum rows (chunks of output voxels) of one pass of a tensor-core weight gradient,
+// and the passes (1, or 3 in split precision); a problem's rows are passes x chunks.
 long long bf16_wgrad_chunks(const Bf16Net& bf, int layer, int B);
-// Per-chunk partial sums part[b][chunk][Co*27*Ci + Co] (weights, then bias) of a layer with
-// .wgrad set; the caller adds the chunks (reduce_rows_f32).
+int bf16_wgrad_passes(const Bf16Net& bf, int layer);
+// Per-chunk partial sums part[b][pass][chunk][Co*27*Ci + Co] (weights, then bias) of a layer
+// with .wgrad set; the caller adds a problem's rows (reduce_rows_f32).
 // With dz_p (layer with projw): also the projection's partial sums
-// part_p[b][chunk][Co*Ci + Co] (its dz_p is staged here unless the fused data gradient did).
+// part_p[b][pass][chunk][Co*Ci + Co] (its dz_p is staged here unless the fused data gradient
+// did).
 // x_staged: the layer's forward has staged x into its kept input copy (keep_inputs) since x
 // last changed; dy_staged: its data gradient has just staged this dy (both skip a staging).
 cudaError_t bf16_conv_wgrad(Bf16Net& bf, int layer, const float* x, const float* dy,

@@ -11,14 +11,6 @@ namespace {
 // LayerNorm over the channel vector of a voxel.  A group of GP lanes (power of two)
 // serves one voxel; lane l holds channels 4l .. 4l+3 (C <= 4*GP, C % 4 == 0).
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ void store_bf16x4(__nv_bfloat16* p, float4 v) {
-  const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
-  uint2 u;
-  u.x = *reinterpret_cast<const uint32_t*>(&a);
-  u.y = *reinterpret_cast<const uint32_t*>(&b);
-  *reinterpret_cast<uint2*>(p) = u;
-}
-
 template <int GP>
 __device__ __forceinline__ float group_sum(float v) {
 #pragma unroll
@@ -37,7 +29,7 @@ __global__ void __launch_bounds__(256)
 ln_fwd_kernel(const float* __restrict__ z, const float* __restrict__ gamma,
               const float* __restrict__ resid, float* __restrict__ y, float* __restrict__ xhat,
               float* __restrict__ rstd, long long nvox, int C, int act, long long g_bs,
-              __nv_bfloat16* __restrict__ ybf) {
+              __nv_bfloat16* __restrict__ ybf, int sp) {
   const int b = blockIdx.y;
   const long long off = (long long)b * nvox * C;
   const float* beta = gamma + b * g_bs + C;
@@ -74,7 +66,7 @@ ln_fwd_kernel(const float* __restrict__ z, const float* __restrict__ gamma,
     o.w = o.w > 0.f ? o.w : kLeakySlope * o.w;
   }
   *reinterpret_cast<float4*>(y + off + vox * C + c) = o;
-  if (ybf) store_bf16x4(ybf + off + vox * C + c, o);  // the next convolution's BF16 input
+  if (ybf) stage_bf16x4(ybf + (off + vox * C) * sp, C, c, o, sp);  // next conv's BF16 input
   *reinterpret_cast<float4*>(xhat + off + vox * C + c) = xh;
   if (lane == 0) rstd[(long long)b * nvox + vox] = rs;
 }
@@ -87,7 +79,7 @@ ln_bwd_kernel(const float* __restrict__ dy, const float* __restrict__ act_out,
               const float* __restrict__ xhat, const float* __restrict__ rstd,
               const float* __restrict__ gamma, float* __restrict__ dz, float* __restrict__ dt,
               float* __restrict__ part, long long nvox, int C, long long g_bs,
-              __nv_bfloat16* __restrict__ dzbf, __nv_bfloat16* __restrict__ dtbf) {
+              __nv_bfloat16* __restrict__ dzbf, __nv_bfloat16* __restrict__ dtbf, int sp) {
   constexpr int kGroups = 256 / GP;
   __shared__ float red[kGroups][2 * 4 * GP];
   const int b = blockIdx.y;
@@ -119,7 +111,7 @@ ln_bwd_kernel(const float* __restrict__ dy, const float* __restrict__ act_out,
         d.w = a.w > 0.f ? d.w : kLeakySlope * d.w;
       }
       if (dt) *reinterpret_cast<float4*>(dt + off + vox * C + c) = d;
-      if (dtbf) store_bf16x4(dtbf + off + vox * C + c, d);
+      if (dtbf) stage_bf16x4(dtbf + (off + vox * C) * sp, C, c, d, sp);
     }
     const float4 dx = make_float4(d.x * g.x, d.y * g.y, d.z * g.z, d.w * g.w);
     const float s1 = group_sum<GP>(dx.x + dx.y + dx.z + dx.w) * inv_c;
@@ -132,7 +124,7 @@ ln_bwd_kernel(const float* __restrict__ dy, const float* __restrict__ act_out,
       o.z = rs * (dx.z - s1 - xh.z * s2);
       o.w = rs * (dx.w - s1 - xh.w * s2);
       *reinterpret_cast<float4*>(dz + off + vox * C + c) = o;
-      if (dzbf) store_bf16x4(dzbf + off + vox * C + c, o);
+      if (dzbf) stage_bf16x4(dzbf + (off + vox * C) * sp, C, c, o, sp);
       ag[0] += d.x * xh.x;
       ag[1] += d.y * xh.y;
       ag[2] += d.z * xh.z;
@@ -189,7 +181,7 @@ __device__ __forceinline__ AxisW axis_map(int o, int s_in, int s_out) {
 __global__ void up_concat_fwd_kernel(const float* __restrict__ low,
                                      const float* __restrict__ skip, float* __restrict__ cat,
                                      Dims3 dl, Dims3 dout, int Cu, int Cs,
-                                     __nv_bfloat16* __restrict__ catbf) {
+                                     __nv_bfloat16* __restrict__ catbf, int sp) {
   const int b = blockIdx.y;
   const int Ct = Cu + Cs, G = Ct / 4;
   const long long nout = dout.count();
@@ -227,7 +219,7 @@ __global__ void up_concat_fwd_kernel(const float* __restrict__ low,
         }
   }
   *reinterpret_cast<float4*>(cat + ((long long)b * nout + vox) * Ct + c) = val;
-  if (catbf) store_bf16x4(catbf + ((long long)b * nout + vox) * Ct + c, val);
+  if (catbf) stage_bf16x4(catbf + ((long long)b * nout + vox) * Ct * sp, Ct, c, val, sp);
 }
 
 // Factor-2 form (every output extent twice the input's): a thread takes one input voxel i
@@ -238,7 +230,7 @@ __global__ void up_concat_fwd_kernel(const float* __restrict__ low,
 __global__ void __launch_bounds__(256)
 up2_concat_fwd_kernel(const float* __restrict__ low, const float* __restrict__ skip,
                       float* __restrict__ cat, Dims3 dl, Dims3 dout, int Cu, int Cs,
-                      __nv_bfloat16* __restrict__ catbf) {
+                      __nv_bfloat16* __restrict__ catbf, int sp) {
   const int b = blockIdx.y;
   const int Ct = Cu + Cs, G = Ct / 4;
   const long long nl = dl.count();
@@ -251,11 +243,11 @@ up2_concat_fwd_kernel(const float* __restrict__ low, const float* __restrict__ s
   const int iy = rr % dl.y, iz = rr / dl.y;
   const long long nout = dout.count();
   float* C = cat + (long long)b * nout * Ct + c;
-  __nv_bfloat16* Cb = catbf ? catbf + (long long)b * nout * Ct + c : nullptr;
+  __nv_bfloat16* Cb = catbf ? catbf + (long long)b * nout * Ct * sp : nullptr;
   auto put = [&](int a, int bb, int cc, float4 v) {
     const long long o = ((long long)(2 * iz + a) * dout.y + (2 * iy + bb)) * dout.x + (2 * ix + cc);
     *reinterpret_cast<float4*>(C + o * Ct) = v;
-    if (Cb) store_bf16x4(Cb + o * Ct, v);
+    if (Cb) stage_bf16x4(Cb + o * Ct * sp, Ct, c, v, sp);
   };
   if (c >= Cu) {  // skip channels of the 8 outputs
     const float* S = skip + (long long)b * nout * Cs + (c - Cu);
@@ -806,13 +798,13 @@ int layernorm_bwd_blocks(long long nvox, int C) {
 cudaError_t layernorm_act_fwd_f32(const float* z, const float* gamma, const float* resid,
                                   float* y, float* xhat, float* rstd, int B, long long nvox,
                                   int C, int act, long long g_bs, cudaStream_t stream,
-                                  __nv_bfloat16* ybf) {
+                                  __nv_bfloat16* ybf, int sp) {
   if (C % 4 != 0 || C > 128) return cudaErrorInvalidValue;
   const int gp = lanes_for(C);
   dim3 grid((unsigned)ceil_div(nvox * gp, 256), B);
 #define D2IP_LNF(G) \
   ln_fwd_kernel<G><<<grid, 256, 0, stream>>>(z, gamma, resid, y, xhat, rstd, nvox, C, act, g_bs, \
-                                             ybf)
+                                             ybf, sp)
   switch (gp) {
     case 1: D2IP_LNF(1); break;
     case 2: D2IP_LNF(2); break;
@@ -829,13 +821,13 @@ cudaError_t layernorm_act_bwd_f32(const float* dy, const float* act_out, const f
                                   const float* rstd, const float* gamma, float* dz, float* dt,
                                   float* part, int B, long long nvox, int C, long long g_bs,
                                   cudaStream_t stream, __nv_bfloat16* dzbf,
-                                  __nv_bfloat16* dtbf) {
+                                  __nv_bfloat16* dtbf, int sp) {
   if (C % 4 != 0 || C > 128) return cudaErrorInvalidValue;
   const int gp = lanes_for(C);
   dim3 grid(layernorm_bwd_blocks(nvox, C), B);
 #define D2IP_LNB(G)                                                                          \
   ln_bwd_kernel<G><<<grid, 256, 0, stream>>>(dy, act_out, xhat, rstd, gamma, dz, dt, part, \
-                                             nvox, C, g_bs, dzbf, dtbf)
+                                             nvox, C, g_bs, dzbf, dtbf, sp)
   switch (gp) {
     case 1: D2IP_LNB(1); break;
     case 2: D2IP_LNB(2); break;
@@ -850,16 +842,17 @@ cudaError_t layernorm_act_bwd_f32(const float* dy, const float* act_out, const f
 
 cudaError_t upsample_concat_fwd_f32(const float* low, const float* skip, float* cat, int B,
                                     Dims3 dlow, Dims3 dout, int Cu, int Cs,
-                                    cudaStream_t stream, __nv_bfloat16* catbf) {
+                                    cudaStream_t stream, __nv_bfloat16* catbf, int sp) {
   if (Cu % 4 || Cs % 4) return cudaErrorInvalidValue;
   const long long total = dout.count() * ((Cu + Cs) / 4);
   dim3 grid((unsigned)ceil_div(total, 256), B);
   if (dout.x == 2 * dlow.x && dout.y == 2 * dlow.y && dout.z == 2 * dlow.z) {
     dim3 g2((unsigned)ceil_div(dlow.count() * ((Cu + Cs) / 4), 256), B);
-    up2_concat_fwd_kernel<<<g2, 256, 0, stream>>>(low, skip, cat, dlow, dout, Cu, Cs, catbf);
+    up2_concat_fwd_kernel<<<g2, 256, 0, stream>>>(low, skip, cat, dlow, dout, Cu, Cs, catbf,
+                                                  sp);
     return cudaGetLastError();
   }
-  up_concat_fwd_kernel<<<grid, 256, 0, stream>>>(low, skip, cat, dlow, dout, Cu, Cs, catbf);
+  up_concat_fwd_kernel<<<grid, 256, 0, stream>>>(low, skip, cat, dlow, dout, Cu, Cs, catbf, sp);
   return cudaGetLastError();
 }
 

@@ -166,7 +166,7 @@ struct Builder {
     L.din = c->dims[lvl_in];
     L.dout = conv_out_dims(L.din, k, s);
     L.w_off = off;
-    if (c->precision == D2IP_BF16)
+    if (c->precision != D2IP_FP32)
       L.tc = input && ci < 16 ? bf16_add_input_layer(c->bf, ci, co, L.din, off)
                               : bf16_add_layer(c->bf, ci, co, k, s, L.din, off);
     const long long fan = (long long)ci * k * k * k;
@@ -223,6 +223,7 @@ void build_plan(d2ip_ctx* c) {
   c->table.clear();
   c->bf = Bf16Net{};
   c->bf.keep_inputs = true;  // layer inputs stay staged in BF16 from forward to backward
+  c->bf.sp = c->precision == D2IP_BF16X3 ? 3 : 1;
   Builder b{c};
   const auto& w = c->w;
   c->stem.conv = b.conv(c->c_in, w[0], 3, 1, 0, /*input=*/true);
@@ -273,9 +274,11 @@ bool co1_layer(const ConvL& L) {
   return L.k == 1 && L.s == 1 && L.co == 1 && conv1x1_co1_supported(L.ci);
 }
 
+// Partial-sum rows per problem of a layer's weight gradient (chunks x operand passes).
 long long wgrad_rows(const d2ip_ctx* c, const ConvL& L) {
   if (co1_layer(L)) return conv1x1_co1_blocks(L.din.count());
-  if (tc_wgrad(c, L)) return bf16_wgrad_chunks(c->bf, L.tc, c->B);
+  if (tc_wgrad(c, L))
+    return bf16_wgrad_chunks(c->bf, L.tc, c->B) * bf16_wgrad_passes(c->bf, L.tc);
   return conv3d_wgrad_chunks(L.din, L.k, L.s);
 }
 
@@ -383,7 +386,7 @@ void layout_buffers(d2ip_ctx* c, Carve& cv) {
   c->status = cv.take<int>(1);
   c->nprev = cv.take<int>(1);
   c->reg_part = cv.take<double>((long long)B * tv4d_blocks(nv(0)));
-  if (c->precision == D2IP_BF16) {
+  if (c->precision != D2IP_FP32) {
     long long max_act = 0;
     for (int l = 0; l < c->L; ++l)
       max_act = std::max(max_act, nv(l) * (w[l] + (l + 1 < c->L ? w[l + 1] : 0)));
@@ -403,7 +406,7 @@ d2ip_status ensure_arena(d2ip_ctx* c) {
   Carve real{static_cast<char*>(p), 0, false};
   layout_buffers(c, real);
   CK(cudaMemsetAsync(p, 0, dry.used, c->stream));
-  if (c->precision == D2IP_BF16) CK(bf16_finalize(c->bf, c->B));
+  if (c->precision != D2IP_FP32) CK(bf16_finalize(c->bf, c->B));
   return D2IP_OK;
 }
 
@@ -451,7 +454,7 @@ struct Launcher {
   const ConvL* ybf_owner = nullptr;
   const void* pbf_owner = nullptr;
   __nv_bfloat16* bf_in(const ConvL* L) {
-    return L && L->tc >= 0 && c->precision == D2IP_BF16 ? bf16_input_buffer(c->bf, L->tc)
+    return L && L->tc >= 0 && c->precision != D2IP_FP32 ? bf16_input_buffer(c->bf, L->tc)
                                                         : nullptr;
   }
   bool take_staged(const ConvL& L) {
@@ -461,7 +464,7 @@ struct Launcher {
     return true;
   }
   bool tc_dy_consumer(const ConvL* L) {
-    return L && L->tc >= 0 && c->precision == D2IP_BF16 &&
+    return L && L->tc >= 0 && c->precision != D2IP_FP32 &&
            (c->bf.layers[L->tc].dgrad || c->bf.layers[L->tc].wgrad);
   }
   void ok(cudaError_t x) {
@@ -521,7 +524,7 @@ struct Launcher {
     beg(D2IP_KCLASS_LN_FWD, 4.0 * nv * (L.c * (resid ? 4 : 3) + 1));
     __nv_bfloat16* ybf = bf_in(consumer);
     ok(layernorm_act_fwd_f32(z, c->theta + L.g_off, resid, y, xh, rs, c->B,
-                             c->dims[lvl].count(), L.c, 1, c->Pp, c->stream, ybf));
+                             c->dims[lvl].count(), L.c, 1, c->Pp, c->stream, ybf, c->bf.sp));
     if (ybf) staged_x.push_back(consumer);
     fin();
   }
@@ -535,7 +538,7 @@ struct Launcher {
     __nv_bfloat16* dzbf = tc_dy_consumer(dz_consumer) ? c->bf.ybf : nullptr;
     __nv_bfloat16* dtbf = dt && dt_owner && c->bf.pbf ? c->bf.pbf : nullptr;
     ok(layernorm_act_bwd_f32(dy, aout, xh, rs, c->theta + L.g_off, dz, dt, c->ws, c->B, nv,
-                             L.c, c->Pp, c->stream, dzbf, dtbf));
+                             L.c, c->Pp, c->stream, dzbf, dtbf, c->bf.sp));
     if (dzbf) ybf_owner = dz_consumer;
     if (dtbf) pbf_owner = dt_owner;
     ok(reduce_rows_f32(c->ws, G(L.g_off), c->B, layernorm_bwd_blocks(nv, L.c), 2 * L.c, c->Pp,
@@ -579,7 +582,8 @@ struct Launcher {
       ok(c->fr.forward(fr_run()));
       return;
     }
-    if (c->precision == D2IP_BF16) ok(bf16_prepare_weights(c->bf, c->theta, c->B, c->Pp, c->stream));
+    if (c->precision != D2IP_FP32)
+      ok(bf16_prepare_weights(c->bf, c->theta, c->B, c->Pp, c->stream));
     staged_x.clear();
     unit_fwd(c->stem, &c->enc[0].a);
     res_fwd(c->enc[0], c->L > 1 ? &c->down[1].conv : nullptr);
@@ -596,7 +600,7 @@ struct Launcher {
       beg(D2IP_KCLASS_UP_FWD, bytes);
       __nv_bfloat16* catbf = bf_in(&c->dec[l].a);
       ok(upsample_concat_fwd_f32(cur, c->enc[l].out, c->lb[l].cat, c->B, c->dims[l + 1],
-                                 c->dims[l], c->w[l + 1], c->w[l], c->stream, catbf));
+                                 c->dims[l], c->w[l + 1], c->w[l], c->stream, catbf, c->bf.sp));
       if (catbf) staged_x.push_back(&c->dec[l].a);
       fin();
       res_fwd(c->dec[l], nullptr);
@@ -804,7 +808,7 @@ d2ip_status ready(d2ip_ctx* c) {
 d2ip_status check_status(d2ip_ctx* c) {
   int st = 0, tc = 0;
   CK(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  if (c->precision == D2IP_BF16 && c->bf.err)
+  if (c->precision != D2IP_FP32 && c->bf.err)
     CK(cudaMemcpyAsync(&tc, c->bf.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (tc) {
@@ -1047,10 +1051,10 @@ d2ip_status d2ip_set_network(d2ip_ctx* c, int levels, const int* widths, int c_i
     if (widths[l] <= 0 || widths[l] % 4 != 0 || widths[l] > 128)
       return fail(c, D2IP_ERR_BAD_SHAPE, "each width must be a positive multiple of 4, <= 128");
   if (c_in <= 0 || c_in > 256) return fail(c, D2IP_ERR_BAD_SHAPE, "c_in must be 1..256");
-  if (precision != D2IP_FP32 && precision != D2IP_BF16)
-    return fail(c, D2IP_ERR_BAD_ARG, "precision must be D2IP_FP32 or D2IP_BF16");
-  if (precision == D2IP_BF16 && !bf16_network_supported(levels, widths, c_in))
-    return fail(c, D2IP_ERR_BAD_SHAPE, "BF16 path needs c_in and widths that are multiples of 8");
+  if (precision != D2IP_FP32 && precision != D2IP_BF16 && precision != D2IP_BF16X3)
+    return fail(c, D2IP_ERR_BAD_ARG, "precision must be D2IP_FP32, D2IP_BF16 or D2IP_BF16X3");
+  if (precision != D2IP_FP32 && !bf16_network_supported(levels, widths, c_in))
+    return fail(c, D2IP_ERR_BAD_SHAPE, "BF16 paths need widths that are multiples of 16");
   if (batch < 1 || batch > 4096) return fail(c, D2IP_ERR_BAD_ARG, "batch must be 1..4096");
   cudaSetDevice(c->device);
   free_arena(c);

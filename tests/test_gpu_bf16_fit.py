@@ -1,10 +1,13 @@
-"""The BF16 tensor-core precision of the whole DIP iteration against the FP64 oracle.
+"""The plain BF16 tensor-core precision of the whole DIP iteration against the FP64 oracle.
 
 Convolutions whose channel counts are multiples of 16 run on tcgen05 with BF16 operands and
 FP32 accumulation (the stem's 8 input channels are zero-padded to 16; the 1-channel tail
-stays FP32); J products read a BF16 copy of J; every other step is FP32.  BF16 rounds each operand to 8 significant bits (relative 2^-9), so the
-per-iteration agreement is about 1e-2, not the FP32 path's 1e-5; the reconstruction error
-(ERR) of a fitted frame is compared with the oracle's."""
+stays FP32); J products read a BF16 copy of J; every other step is FP32.  BF16 rounds each
+operand to 8 significant bits (relative 2^-9), so the per-iteration agreement is about 1e-2,
+not the FP32 path's 1e-5.  Any operand precision below about 15 bits (BF16, and TF32 too)
+carries the 100-step fit onto a different Adam trajectory, which ends 3e-3 to 4e-3 away from
+the oracle's ERR: this precision is bounded at 2e-2 here.  The 1e-3 ERR target is met by the
+split precision D2IP_BF16X3 (tests/test_gpu_bf16x3.py)."""
 import numpy as np
 import pytest
 
