@@ -53,9 +53,10 @@ typedef int d2ip_status;
 #define D2IP_BF16X3 2 /* split BF16: convolutions on tcgen05 tensor cores with every operand
                        v carried as two BF16 numbers hi = bf16(v), lo = bf16(v - hi) (16
                        significant bits); each product sums hi*hi + lo*hi + hi*lo in FP32
-                       (three times the MMAs of D2IP_BF16).  J products in FP32 from the FP32
-                       J.  Plain BF16 operands (8 bits) and TF32 (11) both carry the Adam
-                       trajectory of a 100-step fit away from the FP64 one; 16 bits follow it */
+                       (three times the MMAs of D2IP_BF16).  J products read J as the same
+                       hi + lo pair, added in FP32.  Plain BF16 operands (8 bits) and TF32
+                       (11) both carry the Adam trajectory of a 100-step fit away from the
+                       FP64 one; 16 bits follow it */
 
 /* parameter-table kinds */
 #define D2IP_PARAM_CONV_W 0
@@ -132,8 +133,8 @@ d2ip_status d2ip_plan_param_table(int net, int X, int Y, int Z, int levels, cons
 
 /* Copy J (m x n, n = X*Y*Z) into the context.  normalize_cols != 0 scales every column to
  * unit l2 norm with the norm accumulated in FP64 (Eq. 1, "normalized" sensitivity); a zero
- * column is left as is.  J may be host or device memory.  m <= 6400; with D2IP_BF16 also m a
- * multiple of 4 and at most 1024 (D2IP_ERR_BAD_SHAPE otherwise). */
+ * column is left as is.  J may be host or device memory.  m <= 6400; with the BF16 precisions
+ * also m a multiple of 4 and at most 1024 (D2IP_ERR_BAD_SHAPE otherwise). */
 d2ip_status d2ip_load_J(d2ip_ctx* ctx, const float* J, int m, int n, int normalize_cols);
 /* The FP64 column norms used by the last d2ip_load_J (n values; host or device memory). */
 d2ip_status d2ip_get_colnorms(d2ip_ctx* ctx, double* out);

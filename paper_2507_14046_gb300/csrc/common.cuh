@@ -108,15 +108,19 @@ int jmul_chunks(int n);
 cudaError_t jmul_residual_f32(const float* J, const float* x, const float* dv, float* r,
                               float* part, int B, int m, int n, long long x_bs,
                               cudaStream_t stream);
-// The same products reading a BF16 copy of J (FP32 accumulation).
+// The same products reading a BF16 copy of J (FP32 accumulation); with Jlo, J is the sum of
+// two BF16 copies hi + lo (the split form, 16 significant bits) added in FP32.
 cudaError_t jmul_residual_bf16(const __nv_bfloat16* J, const float* x, const float* dv, float* r,
                                float* part, int B, int m, int n, long long x_bs,
-                               cudaStream_t stream);
+                               cudaStream_t stream, const __nv_bfloat16* Jlo = nullptr);
 cudaError_t jtmul_bf16(const __nv_bfloat16* J, const float* r, float* g, float scale, int B,
-                       int m, int n, long long g_bs, cudaStream_t stream);
+                       int m, int n, long long g_bs, cudaStream_t stream,
+                       const __nv_bfloat16* Jlo = nullptr);
 cudaError_t convert_bf16(const float* x, __nv_bfloat16* y, long long n, cudaStream_t stream);
-// The BF16 forms of the J products take J transposed: Jt[n][m] (BF16), m a multiple of 4.
-cudaError_t transpose_bf16(const float* J, __nv_bfloat16* Jt, int m, int n, cudaStream_t stream);
+// The BF16 forms of the J products take J transposed: Jt[n][m] (BF16), m a multiple of 4;
+// Jlo (optional) receives bf16(J - Jt) transposed.
+cudaError_t transpose_bf16(const float* J, __nv_bfloat16* Jt, int m, int n, cudaStream_t stream,
+                           __nv_bfloat16* Jlo = nullptr);
 // Per-device kernel attributes (opt-in shared memory); call once per device before launches.
 cudaError_t prepare_pointwise_kernels();
 cudaError_t jtmul_f32(const float* J, const float* r, float* g, float scale, int B, int m,

@@ -904,14 +904,16 @@ cudaError_t jmul_residual_f32(const float* J, const float* x, const float* dv, f
   return jmul_impl(J, x, dv, r, part, B, m, n, x_bs, stream);
 }
 
-// ---- BF16 path: J stored transposed, Jt[n][m] (BF16) -------------------------------
+// ---- BF16 paths: J stored transposed, Jt[n][m] (BF16) ------------------------------
 // r[b][i] = sum_j Jt[j][i] x[b][j] - dv[b][i]: a block takes kTCols columns j for up to kTB
 // problems; thread t owns the row pairs i = 2 p, 2 p + 1 (p = t + 256 s) and adds j in order;
-// per-block partial sums, then the chunks in order (jmul_final_kernel).
-template <int SLOTS>
+// per-block partial sums, then the chunks in order (jmul_final_kernel).  SPLIT: J is the sum
+// of two BF16 copies, Jt (hi) + Jlo (lo = bf16(J - hi)), added in FP32 before the product.
+template <int SLOTS, bool SPLIT>
 __global__ void __launch_bounds__(256)
-jmul_t_kernel(const __nv_bfloat16* __restrict__ Jt, const float* __restrict__ x,
-              float* __restrict__ part, int B, int m, int n, long long x_bs) {
+jmul_t_kernel(const __nv_bfloat16* __restrict__ Jt, const __nv_bfloat16* __restrict__ Jlo,
+              const float* __restrict__ x, float* __restrict__ part, int B, int m, int n,
+              long long x_bs) {
   __shared__ __align__(16) float xs[kTB][kTCols];
   const int chunk = blockIdx.x, b0 = blockIdx.y * kTB;
   const int nb = B - b0 < kTB ? B - b0 : kTB;
@@ -932,10 +934,12 @@ jmul_t_kernel(const __nv_bfloat16* __restrict__ Jt, const float* __restrict__ x,
   // (columns past n carry x = 0 and read row n - 1, which exists)
   for (int jj = 0; jj < nj; jj += 4) {
     const __nv_bfloat162* rows[4];
+    const __nv_bfloat162* rlo[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int jr = j0 + jj + u < n ? j0 + jj + u : n - 1;
       rows[u] = reinterpret_cast<const __nv_bfloat162*>(Jt + (long long)jr * m);
+      if (SPLIT) rlo[u] = reinterpret_cast<const __nv_bfloat162*>(Jlo + (long long)jr * m);
     }
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
@@ -943,7 +947,13 @@ jmul_t_kernel(const __nv_bfloat16* __restrict__ Jt, const float* __restrict__ x,
       if (pi >= np) break;
       float2 a[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = __bfloat1622float2(rows[u][pi]);
+      for (int u = 0; u < 4; ++u) {
+        a[u] = __bfloat1622float2(rows[u][pi]);
+        if (SPLIT) {
+          const float2 l = __bfloat1622float2(rlo[u][pi]);
+          a[u].x += l.x, a[u].y += l.y;
+        }
+      }
 #pragma unroll
       for (int q = 0; q < kTB; ++q) {
         const float4 xv = *reinterpret_cast<const float4*>(&xs[q][jj]);
@@ -968,16 +978,30 @@ jmul_t_kernel(const __nv_bfloat16* __restrict__ Jt, const float* __restrict__ x,
 
 // g[b][j] = scale sum_i Jt[j][i] r[b][i]: a thread per column j (kJtRows per block) keeps
 // the kTB problems' sums; the block stages r and, chunk by chunk along i, a tile of Jt rows
-// (coalesced) in shared memory; i is added in order.
+// (coalesced) in shared memory; i is added in order.  SPLIT: the tile holds hi + lo in FP32.
 constexpr int kJtRows = 128, kJtChunk = 64;
 
+template <bool SPLIT>
+struct JtTile {  // element type and padded row of the shared-memory J tile
+  using T = __nv_bfloat16;
+  static constexpr int kLd = kJtChunk + 8;  // 144 bytes
+};
+template <>
+struct JtTile<true> {
+  using T = float;
+  static constexpr int kLd = kJtChunk + 4;  // 272 bytes
+};
+
+template <bool SPLIT>
 __global__ void __launch_bounds__(kJtRows)
-jtmul_t_kernel(const __nv_bfloat16* __restrict__ Jt, const float* __restrict__ r,
-               float* __restrict__ g, float scale, int B, int m, int n, long long g_bs) {
-  extern __shared__ float rs[];  // [kTB][m], then two Jt tiles
-  constexpr int kLd = kJtChunk + 8;  // padded row (bf16): 144 bytes
-  constexpr int kPer = kJtRows * (kJtChunk / 4) / kJtRows;  // 8-byte pieces per thread
-  __nv_bfloat16* jt0 = reinterpret_cast<__nv_bfloat16*>(rs + kTB * m);  // [2][kJtRows][kLd]
+jtmul_t_kernel(const __nv_bfloat16* __restrict__ Jt, const __nv_bfloat16* __restrict__ Jlo,
+               const float* __restrict__ r, float* __restrict__ g, float scale, int B, int m,
+               int n, long long g_bs) {
+  extern __shared__ float rs[];  // [kTB][m], then two J tiles
+  using TT = typename JtTile<SPLIT>::T;
+  constexpr int kLd = JtTile<SPLIT>::kLd;
+  constexpr int kPer = kJtRows * (kJtChunk / 4) / kJtRows;  // 4-element pieces per thread
+  TT* jt0 = reinterpret_cast<TT*>(rs + kTB * m);  // [2][kJtRows][kLd]
   const int b0 = blockIdx.y * kTB;
   const int nb = B - b0 < kTB ? B - b0 : kTB;
   for (int e = threadIdx.x; e < kTB * m; e += blockDim.x)
@@ -989,23 +1013,37 @@ jtmul_t_kernel(const __nv_bfloat16* __restrict__ Jt, const float* __restrict__ r
   for (int q = 0; q < kTB; ++q) acc[q] = 0.f;
   // tile of chunk i0: rows j0 .. j0 + 127, columns i0 .. i0 + 63, 8-byte pieces; the next
   // chunk's pieces are loaded into registers while the current tile is used
-  uint2 pre[kPer];
+  uint2 pre[kPer], prel[kPer];
   auto load = [&](int i0) {
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const int e = threadIdx.x + kJtRows * k;
       const int row = e / (kJtChunk / 4), c4 = (e % (kJtChunk / 4)) * 4;
-      pre[k] = (j0 + row < n && i0 + c4 < m)
-                   ? *reinterpret_cast<const uint2*>(Jt + (j0 + row) * m + i0 + c4)
-                   : make_uint2(0u, 0u);
+      const bool in = j0 + row < n && i0 + c4 < m;
+      pre[k] = in ? *reinterpret_cast<const uint2*>(Jt + (j0 + row) * m + i0 + c4)
+                  : make_uint2(0u, 0u);
+      if (SPLIT)
+        prel[k] = in ? *reinterpret_cast<const uint2*>(Jlo + (j0 + row) * m + i0 + c4)
+                     : make_uint2(0u, 0u);
     }
   };
-  auto store = [&](__nv_bfloat16* jt) {
+  auto f4 = [](uint2 u) {
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+  };
+  auto store = [&](TT* jt) {
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const int e = threadIdx.x + kJtRows * k;
       const int row = e / (kJtChunk / 4), c4 = (e % (kJtChunk / 4)) * 4;
-      *reinterpret_cast<uint2*>(jt + row * kLd + c4) = pre[k];
+      if constexpr (SPLIT) {
+        const float4 h = f4(pre[k]), l = f4(prel[k]);
+        *reinterpret_cast<float4*>(jt + row * kLd + c4) =
+            make_float4(h.x + l.x, h.y + l.y, h.z + l.z, h.w + l.w);
+      } else {
+        *reinterpret_cast<uint2*>(jt + row * kLd + c4) = pre[k];
+      }
     }
   };
   load(0);
@@ -1016,15 +1054,17 @@ jtmul_t_kernel(const __nv_bfloat16* __restrict__ Jt, const float* __restrict__ r
     __syncthreads();  // tile `buf` complete; the other one no longer read
     const bool more = i0 + kJtChunk < m;
     if (more) load(i0 + kJtChunk);
-    const __nv_bfloat16* jt = jt0 + buf * (kJtRows * kLd);
+    const TT* jt = jt0 + buf * (kJtRows * kLd);
     for (int c = 0; c < ni; c += 4) {
-      const uint2 u = *reinterpret_cast<const uint2*>(jt + threadIdx.x * kLd + c);
-      const float2 a01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
-      const float2 a23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+      float4 a;
+      if constexpr (SPLIT)
+        a = *reinterpret_cast<const float4*>(jt + threadIdx.x * kLd + c);
+      else
+        a = f4(*reinterpret_cast<const uint2*>(jt + threadIdx.x * kLd + c));
 #pragma unroll
       for (int q = 0; q < kTB; ++q) {
         const float4 rv = *reinterpret_cast<const float4*>(rs + q * m + i0 + c);
-        acc[q] = fmaf(a01.x, rv.x, fmaf(a01.y, rv.y, fmaf(a23.x, rv.z, fmaf(a23.y, rv.w, acc[q]))));
+        acc[q] = fmaf(a.x, rv.x, fmaf(a.y, rv.y, fmaf(a.z, rv.z, fmaf(a.w, rv.w, acc[q]))));
       }
     }
     if (more) store(jt0 + (buf ^ 1) * (kJtRows * kLd));
@@ -1037,9 +1077,10 @@ jtmul_t_kernel(const __nv_bfloat16* __restrict__ Jt, const float* __restrict__ r
   }
 }
 
-// J [m][n] FP32 -> Jt [n][m] BF16 through 32 x 32 shared-memory tiles.
+// J [m][n] FP32 -> Jt [n][m] BF16 through 32 x 32 shared-memory tiles; Jlo (optional)
+// receives bf16(J - Jt), the low part of the split form.
 __global__ void transpose_bf16_kernel(const float* __restrict__ J, __nv_bfloat16* __restrict__ Jt,
-                                      int m, int n) {
+                                      __nv_bfloat16* __restrict__ Jlo, int m, int n) {
   __shared__ float t[32][33];
   const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
   for (int k = threadIdx.y; k < 32; k += blockDim.y) {
@@ -1049,20 +1090,32 @@ __global__ void transpose_bf16_kernel(const float* __restrict__ J, __nv_bfloat16
   __syncthreads();
   for (int k = threadIdx.y; k < 32; k += blockDim.y) {
     const int j = j0 + k, i = i0 + threadIdx.x;
-    if (i < m && j < n) Jt[(long long)j * m + i] = __float2bfloat16_rn(t[threadIdx.x][k]);
+    if (i < m && j < n) {
+      const float v = t[threadIdx.x][k];
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      Jt[(long long)j * m + i] = h;
+      if (Jlo) Jlo[(long long)j * m + i] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
   }
 }
 
 cudaError_t jmul_residual_bf16(const __nv_bfloat16* Jt, const float* x, const float* dv, float* r,
                                float* part, int B, int m, int n, long long x_bs,
-                               cudaStream_t stream) {
+                               cudaStream_t stream, const __nv_bfloat16* Jlo) {
   if (m % 4 || m > 1024) return cudaErrorInvalidValue;
   const int nch = (int)ceil_div(n, kTCols);
   dim3 grid((unsigned)nch, (unsigned)ceil_div(B, kTB));
-  if (m / 2 <= 256)
-    jmul_t_kernel<1><<<grid, 256, 0, stream>>>(Jt, x, part, B, m, n, x_bs);
-  else
-    jmul_t_kernel<2><<<grid, 256, 0, stream>>>(Jt, x, part, B, m, n, x_bs);
+  if (m / 2 <= 256) {
+    if (Jlo)
+      jmul_t_kernel<1, true><<<grid, 256, 0, stream>>>(Jt, Jlo, x, part, B, m, n, x_bs);
+    else
+      jmul_t_kernel<1, false><<<grid, 256, 0, stream>>>(Jt, Jlo, x, part, B, m, n, x_bs);
+  } else {
+    if (Jlo)
+      jmul_t_kernel<2, true><<<grid, 256, 0, stream>>>(Jt, Jlo, x, part, B, m, n, x_bs);
+    else
+      jmul_t_kernel<2, false><<<grid, 256, 0, stream>>>(Jt, Jlo, x, part, B, m, n, x_bs);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   jmul_final_many_kernel<<<(unsigned)ceil_div((long long)B * m, 32), 256, 0, stream>>>(
@@ -1086,17 +1139,23 @@ cudaError_t jtmul_f32(const float* J, const float* r, float* g, float scale, int
 }
 
 cudaError_t jtmul_bf16(const __nv_bfloat16* Jt, const float* r, float* g, float scale, int B,
-                       int m, int n, long long g_bs, cudaStream_t stream) {
-  const size_t smem = (size_t)kTB * m * sizeof(float) + 2 * (size_t)kJtRows * (kJtChunk + 8) * 2;
+                       int m, int n, long long g_bs, cudaStream_t stream,
+                       const __nv_bfloat16* Jlo) {
+  const size_t tile = Jlo ? (size_t)JtTile<true>::kLd * 4 : (size_t)JtTile<false>::kLd * 2;
+  const size_t smem = (size_t)kTB * m * sizeof(float) + 2 * (size_t)kJtRows * tile;
   if (m % 4 || smem > (size_t)kJtmulMaxSmem) return cudaErrorInvalidValue;
   dim3 grid((unsigned)ceil_div(n, kJtRows), (unsigned)ceil_div(B, kTB));
-  jtmul_t_kernel<<<grid, kJtRows, smem, stream>>>(Jt, r, g, scale, B, m, n, g_bs);
+  if (Jlo)
+    jtmul_t_kernel<true><<<grid, kJtRows, smem, stream>>>(Jt, Jlo, r, g, scale, B, m, n, g_bs);
+  else
+    jtmul_t_kernel<false><<<grid, kJtRows, smem, stream>>>(Jt, Jlo, r, g, scale, B, m, n, g_bs);
   return cudaGetLastError();
 }
 
-cudaError_t transpose_bf16(const float* J, __nv_bfloat16* Jt, int m, int n, cudaStream_t stream) {
+cudaError_t transpose_bf16(const float* J, __nv_bfloat16* Jt, int m, int n, cudaStream_t stream,
+                           __nv_bfloat16* Jlo) {
   dim3 grid((unsigned)ceil_div(n, 32), (unsigned)ceil_div(m, 32));
-  transpose_bf16_kernel<<<grid, dim3(32, 8), 0, stream>>>(J, Jt, m, n);
+  transpose_bf16_kernel<<<grid, dim3(32, 8), 0, stream>>>(J, Jt, Jlo, m, n);
   return cudaGetLastError();
 }
 
@@ -1115,7 +1174,10 @@ cudaError_t prepare_pointwise_kernels() {
   cudaError_t e = cudaFuncSetAttribute(jtmul_kernel<float>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kJtmulMaxSmem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(jtmul_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(jtmul_t_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kJtmulMaxSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(jtmul_t_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               kJtmulMaxSmem);
 }
 

@@ -104,6 +104,7 @@ struct d2ip_ctx {
   int hist_cap = 0;
   float* J = nullptr;
   __nv_bfloat16* Jbf = nullptr;  // BF16 copy of the normalised J, transposed [n][m] (BF16)
+  __nv_bfloat16* Jlo = nullptr;  // its low part bf16(J - Jbf) (split precision)
   float* jpart = nullptr;  // column-chunk partial sums of J x
   double* colnorm = nullptr;
   size_t j_bytes = 0;
@@ -617,13 +618,13 @@ struct Launcher {
   }
   void data_term(bool training) {
     const long long n = c->n();
-    const bool jb16 = c->precision == D2IP_BF16;
-    const double jb = (jb16 ? 2.0 : 4.0) * c->m * (double)n,
+    const bool jb16 = c->precision != D2IP_FP32;  // transposed BF16 J (hi, + lo when split)
+    const double jb = (c->precision == D2IP_BF16 ? 2.0 : 4.0) * c->m * (double)n,
                  vb = 4.0 * c->B * ((double)n + 2.0 * c->m);
     beg(D2IP_KCLASS_JMUL, jb + vb);
     if (jb16)
       ok(jmul_residual_bf16(c->Jbf, c->dsigma, c->dv, c->r, c->jpart, c->B, c->m, (int)n, n,
-                            c->stream));
+                            c->stream, c->Jlo));
     else
       ok(jmul_residual_f32(c->J, c->dsigma, c->dv, c->r, c->jpart, c->B, c->m, (int)n, n,
                            c->stream));
@@ -632,7 +633,7 @@ struct Launcher {
       beg(D2IP_KCLASS_JTMUL, jb + vb);
       if (jb16)
         ok(jtmul_bf16(c->Jbf, c->r, c->gds, 2.0f / (float)c->m, c->B, c->m, (int)n, n,
-                      c->stream));
+                      c->stream, c->Jlo));
       else
         ok(jtmul_f32(c->J, c->r, c->gds, 2.0f / (float)c->m, c->B, c->m, (int)n, n, c->stream));
       fin();
@@ -1020,6 +1021,7 @@ d2ip_status d2ip_destroy(d2ip_ctx* c) {
   if (c->dv) cudaFree(c->dv);
   if (c->jpart) cudaFree(c->jpart);
   if (c->Jbf) cudaFree(c->Jbf);
+  if (c->Jlo) cudaFree(c->Jlo);
   if (c->seq_resid) cudaFree(c->seq_resid);
   if (c->hist) cudaFree(c->hist);
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -1154,8 +1156,8 @@ d2ip_status d2ip_load_J(d2ip_ctx* c, const float* J, int m, int n, int normalize
     return fail(c, D2IP_ERR_BAD_SHAPE, "J must be m x (X*Y*Z)");
   if ((size_t)8 * m * sizeof(float) > 200 * 1024)
     return fail(c, D2IP_ERR_BAD_SHAPE, "m too large for the adjoint kernel (max 6400)");
-  if (c->precision == D2IP_BF16 && (m % 4 != 0 || m > 1024))
-    return fail(c, D2IP_ERR_BAD_SHAPE, "the BF16 path needs m a multiple of 4, at most 1024");
+  if (c->precision != D2IP_FP32 && (m % 4 != 0 || m > 1024))
+    return fail(c, D2IP_ERR_BAD_SHAPE, "the BF16 paths need m a multiple of 4, at most 1024");
   CK(cudaSetDevice(c->device));
   d2ip_status s = ensure_arena(c);
   if (s) return s;
@@ -1168,7 +1170,8 @@ d2ip_status d2ip_load_J(d2ip_ctx* c, const float* J, int m, int n, int normalize
     if (c->dv) cudaFree(c->dv);
     if (c->jpart) cudaFree(c->jpart);
     if (c->Jbf) cudaFree(c->Jbf);
-    c->Jbf = nullptr;
+    if (c->Jlo) cudaFree(c->Jlo);
+    c->Jbf = c->Jlo = nullptr;
     c->J = nullptr;
     c->colnorm = nullptr;
     c->r = c->dv = c->jpart = nullptr;
@@ -1178,8 +1181,10 @@ d2ip_status d2ip_load_J(d2ip_ctx* c, const float* J, int m, int n, int normalize
         cudaMalloc(&c->r, sizeof(float) * m * c->B) != cudaSuccess ||
         cudaMalloc(&c->dv, sizeof(float) * m * c->B) != cudaSuccess ||
         cudaMalloc(&c->jpart, sizeof(float) * jmul_chunks(n) * (size_t)m * c->B) != cudaSuccess ||
-        (c->precision == D2IP_BF16 &&
-         cudaMalloc(&c->Jbf, sizeof(__nv_bfloat16) * (size_t)m * n) != cudaSuccess))
+        (c->precision != D2IP_FP32 &&
+         cudaMalloc(&c->Jbf, sizeof(__nv_bfloat16) * (size_t)m * n) != cudaSuccess) ||
+        (c->precision == D2IP_BF16X3 &&
+         cudaMalloc(&c->Jlo, sizeof(__nv_bfloat16) * (size_t)m * n) != cudaSuccess))
       return fail(c, D2IP_ERR_OOM, "device allocation of J failed");
     c->j_bytes = bytes;
     c->m = m;
@@ -1190,7 +1195,8 @@ d2ip_status d2ip_load_J(d2ip_ctx* c, const float* J, int m, int n, int normalize
   } else {
     CK(cudaMemsetAsync(c->colnorm, 0, sizeof(double) * n, c->stream));
   }
-  if (c->precision == D2IP_BF16) CK(transpose_bf16(c->J, c->Jbf, m, (int)n, c->stream));
+  if (c->precision != D2IP_FP32)
+    CK(transpose_bf16(c->J, c->Jbf, m, (int)n, c->stream, c->Jlo));
   CK(cudaStreamSynchronize(c->stream));
   c->j_ready = true;
   return D2IP_OK;

@@ -62,7 +62,7 @@ def run(w, iters: int = 3000, upws: int = 1800, first: int = 450, every: int = 1
     # the random reconstruction task of UPWS: two random ellipsoids through the same J
     task = synth.ellipsoid_phantom(w.grid, synth.random_ellipsoids(w.grid, w.seed + 1, 0))
     dV0 = synth.measurements(J, task[None, :], w.seed + 1)[0]
-    prec = B.D2IP_BF16 if precision == "bf16" else B.D2IP_FP32
+    prec = {"fp32": B.D2IP_FP32, "bf16": B.D2IP_BF16, "bf16x3": B.D2IP_BF16X3}[precision]
 
     def ctx(batch):
         c = B.Context(w.grid, w.levels, w.widths, w.c_in, prec, batch, device=device,
