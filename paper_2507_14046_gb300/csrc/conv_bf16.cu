@@ -1137,6 +1137,11 @@ wgrad_s2_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
 // plus a block of ones, whose column gives sum(dy) per window: the centre tap's is the bias
 // partial.  A CTA adds the products of a run of tiles for NKX x taps (all three when the
 // accumulators fit in TMEM, else one per grid row) and writes one partial-sum row.
+// NKX = 0, the packed form: the x tap moves to the x operand instead, dW[co][t][ci] =
+// sum_v dy[v + (0, 1 - ky, 1 - kz)][co] x[v + (kx - 1, 0, 0)][ci], so one unshifted dy box
+// serves all 27 taps and B holds the three x-shifted columns side by side plus the ones:
+// N = 3 Ci + CKB, the columns of x tap kx at kx * Ci.  Per 16-voxel K step that is G MMAs of
+// width N instead of 3 G of width Ci + CKB, at nearly the same issue cost per MMA.
 // ------------------------------------------------------------------------------------
 constexpr int kWg3MaxStages = 6;
 
@@ -1171,7 +1176,9 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
   constexpr int kG = (9 + kTpm - 1) / kTpm;        // MMAs per x tap
   constexpr uint32_t kAtomA = 8 * CKA * 2;         // 8 rows of dy
   constexpr uint32_t kAtomB = 8 * CKB * 2;
-  const int N = Ci + CKB;                          // + the ones block
+  constexpr bool kPack = NKX == 0;                 // the three x taps in N
+  constexpr int kNq = kPack ? 1 : NKX;             // dy boxes (accumulator sets) per stage
+  const int N = (kPack ? 3 * Ci : Ci) + CKB;       // + the ones block
   const int nb = Ci / CKB;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -1179,14 +1186,14 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
   __shared__ __align__(8) uint64_t full_bar[kWg3MaxStages], empty_bar[kWg3MaxStages], done_bar;
   __shared__ uint32_t tmem_base_s;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int chunk = blockIdx.x, kx0 = blockIdx.y * NKX, b = blockIdx.z;
+  const int chunk = blockIdx.x, kx0 = blockIdx.y * kNq, b = blockIdx.z;
   const int tile0 = chunk * gm.tiles_per_chunk;
   const int tile1 = min(tile0 + gm.tiles_per_chunk, gm.ntiles);
   const int ksteps = max(tile1 - tile0, 0);
   const int nst = gm.nst;
   // the projection's products go with the centre x tap: D_p[co][ci] = sum_u dz_p[u][co] x[u][ci]
-  const bool proj = gm.proj && kx0 <= 1 && 1 < kx0 + NKX;
-  const uint32_t pcol = (uint32_t)(NKX * kG * N);  // its accumulator
+  const bool proj = gm.proj && (kPack || (kx0 <= 1 && 1 < kx0 + NKX));
+  const uint32_t pcol = (uint32_t)(kNq * kG * N);  // its accumulator
   for (int s = 0; s < nst; ++s) {
     uint32_t* ones = reinterpret_cast<uint32_t*>(smem + (size_t)s * gm.stage + gm.ones_off);
     for (int i = threadIdx.x; i < (int)(gm.b_box / 4); i += blockDim.x) ones[i] = 0x3F803F80u;
@@ -1214,8 +1221,8 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
   const uint32_t tmem = tmem_base_s;
 
   if (warp == 0 && lane == 0) {  // TMA producer
-    const uint32_t tx_bytes =
-        (uint32_t)NKX * gm.a_box + (uint32_t)nb * gm.b_box + (proj ? gm.p_box : 0u);
+    const uint32_t tx_bytes = (uint32_t)kNq * gm.a_box +
+                              (uint32_t)(kPack ? 3 * nb : nb) * gm.b_box + (proj ? gm.p_box : 0u);
     int k = 0;
     for (; k < ksteps; ++k) {
       const int s = k % nst, round = k / nst;
@@ -1230,11 +1237,19 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
       const uint32_t base = smem_u32(smem + (size_t)s * gm.stage);
       const uint32_t fb = smem_u32(&full_bar[s]);
       mbar_expect_tx(fb, tx_bytes);
-      for (int q = 0; q < NKX; ++q)
-        tma_load_5d(base + (uint32_t)q * gm.a_box, &tm_dy, 0, x0 + 1 - (kx0 + q), y0 - 1, z0 - 1,
-                    b, fb);
-      for (int c = 0; c < nb; ++c)
-        tma_load_5d(base + gm.b_off + (uint32_t)c * gm.b_box, &tm_x, c * CKB, x0, y0, z0, b, fb);
+      if (kPack) {  // the unshifted dy box, then x at x offsets -1, 0, +1
+        tma_load_5d(base, &tm_dy, 0, x0, y0 - 1, z0 - 1, b, fb);
+        for (int kx = 0; kx < 3; ++kx)
+          for (int c = 0; c < nb; ++c)
+            tma_load_5d(base + gm.b_off + (uint32_t)(kx * nb + c) * gm.b_box, &tm_x, c * CKB,
+                        x0 + kx - 1, y0, z0, b, fb);
+      } else {
+        for (int q = 0; q < NKX; ++q)
+          tma_load_5d(base + (uint32_t)q * gm.a_box, &tm_dy, 0, x0 + 1 - (kx0 + q), y0 - 1,
+                      z0 - 1, b, fb);
+        for (int c = 0; c < nb; ++c)
+          tma_load_5d(base + gm.b_off + (uint32_t)c * gm.b_box, &tm_x, c * CKB, x0, y0, z0, b, fb);
+      }
       if (proj) tma_load_5d(base + gm.p_off, &tm_p, 0, x0, y0, z0, b, fb);
     }
     drain_loads(full_bar, nst, k, err);
@@ -1260,7 +1275,7 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
       const uint32_t phi = (uint32_t)(p0 >> 32);
       for (int kk = 0; kk < gm.tz / 2; ++kk) {  // K = 16 voxels = z offsets 2kk, 2kk + 1
 #pragma unroll
-        for (int q = 0; q < NKX; ++q)
+        for (int q = 0; q < kNq; ++q)
 #pragma unroll
           for (int g = 0; g < kG; ++g) {
             constexpr int kLast = 9 - kTpm;
@@ -1297,40 +1312,45 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
   const int pl = m / Co, co = m % Co;
   const long long row = (long long)Co * 27 * ci_out + Co;  // the first ci_out channels
   float* prow = part + ((long long)b * gm.rows_b + chunk) * row;
-  for (int q = 0; q < NKX; ++q)
+  for (int q = 0; q < kNq; ++q)
     for (int g = 0; g < kG; ++g) {
       const int s0 = g * kTpm < 9 - kTpm ? g * kTpm : 9 - kTpm;
       const int p = s0 + pl;                      // window p <-> tap 3 kz + ky = 8 - p
       const bool keep = p >= g * kTpm && p < 9;   // rows new to this MMA
-      const int tq = 8 - p, kz = tq / 3, ky = tq % 3, kx = kx0 + q;
-      const int t = kz * 9 + ky * 3 + kx;
-      float* out = prow + ((long long)co * 27 + t) * ci_out;
+      const int tq = 8 - p, kz = tq / 3, ky = tq % 3;
       const uint32_t col = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((q * kG + g) * N);
-      for (int c0 = 0; c0 < Ci; c0 += 16) {
-        uint32_t r[16];
-        if (ok) tmem_ld16(col + (uint32_t)c0, r);
-        if (keep) {
+      for (int xi = 0; xi < (kPack ? 3 : 1); ++xi) {  // packed: x tap xi at columns xi * Ci
+        const int kx = kPack ? xi : kx0 + q;
+        const int t = kz * 9 + ky * 3 + kx;
+        float* out = prow + ((long long)co * 27 + t) * ci_out;
+        const uint32_t cx = col + (uint32_t)(kPack ? xi * Ci : 0);
+        for (int c0 = 0; c0 < Ci; c0 += 16) {
+          uint32_t r[16];
+          if (ok) tmem_ld16(cx + (uint32_t)c0, r);
+          if (keep) {
 #pragma unroll
-          for (int j = 0; j < 16; j += 4)
-            if (c0 + j < ci_out)
-              *reinterpret_cast<float4*>(out + c0 + j) =
-                ok ? make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                 __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]))
-                   : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int j = 0; j < 16; j += 4)
+              if (c0 + j < ci_out)
+                *reinterpret_cast<float4*>(out + c0 + j) =
+                  ok ? make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                   __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]))
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
         }
       }
       uint32_t r[16];
-      if (ok) tmem_ld16(col + (uint32_t)Ci, r);
-      if (keep && t == 13)
+      if (ok) tmem_ld16(col + (uint32_t)(kPack ? 3 * Ci : Ci), r);  // the ones column
+      if (keep && tq == 4 && (kPack || kx0 + q == 1))  // the centre tap (t = 13): the bias
         prow[(long long)Co * 27 * ci_out + co] = ok && gm.bias_on ? __uint_as_float(r[0]) : 0.f;
     }
   if (proj && warp * 32 < Co) {  // rows co < Co of the projection accumulator
     const long long prow_n = (long long)Co * Ci + Co;
     float* pp = part_p + ((long long)b * gm.rows_b + chunk) * prow_n;
     const uint32_t col = tmem + ((uint32_t)(warp * 32) << 16) + pcol;
+    const uint32_t cx = col + (uint32_t)(kPack ? Ci : 0);  // packed: the unshifted x columns
     for (int c0 = 0; c0 < Ci; c0 += 16) {
       uint32_t r[16];
-      if (ok) tmem_ld16(col + (uint32_t)c0, r);
+      if (ok) tmem_ld16(cx + (uint32_t)c0, r);
       if (m < Co) {
 #pragma unroll
         for (int j = 0; j < 16; j += 4)
@@ -1341,7 +1361,7 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
       }
     }
     uint32_t r[16];
-    if (ok) tmem_ld16(col + (uint32_t)Ci, r);
+    if (ok) tmem_ld16(col + (uint32_t)(kPack ? 3 * Ci : Ci), r);
     if (m < Co) pp[(long long)Co * Ci + m] = ok && gm.bias_on ? __uint_as_float(r[0]) : 0.f;
   }
   tc_fence_before();
@@ -2048,8 +2068,9 @@ int wg3_tz(int Z) {
   return best;
 }
 
-// Geometry of the halo weight gradient; nst == 0 when the layer does not fit it.
-Wg3Geom wg3_geom(const TcLayer& L, int B, bool proj) {
+// Geometry of the halo weight gradient in the packed form (pack) or with x taps in separate
+// accumulators; nst == 0 when the layer does not fit that form.
+Wg3Geom wg3_geom_form(const TcLayer& L, int B, bool proj, bool pack) {
   Wg3Geom g{};
   if (L.k != 3 || L.s != 1 || (L.co != 16 && L.co != 32 && L.co != 64)) return g;
   const int ckb = chunk_for(L.ci);
@@ -2061,15 +2082,23 @@ Wg3Geom wg3_geom(const TcLayer& L, int B, bool proj) {
     return t;
   };
   const int extra = proj ? 1 : 0;  // the projection's accumulator
-  g.nkx = (3 * G + extra) * N <= 512 ? 3 : 1;
-  if ((G + extra) * N > 512) return g;
+  const int Np = 3 * L.ci + ckb;   // packed: the three x taps in N
+  if (pack) {
+    if (Np > 256 || (G + extra) * Np > 512) return g;
+    g.nkx = 0;
+    g.tmem_cols = (uint32_t)pow2((G + extra) * Np);
+  } else {
+    g.nkx = (3 * G + extra) * N <= 512 ? 3 : 1;
+    if ((G + extra) * N > 512) return g;
+    g.tmem_cols = (uint32_t)pow2((g.nkx * G + extra) * N);
+  }
   g.proj = extra;
-  g.tmem_cols = (uint32_t)pow2((g.nkx * G + extra) * N);
   g.tz = L.wg_tz > 0 ? L.wg_tz : wg3_tz(L.dout.z);
   g.a_box = (uint32_t)(8 * 3 * (g.tz + 2) * L.co * 2);
   g.b_box = (uint32_t)(8 * g.tz * ckb * 2);
-  g.b_off = (uint32_t)((g.nkx * g.a_box + 1023) / 1024 * 1024);
-  g.ones_off = g.b_off + (uint32_t)(L.ci / ckb) * g.b_box;
+  const int a_boxes = g.nkx == 0 ? 1 : g.nkx, x_boxes = (g.nkx == 0 ? 3 : 1) * (L.ci / ckb);
+  g.b_off = (uint32_t)((a_boxes * g.a_box + 1023) / 1024 * 1024);
+  g.ones_off = g.b_off + (uint32_t)x_boxes * g.b_box;
   g.p_box = proj ? (uint32_t)(8 * g.tz * L.co * 2) : 0u;
   g.p_off = (g.ones_off + g.b_box + 1023) / 1024 * 1024;
   g.stage = (g.p_off + g.p_box + 1023) / 1024 * 1024;
@@ -2081,11 +2110,17 @@ Wg3Geom wg3_geom(const TcLayer& L, int B, bool proj) {
   const size_t smem = (size_t)nst * g.stage + 1024;
   const int cps = std::max(1, std::min((int)(233472 / (smem + 1024)), (int)(512 / g.tmem_cols)));
   const long long slots = (long long)sm_count() * cps;
-  const long long want = std::max(1LL, slots / ((3 / g.nkx) * (long long)B));
+  const long long want = std::max(1LL, slots / ((g.nkx ? 3 / g.nkx : 1) * (long long)B));
   g.tiles_per_chunk = (int)ceil_div(g.ntiles, std::min<long long>(want, g.ntiles));
   g.nchunks = (int)ceil_div(g.ntiles, g.tiles_per_chunk);
   g.nst = nst;
   return g;
+}
+
+// The packed form where it fits (fewer, wider MMAs), else the per-x-tap accumulators.
+Wg3Geom wg3_geom(const TcLayer& L, int B, bool proj) {
+  const Wg3Geom g = wg3_geom_form(L, B, proj, true);
+  return g.nst > 0 ? g : wg3_geom_form(L, B, proj, false);
 }
 
 template <int CKA, int CKB>
@@ -2096,6 +2131,9 @@ cudaError_t wg3_attr() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(wgrad_tc3_kernel<CKA, CKB, 3>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWg3SmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(wgrad_tc3_kernel<CKA, CKB, 0>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWg3SmemMax);
   return e;
 }
 
@@ -2103,9 +2141,12 @@ template <int CKA, int CKB>
 void launch_wg3(const TcLayer& L, const Wg3Geom& g, const CUtensorMap& my, const CUtensorMap& mx,
                 const CUtensorMap& mp, float* part, float* part_p, int B, int* err,
                 cudaStream_t st) {
-  dim3 grid((unsigned)g.nchunks, (unsigned)(3 / g.nkx), (unsigned)B);
+  dim3 grid((unsigned)g.nchunks, (unsigned)(g.nkx ? 3 / g.nkx : 1), (unsigned)B);
   const size_t smem = (size_t)g.nst * g.stage + 1024;
-  if (g.nkx == 3)
+  if (g.nkx == 0)
+    wgrad_tc3_kernel<CKA, CKB, 0><<<grid, 128, smem, st>>>(my, mx, mp, part, part_p, L.dout,
+                                                           L.ci, L.ci_real, g, err);
+  else if (g.nkx == 3)
     wgrad_tc3_kernel<CKA, CKB, 3><<<grid, 128, smem, st>>>(my, mx, mp, part, part_p, L.dout,
                                                            L.ci, L.ci_real, g, err);
   else
