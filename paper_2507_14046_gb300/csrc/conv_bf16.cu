@@ -79,6 +79,35 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// Shared -> global tensor store (or element-wise add into global) of one box, in the bulk
+// async group of the issuing thread.
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap* map, uint32_t src, int c0, int c1,
+                                             int c2, int c3, int c4, bool add) {
+  if (add)
+    asm volatile(
+        "cp.reduce.async.bulk.tensor.5d.global.shared::cta.add.tile.bulk_group"
+        " [%0, {%2, %3, %4, %5, %6}], [%1];" ::"l"(reinterpret_cast<uint64_t>(map)),
+        "r"(src), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+        : "memory");
+  else
+    asm volatile(
+        "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group"
+        " [%0, {%2, %3, %4, %5, %6}], [%1];" ::"l"(reinterpret_cast<uint64_t>(map)),
+        "r"(src), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// the bulk groups committed before the last `n` have finished reading shared memory
+template <int n>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(n) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -158,6 +187,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Zero 16 columns of this warp's 32 TMEM lanes (then tcgen05.wait::st before handing over).
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+      "%1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+      "r"(0u)
+      : "memory");
 }
 
 constexpr int kErrProducer = 1, kErrMma = 2, kErrEpilogue = 4;
@@ -513,6 +551,14 @@ __device__ __forceinline__ bool epi_all(bool p) {
 // y_p = W_p x + bias_p, from one more MMA per slice on the centre window of the kx = 1 stage.
 // mode 2 (data gradient of such a block): dx = conv^T(dz) + W_p^T dz_p, the second term from
 // one more stage per channel chunk (the dz_p box of the tile, no halo).
+// pack: the three kz taps of one (ky, kx) in one MMA of width 3N.  The layer's weights are
+// then stored with ky and kz swapped, so the B box of an x tap holds, for each ky, the kz
+// taps 0, 1, 2 as adjacent N-row blocks.  The window of input slice s (= zz + kz) and ky
+// feeds output slices s, s - 1, s - 2 through the three column blocks of one MMA written at
+// column (TZ + 1 - s) N: slice zz's accumulator sits at (TZ + 1 - zz) N, and blocks that fall
+// outside [0, TZ) land in spare columns.  Every MMA accumulates; the epilogue warps zero an
+// accumulator buffer before handing it back (and both at the start).  9 TZ MMAs of width N
+// per stage become 3 (TZ + 2) of width 3N, at nearly the same issue cost each.
 struct P3Args {
   const float* bias;
   float* out;
@@ -520,8 +566,10 @@ struct P3Args {
   float* out_p;
   int* err;
   Dims3 dout;
-  int N, Np, nchunks, tiles_x, tiles_y, tiles_z, B, accumulate, nst, mode;
+  int N, Np, nchunks, tiles_x, tiles_y, tiles_z, B, accumulate, nst, mode, pack;
   uint32_t ring_bytes, stage_bytes;
+  uint32_t slice_bytes;  // one epilogue staging slice (128 rows x max(N, Np) FP32); two follow
+                         // the ring, then the bias of the current problem
   long long out_bs, bias_bs, outp_bs, biasp_bs;
 };
 
@@ -529,7 +577,8 @@ template <int CK, int TZ>
 __global__ void __launch_bounds__(192, 1)
 conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
                  const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorMap tm_a2,
-                 const __grid_constant__ P3Args g) {
+                 const __grid_constant__ CUtensorMap tm_out,
+                 const __grid_constant__ CUtensorMap tm_outp, const __grid_constant__ P3Args g) {
   constexpr uint32_t kRowB = CK * 2;
   constexpr uint32_t a_bytes = (uint32_t)(8 * 18 * (TZ + 2)) * kRowB;
   const int N = g.N, Np = g.mode == 1 ? g.Np : 0;
@@ -539,7 +588,10 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  float* stg = reinterpret_cast<float*>(smem + g.ring_bytes);  // epilogue staging slice
+  // epilogue: two staging slices (each box of w channels stored as the swizzled rows the
+  // output tensor map expects), then the bias of the current problem
+  float* stg = reinterpret_cast<float*>(smem + g.ring_bytes);
+  float* sbias = reinterpret_cast<float*>(smem + g.ring_bytes + 2 * g.slice_bytes);
   __shared__ __align__(8) uint64_t full_bar[kP3Max], empty_bar[kP3Max], tfull[2], tempty[2],
       done_bar;
   __shared__ uint32_t tmem_base_s;
@@ -549,7 +601,10 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
   const int ntile = blockIdx.x < total ? (total - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int ksteps = g.nchunks * spc;
   const int nst = g.nst;
-  const int acc_cols = TZ * (N + Np);  // one accumulator buffer: TZ slices of N (+ Np)
+  const bool pack = g.pack != 0;
+  // one accumulator buffer: TZ slices of N (+ Np); packed: TZ + 4 blocks of N (+ TZ Np)
+  const int acc_cols = pack ? (TZ + 4) * N + TZ * Np : TZ * (N + Np);
+  const int pbase = pack ? (TZ + 4) * N : TZ * N;  // projection accumulators
   const int cols = 2 * acc_cols;
   const uint32_t tmem_cols = cols <= 32 ? 32u : cols <= 64 ? 64u : cols <= 128 ? 128u
                                                 : cols <= 256 ? 256u : 512u;
@@ -624,11 +679,15 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       const uint32_t idesc = instr_desc(N), idesc_p = instr_desc(Np > 0 ? Np : 16);
+      const uint32_t idesc3 = instr_desc(pack ? 3 * N : N);
       int k = 0;
       bool good = true;
       for (int i = 0; i < ntile && good; ++i) {
         const int buf = i & 1;
-        if (i >= 2 && !mbar_wait(smem_u32(&tempty[buf]), ((i >> 1) - 1) & 1)) {
+        // packed: the epilogue zeroed both buffers once at the start (phase 0 of tempty)
+        const bool wait_buf = pack || i >= 2;
+        const uint32_t par = pack ? (uint32_t)((i >> 1) & 1) : (uint32_t)(((i >> 1) - 1) & 1);
+        if (wait_buf && !mbar_wait(smem_u32(&tempty[buf]), par)) {
           atomicOr(g.err, kErrMma);
           break;
         }
@@ -653,9 +712,40 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
             for (int zz = 0; zz < TZ; ++zz)
 #pragma unroll
               for (int kk = 0; kk < CK / 16; ++kk)
-                mma_lh(dbase + (uint32_t)(zz * N),
+                mma_lh(dbase + (uint32_t)((pack ? TZ + 1 - zz : zz) * N),
                        alo + (uint32_t)(zz * 16 * (8 * kRowB >> 4) + kk * 2), ahi,
                        blo + (uint32_t)(kk * 2), bhi, idesc);
+          } else if (pack) {
+            const uint64_t b0 = smem_desc<CK>(a_addr + a_bytes);
+            const uint32_t blo = (uint32_t)b0, bhi = (uint32_t)(b0 >> 32);
+            const uint32_t bt = b_tap >> 4;
+            // input slice s, row offset ky: B = the kz taps 0..2 of (ky, kx), rows [3 ky N,
+            // 3 ky N + 3 N); D = the three slices s, s - 1, s - 2 at column (TZ + 1 - s) N
+#pragma unroll
+            for (int sl = 0; sl < TZ + 2; ++sl)
+#pragma unroll
+              for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                for (int kk = 0; kk < CK / 16; ++kk) {
+                  constexpr uint32_t kAtom = 8 * kRowB >> 4;
+                  const uint32_t ao = (uint32_t)((sl * 18 + ky) * kAtom + kk * 2);
+                  const uint32_t bo = (uint32_t)(3 * ky) * bt + (uint32_t)(kk * 2);
+                  mma_lh(dbase + (uint32_t)((TZ + 1 - sl) * N), alo + ao, ahi, blo + bo, bhi,
+                         idesc3);
+                }
+            if (Np > 0 && kx == 1) {  // projection: the centre window (ky = kz = 1) per slice
+              const uint64_t p0 = smem_desc<CK>(a_addr + a_bytes + 9 * b_tap);
+              const uint32_t plo = (uint32_t)p0, phi = (uint32_t)(p0 >> 32);
+#pragma unroll
+              for (int zz = 0; zz < TZ; ++zz)
+#pragma unroll
+                for (int kk = 0; kk < CK / 16; ++kk) {
+                  constexpr uint32_t kAtom = 8 * kRowB >> 4;
+                  const uint32_t ao = (uint32_t)(((zz + 1) * 18 + 1) * kAtom + kk * 2);
+                  mma_lh(dbase + (uint32_t)(pbase + zz * Np), alo + ao, ahi,
+                         plo + (uint32_t)(kk * 2), phi, idesc_p);
+                }
+            }
           } else {
             const uint64_t b0 = smem_desc<CK>(a_addr + a_bytes);
             const uint32_t blo = (uint32_t)b0, bhi = (uint32_t)(b0 >> 32);
@@ -705,7 +795,20 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
     const int quad = warp & 3;
     const int m = quad * 32 + lane;  // tile row = y * 8 + x
     const int tid = threadIdx.x - 64;
-    const Dims3 dout = g.dout;
+    const uint32_t lanes = (uint32_t)(quad * 32) << 16;
+    if (pack) {  // both accumulator buffers start at zero
+      for (int c = 0; c < cols; c += 16) tmem_zero16(tmem + lanes + (uint32_t)c);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      tc_fence_before();
+      mbar_arrive(smem_u32(&tempty[0]));
+      mbar_arrive(smem_u32(&tempty[1]));
+    }
+    // Per output slice: TMEM -> (+ bias) -> shared staging slice, then one thread stores the
+    // slice with TMA (a reduce-add when accumulating); out-of-grid rows are clipped by TMA.
+    // Staging rows are the output map's swizzled layout: a box of w channels (w = 32: 128-byte
+    // rows, 128-byte swizzle; w = 16: 64-byte rows, 64-byte swizzle), 16-byte chunk j of row
+    // m at j ^ (m % 8) or j ^ ((m / 2) % 4) -- conflict-free for eight consecutive rows.
+    int slice = 0, bias_b = -1;
     for (int i = 0; i < ntile; ++i) {
       const int buf = i & 1;
       const bool ok = epi_all(mbar_wait(smem_u32(&tfull[buf]), (i >> 1) & 1));
@@ -721,75 +824,67 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
       tile /= g.tiles_x;
       const int y0 = (tile % g.tiles_y) * 16;
       const int z0 = (tile / g.tiles_y) * TZ;
+      if (b != bias_b) {  // this problem's biases (zero when none)
+        epi_sync();
+        for (int c = tid; c < N + Np; c += 128) {
+          const float* bb = c < N ? g.bias : g.bias_p;
+          const long long bs = c < N ? g.bias_bs : g.biasp_bs;
+          sbias[c] = bb ? bb[(long long)b * bs + (c < N ? c : c - N)] : 0.f;
+        }
+        epi_sync();
+        bias_b = b;
+      }
       for (int part = 0; part < (Np > 0 ? 2 : 1); ++part) {
         const int nc = part ? Np : N;
-        const int ld = nc + 4;  // padded staging row (floats)
-        const int n4 = nc / 4;
-        const float* bb = part ? (g.bias_p ? g.bias_p + (long long)b * g.biasp_bs : nullptr)
-                               : (g.bias ? g.bias + (long long)b * g.bias_bs : nullptr);
-        float* dst = part ? g.out_p + (long long)b * g.outp_bs : g.out + (long long)b * g.out_bs;
-        const int accum = part ? 0 : g.accumulate;
+        const int w = nc % 32 == 0 ? 32 : 16;  // channels per stored box
+        const float* bsm = sbias + (part ? N : 0);
+        const CUtensorMap* om = part ? &tm_outp : &tm_out;
+        const bool add = !part && g.accumulate;
         for (int zz = 0; zz < TZ; ++zz) {
-          const int col0 = buf * acc_cols + (part ? TZ * N + zz * Np : zz * N);
+          const int col0 =
+              buf * acc_cols + (part ? pbase + zz * Np : (pack ? TZ + 1 - zz : zz) * N);
+          float* S = stg + (slice & 1) * (g.slice_bytes / 4);
           for (int c0 = 0; c0 < nc; c0 += 16) {
             uint32_t r[16];
-            tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(col0 + c0), r);
+            tmem_ld16(tmem + lanes + (uint32_t)(col0 + c0), r);
+            float* row = S + (c0 / w) * (128 * w) + m * w;  // box c0 / w, row m
+            const int sw = w == 32 ? (m & 7) : ((m >> 1) & 3);
 #pragma unroll
             for (int j = 0; j < 16; j += 4) {
-              float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                     __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-              if (bb) {
-                v.x += __ldg(bb + c0 + j), v.y += __ldg(bb + c0 + j + 1);
-                v.z += __ldg(bb + c0 + j + 2), v.w += __ldg(bb + c0 + j + 3);
-              }
-              *reinterpret_cast<float4*>(stg + m * ld + c0 + j) = v;
+              const float4 bv = *reinterpret_cast<const float4*>(bsm + c0 + j);
+              const float4 v = make_float4(__uint_as_float(r[j]) + bv.x,
+                                           __uint_as_float(r[j + 1]) + bv.y,
+                                           __uint_as_float(r[j + 2]) + bv.z,
+                                           __uint_as_float(r[j + 3]) + bv.w);
+              const int chunk = ((c0 % w) + j) / 4;
+              *reinterpret_cast<float4*>(row + (chunk ^ sw) * 4) = v;
             }
           }
           if (zz == TZ - 1 && part == (Np > 0 ? 1 : 0)) {  // buffer fully read: hand it back
+            if (pack) {  // zeroed first: every MMA of the next tile accumulates
+              for (int c = 0; c < acc_cols; c += 16)
+                tmem_zero16(tmem + lanes + (uint32_t)(buf * acc_cols + c));
+              asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            }
             tc_fence_before();
             mbar_arrive(smem_u32(&tempty[buf]));
           }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // staging -> TMA
           epi_sync();
-          const int oz = z0 + zz;
-          if (oz < dout.z && !accum) {
-            for (int e = tid; e < 128 * n4; e += 128) {
-              const int mv = e / n4, c4 = e % n4;
-              const int ox = x0 + mv % 8, oy = y0 + mv / 8;
-              if (ox >= dout.x || oy >= dout.y) continue;
-              const float4 v = *reinterpret_cast<const float4*>(stg + mv * ld + c4 * 4);
-              *(reinterpret_cast<float4*>(
-                    dst + (((long long)oz * dout.y + oy) * dout.x + ox) * nc) + c4) = v;
+          if (tid == 0) {
+            if (z0 + zz < g.dout.z) {
+              for (int k = 0; k < nc / w; ++k)
+                tma_store_5d(om, smem_u32(S + k * (128 * w)), k * w, x0, y0, z0 + zz, b, add);
             }
-          } else if (oz < dout.z) {  // accumulate: four loads of the old values in flight
-            for (int e0 = tid; e0 < 128 * n4; e0 += 4 * 128) {
-              float4 v[4], p[4];
-              float4* o[4];
-              bool on[4];
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const int e = e0 + 128 * u;
-                const int mv = e / n4, c4 = e % n4;
-                const int ox = x0 + mv % 8, oy = y0 + mv / 8;
-                on[u] = e < 128 * n4 && ox < dout.x && oy < dout.y;
-                o[u] = reinterpret_cast<float4*>(
-                           dst + (((long long)oz * dout.y + oy) * dout.x + ox) * nc) + c4;
-                if (on[u]) {
-                  v[u] = *reinterpret_cast<const float4*>(stg + mv * ld + c4 * 4);
-                  p[u] = *o[u];
-                }
-              }
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                if (!on[u]) continue;
-                v[u].x += p[u].x, v[u].y += p[u].y, v[u].z += p[u].z, v[u].w += p[u].w;
-                *o[u] = v[u];
-              }
-            }
+            bulk_commit();
+            bulk_wait_read<1>();  // the other staging slice is free again
           }
+          ++slice;
           epi_sync();
         }
       }
     }
+    if (tid == 0) bulk_wait_all();  // every store has landed before the CTA may exit
   }
   __syncwarp();
   // TMEM is freed only after the MMA thread's last commit showed every issued MMA complete;
@@ -1403,12 +1498,18 @@ __global__ void f32_to_bf16_rows_kernel(const float* __restrict__ x, __nv_bfloat
   stage_bf16x4(y + v * C * sp, C, c, val, sp);
 }
 
+// Stored tap index of tap t of a 27-tap layer whose halo form packs kz into N: ky and kz
+// swapped, so the kz taps of one (ky, kx) are adjacent in the B box of x tap kx.
+__device__ __forceinline__ int packed_tap(int t, int perm) {
+  return perm ? ((t / 3) % 3) * 9 + (t / 9) * 3 + t % 3 : t;
+}
+
 // Forward weights [t][co][ci] and data-gradient weights [T-1-t][ci][co] of one layer (tap
 // major), for every problem of the batch.
 __global__ void weights_bf16_kernel(const float* __restrict__ theta, __nv_bfloat16* __restrict__ wb,
                                     long long Pp, long long wstride, long long w_off,
                                     long long wf_off, long long wd_off, int ci, int ci_real,
-                                    int co, int T, int dgrad) {
+                                    int co, int T, int dgrad, int permf, int permd) {
   const int b = blockIdx.y;
   const long long n = (long long)co * T * ci;  // padded input channels
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1419,8 +1520,9 @@ __global__ void weights_bf16_kernel(const float* __restrict__ theta, __nv_bfloat
   const float v = c < ci_real ? theta[(long long)b * Pp + w_off + r * ci_real + c] : 0.f;
   const __nv_bfloat16 h = __float2bfloat16_rn(v);  // W[o][t][c]
   __nv_bfloat16* base = wb + (long long)b * wstride;
-  base[wf_off + ((long long)t * co + o) * ci + c] = h;                     // [t][co][ci]
-  if (dgrad) base[wd_off + ((long long)(T - 1 - t) * ci + c) * co + o] = h;  // [26-t][ci][co]
+  base[wf_off + ((long long)packed_tap(t, permf) * co + o) * ci + c] = h;  // [t][co][ci]
+  if (dgrad)  // [26-t][ci][co]
+    base[wd_off + ((long long)packed_tap(T - 1 - t, permd) * ci + c) * co + o] = h;
 }
 
 // All layers' weights in one launch: a block belongs to the layer whose block range holds
@@ -1431,7 +1533,7 @@ struct WTable {
   int blk0[kWMaxLayers + 1];
   long long w_off[kWMaxLayers], wf_off[kWMaxLayers], wd_off[kWMaxLayers];
   int ci[kWMaxLayers], ci_real[kWMaxLayers], co[kWMaxLayers], T[kWMaxLayers],
-      dgrad[kWMaxLayers];
+      dgrad[kWMaxLayers], permf[kWMaxLayers], permd[kWMaxLayers];
 };
 
 // A block takes one (layer, tap, chunk of 32 output channels): it reads W[o][tap][0..ci) rows
@@ -1458,13 +1560,15 @@ weights_all_bf16_kernel(const float* __restrict__ theta, __nv_bfloat16* __restri
     const float v = c < cr ? src[((long long)(o0 + ol) * T + tap) * cr + c] : 0.f;
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     tile[ol][c] = h;
-    base[t.wf_off[l] + ((long long)tap * co + o0 + ol) * ci + c] = h;  // [t][co][ci]
+    base[t.wf_off[l] + ((long long)packed_tap(tap, t.permf[l]) * co + o0 + ol) * ci + c] =
+        h;  // [t][co][ci]
   }
   if (!t.dgrad[l]) return;
   __syncthreads();
   for (int e = threadIdx.x; e < no * ci; e += blockDim.x) {
     const int ol = e % no, c = e / no;
-    base[t.wd_off[l] + ((long long)(T - 1 - tap) * ci + c) * co + o0 + ol] = tile[ol][c];
+    base[t.wd_off[l] + ((long long)packed_tap(T - 1 - tap, t.permd[l]) * ci + c) * co + o0 +
+         ol] = tile[ol][c];
   }
 }
 
@@ -1488,10 +1592,12 @@ weights_split_bf16_kernel(const float* __restrict__ theta, __nv_bfloat16* __rest
   const __nv_bfloat16 hi = __float2bfloat16_rn(v);
   const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
   __nv_bfloat16* base = wb + (long long)b * wstride;
-  __nv_bfloat16* f = base + t.wf_off[l] + ((long long)tap * co + o) * 3 * ci;
+  __nv_bfloat16* f =
+      base + t.wf_off[l] + ((long long)packed_tap(tap, t.permf[l]) * co + o) * 3 * ci;
   f[c] = hi, f[ci + c] = hi, f[2 * ci + c] = lo;
   if (t.dgrad[l]) {
-    __nv_bfloat16* d = base + t.wd_off[l] + ((long long)(T - 1 - tap) * ci + c) * 3 * co;
+    __nv_bfloat16* d =
+        base + t.wd_off[l] + ((long long)packed_tap(T - 1 - tap, t.permd[l]) * ci + c) * 3 * co;
     d[o] = hi, d[co + o] = hi, d[2 * co + o] = lo;
   }
 }
@@ -1602,6 +1708,32 @@ cudaError_t encode_act_halo(CUtensorMap* m, void* base, int B, Dims3 d, int C, i
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// FP32 channels-last output [B][Z][Y][X][C] (batch stride bs elements) as a 5-D map whose
+// box is one 8 x 16 voxel slice of w channels (w = 32: 128-byte swizzle, 16: 64-byte), the
+// store form of the persistent halo convolution's epilogue.
+cudaError_t encode_out(CUtensorMap* m, void* base, int B, Dims3 d, int C, int w, long long bs) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)d.x, (cuuint64_t)d.y, (cuuint64_t)d.z,
+                              (cuuint64_t)B};
+  const cuuint64_t es = 4;
+  const cuuint64_t strides[4] = {C * es, C * es * d.x, C * es * d.x * d.y, (cuuint64_t)bs * es};
+  const cuuint32_t box[5] = {(cuuint32_t)w, 8, 16, 1, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        w == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Epilogue shared memory of the persistent halo convolution: two staging slices of 128 rows
+// x max(n, np) FP32, the bias of one problem, and alignment slack for the ring's end.
+size_t tc3p_staging(int n, int np) {
+  const size_t slice = (size_t)128 * std::max(n, np) * 4;
+  return 2 * slice + ((size_t)(n + np) * 4 + 1023) / 1024 * 1024 + 1024;
+}
+
 size_t smem_bytes(int ck, int n) { return (size_t)kStages * (kBM + n) * ck * 2 + 1024; }
 
 size_t tc3_stage(int ck, int n, int tz = 1) {
@@ -1643,12 +1775,35 @@ struct Tc3Plan {
   int ck = 0, tz = 1, nst = 0;
   size_t stage = 0, staging = 0;
   bool persistent = false;
+  bool pack = false;  // kz taps packed into N (P3Args::pack)
 };
 
 Tc3Plan tc3_plan(int cin, int n, int np, int Z) {
   Tc3Plan best;
   double best_cost = 1e300;
-  const size_t staging = (size_t)128 * (std::max(n, np) + 4) * 4;
+  const size_t staging = tc3p_staging(n, np);
+  // The kz-packed form first (about 2.4x fewer MMAs at tz 8, 2x at tz 4): MMA width 3n <= 256
+  // and both accumulator buffers ((tz + 4) n + tz np columns each) within TMEM; its z depth
+  // is the largest that fits, the channel chunk by the TMA-time model below.
+  if (3 * n <= 256) {
+    for (int tz : {8, 4, 2}) {  // (tz 1: the same MMA count as the plain form, more halo)
+      if ((tz + 4) * n + tz * np > 256) continue;
+      for (int ck : {64, 32, 16}) {
+        if (cin % ck) continue;
+        const size_t stage = tc3_stage(ck, n, tz) + (size_t)np * ck * 2;
+        if (stage > 100 * 1024 || staging + 2 * stage + 1024 > kTc3SmemMax) continue;
+        const int nst = (int)std::min<size_t>(kP3Max, (kTc3SmemMax - 1024 - staging) / stage);
+        const double cost = (3.0 * 144 * (tz + 2) + 9.0 * n + np) / std::min(32, ck);
+        if (!best.pack || cost < best_cost * (1 - 1e-9) ||
+            (cost <= best_cost * (1 + 1e-9) && nst > best.nst)) {
+          best_cost = cost;
+          best.ck = ck, best.tz = tz, best.nst = nst, best.stage = stage, best.staging = staging;
+          best.persistent = best.pack = true;
+        }
+      }
+      if (best.pack) return best;
+    }
+  }
   for (int tz : {8, 4, 2, 1}) {
     if (tz * (n + np) > 256) continue;
     for (int ck : {64, 32, 16}) {
@@ -1686,15 +1841,26 @@ cudaError_t launch_tc3(const CUtensorMap& a, const CUtensorMap& w, int cin, int 
     g.N = n, g.Np = np, g.nchunks = cin / ck;
     g.tiles_x = (int)ceil_div(dout.x, 8), g.tiles_y = (int)ceil_div(dout.y, 16);
     g.tiles_z = (int)ceil_div(dout.z, tz);
-    g.B = B, g.accumulate = acc, g.nst = pl.nst, g.mode = mode;
-    g.stage_bytes = (uint32_t)pl.stage, g.ring_bytes = (uint32_t)(pl.nst * pl.stage);
+    g.B = B, g.accumulate = acc, g.nst = pl.nst, g.mode = mode, g.pack = pl.pack ? 1 : 0;
+    g.stage_bytes = (uint32_t)pl.stage;
+    g.ring_bytes = (uint32_t)((pl.nst * pl.stage + 1023) / 1024 * 1024);
+    g.slice_bytes = (uint32_t)(128 * std::max(n, mode == 1 ? np : 0) * 4);
     g.out_bs = out_bs, g.bias_bs = bias_bs, g.outp_bs = outp_bs, g.biasp_bs = bias_bs;
     const long long total = (long long)g.tiles_x * g.tiles_y * g.tiles_z * B;
     const int grid = (int)std::min<long long>(total, sm_count());
-    const size_t sm = g.ring_bytes + pl.staging + 1024;
+    // (the staging term's slack covers the kernel's 1024-byte alignment of its base)
+    const size_t sm = (size_t)g.ring_bytes + tc3p_staging(n, mode == 1 ? np : 0);
+    CUtensorMap mo, mop;
+    cudaError_t e = encode_out(&mo, out, B, dout, n, n % 32 == 0 ? 32 : 16, out_bs);
+    if (e == cudaSuccess && mode == 1)
+      e = encode_out(&mop, out_p, B, dout, np, np % 32 == 0 ? 32 : 16, outp_bs);
+    else
+      mop = mo;
+    if (e != cudaSuccess) return e;
     const CUtensorMap& mp = wp ? *wp : w;
     const CUtensorMap& m2 = a2 ? *a2 : a;
-#define D2IP_P3(CK_, TZ_) conv_tc3p_kernel<CK_, TZ_><<<grid, 192, sm, st>>>(a, w, mp, m2, g)
+#define D2IP_P3(CK_, TZ_) \
+  conv_tc3p_kernel<CK_, TZ_><<<grid, 192, sm, st>>>(a, w, mp, m2, mo, mop, g)
 #define D2IP_P3Z(CK_) \
   if (tz == 8) D2IP_P3(CK_, 8); else if (tz == 4) D2IP_P3(CK_, 4); \
   else if (tz == 2) D2IP_P3(CK_, 2); else D2IP_P3(CK_, 1)
@@ -1832,10 +1998,10 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
   L.dgrad = (s == 1 || k == 3) && bf16_conv_supported(co, ci, k);
   if (k == 3 && s == 1) {
     const Tc3Plan pf = tc3_plan(L.kf, co, 0, L.dout.z);
-    L.ck3f = pf.ck, L.tz3f = pf.tz;
+    L.ck3f = pf.ck, L.tz3f = pf.tz, L.pack3f = pf.pack;
     if (L.dgrad) {
       const Tc3Plan pd = tc3_plan(L.kd, ci, 0, L.din.z);
-      L.ck3d = pd.ck, L.tz3d = pd.tz;
+      L.ck3d = pd.ck, L.tz3d = pd.tz, L.pack3d = pd.pack;
     }
   }
   L.wgrad = s == 1 && co <= 128 && 128 % co == 0 && ci + chunk_for(ci) <= 256;
@@ -1870,7 +2036,7 @@ int bf16_add_input_layer(Bf16Net& bf, int ci_real, int co, Dims3 din, long long 
   L.input_layer = true;
   if (bf16_conv_supported(16, co, 3)) {
     const Tc3Plan pf = tc3_plan(L.kf, co, 0, din.z);
-    L.ck3f = pf.ck, L.tz3f = pf.tz;
+    L.ck3f = pf.ck, L.tz3f = pf.tz, L.pack3f = pf.pack;
   }
   L.wg_tz = wg3_tz_fit(L);
   L.wgrad = L.wg3 = wg3_geom(L, 1).nst > 0;
@@ -2364,6 +2530,7 @@ cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long lo
       t.w_off[i] = L.w_off, t.wf_off[i] = L.wf_off, t.wd_off[i] = L.wd_off;
       t.ci[i] = L.ci, t.ci_real[i] = L.ci_real, t.co[i] = L.co, t.T[i] = T;
       t.dgrad[i] = L.dgrad ? 1 : 0;
+      t.permf[i] = L.pack3f ? 1 : 0, t.permd[i] = L.pack3d ? 1 : 0;
     }
     t.blk0[t.nl] = blk;
     weights_split_bf16_kernel<<<dim3((unsigned)blk, B), 256, 0, stream>>>(theta, bf.wbuf, Pp,
@@ -2384,6 +2551,7 @@ cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long lo
       t.w_off[i] = L.w_off, t.wf_off[i] = L.wf_off, t.wd_off[i] = L.wd_off;
       t.ci[i] = L.ci, t.ci_real[i] = L.ci_real, t.co[i] = L.co, t.T[i] = T;
       t.dgrad[i] = L.dgrad ? 1 : 0;
+      t.permf[i] = L.pack3f ? 1 : 0, t.permd[i] = L.pack3d ? 1 : 0;
     }
     t.blk0[t.nl] = blk;
     weights_all_bf16_kernel<<<dim3((unsigned)blk, B), 256, 0, stream>>>(theta, bf.wbuf, Pp,
@@ -2396,7 +2564,8 @@ cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long lo
     dim3 grid((unsigned)ceil_div(n, 256), B);
     weights_bf16_kernel<<<grid, 256, 0, stream>>>(theta, bf.wbuf, Pp, bf.wstride, L.w_off,
                                                   L.wf_off, L.wd_off, L.ci, L.ci_real, L.co, T,
-                                                  L.dgrad ? 1 : 0);
+                                                  L.dgrad ? 1 : 0, L.pack3f ? 1 : 0,
+                                                  L.pack3d ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -2443,7 +2612,7 @@ int bf16_fuse_proj(Bf16Net& bf, int la, int lp) {
   A.proj = lp;
   if (A.ck3f) {
     const Tc3Plan pf = tc3_plan(A.kf, A.co, P.co, A.dout.z);
-    if (pf.persistent) A.projf = true, A.ck3f = pf.ck, A.tz3f = pf.tz;
+    if (pf.persistent) A.projf = true, A.ck3f = pf.ck, A.tz3f = pf.tz, A.pack3f = pf.pack;
   }
   if (A.ck3d && P.dgrad) {
     const Tc3Plan pd = tc3_plan(A.kd, A.ci, 0, A.din.z);

@@ -33,6 +33,9 @@ struct TcLayer {
   bool wgrad = false;             // weight gradient on the tensor cores too (3x3x3)
   int ck3f = 0, ck3d = 0;         // channel chunk of the halo-box kernel (0: per-tap kernel)
   int tz3f = 1, tz3d = 1;         // z slices per halo-box tile
+  bool pack3f = false, pack3d = false;  // halo forward / data gradient with the kz taps packed
+                                        // into N: that direction's weights are stored with ky
+                                        // and kz swapped (tap (kz, ky, kx) at (ky, kz, kx))
   int proj = -1;                  // layer index of a 1x1 projection of the same input, fused
   bool projf = false, projd = false, projw = false;  // ... into forward / dgrad / wgrad
   CUtensorMap pw_f, pw_d, pa_d;   // projection: W_p, W_p^T and the dz_p tile box
