@@ -1237,6 +1237,9 @@ wgrad_s2_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
 // serves all 27 taps and B holds the three x-shifted columns side by side plus the ones:
 // N = 3 Ci + CKB, the columns of x tap kx at kx * Ci.  Per 16-voxel K step that is G MMAs of
 // width N instead of 3 G of width Ci + CKB, at nearly the same issue cost per MMA.
+// NX = 2 (packed, split precision): the hi and lo blocks of x (tm_x, tm_x2) side by side,
+// N = 6 Ci + CKB, and the epilogue adds the two products of each tap: dy_hi x_hi + dy_hi x_lo
+// in one MMA stream (the pass with dy_lo x_hi is a separate NX = 1 launch).
 // ------------------------------------------------------------------------------------
 constexpr int kWg3MaxStages = 6;
 
@@ -1255,16 +1258,18 @@ __device__ __forceinline__ uint64_t smem_desc_mn2(uint32_t addr, uint32_t lbo, u
 struct Wg3Geom {
   int tz, nkx, tiles_x, tiles_z, ntiles, tiles_per_chunk, nchunks, nst;
   int rows_b;      // partial-sum rows per problem (nchunks times the operand passes)
+  int nx;          // x operand sets side by side in N (2: hi and lo of the split precision)
   int bias_on;     // write the ones column's sums (else zeros: a pass that repeats them)
   uint32_t a_box, b_box, b_off, ones_off, stage, tmem_cols;
   int proj;        // also the weight gradient of a fused 1x1 projection (its dz_p: p_box)
   uint32_t p_off, p_box;
 };
 
-template <int CKA, int CKB, int NKX>
+template <int CKA, int CKB, int NKX, int NX = 1>
 __global__ void __launch_bounds__(128, 1)
 wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant__ CUtensorMap tm_x,
-                 const __grid_constant__ CUtensorMap tm_p, float* __restrict__ part,
+                 const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorMap tm_x2,
+                 float* __restrict__ part,
                  float* __restrict__ part_p, Dims3 d, int Ci, int ci_out,
                  const __grid_constant__ Wg3Geom gm, int* __restrict__ err) {
   constexpr int kTpm = 128 / CKA;                  // taps per MMA
@@ -1273,7 +1278,8 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
   constexpr uint32_t kAtomB = 8 * CKB * 2;
   constexpr bool kPack = NKX == 0;                 // the three x taps in N
   constexpr int kNq = kPack ? 1 : NKX;             // dy boxes (accumulator sets) per stage
-  const int N = (kPack ? 3 * Ci : Ci) + CKB;       // + the ones block
+  static_assert(NX == 1 || kPack, "two x operand sets only in the packed form");
+  const int N = (kPack ? 3 * NX * Ci : Ci) + CKB;  // + the ones block
   const int nb = Ci / CKB;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -1317,7 +1323,8 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
 
   if (warp == 0 && lane == 0) {  // TMA producer
     const uint32_t tx_bytes = (uint32_t)kNq * gm.a_box +
-                              (uint32_t)(kPack ? 3 * nb : nb) * gm.b_box + (proj ? gm.p_box : 0u);
+                              (uint32_t)(kPack ? 3 * NX * nb : nb) * gm.b_box +
+                              (proj ? gm.p_box : 0u);
     int k = 0;
     for (; k < ksteps; ++k) {
       const int s = k % nst, round = k / nst;
@@ -1334,10 +1341,11 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
       mbar_expect_tx(fb, tx_bytes);
       if (kPack) {  // the unshifted dy box, then x at x offsets -1, 0, +1
         tma_load_5d(base, &tm_dy, 0, x0, y0 - 1, z0 - 1, b, fb);
-        for (int kx = 0; kx < 3; ++kx)
-          for (int c = 0; c < nb; ++c)
-            tma_load_5d(base + gm.b_off + (uint32_t)(kx * nb + c) * gm.b_box, &tm_x, c * CKB,
-                        x0 + kx - 1, y0, z0, b, fb);
+        for (int xs = 0; xs < NX; ++xs)
+          for (int kx = 0; kx < 3; ++kx)
+            for (int c = 0; c < nb; ++c)
+              tma_load_5d(base + gm.b_off + (uint32_t)((xs * 3 + kx) * nb + c) * gm.b_box,
+                          xs ? &tm_x2 : &tm_x, c * CKB, x0 + kx - 1, y0, z0, b, fb);
       } else {
         for (int q = 0; q < NKX; ++q)
           tma_load_5d(base + (uint32_t)q * gm.a_box, &tm_dy, 0, x0 + 1 - (kx0 + q), y0 - 1,
@@ -1422,6 +1430,13 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
         for (int c0 = 0; c0 < Ci; c0 += 16) {
           uint32_t r[16];
           if (ok) tmem_ld16(cx + (uint32_t)c0, r);
+          if (NX == 2) {  // + the lo-x products of the same tap
+            uint32_t r2[16];
+            if (ok) tmem_ld16(cx + (uint32_t)(3 * Ci + c0), r2);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(r2[j]));
+          }
           if (keep) {
 #pragma unroll
             for (int j = 0; j < 16; j += 4)
@@ -1434,7 +1449,7 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
         }
       }
       uint32_t r[16];
-      if (ok) tmem_ld16(col + (uint32_t)(kPack ? 3 * Ci : Ci), r);  // the ones column
+      if (ok) tmem_ld16(col + (uint32_t)(kPack ? 3 * NX * Ci : Ci), r);  // the ones column
       if (keep && tq == 4 && (kPack || kx0 + q == 1))  // the centre tap (t = 13): the bias
         prow[(long long)Co * 27 * ci_out + co] = ok && gm.bias_on ? __uint_as_float(r[0]) : 0.f;
     }
@@ -2236,8 +2251,9 @@ int wg3_tz(int Z) {
 
 // Geometry of the halo weight gradient in the packed form (pack) or with x taps in separate
 // accumulators; nst == 0 when the layer does not fit that form.
-Wg3Geom wg3_geom_form(const TcLayer& L, int B, bool proj, bool pack) {
+Wg3Geom wg3_geom_form(const TcLayer& L, int B, bool proj, bool pack, int nx = 1) {
   Wg3Geom g{};
+  if (nx != 1 && (!pack || proj)) return g;
   if (L.k != 3 || L.s != 1 || (L.co != 16 && L.co != 32 && L.co != 64)) return g;
   const int ckb = chunk_for(L.ci);
   const int tpm = 128 / L.co, G = (9 + tpm - 1) / tpm, N = L.ci + ckb;
@@ -2248,7 +2264,7 @@ Wg3Geom wg3_geom_form(const TcLayer& L, int B, bool proj, bool pack) {
     return t;
   };
   const int extra = proj ? 1 : 0;  // the projection's accumulator
-  const int Np = 3 * L.ci + ckb;   // packed: the three x taps in N
+  const int Np = 3 * nx * L.ci + ckb;  // packed: the three x taps (of nx x sets) in N
   if (pack) {
     if (Np > 256 || (G + extra) * Np > 512) return g;
     g.nkx = 0;
@@ -2262,7 +2278,8 @@ Wg3Geom wg3_geom_form(const TcLayer& L, int B, bool proj, bool pack) {
   g.tz = L.wg_tz > 0 ? L.wg_tz : wg3_tz(L.dout.z);
   g.a_box = (uint32_t)(8 * 3 * (g.tz + 2) * L.co * 2);
   g.b_box = (uint32_t)(8 * g.tz * ckb * 2);
-  const int a_boxes = g.nkx == 0 ? 1 : g.nkx, x_boxes = (g.nkx == 0 ? 3 : 1) * (L.ci / ckb);
+  const int a_boxes = g.nkx == 0 ? 1 : g.nkx, x_boxes = (g.nkx == 0 ? 3 * nx : 1) * (L.ci / ckb);
+  g.nx = nx;
   g.b_off = (uint32_t)((a_boxes * g.a_box + 1023) / 1024 * 1024);
   g.ones_off = g.b_off + (uint32_t)x_boxes * g.b_box;
   g.p_box = proj ? (uint32_t)(8 * g.tz * L.co * 2) : 0u;
@@ -2289,6 +2306,13 @@ Wg3Geom wg3_geom(const TcLayer& L, int B, bool proj) {
   return g.nst > 0 ? g : wg3_geom_form(L, B, proj, false);
 }
 
+// Split precision: the pass with both x sets (dy_hi against x_hi and x_lo), when it fits;
+// its chunking is then shared by the other pass (dy_lo x_hi).
+Wg3Geom wg3_geom_dual(const TcLayer& L, int B) {
+  if (!L.wg3 || L.projw) return Wg3Geom{};
+  return wg3_geom_form(L, B, false, true, 2);
+}
+
 template <int CKA, int CKB>
 cudaError_t wg3_attr() {
   cudaError_t e = cudaFuncSetAttribute(wgrad_tc3_kernel<CKA, CKB, 1>,
@@ -2300,23 +2324,30 @@ cudaError_t wg3_attr() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(wgrad_tc3_kernel<CKA, CKB, 0>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWg3SmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(wgrad_tc3_kernel<CKA, CKB, 0, 2>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWg3SmemMax);
   return e;
 }
 
 template <int CKA, int CKB>
 void launch_wg3(const TcLayer& L, const Wg3Geom& g, const CUtensorMap& my, const CUtensorMap& mx,
                 const CUtensorMap& mp, float* part, float* part_p, int B, int* err,
-                cudaStream_t st) {
+                cudaStream_t st, const CUtensorMap* mx2p = nullptr) {
   dim3 grid((unsigned)g.nchunks, (unsigned)(g.nkx ? 3 / g.nkx : 1), (unsigned)B);
   const size_t smem = (size_t)g.nst * g.stage + 1024;
-  if (g.nkx == 0)
-    wgrad_tc3_kernel<CKA, CKB, 0><<<grid, 128, smem, st>>>(my, mx, mp, part, part_p, L.dout,
+  const CUtensorMap& mx2 = mx2p ? *mx2p : mx;
+  if (g.nkx == 0 && g.nx == 2)
+    wgrad_tc3_kernel<CKA, CKB, 0, 2><<<grid, 128, smem, st>>>(my, mx, mp, mx2, part, part_p,
+                                                              L.dout, L.ci, L.ci_real, g, err);
+  else if (g.nkx == 0)
+    wgrad_tc3_kernel<CKA, CKB, 0><<<grid, 128, smem, st>>>(my, mx, mp, mx2, part, part_p, L.dout,
                                                            L.ci, L.ci_real, g, err);
   else if (g.nkx == 3)
-    wgrad_tc3_kernel<CKA, CKB, 3><<<grid, 128, smem, st>>>(my, mx, mp, part, part_p, L.dout,
+    wgrad_tc3_kernel<CKA, CKB, 3><<<grid, 128, smem, st>>>(my, mx, mp, mx2, part, part_p, L.dout,
                                                            L.ci, L.ci_real, g, err);
   else
-    wgrad_tc3_kernel<CKA, CKB, 1><<<grid, 128, smem, st>>>(my, mx, mp, part, part_p, L.dout,
+    wgrad_tc3_kernel<CKA, CKB, 1><<<grid, 128, smem, st>>>(my, mx, mp, mx2, part, part_p, L.dout,
                                                            L.ci, L.ci_real, g, err);
 }
 
@@ -2361,12 +2392,20 @@ void launch_wgs2(const TcLayer& L, const S2Plan& p, const CUtensorMap& mx, const
 long long bf16_wgrad_chunks(const Bf16Net& bf, int layer, int B) {
   const TcLayer& L = bf.layers[layer];
   if (L.wgs2) return wgs2_plan(L, B).chunks;
-  if (L.wg3) return wg3_geom(L, B, L.projw).nchunks;
+  if (L.wg3) {
+    if (bf.sp > 1) {
+      const Wg3Geom d = wg3_geom_dual(L, B);
+      if (d.nst > 0) return d.nchunks;
+    }
+    return wg3_geom(L, B, L.projw).nchunks;
+  }
   return wgrad_plan(L, B).chunks;
 }
 
 int bf16_wgrad_passes(const Bf16Net& bf, int layer) {
-  return bf.layers[layer].wgrad && bf.sp > 1 ? 3 : 1;
+  const TcLayer& L = bf.layers[layer];
+  if (!L.wgrad || bf.sp == 1) return 1;
+  return wg3_geom_dual(L, 1).nst > 0 ? 2 : 3;
 }
 
 // Operand blocks (dy, x) of weight-gradient pass p: (hi, hi), (lo, hi), (hi, lo).  The ones
@@ -2418,15 +2457,28 @@ cudaError_t bf16_conv_wgrad(Bf16Net& bf, int layer, const float* x, const float*
       if (e != cudaSuccess) return e;
     }
     const long long prow = (long long)L.co * L.ci + L.co;
+    // split precision in two passes: (dy_hi; x_hi and x_lo side by side), then (dy_lo; x_hi)
+    // with the same chunking; else three passes (hi, hi), (lo, hi), (hi, lo) or one
+    Wg3Geom gd{};
+    if (passes == 2) {
+      gd = wg3_geom_dual(L, B);
+      g.tiles_per_chunk = gd.tiles_per_chunk, g.nchunks = gd.nchunks;
+      gd.rows_b = 2 * gd.nchunks;
+      gd.bias_on = 1;
+    }
     g.rows_b = passes * g.nchunks;
     const int ckb = chunk_for(L.ci);
     for (int q = 0; q < passes; ++q) {
-      g.bias_on = kPassBias[q];
+      const bool dual = passes == 2 && q == 0;
+      const int py = passes == 2 ? q : kPassY[q], px = passes == 2 ? 0 : kPassX[q];
+      g.bias_on = passes == 2 ? 1 : kPassBias[q];
       float* pq = part + (long long)q * g.nchunks * row;
       float* ppq = part_p ? part_p + (long long)q * g.nchunks * prow : nullptr;
-      const CUtensorMap &my = L.wgy[kPassY[q]], &mx = L.wgx[kPassX[q]];
-      const CUtensorMap& mp = g.proj ? L.wgp[kPassY[q]] : my;
-#define D2IP_WG3(A_, B_) launch_wg3<A_, B_>(L, g, my, mx, mp, pq, ppq, B, bf.err, stream)
+      const CUtensorMap &my = L.wgy[py], &mx = L.wgx[px];
+      const CUtensorMap& mp = g.proj ? L.wgp[py] : my;
+      const Wg3Geom& gq = dual ? gd : g;
+#define D2IP_WG3(A_, B_) \
+  launch_wg3<A_, B_>(L, gq, my, mx, mp, pq, ppq, B, bf.err, stream, dual ? &L.wgx[1] : nullptr)
       if (L.co == 16) {
         if (ckb == 16) D2IP_WG3(16, 16); else if (ckb == 32) D2IP_WG3(16, 32); else D2IP_WG3(16, 64);
       } else if (L.co == 32) {
