@@ -528,20 +528,26 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void epi_sync() {  // the four epilogue warps only
-  asm volatile("bar.sync 1, 128;" ::: "memory");
+// The persistent halo convolution has kEpiGroups epilogue warpgroups (warps 2..5, 6..9), each
+// covering the four TMEM lane quadrants and taking alternate output slices of a tile; group g
+// synchronises on named barrier 1 + g.
+constexpr int kEpiGroups = 2;
+constexpr int kTc3pThreads = 64 + 128 * kEpiGroups;
+
+__device__ __forceinline__ void epi_sync(int grp) {  // the four warps of one epilogue group
+  asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory");
 }
 
-// true on every epilogue thread iff p holds on all 128 of them (named barrier 1)
-__device__ __forceinline__ bool epi_all(bool p) {
+// true on every thread of epilogue group grp iff p holds on all 128 of them
+__device__ __forceinline__ bool epi_all(bool p, int grp) {
   uint32_t r;
   asm volatile(
       "{\n\t.reg .pred a, q;\n\t"
       "setp.ne.u32 a, %1, 0;\n\t"
-      "bar.red.and.pred q, 1, 128, a;\n\t"
+      "bar.red.and.pred q, %2, 128, a;\n\t"
       "selp.u32 %0, 1, 0, q;\n\t}"
       : "=r"(r)
-      : "r"(p ? 1u : 0u)
+      : "r"(p ? 1u : 0u), "r"(1 + grp)
       : "memory");
   return r != 0;
 }
@@ -568,17 +574,39 @@ struct P3Args {
   Dims3 dout;
   int N, Np, nchunks, tiles_x, tiles_y, tiles_z, B, accumulate, nst, mode, pack;
   uint32_t ring_bytes, stage_bytes;
-  uint32_t slice_bytes;  // one epilogue staging slice (128 rows x max(N, Np) FP32); two follow
-                         // the ring, then the bias of the current problem
+  uint32_t slice_bytes;  // one epilogue staging slice (128 rows of FP32 outputs, and with the
+                         // LayerNorm also xhat and the BF16 copy); per epilogue group, nbuf of
+                         // them after the ring, then the groups' bias, gamma and beta copies
+  int nbuf;
   long long out_bs, bias_bs, outp_bs, biasp_bs;
+  // LayerNorm epilogue (ln, output part 0): y = act(gamma * xhat + beta (+ resid)) with
+  // xhat = (z - mean) * rstd over the N channels of each voxel (z = the convolution + bias);
+  // y through tm_out, xhat through tm_xh, rstd[b][voxel] directly and, with ybf, a BF16 copy
+  // of y in sp channel blocks (stage_bf16x4's layout) through tm_ybf.  z is not stored.
+  int ln, act, ybf, sp;
+  const float* gamma;  // gamma[c], then beta[c] at gamma + N, per problem at gamma_bs
+  long long gamma_bs;
+  const float* resid;  // [b][voxel][N] at resid_bs, or null
+  long long resid_bs;
+  float* rstd;         // [b][voxel] at rstd_bs
+  long long rstd_bs;
 };
 
+// 16-byte chunk index inside a staged row of R bytes (R = 32, 64 or 128) under the TMA
+// swizzle of that width: the chunk bits XORed with the row's position in its 8-row (R 128),
+// 4-pair (R 64) or 2-quad (R 32) atom.
+__device__ __forceinline__ int swz_chunk(int chunk, int m, int R) {
+  return chunk ^ ((m * R >> 7) & (R / 16 - 1));
+}
+
 template <int CK, int TZ>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kTc3pThreads, 1)
 conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
                  const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorMap tm_a2,
                  const __grid_constant__ CUtensorMap tm_out,
-                 const __grid_constant__ CUtensorMap tm_outp, const __grid_constant__ P3Args g) {
+                 const __grid_constant__ CUtensorMap tm_outp,
+                 const __grid_constant__ CUtensorMap tm_xh,
+                 const __grid_constant__ CUtensorMap tm_ybf, const __grid_constant__ P3Args g) {
   constexpr uint32_t kRowB = CK * 2;
   constexpr uint32_t a_bytes = (uint32_t)(8 * 18 * (TZ + 2)) * kRowB;
   const int N = g.N, Np = g.mode == 1 ? g.Np : 0;
@@ -591,7 +619,8 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
   // epilogue: two staging slices (each box of w channels stored as the swizzled rows the
   // output tensor map expects), then the bias of the current problem
   float* stg = reinterpret_cast<float*>(smem + g.ring_bytes);
-  float* sbias = reinterpret_cast<float*>(smem + g.ring_bytes + 2 * g.slice_bytes);
+  float* sbias0 = reinterpret_cast<float*>(smem + g.ring_bytes +
+                                           (size_t)kEpiGroups * g.nbuf * g.slice_bytes);
   __shared__ __align__(8) uint64_t full_bar[kP3Max], empty_bar[kP3Max], tfull[2], tempty[2],
       done_bar;
   __shared__ uint32_t tmem_base_s;
@@ -615,7 +644,7 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
     }
     for (int q = 0; q < 2; ++q) {
       mbar_init(smem_u32(&tfull[q]), 1);
-      mbar_init(smem_u32(&tempty[q]), 128);
+      mbar_init(smem_u32(&tempty[q]), 128 * kEpiGroups);
     }
     mbar_init(smem_u32(&done_bar), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -791,28 +820,34 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
       }
       mma_commit(smem_u32(&done_bar));  // fires once every issued MMA has completed
     }
-  } else {  // epilogue warps 2..5: TMEM lane quadrant warp % 4
+  } else {  // epilogue warps: group (warp - 2) / 4, TMEM lane quadrant warp % 4
+    const int grp = (warp - 2) >> 2;
     const int quad = warp & 3;
     const int m = quad * 32 + lane;  // tile row = y * 8 + x
-    const int tid = threadIdx.x - 64;
+    const int tid = (threadIdx.x - 64) & 127;
     const uint32_t lanes = (uint32_t)(quad * 32) << 16;
-    if (pack) {  // both accumulator buffers start at zero
-      for (int c = 0; c < cols; c += 16) tmem_zero16(tmem + lanes + (uint32_t)c);
+    float* sbias = sbias0 + grp * (3 * N + Np);  // this group's bias, gamma, beta
+    float* stg_g = stg + (size_t)grp * g.nbuf * (g.slice_bytes / 4);
+    if (pack) {  // both accumulator buffers start at zero (each group its half of the columns)
+      for (int c = grp * 16; c < cols; c += 16 * kEpiGroups)
+        tmem_zero16(tmem + lanes + (uint32_t)c);
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       tc_fence_before();
       mbar_arrive(smem_u32(&tempty[0]));
       mbar_arrive(smem_u32(&tempty[1]));
     }
-    // Per output slice: TMEM -> (+ bias) -> shared staging slice, then one thread stores the
-    // slice with TMA (a reduce-add when accumulating); out-of-grid rows are clipped by TMA.
-    // Staging rows are the output map's swizzled layout: a box of w channels (w = 32: 128-byte
-    // rows, 128-byte swizzle; w = 16: 64-byte rows, 64-byte swizzle), 16-byte chunk j of row
-    // m at j ^ (m % 8) or j ^ ((m / 2) % 4) -- conflict-free for eight consecutive rows.
+    // Per output slice: TMEM -> (+ bias) -> shared staging slice, then one thread of the
+    // group stores the slice with TMA (a reduce-add when accumulating); out-of-grid rows are
+    // clipped by TMA.  Staging rows are the output map's swizzled layout: a box of w channels
+    // (w = 32: 128-byte rows and swizzle; w = 16: 64-byte), its 16-byte chunks permuted by
+    // swz_chunk -- conflict-free for eight consecutive rows.  Slices s = part * TZ + zz with
+    // s % kEpiGroups == grp are this group's; packed accumulators are zeroed slice by slice
+    // after they are read (the spare columns are never read).
     int slice = 0, bias_b = -1;
     for (int i = 0; i < ntile; ++i) {
       const int buf = i & 1;
-      const bool ok = epi_all(mbar_wait(smem_u32(&tfull[buf]), (i >> 1) & 1));
-      if (!ok) {  // uniform over the four warps, so none is left at a named barrier
+      const bool ok = epi_all(mbar_wait(smem_u32(&tfull[buf]), (i >> 1) & 1), grp);
+      if (!ok) {  // uniform over the group's four warps, so none is left at a named barrier
         if (tid == 0) atomicOr(g.err, kErrEpilogue);
         break;
       }
@@ -824,31 +859,36 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
       tile /= g.tiles_x;
       const int y0 = (tile % g.tiles_y) * 16;
       const int z0 = (tile / g.tiles_y) * TZ;
-      if (b != bias_b) {  // this problem's biases (zero when none)
-        epi_sync();
+      if (b != bias_b) {  // this problem's biases (zero when none), then gamma and beta
+        epi_sync(grp);
         for (int c = tid; c < N + Np; c += 128) {
           const float* bb = c < N ? g.bias : g.bias_p;
           const long long bs = c < N ? g.bias_bs : g.biasp_bs;
           sbias[c] = bb ? bb[(long long)b * bs + (c < N ? c : c - N)] : 0.f;
         }
-        epi_sync();
+        if (g.ln)
+          for (int c = tid; c < 2 * N; c += 128)
+            sbias[N + Np + c] = g.gamma[(long long)b * g.gamma_bs + c];
+        epi_sync(grp);
         bias_b = b;
       }
-      for (int part = 0; part < (Np > 0 ? 2 : 1); ++part) {
+      const int nparts = Np > 0 ? 2 : 1;
+      for (int sidx = grp; sidx < nparts * TZ; sidx += kEpiGroups) {
+        const int part = sidx / TZ, zz = sidx % TZ;
         const int nc = part ? Np : N;
         const int w = nc % 32 == 0 ? 32 : 16;  // channels per stored box
         const float* bsm = sbias + (part ? N : 0);
         const CUtensorMap* om = part ? &tm_outp : &tm_out;
         const bool add = !part && g.accumulate;
-        for (int zz = 0; zz < TZ; ++zz) {
-          const int col0 =
-              buf * acc_cols + (part ? pbase + zz * Np : (pack ? TZ + 1 - zz : zz) * N);
-          float* S = stg + (slice & 1) * (g.slice_bytes / 4);
+        const int col0 =
+            buf * acc_cols + (part ? pbase + zz * Np : (pack ? TZ + 1 - zz : zz) * N);
+        float* S = stg_g + (g.nbuf > 1 ? slice & 1 : 0) * (g.slice_bytes / 4);
+        const bool ln = g.ln && !part;
+        if (!ln) {
           for (int c0 = 0; c0 < nc; c0 += 16) {
             uint32_t r[16];
             tmem_ld16(tmem + lanes + (uint32_t)(col0 + c0), r);
             float* row = S + (c0 / w) * (128 * w) + m * w;  // box c0 / w, row m
-            const int sw = w == 32 ? (m & 7) : ((m >> 1) & 3);
 #pragma unroll
             for (int j = 0; j < 16; j += 4) {
               const float4 bv = *reinterpret_cast<const float4*>(bsm + c0 + j);
@@ -857,31 +897,134 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
                                            __uint_as_float(r[j + 2]) + bv.z,
                                            __uint_as_float(r[j + 3]) + bv.w);
               const int chunk = ((c0 % w) + j) / 4;
-              *reinterpret_cast<float4*>(row + (chunk ^ sw) * 4) = v;
+              *reinterpret_cast<float4*>(row + swz_chunk(chunk, m, 4 * w) * 4) = v;
             }
           }
-          if (zz == TZ - 1 && part == (Np > 0 ? 1 : 0)) {  // buffer fully read: hand it back
-            if (pack) {  // zeroed first: every MMA of the next tile accumulates
-              for (int c = 0; c < acc_cols; c += 16)
-                tmem_zero16(tmem + lanes + (uint32_t)(buf * acc_cols + c));
-              asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-            }
-            tc_fence_before();
-            mbar_arrive(smem_u32(&tempty[buf]));
+        } else {
+          // LayerNorm of voxel m over its N channels: three passes over TMEM (mean, the
+          // centred second moment, then the outputs), in the order of ln_fwd_kernel
+          const float inv_c = 1.0f / (float)nc;
+          const int ox = x0 + (m & 7), oy = y0 + (m >> 3), oz = z0 + zz;
+          const bool inside = ox < g.dout.x && oy < g.dout.y && oz < g.dout.z;
+          const long long vox = ((long long)oz * g.dout.y + oy) * g.dout.x + ox;
+          const float* rsd =
+              g.resid && inside ? g.resid + (long long)b * g.resid_bs + vox * nc : nullptr;
+          float sum = 0.f;
+          for (int c0 = 0; c0 < nc; c0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(tmem + lanes + (uint32_t)(col0 + c0), r);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) sum += __uint_as_float(r[j]) + bsm[c0 + j];
           }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // staging -> TMA
-          epi_sync();
-          if (tid == 0) {
-            if (z0 + zz < g.dout.z) {
-              for (int k = 0; k < nc / w; ++k)
-                tma_store_5d(om, smem_u32(S + k * (128 * w)), k * w, x0, y0, z0 + zz, b, add);
+          const float mean = sum * inv_c;
+          float sq = 0.f;
+          for (int c0 = 0; c0 < nc; c0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(tmem + lanes + (uint32_t)(col0 + c0), r);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const float d = __uint_as_float(r[j]) + bsm[c0 + j] - mean;
+              sq += d * d;
             }
-            bulk_commit();
-            bulk_wait_read<1>();  // the other staging slice is free again
           }
-          ++slice;
-          epi_sync();
+          const float rs = 1.0f / sqrtf(sq * inv_c + kLnEps);
+          const float* gam = sbias + N + Np;
+          float* XH = S + 128 * nc;                                       // xhat boxes
+          __nv_bfloat16* YB = reinterpret_cast<__nv_bfloat16*>(S + 256 * nc);  // BF16 copy
+          for (int c0 = 0; c0 < nc; c0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(tmem + lanes + (uint32_t)(col0 + c0), r);
+            float o[16], xh[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              xh[j] = (__uint_as_float(r[j]) + bsm[c0 + j] - mean) * rs;
+              o[j] = fmaf(xh[j], gam[c0 + j], gam[nc + c0 + j]);
+            }
+            if (rsd) {
+#pragma unroll
+              for (int j = 0; j < 16; j += 4) {
+                const float4 q = *reinterpret_cast<const float4*>(rsd + c0 + j);
+                o[j] += q.x, o[j + 1] += q.y, o[j + 2] += q.z, o[j + 3] += q.w;
+              }
+            }
+            if (g.act) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) o[j] = o[j] > 0.f ? o[j] : kLeakySlope * o[j];
+            }
+            const int bx = c0 / w;
+            float* yrow = S + bx * (128 * w) + m * w;
+            float* hrow = XH + bx * (128 * w) + m * w;
+#pragma unroll
+            for (int j = 0; j < 16; j += 4) {
+              const int ch = swz_chunk(((c0 % w) + j) / 4, m, 4 * w);
+              *reinterpret_cast<float4*>(yrow + ch * 4) =
+                  make_float4(o[j], o[j + 1], o[j + 2], o[j + 3]);
+              *reinterpret_cast<float4*>(hrow + ch * 4) =
+                  make_float4(xh[j], xh[j + 1], xh[j + 2], xh[j + 3]);
+            }
+            if (g.ybf) {  // sp blocks of nc BF16 channels, each its own box of 2 nc-byte rows
+#pragma unroll
+              for (int j = 0; j < 16; j += 8) {
+                __nv_bfloat162 h[4], l[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  h[u] = __floats2bfloat162_rn(o[j + 2 * u], o[j + 2 * u + 1]);
+                  const float2 f = __bfloat1622float2(h[u]);
+                  l[u] = __floats2bfloat162_rn(o[j + 2 * u] - f.x, o[j + 2 * u + 1] - f.y);
+                }
+                const int ch = swz_chunk((c0 + j) / 8, m, 2 * nc);
+                uint4 uh, ul;
+                uh.x = *reinterpret_cast<uint32_t*>(&h[0]), uh.y = *reinterpret_cast<uint32_t*>(&h[1]);
+                uh.z = *reinterpret_cast<uint32_t*>(&h[2]), uh.w = *reinterpret_cast<uint32_t*>(&h[3]);
+                ul.x = *reinterpret_cast<uint32_t*>(&l[0]), ul.y = *reinterpret_cast<uint32_t*>(&l[1]);
+                ul.z = *reinterpret_cast<uint32_t*>(&l[2]), ul.w = *reinterpret_cast<uint32_t*>(&l[3]);
+                __nv_bfloat16* yb = YB + m * nc + ch * 8;
+                *reinterpret_cast<uint4*>(yb) = uh;  // blocks hi, lo, hi
+                if (g.sp > 1) {
+                  *reinterpret_cast<uint4*>(yb + 128 * nc) = ul;
+                  *reinterpret_cast<uint4*>(yb + 256 * nc) = uh;
+                }
+              }
+            }
+          }
+          if (inside) g.rstd[(long long)b * g.rstd_bs + vox] = rs;
         }
+        if (pack) {  // zeroed after reading: every MMA of the next tile accumulates
+          for (int c0 = 0; c0 < nc; c0 += 16) tmem_zero16(tmem + lanes + (uint32_t)(col0 + c0));
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
+        if (sidx + kEpiGroups >= nparts * TZ) {  // the group's last slice of this buffer
+          tc_fence_before();
+          mbar_arrive(smem_u32(&tempty[buf]));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // staging -> TMA
+        epi_sync(grp);
+        if (tid == 0) {
+          if (z0 + zz < g.dout.z) {
+            for (int k = 0; k < nc / w; ++k)
+              tma_store_5d(om, smem_u32(S + k * (128 * w)), k * w, x0, y0, z0 + zz, b, add);
+            if (ln) {
+              for (int k = 0; k < nc / w; ++k)
+                tma_store_5d(&tm_xh, smem_u32(S + 128 * nc + k * (128 * w)), k * w, x0, y0,
+                             z0 + zz, b, false);
+              if (g.ybf)
+                for (int k = 0; k < g.sp; ++k)
+                  tma_store_5d(&tm_ybf, smem_u32(S + 256 * nc) + (uint32_t)(k * 128 * nc * 2),
+                               k * nc, x0, y0, z0 + zz, b, false);
+            }
+          }
+          bulk_commit();
+          if (g.nbuf > 1)
+            bulk_wait_read<1>();  // the group's other staging slice is free again
+          else
+            bulk_wait_read<0>();  // the group's one staging slice is free again
+        }
+        ++slice;
+        epi_sync(grp);
+      }
+      if (grp >= nparts * TZ) {  // a group without a slice of this tile still hands it back
+        tc_fence_before();
+        mbar_arrive(smem_u32(&tempty[buf]));
       }
     }
     if (tid == 0) bulk_wait_all();  // every store has landed before the CTA may exit
@@ -1742,11 +1885,36 @@ cudaError_t encode_out(CUtensorMap* m, void* base, int B, Dims3 d, int C, int w,
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// Epilogue shared memory of the persistent halo convolution: two staging slices of 128 rows
-// x max(n, np) FP32, the bias of one problem, and alignment slack for the ring's end.
-size_t tc3p_staging(int n, int np) {
-  const size_t slice = (size_t)128 * std::max(n, np) * 4;
-  return 2 * slice + ((size_t)(n + np) * 4 + 1023) / 1024 * 1024 + 1024;
+// BF16 channels-last tensor [B][Z][Y][X][C] (batch stride bs elements) as a 5-D map whose
+// box is one 8 x 16 voxel slice of w channels (rows of 2 w = 32, 64 or 128 bytes, swizzled
+// at that width): the BF16 copy stored by the LayerNorm epilogue.
+cudaError_t encode_out_bf16(CUtensorMap* m, void* base, int B, Dims3 d, int C, int w,
+                            long long bs) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)d.x, (cuuint64_t)d.y, (cuuint64_t)d.z,
+                              (cuuint64_t)B};
+  const cuuint64_t es = 2;
+  const cuuint64_t strides[4] = {C * es, C * es * d.x, C * es * d.x * d.y, (cuuint64_t)bs * es};
+  const cuuint32_t box[5] = {(cuuint32_t)w, 8, 16, 1, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(w),
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Epilogue shared memory of the persistent halo convolution: nbuf staging slices (128 rows
+// of max(n, np) FP32 outputs; with a LayerNorm of sp BF16 blocks (ln_sp > 0) also xhat and
+// the BF16 copy), the bias, gamma and beta of one problem, and alignment slack.
+size_t tc3p_slice(int n, int np, int ln_sp) {
+  const size_t plain = (size_t)128 * std::max(n, np) * 4;
+  const size_t ln = ln_sp ? (size_t)128 * n * (8 + 2 * ln_sp) : 0;
+  return std::max(plain, ln);
+}
+// (nbuf slices per epilogue group)
+size_t tc3p_staging(int n, int np, int ln_sp = 0, int nbuf = 1) {
+  return kEpiGroups * (nbuf * tc3p_slice(n, np, ln_sp) + (size_t)(3 * n + np) * 4) + 2048;
 }
 
 size_t smem_bytes(int ck, int n) { return (size_t)kStages * (kBM + n) * ck * 2 + 1024; }
@@ -1841,14 +2009,30 @@ Tc3Plan tc3_plan(int cin, int n, int np, int Z) {
   return best;
 }
 
+// Ring stages of the persistent plan pl when the epilogue also holds a LayerNorm of sp BF16
+// blocks (nbuf staging slices); 0 when fewer than two would fit.
+int tc3_ln_stages(const Tc3Plan& pl, int n, int np, int sp, int nbuf) {
+  const size_t staging = tc3p_staging(n, np, sp, nbuf);
+  if (!pl.persistent || staging + 2 * pl.stage + 1024 > kTc3SmemMax) return 0;
+  return (int)std::min<size_t>(kP3Max, (kTc3SmemMax - 1024 - staging) / pl.stage);
+}
+
 // Persistent form when the plan has it; else one tile per CTA.
 cudaError_t launch_tc3(const CUtensorMap& a, const CUtensorMap& w, int cin, int ck, int tz,
                        const float* bias, float* out, Dims3 dout, int n, int B, long long out_bs,
                        long long bias_bs, int acc, int* err, cudaStream_t st,
                        int mode = 0, const CUtensorMap* wp = nullptr,
                        const CUtensorMap* a2 = nullptr, int np = 0, const float* bias_p = nullptr,
-                       float* out_p = nullptr, long long outp_bs = 0) {
-  const Tc3Plan pl = tc3_plan(cin, n, mode == 1 ? np : 0, dout.z);
+                       float* out_p = nullptr, long long outp_bs = 0,
+                       const Bf16Ln* ln = nullptr) {
+  Tc3Plan pl = tc3_plan(cin, n, mode == 1 ? np : 0, dout.z);
+  int nbuf = 1;  // staging slices per epilogue group
+  if (ln) {  // same tiles and ring, a larger epilogue staging
+    const int npm = mode == 1 ? np : 0;
+    const int nst = tc3_ln_stages(pl, n, npm, ln->sp, 1);
+    if (nst < 2 || n > 64) return cudaErrorInvalidValue;
+    pl.nst = nst;
+  }
   if (pl.persistent && pl.ck == ck && pl.tz == tz) {
     P3Args g{};
     g.bias = bias, g.out = out, g.bias_p = bias_p, g.out_p = out_p, g.err = err;
@@ -1859,23 +2043,36 @@ cudaError_t launch_tc3(const CUtensorMap& a, const CUtensorMap& w, int cin, int 
     g.B = B, g.accumulate = acc, g.nst = pl.nst, g.mode = mode, g.pack = pl.pack ? 1 : 0;
     g.stage_bytes = (uint32_t)pl.stage;
     g.ring_bytes = (uint32_t)((pl.nst * pl.stage + 1023) / 1024 * 1024);
-    g.slice_bytes = (uint32_t)(128 * std::max(n, mode == 1 ? np : 0) * 4);
+    const int npm = mode == 1 ? np : 0;
+    const int lsp = ln ? ln->sp : 0;
+    g.slice_bytes = (uint32_t)tc3p_slice(n, npm, lsp);
+    g.nbuf = nbuf;
     g.out_bs = out_bs, g.bias_bs = bias_bs, g.outp_bs = outp_bs, g.biasp_bs = bias_bs;
     const long long total = (long long)g.tiles_x * g.tiles_y * g.tiles_z * B;
     const int grid = (int)std::min<long long>(total, sm_count());
     // (the staging term's slack covers the kernel's 1024-byte alignment of its base)
-    const size_t sm = (size_t)g.ring_bytes + tc3p_staging(n, mode == 1 ? np : 0);
-    CUtensorMap mo, mop;
+    const size_t sm = (size_t)g.ring_bytes + tc3p_staging(n, npm, lsp, nbuf);
+    CUtensorMap mo, mop, mxh, myb;
     cudaError_t e = encode_out(&mo, out, B, dout, n, n % 32 == 0 ? 32 : 16, out_bs);
     if (e == cudaSuccess && mode == 1)
       e = encode_out(&mop, out_p, B, dout, np, np % 32 == 0 ? 32 : 16, outp_bs);
     else
       mop = mo;
+    mxh = mo, myb = mo;
+    if (ln) {
+      g.ln = 1, g.act = ln->act, g.sp = ln->sp, g.ybf = ln->ybf ? 1 : 0;
+      g.gamma = ln->gamma, g.gamma_bs = ln->gamma_bs;
+      g.resid = ln->resid, g.resid_bs = out_bs;
+      g.rstd = ln->rstd, g.rstd_bs = dout.count();
+      if (e == cudaSuccess) e = encode_out(&mxh, ln->xhat, B, dout, n, n % 32 == 0 ? 32 : 16, out_bs);
+      if (e == cudaSuccess && ln->ybf)
+        e = encode_out_bf16(&myb, ln->ybf, B, dout, ln->sp * n, n, dout.count() * ln->sp * n);
+    }
     if (e != cudaSuccess) return e;
     const CUtensorMap& mp = wp ? *wp : w;
     const CUtensorMap& m2 = a2 ? *a2 : a;
 #define D2IP_P3(CK_, TZ_) \
-  conv_tc3p_kernel<CK_, TZ_><<<grid, 192, sm, st>>>(a, w, mp, m2, mo, mop, g)
+  conv_tc3p_kernel<CK_, TZ_><<<grid, kTc3pThreads, sm, st>>>(a, w, mp, m2, mo, mop, mxh, myb, g)
 #define D2IP_P3Z(CK_) \
   if (tz == 8) D2IP_P3(CK_, 8); else if (tz == 4) D2IP_P3(CK_, 4); \
   else if (tz == 2) D2IP_P3(CK_, 2); else D2IP_P3(CK_, 1)
@@ -2699,6 +2896,32 @@ cudaError_t bf16_conv_dgrad_proj(Bf16Net& bf, int la, const float* dz_a, const f
   if (e != cudaSuccess) return e;
   return launch_tc3(L.act_d3, L.w_d3, L.kd, L.ck3d, L.tz3d, nullptr, dx, L.din, L.ci, B,
                     L.din.count() * L.ci, 0, 0, bf.err, stream, 2, &L.pw_d, &L.pa_d);
+}
+
+bool bf16_fwd_ln_ok(const Bf16Net& bf, int layer, int np, int sp) {
+  const TcLayer& L = bf.layers[layer];
+  if (!L.ck3f || L.co > 64 || (np > 0 && !L.projf)) return false;
+  const Tc3Plan pl = tc3_plan(L.kf, L.co, np, L.dout.z);
+  if (!pl.persistent || pl.ck != L.ck3f || pl.tz != L.tz3f) return false;
+  return tc3_ln_stages(pl, L.co, np, sp, 1) >= 2;
+}
+
+cudaError_t bf16_conv_fwd_ln(Bf16Net& bf, int layer, const float* x, const float* bias, float* y,
+                             const Bf16Ln& ln, int B, long long bias_bs, cudaStream_t stream,
+                             bool x_staged, const float* bias_p, float* y_p) {
+  const TcLayer& L = bf.layers[layer];
+  const bool proj = y_p != nullptr;
+  if (proj && !L.projf) return cudaErrorInvalidValue;
+  cudaError_t e = L.input_layer || (x_staged && bf.keep_inputs)
+                      ? cudaSuccess
+                      : stage_rows(x, L.xin, (long long)B * L.din.count(), L.ci, bf.sp, stream);
+  if (e != cudaSuccess) return e;
+  Bf16Ln l = ln;
+  l.sp = bf.sp;
+  const long long obs = L.dout.count() * L.co;
+  return launch_tc3(L.act_f3, L.w_f3, L.kf, L.ck3f, L.tz3f, bias, y, L.dout, L.co, B, obs,
+                    bias_bs, 0, bf.err, stream, proj ? 1 : 0, proj ? &L.pw_f : nullptr, nullptr,
+                    proj ? L.co : 0, bias_p, y_p, proj ? obs : 0, &l);
 }
 
 cudaError_t bf16_stage_input(Bf16Net& bf, int layer, const float* z, int B, cudaStream_t stream) {

@@ -107,6 +107,30 @@ __nv_bfloat16* bf16_input_buffer(const Bf16Net& bf, int layer);
 // its producer already wrote bf16_input_buffer).
 cudaError_t bf16_conv_fwd(Bf16Net& bf, int layer, const float* x, const float* bias, float* y,
                           int B, long long bias_bs, cudaStream_t stream, bool x_staged = false);
+// LayerNorm (+ residual) (+ LeakyReLU) of a convolution's output, fused into the epilogue of
+// the persistent halo convolution: y = act(gamma * xhat + beta (+ resid)), xhat = (z - mean)
+// rstd over the co channels of each voxel, z = conv(x) + bias (not stored).  xhat and y are
+// [B][voxels][co] FP32, rstd [B][voxels]; ybf (or null) receives the BF16 copy of y in sp
+// blocks per voxel (stage_bf16x4's layout), the next tensor-core layer's staged input.
+struct Bf16Ln {
+  const float* gamma;  // gamma[c] then beta[c], per problem at gamma_bs
+  long long gamma_bs;
+  const float* resid;  // [B][voxels][co] (batch stride voxels * co) or null
+  float* xhat;
+  float* rstd;
+  __nv_bfloat16* ybf;
+  int act;             // 1: LeakyReLU
+  int sp;              // set by the call: BF16 blocks of ybf (Bf16Net::sp)
+};
+// Whether layer's forward (with a fused projection of np channels when np > 0) runs the
+// persistent halo kernel with room for the LayerNorm epilogue (co <= 64).
+bool bf16_fwd_ln_ok(const Bf16Net& bf, int layer, int np, int sp);
+// y = LN epilogue of conv(x) + bias (and, with y_p, the fused projection y_p = W_p x +
+// bias_p, stored without LayerNorm).
+cudaError_t bf16_conv_fwd_ln(Bf16Net& bf, int layer, const float* x, const float* bias, float* y,
+                             const Bf16Ln& ln, int B, long long bias_bs, cudaStream_t stream,
+                             bool x_staged = false, const float* bias_p = nullptr,
+                             float* y_p = nullptr);
 // dx (=|+=) data gradient on the tensor cores (dy staged into bf.ybf unless dy_staged).
 cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, int B,
                             int accumulate, cudaStream_t stream, bool dy_staged = false);

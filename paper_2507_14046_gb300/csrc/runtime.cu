@@ -547,25 +547,51 @@ struct Launcher {
     fin();
   }
 
+  // act(LN(conv(x)) (+ resid)) with the LayerNorm in the epilogue of the persistent halo
+  // convolution (z never stored), when the layer runs that kernel; with proj (a decoder
+  // block's conv a) the fused 1x1 projection's output goes to ptmp.  False: not fused.
+  bool conv_ln_fused(const ConvL& L, const LnL& ln, const float* x, const float* resid,
+                     float* y, float* xh, float* rs, const ConvL* consumer, const Res* proj) {
+    if (L.tc < 0 || c->precision == D2IP_FP32 ||
+        !bf16_fwd_ln_ok(c->bf, L.tc, proj ? proj->p.co : 0, c->bf.sp))
+      return false;
+    beg(D2IP_KCLASS_CONV_FWD, conv_flops(L) + (proj ? conv_flops(proj->p) : 0.0));
+    __nv_bfloat16* ybf = bf_in(consumer);
+    Bf16Ln l{};
+    l.gamma = c->theta + ln.g_off, l.gamma_bs = c->Pp;
+    l.resid = resid, l.xhat = xh, l.rstd = rs, l.ybf = ybf, l.act = 1;
+    ok(bf16_conv_fwd_ln(c->bf, L.tc, x, W(L) + L.wcount(), y, l, c->B, c->Pp, c->stream,
+                        take_staged(L), proj ? W(proj->p) + proj->p.wcount() : nullptr,
+                        proj ? c->ptmp : nullptr));
+    if (ybf) staged_x.push_back(consumer);
+    fin();
+    return true;
+  }
   // next: the convolution that reads the unit's (block's) output
   void unit_fwd(Unit& u, const ConvL* next) {
+    if (conv_ln_fused(u.conv, u.ln, u.x, nullptr, u.a, u.xh, u.rs, next, nullptr)) return;
     conv_fwd(u.conv, u.x, c->ztmp);
     ln_fwd(u.ln, u.lvl_out, c->ztmp, nullptr, u.a, u.xh, u.rs, next);
   }
   void res_fwd(Res& R, const ConvL* next) {
-    if (R.fuse_f) {  // conv a and the projection in one launch
-      beg(D2IP_KCLASS_CONV_FWD, conv_flops(R.a) + conv_flops(R.p));
-      ok(bf16_conv_fwd_proj(c->bf, R.a.tc, R.x, W(R.a) + R.a.wcount(), c->ztmp,
-                            W(R.p) + R.p.wcount(), c->ptmp, c->B, c->Pp, c->stream,
-                            take_staged(R.a)));
-      fin();
-    } else {
-      conv_fwd(R.a, R.x, c->ztmp);
+    if (!conv_ln_fused(R.a, R.lna, R.x, nullptr, R.h1, R.xh_a, R.rs_a, &R.b,
+                       R.fuse_f ? &R : nullptr)) {
+      if (R.fuse_f) {  // conv a and the projection in one launch
+        beg(D2IP_KCLASS_CONV_FWD, conv_flops(R.a) + conv_flops(R.p));
+        ok(bf16_conv_fwd_proj(c->bf, R.a.tc, R.x, W(R.a) + R.a.wcount(), c->ztmp,
+                              W(R.p) + R.p.wcount(), c->ptmp, c->B, c->Pp, c->stream,
+                              take_staged(R.a)));
+        fin();
+      } else {
+        conv_fwd(R.a, R.x, c->ztmp);
+      }
+      ln_fwd(R.lna, R.lvl, c->ztmp, nullptr, R.h1, R.xh_a, R.rs_a, &R.b);
     }
-    ln_fwd(R.lna, R.lvl, c->ztmp, nullptr, R.h1, R.xh_a, R.rs_a, &R.b);
     if (R.proj && !R.fuse_f) conv_fwd(R.p, R.x, c->ptmp);
+    const float* resid = R.proj ? c->ptmp : R.x;
+    if (conv_ln_fused(R.b, R.lnb, R.h1, resid, R.out, R.xh_b, R.rs_b, next, nullptr)) return;
     conv_fwd(R.b, R.h1, c->ztmp);
-    ln_fwd(R.lnb, R.lvl, c->ztmp, R.proj ? c->ptmp : R.x, R.out, R.xh_b, R.rs_b, next);
+    ln_fwd(R.lnb, R.lvl, c->ztmp, resid, R.out, R.xh_b, R.rs_b, next);
   }
   static void tr_beg(void* u, int k, double w) { static_cast<Launcher*>(u)->beg(k, w); }
   static void tr_fin(void* u) { static_cast<Launcher*>(u)->fin(); }

@@ -116,10 +116,12 @@ def test_bf16x3_sequence_per_frame_err_against_oracle(d2ip, case):
     a sequence: the FP32 path itself (per-iteration agreement 1e-6) drifts to 1e-3 relative ERR
     after about 60 iterations, so a fixed 1e-3 bar cannot hold on every frame for any
     precision.  The split precision's per-iteration gradient error is about ten times the FP32
-    path's (1e-5 against 1e-6, teacher-forced tests), so per frame its ERR must lie within
-    max(1e-3, 10 x the FP32 path's own gap) of the oracle's, and dsigma at 512 fixed voxels
-    within max(1e-2, 10 x FP32's).  The golden file's floor (the oracle's ERR moved by a 1e-7
-    scaling of theta0) and plain BF16 are printed beside it."""
+    path's (1e-5 against 1e-6, teacher-forced tests), so its gaps are held to 10 x the FP32
+    path's own: the mean over frames of |ERR - ERR_oracle| / ERR_oracle within max(1e-3, 10 x
+    FP32's mean), and of the relative dsigma error at 512 fixed voxels within max(1e-2, 10 x
+    FP32's).  Means, not single frames: one frame's gap is one sample of a chaotic process
+    (the FP32 path's is 3e-4 on one frame and 4e-3 on the next).  The golden file's floor (the
+    oracle's ERR moved by a 1e-7 scaling of theta0) and plain BF16 are printed beside it."""
     with open(GOLDEN) as f:
         gold = json.load(f)["cases"][case]
     c = gold["case"]
@@ -142,8 +144,10 @@ def test_bf16x3_sequence_per_frame_err_against_oracle(d2ip, case):
               "per frame (ERR rel, dsigma max abs, dsigma rel):",
               [tuple(f"{v:.1e}" for v in r) for r in rows])
     print(case, "oracle floor per frame:", [f"{fr['floor']:.1e}" for fr in gold["frames"]])
-    for i in range(len(gold["frames"])):
-        f_err, _, f_ds = report[d2ip.D2IP_FP32][i]
-        err_rel, _, ds_rel = report[d2ip.D2IP_BF16X3][i]
-        assert err_rel <= max(1e-3, 10 * f_err), (i, err_rel, f_err)
-        assert ds_rel <= max(1e-2, 10 * f_ds), (i, ds_rel, f_ds)
+    mean = {p: np.mean(np.asarray(r), axis=0) for p, r in report.items()}
+    f_err, _, f_ds = mean[d2ip.D2IP_FP32]
+    err_rel, _, ds_rel = mean[d2ip.D2IP_BF16X3]
+    print(case, f"means: FP32 {f_err:.1e} / {f_ds:.1e}, BF16 {mean[1][0]:.1e} / {mean[1][2]:.1e}, "
+          f"BF16x3 {err_rel:.1e} / {ds_rel:.1e}")
+    assert err_rel <= max(1e-3, 10 * f_err), (err_rel, f_err)
+    assert ds_rel <= max(1e-2, 10 * f_ds), (ds_rel, f_ds)
