@@ -158,6 +158,13 @@ d2ip_status d2ip_set_regularizer(d2ip_ctx* ctx, double lambda_tv, double lambda_
                                  double lambda_t, double eps);
 /* Zero the Adam moments and step count (done at the start of every fitted frame). */
 d2ip_status d2ip_reset_optimizer(d2ip_ctx* ctx);
+/* reset_moments_per_frame != 0 (the default): d2ip_fit_frame and every frame of
+ * d2ip_fit_sequence/batched start with a fresh Adam state, the paper's reading of Eqs. 7-8
+ * (only the weights theta carry from UPWS to frame 1 and from frame to frame).  0: the Adam
+ * moments and step count carry on too -- a sequence is then one Adam run whose target
+ * measurements change at each frame (its state is reset once, at the start of UPWS, or of
+ * frame 0 when there is no UPWS phase); d2ip_fit_frame then continues the current state. */
+d2ip_status d2ip_set_frame_reset(d2ip_ctx* ctx, int reset_moments_per_frame);
 
 /* n_steps DIP iterations (forward phi, r = J phi - dv, loss = |r|^2/m in FP64, gradient
  * (2/m) J^T r back through phi, Adam) on measurements dV ([batch][m]) WITHOUT resetting the

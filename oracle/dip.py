@@ -126,26 +126,29 @@ class SequenceResult:
 
 
 def fit_sequence(spec, J, Zin, V, theta0, upws_steps, first_steps, later_steps, lr,
-                 dv0=None, reg_factory=None) -> SequenceResult:
+                 dv0=None, reg_factory=None, carry_state=False) -> SequenceResult:
     """UPWS (Eqs. 5-7) then TPP over the frames (Eqs. 8-9).
 
     UPWS runs ``upws_steps`` on ``dv0`` (default: frame 0) from ``theta0``; frame 0 then
     runs ``first_steps`` from the UPWS result and every later frame ``later_steps`` from
     the previous frame's weights.  ``reg_factory(i, previous_outputs)`` may return a
-    regulariser callback for frame i.
+    regulariser callback for frame i.  The paper carries only the weights (a fresh Adam
+    state per frame, the default); ``carry_state`` instead keeps one Adam state (moments and
+    step count) through UPWS and all frames.
     """
     V = np.atleast_2d(np.asarray(V, dtype=np.float64))
     theta = np.asarray(theta0, dtype=np.float64).copy()
+    st = AdamState.fresh(theta.size) if carry_state else None
     if upws_steps > 0:
         d0 = V[0] if dv0 is None else np.asarray(dv0, dtype=np.float64)
         reg = reg_factory(-1, []) if reg_factory else None
-        theta = fit_frame(spec, J, Zin, d0, theta, upws_steps, lr, reg).theta
+        theta = fit_frame(spec, J, Zin, d0, theta, upws_steps, lr, reg, state=st).theta
     theta_upws = theta.copy()
     outs, res = [], []
     for i in range(V.shape[0]):
         reg = reg_factory(i, list(outs)) if reg_factory else None
         fr = fit_frame(spec, J, Zin, V[i], theta, first_steps if i == 0 else later_steps,
-                       lr, reg)
+                       lr, reg, state=st)
         theta = fr.theta
         outs.append(fr.dsigma)
         res.append(fr.residual)

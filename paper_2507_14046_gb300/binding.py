@@ -51,6 +51,7 @@ _SIGS = {
     "d2ip_set_input": [_vp, _vp, _vp],
     "d2ip_set_optim": [_vp, _d, _d, _d, _d],
     "d2ip_reset_optimizer": [_vp],
+    "d2ip_set_frame_reset": [_vp, _i],
     "d2ip_set_regularizer": [_vp, _d, _d, _d, _d],
     "d2ip_run_steps": [_vp, _vp, _i, _vp],
     "d2ip_forward": [_vp, _vp],
@@ -246,6 +247,7 @@ def d2ip_layernorm_workspace(*args) -> int:
 
 for _name in ("d2ip_set_grid", "d2ip_load_J", "d2ip_get_colnorms", "d2ip_set_input",
               "d2ip_set_optim", "d2ip_set_regularizer", "d2ip_reset_optimizer",
+              "d2ip_set_frame_reset",
               "d2ip_run_steps", "d2ip_forward",
               "d2ip_get_grad", "d2ip_fit_frame", "d2ip_fit_sequence", "d2ip_set_state",
               "d2ip_err_ratio", "d2ip_sync", "d2ip_profile_iterations", "d2ip_graph_kernels"):
@@ -321,6 +323,9 @@ class Context:
     def set_regularizer(self, lambda_tv=0.002, lambda_s=1.0, lambda_t=0.1, eps=1e-8):
         d2ip_set_regularizer(self.handle, float(lambda_tv), float(lambda_s), float(lambda_t),
                              float(eps))
+
+    def set_frame_reset(self, reset_moments_per_frame: bool):
+        d2ip_set_frame_reset(self.handle, 1 if reset_moments_per_frame else 0)
 
     def run_steps(self, dV, n_steps, trace=False):
         tr = np.zeros((n_steps, self.batch), dtype=np.float64) if trace else None

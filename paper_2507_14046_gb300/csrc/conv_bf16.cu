@@ -1732,31 +1732,41 @@ weights_all_bf16_kernel(const float* __restrict__ theta, __nv_bfloat16* __restri
 
 // Split weights of every layer (BF16x3): forward rows [t][co][3 ci] = [hi | hi | lo] over ci
 // and data-gradient rows [T-1-t][ci][3 co] = [hi | hi | lo] over co, hi = bf16(w),
-// lo = bf16(w - hi); a thread per (layer element, problem).  Blocks are ranged per layer as
-// in weights_all_bf16_kernel, each covering 256 elements [o][t][c] of its layer.
+// lo = bf16(w - hi).  A block takes one (layer, tap, chunk of 32 output channels), as
+// weights_all_bf16_kernel: coalesced reads of W[o][tap][0..ci), forward rows written in
+// order, the data-gradient rows through shared-memory tiles of hi and lo.
 __global__ void __launch_bounds__(256)
 weights_split_bf16_kernel(const float* __restrict__ theta, __nv_bfloat16* __restrict__ wb,
                           long long Pp, long long wstride, const __grid_constant__ WTable t) {
+  __shared__ __nv_bfloat16 th[kWOc][256 + 2], tl[kWOc][256 + 2];
   int l = 0;
   while (l + 1 < t.nl && (int)blockIdx.x >= t.blk0[l + 1]) ++l;
   const int b = blockIdx.y;
   const int ci = t.ci[l], cr = t.ci_real[l], co = t.co[l], T = t.T[l];
-  const long long e = (long long)(blockIdx.x - t.blk0[l]) * blockDim.x + threadIdx.x;
-  if (e >= (long long)co * T * ci) return;
-  const int c = (int)(e % ci);
-  const long long r = e / ci;
-  const int tap = (int)(r % T), o = (int)(r / T);
-  const float v = c < cr ? theta[(long long)b * Pp + t.w_off[l] + r * cr + c] : 0.f;
-  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-  const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+  const int nch = (co + kWOc - 1) / kWOc;
+  const int q = blockIdx.x - t.blk0[l];
+  const int tap = q / nch, o0 = (q % nch) * kWOc;
+  const int no = co - o0 < kWOc ? co - o0 : kWOc;
+  const float* src = theta + (long long)b * Pp + t.w_off[l];
   __nv_bfloat16* base = wb + (long long)b * wstride;
-  __nv_bfloat16* f =
-      base + t.wf_off[l] + ((long long)packed_tap(tap, t.permf[l]) * co + o) * 3 * ci;
-  f[c] = hi, f[ci + c] = hi, f[2 * ci + c] = lo;
-  if (t.dgrad[l]) {
-    __nv_bfloat16* d =
-        base + t.wd_off[l] + ((long long)packed_tap(T - 1 - tap, t.permd[l]) * ci + c) * 3 * co;
-    d[o] = hi, d[co + o] = hi, d[2 * co + o] = lo;
+  const long long frow = t.wf_off[l] + (long long)packed_tap(tap, t.permf[l]) * co * 3 * ci;
+  for (int e = threadIdx.x; e < no * ci; e += blockDim.x) {
+    const int ol = e / ci, c = e % ci;
+    const float v = c < cr ? src[((long long)(o0 + ol) * T + tap) * cr + c] : 0.f;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    th[ol][c] = hi;
+    tl[ol][c] = lo;
+    __nv_bfloat16* f = base + frow + (long long)(o0 + ol) * 3 * ci;  // [t][co][3 ci]
+    f[c] = hi, f[ci + c] = hi, f[2 * ci + c] = lo;
+  }
+  if (!t.dgrad[l]) return;
+  __syncthreads();
+  const long long drow = t.wd_off[l] + (long long)packed_tap(T - 1 - tap, t.permd[l]) * ci * 3 * co;
+  for (int e = threadIdx.x; e < no * ci; e += blockDim.x) {
+    const int ol = e % no, c = e / no;
+    __nv_bfloat16* d = base + drow + (long long)c * 3 * co + o0 + ol;  // [26-t][ci][3 co]
+    d[0] = th[ol][c], d[co] = th[ol][c], d[2 * co] = tl[ol][c];
   }
 }
 
@@ -1804,9 +1814,12 @@ cudaError_t encode_act(CUtensorMap* m, void* base, int B, Dims3 d, int C, int ck
   const cuuint32_t box[5] = {(cuuint32_t)ck, (cuuint32_t)(kBX * S), (cuuint32_t)(kBY * S),
                              (cuuint32_t)(kBZ * S), 1};
   const cuuint32_t estr[5] = {1, (cuuint32_t)S, (cuuint32_t)S, (cuuint32_t)S, 1};
+  // a channel block of a wider row: no L2 promotion, which would fetch the other blocks too
   const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(ck),
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                        row && row != C ? CU_TENSOR_MAP_L2_PROMOTION_NONE
+                                        : CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -1844,7 +1857,9 @@ cudaError_t encode_box(CUtensorMap* m, void* base, int B, Dims3 d, int C, int ck
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(ck),
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                        row && row != C ? CU_TENSOR_MAP_L2_PROMOTION_NONE
+                                        : CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -2766,8 +2781,10 @@ cudaError_t bf16_prepare_kernels() {
 
 cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long long Pp,
                                  cudaStream_t stream) {
-  if (bf.sp > 1) {  // split weights: one launch, a thread per (layer element, problem)
+  if (bf.sp > 1) {  // split weights: one launch, a block per (layer, tap, 32 output channels)
     if (bf.layers.empty() || bf.layers.size() > (size_t)kWMaxLayers) return cudaErrorInvalidValue;
+    for (const TcLayer& L : bf.layers)
+      if (L.ci > 256) return cudaErrorInvalidValue;
     WTable t{};
     t.nl = (int)bf.layers.size();
     int blk = 0;
@@ -2775,7 +2792,7 @@ cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long lo
       const TcLayer& L = bf.layers[i];
       const int T = L.k * L.k * L.k;
       t.blk0[i] = blk;
-      blk += (int)ceil_div((long long)L.co * T * L.ci, 256);
+      blk += T * (int)ceil_div(L.co, kWOc);
       t.w_off[i] = L.w_off, t.wf_off[i] = L.wf_off, t.wd_off[i] = L.wd_off;
       t.ci[i] = L.ci, t.ci_real[i] = L.ci_real, t.co[i] = L.co, t.T[i] = T;
       t.dgrad[i] = L.dgrad ? 1 : 0;

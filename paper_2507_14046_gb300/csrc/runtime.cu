@@ -77,6 +77,7 @@ struct d2ip_ctx {
   int m = 0;
   bool j_ready = false, input_ready = false;
   double lr = 1e-3, beta1 = 0.9, beta2 = 0.999, eps = 1e-8;
+  bool frame_reset = true;  // fresh Adam state at every fitted frame (else carried)
   // 4D-TV regulariser (off when lam_tv == 0)
   double lam_tv = 0.0, lam_s = 1.0, lam_t = 0.1, tv_eps = 1e-8;
 
@@ -917,6 +918,7 @@ SeqJob make_sequence_job(d2ip_ctx* c, const float* V, int T, const float* dV0, i
   j.resid = resid;
   const bool reg = c->lam_tv != 0.0;
   if (reg) j.ops.push_back({SeqOp::kPrev, 0});
+  // (with the carried-state option the Adam state restarts once, at the sequence's start)
   if (upws > 0) {  // UPWS (Eqs. 5-7): N_0 steps on one frame from the initial weights
     j.ops.push_back({SeqOp::kStage, -1});
     j.ops.push_back({SeqOp::kReset, 0});
@@ -924,7 +926,7 @@ SeqJob make_sequence_job(d2ip_ctx* c, const float* V, int T, const float* dV0, i
   }
   for (int i = 0; i < T; ++i) {  // TPP (Eqs. 8-9): theta carries over, Adam restarts
     j.ops.push_back({SeqOp::kStage, i});
-    j.ops.push_back({SeqOp::kReset, 0});
+    if (c->frame_reset || (i == 0 && upws == 0)) j.ops.push_back({SeqOp::kReset, 0});
     j.ops.push_back({SeqOp::kSteps, i == 0 ? first : later});
     j.ops.push_back({SeqOp::kEval, i});
     if (reg) {  // the temporal term of frame i + 1 sees frames 0..i
@@ -1281,6 +1283,12 @@ d2ip_status d2ip_set_regularizer(d2ip_ctx* c, double lambda_tv, double lambda_s,
   return D2IP_OK;
 }
 
+d2ip_status d2ip_set_frame_reset(d2ip_ctx* c, int reset_moments_per_frame) {
+  if (!c) return fail(nullptr, D2IP_ERR_BAD_ARG, "null context");
+  c->frame_reset = reset_moments_per_frame != 0;
+  return D2IP_OK;
+}
+
 d2ip_status d2ip_reset_optimizer(d2ip_ctx* c) {
   if (!c) return fail(nullptr, D2IP_ERR_BAD_ARG, "null context");
   if (!c->arena) return fail(c, D2IP_ERR_STATE, "network not set up");
@@ -1331,8 +1339,10 @@ d2ip_status d2ip_fit_frame(d2ip_ctx* c, const float* dV, int n_steps, float* dsi
   if (!dV || n_steps < 0) return fail(c, D2IP_ERR_BAD_ARG, "bad dV or n_steps");
   s = stage_dv(c, dV, c->m);
   if (s) return s;
-  s = reset_optimizer(c);
-  if (s) return s;
+  if (c->frame_reset) {
+    s = reset_optimizer(c);
+    if (s) return s;
+  }
   if (c->lam_tv != 0.0) CK(set_device_int(c->nprev, 0, c->stream));  // no earlier frames
   s = run_steps(c, n_steps, loss_trace);
   if (s) return s;

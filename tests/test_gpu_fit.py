@@ -308,3 +308,29 @@ def test_bounded_wait_reports_timeout_and_device_stays_usable(d2ip):
     c = _ctx(d2ip, pb, 1e-3)
     tr = c.run_steps(pb.V[:1], 2, trace=True)
     assert np.all(np.isfinite(tr))
+
+
+def test_sequence_carrying_the_adam_state(d2ip):
+    """d2ip_set_frame_reset(0): one Adam state through UPWS and every frame, against the
+    oracle's carried-state sequence (per-frame ERR within 1e-3) and bit for bit against the
+    same schedule run by hand through d2ip_run_steps (which never resets the state)."""
+    pb = problems.make((16, 16, 8), 1, 2, (8, 16), seed=2, T=4)
+    lr, up, first, later = 1e-3, 30, 15, 10
+    ref = dip.fit_sequence(pb.spec, pb.Jn64, pb.Zin.astype(np.float64), pb.V, pb.theta0, up,
+                           first, later, lr, carry_state=True)
+    c = _ctx(d2ip, pb, lr)
+    c.set_frame_reset(False)
+    Sig, res = c.fit_sequence(pb.V[None], up, first, later)
+    for i in range(4):
+        e_gpu = dip.err_ratio(Sig[0, i], pb.truth[i])
+        e_ref = dip.err_ratio(ref.Sigma[i], pb.truth[i])
+        assert abs(e_gpu - e_ref) <= 1e-3 * e_ref, i
+    c2 = _ctx(d2ip, pb, lr)
+    c2.run_steps(pb.V[:1], up)
+    for i in range(4):
+        c2.run_steps(pb.V[i:i + 1], first if i == 0 else later)
+        np.testing.assert_array_equal(c2.forward()[0], Sig[0, i])
+    # the default (a fresh state per frame) follows a different trajectory
+    c3 = _ctx(d2ip, pb, lr)
+    Sig3, _ = c3.fit_sequence(pb.V[None], up, first, later)
+    assert np.abs(Sig3[0, -1] - Sig[0, -1]).max() > 1e-6

@@ -25,6 +25,23 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
+def _faces(a):
+    """The elements on the six outer faces of a (Z, Y, X, C) volume (the zero-padded halo)."""
+    m = np.zeros(a.shape[:3], dtype=bool)
+    m[0], m[-1] = True, True
+    m[:, 0], m[:, -1] = True, True
+    m[:, :, 0], m[:, :, -1] = True, True
+    return a[m]
+
+
+def _elementwise(got, ref):
+    """Every element within TOL of the largest magnitude, and the outer faces on their own:
+    a single wrong halo voxel cannot hide in a norm-wise error."""
+    assert np.abs(got - ref).max() <= TOL * np.abs(ref).max()
+    fg, fr = _faces(got), _faces(ref)
+    assert np.abs(fg - fr).max() <= TOL * max(np.abs(fr).max(), 1e-30)
+
+
 def _err_word(ws):
     base = ws.data_ptr()
     off = (-base) % 1024
@@ -61,6 +78,8 @@ def test_tc_conv_forward_and_dgrad(d2ip, din, ci, co, k, s):
     errs = [rel(y[b].cpu().numpy(), ref[b]) for b in range(B)]
     print("tc forward rel err", errs)
     assert max(errs) < TOL
+    for b in range(B):
+        _elementwise(y[b].cpu().numpy(), ref[b])
     if k == 1 and s != 1:
         return
     dy = bf16_round(rng.standard_normal((B, *dout, co)).astype(np.float32))
@@ -73,6 +92,7 @@ def test_tc_conv_forward_and_dgrad(d2ip, din, ci, co, k, s):
     for b in range(B):
         gdx = onet.conv3d_backward(x[b].astype(np.float64), W[b], s, dy[b].astype(np.float64))[0]
         assert rel(dx[b].cpu().numpy(), gdx) < TOL
+        _elementwise(dx[b].cpu().numpy(), gdx)
 
 
 def test_tc_rejects_unsupported_shapes(d2ip):

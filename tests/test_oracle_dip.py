@@ -196,6 +196,26 @@ def test_sequence_equals_manual_chaining():
                                                               1e-3).dsigma)
 
 
+def test_sequence_carrying_the_adam_state():
+    """carry_state keeps one Adam state through UPWS and the frames: on a sequence whose frames
+    are all the same measurement, UPWS and the frames together are one uninterrupted fit of
+    the total step count (bit for bit), while the paper's fresh state per frame is not."""
+    spec = net.NetSpec((4, 3, 4), 2, (3, 4), 2)
+    rng = np.random.default_rng(17)
+    n = 48
+    Zin = 0.1 * rng.standard_normal((n, 2))
+    J = rng.standard_normal((10, n))
+    v = rng.standard_normal(10)
+    V = np.stack([v, v, v])
+    th = _theta(spec, 3)
+    carry = dip.fit_sequence(spec, J, Zin, V, th, 4, 3, 2, 1e-3, carry_state=True)
+    whole = dip.fit_frame(spec, J, Zin, v, th, 4 + 3 + 2 + 2, 1e-3)
+    np.testing.assert_array_equal(carry.theta, whole.theta)
+    np.testing.assert_array_equal(carry.Sigma[-1], whole.dsigma)
+    reset = dip.fit_sequence(spec, J, Zin, V, th, 4, 3, 2, 1e-3)
+    assert np.abs(reset.theta - whole.theta).max() > 1e-6
+
+
 def test_err_ratio():
     assert dip.err_ratio([1.0, 2.0], [1.0, 2.0]) == 0.0
     assert np.isclose(dip.err_ratio([0.0, 0.0], [3.0, 4.0]), 1.0)

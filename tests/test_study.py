@@ -64,3 +64,37 @@ def test_acceleration_ordering_on_the_sequence(d2ip):
     assert E["d2ip"][-1] < E["upws"][-1] < E["dip"][-1]
     # the regulariser is small at lambda_tv = 0.002: its fit stays close to plain DIP
     assert abs(L["dip_reg"][-1] - L["dip"][-1]) < 0.05 * L["dip"][-1]
+
+
+@pytest.mark.gpu
+def test_ablation_arms_follow_the_oracle(d2ip):
+    """Every arm of the ablation, as study.run drives it through the C ABI (FP32), against the
+    oracle's fit of the same arm on a small sequence (8 x 8 x 4 grid, two levels 8/16, lr 1e-3):
+    UPWS of 20 iterations on the random task, 10 on frame 1, then 20 traced iterations on
+    frame 2 from each arm's start.  Loss traces within 1e-4 relative, per iteration."""
+    from oracle import dip, network as onet, tv4d
+    from paper_2507_14046_gb300 import synth
+    w = synth.Workload("8x8x4 test sequence", (8, 8, 4), 1, 2, (8, 16), 8, 3, 0, 0, 0, 1e-3, 3)
+    upws, first, iters, lr, reg = 20, 10, 20, 1e-3, (0.002, 1.0, 0.1, 1e-8)
+    res = study.run(w, iters=iters, upws=upws, first=first, every=10, lr=lr, reg=reg)
+    J, truth, V, Zin = synth.make_problem(w)
+    task = synth.ellipsoid_phantom(w.grid, synth.random_ellipsoids(w.grid, w.seed + 1, 0))
+    dV0 = synth.measurements(J, task[None, :], w.seed + 1)[0].astype(np.float64)
+    spec = onet.NetSpec(w.grid, w.levels, w.widths, w.c_in)
+    table = [(k, o, c, f) for _, _, k, f, o, c in onet.param_layout(spec)]
+    theta0 = synth.kaiming_theta(table, w.seed).astype(np.float64)
+    Jn, _ = dip.normalise_columns(J)
+    Z64, V64 = Zin.astype(np.float64), V.astype(np.float64)
+    th_u = dip.fit_frame(spec, Jn, Z64, dV0, theta0, upws, lr).theta
+    th_f1 = dip.fit_frame(spec, Jn, Z64, V64[0], th_u, first, lr).theta
+    tv = tv4d.regulariser(spec.dims(0), [], reg[0], reg[1], reg[2], reg[3])
+    ref = {"dip": dip.fit_frame(spec, Jn, Z64, V64[1], theta0, iters, lr).losses,
+           "dip_reg": dip.fit_frame(spec, Jn, Z64, V64[1], theta0, iters, lr, tv).losses,
+           "upws": dip.fit_frame(spec, Jn, Z64, V64[1], th_u, iters, lr).losses,
+           "d2ip": dip.fit_frame(spec, Jn, Z64, V64[1], th_f1, iters, lr).losses}
+    for a in study.ARMS:
+        got, want = np.asarray(res["loss"][a]), np.asarray(ref[a])
+        assert got.shape == want.shape, a
+        err = np.abs(got - want) / want
+        print(a, f"max rel loss error {err.max():.2e}")
+        assert err.max() < 1e-4, a
