@@ -212,6 +212,24 @@ d2ip_status d2ip_set_state(d2ip_ctx* ctx, const float* theta, const float* adam_
 /* ERR = |est - truth| / |truth| per problem in FP64 (Sec. V-A); est, truth [batch][n]. */
 d2ip_status d2ip_err_ratio(d2ip_ctx* ctx, const float* est, const float* truth, double* out);
 
+/* Autotuning of the tensor-core tilings (BF16 precisions; on by default): when the context's
+ * workspace is built (the first d2ip_load_J / d2ip_set_input / d2ip_set_state after
+ * d2ip_set_network), every persistent halo convolution of the network -- forward and data
+ * gradient of each 3x3x3 stride-1 layer -- is timed with CUDA events for every candidate
+ * tiling (kz taps packed into one MMA or not, output z depth 1..8, channel chunk 16/32/64)
+ * on the context's own buffers, and the fastest is kept.  Choices are cached for the process
+ * per shape, so contexts of one shape share them (and their FP32 summation order); on = 0
+ * keeps the cost model's tilings.  Takes effect when the workspace is next built.  The
+ * tuning runs synchronously on the context's stream, before any graph is captured. */
+d2ip_status d2ip_set_autotune(d2ip_ctx* ctx, int on);
+/* The tilings in use, one row per tensor-core layer in module order (host arrays, rows of 15:
+ * ci, co, k, stride, out dims z, y, x, then forward {persistent, kz-packed, channel chunk,
+ * z depth} and data gradient {persistent, kz-packed, channel chunk, z depth}); us (may be
+ * NULL) receives 4 per row: the forward's tuned and cost-model times (us per launch), then the
+ * data gradient's (-1 where not timed).  *n_rows receives the number of layers (0 in FP32).
+ * D2IP_ERR_STATE before the workspace exists. */
+d2ip_status d2ip_tile_plan(d2ip_ctx* ctx, long long* rows, int cap, int* n_rows, double* us);
+
 /* Kernel classes reported by d2ip_profile_iterations, in this order. */
 #define D2IP_KCLASS_CONV_FWD 0   /* work: FLOPs (2 * out voxels * K^3 * ci * co)        */
 #define D2IP_KCLASS_CONV_DGRAD 1 /* work: FLOPs (same count as the forward)             */

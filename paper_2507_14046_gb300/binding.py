@@ -52,6 +52,8 @@ _SIGS = {
     "d2ip_set_optim": [_vp, _d, _d, _d, _d],
     "d2ip_reset_optimizer": [_vp],
     "d2ip_set_frame_reset": [_vp, _i],
+    "d2ip_set_autotune": [_vp, _i],
+    "d2ip_tile_plan": [_vp, _vp, _i, C.POINTER(_i), _vp],
     "d2ip_set_regularizer": [_vp, _d, _d, _d, _d],
     "d2ip_run_steps": [_vp, _vp, _i, _vp],
     "d2ip_forward": [_vp, _vp],
@@ -221,6 +223,16 @@ def d2ip_get_state(ctx, theta=None, adam_m=None, adam_v=None) -> int:
     return t.value
 
 
+def d2ip_tile_plan(ctx):
+    """(rows [n, 15] int64, us [n, 4]) of the tensor-core tilings in use (see d2ip.h)."""
+    n = _i()
+    _call("d2ip_tile_plan", ctx, ctx, None, 0, C.byref(n), None)
+    rows = np.zeros((n.value, 15), dtype=np.int64)
+    us = np.zeros((n.value, 4), dtype=np.float64)
+    _call("d2ip_tile_plan", ctx, ctx, rows.ctypes.data, n.value, C.byref(n), us.ctypes.data)
+    return rows, us
+
+
 def d2ip_conv3d_wgrad_workspace(*args) -> int:
     return int(_lib.d2ip_conv3d_wgrad_workspace(*args))
 
@@ -247,7 +259,7 @@ def d2ip_layernorm_workspace(*args) -> int:
 
 for _name in ("d2ip_set_grid", "d2ip_load_J", "d2ip_get_colnorms", "d2ip_set_input",
               "d2ip_set_optim", "d2ip_set_regularizer", "d2ip_reset_optimizer",
-              "d2ip_set_frame_reset",
+              "d2ip_set_frame_reset", "d2ip_set_autotune",
               "d2ip_run_steps", "d2ip_forward",
               "d2ip_get_grad", "d2ip_fit_frame", "d2ip_fit_sequence", "d2ip_set_state",
               "d2ip_err_ratio", "d2ip_sync", "d2ip_profile_iterations", "d2ip_graph_kernels"):
@@ -285,9 +297,12 @@ class Context:
     calls of the same name without the ``d2ip_`` prefix."""
 
     def __init__(self, grid, levels, widths, c_in=8, precision=D2IP_FP32, batch=1, device=0,
-                 stream=None, net="resunet"):
-        """net: "resunet" (d2ip_set_network) or "fastres" (d2ip_set_network_fastres)."""
+                 stream=None, net="resunet", autotune=True):
+        """net: "resunet" (d2ip_set_network) or "fastres" (d2ip_set_network_fastres);
+        autotune: time the tensor-core tilings when the workspace is built."""
         self.handle = d2ip_create(device, stream)
+        if not autotune:
+            d2ip_set_autotune(self.handle, 0)
         self.grid, self.batch, self.c_in = tuple(grid), batch, c_in
         X, Y, Z = grid
         d2ip_set_grid(self.handle, X, Y, Z)
@@ -323,6 +338,9 @@ class Context:
     def set_regularizer(self, lambda_tv=0.002, lambda_s=1.0, lambda_t=0.1, eps=1e-8):
         d2ip_set_regularizer(self.handle, float(lambda_tv), float(lambda_s), float(lambda_t),
                              float(eps))
+
+    def tile_plan(self):
+        return d2ip_tile_plan(self.handle)
 
     def set_frame_reset(self, reset_moments_per_frame: bool):
         d2ip_set_frame_reset(self.handle, 1 if reset_moments_per_frame else 0)

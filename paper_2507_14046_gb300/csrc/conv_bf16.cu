@@ -19,6 +19,9 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <array>
+#include <map>
+#include <mutex>
 
 #include "conv_bf16.cuh"
 
@@ -1976,46 +1979,56 @@ struct Tc3Plan {
   bool pack = false;  // kz taps packed into N (P3Args::pack)
 };
 
+// One persistent candidate: channel chunk ck, z depth tz, kz packing; persistent = false
+// when it does not fit (TMEM columns of both accumulator buffers, a stage of at most 100 KB,
+// two ring stages besides the epilogue staging).
+Tc3Plan tc3_fixed(int cin, int n, int np, int ck, int tz, bool pack) {
+  Tc3Plan p;
+  if (cin % ck) return p;
+  if (pack ? (3 * n > 256 || tz < 2 || (tz + 4) * n + tz * np > 256) : tz * (n + np) > 256)
+    return p;
+  const size_t staging = tc3p_staging(n, np);
+  const size_t stage = tc3_stage(ck, n, tz) + (size_t)np * ck * 2;
+  if (stage > 100 * 1024 || staging + 2 * stage + 1024 > kTc3SmemMax) return p;
+  p.ck = ck, p.tz = tz, p.pack = pack, p.stage = stage, p.staging = staging;
+  p.nst = (int)std::min<size_t>(kP3Max, (kTc3SmemMax - 1024 - staging) / stage);
+  p.persistent = true;
+  return p;
+}
+
+// Every persistent candidate (the autotuner's search space).
+std::vector<Tc3Plan> tc3_candidates(int cin, int n, int np) {
+  std::vector<Tc3Plan> out;
+  for (bool pack : {true, false})
+    for (int tz : {8, 4, 2, 1})
+      for (int ck : {64, 32, 16}) {
+        const Tc3Plan p = tc3_fixed(cin, n, np, ck, tz, pack);
+        if (p.persistent) out.push_back(p);
+      }
+  return out;
+}
+
+// The model's choice: the kz-packed form at the largest z depth that fits (about 2.4x fewer
+// MMAs at tz 8, 2x at tz 4), else the plain form; the channel chunk (and the plain form's z
+// depth) by TMA time per output voxel -- rows loaded per z column (halo box of tz + 2 planes
+// per x tap, plus the weight boxes) over the TMA line rate (one 32-byte row per clock for
+// ck = 16, 64 bytes for wider chunks); ties to more ring stages.  Without a persistent
+// candidate (np must be 0 then), one tile per CTA.
 Tc3Plan tc3_plan(int cin, int n, int np, int Z) {
   Tc3Plan best;
   double best_cost = 1e300;
-  const size_t staging = tc3p_staging(n, np);
-  // The kz-packed form first (about 2.4x fewer MMAs at tz 8, 2x at tz 4): MMA width 3n <= 256
-  // and both accumulator buffers ((tz + 4) n + tz np columns each) within TMEM; its z depth
-  // is the largest that fits, the channel chunk by the TMA-time model below.
-  if (3 * n <= 256) {
-    for (int tz : {8, 4, 2}) {  // (tz 1: the same MMA count as the plain form, more halo)
-      if ((tz + 4) * n + tz * np > 256) continue;
+  for (bool pack : {true, false}) {
+    for (int tz : {8, 4, 2, 1}) {
       for (int ck : {64, 32, 16}) {
-        if (cin % ck) continue;
-        const size_t stage = tc3_stage(ck, n, tz) + (size_t)np * ck * 2;
-        if (stage > 100 * 1024 || staging + 2 * stage + 1024 > kTc3SmemMax) continue;
-        const int nst = (int)std::min<size_t>(kP3Max, (kTc3SmemMax - 1024 - staging) / stage);
-        const double cost = (3.0 * 144 * (tz + 2) + 9.0 * n + np) / std::min(32, ck);
-        if (!best.pack || cost < best_cost * (1 - 1e-9) ||
-            (cost <= best_cost * (1 + 1e-9) && nst > best.nst)) {
-          best_cost = cost;
-          best.ck = ck, best.tz = tz, best.nst = nst, best.stage = stage, best.staging = staging;
-          best.persistent = best.pack = true;
-        }
+        const Tc3Plan p = tc3_fixed(cin, n, np, ck, tz, pack);
+        if (!p.persistent) continue;
+        const double rows = (3.0 * 144 * (tz + 2) + 9.0 * n + np) / std::min(32, ck);
+        const double cost = pack ? rows : (double)ceil_div(Z, tz) * rows;
+        if (!best.persistent || cost < best_cost * (1 - 1e-9) ||
+            (cost <= best_cost * (1 + 1e-9) && p.nst > best.nst))
+          best = p, best_cost = cost;
       }
-      if (best.pack) return best;
-    }
-  }
-  for (int tz : {8, 4, 2, 1}) {
-    if (tz * (n + np) > 256) continue;
-    for (int ck : {64, 32, 16}) {
-      if (cin % ck) continue;
-      const size_t stage = tc3_stage(ck, n, tz) + (size_t)np * ck * 2;
-      if (stage > 100 * 1024 || staging + 2 * stage + 1024 > kTc3SmemMax) continue;
-      const int nst = (int)std::min<size_t>(kP3Max, (kTc3SmemMax - 1024 - staging) / stage);
-      const double cost = (double)ceil_div(Z, tz) * (3.0 * 144 * (tz + 2) + 9.0 * n + np) /
-                          std::min(32, ck);
-      if (cost < best_cost * (1 - 1e-9) || (cost <= best_cost * (1 + 1e-9) && nst > best.nst)) {
-        best_cost = cost;
-        best.ck = ck, best.tz = tz, best.nst = nst, best.stage = stage, best.staging = staging;
-        best.persistent = true;
-      }
+      if (pack && best.persistent) return best;
     }
   }
   if (best.persistent || np) return best;
@@ -2032,15 +2045,17 @@ int tc3_ln_stages(const Tc3Plan& pl, int n, int np, int sp, int nbuf) {
   return (int)std::min<size_t>(kP3Max, (kTc3SmemMax - 1024 - staging) / pl.stage);
 }
 
-// Persistent form when the plan has it; else one tile per CTA.
+// The persistent form with the layer's choice (ck, tz, pack) when per; else one tile per CTA.
 cudaError_t launch_tc3(const CUtensorMap& a, const CUtensorMap& w, int cin, int ck, int tz,
+                       bool pack, bool per,
                        const float* bias, float* out, Dims3 dout, int n, int B, long long out_bs,
                        long long bias_bs, int acc, int* err, cudaStream_t st,
                        int mode = 0, const CUtensorMap* wp = nullptr,
                        const CUtensorMap* a2 = nullptr, int np = 0, const float* bias_p = nullptr,
                        float* out_p = nullptr, long long outp_bs = 0,
                        const Bf16Ln* ln = nullptr) {
-  Tc3Plan pl = tc3_plan(cin, n, mode == 1 ? np : 0, dout.z);
+  Tc3Plan pl = per ? tc3_fixed(cin, n, mode == 1 ? np : 0, ck, tz, pack) : Tc3Plan{};
+  if (per && !pl.persistent) return cudaErrorInvalidValue;
   int nbuf = 1;  // staging slices per epilogue group
   if (ln) {  // same tiles and ring, a larger epilogue staging
     const int npm = mode == 1 ? np : 0;
@@ -2048,7 +2063,7 @@ cudaError_t launch_tc3(const CUtensorMap& a, const CUtensorMap& w, int cin, int 
     if (nst < 2 || n > 64) return cudaErrorInvalidValue;
     pl.nst = nst;
   }
-  if (pl.persistent && pl.ck == ck && pl.tz == tz) {
+  if (pl.persistent) {
     P3Args g{};
     g.bias = bias, g.out = out, g.bias_p = bias_p, g.out_p = out_p, g.err = err;
     g.dout = dout;
@@ -2225,10 +2240,10 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
   L.dgrad = (s == 1 || k == 3) && bf16_conv_supported(co, ci, k);
   if (k == 3 && s == 1) {
     const Tc3Plan pf = tc3_plan(L.kf, co, 0, L.dout.z);
-    L.ck3f = pf.ck, L.tz3f = pf.tz, L.pack3f = pf.pack;
+    L.ck3f = pf.ck, L.tz3f = pf.tz, L.pack3f = pf.pack, L.per3f = pf.persistent;
     if (L.dgrad) {
       const Tc3Plan pd = tc3_plan(L.kd, ci, 0, L.din.z);
-      L.ck3d = pd.ck, L.tz3d = pd.tz, L.pack3d = pd.pack;
+      L.ck3d = pd.ck, L.tz3d = pd.tz, L.pack3d = pd.pack, L.per3d = pd.persistent;
     }
   }
   L.wgrad = s == 1 && co <= 128 && 128 % co == 0 && ci + chunk_for(ci) <= 256;
@@ -2263,7 +2278,7 @@ int bf16_add_input_layer(Bf16Net& bf, int ci_real, int co, Dims3 din, long long 
   L.input_layer = true;
   if (bf16_conv_supported(16, co, 3)) {
     const Tc3Plan pf = tc3_plan(L.kf, co, 0, din.z);
-    L.ck3f = pf.ck, L.tz3f = pf.tz, L.pack3f = pf.pack;
+    L.ck3f = pf.ck, L.tz3f = pf.tz, L.pack3f = pf.pack, L.per3f = pf.persistent;
   }
   L.wg_tz = wg3_tz_fit(L);
   L.wgrad = L.wg3 = wg3_geom(L, 1).nst > 0;
@@ -2322,6 +2337,32 @@ cudaError_t encode_wgrad_maps(TcLayer& L, const Bf16Net& bf, int B, int blk) {
     e = encode_act(&L.wgy[blk], y, B, L.dout, L.co, chunk_for(L.co), 1, yrow);
     if (e == cudaSuccess)
       e = encode_act(&L.wgx[blk], x, B, L.din, L.ci, chunk_for(L.ci), L.s, xrow);
+  }
+  return e;
+}
+
+// The halo-box maps of one direction (0 forward, 1 data gradient) of a layer for its current
+// channel chunk and z depth (the autotuner re-encodes them per candidate).
+cudaError_t encode_halo_maps(TcLayer& L, const Bf16Net& bf, int B, int dir) {
+  const int T = L.k * L.k * L.k;
+  if (dir == 0) {
+    __nv_bfloat16* src = L.input_layer ? bf.zbf : L.xin;
+    cudaError_t e = encode_act_halo(&L.act_f3, src, B, L.din, L.kf, L.ck3f, L.tz3f);
+    if (e == cudaSuccess)
+      e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, L.kf, T, L.co, L.ck3f, 9, 3);
+    if (e == cudaSuccess && L.projf) {
+      const TcLayer& P = bf.layers[L.proj];
+      e = encode_w(&L.pw_f, bf.wbuf + P.wf_off, B, bf.wstride, P.kf, 1, P.co, L.ck3f, 1, 1);
+    }
+    return e;
+  }
+  cudaError_t e = encode_act_halo(&L.act_d3, bf.ybf, B, L.dout, L.kd, L.ck3d, L.tz3d);
+  if (e == cudaSuccess)
+    e = encode_w(&L.w_d3, bf.wbuf + L.wd_off, B, bf.wstride, L.kd, T, L.ci, L.ck3d, 9, 3);
+  if (e == cudaSuccess && L.projd) {
+    const TcLayer& P = bf.layers[L.proj];
+    e = encode_w(&L.pw_d, bf.wbuf + P.wd_off, B, bf.wstride, P.kd, 1, P.ci, L.ck3d, 1, 1);
+    if (e == cudaSuccess) e = encode_box(&L.pa_d, bf.pbf, B, L.dout, L.kd, L.ck3d, 8, 16, L.tz3d);
   }
   return e;
 }
@@ -2878,12 +2919,10 @@ int bf16_fuse_proj(Bf16Net& bf, int la, int lp) {
   A.proj = lp;
   if (A.ck3f) {
     const Tc3Plan pf = tc3_plan(A.kf, A.co, P.co, A.dout.z);
-    if (pf.persistent) A.projf = true, A.ck3f = pf.ck, A.tz3f = pf.tz, A.pack3f = pf.pack;
+    if (pf.persistent)
+      A.projf = true, A.ck3f = pf.ck, A.tz3f = pf.tz, A.pack3f = pf.pack, A.per3f = true;
   }
-  if (A.ck3d && P.dgrad) {
-    const Tc3Plan pd = tc3_plan(A.kd, A.ci, 0, A.din.z);
-    A.projd = pd.persistent && pd.ck == A.ck3d && pd.tz == A.tz3d;
-  }
+  if (A.ck3d && P.dgrad) A.projd = A.per3d;  // the dz_p stage rides the persistent dgrad
   A.projw = A.wg3 && wg3_geom(A, 1, true).nst > 0;
   return (A.projf ? 1 : 0) | (A.projd ? 2 : 0) | (A.projw ? 4 : 0);
 }
@@ -2897,7 +2936,7 @@ cudaError_t bf16_conv_fwd_proj(Bf16Net& bf, int la, const float* x, const float*
                       ? cudaSuccess
                       : stage_rows(x, L.xin, (long long)B * L.din.count(), L.ci, bf.sp, stream);
   if (e != cudaSuccess) return e;
-  return launch_tc3(L.act_f3, L.w_f3, L.kf, L.ck3f, L.tz3f, bias_a, y_a, L.dout, L.co, B,
+  return launch_tc3(L.act_f3, L.w_f3, L.kf, L.ck3f, L.tz3f, L.pack3f, L.per3f, bias_a, y_a, L.dout, L.co, B,
                     L.dout.count() * L.co, bias_bs, 0, bf.err, stream, 1, &L.pw_f, nullptr,
                     L.co, bias_p, y_p, L.dout.count() * L.co);
 }
@@ -2911,15 +2950,102 @@ cudaError_t bf16_conv_dgrad_proj(Bf16Net& bf, int la, const float* dz_a, const f
   cudaError_t e = dza_staged ? cudaSuccess : stage_rows(dz_a, bf.ybf, nv, L.co, bf.sp, stream);
   if (e == cudaSuccess && !dzp_staged) e = stage_rows(dz_p, bf.pbf, nv, L.co, bf.sp, stream);
   if (e != cudaSuccess) return e;
-  return launch_tc3(L.act_d3, L.w_d3, L.kd, L.ck3d, L.tz3d, nullptr, dx, L.din, L.ci, B,
+  return launch_tc3(L.act_d3, L.w_d3, L.kd, L.ck3d, L.tz3d, L.pack3d, L.per3d, nullptr, dx, L.din, L.ci, B,
                     L.din.count() * L.ci, 0, 0, bf.err, stream, 2, &L.pw_d, &L.pa_d);
+}
+
+namespace {
+// Autotuner cache: shape key -> (ck, tz, pack, time of the choice, time of the model's choice)
+struct TuneEntry {
+  int ck, tz, pack;
+  float us, model_us;
+};
+std::mutex g_tune_mu;
+std::map<std::array<long long, 11>, TuneEntry> g_tune;
+}  // namespace
+
+cudaError_t bf16_autotune(Bf16Net& bf, int B, float* scratch, const float* bias,
+                          cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (size_t li = 0; e == cudaSuccess && li < bf.layers.size(); ++li) {
+    TcLayer& L = bf.layers[li];
+    for (int dir = 0; dir < 2 && e == cudaSuccess; ++dir) {
+      const bool on = dir == 0 ? L.ck3f && L.per3f : L.ck3d && L.per3d;
+      if (!on) continue;
+      const int cin = dir ? L.kd : L.kf, n = dir ? L.ci : L.co;
+      const int np = dir == 0 && L.projf ? bf.layers[L.proj].co : 0;
+      const int mode = dir == 0 ? (L.projf ? 1 : 0) : (L.projd ? 2 : 0);
+      const Dims3 d = dir ? L.din : L.dout;
+      int &ck = dir ? L.ck3d : L.ck3f, &tz = dir ? L.tz3d : L.tz3f;
+      bool& pack = dir ? L.pack3d : L.pack3f;
+      float &tune = dir ? L.tune_d : L.tune_f, &model = dir ? L.model_d : L.model_f;
+      const std::array<long long, 11> key{dev, dir, cin, n, np, mode, d.z, d.y, d.x, B, bf.sp};
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+          ck = it->second.ck, tz = it->second.tz, pack = it->second.pack != 0;
+          tune = it->second.us, model = it->second.model_us;
+          continue;
+        }
+      }
+      const int mck = ck, mtz = tz;
+      const bool mpack = pack;
+      float best = 1e30f, model_us = -1.f;
+      int bck = ck, btz = tz;
+      bool bpack = pack;
+      auto launch = [&](const Tc3Plan& c) {
+        if (dir == 0)
+          return launch_tc3(L.act_f3, L.w_f3, cin, c.ck, c.tz, c.pack, true, bias, scratch, d, n,
+                            B, d.count() * n, 0, 0, bf.err, st, mode,
+                            mode == 1 ? &L.pw_f : nullptr, nullptr, np, bias, scratch,
+                            d.count() * np);
+        return launch_tc3(L.act_d3, L.w_d3, cin, c.ck, c.tz, c.pack, true, nullptr, scratch, d,
+                          n, B, d.count() * n, 0, 0, bf.err, st, mode,
+                          mode == 2 ? &L.pw_d : nullptr, mode == 2 ? &L.pa_d : nullptr);
+      };
+      for (const Tc3Plan& c : tc3_candidates(cin, n, np)) {
+        ck = c.ck, tz = c.tz, pack = c.pack;
+        e = encode_halo_maps(L, bf, B, dir);
+        for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = launch(c);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = launch(c);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) break;
+        const float us = 1e3f * ms / 5.f;
+        if (c.ck == mck && c.tz == mtz && c.pack == mpack) model_us = us;
+        if (us < best) best = us, bck = c.ck, btz = c.tz, bpack = c.pack;
+      }
+      if (e != cudaSuccess) break;
+      ck = bck, tz = btz, pack = bpack, tune = best, model = model_us;
+      e = encode_halo_maps(L, bf, B, dir);
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune[key] = TuneEntry{bck, btz, bpack ? 1 : 0, best, model_us};
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return e;
+}
+
+long long bf16_tune_scratch_floats(const Bf16Net& bf, int B) {
+  long long m = 0;
+  for (const TcLayer& L : bf.layers)
+    m = std::max(m, std::max(L.dout.count() * L.co, L.din.count() * L.ci));
+  return m * B;
 }
 
 bool bf16_fwd_ln_ok(const Bf16Net& bf, int layer, int np, int sp) {
   const TcLayer& L = bf.layers[layer];
-  if (!L.ck3f || L.co > 64 || (np > 0 && !L.projf)) return false;
-  const Tc3Plan pl = tc3_plan(L.kf, L.co, np, L.dout.z);
-  if (!pl.persistent || pl.ck != L.ck3f || pl.tz != L.tz3f) return false;
+  if (!L.ck3f || !L.per3f || L.co > 64 || (np > 0 && !L.projf)) return false;
+  const Tc3Plan pl = tc3_fixed(L.kf, L.co, np, L.ck3f, L.tz3f, L.pack3f);
   return tc3_ln_stages(pl, L.co, np, sp, 1) >= 2;
 }
 
@@ -2936,7 +3062,7 @@ cudaError_t bf16_conv_fwd_ln(Bf16Net& bf, int layer, const float* x, const float
   Bf16Ln l = ln;
   l.sp = bf.sp;
   const long long obs = L.dout.count() * L.co;
-  return launch_tc3(L.act_f3, L.w_f3, L.kf, L.ck3f, L.tz3f, bias, y, L.dout, L.co, B, obs,
+  return launch_tc3(L.act_f3, L.w_f3, L.kf, L.ck3f, L.tz3f, L.pack3f, L.per3f, bias, y, L.dout, L.co, B, obs,
                     bias_bs, 0, bf.err, stream, proj ? 1 : 0, proj ? &L.pw_f : nullptr, nullptr,
                     proj ? L.co : 0, bias_p, y_p, proj ? obs : 0, &l);
 }
@@ -2963,7 +3089,7 @@ cudaError_t bf16_conv_fwd(Bf16Net& bf, int layer, const float* x, const float* b
                       : stage_rows(x, L.xin, (long long)B * L.din.count(), L.ci, bf.sp, stream);
   if (e != cudaSuccess) return e;
   if (L.ck3f)
-    return launch_tc3(L.act_f3, L.w_f3, L.kf, L.ck3f, L.tz3f, bias, y, L.dout, L.co, B,
+    return launch_tc3(L.act_f3, L.w_f3, L.kf, L.ck3f, L.tz3f, L.pack3f, L.per3f, bias, y, L.dout, L.co, B,
                       L.dout.count() * L.co, bias_bs, 0, bf.err, stream);
   const TapPlan plan = conv_plan(L.k, L.s);
   return launch_tc(L.act_f, L.w_f, plan, 1, L.kf, bias, y, L.dout, L.dout, L.co, B,
@@ -2984,7 +3110,7 @@ cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, 
                      L.din.count() * L.ci, 0, accumulate, bf.err, stream);
   }
   if (L.ck3d)
-    return launch_tc3(L.act_d3, L.w_d3, L.kd, L.ck3d, L.tz3d, nullptr, dx, L.din, L.ci, B,
+    return launch_tc3(L.act_d3, L.w_d3, L.kd, L.ck3d, L.tz3d, L.pack3d, L.per3d, nullptr, dx, L.din, L.ci, B,
                       L.din.count() * L.ci, 0, accumulate, bf.err, stream);
   return launch_tc(L.act_d, L.w_d, conv_plan(L.k, 1), 1, L.kd, nullptr, dx, L.din, L.din, L.ci,
                    B, L.din.count() * L.ci, 0, accumulate, bf.err, stream);

@@ -33,6 +33,9 @@ struct TcLayer {
   bool wgrad = false;             // weight gradient on the tensor cores too (3x3x3)
   int ck3f = 0, ck3d = 0;         // channel chunk of the halo-box kernel (0: per-tap kernel)
   int tz3f = 1, tz3d = 1;         // z slices per halo-box tile
+  bool per3f = false, per3d = false;    // halo forward / data gradient by the persistent kernel
+  float tune_f = -1.f, tune_d = -1.f;   // autotuner: time of the chosen tiles (us), or -1
+  float model_f = -1.f, model_d = -1.f; // ... of the cost model's tiles
   bool pack3f = false, pack3d = false;  // halo forward / data gradient with the kz taps packed
                                         // into N: that direction's weights are stored with ky
                                         // and kz swapped (tap (kz, ky, kx) at (ky, kz, kx))
@@ -96,6 +99,17 @@ cudaError_t bf16_conv_dgrad_proj(Bf16Net& bf, int la, const float* dz_a, const f
 void bf16_layout(Bf16Net& bf, char* base, size_t& used, int B, long long max_act);
 // Encode the TMA descriptors once the buffers have addresses.
 cudaError_t bf16_finalize(Bf16Net& bf, int B);
+// Autotuner of the persistent halo convolutions: for every layer and direction that runs the
+// persistent kernel, each candidate tiling (kz packing, z depth, channel chunk) is timed with
+// CUDA events on the network's own buffers (2 warm-up + 5 timed launches, outputs to
+// scratch, bias_f any B-shared FP32 bias) and the fastest kept, with its time and the cost
+// model's choice's time in the layer.  Choices are cached per shape for the process, so every
+// context of one shape uses the same tiles (and FP32 summation order).  Synchronous on st;
+// call after bf16_finalize, before any capture.
+cudaError_t bf16_autotune(Bf16Net& bf, int B, float* scratch, const float* bias_f,
+                          cudaStream_t st);
+// FP32 elements bf16_autotune's scratch needs.
+long long bf16_tune_scratch_floats(const Bf16Net& bf, int B);
 cudaError_t bf16_prepare_kernels();
 // theta (FP32, [B][Pp]) -> BF16 forward and data-gradient weights of every layer.
 cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long long Pp,

@@ -78,6 +78,7 @@ struct d2ip_ctx {
   bool j_ready = false, input_ready = false;
   double lr = 1e-3, beta1 = 0.9, beta2 = 0.999, eps = 1e-8;
   bool frame_reset = true;  // fresh Adam state at every fitted frame (else carried)
+  bool autotune = true;     // time the tensor-core tilings when the arena is built
   // 4D-TV regulariser (off when lam_tv == 0)
   double lam_tv = 0.0, lam_s = 1.0, lam_t = 0.1, tv_eps = 1e-8;
 
@@ -408,7 +409,23 @@ d2ip_status ensure_arena(d2ip_ctx* c) {
   Carve real{static_cast<char*>(p), 0, false};
   layout_buffers(c, real);
   CK(cudaMemsetAsync(p, 0, dry.used, c->stream));
-  if (c->precision != D2IP_FP32) CK(bf16_finalize(c->bf, c->B));
+  if (c->precision != D2IP_FP32) {
+    CK(bf16_finalize(c->bf, c->B));
+    if (c->autotune) {  // on the arena's own (zeroed) buffers, outputs to a scratch buffer
+      float* scratch = nullptr;
+      const size_t bytes = sizeof(float) * (size_t)bf16_tune_scratch_floats(c->bf, c->B);
+      if (cudaMalloc(&scratch, bytes) != cudaSuccess)
+        return fail(c, D2IP_ERR_OOM, "device allocation of the autotuner scratch failed");
+      cudaError_t e = bf16_autotune(c->bf, c->B, scratch, c->theta, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      cudaFree(scratch);
+      if (e != cudaSuccess) return cuda_fail(c, e, "autotuning the tensor-core tilings");
+      CK(bf16_finalize(c->bf, c->B));
+      int tc = 0;
+      CK(cudaMemcpy(&tc, c->bf.err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (tc) return fail(c, D2IP_ERR_TIMEOUT, "a tensor-core kernel timed out while autotuning");
+    }
+  }
   return D2IP_OK;
 }
 
@@ -1280,6 +1297,33 @@ d2ip_status d2ip_set_regularizer(d2ip_ctx* c, double lambda_tv, double lambda_s,
   c->lam_s = lambda_s;
   c->lam_t = lambda_t;
   c->tv_eps = eps;
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_set_autotune(d2ip_ctx* c, int on) {
+  if (!c) return fail(nullptr, D2IP_ERR_BAD_ARG, "null context");
+  c->autotune = on != 0;
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_tile_plan(d2ip_ctx* c, long long* rows, int cap, int* n_rows, double* us) {
+  if (!c || !n_rows) return fail(c, D2IP_ERR_BAD_ARG, "null argument");
+  if (!c->arena) return fail(c, D2IP_ERR_STATE, "network workspace not built yet");
+  const auto& ls = c->bf.layers;
+  const int n = c->precision == D2IP_FP32 ? 0 : (int)ls.size();
+  *n_rows = n;
+  for (int i = 0; i < n && i < cap; ++i) {
+    const TcLayer& L = ls[i];
+    const long long r[15] = {L.ci_real, L.co, L.k, L.s, L.dout.z, L.dout.y, L.dout.x,
+                             L.per3f, L.pack3f, L.ck3f, L.tz3f,
+                             L.per3d, L.pack3d, L.ck3d, L.tz3d};
+    if (rows)
+      for (int j = 0; j < 15; ++j) rows[15LL * i + j] = r[j];
+    if (us) {
+      us[4LL * i] = L.tune_f, us[4LL * i + 1] = L.model_f;
+      us[4LL * i + 2] = L.tune_d, us[4LL * i + 3] = L.model_d;
+    }
+  }
   return D2IP_OK;
 }
 

@@ -1,0 +1,68 @@
+"""The autotuner of the tensor-core tilings: every persistent halo convolution's chosen tiling
+is no slower than the cost model's (both timed in the same sweep), contexts of one shape share
+the cached choice, and the tuned network meets the same parity bars against the oracle as
+the cost model's tilings.  Only the FP32 summation order differs between two tilings, but an
+intermediate staged as BF16 for the next convolution can land on the other side of a rounding
+boundary: with plain BF16 (relative step 2^-8) the two networks' dsigma then differ by about
+3e-3, so they are held to 1e-2 there, and to 1e-5 with the split precision (2^-16)."""
+import numpy as np
+import pytest
+
+from oracle import dip
+from tests import problems
+from tests.problems import rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(d2ip, pb, precision, autotune):
+    s = pb.spec
+    c = d2ip.Context(s.grid, s.levels, s.widths, s.c_in, precision, 2, autotune=autotune)
+    c.load_J(pb.J)
+    c.set_input(np.ascontiguousarray(np.tile(pb.Zin[None], (2, 1, 1))),
+                np.ascontiguousarray(np.tile(pb.theta0[None], (2, 1))))
+    c.set_optim(5e-4)
+    return c
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_autotuned_tilings(d2ip, precision):
+    pb = problems.make((32, 32, 16), 2, 3, (16, 32, 64), seed=5)
+    tuned = _ctx(d2ip, pb, precision, True)
+    rows, us = tuned.tile_plan()
+    assert rows.shape[0] > 0
+    timed = 0
+    for r, t in zip(rows, us):
+        for per, pack, ck, tz, t_tuned, t_model in ((r[7], r[8], r[9], r[10], t[0], t[1]),
+                                                     (r[11], r[12], r[13], r[14], t[2], t[3])):
+            if not per:
+                continue
+            timed += 1
+            assert ck in (16, 32, 64) and tz in (1, 2, 4, 8)
+            assert pack in (0, 1) and (not pack or tz >= 2)
+            assert 0 < t_tuned <= t_model, (r, t)
+    assert timed > 0
+    print("tilings (ci, co, k, s, z, y, x, fwd per/pack/ck/tz, dgrad per/pack/ck/tz):")
+    for r, t in zip(rows, us):
+        print(list(r), [round(v, 1) for v in t])
+    # a second context of the shape takes the cached choice
+    again = _ctx(d2ip, pb, precision, True)
+    rows2, us2 = again.tile_plan()
+    np.testing.assert_array_equal(rows2, rows)
+    np.testing.assert_array_equal(us2, us)
+    # same parity against the oracle with the tuned and the cost model's tilings
+    model = _ctx(d2ip, pb, precision, False)
+    ref = dip.dip_step(pb.spec, pb.Jn64, pb.Zin.astype(np.float64), pb.V[0].astype(np.float64),
+                       pb.theta0.astype(np.float64), dip.AdamState.fresh(pb.theta0.size), 5e-4)
+    bar_ds, bar_g = (2e-2, 5e-2) if precision == 1 else (1e-4, 2e-3)
+    V = np.ascontiguousarray(np.tile(pb.V[:1], (2, 1)))
+    out = []
+    for c in (tuned, model):
+        ds = c.forward()
+        c.run_steps(V, 1)
+        g = c.grad()
+        assert rel(ds[0], ref.dsigma) < bar_ds and rel(g[0], ref.grad) < bar_g
+        out.append((ds[0], g[0]))
+    d = rel(out[0][0], out[1][0])
+    print(f"tuned against cost-model tilings: dsigma rel {d:.2e}")
+    assert d < (1e-2 if precision == 1 else 1e-5)
