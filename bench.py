@@ -526,10 +526,6 @@ def _source_digest(files=None):
 # per (workload, network, precision): the ncu traffic summary and the sources that hold the
 # roofline class's kernels and their launch sequence (a change there voids the figure)
 TRAFFIC_FILES = {
-    ("batch64", "resunet", "bf16"): (
-        "roofline_traffic_batch64_bf16.txt",
-        ("common.cuh", "conv_bf16.cu", "conv_bf16.cuh", "conv_f32.cu", "pointwise.cu",
-         "runtime.cu")),
     ("seq32", "fastres", "fp32"): (
         "roofline_traffic_seq32_fastres_fp32.txt",
         ("common.cuh", "conv_f32.cu", "fastres.cu", "fastres.cuh", "fastres_ops.cu")),
@@ -621,8 +617,12 @@ def run_probe(args):
     groups = synth.batch_workload(64, w.frames, seed=1, c_in=w.c_in)
     g = max(groups, key=lambda q: q.J.shape[1] * len(q.problems))
     nprob = min(args.probe_problems or len(g.problems), len(g.problems))
+    plan = None
+    if args.tile_plan_in:  # tilings saved by an earlier run (no timing sweep in this one)
+        with open(args.tile_plan_in) as f:
+            plan = json.load(f)["rows"]
     c = B.Context(g.grid, w.levels, w.widths, w.c_in, _prec_code(B, args.precision or "bf16"),
-                  nprob)
+                  nprob, tile_plan=plan)
     table = c.table()
     th = np.stack([synth.kaiming_theta([tuple(r) for r in table], 1, stream_offset=p * c.P)
                    for p in g.problems[:nprob]])
@@ -634,6 +634,10 @@ def run_probe(args):
     torch.cuda.synchronize()
     prof = c.profile(v0, args.probe)
     nk_step, nk_eval = c.graph_kernels()
+    if args.tile_plan_out:
+        rows, us = c.tile_plan()
+        with open(args.tile_plan_out, "w") as f:
+            json.dump({"rows": rows.tolist(), "us": us.tolist()}, f)
     print(json.dumps({"probe": f"grid {list(g.grid)}, m {g.J.shape[0]}, {nprob} problems, "
                                f"{(args.precision or 'bf16').upper()}",
                       "iters": args.probe, "step_graph_kernels": nk_step,
@@ -678,6 +682,11 @@ def main():
     ap.add_argument("--probe", type=int, default=0,
                     help="trace this many iterations of the largest batched group and exit")
     ap.add_argument("--probe-problems", type=int, default=0)
+    ap.add_argument("--tile-plan-out", default="",
+                    help="probe: write the tilings in use (JSON) to this file")
+    ap.add_argument("--tile-plan-in", default="",
+                    help="probe: apply the tilings of this file instead of timing them "
+                         "(repeatable runs, e.g. under a profiler)")
     ap.add_argument("--study", type=int, default=0,
                     help="run the convergence ablation for this many iterations and exit")
     ap.add_argument("--study-out", default=None)

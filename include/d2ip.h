@@ -229,6 +229,14 @@ d2ip_status d2ip_set_autotune(d2ip_ctx* ctx, int on);
  * data gradient's (-1 where not timed).  *n_rows receives the number of layers (0 in FP32).
  * D2IP_ERR_STATE before the workspace exists. */
 d2ip_status d2ip_tile_plan(d2ip_ctx* ctx, long long* rows, int cap, int* n_rows, double* us);
+/* Restores tilings saved from d2ip_tile_plan (e.g. by an earlier process on this GPU), so a
+ * context of the same network, grid and batch skips the timing sweep: rows (host, n_rows x 15,
+ * copied) are applied when the workspace is next built, in place of the autotuner.  Call
+ * after d2ip_set_network and before the workspace exists (D2IP_ERR_STATE afterwards).  When
+ * the workspace is built, a row whose shape columns or persistent flags do not match the
+ * layer, or whose tiling cannot run, fails that call with D2IP_ERR_BAD_ARG.  n_rows = 0
+ * clears a stored plan.  BF16 precisions only (rows are ignored in FP32). */
+d2ip_status d2ip_set_tile_plan(d2ip_ctx* ctx, const long long* rows, int n_rows);
 
 /* Kernel classes reported by d2ip_profile_iterations, in this order. */
 #define D2IP_KCLASS_CONV_FWD 0   /* work: FLOPs (2 * out voxels * K^3 * ci * co)        */

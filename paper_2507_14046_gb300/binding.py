@@ -54,6 +54,7 @@ _SIGS = {
     "d2ip_set_frame_reset": [_vp, _i],
     "d2ip_set_autotune": [_vp, _i],
     "d2ip_tile_plan": [_vp, _vp, _i, C.POINTER(_i), _vp],
+    "d2ip_set_tile_plan": [_vp, _vp, _i],
     "d2ip_set_regularizer": [_vp, _d, _d, _d, _d],
     "d2ip_run_steps": [_vp, _vp, _i, _vp],
     "d2ip_forward": [_vp, _vp],
@@ -233,6 +234,12 @@ def d2ip_tile_plan(ctx):
     return rows, us
 
 
+def d2ip_set_tile_plan(ctx, rows):
+    """Tilings saved from d2ip_tile_plan, applied when the workspace is built (see d2ip.h)."""
+    r = np.ascontiguousarray(np.asarray(rows, dtype=np.int64).reshape(-1, 15))
+    _call("d2ip_set_tile_plan", ctx, ctx, r.ctypes.data if r.size else None, r.shape[0])
+
+
 def d2ip_conv3d_wgrad_workspace(*args) -> int:
     return int(_lib.d2ip_conv3d_wgrad_workspace(*args))
 
@@ -297,9 +304,10 @@ class Context:
     calls of the same name without the ``d2ip_`` prefix."""
 
     def __init__(self, grid, levels, widths, c_in=8, precision=D2IP_FP32, batch=1, device=0,
-                 stream=None, net="resunet", autotune=True):
+                 stream=None, net="resunet", autotune=True, tile_plan=None):
         """net: "resunet" (d2ip_set_network) or "fastres" (d2ip_set_network_fastres);
-        autotune: time the tensor-core tilings when the workspace is built."""
+        autotune: time the tensor-core tilings when the workspace is built; tile_plan: rows
+        saved from tile_plan() of a context of the same shape, applied instead of timing."""
         self.handle = d2ip_create(device, stream)
         if not autotune:
             d2ip_set_autotune(self.handle, 0)
@@ -312,6 +320,8 @@ class Context:
             d2ip_set_network(self.handle, levels, list(widths), c_in, precision, batch)
         else:
             raise ValueError(f"unknown network {net!r}")
+        if tile_plan is not None:
+            d2ip_set_tile_plan(self.handle, tile_plan)
         self.P = d2ip_param_count(self.handle)
         self.n = X * Y * Z
         self.m = 0
@@ -341,6 +351,9 @@ class Context:
 
     def tile_plan(self):
         return d2ip_tile_plan(self.handle)
+
+    def set_tile_plan(self, rows):
+        d2ip_set_tile_plan(self.handle, rows)
 
     def set_frame_reset(self, reset_moments_per_frame: bool):
         d2ip_set_frame_reset(self.handle, 1 if reset_moments_per_frame else 0)

@@ -3035,6 +3035,43 @@ cudaError_t bf16_autotune(Bf16Net& bf, int B, float* scratch, const float* bias,
   return e;
 }
 
+cudaError_t bf16_apply_plan(Bf16Net& bf, int B, const long long* rows, int n_rows) {
+  if (n_rows != (int)bf.layers.size()) return cudaErrorInvalidValue;
+  for (int i = 0; i < n_rows; ++i) {  // every row must describe layer i as planned here
+    const TcLayer& L = bf.layers[i];
+    const long long* r = rows + 15LL * i;
+    const long long shape[7] = {L.ci_real, L.co, L.k, L.s, L.dout.z, L.dout.y, L.dout.x};
+    for (int j = 0; j < 7; ++j)
+      if (r[j] != shape[j]) return cudaErrorInvalidValue;
+    for (int dir = 0; dir < 2; ++dir) {
+      const bool on = dir == 0 ? L.ck3f && L.per3f : L.ck3d && L.per3d;
+      const long long* t = r + 7 + 4 * dir;  // persistent, packed, chunk, z depth
+      if ((t[0] != 0) != on) return cudaErrorInvalidValue;
+      if (!on) continue;
+      const int np = dir == 0 && L.projf ? bf.layers[L.proj].co : 0;
+      const Tc3Plan p = tc3_fixed(dir ? L.kd : L.kf, dir ? L.ci : L.co, np, (int)t[2], (int)t[3],
+                                  t[1] != 0);
+      if (!p.persistent) return cudaErrorInvalidValue;
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < n_rows && e == cudaSuccess; ++i) {
+    TcLayer& L = bf.layers[i];
+    const long long* r = rows + 15LL * i;
+    for (int dir = 0; dir < 2 && e == cudaSuccess; ++dir) {
+      if (!r[7 + 4 * dir]) continue;
+      const long long* t = r + 7 + 4 * dir;
+      (dir ? L.pack3d : L.pack3f) = t[1] != 0;
+      (dir ? L.ck3d : L.ck3f) = (int)t[2];
+      (dir ? L.tz3d : L.tz3f) = (int)t[3];
+      (dir ? L.tune_d : L.tune_f) = -1.f;
+      (dir ? L.model_d : L.model_f) = -1.f;
+      e = encode_halo_maps(L, bf, B, dir);
+    }
+  }
+  return e;
+}
+
 long long bf16_tune_scratch_floats(const Bf16Net& bf, int B) {
   long long m = 0;
   for (const TcLayer& L : bf.layers)

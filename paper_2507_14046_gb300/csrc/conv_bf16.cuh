@@ -108,6 +108,10 @@ cudaError_t bf16_finalize(Bf16Net& bf, int B);
 // call after bf16_finalize, before any capture.
 cudaError_t bf16_autotune(Bf16Net& bf, int B, float* scratch, const float* bias_f,
                           cudaStream_t st);
+// Sets the persistent halo tilings from rows laid out as d2ip_tile_plan writes them (one
+// per layer; the shape columns must match the layer), re-encoding the affected descriptors.
+// cudaErrorInvalidValue when a row does not fit the network or names a tiling that cannot run.
+cudaError_t bf16_apply_plan(Bf16Net& bf, int B, const long long* rows, int n_rows);
 // FP32 elements bf16_autotune's scratch needs.
 long long bf16_tune_scratch_floats(const Bf16Net& bf, int B);
 cudaError_t bf16_prepare_kernels();

@@ -79,6 +79,7 @@ struct d2ip_ctx {
   double lr = 1e-3, beta1 = 0.9, beta2 = 0.999, eps = 1e-8;
   bool frame_reset = true;  // fresh Adam state at every fitted frame (else carried)
   bool autotune = true;     // time the tensor-core tilings when the arena is built
+  std::vector<long long> tile_rows;  // tilings to apply instead (d2ip_set_tile_plan)
   // 4D-TV regulariser (off when lam_tv == 0)
   double lam_tv = 0.0, lam_s = 1.0, lam_t = 0.1, tv_eps = 1e-8;
 
@@ -411,7 +412,14 @@ d2ip_status ensure_arena(d2ip_ctx* c) {
   CK(cudaMemsetAsync(p, 0, dry.used, c->stream));
   if (c->precision != D2IP_FP32) {
     CK(bf16_finalize(c->bf, c->B));
-    if (c->autotune) {  // on the arena's own (zeroed) buffers, outputs to a scratch buffer
+    if (!c->tile_rows.empty()) {  // a saved plan replaces the sweep
+      const cudaError_t e = bf16_apply_plan(c->bf, c->B, c->tile_rows.data(),
+                                            (int)(c->tile_rows.size() / 15));
+      if (e == cudaErrorInvalidValue)
+        return fail(c, D2IP_ERR_BAD_ARG, "the stored tile plan does not fit this network");
+      if (e != cudaSuccess) return cuda_fail(c, e, "applying the stored tile plan");
+      CK(bf16_finalize(c->bf, c->B));
+    } else if (c->autotune) {  // on the arena's own (zeroed) buffers, outputs to a scratch buffer
       float* scratch = nullptr;
       const size_t bytes = sizeof(float) * (size_t)bf16_tune_scratch_floats(c->bf, c->B);
       if (cudaMalloc(&scratch, bytes) != cudaSuccess)
@@ -1324,6 +1332,13 @@ d2ip_status d2ip_tile_plan(d2ip_ctx* c, long long* rows, int cap, int* n_rows, d
       us[4LL * i + 2] = L.tune_d, us[4LL * i + 3] = L.model_d;
     }
   }
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_set_tile_plan(d2ip_ctx* c, const long long* rows, int n_rows) {
+  if (!c || n_rows < 0 || (n_rows > 0 && !rows)) return fail(c, D2IP_ERR_BAD_ARG, "bad argument");
+  if (c->arena) return fail(c, D2IP_ERR_STATE, "the workspace already exists");
+  c->tile_rows.assign(rows, rows + 15LL * n_rows);
   return D2IP_OK;
 }
 

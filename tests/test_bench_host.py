@@ -54,19 +54,20 @@ def test_roofline_picks_the_dominant_class_and_divides_work_by_time(bench):
 
 def test_traffic_only_for_a_matching_capture(bench, monkeypatch):
     import json
-    name, sources = bench.TRAFFIC_FILES[("batch64", "resunet", "bf16")]
+    key = ("seq32", "fastres", "fp32")
+    name, sources = bench.TRAFFIC_FILES[key]
     with open(os.path.join(ROOT, "profiles", name)) as fh:
         stored = json.load(fh)
+    cls = next(iter(stored["bytes_per_launch"]))
     # no capture for this workload at all
-    assert bench._traffic("conv_wgrad", Args("seq32", "resunet", "fp32")) is None
+    assert bench._traffic(cls, Args("seq32", "resunet", "fp32")) is None
     # the sources match the capture: its figure; a class without a figure: None
     monkeypatch.setattr(bench, "_source_digest", lambda files=None: stored["source_sha1"])
-    assert bench._traffic("conv_wgrad", Args()) == pytest.approx(
-        stored["bytes_per_launch"]["conv_wgrad"])
-    assert bench._traffic("ln_fwd", Args()) is None
+    assert bench._traffic(cls, Args(*key)) == pytest.approx(stored["bytes_per_launch"][cls])
+    assert bench._traffic("ln_fwd", Args(*key)) is None
     # a kernel source changed since the capture: no figure
     monkeypatch.setattr(bench, "_source_digest", lambda files=None: "0" * 40)
-    assert bench._traffic("conv_wgrad", Args()) is None
+    assert bench._traffic(cls, Args(*key)) is None
 
 
 def test_source_digest_depends_on_the_named_files(bench):

@@ -15,9 +15,10 @@ from tests.problems import rel
 pytestmark = pytest.mark.gpu
 
 
-def _ctx(d2ip, pb, precision, autotune):
+def _ctx(d2ip, pb, precision, autotune, tile_plan=None):
     s = pb.spec
-    c = d2ip.Context(s.grid, s.levels, s.widths, s.c_in, precision, 2, autotune=autotune)
+    c = d2ip.Context(s.grid, s.levels, s.widths, s.c_in, precision, 2, autotune=autotune,
+                     tile_plan=tile_plan)
     c.load_J(pb.J)
     c.set_input(np.ascontiguousarray(np.tile(pb.Zin[None], (2, 1, 1))),
                 np.ascontiguousarray(np.tile(pb.theta0[None], (2, 1))))
@@ -63,6 +64,19 @@ def test_autotuned_tilings(d2ip, precision):
         g = c.grad()
         assert rel(ds[0], ref.dsigma) < bar_ds and rel(g[0], ref.grad) < bar_g
         out.append((ds[0], g[0]))
+    # a saved plan restored into a new context: no sweep, same tiles, the same numbers
+    restored = _ctx(d2ip, pb, precision, True, tile_plan=rows)
+    rows3, us3 = restored.tile_plan()
+    np.testing.assert_array_equal(rows3, rows)
+    assert np.all(us3 == -1.0)
+    ds3 = restored.forward()
+    restored.run_steps(V, 1)
+    np.testing.assert_array_equal(ds3[0], out[0][0])
+    np.testing.assert_array_equal(restored.grad()[0], out[0][1])
+    bad = rows.copy()
+    bad[0, 4] += 1  # a grid the network does not have
+    with pytest.raises(RuntimeError):
+        _ctx(d2ip, pb, precision, True, tile_plan=bad)
     d = rel(out[0][0], out[1][0])
     print(f"tuned against cost-model tilings: dsigma rel {d:.2e}")
     assert d < (1e-2 if precision == 1 else 1e-5)
