@@ -229,6 +229,16 @@ d2ip_status d2ip_set_autotune(d2ip_ctx* ctx, int on);
  * data gradient's (-1 where not timed).  *n_rows receives the number of layers (0 in FP32).
  * D2IP_ERR_STATE before the workspace exists. */
 d2ip_status d2ip_tile_plan(d2ip_ctx* ctx, long long* rows, int cap, int* n_rows, double* us);
+/* LayerNorm (+ LeakyReLU) backward in the epilogue of the data gradient that produces its
+ * input gradient (BF16 precisions; off by default): conv b's data gradient then also runs
+ * LayerNorm a's backward, and conv a's (adding the residual gradient already in dx) the
+ * backward of the unit before the block, writing the BF16 dy staging of the next layer and
+ * per-tile (dgamma, dbeta) partial sums instead of the FP32 gradients in between.  Applies
+ * where that data gradient runs the persistent halo kernel with room for the epilogue.
+ * Measured on the batched 48x48x24 group it moves about as much time into the data
+ * gradients as it removes from the standalone LayerNorm backward (whose loads run near
+ * HBM speed), hence opt-in.  Takes effect at the next graph capture. */
+d2ip_status d2ip_set_ln_backward_fusion(d2ip_ctx* ctx, int on);
 /* Restores tilings saved from d2ip_tile_plan (e.g. by an earlier process on this GPU), so a
  * context of the same network, grid and batch skips the timing sweep: rows (host, n_rows x 15,
  * copied) are applied when the workspace is next built, in place of the autotuner.  Call

@@ -55,6 +55,7 @@ _SIGS = {
     "d2ip_set_autotune": [_vp, _i],
     "d2ip_tile_plan": [_vp, _vp, _i, C.POINTER(_i), _vp],
     "d2ip_set_tile_plan": [_vp, _vp, _i],
+    "d2ip_set_ln_backward_fusion": [_vp, _i],
     "d2ip_set_regularizer": [_vp, _d, _d, _d, _d],
     "d2ip_run_steps": [_vp, _vp, _i, _vp],
     "d2ip_forward": [_vp, _vp],
@@ -266,7 +267,7 @@ def d2ip_layernorm_workspace(*args) -> int:
 
 for _name in ("d2ip_set_grid", "d2ip_load_J", "d2ip_get_colnorms", "d2ip_set_input",
               "d2ip_set_optim", "d2ip_set_regularizer", "d2ip_reset_optimizer",
-              "d2ip_set_frame_reset", "d2ip_set_autotune",
+              "d2ip_set_frame_reset", "d2ip_set_autotune", "d2ip_set_ln_backward_fusion",
               "d2ip_run_steps", "d2ip_forward",
               "d2ip_get_grad", "d2ip_fit_frame", "d2ip_fit_sequence", "d2ip_set_state",
               "d2ip_err_ratio", "d2ip_sync", "d2ip_profile_iterations", "d2ip_graph_kernels"):
@@ -354,6 +355,9 @@ class Context:
 
     def set_tile_plan(self, rows):
         d2ip_set_tile_plan(self.handle, rows)
+
+    def set_ln_backward_fusion(self, on: bool):
+        d2ip_set_ln_backward_fusion(self.handle, 1 if on else 0)
 
     def set_frame_reset(self, reset_moments_per_frame: bool):
         d2ip_set_frame_reset(self.handle, 1 if reset_moments_per_frame else 0)

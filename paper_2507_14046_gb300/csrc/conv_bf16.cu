@@ -582,17 +582,29 @@ struct P3Args {
                          // them after the ring, then the groups' bias, gamma and beta copies
   int nbuf;
   long long out_bs, bias_bs, outp_bs, biasp_bs;
-  // LayerNorm epilogue (ln, output part 0): y = act(gamma * xhat + beta (+ resid)) with
+  // LayerNorm epilogue (ln = 1, output part 0): y = act(gamma * xhat + beta (+ resid)) with
   // xhat = (z - mean) * rstd over the N channels of each voxel (z = the convolution + bias);
   // y through tm_out, xhat through tm_xh, rstd[b][voxel] directly and, with ybf, a BF16 copy
   // of y in sp channel blocks (stage_bf16x4's layout) through tm_ybf.  z is not stored.
+  // LayerNorm backward epilogue (ln = 2, mode 0): the data gradient D (+ resid, a gradient
+  // already accumulated for the same tensor) is the gradient of a = act(LN(z) ...), the
+  // output of the block before; with dp = D act'(a) (the mask from a >= 0 as stored),
+  // dz = rstd (gamma dp - mean(gamma dp) - xhat mean(gamma dp xhat)) over the N channels
+  // goes to the BF16 staging through tm_ybf (and, when out is set, as FP32 through tm_out);
+  // the sums of dp xhat and dp (the dgamma, dbeta terms) over the voxels of the slices an
+  // epilogue group takes from a tile go to row tile * kEpiGroups + group of part[b] (2 N
+  // floats; rows_b rows per problem).
   int ln, act, ybf, sp;
   const float* gamma;  // gamma[c], then beta[c] at gamma + N, per problem at gamma_bs
   long long gamma_bs;
   const float* resid;  // [b][voxel][N] at resid_bs, or null
   long long resid_bs;
-  float* rstd;         // [b][voxel] at rstd_bs
+  float* rstd;         // [b][voxel] at rstd_bs (an input of the backward)
   long long rstd_bs;
+  const float* aout;   // backward: a [b][voxel][N] at resid_bs
+  const float* xh_in;  // backward: xhat [b][voxel][N] at resid_bs
+  float* part;         // backward: [b][rows_b][2 N]
+  long long rows_b;
 };
 
 // 16-byte chunk index inside a staged row of R bytes (R = 32, 64 or 128) under the TMA
@@ -600,6 +612,35 @@ struct P3Args {
 // 4-pair (R 64) or 2-quad (R 32) atom.
 __device__ __forceinline__ int swz_chunk(int chunk, int m, int R) {
   return chunk ^ ((m * R >> 7) & (R / 16 - 1));
+}
+
+// Channels c0..c0+15 of tile row m, values o, into the epilogue's BF16 staging slice: sp
+// blocks (hi; or hi, lo, hi) of 128 rows x nc channels, each the swizzled rows of one
+// output box (2 nc bytes per row).
+__device__ __forceinline__ void stage_slice_bf16(__nv_bfloat16* YB, int m, int nc, int c0,
+                                                 const float (&o)[16], int sp) {
+#pragma unroll
+  for (int j = 0; j < 16; j += 8) {
+    __nv_bfloat162 h[4], l[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      h[u] = __floats2bfloat162_rn(o[j + 2 * u], o[j + 2 * u + 1]);
+      const float2 f = __bfloat1622float2(h[u]);
+      l[u] = __floats2bfloat162_rn(o[j + 2 * u] - f.x, o[j + 2 * u + 1] - f.y);
+    }
+    const int ch = swz_chunk((c0 + j) / 8, m, 2 * nc);
+    uint4 uh, ul;
+    uh.x = *reinterpret_cast<uint32_t*>(&h[0]), uh.y = *reinterpret_cast<uint32_t*>(&h[1]);
+    uh.z = *reinterpret_cast<uint32_t*>(&h[2]), uh.w = *reinterpret_cast<uint32_t*>(&h[3]);
+    ul.x = *reinterpret_cast<uint32_t*>(&l[0]), ul.y = *reinterpret_cast<uint32_t*>(&l[1]);
+    ul.z = *reinterpret_cast<uint32_t*>(&l[2]), ul.w = *reinterpret_cast<uint32_t*>(&l[3]);
+    __nv_bfloat16* yb = YB + m * nc + ch * 8;
+    *reinterpret_cast<uint4*>(yb) = uh;  // blocks hi, lo, hi
+    if (sp > 1) {
+      *reinterpret_cast<uint4*>(yb + 128 * nc) = ul;
+      *reinterpret_cast<uint4*>(yb + 256 * nc) = uh;
+    }
+  }
 }
 
 template <int CK, int TZ>
@@ -847,6 +888,10 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
     // s % kEpiGroups == grp are this group's; packed accumulators are zeroed slice by slice
     // after they are read (the spare columns are never read).
     int slice = 0, bias_b = -1;
+    // LayerNorm backward: this lane's warp sums of the (dgamma, dbeta) terms over the group's
+    // slices of the current tile, one per 16-channel chunk (lane l < 16: dgamma of channel
+    // 16 k + l; l >= 16: dbeta of channel 16 k + l - 16)
+    float lnacc0 = 0.f, lnacc1 = 0.f, lnacc2 = 0.f, lnacc3 = 0.f;
     for (int i = 0; i < ntile; ++i) {
       const int buf = i & 1;
       const bool ok = epi_all(mbar_wait(smem_u32(&tfull[buf]), (i >> 1) & 1), grp);
@@ -858,6 +903,7 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
       int tile = blockIdx.x + i * gridDim.x;
       const int b = tile / per_b;
       tile %= per_b;
+      const int tile_b = tile;  // the tile's index within its problem
       const int x0 = (tile % g.tiles_x) * 8;
       tile /= g.tiles_x;
       const int y0 = (tile % g.tiles_y) * 16;
@@ -902,6 +948,99 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
               const int chunk = ((c0 % w) + j) / 4;
               *reinterpret_cast<float4*>(row + swz_chunk(chunk, m, 4 * w) * 4) = v;
             }
+          }
+        } else if (g.ln == 2) {
+          // LayerNorm backward of voxel m (the order of ln_bwd_kernel): dp and xhat into this
+          // thread's rows of the slice's two FP32 areas while the sums of gamma dp and gamma
+          // dp xhat run and the warp sums of dp xhat and dp accumulate (lnacc); then dz from
+          // the thread's own rows
+          const float inv_c = 1.0f / (float)nc;
+          const int ox = x0 + (m & 7), oy = y0 + (m >> 3), oz = z0 + zz;
+          const bool inside = ox < g.dout.x && oy < g.dout.y && oz < g.dout.z;
+          const long long vox = ((long long)oz * g.dout.y + oy) * g.dout.x + ox;
+          const long long vo = (long long)b * g.resid_bs + vox * nc;
+          const float* gam = sbias + N + Np;
+          const float rs = inside ? g.rstd[(long long)b * g.rstd_bs + vox] : 0.f;
+          float* DP = S;
+          float* XH = S + 128 * nc;
+          __nv_bfloat16* YB = reinterpret_cast<__nv_bfloat16*>(S + 256 * nc);
+          float s1 = 0.f, s2 = 0.f;
+#pragma unroll 1
+          for (int c0 = 0; c0 < nc; c0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(tmem + lanes + (uint32_t)(col0 + c0), r);
+            float d[16], xh[16], a[16];
+#pragma unroll
+            for (int j = 0; j < 16; j += 4) {
+              float4 q = make_float4(0.f, 0.f, 0.f, 0.f), av = q, hv = q;
+              if (inside) {
+                if (g.resid) q = *reinterpret_cast<const float4*>(g.resid + vo + c0 + j);
+                av = *reinterpret_cast<const float4*>(g.aout + vo + c0 + j);
+                hv = *reinterpret_cast<const float4*>(g.xh_in + vo + c0 + j);
+              }
+              d[j] = __uint_as_float(r[j]) + q.x, d[j + 1] = __uint_as_float(r[j + 1]) + q.y;
+              d[j + 2] = __uint_as_float(r[j + 2]) + q.z, d[j + 3] = __uint_as_float(r[j + 3]) + q.w;
+              a[j] = av.x, a[j + 1] = av.y, a[j + 2] = av.z, a[j + 3] = av.w;
+              xh[j] = hv.x, xh[j + 1] = hv.y, xh[j + 2] = hv.z, xh[j + 3] = hv.w;
+            }
+            float v[32];  // dp xhat (dgamma terms) then dp (dbeta terms) of the 16 channels
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              float dp = inside ? d[u] : 0.f;
+              if (g.act) dp = a[u] > 0.f ? dp : kLeakySlope * dp;
+              const float gd = dp * gam[c0 + u];
+              s1 += gd;
+              s2 += gd * xh[u];
+              d[u] = dp;
+              v[u] = dp * xh[u];
+              v[16 + u] = dp;
+            }
+            // reduce-scatter over the warp: afterwards lane l holds the warp's sum of v[l]
+#pragma unroll
+            for (int k = 16; k >= 1; k >>= 1) {
+              const bool up = (lane & k) != 0;
+#pragma unroll
+              for (int i = 0; i < k; ++i) {
+                const float give = up ? v[i] : v[i + k];
+                const float keep = up ? v[i + k] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, give, k);
+              }
+            }
+            switch (c0 >> 4) {  // (named registers: the chunk loop is not unrolled)
+              case 0: lnacc0 += v[0]; break;
+              case 1: lnacc1 += v[0]; break;
+              case 2: lnacc2 += v[0]; break;
+              default: lnacc3 += v[0]; break;
+            }
+            float* drow = DP + (c0 / w) * (128 * w) + m * w;
+            float* hrow = XH + (c0 / w) * (128 * w) + m * w;
+#pragma unroll
+            for (int j = 0; j < 16; j += 4) {
+              const int ch = swz_chunk(((c0 % w) + j) / 4, m, 4 * w);
+              *reinterpret_cast<float4*>(drow + ch * 4) = make_float4(d[j], d[j + 1], d[j + 2], d[j + 3]);
+              *reinterpret_cast<float4*>(hrow + ch * 4) =
+                  make_float4(xh[j], xh[j + 1], xh[j + 2], xh[j + 3]);
+            }
+          }
+          const float m1 = s1 * inv_c, m2 = s2 * inv_c;
+#pragma unroll 1
+          for (int c0 = 0; c0 < nc; c0 += 16) {
+            float* drow = DP + (c0 / w) * (128 * w) + m * w;
+            const float* hrow = XH + (c0 / w) * (128 * w) + m * w;
+            float o[16];
+#pragma unroll
+            for (int j = 0; j < 16; j += 4) {
+              const int ch = swz_chunk(((c0 % w) + j) / 4, m, 4 * w);
+              const float4 dd = *reinterpret_cast<const float4*>(drow + ch * 4);
+              const float4 xx = *reinterpret_cast<const float4*>(hrow + ch * 4);
+              o[j] = rs * (dd.x * gam[c0 + j] - m1 - xx.x * m2);
+              o[j + 1] = rs * (dd.y * gam[c0 + j + 1] - m1 - xx.y * m2);
+              o[j + 2] = rs * (dd.z * gam[c0 + j + 2] - m1 - xx.z * m2);
+              o[j + 3] = rs * (dd.w * gam[c0 + j + 3] - m1 - xx.w * m2);
+              *reinterpret_cast<float4*>(drow + ch * 4) =
+                  make_float4(o[j], o[j + 1], o[j + 2], o[j + 3]);  // FP32 dz, own row
+            }
+            if (g.ybf) stage_slice_bf16(YB, m, nc, c0, o, g.sp);
           }
         } else {
           // LayerNorm of voxel m over its N channels: three passes over TMEM (mean, the
@@ -965,30 +1104,7 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
               *reinterpret_cast<float4*>(hrow + ch * 4) =
                   make_float4(xh[j], xh[j + 1], xh[j + 2], xh[j + 3]);
             }
-            if (g.ybf) {  // sp blocks of nc BF16 channels, each its own box of 2 nc-byte rows
-#pragma unroll
-              for (int j = 0; j < 16; j += 8) {
-                __nv_bfloat162 h[4], l[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  h[u] = __floats2bfloat162_rn(o[j + 2 * u], o[j + 2 * u + 1]);
-                  const float2 f = __bfloat1622float2(h[u]);
-                  l[u] = __floats2bfloat162_rn(o[j + 2 * u] - f.x, o[j + 2 * u + 1] - f.y);
-                }
-                const int ch = swz_chunk((c0 + j) / 8, m, 2 * nc);
-                uint4 uh, ul;
-                uh.x = *reinterpret_cast<uint32_t*>(&h[0]), uh.y = *reinterpret_cast<uint32_t*>(&h[1]);
-                uh.z = *reinterpret_cast<uint32_t*>(&h[2]), uh.w = *reinterpret_cast<uint32_t*>(&h[3]);
-                ul.x = *reinterpret_cast<uint32_t*>(&l[0]), ul.y = *reinterpret_cast<uint32_t*>(&l[1]);
-                ul.z = *reinterpret_cast<uint32_t*>(&l[2]), ul.w = *reinterpret_cast<uint32_t*>(&l[3]);
-                __nv_bfloat16* yb = YB + m * nc + ch * 8;
-                *reinterpret_cast<uint4*>(yb) = uh;  // blocks hi, lo, hi
-                if (g.sp > 1) {
-                  *reinterpret_cast<uint4*>(yb + 128 * nc) = ul;
-                  *reinterpret_cast<uint4*>(yb + 256 * nc) = uh;
-                }
-              }
-            }
+            if (g.ybf) stage_slice_bf16(YB, m, nc, c0, o, g.sp);
           }
           if (inside) g.rstd[(long long)b * g.rstd_bs + vox] = rs;
         }
@@ -1004,12 +1120,14 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
         epi_sync(grp);
         if (tid == 0) {
           if (z0 + zz < g.dout.z) {
-            for (int k = 0; k < nc / w; ++k)
-              tma_store_5d(om, smem_u32(S + k * (128 * w)), k * w, x0, y0, z0 + zz, b, add);
-            if (ln) {
+            if (!(ln && g.ln == 2) || g.out)  // the backward's FP32 dz only when asked for
               for (int k = 0; k < nc / w; ++k)
-                tma_store_5d(&tm_xh, smem_u32(S + 128 * nc + k * (128 * w)), k * w, x0, y0,
-                             z0 + zz, b, false);
+                tma_store_5d(om, smem_u32(S + k * (128 * w)), k * w, x0, y0, z0 + zz, b, add);
+            if (ln) {
+              if (g.ln == 1)
+                for (int k = 0; k < nc / w; ++k)
+                  tma_store_5d(&tm_xh, smem_u32(S + 128 * nc + k * (128 * w)), k * w, x0, y0,
+                               z0 + zz, b, false);
               if (g.ybf)
                 for (int k = 0; k < g.sp; ++k)
                   tma_store_5d(&tm_ybf, smem_u32(S + 256 * nc) + (uint32_t)(k * 128 * nc * 2),
@@ -1028,6 +1146,26 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
       if (grp >= nparts * TZ) {  // a group without a slice of this tile still hands it back
         tc_fence_before();
         mbar_arrive(smem_u32(&tempty[buf]));
+      }
+      if (g.ln == 2) {  // the group's row of this tile: the four warps' sums in order
+        // (the staging slice is free: every store of the group's slices has read it)
+        float* W = stg_g;
+        const int nk = N / 16;
+        const float acc4[4] = {lnacc0, lnacc1, lnacc2, lnacc3};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (k < nk) W[(quad * 4 + k) * 32 + lane] = acc4[k];
+        epi_sync(grp);
+        if (tid < 2 * N) {
+          const int cc = tid < N ? tid : tid - N;
+          const int k = cc / 16, l = (tid < N ? 0 : 16) + cc % 16;
+          float acc = 0.f;
+          for (int q = 0; q < 4; ++q) acc += W[(q * 4 + k) * 32 + l];
+          g.part[((long long)b * g.rows_b + (long long)tile_b * kEpiGroups + grp) *
+                     (2 * N) + tid] = acc;
+        }
+        epi_sync(grp);
+        lnacc0 = lnacc1 = lnacc2 = lnacc3 = 0.f;
       }
     }
     if (tid == 0) bulk_wait_all();  // every store has landed before the CTA may exit
@@ -2082,19 +2220,28 @@ cudaError_t launch_tc3(const CUtensorMap& a, const CUtensorMap& w, int cin, int 
     const int grid = (int)std::min<long long>(total, sm_count());
     // (the staging term's slack covers the kernel's 1024-byte alignment of its base)
     const size_t sm = (size_t)g.ring_bytes + tc3p_staging(n, npm, lsp, nbuf);
-    CUtensorMap mo, mop, mxh, myb;
-    cudaError_t e = encode_out(&mo, out, B, dout, n, n % 32 == 0 ? 32 : 16, out_bs);
+    CUtensorMap mo{}, mop, mxh, myb;
+    // (the LayerNorm backward stores its FP32 output only when asked to)
+    cudaError_t e = out ? encode_out(&mo, out, B, dout, n, n % 32 == 0 ? 32 : 16, out_bs)
+                        : cudaSuccess;
     if (e == cudaSuccess && mode == 1)
       e = encode_out(&mop, out_p, B, dout, np, np % 32 == 0 ? 32 : 16, outp_bs);
     else
       mop = mo;
     mxh = mo, myb = mo;
     if (ln) {
-      g.ln = 1, g.act = ln->act, g.sp = ln->sp, g.ybf = ln->ybf ? 1 : 0;
+      g.ln = ln->bwd ? 2 : 1, g.act = ln->act, g.sp = ln->sp, g.ybf = ln->ybf ? 1 : 0;
       g.gamma = ln->gamma, g.gamma_bs = ln->gamma_bs;
       g.resid = ln->resid, g.resid_bs = out_bs;
       g.rstd = ln->rstd, g.rstd_bs = dout.count();
-      if (e == cudaSuccess) e = encode_out(&mxh, ln->xhat, B, dout, n, n % 32 == 0 ? 32 : 16, out_bs);
+      if (ln->bwd) {
+        if (mode != 0 || acc || !ln->aout || !ln->xhat || !ln->part)
+          return cudaErrorInvalidValue;
+        g.aout = ln->aout, g.xh_in = ln->xhat, g.part = ln->part;
+        g.rows_b = (long long)g.tiles_x * g.tiles_y * g.tiles_z * kEpiGroups;
+      } else if (e == cudaSuccess) {
+        e = encode_out(&mxh, ln->xhat, B, dout, n, n % 32 == 0 ? 32 : 16, out_bs);
+      }
       if (e == cudaSuccess && ln->ybf)
         e = encode_out_bf16(&myb, ln->ybf, B, dout, ln->sp * n, n, dout.count() * ln->sp * n);
     }
@@ -2290,6 +2437,14 @@ int bf16_add_input_layer(Bf16Net& bf, int ci_real, int co, Dims3 din, long long 
   return (int)bf.layers.size() - 1;
 }
 
+static __nv_bfloat16* dy_buf(const Bf16Net& bf, const TcLayer& L) {
+  return L.dyslot ? bf.ybf2 : bf.ybf;
+}
+
+__nv_bfloat16* bf16_dy_buffer(const Bf16Net& bf, int layer) {
+  return dy_buf(bf, bf.layers[layer]);
+}
+
 void bf16_layout(Bf16Net& bf, char* base, size_t& used, int B, long long max_act) {
   auto take = [&](size_t bytes) {
     char* p = base ? base + used : nullptr;
@@ -2301,6 +2456,9 @@ void bf16_layout(Bf16Net& bf, char* base, size_t& used, int B, long long max_act
   bf.err = reinterpret_cast<int*>(take(sizeof(int)));
   bf.xbf = reinterpret_cast<__nv_bfloat16*>(take(act_bytes));
   bf.ybf = reinterpret_cast<__nv_bfloat16*>(take(act_bytes));
+  bool two_dy = false;
+  for (const TcLayer& L : bf.layers) two_dy |= L.dyslot != 0;
+  bf.ybf2 = two_dy ? reinterpret_cast<__nv_bfloat16*>(take(act_bytes)) : nullptr;
   bool any_proj = false;
   for (const TcLayer& L : bf.layers) any_proj |= L.projd || L.projw;
   bf.pbf = any_proj ? reinterpret_cast<__nv_bfloat16*>(take(act_bytes)) : nullptr;
@@ -2321,7 +2479,7 @@ void bf16_layout(Bf16Net& bf, char* base, size_t& used, int B, long long max_act
 // form of the kernel that runs it; a fused projection's dz_p column (pbf) likewise.
 cudaError_t encode_wgrad_maps(TcLayer& L, const Bf16Net& bf, int B, int blk) {
   const int sp = bf.sp;
-  __nv_bfloat16* y = bf.ybf + (size_t)blk * L.co;
+  __nv_bfloat16* y = dy_buf(bf, L) + (size_t)blk * L.co;
   __nv_bfloat16* x = L.xin + (size_t)blk * L.ci;
   const int yrow = sp * L.co, xrow = sp * L.ci;
   cudaError_t e = cudaSuccess;
@@ -2356,7 +2514,7 @@ cudaError_t encode_halo_maps(TcLayer& L, const Bf16Net& bf, int B, int dir) {
     }
     return e;
   }
-  cudaError_t e = encode_act_halo(&L.act_d3, bf.ybf, B, L.dout, L.kd, L.ck3d, L.tz3d);
+  cudaError_t e = encode_act_halo(&L.act_d3, dy_buf(bf, L), B, L.dout, L.kd, L.ck3d, L.tz3d);
   if (e == cudaSuccess)
     e = encode_w(&L.w_d3, bf.wbuf + L.wd_off, B, bf.wstride, L.kd, T, L.ci, L.ck3d, 9, 3);
   if (e == cudaSuccess && L.projd) {
@@ -2384,7 +2542,7 @@ cudaError_t bf16_finalize(Bf16Net& bf, int B) {
       e = encode_w(&L.w_f, bf.wbuf + L.wf_off, B, bf.wstride, L.kf, T, L.co, chunk_for(L.kf), 1,
                    1);
     if (e == cudaSuccess && L.dgrad) {
-      e = encode_act(&L.act_d, bf.ybf, B, L.dout, L.kd, chunk_for(L.kd), 1);
+      e = encode_act(&L.act_d, dy_buf(bf, L), B, L.dout, L.kd, chunk_for(L.kd), 1);
       if (e == cudaSuccess)
         e = encode_w(&L.w_d, bf.wbuf + L.wd_off, B, bf.wstride, L.kd, T, L.ci, chunk_for(L.kd), 1,
                      1);
@@ -2397,7 +2555,7 @@ cudaError_t bf16_finalize(Bf16Net& bf, int B) {
         e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, L.kf, T, L.co, L.ck3f, 9, 3);
     }
     if (e == cudaSuccess && L.ck3d) {
-      e = encode_act_halo(&L.act_d3, bf.ybf, B, L.dout, L.kd, L.ck3d, L.tz3d);
+      e = encode_act_halo(&L.act_d3, dy_buf(bf, L), B, L.dout, L.kd, L.ck3d, L.tz3d);
       if (e == cudaSuccess)
         e = encode_w(&L.w_d3, bf.wbuf + L.wd_off, B, bf.wstride, L.kd, T, L.ci, L.ck3d, 9, 3);
     }
@@ -2676,7 +2834,7 @@ cudaError_t bf16_conv_wgrad(Bf16Net& bf, int layer, const float* x, const float*
                       ? cudaSuccess
                       : stage_rows(x, L.xin, (long long)B * L.din.count(), L.ci, bf.sp, stream);
   if (e == cudaSuccess && !dy_staged)
-    e = stage_rows(dy, bf.ybf, (long long)B * L.dout.count(), L.co, bf.sp, stream);
+    e = stage_rows(dy, dy_buf(bf, L), (long long)B * L.dout.count(), L.co, bf.sp, stream);
   if (e != cudaSuccess) return e;
   const int passes = bf16_wgrad_passes(bf, layer);
   // partial-row length as the kernels write it: the input layer keeps its real channels
@@ -2947,7 +3105,7 @@ cudaError_t bf16_conv_dgrad_proj(Bf16Net& bf, int la, const float* dz_a, const f
   const TcLayer& L = bf.layers[la];
   if (!L.projd) return cudaErrorInvalidValue;
   const long long nv = (long long)B * L.dout.count();
-  cudaError_t e = dza_staged ? cudaSuccess : stage_rows(dz_a, bf.ybf, nv, L.co, bf.sp, stream);
+  cudaError_t e = dza_staged ? cudaSuccess : stage_rows(dz_a, dy_buf(bf, L), nv, L.co, bf.sp, stream);
   if (e == cudaSuccess && !dzp_staged) e = stage_rows(dz_p, bf.pbf, nv, L.co, bf.sp, stream);
   if (e != cudaSuccess) return e;
   return launch_tc3(L.act_d3, L.w_d3, L.kd, L.ck3d, L.tz3d, L.pack3d, L.per3d, nullptr, dx, L.din, L.ci, B,
@@ -3139,7 +3297,7 @@ cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, 
   if (!L.dgrad) return cudaErrorInvalidValue;
   cudaError_t e =
       dy_staged ? cudaSuccess
-                : stage_rows(dy, bf.ybf, (long long)B * L.dout.count(), L.co, bf.sp, stream);
+                : stage_rows(dy, dy_buf(bf, L), (long long)B * L.dout.count(), L.co, bf.sp, stream);
   if (e != cudaSuccess) return e;
   if (L.s == 2) {
     const Dims3 q{(L.din.z + 1) / 2, (L.din.y + 1) / 2, (L.din.x + 1) / 2};
@@ -3151,6 +3309,34 @@ cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, 
                       L.din.count() * L.ci, 0, accumulate, bf.err, stream);
   return launch_tc(L.act_d, L.w_d, conv_plan(L.k, 1), 1, L.kd, nullptr, dx, L.din, L.din, L.ci,
                    B, L.din.count() * L.ci, 0, accumulate, bf.err, stream);
+}
+
+bool bf16_dgrad_ln_ok(const Bf16Net& bf, int layer, int sp) {
+  const TcLayer& L = bf.layers[layer];
+  if (!L.dgrad || L.s != 1 || !L.ck3d || !L.per3d || L.projd || L.ci > 64) return false;
+  const Tc3Plan pl = tc3_fixed(L.kd, L.ci, 0, L.ck3d, L.tz3d, L.pack3d);
+  return tc3_ln_stages(pl, L.ci, 0, sp, 1) >= 2;
+}
+
+long long bf16_dgrad_ln_rows(const Bf16Net& bf, int layer) {
+  const TcLayer& L = bf.layers[layer];
+  const int tz = std::max(L.tz3d, 1);
+  return ceil_div(L.din.x, 8) * ceil_div(L.din.y, 16) * ceil_div(L.din.z, tz) * kEpiGroups;
+}
+
+cudaError_t bf16_conv_dgrad_ln(Bf16Net& bf, int layer, const float* dy, float* dz_out,
+                               const Bf16Ln& ln, int B, cudaStream_t stream, bool dy_staged) {
+  const TcLayer& L = bf.layers[layer];
+  if (!ln.bwd || !bf16_dgrad_ln_ok(bf, layer, bf.sp)) return cudaErrorInvalidValue;
+  cudaError_t e =
+      dy_staged ? cudaSuccess
+                : stage_rows(dy, dy_buf(bf, L), (long long)B * L.dout.count(), L.co, bf.sp, stream);
+  if (e != cudaSuccess) return e;
+  Bf16Ln l = ln;
+  l.sp = bf.sp;
+  return launch_tc3(L.act_d3, L.w_d3, L.kd, L.ck3d, L.tz3d, L.pack3d, L.per3d, nullptr, dz_out,
+                    L.din, L.ci, B, L.din.count() * L.ci, 0, 0, bf.err, stream, 0, nullptr,
+                    nullptr, 0, nullptr, nullptr, 0, &l);
 }
 
 long long bf16_op_workspace(int B, Dims3 din, int ci, int co, int k, int s) {

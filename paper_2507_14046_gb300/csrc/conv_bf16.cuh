@@ -48,12 +48,15 @@ struct TcLayer {
   __nv_bfloat16* xin = nullptr;   // BF16 copy of the forward input (kept for the weight gradient)
   int ci_real = 0;                // input channels of the model (ci is padded up to 16)
   bool input_layer = false;       // reads the padded BF16 copy of the network input (zbf)
+  int dyslot = 0;                 // BF16 staging buffer of this layer's dy: 0 ybf, 1 ybf2
 };
 
 // Device buffers of the BF16 path (carved from the context arena) and its layers.
 struct Bf16Net {
   __nv_bfloat16* xbf = nullptr;   // BF16 staging of one convolution input (or dy)
   __nv_bfloat16* ybf = nullptr;   // BF16 staging of dy for the weight gradient
+  __nv_bfloat16* ybf2 = nullptr;  // a second dy staging buffer (layers with dyslot 1), so a
+                                  // data gradient can stage the next layer's dy while it reads
   __nv_bfloat16* pbf = nullptr;   // BF16 staging of a fused projection's dy
   __nv_bfloat16* wbuf = nullptr;  // BF16 weights of every tensor-core layer, per problem
   __nv_bfloat16* zbf = nullptr;   // network input, BF16, channels padded to 16 (input layer)
@@ -139,6 +142,11 @@ struct Bf16Ln {
   __nv_bfloat16* ybf;
   int act;             // 1: LeakyReLU
   int sp;              // set by the call: BF16 blocks of ybf (Bf16Net::sp)
+  // Backward form (bf16_conv_dgrad_ln): xhat and rstd are the saved inputs, resid (or null)
+  // a gradient already accumulated for the data gradient's output, ybf the staging of dz.
+  int bwd = 0;
+  const float* aout = nullptr;  // the block output a = act(LN(z) ...) [B][voxels][C]
+  float* part = nullptr;        // [B][bf16_dgrad_ln_rows][2 C]: dgamma, dbeta partial sums
 };
 // Whether layer's forward (with a fused projection of np channels when np > 0) runs the
 // persistent halo kernel with room for the LayerNorm epilogue (co <= 64).
@@ -149,9 +157,27 @@ cudaError_t bf16_conv_fwd_ln(Bf16Net& bf, int layer, const float* x, const float
                              const Bf16Ln& ln, int B, long long bias_bs, cudaStream_t stream,
                              bool x_staged = false, const float* bias_p = nullptr,
                              float* y_p = nullptr);
-// dx (=|+=) data gradient on the tensor cores (dy staged into bf.ybf unless dy_staged).
+// dx (=|+=) data gradient on the tensor cores (dy staged into the layer's dy buffer unless
+// dy_staged).
 cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, int B,
                             int accumulate, cudaStream_t stream, bool dy_staged = false);
+// The BF16 staging buffer that holds this layer's dy (its data and weight gradients read it).
+__nv_bfloat16* bf16_dy_buffer(const Bf16Net& bf, int layer);
+// Whether the layer's data gradient runs the persistent halo kernel with room for the
+// LayerNorm backward epilogue (C = ci <= 64, no fused projection), and the partial-sum rows
+// per problem that epilogue writes.
+bool bf16_dgrad_ln_ok(const Bf16Net& bf, int layer, int sp);
+long long bf16_dgrad_ln_rows(const Bf16Net& bf, int layer);
+// The data gradient D of the layer (dy staged unless dy_staged) followed, in its epilogue,
+// by the LayerNorm (+ LeakyReLU) backward of the block that produced the layer's input x:
+// with d = D (+ ln.resid), dp = d act'(ln.aout), dz = rstd (gamma dp - mean(gamma dp) -
+// xhat mean(gamma dp xhat)) per voxel over the C = ci channels; dz goes to ln.ybf (the
+// consumer's dy staging, sp blocks) and, when dz_out is set, to dz_out [B][voxels][C] FP32;
+// the (dgamma, dbeta) sums of each 8 x 16 voxel slice go to ln.part (fixed order; a row
+// reduction gives the gradients).  x's own gradient D + resid is not stored.
+cudaError_t bf16_conv_dgrad_ln(Bf16Net& bf, int layer, const float* dy, float* dz_out,
+                               const Bf16Ln& ln, int B, cudaStream_t stream,
+                               bool dy_staged = false);
 
 // Partial-sum rows (chunks of output voxels) of one pass of a tensor-core weight gradient,
 // and the passes (1, or 3 in split precision); a problem's rows are passes x chunks.

@@ -80,6 +80,7 @@ struct d2ip_ctx {
   bool frame_reset = true;  // fresh Adam state at every fitted frame (else carried)
   bool autotune = true;     // time the tensor-core tilings when the arena is built
   std::vector<long long> tile_rows;  // tilings to apply instead (d2ip_set_tile_plan)
+  bool ln_bwd_fused = false;  // LayerNorm backward in data-gradient epilogues (opt-in)
   // 4D-TV regulariser (off when lam_tv == 0)
   double lam_tv = 0.0, lam_s = 1.0, lam_t = 0.1, tv_eps = 1e-8;
 
@@ -194,6 +195,9 @@ struct Builder {
     Res R;
     R.lvl = lvl;
     R.a = conv(ci, co, 3, 1, lvl);
+    // conv a's dy has a staging buffer of its own: conv b's data gradient writes it (the
+    // LayerNorm backward in its epilogue) while reading conv b's dy from the other one
+    if (R.a.tc >= 0) c->bf.layers[R.a.tc].dyslot = 1;
     R.lna = ln(co);
     R.b = conv(co, co, 3, 1, lvl);
     R.lnb = ln(co);
@@ -378,6 +382,11 @@ void layout_buffers(d2ip_ctx* c, Carve& cv) {
       }
     }
     for (int l = 0; l + 1 < c->L; ++l) res_ws(c->dec[l]);
+    // the LayerNorm backward fused into a data gradient: (dgamma, dbeta) rows per slice
+    for (const TcLayer& T : c->bf.layers)
+      if (T.dgrad && T.s == 1)
+        ws = std::max(ws, (long long)B * ceil_div(T.din.x, 8) * ceil_div(T.din.y, 16) *
+                              (T.din.z + 7) * 2 * T.ci);
     ws = std::max(ws, conv_ws_floats(c, c->tail));
     c->ws_floats = ws;
     c->ws = cv.take<float>(ws);
@@ -478,7 +487,7 @@ struct Launcher {
   // producing kernel wrote this pass, the layer whose dy sits in the dy staging buffer, and
   // the block whose projection dy sits in the projection staging buffer.
   std::vector<const ConvL*> staged_x;
-  const ConvL* ybf_owner = nullptr;
+  const ConvL* dy_owner[2] = {nullptr, nullptr};  // the layer whose dy each staging slot holds
   const void* pbf_owner = nullptr;
   __nv_bfloat16* bf_in(const ConvL* L) {
     return L && L->tc >= 0 && c->precision != D2IP_FP32 ? bf16_input_buffer(c->bf, L->tc)
@@ -494,6 +503,9 @@ struct Launcher {
     return L && L->tc >= 0 && c->precision != D2IP_FP32 &&
            (c->bf.layers[L->tc].dgrad || c->bf.layers[L->tc].wgrad);
   }
+  int dy_slot(const ConvL& L) const { return L.tc >= 0 ? c->bf.layers[L.tc].dyslot : 0; }
+  bool dy_staged(const ConvL& L) const { return dy_owner[dy_slot(L)] == &L; }
+  void own_dy(const ConvL& L) { dy_owner[dy_slot(L)] = &L; }
   void ok(cudaError_t x) {
     if (e == cudaSuccess) e = x;
   }
@@ -524,8 +536,8 @@ struct Launcher {
   void conv_dgrad(const ConvL& L, const float* dy, float* dx, int acc) {
     beg(D2IP_KCLASS_CONV_DGRAD, conv_flops(L));
     if (L.tc >= 0 && c->bf.layers[L.tc].dgrad) {
-      ok(bf16_conv_dgrad(c->bf, L.tc, dy, dx, c->B, acc, c->stream, ybf_owner == &L));
-      ybf_owner = &L;  // dy now sits in the staging buffer
+      ok(bf16_conv_dgrad(c->bf, L.tc, dy, dx, c->B, acc, c->stream, dy_staged(L)));
+      own_dy(L);  // dy now sits in the staging buffer
     } else
       ok(conv3d_dgrad_f32(dy, W(L), dx, c->B, L.din, L.ci, L.co, L.k, L.s,
                           L.dout.count() * L.co, L.din.count() * L.ci, c->Pp, acc, c->stream));
@@ -536,7 +548,7 @@ struct Launcher {
     beg(D2IP_KCLASS_CONV_WGRAD, conv_flops(L));
     if (tc_wgrad(c, L))
       ok(bf16_conv_wgrad(c->bf, L.tc, x, dy, c->ws, c->B, c->stream, nullptr, nullptr, true,
-                         ybf_owner == &L));
+                         dy_staged(L)));
     else
       ok(conv3d_wgrad_partial_f32(x, dy, c->ws, c->B, L.din, L.ci, L.co, L.k, L.s,
                                   L.din.count() * L.ci, L.dout.count() * L.co, c->stream));
@@ -562,11 +574,12 @@ struct Launcher {
               const void* dt_owner = nullptr) {
     const long long nv = c->dims[lvl].count();
     beg(D2IP_KCLASS_LN_BWD, 4.0 * c->B * nv * (L.c * (dt ? 5 : 4) + 1));
-    __nv_bfloat16* dzbf = tc_dy_consumer(dz_consumer) ? c->bf.ybf : nullptr;
+    __nv_bfloat16* dzbf =
+        tc_dy_consumer(dz_consumer) ? bf16_dy_buffer(c->bf, dz_consumer->tc) : nullptr;
     __nv_bfloat16* dtbf = dt && dt_owner && c->bf.pbf ? c->bf.pbf : nullptr;
     ok(layernorm_act_bwd_f32(dy, aout, xh, rs, c->theta + L.g_off, dz, dt, c->ws, c->B, nv,
                              L.c, c->Pp, c->stream, dzbf, dtbf, c->bf.sp));
-    if (dzbf) ybf_owner = dz_consumer;
+    if (dzbf) own_dy(*dz_consumer);
     if (dtbf) pbf_owner = dt_owner;
     ok(reduce_rows_f32(c->ws, G(L.g_off), c->B, layernorm_bwd_blocks(nv, L.c), 2 * L.c, c->Pp,
                        0, c->stream));
@@ -709,22 +722,59 @@ struct Launcher {
     }
     fin();
   }
+  // The data gradient of L (dy: its output gradient) with the LayerNorm (+ LeakyReLU)
+  // backward of the block whose output (aout, saved xh, rs) is L's input, in the epilogue of
+  // the persistent halo kernel: dz of that block goes to consumer's dy staging, (dgamma,
+  // dbeta) to the gradient; resid: a gradient already accumulated for L's input.  False
+  // (nothing launched) where the fused form does not apply.
+  bool dgrad_ln(const ConvL& L, const float* dy, const LnL& ln, const float* resid,
+                const float* aout, const float* xh, const float* rs, const ConvL* consumer) {
+    if (!c->ln_bwd_fused || L.tc < 0 || c->precision == D2IP_FP32 ||
+        !c->bf.layers[L.tc].dgrad ||
+        ln.c != L.ci || !tc_dy_consumer(consumer) || dy_slot(L) == dy_slot(*consumer) ||
+        !bf16_dgrad_ln_ok(c->bf, L.tc, c->bf.sp))
+      return false;
+    const long long rows = bf16_dgrad_ln_rows(c->bf, L.tc);
+    if ((long long)c->B * rows * 2 * ln.c > c->ws_floats) return false;
+    beg(D2IP_KCLASS_CONV_DGRAD, conv_flops(L));
+    Bf16Ln l{};
+    l.gamma = c->theta + ln.g_off, l.gamma_bs = c->Pp;
+    l.resid = resid, l.xhat = const_cast<float*>(xh), l.rstd = const_cast<float*>(rs);
+    l.ybf = bf16_dy_buffer(c->bf, consumer->tc), l.act = 1;
+    l.bwd = 1, l.aout = aout, l.part = c->ws;
+    ok(bf16_conv_dgrad_ln(c->bf, L.tc, dy, nullptr, l, c->B, c->stream, dy_staged(L)));
+    own_dy(L);
+    own_dy(*consumer);
+    ok(reduce_rows_f32(c->ws, G(ln.g_off), c->B, rows, 2 * ln.c, c->Pp, 0, c->stream));
+    fin();
+    return true;
+  }
   // dout: gradient of R.out; writes dx (gradient of R.x).  Without a projection the residual
-  // gradient dt goes straight into dx and conv a's data gradient adds onto it.
-  void res_bwd(Res& R, const float* dout, float* dx) {
+  // gradient dt goes straight into dx and conv a's data gradient adds onto it; then, when
+  // next (the unit whose output is R.x) can take it, next's LayerNorm backward runs in that
+  // data gradient's epilogue instead (dx is not stored) and true is returned.
+  bool res_bwd(Res& R, const float* dout, float* dx, Unit* next = nullptr) {
     LevelBufs& T = c->lb[R.lvl];
     ln_bwd(R.lnb, R.lvl, dout, R.out, R.xh_b, R.rs_b, T.tz, R.proj ? T.tt : dx, &R.b,
            R.fuse_d || R.fuse_w ? &R : nullptr);
-    conv_dgrad(R.b, T.tz, T.th, 0);
-    conv_wgrad(R.b, R.h1, T.tz);
-    ln_bwd(R.lna, R.lvl, T.th, R.h1, R.xh_a, R.rs_a, T.tz, nullptr, &R.a);
+    if (dgrad_ln(R.b, T.tz, R.lna, nullptr, R.h1, R.xh_a, R.rs_a, &R.a)) {
+      conv_wgrad(R.b, R.h1, T.tz);
+    } else {
+      conv_dgrad(R.b, T.tz, T.th, 0);
+      conv_wgrad(R.b, R.h1, T.tz);
+      ln_bwd(R.lna, R.lvl, T.th, R.h1, R.xh_a, R.rs_a, T.tz, nullptr, &R.a);
+    }
+    bool next_done = false;
     if (R.fuse_d) {  // dx = conv_a^T(dz_a) + W_p^T dz_p in one launch
       beg(D2IP_KCLASS_CONV_DGRAD, conv_flops(R.a) + conv_flops(R.p));
       ok(bf16_conv_dgrad_proj(c->bf, R.a.tc, T.tz, T.tt, dx, c->B, c->stream,
-                              ybf_owner == &R.a, pbf_owner == &R));
-      ybf_owner = &R.a;
+                              dy_staged(R.a), pbf_owner == &R));
+      own_dy(R.a);
       pbf_owner = &R;
       fin();
+    } else if (next && !R.proj &&
+               dgrad_ln(R.a, T.tz, next->ln, dx, next->a, next->xh, next->rs, &next->conv)) {
+      next_done = true;
     } else {
       conv_dgrad(R.a, T.tz, dx, R.proj ? 0 : 1);
     }
@@ -733,7 +783,7 @@ struct Launcher {
       float* part_p = c->ws + (long long)c->B * rows * (R.a.wcount() + R.a.co);
       beg(D2IP_KCLASS_CONV_WGRAD, conv_flops(R.a) + conv_flops(R.p));
       ok(bf16_conv_wgrad(c->bf, R.a.tc, R.x, T.tz, c->ws, c->B, c->stream, T.tt, part_p, true,
-                         ybf_owner == &R.a));
+                         dy_staged(R.a)));
       ok(reduce_rows_f32(c->ws, G(R.a.w_off), c->B, rows, R.a.wcount() + R.a.co, c->Pp, 0,
                          c->stream));
       ok(reduce_rows_f32(part_p, G(R.p.w_off), c->B, rows, R.p.wcount() + R.p.co, c->Pp, 0,
@@ -746,10 +796,12 @@ struct Launcher {
       if (!R.fuse_d) conv_dgrad(R.p, T.tt, dx, 1);
       if (!R.fuse_w) conv_wgrad(R.p, R.x, T.tt);
     }
+    return next_done;
   }
-  void unit_bwd(Unit& u, const float* da, float* dx, int acc, bool dgrad) {
+  // ln_done: the unit's LayerNorm backward already ran (dz staged for u.conv)
+  void unit_bwd(Unit& u, const float* da, float* dx, int acc, bool dgrad, bool ln_done = false) {
     float* tz = c->lb[u.lvl_out].tz;
-    ln_bwd(u.ln, u.lvl_out, da, u.a, u.xh, u.rs, tz, nullptr, &u.conv);
+    if (!ln_done) ln_bwd(u.ln, u.lvl_out, da, u.a, u.xh, u.rs, tz, nullptr, &u.conv);
     if (dgrad) conv_dgrad(u.conv, tz, dx, acc);
     conv_wgrad(u.conv, u.x, tz);
   }
@@ -758,7 +810,7 @@ struct Launcher {
       ok(c->fr.backward(fr_run()));
       return;
     }
-    ybf_owner = nullptr;
+    dy_owner[0] = dy_owner[1] = nullptr;
     pbf_owner = nullptr;
     const int L = c->L;
     const float* tail_in = L > 1 ? c->dec[0].out : c->enc[0].out;
@@ -787,12 +839,12 @@ struct Launcher {
     }
     for (int l = L - 1; l >= 1; --l) {
       const float* dout = l == L - 1 ? c->lb[l].g1 : c->lb[l].de;
-      res_bwd(c->enc[l], dout, c->lb[l].g2);
-      unit_bwd(c->down[l], c->lb[l].g2, c->lb[l - 1].de, 1, true);
+      const bool done = res_bwd(c->enc[l], dout, c->lb[l].g2, &c->down[l]);
+      unit_bwd(c->down[l], c->lb[l].g2, c->lb[l - 1].de, 1, true, done);
     }
     const float* d0 = L == 1 ? c->lb[0].g1 : c->lb[0].de;
-    res_bwd(c->enc[0], d0, c->lb[0].g2);
-    unit_bwd(c->stem, c->lb[0].g2, nullptr, 0, false);
+    const bool done0 = res_bwd(c->enc[0], d0, c->lb[0].g2, &c->stem);
+    unit_bwd(c->stem, c->lb[0].g2, nullptr, 0, false, done0);
   }
   void adam() {
     beg(D2IP_KCLASS_ADAM, 28.0 * c->B * c->P);
@@ -1339,6 +1391,13 @@ d2ip_status d2ip_set_tile_plan(d2ip_ctx* c, const long long* rows, int n_rows) {
   if (!c || n_rows < 0 || (n_rows > 0 && !rows)) return fail(c, D2IP_ERR_BAD_ARG, "bad argument");
   if (c->arena) return fail(c, D2IP_ERR_STATE, "the workspace already exists");
   c->tile_rows.assign(rows, rows + 15LL * n_rows);
+  return D2IP_OK;
+}
+
+d2ip_status d2ip_set_ln_backward_fusion(d2ip_ctx* c, int on) {
+  if (!c) return fail(nullptr, D2IP_ERR_BAD_ARG, "null context");
+  c->ln_bwd_fused = on != 0;
+  drop_graphs(c);  // captured graphs hold the old launch sequence
   return D2IP_OK;
 }
 

@@ -4,9 +4,10 @@ convolutions span several persistent-kernel tiles (24 x 24 x 12) against a B = 1
 that problem and against the oracle's teacher-forced step; and d2ip_fit_batched over two
 uneven groups against separate d2ip_fit_sequence calls.
 
-The forward pass has no reduction across problems, so Delta sigma and the loss are
-bit-identical whatever the batch; the weight gradients are split-K sums whose chunking is
-sized to fill the GPU for the batch at hand, so they agree to FP32 rounding order only."""
+The forward pass has no reduction across problems, so with the same tilings Delta sigma and
+the loss are bit-identical whatever the batch; the weight gradients are split-K sums whose
+chunking is sized to fill the GPU for the batch at hand, so they agree to FP32 rounding order
+only."""
 import numpy as np
 import pytest
 
@@ -29,8 +30,8 @@ def _group(seeds):
     return base, pbs, V
 
 
-def _ctx(d2ip, base, Zs, thetas, precision, batch):
-    c = d2ip.Context(GRID, LEVELS, WIDTHS, 8, precision, batch)
+def _ctx(d2ip, base, Zs, thetas, precision, batch, tile_plan=None):
+    c = d2ip.Context(GRID, LEVELS, WIDTHS, 8, precision, batch, tile_plan=tile_plan)
     c.load_J(base.J)
     c.set_input(np.ascontiguousarray(Zs), np.ascontiguousarray(thetas))
     c.set_optim(5e-4)
@@ -48,8 +49,11 @@ def test_batch_of_seven_equals_single_problem_contexts(d2ip, precision):
     tr_b = cb.run_steps(V, 1, trace=True)
     g_b = cb.grad()
     th_b = cb.state()[0]
+    # the single-problem contexts take the batch context's tilings (the autotuner chooses per
+    # shape and batch size, and a different tiling sums in a different order)
+    plan, _ = cb.tile_plan()
     for i in range(B):
-        c1 = _ctx(d2ip, base, Zs[i:i + 1], th[i:i + 1], precision, 1)
+        c1 = _ctx(d2ip, base, Zs[i:i + 1], th[i:i + 1], precision, 1, tile_plan=plan)
         ds1 = c1.forward()
         tr1 = c1.run_steps(V[i:i + 1], 1, trace=True)
         np.testing.assert_array_equal(ds_b[i], ds1[0])
