@@ -1521,6 +1521,11 @@ wgrad_s2_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
 // serves all 27 taps and B holds the three x-shifted columns side by side plus the ones:
 // N = 3 Ci + CKB, the columns of x tap kx at kx * Ci.  Per 16-voxel K step that is G MMAs of
 // width N instead of 3 G of width Ci + CKB, at nearly the same issue cost per MMA.
+// fold (packed, split precision, a 16 -> 16 layer in one pass): dy and x are read as their
+// [hi | lo] 32-channel rows, so M = windows x [co_hi | co_lo] and N = x taps x [ci_hi | ci_lo]
+// (+ ones); the template sees Co = Ci = 32 and the epilogue adds the four products of each
+// weight (lanes co and co + 16 through a shuffle, columns ci and ci + 16), the whole
+// (dy_hi + dy_lo)(x_hi + x_lo).
 // NX = 2 (packed, split precision): the hi and lo blocks of x (tm_x, tm_x2) side by side,
 // N = 6 Ci + CKB, and the epilogue adds the two products of each tap: dy_hi x_hi + dy_hi x_lo
 // in one MMA stream (the pass with dy_lo x_hi is a separate NX = 1 launch).
@@ -1544,6 +1549,7 @@ struct Wg3Geom {
   int rows_b;      // partial-sum rows per problem (nchunks times the operand passes)
   int nx;          // x operand sets side by side in N (2: hi and lo of the split precision)
   int bias_on;     // write the ones column's sums (else zeros: a pass that repeats them)
+  int fold;        // split precision in one pass (below)
   uint32_t a_box, b_box, b_off, ones_off, stage, tmem_cols;
   int proj;        // also the weight gradient of a fused 1x1 projection (its dz_p: p_box)
   uint32_t p_off, p_box;
@@ -1697,6 +1703,45 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
   const int Co = CKA;
   const int m = warp * 32 + lane;  // TMEM lane = (window in the MMA, co)
   const int pl = m / Co, co = m % Co;
+  if (kPack && gm.fold) {
+    const int Cr = Co / 2;  // the layer's output channels; lanes co, co + Cr: dy_hi, dy_lo
+    const long long rowf = (long long)Cr * 27 * ci_out + Cr;
+    float* prf = part + ((long long)b * gm.rows_b + chunk) * rowf;
+    const bool writer = co < Cr;
+    for (int g = 0; g < kG; ++g) {
+      const int s0 = g * kTpm < 9 - kTpm ? g * kTpm : 9 - kTpm;
+      const int p = s0 + pl;
+      const bool keep = p >= g * kTpm && p < 9;
+      const int tq = 8 - p, kz = tq / 3, ky = tq % 3;
+      const uint32_t col = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * N);
+      for (int xi = 0; xi < 3; ++xi) {
+        const int t = kz * 9 + ky * 3 + xi;
+        uint32_t r[16], r2[16];
+        if (ok) {
+          tmem_ld16(col + (uint32_t)(xi * Ci), r);        // x_hi columns
+          tmem_ld16(col + (uint32_t)(xi * Ci + Cr), r2);  // x_lo columns
+        }
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          v[j] = ok ? __uint_as_float(r[j]) + __uint_as_float(r2[j]) : 0.f;
+          v[j] += __shfl_xor_sync(0xffffffffu, v[j], Cr);  // + the other dy block
+        }
+        if (keep && writer) {
+          float* out = prf + ((long long)co * 27 + t) * ci_out;
+#pragma unroll
+          for (int j = 0; j < 16; j += 4)
+            if (j < ci_out)
+              *reinterpret_cast<float4*>(out + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+      }
+      uint32_t r[16];
+      if (ok) tmem_ld16(col + (uint32_t)(3 * Ci), r);  // the ones column
+      float v0 = ok ? __uint_as_float(r[0]) : 0.f;
+      v0 += __shfl_xor_sync(0xffffffffu, v0, Cr);
+      if (keep && writer && tq == 4) prf[(long long)Cr * 27 * ci_out + co] = gm.bias_on ? v0 : 0.f;
+    }
+  } else {
   const long long row = (long long)Co * 27 * ci_out + Co;  // the first ci_out channels
   float* prow = part + ((long long)b * gm.rows_b + chunk) * row;
   for (int q = 0; q < kNq; ++q)
@@ -1758,6 +1803,7 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
     if (ok) tmem_ld16(col + (uint32_t)(kPack ? 3 * Ci : Ci), r);
     if (m < Co) pp[(long long)Co * Ci + m] = ok && gm.bias_on ? __uint_as_float(r[0]) : 0.f;
   }
+  }  // not fold
   tc_fence_before();
   // TMEM is freed only once the last commit showed every issued MMA complete
   const int all_drained = __syncthreads_and(drained ? 1 : 0);
@@ -1934,6 +1980,7 @@ int chunk_for(int c) { return c % 64 == 0 ? 64 : (c % 32 == 0 ? 32 : 16); }
 int wg3_tz(int Z);
 int wg3_tz_fit(const TcLayer& L);
 Wg3Geom wg3_geom(const TcLayer& L, int B, bool proj = false);
+Wg3Geom wg3_geom_fold(const TcLayer& L, int B, int sp);
 
 CUtensorMapSwizzle swizzle_for(int ck) {
   return ck == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
@@ -2485,6 +2532,11 @@ cudaError_t encode_wgrad_maps(TcLayer& L, const Bf16Net& bf, int B, int blk) {
   cudaError_t e = cudaSuccess;
   if (L.wg3) {
     const int tz = L.wg_tz;
+    if (blk == 0 && wg3_geom_fold(L, B, sp).nst > 0) {  // [hi | lo]: the first 2 blocks
+      e = encode_box(&L.wgqy, y, B, L.dout, 2 * L.co, 2 * L.co, 8, 3, tz + 2, yrow);
+      if (e == cudaSuccess) e = encode_box(&L.wgqx, x, B, L.din, 2 * L.ci, 2 * L.ci, 8, 1, tz, xrow);
+      if (e != cudaSuccess) return e;
+    }
     e = encode_box(&L.wgy[blk], y, B, L.dout, L.co, L.co, 8, 3, tz + 2, yrow);
     if (e == cudaSuccess)
       e = encode_box(&L.wgx[blk], x, B, L.din, L.ci, chunk_for(L.ci), 8, 1, tz, xrow);
@@ -2724,6 +2776,20 @@ Wg3Geom wg3_geom_dual(const TcLayer& L, int B) {
   return wg3_geom_form(L, B, false, true, 2);
 }
 
+// Split precision, a 16 -> 16 layer (no fused projection): the packed form on [hi | lo]
+// rows of dy and x seen as 32 channels, all four products in one pass (the kernel's fold).
+TcLayer wg3_fold_view(const TcLayer& L) {
+  TcLayer Q = L;
+  Q.co = 32, Q.ci = 32;
+  return Q;
+}
+Wg3Geom wg3_geom_fold(const TcLayer& L, int B, int sp) {
+  if (sp != 3 || !L.wg3 || L.projw || L.co != 16 || L.ci != 16) return Wg3Geom{};
+  Wg3Geom g = wg3_geom_form(wg3_fold_view(L), B, false, true, 1);
+  if (g.nst > 0) g.fold = 1, g.rows_b = g.nchunks, g.bias_on = 1;
+  return g;
+}
+
 template <int CKA, int CKB>
 cudaError_t wg3_attr() {
   cudaError_t e = cudaFuncSetAttribute(wgrad_tc3_kernel<CKA, CKB, 1>,
@@ -2805,6 +2871,8 @@ long long bf16_wgrad_chunks(const Bf16Net& bf, int layer, int B) {
   if (L.wgs2) return wgs2_plan(L, B).chunks;
   if (L.wg3) {
     if (bf.sp > 1) {
+      const Wg3Geom f = wg3_geom_fold(L, B, bf.sp);
+      if (f.nst > 0) return f.nchunks;
       const Wg3Geom d = wg3_geom_dual(L, B);
       if (d.nst > 0) return d.nchunks;
     }
@@ -2815,7 +2883,7 @@ long long bf16_wgrad_chunks(const Bf16Net& bf, int layer, int B) {
 
 int bf16_wgrad_passes(const Bf16Net& bf, int layer) {
   const TcLayer& L = bf.layers[layer];
-  if (!L.wgrad || bf.sp == 1) return 1;
+  if (!L.wgrad || bf.sp == 1 || wg3_geom_fold(L, 1, bf.sp).nst > 0) return 1;
   return wg3_geom_dual(L, 1).nst > 0 ? 2 : 3;
 }
 
@@ -2857,6 +2925,13 @@ cudaError_t bf16_conv_wgrad(Bf16Net& bf, int layer, const float* x, const float*
       }
 #undef D2IP_WS2
     }
+    return cudaGetLastError();
+  }
+  if (L.wg3 && passes == 1 && bf.sp > 1) {  // the split products in one pass
+    const Wg3Geom gf = wg3_geom_fold(L, B, bf.sp);
+    if (gf.nst <= 0) return cudaErrorInvalidValue;
+    launch_wg3<32, 32>(wg3_fold_view(L), gf, L.wgqy, L.wgqx, L.wgqy, part, nullptr, B, bf.err,
+                       stream);
     return cudaGetLastError();
   }
   if (L.wg3) {

@@ -23,6 +23,7 @@ struct TcLayer {
   // tiles) for the hi (index 0) and lo (index 1, split precision only) channel blocks of the
   // staged dy and x, and a fused projection's dz_p column.
   CUtensorMap wgy[2], wgx[2], wgp[2];
+  CUtensorMap wgqy, wgqx;   // split precision in one pass: dy and x as [hi | lo] rows
   int ci = 0, co = 0, k = 3, s = 1;
   int kf = 0, kd = 0;             // K channels of the forward and data-gradient operands:
                                   // ci and co times the operand blocks (Bf16Net::sp)
