@@ -400,6 +400,20 @@ d2ip_status d2ip_sensitivity_residual(const float* J, const float* x, const floa
 /* g[b] = scale * J^T r[b]  (scale = 2/m gives the gradient of the mean-square data term). */
 d2ip_status d2ip_sensitivity_adjoint(const float* J, const float* r, float* g, float scale,
                                      int batch, int m, int n, void* stream);
+/* The two products above on the tensor cores (tcgen05, the form the BF16 precisions use in a
+ * context): J is rounded to BF16 (split != 0: carried as hi + lo, hi = bf16(J), lo =
+ * bf16(J - hi)), and so are x and r, the products accumulate in FP32 with the problems as the
+ * MMA's N: r = J x - dv (FP32, summed over fixed voxel chunks, so deterministic) and, when g is
+ * not NULL, g = scale J^T r.  J [m][n] FP32, x and g [batch][n], dv and r [batch][m], all
+ * device memory.  m a multiple of 8 and at most 1024 (D2IP_ERR_BAD_SHAPE otherwise).
+ * workspace: d2ip_sensitivity_tc_workspace bytes (device; holds the transposed BF16 J, the
+ * staged x and r and the partial sums); its int at the first 256-byte aligned address is the
+ * error word, non-zero after the call when a pipeline wait of the kernel gave up. */
+long long d2ip_sensitivity_tc_workspace(int batch, int m, int n, int split);
+d2ip_status d2ip_sensitivity_products_tc(const float* J, const float* x, const float* dv,
+                                         float* r, float* g, float scale, int batch, int m,
+                                         int n, int split, void* workspace,
+                                         long long workspace_bytes, void* stream);
 /* The 4D-TV regulariser alone: grad[b] += its gradient at dsigma[b] ([batch][n]) given
  * n_previous earlier outputs previous[b][j][n]; value_host[b] (host, may be NULL) receives
  * its value (a synchronising copy).  Workspace: d2ip_tv4d_workspace bytes (device). */

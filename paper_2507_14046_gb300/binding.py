@@ -88,6 +88,7 @@ _SIGS = {
     "d2ip_upsample_concat_backward": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _i, _vp],
     "d2ip_sensitivity_residual": [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _vp, _ll, _vp],
     "d2ip_sensitivity_adjoint": [_vp, _vp, _vp, _f, _i, _i, _i, _vp],
+    "d2ip_sensitivity_products_tc": [_vp, _vp, _vp, _vp, _vp, _f, _i, _i, _i, _i, _vp, _ll, _vp],
     "d2ip_normalize_columns": [_vp, _vp, _i, _i, _vp],
     "d2ip_tv4d": [_vp, _vp, _i, _vp, _vp, _i, _i, _i, _i, _d, _d, _d, _d, _vp, _ll, _vp],
     "d2ip_adam_update": [_vp, _vp, _vp, _vp, _ll, _d, _d, _d, _d, _i, _vp],
@@ -98,6 +99,7 @@ _SIZE_FNS = {
     "d2ip_conv3d_wgrad_tc_workspace": [_i] * 7,
     "d2ip_layernorm_workspace": [_i, _ll, _i],
     "d2ip_sensitivity_workspace": [_i, _i, _i],
+    "d2ip_sensitivity_tc_workspace": [_i, _i, _i, _i],
     "d2ip_tv4d_workspace": [_i, _i, _i, _i],
 }
 
@@ -257,6 +259,10 @@ def d2ip_sensitivity_workspace(*args) -> int:
     return int(_lib.d2ip_sensitivity_workspace(*args))
 
 
+def d2ip_sensitivity_tc_workspace(*args) -> int:
+    return int(_lib.d2ip_sensitivity_tc_workspace(*args))
+
+
 def d2ip_tv4d_workspace(*args) -> int:
     return int(_lib.d2ip_tv4d_workspace(*args))
 
@@ -278,6 +284,7 @@ for _name in ("d2ip_conv3d_forward", "d2ip_conv3d_dgrad", "d2ip_conv3d_wgrad",
               "d2ip_layernorm_act_forward", "d2ip_layernorm_act_backward",
               "d2ip_upsample_concat_forward", "d2ip_upsample_concat_backward",
               "d2ip_sensitivity_residual", "d2ip_sensitivity_adjoint", "d2ip_normalize_columns",
+              "d2ip_sensitivity_products_tc",
               "d2ip_tv4d",
               "d2ip_adam_update"):
     globals()[_name] = _wrap_op(_name)

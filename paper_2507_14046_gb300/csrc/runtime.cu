@@ -10,6 +10,7 @@
 #include "../../include/d2ip.h"
 #include "common.cuh"
 #include "conv_bf16.cuh"
+#include "jprod_tc.cuh"
 #include "fastres.cuh"
 
 using namespace d2ip;
@@ -109,6 +110,8 @@ struct d2ip_ctx {
   float* J = nullptr;
   __nv_bfloat16* Jbf = nullptr;  // BF16 copy of the normalised J, transposed [n][m] (BF16)
   __nv_bfloat16* Jlo = nullptr;  // its low part bf16(J - Jbf) (split precision)
+  JprodTc jp;                    // the J products on the tensor cores (when jp_stage is set)
+  void* jp_stage = nullptr;      // their BF16 staging of x and r
   float* jpart = nullptr;  // column-chunk partial sums of J x
   double* colnorm = nullptr;
   size_t j_bytes = 0;
@@ -687,7 +690,9 @@ struct Launcher {
     const double jb = (c->precision == D2IP_BF16 ? 2.0 : 4.0) * c->m * (double)n,
                  vb = 4.0 * c->B * ((double)n + 2.0 * c->m);
     beg(D2IP_KCLASS_JMUL, jb + vb);
-    if (jb16)
+    if (jb16 && c->jp_stage)
+      ok(jprod_tc_residual(c->jp, c->dsigma, n, c->dv, c->r, c->jpart, c->bf.err, c->stream));
+    else if (jb16)
       ok(jmul_residual_bf16(c->Jbf, c->dsigma, c->dv, c->r, c->jpart, c->B, c->m, (int)n, n,
                             c->stream, c->Jlo));
     else
@@ -696,7 +701,9 @@ struct Launcher {
     fin();
     if (training) {
       beg(D2IP_KCLASS_JTMUL, jb + vb);
-      if (jb16)
+      if (jb16 && c->jp_stage)
+        ok(jprod_tc_adjoint(c->jp, c->gds, 2.0f / (float)c->m, n, c->bf.err, c->stream));
+      else if (jb16)
         ok(jtmul_bf16(c->Jbf, c->r, c->gds, 2.0f / (float)c->m, c->B, c->m, (int)n, n,
                       c->stream, c->Jlo));
       else
@@ -1127,6 +1134,7 @@ d2ip_status d2ip_destroy(d2ip_ctx* c) {
   if (c->jpart) cudaFree(c->jpart);
   if (c->Jbf) cudaFree(c->Jbf);
   if (c->Jlo) cudaFree(c->Jlo);
+  if (c->jp_stage) cudaFree(c->jp_stage);
   if (c->seq_resid) cudaFree(c->seq_resid);
   if (c->hist) cudaFree(c->hist);
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -1277,6 +1285,8 @@ d2ip_status d2ip_load_J(d2ip_ctx* c, const float* J, int m, int n, int normalize
     if (c->Jbf) cudaFree(c->Jbf);
     if (c->Jlo) cudaFree(c->Jlo);
     c->Jbf = c->Jlo = nullptr;
+    if (c->jp_stage) cudaFree(c->jp_stage);
+    c->jp_stage = nullptr;
     c->J = nullptr;
     c->colnorm = nullptr;
     c->r = c->dv = c->jpart = nullptr;
@@ -1300,8 +1310,18 @@ d2ip_status d2ip_load_J(d2ip_ctx* c, const float* J, int m, int n, int normalize
   } else {
     CK(cudaMemsetAsync(c->colnorm, 0, sizeof(double) * n, c->stream));
   }
-  if (c->precision != D2IP_FP32)
+  if (c->precision != D2IP_FP32) {
     CK(transpose_bf16(c->J, c->Jbf, m, (int)n, c->stream, c->Jlo));
+    if (jprod_tc_supported(m, (int)n)) {  // J x and J^T r on the tensor cores
+      if (!c->jp_stage &&
+          cudaMalloc(&c->jp_stage, jprod_tc_staging_bytes(m, (int)n, c->B, c->Jlo != nullptr)) !=
+              cudaSuccess) {
+        c->jp_stage = nullptr;
+        return fail(c, D2IP_ERR_OOM, "device allocation of the J-product staging failed");
+      }
+      CK(jprod_tc_init(c->jp, c->Jbf, c->Jlo, c->jp_stage, m, (int)n, c->B, c->stream));
+    }
+  }
   CK(cudaStreamSynchronize(c->stream));
   c->j_ready = true;
   return D2IP_OK;
@@ -1863,6 +1883,50 @@ d2ip_status d2ip_sensitivity_adjoint(const float* J, const float* r, float* g, f
     return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad J shape (m <= 6400)");
   OPCK(prepare_pointwise_kernels());
   OPCK(jtmul_f32(J, r, g, scale, batch, m, n, n, (cudaStream_t)stream));
+  return D2IP_OK;
+}
+
+static size_t ws_round(size_t b) { return (b + 255) / 256 * 256; }
+
+long long d2ip_sensitivity_tc_workspace(int batch, int m, int n, int split) {
+  if (batch < 1 || n < 1 || !jprod_tc_supported(m, n) || m > 1024) return -1;
+  const size_t jt = ws_round((size_t)m * n * 2);
+  return (long long)(256 + 256 + (split ? 2 : 1) * jt +
+                     ws_round(jprod_tc_staging_bytes(m, n, batch, split != 0)) +
+                     ws_round(sizeof(float) * jprod_tc_chunks(m, n) * (size_t)batch * m));
+}
+
+d2ip_status d2ip_sensitivity_products_tc(const float* J, const float* x, const float* dv,
+                                         float* r, float* g, float scale, int batch, int m,
+                                         int n, int split, void* workspace,
+                                         long long workspace_bytes, void* stream) {
+  if (!J || !x || !dv || !r || !workspace) return fail(nullptr, D2IP_ERR_BAD_ARG, "null pointer");
+  const long long need = d2ip_sensitivity_tc_workspace(batch, m, n, split);
+  if (need < 0)
+    return fail(nullptr, D2IP_ERR_BAD_SHAPE, "bad shape (m a multiple of 8, at most 1024)");
+  if (workspace_bytes < need) return fail(nullptr, D2IP_ERR_BAD_ARG, "workspace too small");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(workspace) + 255) & ~(uintptr_t)255);
+  int* err = reinterpret_cast<int*>(p);
+  p += 256;
+  const size_t jt = ws_round((size_t)m * n * 2);
+  __nv_bfloat16* Jt = reinterpret_cast<__nv_bfloat16*>(p);
+  p += jt;
+  __nv_bfloat16* Jlo = nullptr;
+  if (split) {
+    Jlo = reinterpret_cast<__nv_bfloat16*>(p);
+    p += jt;
+  }
+  void* stage = p;
+  p += ws_round(jprod_tc_staging_bytes(m, n, batch, split != 0));
+  float* part = reinterpret_cast<float*>(p);
+  OPCK(prepare_pointwise_kernels());
+  OPCK(cudaMemsetAsync(err, 0, sizeof(int), st));
+  OPCK(transpose_bf16(J, Jt, m, n, st, Jlo));
+  JprodTc jp;
+  OPCK(jprod_tc_init(jp, Jt, Jlo, stage, m, n, batch, st));
+  OPCK(jprod_tc_residual(jp, x, n, dv, r, part, err, st));
+  if (g) OPCK(jprod_tc_adjoint(jp, g, scale, n, err, st));
   return D2IP_OK;
 }
 
