@@ -526,6 +526,10 @@ def _source_digest(files=None):
 # per (workload, network, precision): the ncu traffic summary and the sources that hold the
 # roofline class's kernels and their launch sequence (a change there voids the figure)
 TRAFFIC_FILES = {
+    ("batch64", "resunet", "bf16x3"): (
+        "roofline_traffic_batch64_bf16x3.txt",
+        ("common.cuh", "conv_bf16.cu", "conv_bf16.cuh", "conv_f32.cu", "pointwise.cu",
+         "runtime.cu", "tc_prims.cuh")),
     ("seq32", "fastres", "fp32"): (
         "roofline_traffic_seq32_fastres_fp32.txt",
         ("common.cuh", "conv_f32.cu", "fastres.cu", "fastres.cuh", "fastres_ops.cu")),
