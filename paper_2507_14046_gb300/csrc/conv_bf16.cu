@@ -392,6 +392,7 @@ struct P3Args {
   int* err;
   Dims3 dout;
   int N, Np, nchunks, tiles_x, tiles_y, tiles_z, B, accumulate, nst, mode, pack;
+  int fold;  // N = 2 outputs: output channel c is D[c] + D[N / 2 + c] (split rows, mode 0)
   uint32_t ring_bytes, stage_bytes;
   uint32_t slice_bytes;  // one epilogue staging slice (128 rows of FP32 outputs, and with the
                          // LayerNorm also xhat and the BF16 copy); per epilogue group, nbuf of
@@ -428,6 +429,18 @@ struct P3Args {
 // 4-pair (R 64) or 2-quad (R 32) atom.
 __device__ __forceinline__ int swz_chunk(int chunk, int m, int R) {
   return chunk ^ ((m * R >> 7) & (R / 16 - 1));
+}
+
+// 16 accumulator columns of this warp's lanes; with off, plus the 16 columns off further on
+// (the two halves of a folded accumulator).
+__device__ __forceinline__ void tmem_ld16f(uint32_t taddr, uint32_t (&r)[16], uint32_t off) {
+  tmem_ld16(taddr, r);
+  if (off) {
+    uint32_t r2[16];
+    tmem_ld16(taddr + off, r2);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(r2[j]));
+  }
 }
 
 // Channels c0..c0+15 of tile row m, values o, into the epilogue's BF16 staging slice: sp
@@ -682,11 +695,13 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
     }
   } else {  // epilogue warps: group (warp - 2) / 4, TMEM lane quadrant warp % 4
     const int grp = (warp - 2) >> 2;
+    const int No = g.fold ? N / 2 : N;          // output channels
+    const uint32_t fo = g.fold ? (uint32_t)No : 0u;  // column offset of the second half
     const int quad = warp & 3;
     const int m = quad * 32 + lane;  // tile row = y * 8 + x
     const int tid = (threadIdx.x - 64) & 127;
     const uint32_t lanes = (uint32_t)(quad * 32) << 16;
-    float* sbias = sbias0 + grp * (3 * N + Np);  // this group's bias, gamma, beta
+    float* sbias = sbias0 + grp * (3 * No + Np);  // this group's bias, gamma, beta
     float* stg_g = stg + (size_t)grp * g.nbuf * (g.slice_bytes / 4);
     if (pack) {  // both accumulator buffers start at zero (each group its half of the columns)
       for (int c = grp * 16; c < cols; c += 16 * kEpiGroups)
@@ -726,23 +741,23 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
       const int z0 = (tile / g.tiles_y) * TZ;
       if (b != bias_b) {  // this problem's biases (zero when none), then gamma and beta
         epi_sync(grp);
-        for (int c = tid; c < N + Np; c += 128) {
-          const float* bb = c < N ? g.bias : g.bias_p;
-          const long long bs = c < N ? g.bias_bs : g.biasp_bs;
-          sbias[c] = bb ? bb[(long long)b * bs + (c < N ? c : c - N)] : 0.f;
+        for (int c = tid; c < No + Np; c += 128) {
+          const float* bb = c < No ? g.bias : g.bias_p;
+          const long long bs = c < No ? g.bias_bs : g.biasp_bs;
+          sbias[c] = bb ? bb[(long long)b * bs + (c < No ? c : c - No)] : 0.f;
         }
         if (g.ln)
-          for (int c = tid; c < 2 * N; c += 128)
-            sbias[N + Np + c] = g.gamma[(long long)b * g.gamma_bs + c];
+          for (int c = tid; c < 2 * No; c += 128)
+            sbias[No + Np + c] = g.gamma[(long long)b * g.gamma_bs + c];
         epi_sync(grp);
         bias_b = b;
       }
       const int nparts = Np > 0 ? 2 : 1;
       for (int sidx = grp; sidx < nparts * TZ; sidx += kEpiGroups) {
         const int part = sidx / TZ, zz = sidx % TZ;
-        const int nc = part ? Np : N;
+        const int nc = part ? Np : No;
         const int w = nc % 32 == 0 ? 32 : 16;  // channels per stored box
-        const float* bsm = sbias + (part ? N : 0);
+        const float* bsm = sbias + (part ? No : 0);
         const CUtensorMap* om = part ? &tm_outp : &tm_out;
         const bool add = !part && g.accumulate;
         const int col0 =
@@ -752,7 +767,7 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
         if (!ln) {
           for (int c0 = 0; c0 < nc; c0 += 16) {
             uint32_t r[16];
-            tmem_ld16(tmem + lanes + (uint32_t)(col0 + c0), r);
+            tmem_ld16f(tmem + lanes + (uint32_t)(col0 + c0), r, fo);
             float* row = S + (c0 / w) * (128 * w) + m * w;  // box c0 / w, row m
 #pragma unroll
             for (int j = 0; j < 16; j += 4) {
@@ -775,7 +790,7 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
           const bool inside = ox < g.dout.x && oy < g.dout.y && oz < g.dout.z;
           const long long vox = ((long long)oz * g.dout.y + oy) * g.dout.x + ox;
           const long long vo = (long long)b * g.resid_bs + vox * nc;
-          const float* gam = sbias + N + Np;
+          const float* gam = sbias + No + Np;
           const float rs = inside ? g.rstd[(long long)b * g.rstd_bs + vox] : 0.f;
           float* DP = S;
           float* XH = S + 128 * nc;
@@ -784,7 +799,7 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
 #pragma unroll 1
           for (int c0 = 0; c0 < nc; c0 += 16) {
             uint32_t r[16];
-            tmem_ld16(tmem + lanes + (uint32_t)(col0 + c0), r);
+            tmem_ld16f(tmem + lanes + (uint32_t)(col0 + c0), r, fo);
             float d[16], xh[16], a[16];
 #pragma unroll
             for (int j = 0; j < 16; j += 4) {
@@ -870,7 +885,7 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
           float sum = 0.f;
           for (int c0 = 0; c0 < nc; c0 += 16) {
             uint32_t r[16];
-            tmem_ld16(tmem + lanes + (uint32_t)(col0 + c0), r);
+            tmem_ld16f(tmem + lanes + (uint32_t)(col0 + c0), r, fo);
 #pragma unroll
             for (int j = 0; j < 16; ++j) sum += __uint_as_float(r[j]) + bsm[c0 + j];
           }
@@ -878,7 +893,7 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
           float sq = 0.f;
           for (int c0 = 0; c0 < nc; c0 += 16) {
             uint32_t r[16];
-            tmem_ld16(tmem + lanes + (uint32_t)(col0 + c0), r);
+            tmem_ld16f(tmem + lanes + (uint32_t)(col0 + c0), r, fo);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const float d = __uint_as_float(r[j]) + bsm[c0 + j] - mean;
@@ -886,12 +901,12 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
             }
           }
           const float rs = 1.0f / sqrtf(sq * inv_c + kLnEps);
-          const float* gam = sbias + N + Np;
+          const float* gam = sbias + No + Np;
           float* XH = S + 128 * nc;                                       // xhat boxes
           __nv_bfloat16* YB = reinterpret_cast<__nv_bfloat16*>(S + 256 * nc);  // BF16 copy
           for (int c0 = 0; c0 < nc; c0 += 16) {
             uint32_t r[16];
-            tmem_ld16(tmem + lanes + (uint32_t)(col0 + c0), r);
+            tmem_ld16f(tmem + lanes + (uint32_t)(col0 + c0), r, fo);
             float o[16], xh[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
@@ -925,7 +940,8 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
           if (inside) g.rstd[(long long)b * g.rstd_bs + vox] = rs;
         }
         if (pack) {  // zeroed after reading: every MMA of the next tile accumulates
-          for (int c0 = 0; c0 < nc; c0 += 16) tmem_zero16(tmem + lanes + (uint32_t)(col0 + c0));
+          for (int c0 = 0; c0 < (g.fold ? N : nc); c0 += 16)
+            tmem_zero16(tmem + lanes + (uint32_t)(col0 + c0));
           asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         }
         if (sidx + kEpiGroups >= nparts * TZ) {  // the group's last slice of this buffer
@@ -1684,6 +1700,7 @@ struct WTable {
   long long w_off[kWMaxLayers], wf_off[kWMaxLayers], wd_off[kWMaxLayers];
   int ci[kWMaxLayers], ci_real[kWMaxLayers], co[kWMaxLayers], T[kWMaxLayers],
       dgrad[kWMaxLayers], permf[kWMaxLayers], permd[kWMaxLayers];
+  int hlf[kWMaxLayers], hld[kWMaxLayers];  // split rows doubled in N (TcLayer::hlf / hld)
 };
 
 // A block takes one (layer, tap, chunk of 32 output channels): it reads W[o][tap][0..ci) rows
@@ -1741,7 +1758,8 @@ weights_split_bf16_kernel(const float* __restrict__ theta, __nv_bfloat16* __rest
   const int no = co - o0 < kWOc ? co - o0 : kWOc;
   const float* src = theta + (long long)b * Pp + t.w_off[l];
   __nv_bfloat16* base = wb + (long long)b * wstride;
-  const long long frow = t.wf_off[l] + (long long)packed_tap(tap, t.permf[l]) * co * 3 * ci;
+  const bool hf = t.hlf[l] != 0, hd = t.hld[l] != 0;
+  const long long frow = t.wf_off[l] + (long long)packed_tap(tap, t.permf[l]) * co * (hf ? 4 : 3) * ci;
   for (int e = threadIdx.x; e < no * ci; e += blockDim.x) {
     const int ol = e / ci, c = e % ci;
     const float v = c < cr ? src[((long long)(o0 + ol) * T + tap) * cr + c] : 0.f;
@@ -1749,16 +1767,29 @@ weights_split_bf16_kernel(const float* __restrict__ theta, __nv_bfloat16* __rest
     const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
     th[ol][c] = hi;
     tl[ol][c] = lo;
-    __nv_bfloat16* f = base + frow + (long long)(o0 + ol) * 3 * ci;  // [t][co][3 ci]
-    f[c] = hi, f[ci + c] = hi, f[2 * ci + c] = lo;
+    if (hf) {  // [t][2 co][2 ci]: rows o: [hi | hi], rows co + o: [lo | lo]
+      __nv_bfloat16* f = base + frow + (long long)(o0 + ol) * 2 * ci;
+      __nv_bfloat16* g = base + frow + (long long)(co + o0 + ol) * 2 * ci;
+      f[c] = hi, f[ci + c] = hi, g[c] = lo, g[ci + c] = lo;
+    } else {
+      __nv_bfloat16* f = base + frow + (long long)(o0 + ol) * 3 * ci;  // [t][co][3 ci]
+      f[c] = hi, f[ci + c] = hi, f[2 * ci + c] = lo;
+    }
   }
   if (!t.dgrad[l]) return;
   __syncthreads();
-  const long long drow = t.wd_off[l] + (long long)packed_tap(T - 1 - tap, t.permd[l]) * ci * 3 * co;
+  const long long drow =
+      t.wd_off[l] + (long long)packed_tap(T - 1 - tap, t.permd[l]) * ci * (hd ? 4 : 3) * co;
   for (int e = threadIdx.x; e < no * ci; e += blockDim.x) {
     const int ol = e % no, c = e / no;
-    __nv_bfloat16* d = base + drow + (long long)c * 3 * co + o0 + ol;  // [26-t][ci][3 co]
-    d[0] = th[ol][c], d[co] = th[ol][c], d[2 * co] = tl[ol][c];
+    if (hd) {  // [26-t][2 ci][2 co]: rows c: [hi | hi], rows ci + c: [lo | lo]
+      __nv_bfloat16* d = base + drow + (long long)c * 2 * co + o0 + ol;
+      __nv_bfloat16* d2 = base + drow + (long long)(ci + c) * 2 * co + o0 + ol;
+      d[0] = th[ol][c], d[co] = th[ol][c], d2[0] = tl[ol][c], d2[co] = tl[ol][c];
+    } else {
+      __nv_bfloat16* d = base + drow + (long long)c * 3 * co + o0 + ol;  // [26-t][ci][3 co]
+      d[0] = th[ol][c], d[co] = th[ol][c], d[2 * co] = tl[ol][c];
+    }
   }
 }
 
@@ -1840,19 +1871,23 @@ cudaError_t encode_box(CUtensorMap* m, void* base, int B, Dims3 d, int C, int ck
 
 // Channels-last activations with an 8 x 18 x (tz + 2) box: the x-shifted halo of an
 // 8 x 16 x tz tile for the (y, z) offsets of every tap.
-cudaError_t encode_act_halo(CUtensorMap* m, void* base, int B, Dims3 d, int C, int ck, int tz) {
+// (row: the staged row's channel count when the map shows only its first C channels)
+cudaError_t encode_act_halo(CUtensorMap* m, void* base, int B, Dims3 d, int C, int ck, int tz,
+                            int row = 0) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   const cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)d.x, (cuuint64_t)d.y, (cuuint64_t)d.z,
                               (cuuint64_t)B};
-  const cuuint64_t es = 2;
-  const cuuint64_t strides[4] = {C * es, C * es * d.x, C * es * d.x * d.y,
-                                 C * es * d.x * d.y * d.z};
+  const cuuint64_t es = 2, R = (cuuint64_t)(row ? row : C);
+  const cuuint64_t strides[4] = {R * es, R * es * d.x, R * es * d.x * d.y,
+                                 R * es * d.x * d.y * d.z};
   const cuuint32_t box[5] = {(cuuint32_t)ck, 8, 18, (cuuint32_t)(tz + 2), 1};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(ck),
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                        row && row != C ? CU_TENSOR_MAP_L2_PROMOTION_NONE
+                                        : CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -2024,14 +2059,16 @@ cudaError_t launch_tc3(const CUtensorMap& a, const CUtensorMap& w, int cin, int 
                        int mode = 0, const CUtensorMap* wp = nullptr,
                        const CUtensorMap* a2 = nullptr, int np = 0, const float* bias_p = nullptr,
                        float* out_p = nullptr, long long outp_bs = 0,
-                       const Bf16Ln* ln = nullptr) {
+                       const Bf16Ln* ln = nullptr, int fold = 0) {
   Tc3Plan pl = per ? tc3_fixed(cin, n, mode == 1 ? np : 0, ck, tz, pack) : Tc3Plan{};
   if (per && !pl.persistent) return cudaErrorInvalidValue;
+  if (fold && (!per || mode != 0 || n % 32 || (ln && ln->bwd))) return cudaErrorInvalidValue;
+  const int no = fold ? n / 2 : n;  // output channels (n: the MMA width)
   int nbuf = 1;  // staging slices per epilogue group
   if (ln) {  // same tiles and ring, a larger epilogue staging
     const int npm = mode == 1 ? np : 0;
-    const int nst = tc3_ln_stages(pl, n, npm, ln->sp, 1);
-    if (nst < 2 || n > 64) return cudaErrorInvalidValue;
+    const int nst = tc3_ln_stages(pl, no, npm, ln->sp, 1);
+    if (nst < 2 || no > 64) return cudaErrorInvalidValue;
     pl.nst = nst;
   }
   if (pl.persistent) {
@@ -2042,20 +2079,21 @@ cudaError_t launch_tc3(const CUtensorMap& a, const CUtensorMap& w, int cin, int 
     g.tiles_x = (int)ceil_div(dout.x, 8), g.tiles_y = (int)ceil_div(dout.y, 16);
     g.tiles_z = (int)ceil_div(dout.z, tz);
     g.B = B, g.accumulate = acc, g.nst = pl.nst, g.mode = mode, g.pack = pl.pack ? 1 : 0;
+    g.fold = fold;
     g.stage_bytes = (uint32_t)pl.stage;
     g.ring_bytes = (uint32_t)((pl.nst * pl.stage + 1023) / 1024 * 1024);
     const int npm = mode == 1 ? np : 0;
     const int lsp = ln ? ln->sp : 0;
-    g.slice_bytes = (uint32_t)tc3p_slice(n, npm, lsp);
+    g.slice_bytes = (uint32_t)tc3p_slice(no, npm, lsp);
     g.nbuf = nbuf;
     g.out_bs = out_bs, g.bias_bs = bias_bs, g.outp_bs = outp_bs, g.biasp_bs = bias_bs;
     const long long total = (long long)g.tiles_x * g.tiles_y * g.tiles_z * B;
     const int grid = (int)std::min<long long>(total, sm_count());
     // (the staging term's slack covers the kernel's 1024-byte alignment of its base)
-    const size_t sm = (size_t)g.ring_bytes + tc3p_staging(n, npm, lsp, nbuf);
+    const size_t sm = (size_t)g.ring_bytes + tc3p_staging(no, npm, lsp, nbuf);
     CUtensorMap mo{}, mop, mxh, myb;
     // (the LayerNorm backward stores its FP32 output only when asked to)
-    cudaError_t e = out ? encode_out(&mo, out, B, dout, n, n % 32 == 0 ? 32 : 16, out_bs)
+    cudaError_t e = out ? encode_out(&mo, out, B, dout, no, no % 32 == 0 ? 32 : 16, out_bs)
                         : cudaSuccess;
     if (e == cudaSuccess && mode == 1)
       e = encode_out(&mop, out_p, B, dout, np, np % 32 == 0 ? 32 : 16, outp_bs);
@@ -2073,10 +2111,10 @@ cudaError_t launch_tc3(const CUtensorMap& a, const CUtensorMap& w, int cin, int 
         g.aout = ln->aout, g.xh_in = ln->xhat, g.part = ln->part;
         g.rows_b = (long long)g.tiles_x * g.tiles_y * g.tiles_z * kEpiGroups;
       } else if (e == cudaSuccess) {
-        e = encode_out(&mxh, ln->xhat, B, dout, n, n % 32 == 0 ? 32 : 16, out_bs);
+        e = encode_out(&mxh, ln->xhat, B, dout, no, no % 32 == 0 ? 32 : 16, out_bs);
       }
       if (e == cudaSuccess && ln->ybf)
-        e = encode_out_bf16(&myb, ln->ybf, B, dout, ln->sp * n, n, dout.count() * ln->sp * n);
+        e = encode_out_bf16(&myb, ln->ybf, B, dout, ln->sp * no, no, dout.count() * ln->sp * no);
     }
     if (e != cudaSuccess) return e;
     const CUtensorMap& mp = wp ? *wp : w;
@@ -2217,12 +2255,22 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
   L.w_off = w_off;
   L.kf = bf.sp * ci;
   L.kd = bf.sp * co;
+  L.kf3 = L.kf, L.nf3 = co, L.kd3 = L.kd, L.nd3 = ci;
   L.dgrad = (s == 1 || k == 3) && bf16_conv_supported(co, ci, k);
   if (k == 3 && s == 1) {
-    const Tc3Plan pf = tc3_plan(L.kf, co, 0, L.dout.z);
+    const bool hl = bf.sp == 3 && ci == 16 && co == 16;  // [hi | lo] rows, doubled weights
+    Tc3Plan pf = hl ? tc3_plan(2 * ci, 2 * co, 0, L.dout.z) : Tc3Plan{};
+    if (pf.persistent)
+      L.hlf = true, L.kf3 = 2 * ci, L.nf3 = 2 * co;
+    else
+      pf = tc3_plan(L.kf, co, 0, L.dout.z);
     L.ck3f = pf.ck, L.tz3f = pf.tz, L.pack3f = pf.pack, L.per3f = pf.persistent;
     if (L.dgrad) {
-      const Tc3Plan pd = tc3_plan(L.kd, ci, 0, L.din.z);
+      Tc3Plan pd = hl ? tc3_plan(2 * co, 2 * ci, 0, L.din.z) : Tc3Plan{};
+      if (pd.persistent)
+        L.hld = true, L.kd3 = 2 * co, L.nd3 = 2 * ci;
+      else
+        pd = tc3_plan(L.kd, ci, 0, L.din.z);
       L.ck3d = pd.ck, L.tz3d = pd.tz, L.pack3d = pd.pack, L.per3d = pd.persistent;
     }
   }
@@ -2232,11 +2280,12 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
   if (k == 3 && s == 2 && (ci == 16 || ci == 32 || ci == 64) && co % 16 == 0 && co <= 256)
     L.wgrad = L.wgs2 = true;
   const long long n = (long long)co * k * k * k * ci * bf.sp;
+  const long long n4 = (long long)co * k * k * k * ci * 4;  // the doubled [2 co][2 ci] rows
   L.wf_off = bf.wstride;
-  bf.wstride += (n + 63) / 64 * 64;
+  bf.wstride += ((L.hlf ? n4 : n) + 63) / 64 * 64;
   if (L.dgrad) {
     L.wd_off = bf.wstride;
-    bf.wstride += (n + 63) / 64 * 64;
+    bf.wstride += ((L.hld ? n4 : n) + 63) / 64 * 64;
   }
   bf.layers.push_back(L);
   return (int)bf.layers.size() - 1;
@@ -2255,16 +2304,21 @@ int bf16_add_input_layer(Bf16Net& bf, int ci_real, int co, Dims3 din, long long 
   L.w_off = w_off;
   L.kf = 16 * bf.sp;
   L.kd = co * bf.sp;
+  L.kf3 = L.kf, L.nf3 = co, L.kd3 = L.kd, L.nd3 = 16;
   L.input_layer = true;
   if (bf16_conv_supported(16, co, 3)) {
-    const Tc3Plan pf = tc3_plan(L.kf, co, 0, din.z);
+    Tc3Plan pf = bf.sp == 3 && co == 16 ? tc3_plan(32, 2 * co, 0, din.z) : Tc3Plan{};
+    if (pf.persistent)
+      L.hlf = true, L.kf3 = 32, L.nf3 = 2 * co;
+    else
+      pf = tc3_plan(L.kf, co, 0, din.z);
     L.ck3f = pf.ck, L.tz3f = pf.tz, L.pack3f = pf.pack, L.per3f = pf.persistent;
   }
   L.wg_tz = wg3_tz_fit(L);
   L.wgrad = L.wg3 = wg3_geom(L, 1).nst > 0;
   if (!L.ck3f || !L.wg3) return -1;
   L.wf_off = bf.wstride;
-  bf.wstride += ((long long)co * 27 * L.kf + 63) / 64 * 64;
+  bf.wstride += ((long long)(L.hlf ? 2 * co : co) * 27 * (L.hlf ? 32 : L.kf) + 63) / 64 * 64;
   bf.zcount = din.count() * L.kf;
   bf.layers.push_back(L);
   return (int)bf.layers.size() - 1;
@@ -2343,18 +2397,19 @@ cudaError_t encode_halo_maps(TcLayer& L, const Bf16Net& bf, int B, int dir) {
   const int T = L.k * L.k * L.k;
   if (dir == 0) {
     __nv_bfloat16* src = L.input_layer ? bf.zbf : L.xin;
-    cudaError_t e = encode_act_halo(&L.act_f3, src, B, L.din, L.kf, L.ck3f, L.tz3f);
+    cudaError_t e = encode_act_halo(&L.act_f3, src, B, L.din, L.kf3, L.ck3f, L.tz3f, L.kf);
     if (e == cudaSuccess)
-      e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, L.kf, T, L.co, L.ck3f, 9, 3);
+      e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, L.kf3, T, L.nf3, L.ck3f, 9, 3);
     if (e == cudaSuccess && L.projf) {
       const TcLayer& P = bf.layers[L.proj];
       e = encode_w(&L.pw_f, bf.wbuf + P.wf_off, B, bf.wstride, P.kf, 1, P.co, L.ck3f, 1, 1);
     }
     return e;
   }
-  cudaError_t e = encode_act_halo(&L.act_d3, dy_buf(bf, L), B, L.dout, L.kd, L.ck3d, L.tz3d);
+  cudaError_t e =
+      encode_act_halo(&L.act_d3, dy_buf(bf, L), B, L.dout, L.kd3, L.ck3d, L.tz3d, L.kd);
   if (e == cudaSuccess)
-    e = encode_w(&L.w_d3, bf.wbuf + L.wd_off, B, bf.wstride, L.kd, T, L.ci, L.ck3d, 9, 3);
+    e = encode_w(&L.w_d3, bf.wbuf + L.wd_off, B, bf.wstride, L.kd3, T, L.nd3, L.ck3d, 9, 3);
   if (e == cudaSuccess && L.projd) {
     const TcLayer& P = bf.layers[L.proj];
     e = encode_w(&L.pw_d, bf.wbuf + P.wd_off, B, bf.wstride, P.kd, 1, P.ci, L.ck3d, 1, 1);
@@ -2367,9 +2422,9 @@ cudaError_t bf16_finalize(Bf16Net& bf, int B) {
   for (TcLayer& L : bf.layers) {
     const int T = L.k * L.k * L.k;
     if (L.input_layer) {  // halo-box forward and weight gradient over zbf only
-      cudaError_t e = encode_act_halo(&L.act_f3, bf.zbf, B, L.din, L.kf, L.ck3f, L.tz3f);
+      cudaError_t e = encode_act_halo(&L.act_f3, bf.zbf, B, L.din, L.kf3, L.ck3f, L.tz3f, L.kf);
       if (e == cudaSuccess)
-        e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, L.kf, T, L.co, L.ck3f, 9, 3);
+        e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, L.kf3, T, L.nf3, L.ck3f, 9, 3);
       for (int blk = 0; blk < (bf.sp > 1 ? 2 : 1) && e == cudaSuccess; ++blk)
         e = encode_wgrad_maps(L, bf, B, blk);
       if (e != cudaSuccess) return e;
@@ -2388,14 +2443,14 @@ cudaError_t bf16_finalize(Bf16Net& bf, int B) {
     for (int blk = 0; L.wgrad && blk < (bf.sp > 1 ? 2 : 1) && e == cudaSuccess; ++blk)
       e = encode_wgrad_maps(L, bf, B, blk);
     if (e == cudaSuccess && L.ck3f) {
-      e = encode_act_halo(&L.act_f3, L.xin, B, L.din, L.kf, L.ck3f, L.tz3f);
+      e = encode_act_halo(&L.act_f3, L.xin, B, L.din, L.kf3, L.ck3f, L.tz3f, L.kf);
       if (e == cudaSuccess)
-        e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, L.kf, T, L.co, L.ck3f, 9, 3);
+        e = encode_w(&L.w_f3, bf.wbuf + L.wf_off, B, bf.wstride, L.kf3, T, L.nf3, L.ck3f, 9, 3);
     }
     if (e == cudaSuccess && L.ck3d) {
-      e = encode_act_halo(&L.act_d3, dy_buf(bf, L), B, L.dout, L.kd, L.ck3d, L.tz3d);
+      e = encode_act_halo(&L.act_d3, dy_buf(bf, L), B, L.dout, L.kd3, L.ck3d, L.tz3d, L.kd);
       if (e == cudaSuccess)
-        e = encode_w(&L.w_d3, bf.wbuf + L.wd_off, B, bf.wstride, L.kd, T, L.ci, L.ck3d, 9, 3);
+        e = encode_w(&L.w_d3, bf.wbuf + L.wd_off, B, bf.wstride, L.kd3, T, L.nd3, L.ck3d, 9, 3);
     }
     if (e == cudaSuccess && L.projf) {  // W_p [1][co][kf] in chunks of this layer's ck
       const TcLayer& P = bf.layers[L.proj];
@@ -2847,6 +2902,7 @@ cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long lo
       t.ci[i] = L.ci, t.ci_real[i] = L.ci_real, t.co[i] = L.co, t.T[i] = T;
       t.dgrad[i] = L.dgrad ? 1 : 0;
       t.permf[i] = L.pack3f ? 1 : 0, t.permd[i] = L.pack3d ? 1 : 0;
+      t.hlf[i] = L.hlf ? 1 : 0, t.hld[i] = L.hld ? 1 : 0;
     }
     t.blk0[t.nl] = blk;
     weights_split_bf16_kernel<<<dim3((unsigned)blk, B), 256, 0, stream>>>(theta, bf.wbuf, Pp,
@@ -2868,6 +2924,7 @@ cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long lo
       t.ci[i] = L.ci, t.ci_real[i] = L.ci_real, t.co[i] = L.co, t.T[i] = T;
       t.dgrad[i] = L.dgrad ? 1 : 0;
       t.permf[i] = L.pack3f ? 1 : 0, t.permd[i] = L.pack3d ? 1 : 0;
+      t.hlf[i] = L.hlf ? 1 : 0, t.hld[i] = L.hld ? 1 : 0;
     }
     t.blk0[t.nl] = blk;
     weights_all_bf16_kernel<<<dim3((unsigned)blk, B), 256, 0, stream>>>(theta, bf.wbuf, Pp,
@@ -2927,7 +2984,7 @@ int bf16_fuse_proj(Bf16Net& bf, int la, int lp) {
     return 0;
   A.proj = lp;
   if (A.ck3f) {
-    const Tc3Plan pf = tc3_plan(A.kf, A.co, P.co, A.dout.z);
+    const Tc3Plan pf = A.hlf ? Tc3Plan{} : tc3_plan(A.kf3, A.nf3, P.co, A.dout.z);
     if (pf.persistent)
       A.projf = true, A.ck3f = pf.ck, A.tz3f = pf.tz, A.pack3f = pf.pack, A.per3f = true;
   }
@@ -2985,7 +3042,8 @@ cudaError_t bf16_autotune(Bf16Net& bf, int B, float* scratch, const float* bias,
     for (int dir = 0; dir < 2 && e == cudaSuccess; ++dir) {
       const bool on = dir == 0 ? L.ck3f && L.per3f : L.ck3d && L.per3d;
       if (!on) continue;
-      const int cin = dir ? L.kd : L.kf, n = dir ? L.ci : L.co;
+      const int cin = dir ? L.kd3 : L.kf3, n = dir ? L.nd3 : L.nf3;
+      const int fold = dir ? (L.hld ? 1 : 0) : (L.hlf ? 1 : 0), no = fold ? n / 2 : n;
       const int np = dir == 0 && L.projf ? bf.layers[L.proj].co : 0;
       const int mode = dir == 0 ? (L.projf ? 1 : 0) : (L.projd ? 2 : 0);
       const Dims3 d = dir ? L.din : L.dout;
@@ -3010,12 +3068,13 @@ cudaError_t bf16_autotune(Bf16Net& bf, int B, float* scratch, const float* bias,
       auto launch = [&](const Tc3Plan& c) {
         if (dir == 0)
           return launch_tc3(L.act_f3, L.w_f3, cin, c.ck, c.tz, c.pack, true, bias, scratch, d, n,
-                            B, d.count() * n, 0, 0, bf.err, st, mode,
+                            B, d.count() * no, 0, 0, bf.err, st, mode,
                             mode == 1 ? &L.pw_f : nullptr, nullptr, np, bias, scratch,
-                            d.count() * np);
+                            d.count() * np, nullptr, fold);
         return launch_tc3(L.act_d3, L.w_d3, cin, c.ck, c.tz, c.pack, true, nullptr, scratch, d,
-                          n, B, d.count() * n, 0, 0, bf.err, st, mode,
-                          mode == 2 ? &L.pw_d : nullptr, mode == 2 ? &L.pa_d : nullptr);
+                          n, B, d.count() * no, 0, 0, bf.err, st, mode,
+                          mode == 2 ? &L.pw_d : nullptr, mode == 2 ? &L.pa_d : nullptr, 0,
+                          nullptr, nullptr, 0, nullptr, fold);
       };
       for (const Tc3Plan& c : tc3_candidates(cin, n, np)) {
         ck = c.ck, tz = c.tz, pack = c.pack;
@@ -3058,7 +3117,7 @@ cudaError_t bf16_apply_plan(Bf16Net& bf, int B, const long long* rows, int n_row
       if ((t[0] != 0) != on) return cudaErrorInvalidValue;
       if (!on) continue;
       const int np = dir == 0 && L.projf ? bf.layers[L.proj].co : 0;
-      const Tc3Plan p = tc3_fixed(dir ? L.kd : L.kf, dir ? L.ci : L.co, np, (int)t[2], (int)t[3],
+      const Tc3Plan p = tc3_fixed(dir ? L.kd3 : L.kf3, dir ? L.nd3 : L.nf3, np, (int)t[2], (int)t[3],
                                   t[1] != 0);
       if (!p.persistent) return cudaErrorInvalidValue;
     }
@@ -3091,7 +3150,7 @@ long long bf16_tune_scratch_floats(const Bf16Net& bf, int B) {
 bool bf16_fwd_ln_ok(const Bf16Net& bf, int layer, int np, int sp) {
   const TcLayer& L = bf.layers[layer];
   if (!L.ck3f || !L.per3f || L.co > 64 || (np > 0 && !L.projf)) return false;
-  const Tc3Plan pl = tc3_fixed(L.kf, L.co, np, L.ck3f, L.tz3f, L.pack3f);
+  const Tc3Plan pl = tc3_fixed(L.kf3, L.nf3, np, L.ck3f, L.tz3f, L.pack3f);
   return tc3_ln_stages(pl, L.co, np, sp, 1) >= 2;
 }
 
@@ -3108,9 +3167,10 @@ cudaError_t bf16_conv_fwd_ln(Bf16Net& bf, int layer, const float* x, const float
   Bf16Ln l = ln;
   l.sp = bf.sp;
   const long long obs = L.dout.count() * L.co;
-  return launch_tc3(L.act_f3, L.w_f3, L.kf, L.ck3f, L.tz3f, L.pack3f, L.per3f, bias, y, L.dout, L.co, B, obs,
-                    bias_bs, 0, bf.err, stream, proj ? 1 : 0, proj ? &L.pw_f : nullptr, nullptr,
-                    proj ? L.co : 0, bias_p, y_p, proj ? obs : 0, &l);
+  return launch_tc3(L.act_f3, L.w_f3, L.kf3, L.ck3f, L.tz3f, L.pack3f, L.per3f, bias, y, L.dout,
+                    L.nf3, B, obs, bias_bs, 0, bf.err, stream, proj ? 1 : 0,
+                    proj ? &L.pw_f : nullptr, nullptr, proj ? L.co : 0, bias_p, y_p,
+                    proj ? obs : 0, &l, L.hlf ? 1 : 0);
 }
 
 cudaError_t bf16_stage_input(Bf16Net& bf, int layer, const float* z, int B, cudaStream_t stream) {
@@ -3135,8 +3195,9 @@ cudaError_t bf16_conv_fwd(Bf16Net& bf, int layer, const float* x, const float* b
                       : stage_rows(x, L.xin, (long long)B * L.din.count(), L.ci, bf.sp, stream);
   if (e != cudaSuccess) return e;
   if (L.ck3f)
-    return launch_tc3(L.act_f3, L.w_f3, L.kf, L.ck3f, L.tz3f, L.pack3f, L.per3f, bias, y, L.dout, L.co, B,
-                      L.dout.count() * L.co, bias_bs, 0, bf.err, stream);
+    return launch_tc3(L.act_f3, L.w_f3, L.kf3, L.ck3f, L.tz3f, L.pack3f, L.per3f, bias, y,
+                      L.dout, L.nf3, B, L.dout.count() * L.co, bias_bs, 0, bf.err, stream, 0,
+                      nullptr, nullptr, 0, nullptr, nullptr, 0, nullptr, L.hlf ? 1 : 0);
   const TapPlan plan = conv_plan(L.k, L.s);
   return launch_tc(L.act_f, L.w_f, plan, 1, L.kf, bias, y, L.dout, L.dout, L.co, B,
                    L.dout.count() * L.co, bias_bs, 0, bf.err, stream);
@@ -3156,16 +3217,18 @@ cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, 
                      L.din.count() * L.ci, 0, accumulate, bf.err, stream);
   }
   if (L.ck3d)
-    return launch_tc3(L.act_d3, L.w_d3, L.kd, L.ck3d, L.tz3d, L.pack3d, L.per3d, nullptr, dx, L.din, L.ci, B,
-                      L.din.count() * L.ci, 0, accumulate, bf.err, stream);
+    return launch_tc3(L.act_d3, L.w_d3, L.kd3, L.ck3d, L.tz3d, L.pack3d, L.per3d, nullptr, dx,
+                      L.din, L.nd3, B, L.din.count() * L.ci, 0, accumulate, bf.err, stream, 0,
+                      nullptr, nullptr, 0, nullptr, nullptr, 0, nullptr, L.hld ? 1 : 0);
   return launch_tc(L.act_d, L.w_d, conv_plan(L.k, 1), 1, L.kd, nullptr, dx, L.din, L.din, L.ci,
                    B, L.din.count() * L.ci, 0, accumulate, bf.err, stream);
 }
 
 bool bf16_dgrad_ln_ok(const Bf16Net& bf, int layer, int sp) {
   const TcLayer& L = bf.layers[layer];
-  if (!L.dgrad || L.s != 1 || !L.ck3d || !L.per3d || L.projd || L.ci > 64) return false;
-  const Tc3Plan pl = tc3_fixed(L.kd, L.ci, 0, L.ck3d, L.tz3d, L.pack3d);
+  if (!L.dgrad || L.s != 1 || !L.ck3d || !L.per3d || L.projd || L.ci > 64 || L.hld)
+    return false;
+  const Tc3Plan pl = tc3_fixed(L.kd3, L.nd3, 0, L.ck3d, L.tz3d, L.pack3d);
   return tc3_ln_stages(pl, L.ci, 0, sp, 1) >= 2;
 }
 
@@ -3185,8 +3248,8 @@ cudaError_t bf16_conv_dgrad_ln(Bf16Net& bf, int layer, const float* dy, float* d
   if (e != cudaSuccess) return e;
   Bf16Ln l = ln;
   l.sp = bf.sp;
-  return launch_tc3(L.act_d3, L.w_d3, L.kd, L.ck3d, L.tz3d, L.pack3d, L.per3d, nullptr, dz_out,
-                    L.din, L.ci, B, L.din.count() * L.ci, 0, 0, bf.err, stream, 0, nullptr,
+  return launch_tc3(L.act_d3, L.w_d3, L.kd3, L.ck3d, L.tz3d, L.pack3d, L.per3d, nullptr, dz_out,
+                    L.din, L.nd3, B, L.din.count() * L.ci, 0, 0, bf.err, stream, 0, nullptr,
                     nullptr, 0, nullptr, nullptr, 0, &l);
 }
 

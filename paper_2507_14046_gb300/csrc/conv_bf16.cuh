@@ -25,6 +25,13 @@ struct TcLayer {
   CUtensorMap wgy[2], wgx[2], wgp[2];
   CUtensorMap wgqy, wgqx;   // split precision in one pass: dy and x as [hi | lo] rows
   int ci = 0, co = 0, k = 3, s = 1;
+  // The halo-form (persistent kernel) view of the forward and data gradient: K channels and
+  // MMA width N.  Normally kf, co and kd, ci; with hlf / hld (split precision, a 16 -> 16
+  // layer) the kernel reads the first two blocks [hi | lo] of each staged row (K = 2 ci)
+  // against weights doubled in N ([w_hi; w_lo] rows, N = 2 co) and its epilogue adds the two
+  // column halves: x_hi w_hi + x_lo w_hi + x_hi w_lo + x_lo w_lo.
+  int kf3 = 0, nf3 = 0, kd3 = 0, nd3 = 0;
+  bool hlf = false, hld = false;
   int kf = 0, kd = 0;             // K channels of the forward and data-gradient operands:
                                   // ci and co times the operand blocks (Bf16Net::sp)
   Dims3 din{}, dout{};
