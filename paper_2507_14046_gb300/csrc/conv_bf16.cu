@@ -703,6 +703,17 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
     const uint32_t lanes = (uint32_t)(quad * 32) << 16;
     float* sbias = sbias0 + grp * (3 * No + Np);  // this group's bias, gamma, beta
     float* stg_g = stg + (size_t)grp * g.nbuf * (g.slice_bytes / 4);
+    // Before a slice's first write into the staging: the group's earlier stores have finished
+    // reading it (the wait sits here, not after each store, so it overlaps the TMEM passes).
+    auto stage_free = [&]() {
+      if (tid == 0) {
+        if (g.nbuf > 1)
+          bulk_wait_read<1>();
+        else
+          bulk_wait_read<0>();
+      }
+      epi_sync(grp);
+    };
     if (pack) {  // both accumulator buffers start at zero (each group its half of the columns)
       for (int c = grp * 16; c < cols; c += 16 * kEpiGroups)
         tmem_zero16(tmem + lanes + (uint32_t)c);
@@ -765,6 +776,7 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
         float* S = stg_g + (g.nbuf > 1 ? slice & 1 : 0) * (g.slice_bytes / 4);
         const bool ln = g.ln && !part;
         if (!ln) {
+          stage_free();
           for (int c0 = 0; c0 < nc; c0 += 16) {
             uint32_t r[16];
             tmem_ld16f(tmem + lanes + (uint32_t)(col0 + c0), r, fo);
@@ -796,6 +808,7 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
           float* XH = S + 128 * nc;
           __nv_bfloat16* YB = reinterpret_cast<__nv_bfloat16*>(S + 256 * nc);
           float s1 = 0.f, s2 = 0.f;
+          stage_free();
 #pragma unroll 1
           for (int c0 = 0; c0 < nc; c0 += 16) {
             uint32_t r[16];
@@ -902,6 +915,7 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
           }
           const float rs = 1.0f / sqrtf(sq * inv_c + kLnEps);
           const float* gam = sbias + No + Np;
+          stage_free();
           float* XH = S + 128 * nc;                                       // xhat boxes
           __nv_bfloat16* YB = reinterpret_cast<__nv_bfloat16*>(S + 256 * nc);  // BF16 copy
           for (int c0 = 0; c0 < nc; c0 += 16) {
@@ -966,23 +980,18 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
                                k * nc, x0, y0, z0 + zz, b, false);
             }
           }
-          bulk_commit();
-          if (g.nbuf > 1)
-            bulk_wait_read<1>();  // the group's other staging slice is free again
-          else
-            bulk_wait_read<0>();  // the group's one staging slice is free again
+          bulk_commit();  // (read back before the group next writes this slice: stage_free)
         }
         ++slice;
-        epi_sync(grp);
       }
       if (grp >= nparts * TZ) {  // a group without a slice of this tile still hands it back
         tc_fence_before();
         mbar_arrive(smem_u32(&tempty[buf]));
       }
       if (g.ln == 2) {  // the group's row of this tile: the four warps' sums in order
-        // (the staging slice is free: every store of the group's slices has read it)
         float* W = stg_g;
         const int nk = N / 16;
+        stage_free();
         const float acc4[4] = {lnacc0, lnacc1, lnacc2, lnacc3};
 #pragma unroll
         for (int k = 0; k < 4; ++k)
