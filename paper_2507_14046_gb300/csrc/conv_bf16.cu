@@ -393,6 +393,7 @@ struct P3Args {
   Dims3 dout;
   int N, Np, nchunks, tiles_x, tiles_y, tiles_z, B, accumulate, nst, mode, pack;
   int fold;  // N = 2 outputs: output channel c is D[c] + D[N / 2 + c] (split rows, mode 0)
+  int split_c;  // > 0: output channels from split_c on go to tm_outp (at channel - split_c)
   uint32_t ring_bytes, stage_bytes;
   uint32_t slice_bytes;  // one epilogue staging slice (128 rows of FP32 outputs, and with the
                          // LayerNorm also xhat and the BF16 copy); per epilogue group, nbuf of
@@ -967,8 +968,11 @@ conv_tc3p_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant
         if (tid == 0) {
           if (z0 + zz < g.dout.z) {
             if (!(ln && g.ln == 2) || g.out)  // the backward's FP32 dz only when asked for
-              for (int k = 0; k < nc / w; ++k)
-                tma_store_5d(om, smem_u32(S + k * (128 * w)), k * w, x0, y0, z0 + zz, b, add);
+              for (int k = 0; k < nc / w; ++k) {
+                const bool second = !part && g.split_c > 0 && k * w >= g.split_c;
+                tma_store_5d(second ? &tm_outp : om, smem_u32(S + k * (128 * w)),
+                             second ? k * w - g.split_c : k * w, x0, y0, z0 + zz, b, add);
+              }
             if (ln) {
               if (g.ln == 1)
                 for (int k = 0; k < nc / w; ++k)
@@ -2068,11 +2072,16 @@ cudaError_t launch_tc3(const CUtensorMap& a, const CUtensorMap& w, int cin, int 
                        int mode = 0, const CUtensorMap* wp = nullptr,
                        const CUtensorMap* a2 = nullptr, int np = 0, const float* bias_p = nullptr,
                        float* out_p = nullptr, long long outp_bs = 0,
-                       const Bf16Ln* ln = nullptr, int fold = 0) {
+                       const Bf16Ln* ln = nullptr, int fold = 0, float* out2 = nullptr,
+                       int split_c = 0) {
   Tc3Plan pl = per ? tc3_fixed(cin, n, mode == 1 ? np : 0, ck, tz, pack) : Tc3Plan{};
   if (per && !pl.persistent) return cudaErrorInvalidValue;
   if (fold && (!per || mode != 0 || n % 32 || (ln && ln->bwd))) return cudaErrorInvalidValue;
   const int no = fold ? n / 2 : n;  // output channels (n: the MMA width)
+  const int wbox = no % 32 == 0 ? 32 : 16;  // channels per stored box (the kernel's choice)
+  if (split_c && (!per || mode == 1 || ln || !out2 || split_c % wbox || (no - split_c) <= 0 ||
+                  (no - split_c) % wbox))
+    return cudaErrorInvalidValue;
   int nbuf = 1;  // staging slices per epilogue group
   if (ln) {  // same tiles and ring, a larger epilogue staging
     const int npm = mode == 1 ? np : 0;
@@ -2089,6 +2098,7 @@ cudaError_t launch_tc3(const CUtensorMap& a, const CUtensorMap& w, int cin, int 
     g.tiles_z = (int)ceil_div(dout.z, tz);
     g.B = B, g.accumulate = acc, g.nst = pl.nst, g.mode = mode, g.pack = pl.pack ? 1 : 0;
     g.fold = fold;
+    g.split_c = split_c;
     g.stage_bytes = (uint32_t)pl.stage;
     g.ring_bytes = (uint32_t)((pl.nst * pl.stage + 1023) / 1024 * 1024);
     const int npm = mode == 1 ? np : 0;
@@ -2102,12 +2112,18 @@ cudaError_t launch_tc3(const CUtensorMap& a, const CUtensorMap& w, int cin, int 
     const size_t sm = (size_t)g.ring_bytes + tc3p_staging(no, npm, lsp, nbuf);
     CUtensorMap mo{}, mop, mxh, myb;
     // (the LayerNorm backward stores its FP32 output only when asked to)
-    cudaError_t e = out ? encode_out(&mo, out, B, dout, no, no % 32 == 0 ? 32 : 16, out_bs)
-                        : cudaSuccess;
-    if (e == cudaSuccess && mode == 1)
-      e = encode_out(&mop, out_p, B, dout, np, np % 32 == 0 ? 32 : 16, outp_bs);
-    else
-      mop = mo;
+    cudaError_t e = cudaSuccess;
+    if (split_c) {  // two output tensors of split_c and no - split_c channels
+      e = encode_out(&mo, out, B, dout, split_c, wbox, dout.count() * split_c);
+      if (e == cudaSuccess)
+        e = encode_out(&mop, out2, B, dout, no - split_c, wbox, dout.count() * (no - split_c));
+    } else {
+      if (out) e = encode_out(&mo, out, B, dout, no, wbox, out_bs);
+      if (e == cudaSuccess && mode == 1)
+        e = encode_out(&mop, out_p, B, dout, np, np % 32 == 0 ? 32 : 16, outp_bs);
+      else
+        mop = mo;
+    }
     mxh = mo, myb = mo;
     if (ln) {
       g.ln = ln->bwd ? 2 : 1, g.act = ln->act, g.sp = ln->sp, g.ybf = ln->ybf ? 1 : 0;
@@ -3018,7 +3034,7 @@ cudaError_t bf16_conv_fwd_proj(Bf16Net& bf, int la, const float* x, const float*
 
 cudaError_t bf16_conv_dgrad_proj(Bf16Net& bf, int la, const float* dz_a, const float* dz_p,
                                  float* dx, int B, cudaStream_t stream, bool dza_staged,
-                                 bool dzp_staged) {
+                                 bool dzp_staged, float* dx2, int split_c) {
   const TcLayer& L = bf.layers[la];
   if (!L.projd) return cudaErrorInvalidValue;
   const long long nv = (long long)B * L.dout.count();
@@ -3026,7 +3042,8 @@ cudaError_t bf16_conv_dgrad_proj(Bf16Net& bf, int la, const float* dz_a, const f
   if (e == cudaSuccess && !dzp_staged) e = stage_rows(dz_p, bf.pbf, nv, L.co, bf.sp, stream);
   if (e != cudaSuccess) return e;
   return launch_tc3(L.act_d3, L.w_d3, L.kd, L.ck3d, L.tz3d, L.pack3d, L.per3d, nullptr, dx, L.din, L.ci, B,
-                    L.din.count() * L.ci, 0, 0, bf.err, stream, 2, &L.pw_d, &L.pa_d);
+                    L.din.count() * L.ci, 0, 0, bf.err, stream, 2, &L.pw_d, &L.pa_d, 0, nullptr,
+                    nullptr, 0, nullptr, 0, dx2, split_c);
 }
 
 namespace {

@@ -103,9 +103,11 @@ cudaError_t bf16_conv_fwd_proj(Bf16Net& bf, int la, const float* x, const float*
                                long long bias_bs, cudaStream_t stream, bool x_staged = false);
 // dx = conv_a^T(dz_a) + W_p^T dz_p in one launch (layer la with projd); dz_a is staged into
 // bf.ybf and dz_p into bf.pbf unless their producer already wrote them there.
+// With dx2 and split_c > 0, dx is stored as two tensors: channels [0, split_c) into dx
+// ([B][voxels][split_c]) and the rest into dx2 ([B][voxels][ci - split_c]).
 cudaError_t bf16_conv_dgrad_proj(Bf16Net& bf, int la, const float* dz_a, const float* dz_p,
                                  float* dx, int B, cudaStream_t stream, bool dza_staged = false,
-                                 bool dzp_staged = false);
+                                 bool dzp_staged = false, float* dx2 = nullptr, int split_c = 0);
 // Reserve the BF16 buffers in the arena (base == nullptr: size only).
 void bf16_layout(Bf16Net& bf, char* base, size_t& used, int B, long long max_act);
 // Encode the TMA descriptors once the buffers have addresses.

@@ -71,8 +71,9 @@ ln_fwd_kernel(const float* __restrict__ z, const float* __restrict__ gamma,
   if (lane == 0) rstd[(long long)b * nvox + vox] = rs;
 }
 
-// dpre = dy * act'(.) (mask from the stored activation output), dz = LN backward of dpre,
-// dt = dpre (optional); per-block partial sums of (dgamma, dbeta).
+// dpre = dy * act'(.) (mask from the stored activation output), dz = LN backward of dpre
+// (FP32 into dz and/or BF16 staging into dzbf; either may be null), dt = dpre (optional);
+// per-block partial sums of (dgamma, dbeta).
 template <int GP>
 __global__ void __launch_bounds__(256)
 ln_bwd_kernel(const float* __restrict__ dy, const float* __restrict__ act_out,
@@ -123,7 +124,7 @@ ln_bwd_kernel(const float* __restrict__ dy, const float* __restrict__ act_out,
       o.y = rs * (dx.y - s1 - xh.y * s2);
       o.z = rs * (dx.z - s1 - xh.z * s2);
       o.w = rs * (dx.w - s1 - xh.w * s2);
-      *reinterpret_cast<float4*>(dz + off + vox * C + c) = o;
+      if (dz) *reinterpret_cast<float4*>(dz + off + vox * C + c) = o;
       if (dzbf) stage_bf16x4(dzbf + (off + vox * C) * sp, C, c, o, sp);
       ag[0] += d.x * xh.x;
       ag[1] += d.y * xh.y;

@@ -580,8 +580,14 @@ struct Launcher {
     __nv_bfloat16* dzbf =
         tc_dy_consumer(dz_consumer) ? bf16_dy_buffer(c->bf, dz_consumer->tc) : nullptr;
     __nv_bfloat16* dtbf = dt && dt_owner && c->bf.pbf ? c->bf.pbf : nullptr;
-    ok(layernorm_act_bwd_f32(dy, aout, xh, rs, c->theta + L.g_off, dz, dt, c->ws, c->B, nv,
-                             L.c, c->Pp, c->stream, dzbf, dtbf, c->bf.sp));
+    // dz in FP32 only when the consumer reads it so: a data gradient off the tensor cores (a
+    // layer that needs one) or a weight gradient off them
+    const bool fp32_dz = !dzbf ||
+                         (!c->bf.layers[dz_consumer->tc].dgrad &&
+                          !c->bf.layers[dz_consumer->tc].input_layer) ||
+                         !tc_wgrad(c, *dz_consumer);
+    ok(layernorm_act_bwd_f32(dy, aout, xh, rs, c->theta + L.g_off, fp32_dz ? dz : nullptr, dt,
+                             c->ws, c->B, nv, L.c, c->Pp, c->stream, dzbf, dtbf, c->bf.sp));
     if (dzbf) own_dy(*dz_consumer);
     if (dtbf) pbf_owner = dt_owner;
     ok(reduce_rows_f32(c->ws, G(L.g_off), c->B, layernorm_bwd_blocks(nv, L.c), 2 * L.c, c->Pp,
@@ -760,7 +766,11 @@ struct Launcher {
   // gradient dt goes straight into dx and conv a's data gradient adds onto it; then, when
   // next (the unit whose output is R.x) can take it, next's LayerNorm backward runs in that
   // data gradient's epilogue instead (dx is not stored) and true is returned.
-  bool res_bwd(Res& R, const float* dout, float* dx, Unit* next = nullptr) {
+  // dskip / split (a decoder block): with the fused projection's data gradient, its input
+  // gradient is stored split, the first `split` channels (the up-sampled part) into dx and the
+  // rest (the skip part) into dskip; *split_done reports it.
+  bool res_bwd(Res& R, const float* dout, float* dx, Unit* next = nullptr, float* dskip = nullptr,
+               int split = 0, bool* split_done = nullptr) {
     LevelBufs& T = c->lb[R.lvl];
     ln_bwd(R.lnb, R.lvl, dout, R.out, R.xh_b, R.rs_b, T.tz, R.proj ? T.tt : dx, &R.b,
            R.fuse_d || R.fuse_w ? &R : nullptr);
@@ -774,8 +784,11 @@ struct Launcher {
     bool next_done = false;
     if (R.fuse_d) {  // dx = conv_a^T(dz_a) + W_p^T dz_p in one launch
       beg(D2IP_KCLASS_CONV_DGRAD, conv_flops(R.a) + conv_flops(R.p));
+      const bool sp = dskip && split > 0;
       ok(bf16_conv_dgrad_proj(c->bf, R.a.tc, T.tz, T.tt, dx, c->B, c->stream,
-                              dy_staged(R.a), pbf_owner == &R));
+                              dy_staged(R.a), pbf_owner == &R, sp ? dskip : nullptr,
+                              sp ? split : 0));
+      if (split_done) *split_done = sp;
       own_dy(R.a);
       pbf_owner = &R;
       fin();
@@ -834,14 +847,16 @@ struct Launcher {
       conv_wgrad(c->tail, tail_in, c->gds);
     }
     for (int l = 0; l + 1 < L; ++l) {
-      res_bwd(c->dec[l], c->lb[l].g1, c->lb[l].g2);
+      bool split = false;  // the skip part already in de, g2 holds the up-sampled part only
+      res_bwd(c->dec[l], c->lb[l].g1, c->lb[l].g2, nullptr, c->lb[l].de, c->w[l + 1], &split);
       const double bytes = 4.0 * c->B *
                            ((double)c->dims[l + 1].count() * c->w[l + 1] +
                             2.0 * c->dims[l].count() * c->w[l] +
                             (double)c->dims[l].count() * c->w[l + 1]);
       beg(D2IP_KCLASS_UP_BWD, bytes);
-      ok(upsample_concat_bwd_f32(c->lb[l].g2, c->lb[l + 1].g1, c->lb[l].de, c->B,
-                                 c->dims[l + 1], c->dims[l], c->w[l + 1], c->w[l], c->stream));
+      ok(upsample_concat_bwd_f32(c->lb[l].g2, c->lb[l + 1].g1, split ? nullptr : c->lb[l].de,
+                                 c->B, c->dims[l + 1], c->dims[l], c->w[l + 1],
+                                 split ? 0 : c->w[l], c->stream));
       fin();
     }
     for (int l = L - 1; l >= 1; --l) {
