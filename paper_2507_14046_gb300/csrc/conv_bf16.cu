@@ -1537,43 +1537,81 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
   const int Co = CKA;
   const int m = warp * 32 + lane;  // TMEM lane = (window in the MMA, co)
   const int pl = m / Co, co = m % Co;
-  if (kPack && gm.fold) {
+  if (gm.fold) {
     const int Cr = Co / 2;  // the layer's output channels; lanes co, co + Cr: dy_hi, dy_lo
+    const int Ch = Ci / 2;  // the layer's input channels; columns c, Ch + c: x_hi, x_lo
     const long long rowf = (long long)Cr * 27 * ci_out + Cr;
     float* prf = part + ((long long)b * gm.rows_b + chunk) * rowf;
     const bool writer = co < Cr;
-    for (int g = 0; g < kG; ++g) {
-      const int s0 = g * kTpm < 9 - kTpm ? g * kTpm : 9 - kTpm;
-      const int p = s0 + pl;
-      const bool keep = p >= g * kTpm && p < 9;
-      const int tq = 8 - p, kz = tq / 3, ky = tq % 3;
-      const uint32_t col = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * N);
-      for (int xi = 0; xi < 3; ++xi) {
-        const int t = kz * 9 + ky * 3 + xi;
+    for (int q = 0; q < kNq; ++q)
+      for (int g = 0; g < kG; ++g) {
+        const int s0 = g * kTpm < 9 - kTpm ? g * kTpm : 9 - kTpm;
+        const int p = s0 + pl;
+        const bool keep = p >= g * kTpm && p < 9;
+        const int tq = 8 - p, kz = tq / 3, ky = tq % 3;
+        const uint32_t col =
+            tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((q * kG + g) * N);
+        for (int xi = 0; xi < (kPack ? 3 : 1); ++xi) {
+          const int kx = kPack ? xi : kx0 + q;
+          const int t = kz * 9 + ky * 3 + kx;
+          const uint32_t cx = col + (uint32_t)(kPack ? xi * Ci : 0);
+          for (int c0 = 0; c0 < Ch; c0 += 16) {
+            uint32_t r[16], r2[16];
+            if (ok) {
+              tmem_ld16(cx + (uint32_t)c0, r);        // x_hi columns
+              tmem_ld16(cx + (uint32_t)(Ch + c0), r2);  // x_lo columns
+            }
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              v[j] = ok ? __uint_as_float(r[j]) + __uint_as_float(r2[j]) : 0.f;
+              v[j] += __shfl_xor_sync(0xffffffffu, v[j], Cr);  // + the other dy block
+            }
+            if (keep && writer) {
+              float* out = prf + ((long long)co * 27 + t) * ci_out + c0;
+#pragma unroll
+              for (int j = 0; j < 16; j += 4)
+                if (c0 + j < ci_out)
+                  *reinterpret_cast<float4*>(out + j) =
+                      make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            }
+          }
+        }
+        uint32_t r[16];
+        if (ok) tmem_ld16(col + (uint32_t)(kPack ? 3 * Ci : Ci), r);  // the ones column
+        float v0 = ok ? __uint_as_float(r[0]) : 0.f;
+        v0 += __shfl_xor_sync(0xffffffffu, v0, Cr);
+        if (keep && writer && tq == 4 && (kPack || kx0 + q == 1))
+          prf[(long long)Cr * 27 * ci_out + co] = gm.bias_on ? v0 : 0.f;
+      }
+    if (proj && warp * 32 < Co) {  // the projection: rows [co_hi | co_lo], centre x columns
+      const long long prow_n = (long long)Cr * Ch + Cr;
+      float* pp = part_p + ((long long)b * gm.rows_b + chunk) * prow_n;
+      const uint32_t col = tmem + ((uint32_t)(warp * 32) << 16) + pcol;
+      const uint32_t cx = col + (uint32_t)(kPack ? Ci : 0);
+      for (int c0 = 0; c0 < Ch; c0 += 16) {
         uint32_t r[16], r2[16];
         if (ok) {
-          tmem_ld16(col + (uint32_t)(xi * Ci), r);        // x_hi columns
-          tmem_ld16(col + (uint32_t)(xi * Ci + Cr), r2);  // x_lo columns
+          tmem_ld16(cx + (uint32_t)c0, r);
+          tmem_ld16(cx + (uint32_t)(Ch + c0), r2);
         }
         float v[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           v[j] = ok ? __uint_as_float(r[j]) + __uint_as_float(r2[j]) : 0.f;
-          v[j] += __shfl_xor_sync(0xffffffffu, v[j], Cr);  // + the other dy block
+          v[j] += __shfl_xor_sync(0xffffffffu, v[j], Cr);
         }
-        if (keep && writer) {
-          float* out = prf + ((long long)co * 27 + t) * ci_out;
+        if (writer)
 #pragma unroll
           for (int j = 0; j < 16; j += 4)
-            if (j < ci_out)
-              *reinterpret_cast<float4*>(out + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-        }
+            *reinterpret_cast<float4*>(pp + (long long)co * Ch + c0 + j) =
+                make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
       }
       uint32_t r[16];
-      if (ok) tmem_ld16(col + (uint32_t)(3 * Ci), r);  // the ones column
+      if (ok) tmem_ld16(col + (uint32_t)(kPack ? 3 * Ci : Ci), r);
       float v0 = ok ? __uint_as_float(r[0]) : 0.f;
       v0 += __shfl_xor_sync(0xffffffffu, v0, Cr);
-      if (keep && writer && tq == 4) prf[(long long)Cr * 27 * ci_out + co] = gm.bias_on ? v0 : 0.f;
+      if (writer) pp[(long long)Cr * Ch + co] = gm.bias_on ? v0 : 0.f;
     }
   } else {
   const long long row = (long long)Co * 27 * ci_out + Co;  // the first ci_out channels
@@ -1812,6 +1850,7 @@ int wg3_tz(int Z);
 int wg3_tz_fit(const TcLayer& L);
 Wg3Geom wg3_geom(const TcLayer& L, int B, bool proj = false);
 Wg3Geom wg3_geom_fold(const TcLayer& L, int B, int sp);
+TcLayer wg3_fold_view(const TcLayer& L);
 
 CUtensorMapSwizzle swizzle_for(int ck) {
   return ck == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
@@ -2398,8 +2437,12 @@ cudaError_t encode_wgrad_maps(TcLayer& L, const Bf16Net& bf, int B, int blk) {
   if (L.wg3) {
     const int tz = L.wg_tz;
     if (blk == 0 && wg3_geom_fold(L, B, sp).nst > 0) {  // [hi | lo]: the first 2 blocks
-      e = encode_box(&L.wgqy, y, B, L.dout, 2 * L.co, 2 * L.co, 8, 3, tz + 2, yrow);
-      if (e == cudaSuccess) e = encode_box(&L.wgqx, x, B, L.din, 2 * L.ci, 2 * L.ci, 8, 1, tz, xrow);
+      const int tq = wg3_fold_view(L).wg_tz;
+      e = encode_box(&L.wgqy, y, B, L.dout, 2 * L.co, 2 * L.co, 8, 3, tq + 2, yrow);
+      if (e == cudaSuccess)
+        e = encode_box(&L.wgqx, x, B, L.din, 2 * L.ci, chunk_for(2 * L.ci), 8, 1, tq, xrow);
+      if (e == cudaSuccess && L.projw)
+        e = encode_box(&L.wgqp, bf.pbf, B, L.dout, 2 * L.co, 2 * L.co, 8, 1, tq, yrow);
       if (e != cudaSuccess) return e;
     }
     e = encode_box(&L.wgy[blk], y, B, L.dout, L.co, L.co, 8, 3, tz + 2, yrow);
@@ -2632,16 +2675,20 @@ Wg3Geom wg3_geom_dual(const TcLayer& L, int B) {
   return wg3_geom_form(L, B, false, true, 2);
 }
 
-// Split precision, a 16 -> 16 layer (no fused projection): the packed form on [hi | lo]
-// rows of dy and x seen as 32 channels, all four products in one pass (the kernel's fold).
+// Split precision, a layer with 16 output channels: the halo kernel on [hi | lo] rows of dy
+// and x seen as 32 and 2 ci channels, all four products (and a fused projection's) in one
+// pass (the kernel's fold); packed when the x taps fit in N, else one x tap per CTA.  The
+// column depth is the layer's own when two stages fit, else refitted for the wider rows.
 TcLayer wg3_fold_view(const TcLayer& L) {
   TcLayer Q = L;
-  Q.co = 32, Q.ci = 32;
+  Q.co = 2 * L.co, Q.ci = 2 * L.ci;
+  Wg3Geom g = wg3_geom(Q, 1, L.projw);
+  if (g.nst <= 0) Q.wg_tz = wg3_tz_fit(Q);
   return Q;
 }
 Wg3Geom wg3_geom_fold(const TcLayer& L, int B, int sp) {
-  if (sp != 3 || !L.wg3 || L.projw || L.co != 16 || L.ci != 16) return Wg3Geom{};
-  Wg3Geom g = wg3_geom_form(wg3_fold_view(L), B, false, true, 1);
+  if (sp != 3 || !L.wg3 || L.co != 16 || L.ci % 16 || L.ci > 48) return Wg3Geom{};
+  Wg3Geom g = wg3_geom(wg3_fold_view(L), B, L.projw);
   if (g.nst > 0) g.fold = 1, g.rows_b = g.nchunks, g.bias_on = 1;
   return g;
 }
@@ -2785,9 +2832,12 @@ cudaError_t bf16_conv_wgrad(Bf16Net& bf, int layer, const float* x, const float*
   }
   if (L.wg3 && passes == 1 && bf.sp > 1) {  // the split products in one pass
     const Wg3Geom gf = wg3_geom_fold(L, B, bf.sp);
-    if (gf.nst <= 0) return cudaErrorInvalidValue;
-    launch_wg3<32, 32>(wg3_fold_view(L), gf, L.wgqy, L.wgqx, L.wgqy, part, nullptr, B, bf.err,
-                       stream);
+    if (gf.nst <= 0 || (L.projw && (!dz_p || !part_p))) return cudaErrorInvalidValue;
+    if (L.projw && !L.projd)  // the fused projection's dz_p staged (else kept from the dgrad)
+      e = stage_rows(dz_p, bf.pbf, (long long)B * L.dout.count(), L.co, bf.sp, stream);
+    if (e != cudaSuccess) return e;
+    launch_wg3<32, 32>(wg3_fold_view(L), gf, L.wgqy, L.wgqx, L.projw ? L.wgqp : L.wgqy, part,
+                       L.projw ? part_p : nullptr, B, bf.err, stream);
     return cudaGetLastError();
   }
   if (L.wg3) {

@@ -23,7 +23,8 @@ struct TcLayer {
   // tiles) for the hi (index 0) and lo (index 1, split precision only) channel blocks of the
   // staged dy and x, and a fused projection's dz_p column.
   CUtensorMap wgy[2], wgx[2], wgp[2];
-  CUtensorMap wgqy, wgqx;   // split precision in one pass: dy and x as [hi | lo] rows
+  CUtensorMap wgqy, wgqx, wgqp;  // split precision in one pass: dy, x (and a fused
+                                 // projection's dz_p) as [hi | lo] rows
   int ci = 0, co = 0, k = 3, s = 1;
   // The halo-form (persistent kernel) view of the forward and data gradient: K channels and
   // MMA width N.  Normally kf, co and kd, ci; with hlf / hld (split precision, a 16 -> 16
