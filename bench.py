@@ -14,7 +14,7 @@ data term, adjoint, backward and Adam.
 The default workload is the 64 batched sequences in the split BF16 precision (BF16x3): the
 metric compares it with the plain FP32 form at equal ERR, and the line carries the evidence
 (plain_fp32: per-frame ERR differences against the FP32 fits of a sample of the sequences,
-and the FP32 fits' own floor under a 1e-7 change of their starting weights).
+and the FP32 fits' own floor under 1e-7 changes of their starting weights, four of them).
 
 Multi-GPU: replicas only.  Every rank fits its own copy of the workload (weak scaling);
 there is no collective on the data path, only a barrier and a max over ranks of the time.
@@ -386,10 +386,10 @@ def run_batched(args, rank, world, local_rank):
             err_b[p] = [_err(S[i, t], g.truth[i, t]) for t in range(T)
                         if np.abs(g.truth[i, t]).max() > 0]
     # plain FP32 single-problem form on one sequence per group, at equal schedule; and the
-    # same sequences in FP32 twice more, from theta0 * (1 + 1e-7 sin(index)) and from
-    # theta0 * (1 - 1e-7 cos(index)) (rounded to FP32): how far the FP32 fit itself moves
-    # under a rounding-level change of its start, the floor below which an ERR difference
-    # between two precisions means nothing
+    # same sequences in FP32 four times more, from theta0 * (1 + 1e-7 f(index)) with f = sin,
+    # -cos, cos, -sin (rounded to FP32): how far the FP32 fit itself moves under a
+    # rounding-level change of its start, the floor below which an ERR difference between two
+    # precisions means nothing
     plain_s, plain_frames, err_p, err_f = 0.0, 0, {}, {}
     for g, b in zip(groups, dv):
         i, p = 0, g.problems[0]
@@ -401,7 +401,8 @@ def run_batched(args, rank, world, local_rank):
         R1 = torch.zeros((1, T), dtype=torch.float64, device=dev)
         ks = np.arange(b["th_np"].shape[1])
         th_pert = [torch.from_numpy((b["th_np"][i] * (1.0 + 1e-7 * f(ks))).astype(np.float32)
-                                    [None]).to(dev) for f in (np.sin, lambda k: -np.cos(k))]
+                                    [None]).to(dev)
+                   for f in (np.sin, lambda k: -np.cos(k), np.cos, lambda k: -np.sin(k))]
 
         def one(th):
             B.d2ip_load_J(c1.handle, b["J"], b["m"], b["n"], 1)
@@ -435,10 +436,10 @@ def run_batched(args, rank, world, local_rank):
     # per-frame relative ERR differences against the plain FP32 form, over the sample
     d_bp = np.concatenate([np.abs(np.subtract(err_b[p], err_p[p])) / err_p[p] for p in sample])
     d_fp = [np.concatenate([np.abs(np.subtract(err_f[p][k], err_p[p])) / err_p[p]
-                            for p in sample]) for k in range(2)]
+                            for p in sample]) for k in range(len(err_f[sample[0]]))]
     floor = float(np.mean(np.concatenate(d_fp)))
     # a mean over six sequences of correlated frames: allow 1.5x for its sampling noise (the
-    # two floor samples' means are reported side by side as a measure of it)
+    # four floor samples' means are reported side by side as a measure of it)
     equal_err = bool(np.mean(d_bp) <= max(1e-3, 1.5 * floor))
 
     # roofline of the dominant kernel class on the largest group
@@ -498,8 +499,8 @@ def run_batched(args, rank, world, local_rank):
                                       "sample_means": [float(np.mean(d)) for d in d_fp],
                                       "max": float(max(np.max(d) for d in d_fp)),
                                       "how": "the same FP32 fits from theta0 * (1 + 1e-7 "
-                                             "sin(index)) and theta0 * (1 - 1e-7 cos(index)); "
-                                             "per-frame relative ERR change"},
+                                             "f(index)), f = sin, -cos, cos, -sin; per-frame "
+                                             "relative ERR change"},
                        "equal_err": equal_err,
                        "equal_err_rule": "mean per-frame |ERR - ERR_fp32| / ERR_fp32 of the "
                                          "batched form <= max(1e-3, 1.5 x mean FP32 floor)",
