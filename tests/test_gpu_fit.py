@@ -236,9 +236,12 @@ def test_largest_workload_iteration(d2ip, precision):
     iteration at full size against the oracle.  FP32: Delta sigma and the loss within 1e-5;
     the weight gradients are sums over 131072 voxels with heavy cancellation, and the same
     formulas evaluated in float32 arithmetic already differ from FP64 by up to 3.8e-4 (stem
-    weights) there, so their bar is 5e-4.  theta_1 = theta_0 - lr g/(|g| + eps) is close to
-    lr sign(g), so elements whose gradient lies below that floor move by up to 2 lr; theta
-    gets the same 5e-4 bar.  BF16: 2e-2 on Delta sigma."""
+    weights) there, so the stem's bar is 5e-4 and every other tensor's 2e-4 (measured 4.1e-4
+    and at most 1.1e-4).  Carrying the cross-chunk sums of the partial rows in FP64 changes
+    none of these errors in its first three digits: the floor is the float32 rounding of the
+    activations and of dy, not the summation order.  theta_1 = theta_0 - lr g/(|g| + eps) is
+    close to lr sign(g), so elements whose gradient lies below that floor move by up to 2 lr;
+    theta gets the 2e-4 bar (measured 8.9e-5).  BF16: 2e-2 on Delta sigma."""
     pb = problems.make((64, 64, 32), 3, 4, (16, 32, 64, 128), seed=3)
     Z64, dv = pb.Zin.astype(np.float64), pb.V[0].astype(np.float64)
     st = dip.AdamState.fresh(pb.theta0.size)
@@ -253,8 +256,9 @@ def test_largest_workload_iteration(d2ip, precision):
     assert abs(tr[0, 0] - ref.loss) <= (TOL if precision == 0 else 4e-2) * ref.loss
     if precision == 0:
         for name, shape, kind, fi, off, cnt in onet.param_layout(pb.spec):
-            assert rel(g[off:off + cnt], ref.grad[off:off + cnt]) < 5e-4, name
-        assert rel(th1, ref.theta) < 5e-4
+            bar = 5e-4 if name == "stem.W" else 2e-4
+            assert rel(g[off:off + cnt], ref.grad[off:off + cnt]) < bar, name
+        assert rel(th1, ref.theta) < 2e-4
     else:
         assert rel(g, ref.grad) < 5e-2
 
