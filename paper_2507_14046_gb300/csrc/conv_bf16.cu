@@ -35,7 +35,11 @@ constexpr int kStages = 4;
 // Taps of one launch: the input box of tap j starts at origin * s_in + off[j] (x, y, z), its
 // weights are tap widx[j] of the weight tensor, and the tile's output voxel q is written at
 // q * s_out + r.  A forward convolution is one class of 27 (or 1) taps; the stride-2 data
-// gradient is 8 classes, one per output parity, of 1, 2, 4 or 8 taps.
+// gradient is 8 classes, one per output parity, of 1, 2, 4 or 8 taps -- or, packed (pack =
+// 8), one CTA per tile whose 8 "taps" are the coarse windows (ox, oy, oz) in {0, 1}^3 and
+// whose N holds all 8 classes side by side: class p = px + 2 py + 4 pz takes columns
+// [p n0, p n0 + n0) and writes parity r = (px, py, pz); a window's weight block for a class
+// that does not read it is zero.
 struct TapClass {
   int n;
   int8_t off[27][3];
@@ -44,6 +48,7 @@ struct TapClass {
 };
 struct TapPlan {
   int s_in, s_out;
+  int pack;  // 0: one class per CTA (blockIdx.y); 8: the packed stride-2 data gradient
   TapClass cls[8];
 };
 
@@ -137,21 +142,39 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__
   tc_fence_after();
   if (ok) {
     const int m = warp * 32 + lane;  // TMEM lane = tile row = voxel of the box
-    const int ox = (x0 + m % kBX) * plan.s_out + cls.r[0],
-              oy = (y0 + (m / kBX) % kBY) * plan.s_out + cls.r[1],
-              oz = (z0 + m / (kBX * kBY)) * plan.s_out + cls.r[2];
-    const bool inside = ox < dout.x && oy < dout.y && oz < dout.z;
-    const long long vox = ((long long)oz * dout.y + oy) * dout.x + ox;
-    float* o = out + (long long)b * out_bs + vox * N;
+    const int n0 = plan.pack ? N / plan.pack : N;  // output channels (columns of one class)
     const float* bb = bias ? bias + (long long)b * bias_bs : nullptr;
     for (int c0 = 0; c0 < N; c0 += 16) {
+      const int p = c0 / n0, cc = c0 - p * n0;  // packed: class p, its channel cc
+      const int rx = plan.pack ? (p & 1) : cls.r[0], ry = plan.pack ? (p >> 1) & 1 : cls.r[1],
+                rz = plan.pack ? (p >> 2) & 1 : cls.r[2];
+      const int ox = (x0 + m % kBX) * plan.s_out + rx,
+                oy = (y0 + (m / kBX) % kBY) * plan.s_out + ry,
+                oz = (z0 + m / (kBX * kBY)) * plan.s_out + rz;
+      const bool inside = ox < dout.x && oy < dout.y && oz < dout.z;
+      const long long vox = ((long long)oz * dout.y + oy) * dout.x + ox;
+      float* o = out + (long long)b * out_bs + vox * n0 + cc;
       uint32_t r[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-      if (inside) {
+      if (inside && (reinterpret_cast<uintptr_t>(o) & 15) == 0) {  // 16-byte stores
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) {
+          float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                 __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+          if (bb) v.x += bb[cc + j], v.y += bb[cc + j + 1], v.z += bb[cc + j + 2],
+                  v.w += bb[cc + j + 3];
+          float4* d = reinterpret_cast<float4*>(o + j);
+          if (accumulate) {
+            const float4 a = *d;
+            v.x += a.x, v.y += a.y, v.z += a.z, v.w += a.w;
+          }
+          *d = v;
+        }
+      } else if (inside) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          float v = __uint_as_float(r[j]) + (bb ? bb[c0 + j] : 0.f);
-          o[c0 + j] = accumulate ? o[c0 + j] + v : v;
+          const float v = __uint_as_float(r[j]) + (bb ? bb[cc + j] : 0.f);
+          o[j] = accumulate ? o[j] + v : v;
         }
       }
     }
@@ -1374,6 +1397,12 @@ wgrad_s2_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
 // NX = 2 (packed, split precision): the hi and lo blocks of x (tm_x, tm_x2) side by side,
 // N = 6 Ci + CKB, and the epilogue adds the two products of each tap: dy_hi x_hi + dy_hi x_lo
 // in one MMA stream (the pass with dy_lo x_hi is a separate NX = 1 launch).
+// ones_sep (the per-x-tap forms): B is the x column alone (N = Ci, one CKB-wide block per
+// channel chunk, no partial swizzle atom) and the centre x tap's CTA adds one MMA of N = 16
+// per K step, the M block holding window 4 (tap 13) against a K-major block of ones, into a
+// 16-column accumulator of its own (one more for a fused projection's dz_p).  G accumulators
+// of Ci columns then fit in tensor memory where G of Ci + CKB do not (64 -> 64 layers), and
+// every MMA reads CKB fewer columns of B.
 // ------------------------------------------------------------------------------------
 constexpr int kWg3MaxStages = 6;
 
@@ -1384,6 +1413,7 @@ struct Wg3Geom {
   int nx;          // x operand sets side by side in N (2: hi and lo of the split precision)
   int bias_on;     // write the ones column's sums (else zeros: a pass that repeats them)
   int fold;        // split precision in one pass (below)
+  int ones_sep;    // per-x-tap form: the ones column as separate N = 16 MMAs (below)
   uint32_t a_box, b_box, b_off, ones_off, stage, tmem_cols;
   int proj;        // also the weight gradient of a fused 1x1 projection (its dz_p: p_box)
   uint32_t p_off, p_box;
@@ -1403,7 +1433,7 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
   constexpr bool kPack = NKX == 0;                 // the three x taps in N
   constexpr int kNq = kPack ? 1 : NKX;             // dy boxes (accumulator sets) per stage
   static_assert(NX == 1 || kPack, "two x operand sets only in the packed form");
-  const int N = (kPack ? 3 * NX * Ci : Ci) + CKB;  // + the ones block
+  const int N = (kPack ? 3 * NX * Ci : Ci) + (gm.ones_sep ? 0 : CKB);  // + the ones block
   const int nb = Ci / CKB;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -1419,6 +1449,11 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
   // the projection's products go with the centre x tap: D_p[co][ci] = sum_u dz_p[u][co] x[u][ci]
   const bool proj = gm.proj && (kPack || (kx0 <= 1 && 1 < kx0 + NKX));
   const uint32_t pcol = (uint32_t)(kNq * kG * N);  // its accumulator
+  // ones_sep: the accumulators of the window-4 block's and the projection's ones columns
+  constexpr int kGc = 4 / kTpm;                    // the M block holding window 4
+  const uint32_t ocol = pcol + (gm.proj ? (uint32_t)N : 0u);
+  const int qc = 1 - kx0;                          // the centre x tap's accumulator set
+  const bool ones_mma = gm.ones_sep && !kPack && qc >= 0 && qc < kNq;
   for (int s = 0; s < nst; ++s) {
     uint32_t* ones = reinterpret_cast<uint32_t*>(smem + (size_t)s * gm.stage + gm.ones_off);
     for (int i = threadIdx.x; i < (int)(gm.b_box / 4); i += blockDim.x) ones[i] = 0x3F803F80u;
@@ -1482,6 +1517,7 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
     drain_loads(full_bar, nst, k, err);
   } else if (warp == 1 && lane == 0) {  // MMA issuer
     const uint32_t idesc = instr_desc_mn(N);
+    const uint32_t idesc_o = instr_desc_major(16, true, false);  // A MN-major, ones K-major
     for (int k = 0; k < ksteps; ++k) {
       const int s = k % nst;
       if (!mbar_wait(smem_u32(&full_bar[s]), (k / nst) & 1)) {
@@ -1490,6 +1526,9 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
       }
       tc_fence_after();
       const uint32_t base = smem_u32(smem + (size_t)s * gm.stage);
+      // the ones block read K-major (16 rows of 32 bytes, 32-byte swizzle: ones either way)
+      const uint64_t o0 = smem_desc<16>(base + gm.ones_off);
+      const uint32_t olo = (uint32_t)o0, ohi = (uint32_t)(o0 >> 32);
       // descriptors are linear in the address (start >> 4 in the low word): offset a base
       const uint64_t a0 = smem_desc_mn2<CKA>(base, kAtomA, 3 * kAtomA);
       const uint64_t b0 = smem_desc_mn2<CKB>(base + gm.b_off, gm.b_box, kAtomB);
@@ -1519,6 +1558,13 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
             mma_lh_p(tmem + pcol, plo, phi, blo, bhi, idesc, k > 0 ? 1u : 0u);
           else
             mma_lh(tmem + pcol, plo, phi, blo, bhi, idesc);
+        }
+        if (ones_mma) {  // sum(dy) of the window-4 block (and of dz_p): B = 16 x 16 ones
+          const uint32_t ao = (uint32_t)qc * abx + (uint32_t)((kGc * kTpm * kAtomA) >> 4);
+          mma_lh_p(tmem + ocol, alo + ao, ahi, olo, ohi, idesc_o, (k > 0 || kk > 0) ? 1u : 0u);
+          if (proj)
+            mma_lh_p(tmem + ocol + 16, plo, phi, olo, ohi, idesc_o,
+                     (k > 0 || kk > 0) ? 1u : 0u);
         }
         alo += (6 * kAtomA) >> 4;  // next two z offsets: 6 dy atoms, 2 x atoms
         blo += (2 * kAtomB) >> 4;
@@ -1578,10 +1624,16 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
           }
         }
         uint32_t r[16];
-        if (ok) tmem_ld16(col + (uint32_t)(kPack ? 3 * Ci : Ci), r);  // the ones column
+        const bool centre = kPack || kx0 + q == 1;
+        if (gm.ones_sep) {  // the ones column lives in its own accumulator (window-4 block)
+          if (ok && centre && g == kGc)
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + ocol, r);
+        } else if (ok) {
+          tmem_ld16(col + (uint32_t)(kPack ? 3 * Ci : Ci), r);  // the ones column
+        }
         float v0 = ok ? __uint_as_float(r[0]) : 0.f;
         v0 += __shfl_xor_sync(0xffffffffu, v0, Cr);
-        if (keep && writer && tq == 4 && (kPack || kx0 + q == 1))
+        if (keep && writer && tq == 4 && centre)
           prf[(long long)Cr * 27 * ci_out + co] = gm.bias_on ? v0 : 0.f;
       }
     if (proj && warp * 32 < Co) {  // the projection: rows [co_hi | co_lo], centre x columns
@@ -1608,7 +1660,9 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
                 make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
       }
       uint32_t r[16];
-      if (ok) tmem_ld16(col + (uint32_t)(kPack ? 3 * Ci : Ci), r);
+      if (ok)
+        tmem_ld16(gm.ones_sep ? tmem + ((uint32_t)(warp * 32) << 16) + ocol + 16
+                              : col + (uint32_t)(kPack ? 3 * Ci : Ci), r);
       float v0 = ok ? __uint_as_float(r[0]) : 0.f;
       v0 += __shfl_xor_sync(0xffffffffu, v0, Cr);
       if (writer) pp[(long long)Cr * Ch + co] = gm.bias_on ? v0 : 0.f;
@@ -1650,8 +1704,13 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
         }
       }
       uint32_t r[16];
-      if (ok) tmem_ld16(col + (uint32_t)(kPack ? 3 * NX * Ci : Ci), r);  // the ones column
-      if (keep && tq == 4 && (kPack || kx0 + q == 1))  // the centre tap (t = 13): the bias
+      const bool centre = kPack || kx0 + q == 1;
+      if (gm.ones_sep) {  // the ones column lives in its own accumulator (window-4 block)
+        if (ok && centre && g == kGc) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + ocol, r);
+      } else if (ok) {
+        tmem_ld16(col + (uint32_t)(kPack ? 3 * NX * Ci : Ci), r);  // the ones column
+      }
+      if (keep && tq == 4 && centre)  // the centre tap (t = 13): the bias
         prow[(long long)Co * 27 * ci_out + co] = ok && gm.bias_on ? __uint_as_float(r[0]) : 0.f;
     }
   if (proj && warp * 32 < Co) {  // rows co < Co of the projection accumulator
@@ -1672,7 +1731,9 @@ wgrad_tc3_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constan
       }
     }
     uint32_t r[16];
-    if (ok) tmem_ld16(col + (uint32_t)(kPack ? 3 * Ci : Ci), r);
+    if (ok)
+      tmem_ld16(gm.ones_sep ? tmem + ((uint32_t)(warp * 32) << 16) + ocol + 16
+                            : col + (uint32_t)(kPack ? 3 * Ci : Ci), r);
     if (m < Co) pp[(long long)Co * Ci + m] = ok && gm.bias_on ? __uint_as_float(r[0]) : 0.f;
   }
   }  // not fold
@@ -1717,7 +1778,22 @@ __global__ void f32_to_bf16_rows_kernel(const float* __restrict__ x, __nv_bfloat
 
 // Stored tap index of tap t of a 27-tap layer whose halo form packs kz into N: ky and kz
 // swapped, so the kz taps of one (ky, kx) are adjacent in the B box of x tap kx.
+// perm 2 (the packed stride-2 data gradient): the data-gradient row of t = 26 - (forward tap
+// f) goes to block 8 w + p, the (window w, class p) pair that reads tap f.  Per axis, tap k
+// = 1 is read by parity 0 from window 0, k = 2 by parity 1 from window 0, k = 0 by parity 1
+// from window 1.
 __device__ __forceinline__ int packed_tap(int t, int perm) {
+  if (perm == 2) {
+    const int f = 26 - t;
+    int w = 0, p = 0;
+#pragma unroll
+    for (int a = 0, s = 1; a < 3; ++a, s *= 3) {
+      const int k = (f / s) % 3;
+      w |= (k == 0 ? 1 : 0) << a;
+      p |= (k != 1 ? 1 : 0) << a;
+    }
+    return 8 * w + p;
+  }
   return perm ? ((t / 3) % 3) * 9 + (t / 9) * 3 + t % 3 : t;
 }
 
@@ -2266,6 +2342,24 @@ TapPlan dgrad_s2_plan() {
   return p;
 }
 
+// The stride-2 data gradient with its classes packed in N: the 8 windows (ox, oy, oz) in
+// {0, 1}^3 of dy, window w's weights at block w of the packed tensor.
+TapPlan dgrad_s2_packed_plan() {
+  TapPlan p{};
+  p.s_in = 1;
+  p.s_out = 2;
+  p.pack = 8;
+  TapClass& c = p.cls[0];
+  c.n = 8;
+  for (int w = 0; w < 8; ++w) {
+    c.off[w][0] = (int8_t)(w & 1);
+    c.off[w][1] = (int8_t)((w >> 1) & 1);
+    c.off[w][2] = (int8_t)((w >> 2) & 1);
+    c.widx[w] = (uint8_t)w;
+  }
+  return p;
+}
+
 // qdims: extent of the tile grid (output voxels for s_out = 1, coarse positions for 2).
 cudaError_t launch_tc(const CUtensorMap& a, const CUtensorMap& w, const TapPlan& plan,
                       int nclass, int cin, const float* bias, float* out, Dims3 dout,
@@ -2343,13 +2437,15 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
   L.wg3 = L.wgrad && wg3_geom(L, 1).nst > 0;
   if (k == 3 && s == 2 && (ci == 16 || ci == 32 || ci == 64) && co % 16 == 0 && co <= 256)
     L.wgrad = L.wgs2 = true;
+  L.s2p = L.dgrad && s == 2 && k == 3 && 8 * ci <= 256;
   const long long n = (long long)co * k * k * k * ci * bf.sp;
   const long long n4 = (long long)co * k * k * k * ci * 4;  // the doubled [2 co][2 ci] rows
+  const long long n64 = (long long)co * 64 * ci * bf.sp;    // 8 x 8 window-class blocks
   L.wf_off = bf.wstride;
   bf.wstride += ((L.hlf ? n4 : n) + 63) / 64 * 64;
   if (L.dgrad) {
     L.wd_off = bf.wstride;
-    bf.wstride += ((L.hld ? n4 : n) + 63) / 64 * 64;
+    bf.wstride += ((L.hld ? n4 : L.s2p ? n64 : n) + 63) / 64 * 64;
   }
   bf.layers.push_back(L);
   return (int)bf.layers.size() - 1;
@@ -2504,7 +2600,10 @@ cudaError_t bf16_finalize(Bf16Net& bf, int B) {
                    1);
     if (e == cudaSuccess && L.dgrad) {
       e = encode_act(&L.act_d, dy_buf(bf, L), B, L.dout, L.kd, chunk_for(L.kd), 1);
-      if (e == cudaSuccess)
+      if (e == cudaSuccess && L.s2p)  // [window][class x ci][kd]: one box per window
+        e = encode_w(&L.w_d, bf.wbuf + L.wd_off, B, bf.wstride, L.kd, 8, 8 * L.ci,
+                     chunk_for(L.kd), 1, 1);
+      else if (e == cudaSuccess)
         e = encode_w(&L.w_d, bf.wbuf + L.wd_off, B, bf.wstride, L.kd, T, L.ci, chunk_for(L.kd), 1,
                      1);
     }
@@ -2631,10 +2730,12 @@ Wg3Geom wg3_geom_form(const TcLayer& L, int B, bool proj, bool pack, int nx = 1)
     if (Np > 256 || (G + extra) * Np > 512) return g;
     g.nkx = 0;
     g.tmem_cols = (uint32_t)pow2((G + extra) * Np);
-  } else {
-    g.nkx = (3 * G + extra) * N <= 512 ? 3 : 1;
-    if ((G + extra) * N > 512) return g;
-    g.tmem_cols = (uint32_t)pow2((g.nkx * G + extra) * N);
+  } else {  // per-x-tap accumulators of Ci columns; the ones columns apart (ones_sep)
+    const int on = 16 * (1 + extra);
+    g.nkx = (3 * G + extra) * L.ci + on <= 512 ? 3 : 1;
+    if ((G + extra) * L.ci + on > 512) return g;
+    g.ones_sep = 1;
+    g.tmem_cols = (uint32_t)pow2((g.nkx * G + extra) * L.ci + on);
   }
   g.proj = extra;
   g.tz = L.wg_tz > 0 ? L.wg_tz : wg3_tz(L.dout.z);
@@ -2976,7 +3077,7 @@ cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long lo
       t.w_off[i] = L.w_off, t.wf_off[i] = L.wf_off, t.wd_off[i] = L.wd_off;
       t.ci[i] = L.ci, t.ci_real[i] = L.ci_real, t.co[i] = L.co, t.T[i] = T;
       t.dgrad[i] = L.dgrad ? 1 : 0;
-      t.permf[i] = L.pack3f ? 1 : 0, t.permd[i] = L.pack3d ? 1 : 0;
+      t.permf[i] = L.pack3f ? 1 : 0, t.permd[i] = L.s2p ? 2 : L.pack3d ? 1 : 0;
       t.hlf[i] = L.hlf ? 1 : 0, t.hld[i] = L.hld ? 1 : 0;
     }
     t.blk0[t.nl] = blk;
@@ -2998,7 +3099,7 @@ cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long lo
       t.w_off[i] = L.w_off, t.wf_off[i] = L.wf_off, t.wd_off[i] = L.wd_off;
       t.ci[i] = L.ci, t.ci_real[i] = L.ci_real, t.co[i] = L.co, t.T[i] = T;
       t.dgrad[i] = L.dgrad ? 1 : 0;
-      t.permf[i] = L.pack3f ? 1 : 0, t.permd[i] = L.pack3d ? 1 : 0;
+      t.permf[i] = L.pack3f ? 1 : 0, t.permd[i] = L.s2p ? 2 : L.pack3d ? 1 : 0;
       t.hlf[i] = L.hlf ? 1 : 0, t.hld[i] = L.hld ? 1 : 0;
     }
     t.blk0[t.nl] = blk;
@@ -3013,7 +3114,7 @@ cudaError_t bf16_prepare_weights(Bf16Net& bf, const float* theta, int B, long lo
     weights_bf16_kernel<<<grid, 256, 0, stream>>>(theta, bf.wbuf, Pp, bf.wstride, L.w_off,
                                                   L.wf_off, L.wd_off, L.ci, L.ci_real, L.co, T,
                                                   L.dgrad ? 1 : 0, L.pack3f ? 1 : 0,
-                                                  L.pack3d ? 1 : 0);
+                                                  L.s2p ? 2 : L.pack3d ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -3289,6 +3390,9 @@ cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, 
   if (e != cudaSuccess) return e;
   if (L.s == 2) {
     const Dims3 q{(L.din.z + 1) / 2, (L.din.y + 1) / 2, (L.din.x + 1) / 2};
+    if (L.s2p)
+      return launch_tc(L.act_d, L.w_d, dgrad_s2_packed_plan(), 1, L.kd, nullptr, dx, L.din, q,
+                       8 * L.ci, B, L.din.count() * L.ci, 0, accumulate, bf.err, stream);
     return launch_tc(L.act_d, L.w_d, dgrad_s2_plan(), 8, L.kd, nullptr, dx, L.din, q, L.ci, B,
                      L.din.count() * L.ci, 0, accumulate, bf.err, stream);
   }
@@ -3333,7 +3437,8 @@ long long bf16_op_workspace(int B, Dims3 din, int ci, int co, int k, int s) {
   const Dims3 dout = conv_out_dims(din, k, s);
   const long long T = (long long)k * k * k;
   const long long act = std::max(din.count() * ci, dout.count() * co);
-  const long long w = 2 * ((co * T * ci + 63) / 64 * 64);
+  // forward and data-gradient weights (the packed stride-2 form holds 64 blocks, not 27)
+  const long long w = (co * T * ci + 63) / 64 * 64 + (co * 64 * ci + 63) / 64 * 64;
   return 1024 + 2 * (((long long)B * act * 2 + 1023) / 1024 * 1024) +
          ((long long)B * w * 2 + 1023) / 1024 * 1024 + 1024;
 }
@@ -3354,6 +3459,8 @@ cudaError_t bf16_op_conv(bool dgrad, const float* in, const float* W, const floa
   bf16_layout(bf, base, used, B, std::max(din.count() * ci, dout.count() * co));
   e = bf16_finalize(bf, B);
   if (e == cudaSuccess) e = cudaMemsetAsync(bf.err, 0, sizeof(int), st);
+  if (e == cudaSuccess && bf.layers[idx].s2p)  // the packed form's unwritten blocks are zeros
+    e = cudaMemsetAsync(bf.wbuf, 0, (size_t)B * bf.wstride * 2, st);
   if (e == cudaSuccess) e = bf16_prepare_weights(bf, W, B, w_bs, st);
   if (e != cudaSuccess) return e;
   return dgrad ? bf16_conv_dgrad(bf, idx, in, out, B, accumulate, st)

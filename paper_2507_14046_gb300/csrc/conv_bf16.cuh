@@ -54,6 +54,9 @@ struct TcLayer {
   bool wg3 = false;               // weight gradient by the halo-box kernel
   int wg_tz = 0;                  // its column depth (z voxels per K tile)
   bool wgs2 = false;              // stride-2 weight gradient on the tensor cores
+  bool s2p = false;               // stride-2 data gradient with its 8 parity classes packed
+                                  // in N (one CTA per tile; weights as 8 x 8 window-class
+                                  // blocks, 37 of them zero)
   __nv_bfloat16* xin = nullptr;   // BF16 copy of the forward input (kept for the weight gradient)
   int ci_real = 0;                // input channels of the model (ci is padded up to 16)
   bool input_layer = false;       // reads the padded BF16 copy of the network input (zbf)
