@@ -1397,12 +1397,11 @@ wgrad_s2_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
 // NX = 2 (packed, split precision): the hi and lo blocks of x (tm_x, tm_x2) side by side,
 // N = 6 Ci + CKB, and the epilogue adds the two products of each tap: dy_hi x_hi + dy_hi x_lo
 // in one MMA stream (the pass with dy_lo x_hi is a separate NX = 1 launch).
-// ones_sep (the per-x-tap forms): B is the x column alone (N = Ci, one CKB-wide block per
+// ones_sep (the per-x-tap forms whose accumulators of Ci + CKB columns do not fit in tensor
+// memory, e.g. 64 -> 64 layers): B is the x column alone (N = Ci, one CKB-wide block per
 // channel chunk, no partial swizzle atom) and the centre x tap's CTA adds one MMA of N = 16
 // per K step, the M block holding window 4 (tap 13) against a K-major block of ones, into a
-// 16-column accumulator of its own (one more for a fused projection's dz_p).  G accumulators
-// of Ci columns then fit in tensor memory where G of Ci + CKB do not (64 -> 64 layers), and
-// every MMA reads CKB fewer columns of B.
+// 16-column accumulator of its own (one more for a fused projection's dz_p).
 // ------------------------------------------------------------------------------------
 constexpr int kWg3MaxStages = 6;
 
@@ -2416,8 +2415,12 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
   L.kf3 = L.kf, L.nf3 = co, L.kd3 = L.kd, L.nd3 = ci;
   L.dgrad = (s == 1 || k == 3) && bf16_conv_supported(co, ci, k);
   if (k == 3 && s == 1) {
-    const bool hl = bf.sp == 3 && ci == 16 && co == 16;  // [hi | lo] rows, doubled weights
-    Tc3Plan pf = hl ? tc3_plan(2 * ci, 2 * co, 0, L.dout.z) : Tc3Plan{};
+    // [hi | lo] rows against doubled weights: the forward of 16-output layers with up to 48
+    // inputs (a decoder's first conv; its projection then runs on its own), the data
+    // gradient of 16 -> 16 layers
+    const bool hl = bf.sp == 3 && ci == 16 && co == 16;
+    const bool hlf = bf.sp == 3 && co == 16 && ci % 16 == 0 && ci <= 48;
+    Tc3Plan pf = hlf ? tc3_plan(2 * ci, 2 * co, 0, L.dout.z) : Tc3Plan{};
     if (pf.persistent)
       L.hlf = true, L.kf3 = 2 * ci, L.nf3 = 2 * co;
     else
@@ -2514,6 +2517,8 @@ void bf16_layout(Bf16Net& bf, char* base, size_t& used, int B, long long max_act
   for (TcLayer& L : bf.layers) {
     if (L.input_layer)
       L.xin = bf.zbf;
+    else if (bf.keep_inputs && L.xin_of >= 0)  // an earlier layer's copy of the same input
+      L.xin = bf.layers[L.xin_of].xin;
     else if (bf.keep_inputs)
       L.xin = reinterpret_cast<__nv_bfloat16*>(take((size_t)B * L.din.count() * L.kf * 2));
     else
@@ -2730,7 +2735,11 @@ Wg3Geom wg3_geom_form(const TcLayer& L, int B, bool proj, bool pack, int nx = 1)
     if (Np > 256 || (G + extra) * Np > 512) return g;
     g.nkx = 0;
     g.tmem_cols = (uint32_t)pow2((G + extra) * Np);
-  } else {  // per-x-tap accumulators of Ci columns; the ones columns apart (ones_sep)
+  } else if ((G + extra) * N <= 512) {  // per-x-tap accumulators with the ones block in N
+    g.nkx = (3 * G + extra) * N <= 512 ? 3 : 1;
+    g.tmem_cols = (uint32_t)pow2((g.nkx * G + extra) * N);
+  } else {  // accumulators of Ci columns, the ones columns apart (ones_sep): the centre x
+            // tap's CTA pays one more MMA per K step, so only where the above does not fit
     const int on = 16 * (1 + extra);
     g.nkx = (3 * G + extra) * L.ci + on <= 512 ? 3 : 1;
     if ((G + extra) * L.ci + on > 512) return g;
@@ -3155,7 +3164,7 @@ __global__ void pad_input_kernel(const float* __restrict__ z, __nv_bfloat16* __r
 
 int bf16_fuse_proj(Bf16Net& bf, int la, int lp) {
   TcLayer& A = bf.layers[la];
-  const TcLayer& P = bf.layers[lp];
+  TcLayer& P = bf.layers[lp];
   if (A.k != 3 || A.s != 1 || P.k != 1 || P.ci != A.ci || P.co != A.co || A.input_layer)
     return 0;
   A.proj = lp;
@@ -3166,7 +3175,12 @@ int bf16_fuse_proj(Bf16Net& bf, int la, int lp) {
   }
   if (A.ck3d && P.dgrad) A.projd = A.per3d;  // the dz_p stage rides the persistent dgrad
   A.projw = A.wg3 && wg3_geom(A, 1, true).nst > 0;
+  if (!A.projf && P.kf == A.kf) P.xin_of = la;  // its own launch over la's staged input
   return (A.projf ? 1 : 0) | (A.projd ? 2 : 0) | (A.projw ? 4 : 0);
+}
+
+bool bf16_input_shared(const Bf16Net& bf, int layer) {
+  return bf.keep_inputs && bf.layers[layer].xin_of >= 0;
 }
 
 cudaError_t bf16_conv_fwd_proj(Bf16Net& bf, int la, const float* x, const float* bias_a,

@@ -61,6 +61,8 @@ struct TcLayer {
   int ci_real = 0;                // input channels of the model (ci is padded up to 16)
   bool input_layer = false;       // reads the padded BF16 copy of the network input (zbf)
   int dyslot = 0;                 // BF16 staging buffer of this layer's dy: 0 ybf, 1 ybf2
+  int xin_of = -1;                // a projection run on its own: the layer whose kept BF16
+                                  // input (the same tensor, the same layout) it reads
 };
 
 // Device buffers of the BF16 path (carved from the context arena) and its layers.
@@ -99,8 +101,11 @@ cudaError_t bf16_stage_input(Bf16Net& bf, int layer, const float* z, int B, cuda
 // Fuse the 1x1 projection lp (same input, same output channels) into the 3x3x3 stride-1
 // layer la: its forward and data gradient then run in la's halo-box launches.  Returns
 // whether the forward (bit 0), the data gradient (bit 1) and the weight gradient (bit 2)
-// were fused.
+// were fused.  A forward left unfused (la's folded split form) reads la's kept BF16 input.
 int bf16_fuse_proj(Bf16Net& bf, int la, int lp);
+// Whether the layer reads another layer's kept BF16 input: once that layer's forward ran,
+// this one's input is staged.
+bool bf16_input_shared(const Bf16Net& bf, int layer);
 // y_a = conv_a(x) + bias_a and y_p = W_p x + bias_p in one launch (layer la with projf).
 cudaError_t bf16_conv_fwd_proj(Bf16Net& bf, int la, const float* x, const float* bias_a,
                                float* y_a, const float* bias_p, float* y_p, int B,

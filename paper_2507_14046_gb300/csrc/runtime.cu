@@ -525,11 +525,12 @@ struct Launcher {
     return 2.0 * c->B * (double)L.dout.count() * L.k * L.k * L.k * L.ci * L.co;
   }
 
-  void conv_fwd(const ConvL& L, const float* x, float* y) {
+  // staged: x already sits in the layer's BF16 input (another layer's kept copy of it)
+  void conv_fwd(const ConvL& L, const float* x, float* y, bool staged = false) {
     beg(D2IP_KCLASS_CONV_FWD, conv_flops(L));
     if (L.tc >= 0) {
       ok(bf16_conv_fwd(c->bf, L.tc, x, W(L) + L.wcount(), y, c->B, c->Pp, c->stream,
-                       take_staged(L)));
+                       take_staged(L) || staged));
     } else {
       ok(conv3d_fwd_f32(x, W(L), W(L) + L.wcount(), y, c->B, L.din, L.ci, L.co, L.k, L.s,
                         L.din.count() * L.ci, L.dout.count() * L.co, c->Pp, c->stream));
@@ -635,7 +636,8 @@ struct Launcher {
       }
       ln_fwd(R.lna, R.lvl, c->ztmp, nullptr, R.h1, R.xh_a, R.rs_a, &R.b);
     }
-    if (R.proj && !R.fuse_f) conv_fwd(R.p, R.x, c->ptmp);
+    if (R.proj && !R.fuse_f)  // reading conv a's kept input where it shares it (staged now)
+      conv_fwd(R.p, R.x, c->ptmp, R.p.tc >= 0 && bf16_input_shared(c->bf, R.p.tc));
     const float* resid = R.proj ? c->ptmp : R.x;
     if (conv_ln_fused(R.b, R.lnb, R.h1, resid, R.out, R.xh_b, R.rs_b, next, nullptr)) return;
     conv_fwd(R.b, R.h1, c->ztmp);
