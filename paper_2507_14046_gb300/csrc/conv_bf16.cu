@@ -49,8 +49,21 @@ struct TapClass {
 struct TapPlan {
   int s_in, s_out;
   int pack;  // 0: one class per CTA (blockIdx.y); 8: the packed stride-2 data gradient
+  int fold;  // split rows (pack 0): N = 2 n0, output channel c is D[c] + D[n0 + c]
   TapClass cls[8];
 };
+
+// 16 accumulator columns of this warp's lanes; with off, plus the 16 columns off further on
+// (the two halves of a folded accumulator).
+__device__ __forceinline__ void tmem_ld16f(uint32_t taddr, uint32_t (&r)[16], uint32_t off) {
+  tmem_ld16(taddr, r);
+  if (off) {
+    uint32_t r2[16];
+    tmem_ld16(taddr + off, r2);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(r2[j]));
+  }
+}
 
 template <int CK>
 __global__ void __launch_bounds__(128, 1)
@@ -142,9 +155,11 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__
   tc_fence_after();
   if (ok) {
     const int m = warp * 32 + lane;  // TMEM lane = tile row = voxel of the box
-    const int n0 = plan.pack ? N / plan.pack : N;  // output channels (columns of one class)
+    // output channels (columns of one class; folded: half the columns, added to the other)
+    const int n0 = plan.pack ? N / plan.pack : plan.fold ? N / 2 : N;
+    const int ncol = plan.fold ? n0 : N;
     const float* bb = bias ? bias + (long long)b * bias_bs : nullptr;
-    for (int c0 = 0; c0 < N; c0 += 16) {
+    for (int c0 = 0; c0 < ncol; c0 += 16) {
       const int p = c0 / n0, cc = c0 - p * n0;  // packed: class p, its channel cc
       const int rx = plan.pack ? (p & 1) : cls.r[0], ry = plan.pack ? (p >> 1) & 1 : cls.r[1],
                 rz = plan.pack ? (p >> 2) & 1 : cls.r[2];
@@ -155,7 +170,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__
       const long long vox = ((long long)oz * dout.y + oy) * dout.x + ox;
       float* o = out + (long long)b * out_bs + vox * n0 + cc;
       uint32_t r[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+      tmem_ld16f(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r,
+                 plan.fold ? (uint32_t)n0 : 0u);
       if (inside && (reinterpret_cast<uintptr_t>(o) & 15) == 0) {  // 16-byte stores
 #pragma unroll
         for (int j = 0; j < 16; j += 4) {
@@ -455,17 +471,6 @@ __device__ __forceinline__ int swz_chunk(int chunk, int m, int R) {
   return chunk ^ ((m * R >> 7) & (R / 16 - 1));
 }
 
-// 16 accumulator columns of this warp's lanes; with off, plus the 16 columns off further on
-// (the two halves of a folded accumulator).
-__device__ __forceinline__ void tmem_ld16f(uint32_t taddr, uint32_t (&r)[16], uint32_t off) {
-  tmem_ld16(taddr, r);
-  if (off) {
-    uint32_t r2[16];
-    tmem_ld16(taddr + off, r2);
-#pragma unroll
-    for (int j = 0; j < 16; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(r2[j]));
-  }
-}
 
 // Channels c0..c0+15 of tile row m, values o, into the epilogue's BF16 staging slice: sp
 // blocks (hi; or hi, lo, hi) of 128 rows x nc channels, each the swizzled rows of one
@@ -1921,6 +1926,13 @@ weights_split_bf16_kernel(const float* __restrict__ theta, __nv_bfloat16* __rest
 
 int chunk_for(int c) { return c % 64 == 0 ? 64 : (c % 32 == 0 ? 32 : 16); }
 
+// Split precision, per-tap forward: reading [hi | lo] rows (K = 2 ci) against weights doubled
+// in N (2 co) moves fewer, longer TMA rows than [hi | lo | hi] rows (3 ci) wherever it allows
+// a wider channel chunk.
+bool bf16_fold_pays(const Bf16Net& bf, int ci, int co) {
+  return bf.sp == 3 && 2 * co <= 256 && chunk_for(2 * ci) > chunk_for(3 * ci);
+}
+
 int wg3_tz(int Z);
 int wg3_tz_fit(const TcLayer& L);
 Wg3Geom wg3_geom(const TcLayer& L, int B, bool proj = false);
@@ -2441,11 +2453,14 @@ int bf16_add_layer(Bf16Net& bf, int ci, int co, int k, int s, Dims3 din, long lo
   if (k == 3 && s == 2 && (ci == 16 || ci == 32 || ci == 64) && co % 16 == 0 && co <= 256)
     L.wgrad = L.wgs2 = true;
   L.s2p = L.dgrad && s == 2 && k == 3 && 8 * ci <= 256;
+  // the per-tap forward (stride 2) folded where [hi | lo] rows take a wider channel chunk
+  if (k == 3 && s == 2 && bf16_fold_pays(bf, ci, co)) L.hlf = true;
   const long long n = (long long)co * k * k * k * ci * bf.sp;
   const long long n4 = (long long)co * k * k * k * ci * 4;  // the doubled [2 co][2 ci] rows
   const long long n64 = (long long)co * 64 * ci * bf.sp;    // 8 x 8 window-class blocks
   L.wf_off = bf.wstride;
-  bf.wstride += ((L.hlf ? n4 : n) + 63) / 64 * 64;
+  // (a 1x1 layer keeps room for the doubled rows: a projection run on its own folds)
+  bf.wstride += ((L.hlf || (k == 1 && bf.sp == 3) ? n4 : n) + 63) / 64 * 64;
   if (L.dgrad) {
     L.wd_off = bf.wstride;
     bf.wstride += ((L.hld ? n4 : L.s2p ? n64 : n) + 63) / 64 * 64;
@@ -2599,10 +2614,15 @@ cudaError_t bf16_finalize(Bf16Net& bf, int B) {
       if (e != cudaSuccess) return e;
       continue;
     }
-    cudaError_t e = encode_act(&L.act_f, L.xin, B, L.din, L.kf, chunk_for(L.kf), L.s);
+    // per-tap forward; folded (hlf without the halo form): the first 2 ci channels of each
+    // staged row against the doubled [2 co][2 ci] weights
+    const bool fold = L.hlf && !L.ck3f;
+    const int kff = fold ? 2 * L.ci : L.kf;
+    cudaError_t e = encode_act(&L.act_f, L.xin, B, L.din, kff, chunk_for(kff), L.s,
+                               fold ? L.kf : 0);
     if (e == cudaSuccess)
-      e = encode_w(&L.w_f, bf.wbuf + L.wf_off, B, bf.wstride, L.kf, T, L.co, chunk_for(L.kf), 1,
-                   1);
+      e = encode_w(&L.w_f, bf.wbuf + L.wf_off, B, bf.wstride, kff, T, fold ? 2 * L.co : L.co,
+                   chunk_for(kff), 1, 1);
     if (e == cudaSuccess && L.dgrad) {
       e = encode_act(&L.act_d, dy_buf(bf, L), B, L.dout, L.kd, chunk_for(L.kd), 1);
       if (e == cudaSuccess && L.s2p)  // [window][class x ci][kd]: one box per window
@@ -3175,7 +3195,10 @@ int bf16_fuse_proj(Bf16Net& bf, int la, int lp) {
   }
   if (A.ck3d && P.dgrad) A.projd = A.per3d;  // the dz_p stage rides the persistent dgrad
   A.projw = A.wg3 && wg3_geom(A, 1, true).nst > 0;
-  if (!A.projf && P.kf == A.kf) P.xin_of = la;  // its own launch over la's staged input
+  if (!A.projf && P.kf == A.kf) {  // its own launch over la's staged input
+    P.xin_of = la;
+    P.hlf = bf16_fold_pays(bf, P.ci, P.co);
+  }
   return (A.projf ? 1 : 0) | (A.projd ? 2 : 0) | (A.projw ? 4 : 0);
 }
 
@@ -3389,9 +3412,11 @@ cudaError_t bf16_conv_fwd(Bf16Net& bf, int layer, const float* x, const float* b
     return launch_tc3(L.act_f3, L.w_f3, L.kf3, L.ck3f, L.tz3f, L.pack3f, L.per3f, bias, y,
                       L.dout, L.nf3, B, L.dout.count() * L.co, bias_bs, 0, bf.err, stream, 0,
                       nullptr, nullptr, 0, nullptr, nullptr, 0, nullptr, L.hlf ? 1 : 0);
-  const TapPlan plan = conv_plan(L.k, L.s);
-  return launch_tc(L.act_f, L.w_f, plan, 1, L.kf, bias, y, L.dout, L.dout, L.co, B,
-                   L.dout.count() * L.co, bias_bs, 0, bf.err, stream);
+  TapPlan plan = conv_plan(L.k, L.s);
+  plan.fold = L.hlf ? 1 : 0;  // (no halo form here)
+  return launch_tc(L.act_f, L.w_f, plan, 1, L.hlf ? 2 * L.ci : L.kf, bias, y, L.dout, L.dout,
+                   L.hlf ? 2 * L.co : L.co, B, L.dout.count() * L.co, bias_bs, 0, bf.err,
+                   stream);
 }
 
 cudaError_t bf16_conv_dgrad(Bf16Net& bf, int layer, const float* dy, float* dx, int B,
