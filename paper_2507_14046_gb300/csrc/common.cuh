@@ -91,7 +91,7 @@ cudaError_t layernorm_act_bwd_f32(const float* dy, const float* act_out, const f
                                   __nv_bfloat16* dtbf = nullptr, int sp = 1);
 
 // cat[:, :Cu] = trilinear(low -> dout), cat[:, Cu:] = skip; catbf (optional): a BF16 copy in
-// sp blocks per voxel.
+// sp blocks per voxel.  cat may be null when catbf is set (only the BF16 copy is written).
 cudaError_t upsample_concat_fwd_f32(const float* low, const float* skip, float* cat, int B,
                                     Dims3 dlow, Dims3 dout, int Cu, int Cs,
                                     cudaStream_t stream, __nv_bfloat16* catbf = nullptr,

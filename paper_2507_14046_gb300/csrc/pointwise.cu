@@ -219,7 +219,7 @@ __global__ void up_concat_fwd_kernel(const float* __restrict__ low,
           val.w += w * v.w;
         }
   }
-  *reinterpret_cast<float4*>(cat + ((long long)b * nout + vox) * Ct + c) = val;
+  if (cat) *reinterpret_cast<float4*>(cat + ((long long)b * nout + vox) * Ct + c) = val;
   if (catbf) stage_bf16x4(catbf + ((long long)b * nout + vox) * Ct * sp, Ct, c, val, sp);
 }
 
@@ -243,11 +243,11 @@ up2_concat_fwd_kernel(const float* __restrict__ low, const float* __restrict__ s
   const int rr = (int)(vox / dl.x);
   const int iy = rr % dl.y, iz = rr / dl.y;
   const long long nout = dout.count();
-  float* C = cat + (long long)b * nout * Ct + c;
+  float* C = cat ? cat + (long long)b * nout * Ct + c : nullptr;
   __nv_bfloat16* Cb = catbf ? catbf + (long long)b * nout * Ct * sp : nullptr;
   auto put = [&](int a, int bb, int cc, float4 v) {
     const long long o = ((long long)(2 * iz + a) * dout.y + (2 * iy + bb)) * dout.x + (2 * ix + cc);
-    *reinterpret_cast<float4*>(C + o * Ct) = v;
+    if (C) *reinterpret_cast<float4*>(C + o * Ct) = v;
     if (Cb) stage_bf16x4(Cb + o * Ct * sp, Ct, c, v, sp);
   };
   if (c >= Cu) {  // skip channels of the 8 outputs
@@ -434,6 +434,77 @@ __global__ void __launch_bounds__(256) up2_bwd_kernel(const float* __restrict__ 
   float* O = dlow + ((long long)b * dl.count() + ((long long)iz * dl.y + iy) * dl.x + ix0) * Cu + c;
   *reinterpret_cast<float4*>(O) = A;
   if (two) *reinterpret_cast<float4*>(O + Cu) = Bv;
+}
+
+// The same factor-2 adjoint through shared memory: a CTA takes 8 x 4 x 2 low voxels and 8
+// channels, loads the 18 x 10 x 6 output voxels they read (zeros outside the grid), and
+// applies the transposed stencil one axis at a time (z, then y, then x).  Each output value
+// is read about twice instead of eight times, and a low value costs 4 + 4 + 4 weighted taps
+// per staged line instead of 64 scattered loads.
+constexpr int kU2X = 8, kU2Y = 4, kU2Z = 2;
+__device__ __forceinline__ float up2_adj_w(int i, int n, int a) {  // tap a: output 2i - 1 + a
+  return a == 0 ? (i >= 1 ? 0.25f : 0.f)
+       : a == 1 ? (i == 0 ? 1.f : 0.75f)
+       : a == 2 ? (i == n - 1 ? 1.f : 0.75f)
+                : (i <= n - 2 ? 0.25f : 0.f);
+}
+__device__ __forceinline__ void fma4(float4& o, float w, const float4& v) {
+  o.x = fmaf(w, v.x, o.x), o.y = fmaf(w, v.y, o.y), o.z = fmaf(w, v.z, o.z), o.w = fmaf(w, v.w, o.w);
+}
+
+__global__ void __launch_bounds__(256) up2_bwd_tile_kernel(const float* __restrict__ dcat,
+                                                           float* __restrict__ dlow, Dims3 dl,
+                                                           Dims3 dout, int Cu, int Ct) {
+  constexpr int FX = 2 * kU2X + 2, FY = 2 * kU2Y + 2, FZ = 2 * kU2Z + 2;
+  __shared__ float4 F[FZ][FY][FX][2];   // output tile (8 channels: two float4)
+  __shared__ float4 T1[kU2Z][FY][FX][2];  // after the z pass
+  float4 (*T2)[kU2Y][FX][2] = reinterpret_cast<float4 (*)[kU2Y][FX][2]>(&F[0][0][0][0]);
+  const int b = blockIdx.y;
+  const int ncg = Cu / 8;
+  const int cg = blockIdx.x % ncg, tile = blockIdx.x / ncg;  // channel groups of a tile adjacent
+  const int tx = (dl.x + kU2X - 1) / kU2X, ty = (dl.y + kU2Y - 1) / kU2Y;
+  const int lx0 = (tile % tx) * kU2X, ly0 = ((tile / tx) % ty) * kU2Y,
+            lz0 = (tile / (tx * ty)) * kU2Z;
+  const int c0 = cg * 8;
+  const float* D = dcat + (long long)b * dout.count() * Ct + c0;
+  for (int e = threadIdx.x; e < FZ * FY * FX * 2; e += blockDim.x) {
+    const int h = e & 1, fx = (e >> 1) % FX, fy = (e >> 1) / FX % FY, fz = (e >> 1) / (FX * FY);
+    const int ox = 2 * lx0 - 1 + fx, oy = 2 * ly0 - 1 + fy, oz = 2 * lz0 - 1 + fz;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ox >= 0 && ox < dout.x && oy >= 0 && oy < dout.y && oz >= 0 && oz < dout.z)
+      v = *reinterpret_cast<const float4*>(
+          D + (((long long)oz * dout.y + oy) * dout.x + ox) * Ct + 4 * h);
+    F[fz][fy][fx][h] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kU2Z * FY * FX * 2; e += blockDim.x) {  // z
+    const int h = e & 1, fx = (e >> 1) % FX, fy = (e >> 1) / FX % FY, lz = (e >> 1) / (FX * FY);
+    float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) fma4(o, up2_adj_w(lz0 + lz, dl.z, a), F[2 * lz + a][fy][fx][h]);
+    T1[lz][fy][fx][h] = o;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kU2Z * kU2Y * FX * 2; e += blockDim.x) {  // y (into F's space)
+    const int h = e & 1, fx = (e >> 1) % FX, ly = (e >> 1) / FX % kU2Y, lz = (e >> 1) / (FX * kU2Y);
+    float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) fma4(o, up2_adj_w(ly0 + ly, dl.y, a), T1[lz][2 * ly + a][fx][h]);
+    T2[lz][ly][fx][h] = o;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kU2Z * kU2Y * kU2X * 2; e += blockDim.x) {  // x, then store
+    const int h = e & 1, lx = (e >> 1) % kU2X, ly = (e >> 1) / kU2X % kU2Y,
+              lz = (e >> 1) / (kU2X * kU2Y);
+    const int ix = lx0 + lx, iy = ly0 + ly, iz = lz0 + lz;
+    if (ix >= dl.x || iy >= dl.y || iz >= dl.z) continue;
+    float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) fma4(o, up2_adj_w(ix, dl.x, a), T2[lz][ly][2 * lx + a][h]);
+    *reinterpret_cast<float4*>(
+        dlow + ((long long)b * dl.count() + ((long long)iz * dl.y + iy) * dl.x + ix) * Cu + c0 +
+        4 * h) = o;
+  }
 }
 
 __global__ void split_skip_kernel(const float* __restrict__ dcat, float* __restrict__ dskip,
@@ -844,7 +915,7 @@ cudaError_t layernorm_act_bwd_f32(const float* dy, const float* act_out, const f
 cudaError_t upsample_concat_fwd_f32(const float* low, const float* skip, float* cat, int B,
                                     Dims3 dlow, Dims3 dout, int Cu, int Cs,
                                     cudaStream_t stream, __nv_bfloat16* catbf, int sp) {
-  if (Cu % 4 || Cs % 4) return cudaErrorInvalidValue;
+  if (Cu % 4 || Cs % 4 || (!cat && !catbf)) return cudaErrorInvalidValue;
   const long long total = dout.count() * ((Cu + Cs) / 4);
   dim3 grid((unsigned)ceil_div(total, 256), B);
   if (dout.x == 2 * dlow.x && dout.y == 2 * dlow.y && dout.z == 2 * dlow.z) {
@@ -861,7 +932,14 @@ cudaError_t upsample_concat_bwd_f32(const float* dcat, float* dlow, float* dskip
                                     Dims3 dlow_dims, Dims3 dout, int Cu, int Cs,
                                     cudaStream_t stream) {
   if (Cu % 4 || Cs % 4) return cudaErrorInvalidValue;
-  if (dout.x == 2 * dlow_dims.x && dout.y == 2 * dlow_dims.y && dout.z == 2 * dlow_dims.z) {
+  if (dout.x == 2 * dlow_dims.x && dout.y == 2 * dlow_dims.y && dout.z == 2 * dlow_dims.z &&
+      Cu % 8 == 0) {
+    const long long tiles = ceil_div(dlow_dims.x, kU2X) * ceil_div(dlow_dims.y, kU2Y) *
+                            ceil_div(dlow_dims.z, kU2Z);
+    dim3 g2((unsigned)(tiles * (Cu / 8)), B);
+    up2_bwd_tile_kernel<<<g2, 256, 0, stream>>>(dcat, dlow, dlow_dims, dout, Cu, Cu + Cs);
+  } else if (dout.x == 2 * dlow_dims.x && dout.y == 2 * dlow_dims.y &&
+             dout.z == 2 * dlow_dims.z) {
     const long long pairs = (long long)dlow_dims.z * dlow_dims.y * ((dlow_dims.x + 1) / 2);
     dim3 g2((unsigned)ceil_div(pairs * (Cu / 4), 256), B);
     up2_bwd_kernel<<<g2, 256, 0, stream>>>(dcat, dlow, dlow_dims, dout, Cu, Cs);

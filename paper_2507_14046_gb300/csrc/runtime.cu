@@ -280,6 +280,16 @@ bool tc_wgrad(const d2ip_ctx* c, const ConvL& L) {
   return L.tc >= 0 && L.k == 3 && c->bf.layers[L.tc].wgrad;
 }
 
+// Whether every reader of a residual block's input takes its BF16 staged copy: conv a and
+// its projection on the tensor cores (the projection fused, or reading conv a's kept copy),
+// both weight gradients there too, and the residual taken from the projection.
+bool bf16_only_input(const d2ip_ctx* c, const Res& R) {
+  if (c->precision == D2IP_FP32 || !c->bf.keep_inputs || R.a.tc < 0 || !R.proj || R.p.tc < 0)
+    return false;
+  const bool p_fwd = R.fuse_f || bf16_input_shared(c->bf, R.p.tc);
+  return p_fwd && tc_wgrad(c, R.a) && (R.fuse_w || tc_wgrad(c, R.p));
+}
+
 // The last layer (1x1x1 to one channel) has its own memory-bound kernels.
 bool co1_layer(const ConvL& L) {
   return L.k == 1 && L.s == 1 && L.co == 1 && conv1x1_co1_supported(L.ci);
@@ -670,14 +680,19 @@ struct Launcher {
     }
     const float* cur = c->enc[c->L - 1].out;
     for (int l = c->L - 2; l >= 0; --l) {
-      const double bytes = 4.0 * c->B *
-                           ((double)c->dims[l + 1].count() * c->w[l + 1] +
-                            2.0 * c->dims[l].count() * c->w[l] +
-                            (double)c->dims[l].count() * c->w[l + 1]);
-      beg(D2IP_KCLASS_UP_FWD, bytes);
       __nv_bfloat16* catbf = bf_in(&c->dec[l].a);
-      ok(upsample_concat_fwd_f32(cur, c->enc[l].out, c->lb[l].cat, c->B, c->dims[l + 1],
-                                 c->dims[l], c->w[l + 1], c->w[l], c->stream, catbf, c->bf.sp));
+      // the FP32 concatenation only where a consumer reads it (not the tensor-core block
+      // whose layers all take the BF16 copy)
+      const bool cat32 = !catbf || !bf16_only_input(c, c->dec[l]);
+      const double fine = (double)c->dims[l].count() * (c->w[l] + c->w[l + 1]);
+      const double bytes = c->B * (4.0 * ((double)c->dims[l + 1].count() * c->w[l + 1] +
+                                          (double)c->dims[l].count() * c->w[l]) +
+                                   (cat32 ? 4.0 * fine : 0.0) +
+                                   (catbf ? 2.0 * c->bf.sp * fine : 0.0));
+      beg(D2IP_KCLASS_UP_FWD, bytes);
+      ok(upsample_concat_fwd_f32(cur, c->enc[l].out, cat32 ? c->lb[l].cat : nullptr, c->B,
+                                 c->dims[l + 1], c->dims[l], c->w[l + 1], c->w[l], c->stream,
+                                 catbf, c->bf.sp));
       if (catbf) staged_x.push_back(&c->dec[l].a);
       fin();
       res_fwd(c->dec[l], nullptr);

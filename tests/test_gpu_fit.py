@@ -118,14 +118,22 @@ def test_sequence_matches_oracle_and_manual_chaining(d2ip):
                            first, later, lr)
     c = _ctx(d2ip, pb, lr)
     Sig, res = c.fit_sequence(pb.V[None], up, first, later)
+    # the residual follows the trajectory's FP32 drift: its own sensitivity, measured by the
+    # same fit from theta0 (1 + 1e-7 sin(index)), sets its bar (at least 1e-2)
+    pert = _ctx(d2ip, pb, lr)
+    idx = np.arange(pb.theta0.size)
+    pert.set_input(pb.Zin[None], (pb.theta0 * (1 + 1e-7 * np.sin(idx))).astype(np.float32)[None])
+    _, res_p = pert.fit_sequence(pb.V[None], up, first, later)
     for i in range(4):
         if np.abs(pb.truth[i]).max() == 0:
             continue
         e_gpu = dip.err_ratio(Sig[0, i], pb.truth[i])
         e_ref = dip.err_ratio(ref.Sigma[i], pb.truth[i])
         assert abs(e_gpu - e_ref) <= 1e-3 * e_ref, i
-        # the residual is reported, not gated: it follows the trajectory's FP32 drift
-        assert abs(res[0, i] - ref.residuals[i]) <= 1e-2 * ref.residuals[i]
+        floor = abs(res_p[0, i] - res[0, i]) / res[0, i]
+        print("frame", i, "residual rel. gap", abs(res[0, i] - ref.residuals[i]) /
+              ref.residuals[i], "FP32 floor", floor)
+        assert abs(res[0, i] - ref.residuals[i]) <= max(1e-2, 3 * floor) * ref.residuals[i]
     # the same schedule chained by hand through the frame API is bit-identical
     c2 = _ctx(d2ip, pb, lr)
     c2.run_steps(pb.V[:1], up)
