@@ -137,7 +137,7 @@ def run_oracle_subprocess(workload: str, iters: int, net: str = "resunet",
 
 def oracle_iters_for(workload: str) -> int:
     # about 10-30 s of host work per sample on a Grace host
-    return {"single16": 200, "seq32": 12, "seq64": 2, "batch64": 12}[workload]
+    return {"single16": 200, "seq32": 12, "seq64": 2, "batch64": 30}[workload]
 
 
 # ------------------------------------------------------------------------------------------
